@@ -1,0 +1,335 @@
+"""Oracle primal-dual filter line-search interior-point method (FP64, TEST ONLY).
+
+Follows Section 2 of the paper: problem (2) with slacks h(x) + s = 0, s >= 0,
+the barrier system F_mu = 0 (Eq. (5)), Newton steps from the augmented system
+(K_2) solved in condensed form (K_1) by LiftedKKT (Section 3.2) or HyKKT
+(Section 3.1), and a step that keeps (x, s, v) strictly interior.  The paper
+leaves the line search, barrier update and inertia correction to Ipopt
+(Waechter & Biegler 2006, cited in Section 2.2); their published constants are
+used and written out below.  Variable bounds xl <= x <= xu are handled as in
+Ipopt by bound multipliers (zl, zu) that are eliminated into
+Sigma_x = Zl (X - Xl)^{-1} + Zu (Xu - X)^{-1} on the diagonal of K.
+
+A model provides: n, m_e, m_i, xl, xu, x0(), objective, grad, cons -> (g, h),
+jacobian -> CSR [G; H] with a fixed pattern, hessian(x, y, z, sigma_f) -> full
+symmetric CSR with a fixed pattern.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import kkt as K
+
+# Ipopt constants (Waechter & Biegler 2006)
+KAPPA1 = KAPPA2 = 1e-2      # initial push into the bounds
+KAPPA_EPS = 10.0            # barrier stop test E_mu <= kappa_eps mu
+KAPPA_MU, THETA_MU = 0.2, 1.5
+TAU_MIN = 0.99
+S_MAX = 100.0
+GAMMA_THETA, GAMMA_PHI = 1e-5, 1e-8
+S_THETA, S_PHI, DELTA = 1.1, 2.3, 1.0
+ETA_PHI = 1e-8
+GAMMA_ALPHA = 0.05
+KAPPA_SIGMA = 1e10
+
+
+@dataclasses.dataclass
+class Options:
+    kkt: str = "lifted"          # "lifted" | "hykkt"
+    tol: float = 1e-6
+    gamma: float = 1e6           # HyKKT
+    tau: float | None = None     # LiftedKKT relaxation; None -> tol
+    max_iter: int = 3000
+    mu0: float = 0.1
+    cg_rtol: float = 1e-10
+    max_refine: int = 10
+    verbose: bool = False
+
+
+class RelaxedModel:
+    """LiftedKKT problem (12): -tau <= g(x) <= tau written as two inequality
+    rows g - tau <= 0 and -g - tau <= 0 in front of h <= 0."""
+
+    def __init__(self, base, tau):
+        self.base, self.tau = base, tau
+        self.n, self.m_e, self.m_i = base.n, 0, 2 * base.m_e + base.m_i
+        self.xl, self.xu = base.xl, base.xu
+
+    def x0(self):
+        return self.base.x0()
+
+    def objective(self, x):
+        return self.base.objective(x)
+
+    def grad(self, x):
+        return self.base.grad(x)
+
+    def cons(self, x):
+        g, h = self.base.cons(x)
+        return np.zeros(0), np.concatenate([g - self.tau, -g - self.tau, h])
+
+    def jacobian(self, x):
+        J = self.base.jacobian(x)
+        me = self.base.m_e
+        G, H = J[:me], J[me:]
+        return sp.vstack([G, -G, H]).tocsr()
+
+    def hessian(self, x, y, z, sigma_f=1.0):
+        me = self.base.m_e
+        return self.base.hessian(x, z[:me] - z[me:2 * me], z[2 * me:], sigma_f)
+
+
+class ScaledModel:
+    """Ipopt's gradient-based scaling of the constraint rows: row i is multiplied
+    by min(1, 100 / ||grad c_i(x0)||_inf), computed once at the starting point."""
+
+    def __init__(self, base, x0):
+        self.base = base
+        self.n, self.m_e, self.m_i = base.n, base.m_e, base.m_i
+        self.xl, self.xu = base.xl, base.xu
+        J = sp.csr_matrix(abs(base.jacobian(x0)))
+        rmax = np.zeros(J.shape[0])
+        nz = np.diff(J.indptr) > 0
+        rmax[nz] = np.maximum.reduceat(J.data, J.indptr[:-1][nz])
+        self.d = np.minimum(1.0, 100.0 / np.maximum(rmax, 1e-300))
+        self.de, self.di = self.d[:base.m_e], self.d[base.m_e:]
+
+    def x0(self):
+        return self.base.x0()
+
+    def objective(self, x):
+        return self.base.objective(x)
+
+    def grad(self, x):
+        return self.base.grad(x)
+
+    def cons(self, x):
+        g, h = self.base.cons(x)
+        return g * self.de, h * self.di
+
+    def jacobian(self, x):
+        return sp.diags(self.d) @ self.base.jacobian(x)
+
+    def hessian(self, x, y, z, sigma_f=1.0):
+        return self.base.hessian(x, y * self.de, z * self.di, sigma_f)
+
+
+@dataclasses.dataclass
+class Result:
+    status: str
+    iters: int
+    x: np.ndarray
+    s: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    v: np.ndarray
+    zl: np.ndarray
+    zu: np.ndarray
+    obj: float
+    kkt_error: float
+    mu: float
+    history: list
+
+
+def _push(x, xl, xu):
+    """Initial point moved strictly inside the bounds (Ipopt bound push)."""
+    hl, hu = np.isfinite(xl), np.isfinite(xu)
+    x = x.copy()
+    both = hl & hu
+    pl = np.where(hl, KAPPA1 * np.maximum(1.0, np.abs(np.where(hl, xl, 0.0))), 0.0)
+    pu = np.where(hu, KAPPA1 * np.maximum(1.0, np.abs(np.where(hu, xu, 0.0))), 0.0)
+    width = np.where(both, xu - xl, np.inf)
+    pl = np.where(both, np.minimum(pl, KAPPA2 * width), pl)
+    pu = np.where(both, np.minimum(pu, KAPPA2 * width), pu)
+    x = np.where(hl, np.maximum(x, np.where(hl, xl, 0.0) + pl), x)
+    x = np.where(hu, np.minimum(x, np.where(hu, xu, 0.0) - pu), x)
+    return x
+
+
+def solve(model, opt: Options | None = None, x0=None):
+    opt = opt or Options()
+    base = model
+    model = ScaledModel(base, _push(base.x0() if x0 is None else x0, base.xl, base.xu))
+    if opt.kkt == "lifted":
+        model = RelaxedModel(model, opt.tau if opt.tau is not None else opt.tol)
+    n, me, mi = model.n, model.m_e, model.m_i
+    xl, xu = model.xl, model.xu
+    hl, hu = np.isfinite(xl), np.isfinite(xu)
+    xlf, xuf = np.where(hl, xl, 0.0), np.where(hu, xu, 0.0)
+    x = _push(model.x0() if x0 is None else x0, xl, xu)
+    sig_f = min(1.0, 100.0 / max(np.abs(model.grad(x)).max(), 1e-300))
+    g, h = model.cons(x)
+    s = np.maximum(-h, KAPPA1)
+    y = np.zeros(me)
+    z = np.ones(mi)
+    v = np.ones(mi)
+    zl = np.where(hl, 1.0, 0.0)
+    zu = np.where(hu, 1.0, 0.0)
+    mu = opt.mu0
+    tau = max(TAU_MIN, 1.0 - mu)
+    nl, nu = int(hl.sum()), int(hu.sum())
+
+    J = model.jacobian(x)
+    W = model.hessian(x, y, z, sig_f)
+    solver = K.CondensedSolver(W, J)
+    filt = []
+    delta_last = 0.0
+    hist = []
+    theta0 = None
+
+    def theta_of(gx, hx, sx):
+        return float(np.abs(gx).sum() + np.abs(hx + sx).sum())
+
+    def phi_of(xx, sx, mu_):
+        val = sig_f * model.objective(xx) - mu_ * np.log(sx).sum()
+        val -= mu_ * np.log((xx - xlf)[hl]).sum() + mu_ * np.log((xuf - xx)[hu]).sum()
+        return float(val)
+
+    def errors(gradf, J, g, h, mu_):
+        G, H = J[:me], J[me:]
+        gl = gradf * sig_f + G.T @ y + H.T @ z - zl + zu
+        sd = max(S_MAX, (np.abs(y).sum() + np.abs(z).sum() + np.abs(v).sum() + np.abs(zl).sum()
+                         + np.abs(zu).sum()) / max(me + 2 * mi + nl + nu, 1)) / S_MAX
+        sc = max(S_MAX, (np.abs(v).sum() + np.abs(zl).sum() + np.abs(zu).sum())
+                 / max(mi + nl + nu, 1)) / S_MAX
+        dual = max(np.abs(gl).max(initial=0.0), np.abs(z - v).max(initial=0.0)) / sd
+        prim = max(np.abs(g).max(initial=0.0), np.abs(h + s).max(initial=0.0))
+        comp = max(np.abs(s * v - mu_).max(initial=0.0),
+                   np.abs(((x - xlf) * zl - mu_)[hl]).max(initial=0.0),
+                   np.abs(((xuf - x) * zu - mu_)[hu]).max(initial=0.0)) / sc
+        return max(dual, prim, comp)
+
+    status = "max_iter"
+    it = 0
+    for it in range(opt.max_iter + 1):
+        g, h = model.cons(x)
+        gradf = model.grad(x)
+        J = model.jacobian(x)
+        e0 = errors(gradf, J, g, h, 0.0)
+        if theta0 is None:
+            theta0 = theta_of(g, h, s)
+            theta_max = 1e4 * max(1.0, theta0)
+            theta_min = 1e-4 * max(1.0, theta0)
+        if e0 <= opt.tol:
+            status = "converged"
+            break
+        if it == opt.max_iter:
+            break
+        first = True
+        while errors(gradf, J, g, h, mu) <= KAPPA_EPS * mu and (first or it == 0):
+            mu = max(opt.tol / 10.0, min(KAPPA_MU * mu, mu ** THETA_MU))
+            tau = max(TAU_MIN, 1.0 - mu)
+            filt = []
+            first = False
+        W = model.hessian(x, y, z, sig_f)
+        G, H = J[:me], J[me:]
+        dxl = np.where(hl, x - xlf, 1.0)
+        dxu = np.where(hu, xuf - x, 1.0)
+        sigma_x = np.where(hl, zl / dxl, 0.0) + np.where(hu, zu / dxu, 0.0)
+        Ds = v / s
+        r1 = sig_f * gradf + G.T @ y + H.T @ z - np.where(hl, mu / dxl, 0.0) + np.where(hu, mu / dxu, 0.0)
+        r2 = z - mu / s
+        r3 = g
+        r4 = h + s
+
+        def kmat(dw):
+            dh = Ds + dw
+            d = np.concatenate([np.full(me, opt.gamma), dh]) if opt.kkt == "hykkt" else dh
+            return K.condensed_matrix(W, sigma_x, J, d, dw)
+
+        dw, F, nfac = K.inertia_schedule(kmat, solver, delta_last)
+        if dw > 0:
+            delta_last = dw
+        dh = Ds + dw
+        a = -r1
+        bH = -r4 + r2 / dh
+        cg_its = 0
+        if opt.kkt == "hykkt":
+            b = np.concatenate([-r3, bH])
+            dx, dy, dz, cg_its, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, opt.gamma, a, b,
+                                                   rtol=opt.cg_rtol)
+            eta = K.backward_error(K.aug_matrix(W, sigma_x, J, dh, me, dw),
+                                   np.concatenate([dx, dy, dz]), np.concatenate([a, b]))
+        else:
+            A = K.aug_matrix(W, sigma_x, J, dh, 0, dw)
+            dx, dz, eh = K.lifted_solve(F, A, J, dh, a, bH, max_refine=opt.max_refine)
+            dy = np.zeros(0)
+            eta = eh[-1]
+        ds = -(r2 + dz) / dh
+        dv = (mu - v * ds) / s - v
+        dzl = np.where(hl, mu / dxl - zl - zl / dxl * dx, 0.0)
+        dzu = np.where(hu, mu / dxu - zu + zu / dxu * dx, 0.0)
+
+        # fraction to the boundary
+        def ftb(val, dval):
+            neg = dval < 0
+            if not neg.any():
+                return 1.0
+            return float(min(1.0, np.min(-tau * val[neg] / dval[neg])))
+
+        amax = min(ftb(x[hl] - xl[hl], dx[hl]), ftb(xu[hu] - x[hu], -dx[hu]), ftb(s, ds))
+        az = min(ftb(v, dv), ftb(zl[hl], dzl[hl]), ftb(zu[hu], dzu[hu]))
+
+        theta = theta_of(g, h, s)
+        phi = phi_of(x, s, mu)
+        gphi = (sig_f * gradf @ dx - mu * np.sum(ds / s) - mu * np.sum((dx / dxl)[hl])
+                + mu * np.sum((dx / dxu)[hu]))
+        if gphi < 0:
+            amin = GAMMA_ALPHA * min(GAMMA_THETA, GAMMA_PHI * theta / -gphi,
+                                     DELTA * theta ** S_THETA / (-gphi) ** S_PHI)
+        else:
+            amin = GAMMA_ALPHA * GAMMA_THETA
+        alpha = amax
+        accepted = False
+        ls = 0
+        while True:
+            xt = x + alpha * dx
+            st = s + alpha * ds
+            gt, ht = model.cons(xt)
+            tht = theta_of(gt, ht, st)
+            pht = phi_of(xt, st, mu)
+            ok_f = tht < theta_max and all(tht < tf or pht < pf for tf, pf in filt)
+            if ok_f and np.isfinite(pht):
+                switching = gphi < 0 and alpha * (-gphi) ** S_PHI > DELTA * theta ** S_THETA
+                if switching and theta <= theta_min:
+                    if pht <= phi + ETA_PHI * alpha * gphi:
+                        accepted, ftype = True, True
+                elif tht <= (1 - GAMMA_THETA) * theta or pht <= phi - GAMMA_PHI * theta:
+                    accepted, ftype = True, False
+            if accepted:
+                break
+            ls += 1
+            alpha *= 0.5
+            if alpha < amin:
+                break
+        if not accepted:
+            status = "restoration_needed"
+            break
+        if not ftype:
+            filt.append(((1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta))
+        x = xt
+        s = st
+        y = y + alpha * dy
+        z = z + alpha * dz
+        v = v + az * dv
+        zl = zl + az * dzl
+        zu = zu + az * dzu
+        # bound-multiplier safeguard (Ipopt Eq. (16))
+        dxl = np.where(hl, x - xlf, 1.0)
+        dxu = np.where(hu, xuf - x, 1.0)
+        zl = np.where(hl, np.clip(zl, mu / (KAPPA_SIGMA * dxl), KAPPA_SIGMA * mu / dxl), 0.0)
+        zu = np.where(hu, np.clip(zu, mu / (KAPPA_SIGMA * dxu), KAPPA_SIGMA * mu / dxu), 0.0)
+        v = np.clip(v, mu / (KAPPA_SIGMA * s), KAPPA_SIGMA * mu / s)
+        hist.append(dict(k=it, mu=mu, e0=e0, alpha=alpha, delta_w=dw, nfac=nfac, cg=cg_its,
+                         eta=eta, ls=ls, obj=model.objective(x)))
+        if opt.verbose:
+            print(f"{it:4d} mu={mu:.1e} E0={e0:.2e} a={alpha:.2e} dw={dw:.1e} cg={cg_its} eta={eta:.1e}")
+    g, h = model.cons(x)
+    J = model.jacobian(x)
+    return Result(status=status, iters=it, x=x, s=s, y=y, z=z, v=v, zl=zl, zu=zu,
+                  obj=base.objective(x), kkt_error=errors(model.grad(x), J, g, h, 0.0), mu=mu,
+                  history=hist)

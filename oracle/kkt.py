@@ -1,0 +1,170 @@
+"""Oracle KKT solves in FP64 (TEST INFRASTRUCTURE ONLY).
+
+Notation follows Section 2.2 and Section 3 of the paper.  J = [G; H] stacks the
+m_e equality rows G over the m_i inequality rows H.  With the slack block of the
+augmented system (K_2) eliminated (it is diagonal: D_s + delta_w I), what remains
+is the augmented system
+
+    [ W + Sigma_x + delta_w I   G^T    H^T      ] [dx]   [a  ]
+    [ G                          0      0        ] [dy] = [b_G]          (AUG)
+    [ H                          0   -D_H^{-1}   ] [dz]   [b_H]
+
+with D_H = D_s + delta_w (delta_c = 0, so C = I in Eq. (K_1)).  Eliminating dz
+gives the condensed system (K_1):
+    K dx + G^T dy = a + H^T D_H b_H,   G dx = b_G,   K = W + Sigma_x + delta_w I + H^T D_H H,
+and dz = D_H (H dx - b_H).
+
+* LiftedKKT (Section 3.2, Eq. (12)-(13)): every row is an inequality (the
+  equalities relaxed to -tau <= g <= tau), so m_e = 0 and K_tau dx = a + J^T D b.
+  Iterative refinement (Richardson) runs on (AUG) in FP64 (Section 2.2,
+  "Iterative refinement"; Section 3.2 last paragraph).
+* HyKKT (Section 3.1, Eq. (9)-(10)): K_gamma = K + gamma G^T G is factored by
+  Cholesky and the Schur system (G K_gamma^{-1} G^T) dy = G K_gamma^{-1}
+  (r1bar + gamma G^T r2bar) - r2bar is solved by CG; then
+  K_gamma dx = r1bar + gamma G^T r2bar - G^T dy.
+
+Readings where the paper is silent (also listed in the design notes):
+  CG starts at dy = 0 and stops when ||r_k||_2 <= max(rtol ||r_0||_2, atol);
+  refinement stops at backward error <= 1e-10, when the error stops halving,
+  or after 10 steps.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .sparse import Symbolic, Cholesky, condensed_pattern
+
+
+def lower(W: sp.spmatrix) -> sp.csr_matrix:
+    return sp.tril(sp.csr_matrix(W), format="csr")
+
+
+def full_from_lower(Wl: sp.spmatrix) -> sp.csr_matrix:
+    Wl = sp.csr_matrix(Wl)
+    return (Wl + sp.tril(Wl, -1).T).tocsr()
+
+
+def condensed_matrix(W, sigma_x, J, d, delta_w):
+    """K = W + diag(sigma_x + delta_w) + J^T diag(d) J  (Eq. (K_1), (9), (13))."""
+    n = J.shape[1]
+    K = W + sp.diags(sigma_x + delta_w) + J.T @ sp.diags(d) @ J
+    K = sp.csr_matrix(K)
+    K.sum_duplicates()
+    return K
+
+
+def aug_matrix(W, sigma_x, J, d_h, m_e, delta_w):
+    """The augmented matrix (AUG) above, rows/cols ordered (x, y, z)."""
+    n = J.shape[1]
+    m = J.shape[0]
+    E = np.zeros(m)
+    E[m_e:] = -1.0 / d_h
+    top = sp.hstack([W + sp.diags(sigma_x + delta_w), J.T])
+    bot = sp.hstack([J, sp.diags(E)])
+    return sp.vstack([top, bot]).tocsr()
+
+
+def backward_error(A, sol, rhs) -> float:
+    """eta = ||A sol - rhs||_inf / (||A||_inf ||sol||_inf + ||rhs||_inf)."""
+    r = A @ sol - rhs
+    nA = abs(A).sum(axis=1).max()
+    return float(np.abs(r).max() / (nA * np.abs(sol).max() + np.abs(rhs).max()))
+
+
+class CondensedSolver:
+    """Symbolic analysis once per pattern, then factor / solve per iteration."""
+
+    def __init__(self, W_pattern, J_pattern):
+        self.P = condensed_pattern(W_pattern, J_pattern)
+        self.sym = Symbolic(self.P)
+
+    def factor(self, K):
+        return Cholesky(K, self.sym)
+
+
+def inertia_schedule(K_of_delta, solver, delta_last=0.0):
+    """Primal regularization search (Section 2.2, inertia correction of
+    Waechter & Biegler Section 3.1, Cholesky success replacing the inertia test
+    as in Section 3): try delta_w = 0; then delta_last/3 (or 1e-4 the first time),
+    growing by 8 (after a previous success) or 100 (first time) until the
+    Cholesky factorization succeeds.  Returns (delta_w, factor, n_factorizations)."""
+    nf = 1
+    F = solver.factor(K_of_delta(0.0))
+    if F.ok:
+        return 0.0, F, nf
+    delta = max(1e-20, delta_last / 3.0) if delta_last > 0 else 1e-4
+    grow = 8.0 if delta_last > 0 else 100.0
+    while delta < 1e40:
+        nf += 1
+        F = solver.factor(K_of_delta(delta))
+        if F.ok:
+            return delta, F, nf
+        delta *= grow
+    raise RuntimeError("inertia correction failed")
+
+
+def lifted_solve(F, A, J, d, a, b, max_refine=10, tol=1e-10):
+    """LiftedKKT solve of (AUG) with m_e = 0: condensed solve + Richardson refinement."""
+    n = J.shape[1]
+
+    def csolve(ra, rb):
+        dx = F.solve(ra + J.T @ (d * rb))
+        dz = d * (J @ dx - rb)
+        return np.concatenate([dx, dz])
+
+    rhs = np.concatenate([a, b])
+    sol = csolve(a, b)
+    eta = backward_error(A, sol, rhs)
+    hist = [eta]
+    for _ in range(max_refine):
+        if eta <= tol:
+            break
+        res = rhs - A @ sol
+        sol = sol + csolve(res[:n], res[n:])
+        eta_new = backward_error(A, sol, rhs)
+        hist.append(eta_new)
+        if eta_new > 0.5 * eta:
+            eta = eta_new
+            break
+        eta = eta_new
+    return sol[:n], sol[n:], hist
+
+
+def hykkt_cg(F, G, gamma, r1bar, r2bar, rtol=1e-10, atol=1e-14, maxit=None):
+    """Eq. (10): CG on S_gamma = G K_gamma^{-1} G^T, then the primal back-solve."""
+    m_e = G.shape[0]
+    if maxit is None:
+        maxit = max(m_e, 1)
+    rhs1 = r1bar + gamma * (G.T @ r2bar)
+    w = F.solve(rhs1)
+    rhs = G @ w - r2bar
+    dy = np.zeros(m_e)
+    r = rhs.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    r0 = np.sqrt(rr)
+    stop = max(rtol * r0, atol)
+    it = 0
+    while np.sqrt(rr) > stop and it < maxit:
+        Sp = G @ F.solve(G.T @ p)
+        alpha = rr / float(p @ Sp)
+        dy += alpha * p
+        r -= alpha * Sp
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    dx = F.solve(rhs1 - G.T @ dy)
+    return dx, dy, it, float(np.sqrt(rr) / max(r0, 1e-300))
+
+
+def hykkt_solve(F, W, sigma_x, J, d_h, m_e, delta_w, gamma, a, b, **cg):
+    """HyKKT solve of (AUG): condense H, CG on the Schur complement, recover dz."""
+    G = J[:m_e]
+    H = J[m_e:]
+    r1bar = a + H.T @ (d_h * b[m_e:])
+    r2bar = b[:m_e]
+    dx, dy, it, rel = hykkt_cg(F, G, gamma, r1bar, r2bar, **cg)
+    dz = d_h * (H @ dx - b[m_e:])
+    return dx, dy, dz, it, rel
