@@ -1,0 +1,133 @@
+"""Pins for the oracle AC-OPF model and interior-point method (no GPU)."""
+import dataclasses
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from synth import config_grid, kkt_point, ring_grid
+from oracle.opf import OPFModel
+from oracle import ipm
+
+
+def fd_jacobian(m, x, eps=1e-7):
+    cols = []
+    for k in range(m.n):
+        e = np.zeros(m.n)
+        e[k] = eps
+        gp, hp = m.cons(x + e)
+        gm, hm = m.cons(x - e)
+        cols.append((np.concatenate([gp, hp]) - np.concatenate([gm, hm])) / (2 * eps))
+    return np.array(cols).T
+
+
+def test_derivatives_match_finite_differences():
+    g = config_grid("ring30")
+    m = OPFModel(g)
+    p = kkt_point(g, 7)
+    x, y, z = p["x"], p["y"], p["z"]
+    J = m.jacobian(x).toarray()
+    assert np.abs(J - fd_jacobian(m, x)).max() < 1e-6 * max(1, np.abs(J).max())
+    sf = 0.3
+    W = m.hessian(x, y, z, sf).toarray()
+    eps = 1e-6
+    Wfd = np.zeros_like(W)
+    lag = lambda xx: sf * m.grad(xx) + m.jacobian(xx).T @ np.concatenate([y, z])
+    for k in range(m.n):
+        e = np.zeros(m.n)
+        e[k] = eps
+        Wfd[:, k] = (lag(x + e) - lag(x - e)) / (2 * eps)
+    assert np.abs(W - Wfd).max() < 1e-5 * max(1, np.abs(W).max())
+    assert np.abs(W - W.T).max() <= 1e-13 * np.abs(W).max()
+
+
+def test_branch_physics():
+    """Lossless lines transfer power exactly; resistive lines only lose power."""
+    g = ring_grid(12, 3, 3, seed=5)
+    g0 = dataclasses.replace(g, r=np.zeros(g.nbr), b=np.zeros(g.nbr))
+    m0 = OPFModel(g0)
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(0.9, 1.1, g.nb), rng.uniform(-0.3, 0.3, g.nb),
+                        np.zeros(2 * g.ng)])
+    (_, _, Pf, Qf, *_), (_, _, Pt, Qt, *_) = m0._flows(x)
+    np.testing.assert_allclose(Pf + Pt, 0.0, atol=1e-12)
+    m1 = OPFModel(dataclasses.replace(g, b=np.zeros(g.nbr)))
+    (_, _, Pf, _, *_), (_, _, Pt, _, *_) = m1._flows(x)
+    assert np.all(Pf + Pt >= -1e-12)
+
+
+class QP:
+    """min 1/2 x^T Q x + c^T x  s.t.  A x = b,  xl <= x <= xu."""
+
+    def __init__(self, Q, c, A, b, xl, xu):
+        self.Q, self.c, self.A, self.b = sp.csr_matrix(Q), c, sp.csr_matrix(A), b
+        self.n, self.m_e, self.m_i = len(c), A.shape[0], 0
+        self.xl, self.xu = xl, xu
+
+    def x0(self):
+        return np.zeros(self.n)
+
+    def objective(self, x):
+        return float(0.5 * x @ (self.Q @ x) + self.c @ x)
+
+    def grad(self, x):
+        return self.Q @ x + self.c
+
+    def cons(self, x):
+        return self.A @ x - self.b, np.zeros(0)
+
+    def jacobian(self, x):
+        return self.A.copy()
+
+    def hessian(self, x, y, z, sigma_f=1.0):
+        return (sigma_f * self.Q).tocsr()
+
+
+def test_equality_qp_closed_form():
+    rng = np.random.default_rng(1)
+    n, me = 12, 4
+    M = rng.standard_normal((n, n))
+    Q = M @ M.T + np.eye(n)
+    c = rng.standard_normal(n)
+    A = rng.standard_normal((me, n))
+    b = rng.standard_normal(me)
+    inf = np.full(n, np.inf)
+    r = ipm.solve(QP(Q, c, A, b, -inf, inf), ipm.Options(kkt="hykkt", gamma=1e4))
+    kkt = np.block([[Q, A.T], [A, np.zeros((me, me))]])
+    ref = np.linalg.solve(kkt, np.concatenate([-c, b]))[:n]
+    assert r.status == "converged"
+    np.testing.assert_allclose(r.x, ref, rtol=1e-6, atol=1e-7)
+
+
+def test_box_qp_is_clipped_minimizer():
+    rng = np.random.default_rng(2)
+    n = 20
+    q = rng.uniform(0.5, 2.0, n)
+    c = rng.standard_normal(n) * 3
+    xl, xu = np.full(n, -1.0), np.full(n, 1.0)
+    xl[::5] = -np.inf
+    prob = QP(np.diag(q), c, np.zeros((0, n)), np.zeros(0), xl, xu)
+    for kkt in ("hykkt", "lifted"):
+        r = ipm.solve(prob, ipm.Options(kkt=kkt))
+        assert r.status == "converged"
+        np.testing.assert_allclose(r.x, np.clip(-c / q, xl, xu), atol=1e-5)
+
+
+@pytest.mark.parametrize("kkt", ["hykkt", "lifted"])
+def test_ring30_converges(kkt):
+    g = config_grid("ring30")
+    r = ipm.solve(OPFModel(g), ipm.Options(kkt=kkt, gamma=1e6))
+    assert r.status == "converged"
+    assert r.kkt_error <= 1e-6
+    gx, hx = OPFModel(g).cons(r.x)
+    assert np.abs(gx).max() <= (1e-5 if kkt == "lifted" else 1e-8)
+    assert hx.max() <= 1e-6
+
+
+def test_lifted_optimum_within_tau_of_hykkt():
+    """Section 3.2: the relaxation error is of the order of the tolerance tau."""
+    g = config_grid("ring30")
+    rh = ipm.solve(OPFModel(g), ipm.Options(kkt="hykkt", gamma=1e6))
+    rl = ipm.solve(OPFModel(g), ipm.Options(kkt="lifted"))
+    tau = 1e-6
+    assert abs(rl.obj - rh.obj) <= 1e3 * tau * max(1.0, abs(rh.obj))
