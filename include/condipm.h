@@ -1,0 +1,170 @@
+/*
+ * condipm — condensed-space interior-point KKT solves on one GB300 (sm_103a).
+ *
+ * C ABI of libcondipm.so.  Every compute step runs in this library's own CUDA kernels.
+ *
+ * Conventions (all entry points):
+ *  - Pointers are DEVICE pointers owned by the caller unless the argument says "host".
+ *    The library never frees or keeps caller pointers beyond the call.
+ *  - Index arrays are int32, CSR row pointers are int32 (nnz < 2^31), values FP64.
+ *  - Work is ordered on the given cudaStream_t (0 = legacy default stream).  Calls do not
+ *    synchronize the stream unless stated ("synchronizes").
+ *  - Library-owned state lives in opaque handles; all their device memory is allocated by
+ *    the *_create / ipm_symbolic calls and released by *_destroy.  The numeric calls
+ *    (ipm_condense, ipm_factor, ipm_solve, ipm_aug_solve, hykkt_cg) allocate nothing.
+ *  - Return value: IPM_OK (0), a positive numerical event, or a negative usage/CUDA error.
+ *    No call throws or aborts across the ABI.
+ *
+ * Notation (paper, Section 2): x in R^n; J = [G; H] stacks the m_e equality rows G on
+ * the m_i inequality rows H (m = m_e + m_i rows); W is the Hessian of the Lagrangian;
+ * Sigma_x the bound-barrier diagonal; D_H = D_s + delta_w the slack diagonal.
+ */
+#ifndef CONDIPM_H
+#define CONDIPM_H
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  IPM_OK = 0,
+  IPM_ERR_NOT_PD = 1,       /* Cholesky met a pivot <= 0 or non-finite (inertia wrong) */
+  IPM_ERR_CG_MAXIT = 2,     /* HyKKT CG hit its iteration limit */
+  IPM_ERR_NONFINITE = 3,    /* NaN/Inf in inputs or results */
+  IPM_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+  IPM_ERR_RESTORATION = 5,  /* line search failed: feasibility restoration needed */
+  IPM_ERR_BAD_ARG = -1,
+  IPM_ERR_OOM = -2,
+  IPM_ERR_CUDA = -3
+};
+
+/* Text of the last error recorded by any call (thread-shared, overwritten by later errors). */
+const char *ipm_last_error_message(void);
+
+typedef struct ipm_sym_s *ipm_sym_t; /* symbolic analysis of one sparsity pattern */
+typedef struct ipm_num_s *ipm_num_t; /* numeric factor storage + workspaces for one pattern */
+
+/* ipm_symbolic — symbolic analysis, once per sparsity pattern (paper Section 5, "cuDSS
+ * analysis": ordering, elimination tree and supernodes, reused across iterations).
+ *
+ * Pattern of the condensed matrix K = W + Sigma_x + delta_w I + J^T D J (Eq. (K_1), (9),
+ * (13)): pat(W) united with the diagonal and pat(J^T J).  Computed entirely on the GPU:
+ * graph of K, nested-dissection ordering (project-defined deterministic rule), elimination
+ * tree, column structures of L, supernodes (width <= 64), condensation index maps and the
+ * level schedule.
+ *   n            number of primal variables
+ *   m            rows of J (m_e + m_i)
+ *   J_rowptr     [m+1] CSR row pointers of J (device)
+ *   J_colind     [nnzJ] CSR column indices of J, each row strictly increasing (device)
+ *   nnzJ         J_rowptr[m] (host value)
+ *   W_rowptr     [n+1] CSR row pointers of the LOWER triangle of W, diagonal included (device)
+ *   W_colind     [nnzW] column indices (col <= row, strictly increasing per row) (device)
+ *   nnzW         W_rowptr[n] (host value)
+ *   out          receives the handle.
+ * Synchronizes the stream.  Errors: IPM_ERR_BAD_ARG on sizes/NULLs, IPM_ERR_OOM, IPM_ERR_CUDA.
+ */
+int ipm_symbolic(int n, int m, const int *J_rowptr, const int *J_colind, int nnzJ,
+                 const int *W_rowptr, const int *W_colind, int nnzW, cudaStream_t stream,
+                 ipm_sym_t *out);
+
+/* Sizes of a symbolic analysis (host outputs; NULL outputs are skipped).
+ *   nsuper      number of supernodes
+ *   nnz_offdiag entries of L below the diagonal (sum of column counts - n)
+ *   panel_len   FP64 slots of the supernodal panel storage
+ *   nlevels     levels of the supernodal elimination tree
+ *   flops       textbook factorization flop count sum_j eta_j (eta_j + 3)              */
+int ipm_symbolic_info(ipm_sym_t sym, int *nsuper, int64_t *nnz_offdiag, int64_t *panel_len,
+                      int *nlevels, double *flops);
+
+/* Copies the symbolic result to HOST buffers (for bit-exact checks):
+ *   perm [n]        perm[k] = original variable at elimination position k
+ *   parent [n]      elimination tree over positions (-1 = root)
+ *   sptr [nsuper+1] first position of each supernode
+ *   colptr [n+1]    int64 column pointers of the below-diagonal structure of L
+ *   rowind [nnz_offdiag] row positions, increasing within each column
+ * NULL pointers are skipped.  Synchronizes. */
+int ipm_symbolic_export(ipm_sym_t sym, int *perm, int *parent, int *sptr, int64_t *colptr,
+                        int *rowind);
+
+/* Copies the supernodal layout to HOST buffers: srow_ptr [nsuper+1], srow [srow_ptr[nsuper]]
+ * (rows of each supernode, own columns first), lptr [nsuper+1] (panel offsets; panel s is
+ * column-major with leading dimension srow_ptr[s+1]-srow_ptr[s]).  NULLs skipped.
+ * Synchronizes. */
+int ipm_symbolic_export_panels(ipm_sym_t sym, int *srow_ptr, int *srow, int64_t *lptr);
+
+void ipm_symbolic_destroy(ipm_sym_t sym);
+
+/* Numeric storage for one pattern.  precision: 64 (FP64 factor).  Allocates the panel
+ * values and every workspace the numeric calls need. */
+int ipm_num_create(ipm_sym_t sym, int precision, ipm_num_t *out);
+void ipm_num_destroy(ipm_num_t num);
+
+/* Copies the panel values (panel_len doubles: K after ipm_condense, L after ipm_factor) to a
+ * HOST buffer.  Synchronizes. */
+int ipm_num_export(ipm_num_t num, double *Lx_host);
+
+/* ipm_condense — K = W + diag(sigma_x) + delta_w I + J^T diag(d_row) J written straight into
+ * the supernodal panels of L (fill entries zeroed) (Eq. (K_1): K = W + delta_w I + H^T D_H H;
+ * Eq. (9): K_gamma = K + gamma G^T G; Eq. (13): K_tau = W + delta_w I + H_tau^T D_H H_tau).
+ *   W_val [nnzW]    values of the lower triangle of W in the pattern given to ipm_symbolic
+ *   sigma_x [n]     bound-barrier diagonal Sigma_x (0 for free variables)
+ *   J_val [nnzJ]    values of J in its pattern
+ *   d_row [m]       per-row weight: gamma on HyKKT equality rows, D_H on inequality rows
+ *   delta_w         primal regularization
+ * Deterministic: each panel entry is one fixed-order sum, no atomics. */
+int ipm_condense(ipm_sym_t sym, ipm_num_t num, const double *W_val, const double *sigma_x,
+                 const double *J_val, const double *d_row, double delta_w, cudaStream_t stream);
+
+/* ipm_factor — supernodal Cholesky P K P^T = L L^T in place (Section 3: Cholesky of the
+ * SPD condensed matrix; positive definiteness stands in for the inertia test, Eq. (7)).
+ *   d_info  DEVICE int: set to -1 on success, else the smallest elimination position whose
+ *           pivot was <= 0 or non-finite.  The call does not read it back.
+ * The panels then hold L.  Returns IPM_OK unless a usage/CUDA error occurred. */
+int ipm_factor(ipm_sym_t sym, ipm_num_t num, int *d_info, cudaStream_t stream);
+
+/* ipm_solve — x = K^{-1} b with the factor: y = P b, L z = y, L^T w = z, x = P^T w.
+ *   b [n], x [n] (may alias).  nrhs must be 1. */
+int ipm_solve(ipm_sym_t sym, ipm_num_t num, const double *b, double *x, int nrhs,
+              cudaStream_t stream);
+
+/* ipm_aug_solve — LiftedKKT solve (Section 3.2, Eq. (13)) of the augmented system with the
+ * slack block eliminated (all rows inequality rows):
+ *     [ W + Sigma_x + delta_w I   J^T      ] [dx]   [a]
+ *     [ J                        -D_H^{-1} ] [dz] = [b]
+ * by K dx = a + J^T D_H b, dz = D_H (J dx - b), followed by Richardson iterative refinement
+ * on this system in FP64 (Section 2.2 "Iterative refinement") until the backward error
+ * eta = ||res||_inf / (||A||_inf ||sol||_inf + ||rhs||_inf) <= tol, it stops halving, or
+ * max_refine steps.  Requires a successful ipm_factor of the matching K.
+ *   a [n], b [m], dx [n], dz [m];  d_eta (device double), d_steps (device int) receive the
+ *   final backward error and the refinement steps taken.
+ * Synchronizes once per refinement step (host decides whether to continue). */
+int ipm_aug_solve(ipm_sym_t sym, ipm_num_t num, const double *W_val, const double *sigma_x,
+                  const double *J_val, const double *d_row, double delta_w, const double *a,
+                  const double *b, double *dx, double *dz, int max_refine, double tol,
+                  double *d_eta, int *d_steps, cudaStream_t stream);
+
+/* hykkt_cg — HyKKT (Section 3.1, Eq. (10)).  With the first m_e rows of J being G and the
+ * rest H, solves the augmented system
+ *     [ W + Sigma_x + delta_w I   G^T   H^T      ] [dx]   [a  ]
+ *     [ G                         0     0        ] [dy] = [b_G]
+ *     [ H                         0    -D_H^{-1} ] [dz]   [b_H]
+ * using the factor of K_gamma = W + Sigma_x + delta_w I + H^T D_H H + gamma G^T G
+ * (ipm_condense with d_row = [gamma..., D_H...]): r1 = a + H^T D_H b_H, r2 = b_G,
+ * CG from dy = 0 on (G K_gamma^{-1} G^T) dy = G K_gamma^{-1}(r1 + gamma G^T r2) - r2 until
+ * ||r_k||_2 <= max(rtol ||r_0||_2, 1e-14) or maxit; then
+ * dx = K_gamma^{-1}(r1 + gamma G^T r2 - G^T dy) and dz = D_H (H dx - b_H).
+ *   d_row [m] as passed to ipm_condense (d_row[0..m_e) = gamma).
+ *   a [n], b [m], dx [n], dy [m_e], dz [m - m_e]
+ *   h_iters, h_relres: HOST outputs (CG iterations, final ||r||/||r_0||).
+ * Returns IPM_ERR_CG_MAXIT if maxit was reached.  Synchronizes (convergence tests). */
+int hykkt_cg(ipm_sym_t sym, ipm_num_t num, int m_e, const double *J_val, const double *d_row,
+             double gamma, const double *a, const double *b, double rtol, int maxit, double *dx,
+             double *dy, double *dz, int *h_iters, double *h_relres, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONDIPM_H */

@@ -1,0 +1,184 @@
+"""Python binding of libcondipm (condensed-space IPM KKT solves on GB300).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  Tensors are
+passed by device pointer on torch's current CUDA stream.  The extension must be built
+(``__graft_entry__.build()``); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+_lib = None
+
+IPM_OK, IPM_ERR_NOT_PD, IPM_ERR_CG_MAXIT, IPM_ERR_NONFINITE = 0, 1, 2, 3
+IPM_ERR_TIMEOUT, IPM_ERR_RESTORATION = 4, 5
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+I64 = ctypes.c_int64
+
+_SIGS = {
+    "ipm_last_error_message": (ctypes.c_char_p, []),
+    "ipm_symbolic": (I, [I, I, P, P, I, P, P, I, P, P]),
+    "ipm_symbolic_info": (I, [P, P, P, P, P, P]),
+    "ipm_symbolic_export": (I, [P, P, P, P, P, P]),
+    "ipm_symbolic_export_panels": (I, [P, P, P, P]),
+    "ipm_symbolic_destroy": (None, [P]),
+    "ipm_num_create": (I, [P, I, P]),
+    "ipm_num_destroy": (None, [P]),
+    "ipm_num_export": (I, [P, P]),
+    "ipm_condense": (I, [P, P, P, P, P, P, D, P]),
+    "ipm_factor": (I, [P, P, P, P]),
+    "ipm_solve": (I, [P, P, P, P, I, P]),
+    "ipm_aug_solve": (I, [P, P, P, P, P, P, D, P, P, P, P, I, D, P, P, P]),
+    "hykkt_cg": (I, [P, P, I, P, P, D, P, P, D, I, P, P, P, P, P, P]),
+}
+
+
+class CondipmError(RuntimeError):
+    pass
+
+
+def lib():
+    """Loads libcondipm.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise CondipmError(f"{LIB} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc, name):
+    if rc < 0:
+        msg = lib().ipm_last_error_message()
+        raise CondipmError(f"{name} failed ({rc}): {msg.decode() if msg else ''}")
+    return rc
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, f"expected {dtype}, got {t.dtype}"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Symbolic:
+    """ipm_symbolic handle for one (J, W-lower) sparsity pattern (int32 CUDA tensors)."""
+
+    def __init__(self, n, m, J_rowptr, J_colind, W_rowptr, W_colind, stream=None):
+        import torch
+        h = ctypes.c_void_p()
+        _check(lib().ipm_symbolic(n, m, _ptr(J_rowptr, torch.int32), _ptr(J_colind, torch.int32),
+                                  int(J_colind.numel()), _ptr(W_rowptr, torch.int32),
+                                  _ptr(W_colind, torch.int32), int(W_colind.numel()),
+                                  _stream(stream), ctypes.byref(h)), "ipm_symbolic")
+        self.h = h
+        self.n, self.m = n, m
+        ns, nnz, plen, nl, fl = I(), I64(), I64(), I(), D()
+        _check(lib().ipm_symbolic_info(h, ctypes.byref(ns), ctypes.byref(nnz), ctypes.byref(plen),
+                                       ctypes.byref(nl), ctypes.byref(fl)), "ipm_symbolic_info")
+        self.nsuper, self.nnz_offdiag, self.panel_len = ns.value, nnz.value, plen.value
+        self.nlevels, self.flops = nl.value, fl.value
+
+    def export(self):
+        n = self.n
+        perm = np.zeros(n, np.int32)
+        parent = np.zeros(n, np.int32)
+        sptr = np.zeros(self.nsuper + 1, np.int32)
+        colptr = np.zeros(n + 1, np.int64)
+        rowind = np.zeros(max(self.nnz_offdiag, 1), np.int32)
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_symbolic_export(self.h, c(perm), c(parent), c(sptr), c(colptr), c(rowind)),
+               "ipm_symbolic_export")
+        return dict(perm=perm, parent=parent, sptr=sptr, colptr=colptr,
+                    rowind=rowind[:self.nnz_offdiag])
+
+    def export_panels(self):
+        srow_ptr = np.zeros(self.nsuper + 1, np.int32)
+        lptr = np.zeros(self.nsuper + 1, np.int64)
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_symbolic_export_panels(self.h, c(srow_ptr), None, c(lptr)), "export_panels")
+        srow = np.zeros(max(int(srow_ptr[-1]), 1), np.int32)
+        _check(lib().ipm_symbolic_export_panels(self.h, None, c(srow), None), "export_panels")
+        return srow_ptr, srow[:int(srow_ptr[-1])], lptr
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipm_symbolic_destroy(self.h)
+            self.h = None
+
+
+class Numeric:
+    """ipm_num handle: panel storage + workspaces for one Symbolic."""
+
+    def __init__(self, sym: Symbolic, precision: int = 64):
+        h = ctypes.c_void_p()
+        _check(lib().ipm_num_create(sym.h, precision, ctypes.byref(h)), "ipm_num_create")
+        self.h, self.sym = h, sym
+
+    def export(self):
+        out = np.zeros(max(self.sym.panel_len, 1), np.float64)
+        _check(lib().ipm_num_export(self.h, out.ctypes.data_as(ctypes.c_void_p)), "ipm_num_export")
+        return out[:self.sym.panel_len]
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipm_num_destroy(self.h)
+            self.h = None
+
+
+def ipm_condense(sym, num, W_val, sigma_x, J_val, d_row, delta_w, stream=None):
+    return _check(lib().ipm_condense(sym.h, num.h, _ptr(W_val), _ptr(sigma_x), _ptr(J_val),
+                                     _ptr(d_row), float(delta_w), _stream(stream)), "ipm_condense")
+
+
+def ipm_factor(sym, num, d_info, stream=None):
+    return _check(lib().ipm_factor(sym.h, num.h, _ptr(d_info), _stream(stream)), "ipm_factor")
+
+
+def ipm_solve(sym, num, b, x, stream=None):
+    return _check(lib().ipm_solve(sym.h, num.h, _ptr(b), _ptr(x), 1, _stream(stream)), "ipm_solve")
+
+
+def ipm_aug_solve(sym, num, W_val, sigma_x, J_val, d_row, delta_w, a, b, dx, dz, d_eta, d_steps,
+                  max_refine=10, tol=1e-10, stream=None):
+    return _check(lib().ipm_aug_solve(sym.h, num.h, _ptr(W_val), _ptr(sigma_x), _ptr(J_val),
+                                      _ptr(d_row), float(delta_w), _ptr(a), _ptr(b), _ptr(dx),
+                                      _ptr(dz), int(max_refine), float(tol), _ptr(d_eta),
+                                      _ptr(d_steps), _stream(stream)), "ipm_aug_solve")
+
+
+def hykkt_cg(sym, num, m_e, J_val, d_row, gamma, a, b, dx, dy, dz, rtol=1e-10, maxit=None,
+             stream=None):
+    its, rel = I(), D()
+    maxit = max(m_e, 1) if maxit is None else maxit
+    rc = _check(lib().hykkt_cg(sym.h, num.h, int(m_e), _ptr(J_val), _ptr(d_row), float(gamma),
+                               _ptr(a), _ptr(b), float(rtol), int(maxit), _ptr(dx), _ptr(dy),
+                               _ptr(dz), ctypes.byref(its), ctypes.byref(rel), _stream(stream)),
+                "hykkt_cg")
+    return rc, its.value, rel.value

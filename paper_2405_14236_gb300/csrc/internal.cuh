@@ -1,0 +1,50 @@
+// Library-internal layout of the symbolic and numeric handles.
+#pragma once
+#include "common.cuh"
+
+// Project-defined ordering parameters (kept equal to the CPU checker's constants).
+#define CIPM_LEAF 64     // parts of at most this many vertices are ordered by minimum degree
+#define CIPM_REROOT 4    // pseudo-peripheral root search: at most this many re-roots
+#define CIPM_SN_MAXW 64  // maximum supernode width
+
+struct ipm_sym_s {
+  int n = 0, m = 0, nnzJ = 0, nnzW = 0;
+  // copies of the caller's patterns
+  int *J_rowptr = nullptr, *J_colind = nullptr, *J_rowidx = nullptr;
+  int *W_rowptr = nullptr, *W_colind = nullptr, *W_rowidx = nullptr;
+  int *JT_ptr = nullptr, *JT_ent = nullptr;  // column j of J: J entry indices, by row
+  int *WT_ptr = nullptr, *WT_ent = nullptr;  // column j of lower W: W entry indices
+  // ordering and elimination tree (positions)
+  int *perm = nullptr, *iperm = nullptr, *parent = nullptr, *cc = nullptr;
+  int64_t *colptr = nullptr;
+  int *rowind = nullptr;
+  int64_t nnz_offdiag = 0;
+  // supernodes
+  int nsuper = 0;
+  int *sptr = nullptr, *snode = nullptr;
+  int *srow_ptr = nullptr, *srow = nullptr;  // rows of each supernode (own columns first)
+  int64_t *lptr = nullptr;                   // panel offsets (column-major, ld = rows)
+  int64_t panel_len = 0;
+  int max_ld = 0, max_w = 0;
+  // condensation: items per panel slot (p, q): J entries p, q (q >= 0) or W entry p (q = -1)
+  int *slot_ptr = nullptr;
+  int2 *items = nullptr;
+  int64_t nitems = 0;
+  // level schedule of the supernodal elimination tree, deepest level first
+  int nlevels = 0;
+  int *level_sn = nullptr;             // supernodes grouped by level
+  std::vector<int> h_level_ptr;        // host copy, nlevels + 1 entries
+  std::vector<int> h_level_maxld;      // max panel rows in each level
+  double flops = 0.0;
+};
+
+struct ipm_num_s {
+  ipm_sym_t sym = nullptr;
+  int precision = 64;
+  double *Lx = nullptr;  // panel values
+  // workspaces (n or m sized), allocated once
+  double *vn[8] = {nullptr};
+  double *vm[6] = {nullptr};
+  double *scal = nullptr;  // device scalars
+  double *h_scal = nullptr;  // pinned host mirror
+};
