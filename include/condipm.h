@@ -164,6 +164,36 @@ int hykkt_cg(ipm_sym_t sym, ipm_num_t num, int m_e, const double *J_val, const d
              double gamma, const double *a, const double *b, double rtol, int maxit, double *dx,
              double *dy, double *dz, int *h_iters, double *h_relres, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------------------
+ * AC optimal power flow model (the NLP (1) the benchmarks solve; its derivative evaluation is
+ * the "AD" part of an IPM iteration, Section 5).  Variables x = [V | theta | Pg | Qg],
+ * equalities g = [P balance | Q balance | theta_ref], inequalities
+ * h = [|S_from|^2 - rate^2 | |S_to|^2 - rate^2] (h <= 0), cost sum c2 (100 Pg)^2 + c1 (100 Pg).
+ */
+typedef struct ipm_opf_s *ipm_opf_t;
+
+/* All array arguments are HOST arrays (copied).  Branch k joins f_bus[k] -> t_bus[k] (pi model,
+ * series r + j x, total charging b, limit rate); generator g sits at gen_bus[g] (gen_bus[0] is
+ * the reference bus); xl/xu are the n = 2nb+2ng variable bounds (+-inf where absent).
+ * Builds the sparsity patterns of J and of the lower triangle of W on the GPU.
+ * Synchronizes.  IPM_ERR_BAD_ARG on out-of-range bus indices. */
+int ipm_opf_create(int nb, int nbr, int ng, const int *f_bus, const int *t_bus, const double *r,
+                   const double *x, const double *b, const double *rate, const double *pd,
+                   const double *qd, const int *gen_bus, const double *c2, const double *c1,
+                   const double *xl, const double *xu, cudaStream_t stream, ipm_opf_t *out);
+int ipm_opf_info(ipm_opf_t opf, int *n, int *m_e, int *m_i, int *nnzJ, int *nnzW);
+/* Copies the handle's patterns into caller buffers (host or device; NULLs skipped): CSR of J
+ * (J_rowptr [m_e+m_i+1], J_colind [nnzJ]) and CSR of the lower triangle of W (W_rowptr [n+1],
+ * W_colind [nnzW]); columns increase within each row.  Synchronizes. */
+int ipm_opf_patterns(ipm_opf_t opf, int *J_rowptr, int *J_colind, int *W_rowptr, int *W_colind);
+/* Evaluates at x (device): f (device scalar, may be NULL), grad [n] (may be NULL),
+ * g [m_e], h [m_i], J_val [nnzJ] and, when W_val is not NULL, W_val [nnzW] =
+ * sigma_f grad^2 f + sum y_i grad^2 g_i + sum z_j grad^2 h_j (y [m_e], z [m_i]). */
+int ipm_opf_eval(ipm_opf_t opf, const double *x, const double *y, const double *z,
+                 double sigma_f, double *f, double *grad, double *g, double *h, double *J_val,
+                 double *W_val, cudaStream_t stream);
+void ipm_opf_destroy(ipm_opf_t opf);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,11 @@ _SIGS = {
     "ipm_solve": (I, [P, P, P, P, I, P]),
     "ipm_aug_solve": (I, [P, P, P, P, P, P, D, P, P, P, P, I, D, P, P, P]),
     "hykkt_cg": (I, [P, P, I, P, P, D, P, P, D, I, P, P, P, P, P, P]),
+    "ipm_opf_create": (I, [I, I, I] + [P] * 14 + [P, P]),
+    "ipm_opf_info": (I, [P, P, P, P, P, P]),
+    "ipm_opf_patterns": (I, [P, P, P, P, P]),
+    "ipm_opf_eval": (I, [P, P, P, P, D, P, P, P, P, P, P, P]),
+    "ipm_opf_destroy": (None, [P]),
 }
 
 
@@ -182,3 +187,44 @@ def hykkt_cg(sym, num, m_e, J_val, d_row, gamma, a, b, dx, dy, dz, rtol=1e-10, m
                                _ptr(dz), ctypes.byref(its), ctypes.byref(rel), _stream(stream)),
                 "hykkt_cg")
     return rc, its.value, rel.value
+
+
+class Opf:
+    """ipm_opf handle for one synthetic grid (``synth.Grid``); patterns as int32 CUDA tensors."""
+
+    def __init__(self, grid, stream=None):
+        import torch
+        c = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+        self._keep = [c(grid.f_bus, np.int32), c(grid.t_bus, np.int32), c(grid.r, np.float64),
+                      c(grid.x, np.float64), c(grid.b, np.float64), c(grid.rate, np.float64),
+                      c(grid.pd, np.float64), c(grid.qd, np.float64), c(grid.gen_bus, np.int32),
+                      c(grid.c2, np.float64), c(grid.c1, np.float64)]
+        lo, hi = grid.bounds()
+        self._keep += [c(lo, np.float64), c(hi, np.float64)]
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in self._keep]
+        h = ctypes.c_void_p()
+        _check(lib().ipm_opf_create(grid.nb, grid.nbr, grid.ng, *ptrs, _stream(stream),
+                                    ctypes.byref(h)), "ipm_opf_create")
+        self.h = h
+        n, me, mi, nj, nw = I(), I(), I(), I(), I()
+        _check(lib().ipm_opf_info(h, *(ctypes.byref(v) for v in (n, me, mi, nj, nw))), "ipm_opf_info")
+        self.n, self.m_e, self.m_i, self.nnzJ, self.nnzW = n.value, me.value, mi.value, nj.value, nw.value
+        dev = dict(dtype=torch.int32, device="cuda")
+        self.J_rowptr = torch.empty(self.m_e + self.m_i + 1, **dev)
+        self.J_colind = torch.empty(max(self.nnzJ, 1), **dev)
+        self.W_rowptr = torch.empty(self.n + 1, **dev)
+        self.W_colind = torch.empty(max(self.nnzW, 1), **dev)
+        _check(lib().ipm_opf_patterns(h, _ptr(self.J_rowptr), _ptr(self.J_colind), _ptr(self.W_rowptr),
+                                      _ptr(self.W_colind)), "ipm_opf_patterns")
+        self.J_colind = self.J_colind[:self.nnzJ]
+        self.W_colind = self.W_colind[:self.nnzW]
+
+    def eval(self, x, y, z, sigma_f, f, grad, g, h, J_val, W_val, stream=None):
+        return _check(lib().ipm_opf_eval(self.h, _ptr(x), _ptr(y), _ptr(z), float(sigma_f), _ptr(f),
+                                         _ptr(grad), _ptr(g), _ptr(h), _ptr(J_val), _ptr(W_val),
+                                         _stream(stream)), "ipm_opf_eval")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipm_opf_destroy(self.h)
+            self.h = None
