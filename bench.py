@@ -1,0 +1,344 @@
+"""Benchmark: condensed KKT solves on one GB300 (or N independent replicas).
+
+Workload (default, "kkt10k-lifted"): one LiftedKKT KKT solve of a seeded synthetic
+10,000-bus AC-OPF grid (24,000 primal variables, 46,001 relaxed rows) at a late-iteration
+shaped point: Sigma_x and D_H log-uniform in [1e-8, 1e8].  One step = condensation of
+K = W + Sigma_x + delta_w I + J^T D_H J, supernodal Cholesky, and the FP64-refined solve of
+the augmented system (backward error <= 1e-10).  W and J are evaluated once by the GPU
+model kernels at setup; the symbolic analysis is done once (reported as symbolic_s, like
+the paper's "init").  L2 is flushed between timed steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IPM solves/s at 1e-6 KKT tol, plain vs batched/warm-start; factor GB/s"
+UNIT = "KKT solves/s"
+WORKLOAD = ("kkt10k-lifted: LiftedKKT condensed KKT solve (condense + supernodal Cholesky + "
+            "FP64-refined solve) on a seeded synthetic 10,000-bus grid, Sigma log-uniform [1e-8,1e8]")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def build_inputs(seed=3):
+    from synth import config_grid, kkt_point
+    g = config_grid("planar10k")
+    p = kkt_point(g, seed)
+    d = np.concatenate([p["d_g"], p["d_s"]])
+    b = np.concatenate([p["r3"], p["r4"]])
+    return g, p, d, b
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+def oracle_setup():
+    from oracle.opf import OPFModel
+    from oracle import kkt as K
+    g, p, d, b = build_inputs()
+    m = OPFModel(g)
+    J = m.jacobian(p["x"]).tocsr()
+    Wf = m.hessian(p["x"], p["y"], p["z"])
+    solver = K.CondensedSolver(Wf, J)
+    dw, F, _ = K.inertia_schedule(lambda dw: K.condensed_matrix(Wf, p["sigma_x"], J, d, dw), solver)
+    return dict(J=J, Wf=Wf, sigma=p["sigma_x"], d=d, a=p["r1"], b=b, solver=solver, dw=dw)
+
+
+def oracle_step(o):
+    from oracle import kkt as K
+    Km = K.condensed_matrix(o["Wf"], o["sigma"], o["J"], o["d"], o["dw"])
+    F = o["solver"].factor(Km)
+    A = K.aug_matrix(o["Wf"], o["sigma"], o["J"], o["d"], 0, o["dw"])
+    dx, dz, hist = K.lifted_solve(F, A, o["J"], o["d"], o["a"], o["b"])
+    return hist[-1]
+
+
+def cpu_baseline(budget_s=12.0, min_solves=3):
+    o = oracle_setup()
+    oracle_step(o)  # warm
+    t0 = time.perf_counter()
+    k = 0
+    while k < min_solves or time.perf_counter() - t0 < budget_s:
+        oracle_step(o)
+        k += 1
+        if k >= 200:
+            break
+    el = time.perf_counter() - t0
+    return {"value": k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} full KKT solves of the same workload in {el:.1f} s "
+                      f"(scipy condensation + plain C up-looking Cholesky + numpy refinement, "
+                      f"single thread; host has {os.cpu_count()} cores)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    o = oracle_setup()
+    for _ in range(args.warmup):
+        oracle_step(o)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(o)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full KKT solves, single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2405_14236_gb300 as cp
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    f64 = dict(dtype=torch.float64, device="cuda")
+    g, p, d, b = build_inputs()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), **f64)
+    opf = cp.Opf(g)
+    n, m = g.n, g.m_e + g.m_i
+    Jv = torch.zeros(opf.nnzJ, **f64)
+    Wv = torch.zeros(opf.nnzW, **f64)
+    gg, hh = torch.zeros(g.m_e, **f64), torch.zeros(g.m_i, **f64)
+    opf.eval(t(p["x"]), t(p["y"]), t(p["z"]), 1.0, None, None, gg, hh, Jv, Wv)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = cp.Symbolic(n, m, opf.J_rowptr, opf.J_colind, opf.W_rowptr, opf.W_colind)
+    symbolic_s = time.perf_counter() - t0
+    N = cp.Numeric(S)
+    sig, dd, a, bb = t(p["sigma_x"]), t(d), t(p["r1"]), t(b)
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dw = 0.0
+    for k in range(40):
+        dw = 0.0 if k == 0 else 1e-4 * 100.0 ** (k - 1)
+        cp.ipm_condense(S, N, Wv, sig, Jv, dd, dw)
+        cp.ipm_factor(S, N, info)
+        if int(info.item()) == -1:
+            break
+    dx, dz = torch.zeros(n, **f64), torch.zeros(m, **f64)
+    eta = torch.zeros(1, **f64)
+    steps_t = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        cp.ipm_condense(S, N, Wv, sig, Jv, dd, dw)
+        e1.record(stream)
+        cp.ipm_factor(S, N, info)
+        e2.record(stream)
+        cp.ipm_aug_solve(S, N, Wv, sig, Jv, dd, dw, a, bb, dx, dz, eta, steps_t)
+
+    e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    for _ in range(args.warmup):
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e3.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ph = np.zeros((args.steps, 3))
+    l0 = cp.launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e3.record(stream)
+        e3.synchronize()
+        ph[k] = [e0.elapsed_time(e1), e1.elapsed_time(e2), e2.elapsed_time(e3)]
+    launches = cp.launch_count() - l0
+    torch.cuda.synchronize()
+    ok = int(info.item()) == -1
+    eta_v, refine = float(eta.item()), int(steps_t.item())
+    # ---- e2e: host buffers, copies inside the timed region
+    hW, hJ, hs, hd, ha, hb = (x.cpu().pin_memory() for x in (Wv, Jv, sig, dd, a, bb))
+    hdx, hdz = torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(m, dtype=torch.float64).pin_memory()
+    dW, dJ, ds_, ddd, da, db = (torch.empty_like(x) for x in (Wv, Jv, sig, dd, a, bb))
+    e_tot = 0.0
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        e0.record(stream)
+        for dst, src in ((dW, hW), (dJ, hJ), (ds_, hs), (ddd, hd), (da, ha), (db, hb)):
+            dst.copy_(src, non_blocking=True)
+        cp.ipm_condense(S, N, dW, ds_, dJ, ddd, dw)
+        cp.ipm_factor(S, N, info)
+        cp.ipm_aug_solve(S, N, dW, ds_, dJ, ddd, dw, da, db, dx, dz, eta, steps_t)
+        hdx.copy_(dx, non_blocking=True)
+        hdz.copy_(dz, non_blocking=True)
+        e3.record(stream)
+        e3.synchronize()
+        e_tot += e0.elapsed_time(e3)
+    n_e2e = max(3, args.steps // 2)
+    clk = clocks.stop()
+    h2d = 8 * (opf.nnzW + opf.nnzJ + n + m + n + m)
+    d2h = 8 * (n + m)
+    step_ms = ph.sum(axis=1)
+    t_max = float(step_ms.sum())
+    if world > 1:
+        tt = torch.tensor([t_max], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / (t_max / 1e3)
+    if rank != 0:
+        return
+    # ---- roofline of the dominant phase
+    hbm, hbm_src = measured_peaks()
+    mean = ph.mean(axis=0)
+    nnzL = S.nnz_offdiag + n
+    nsolves = 1 + refine
+    bytes_ = {
+        "condense": 8.0 * (opf.nnzJ + m + opf.nnzW + n) + 8.0 * S.nnz_k,
+        "factor": 8.0 * (S.nnz_k + nnzL),
+        "solve": nsolves * (2 * 8.0 * nnzL + 3 * 8.0 * n) + 8.0 * (2 * opf.nnzJ + 2 * opf.nnzW),
+    }
+    names = ["condense", "factor", "solve"]
+    dom = int(np.argmax(mean))
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            import hashlib
+            tr = json.load(open(tfile))
+            h = hashlib.sha256(open(os.path.join(ROOT, "paper_2405_14236_gb300", "csrc",
+                                                  "numeric.cu"), "rb").read()).hexdigest()[:16]
+            if tr.get("numeric_cu_sha") == h and names[dom] in tr.get("bytes_per_step", {}):
+                traffic = tr["bytes_per_step"][names[dom]]
+        except Exception:
+            traffic = None
+    ach = bytes_[names[dom]] / (mean[dom] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "nnzJ": opf.nnzJ, "nnzW": opf.nnzW,
+                   "nnzK_lower": S.nnz_k, "nnzL": nnzL, "nsuper": S.nsuper,
+                   "nlevels": S.nlevels, "factor_flops": S.flops, "delta_w": dw,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm,
+                     "unit": "GB/s", "frac": ach / hbm, "peak_source": hbm_src,
+                     "traffic": traffic, "algorithmic_bytes": bytes_[names[dom]]},
+        "phases_ms": {nm: float(v) for nm, v in zip(names, mean)},
+        "factor": {"GB_s": bytes_["factor"] / (mean[1] / 1e3) / 1e9,
+                   "GFLOP_s": S.flops / (mean[1] / 1e3) / 1e9},
+        "backward_error": eta_v, "refine_steps": refine, "factor_ok": ok,
+        "symbolic_s": symbolic_s,
+        "e2e": {"value": n_e2e / (e_tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -71,13 +71,17 @@ int ipm_symbolic(int n, int m, const int *J_rowptr, const int *J_colind, int nnz
                  ipm_sym_t *out);
 
 /* Sizes of a symbolic analysis (host outputs; NULL outputs are skipped).
+ *   nnz_k       structural entries of the lower triangle of K (diagonal included)
  *   nsuper      number of supernodes
  *   nnz_offdiag entries of L below the diagonal (sum of column counts - n)
  *   panel_len   FP64 slots of the supernodal panel storage
  *   nlevels     levels of the supernodal elimination tree
  *   flops       textbook factorization flop count sum_j eta_j (eta_j + 3)              */
-int ipm_symbolic_info(ipm_sym_t sym, int *nsuper, int64_t *nnz_offdiag, int64_t *panel_len,
-                      int *nlevels, double *flops);
+int ipm_symbolic_info(ipm_sym_t sym, int64_t *nnz_k, int *nsuper, int64_t *nnz_offdiag,
+                      int64_t *panel_len, int *nlevels, double *flops);
+
+/* Number of kernels launched so far by the numeric entry points of this process. */
+long long ipm_launch_count(void);
 
 /* Copies the symbolic result to HOST buffers (for bit-exact checks):
  *   perm [n]        perm[k] = original variable at elimination position k
@@ -102,8 +106,8 @@ void ipm_symbolic_destroy(ipm_sym_t sym);
 int ipm_num_create(ipm_sym_t sym, int precision, ipm_num_t *out);
 void ipm_num_destroy(ipm_num_t num);
 
-/* Copies the panel values (panel_len doubles: K after ipm_condense, L after ipm_factor) to a
- * HOST buffer.  Synchronizes. */
+/* Copies the panel values (panel_len doubles: the lower triangle of P K P^T after
+ * ipm_condense, L after ipm_factor) to a HOST buffer.  Synchronizes. */
 int ipm_num_export(ipm_num_t num, double *Lx_host);
 
 /* ipm_condense — K = W + diag(sigma_x) + delta_w I + J^T diag(d_row) J written straight into
@@ -120,10 +124,27 @@ int ipm_condense(ipm_sym_t sym, ipm_num_t num, const double *W_val, const double
 
 /* ipm_factor — supernodal Cholesky P K P^T = L L^T in place (Section 3: Cholesky of the
  * SPD condensed matrix; positive definiteness stands in for the inertia test, Eq. (7)).
- *   d_info  DEVICE int: set to -1 on success, else the smallest elimination position whose
- *           pivot was <= 0 or non-finite.  The call does not read it back.
+ * One persistent kernel runs all panel and update tasks in a topological order; tasks wait on
+ * dependency counters with a bounded number of polls.
+ *   d_info  DEVICE int: set to -1 on success, -2 if a device wait gave up (the factor is then
+ *           invalid and ipm_num_status reports IPM_ERR_TIMEOUT), else the smallest elimination
+ *           position whose pivot was <= 0 or non-finite.  The call does not read it back.
  * The panels then hold L.  Returns IPM_OK unless a usage/CUDA error occurred. */
 int ipm_factor(ipm_sym_t sym, ipm_num_t num, int *d_info, cudaStream_t stream);
+
+/* Device status of the last factorization / solves of this handle: IPM_OK or IPM_ERR_TIMEOUT
+ * (a bounded wait gave up; later solves do nothing until the next ipm_factor).  HOST output.
+ * Synchronizes the device. */
+int ipm_num_status(ipm_num_t num, int *status);
+
+/* Number of ~0.2 us polls a device wait may take before it gives up (default 2^23, about
+ * 2 s).  Process-wide.  IPM_ERR_BAD_ARG if polls < 1. */
+int ipm_set_spin_limit(long long polls);
+
+/* Test hook: raises the number of updates supernode `supernode` waits for by `extra`, so that
+ * the next ipm_factor meets a wait that nothing satisfies (exercises the timeout path
+ * without any fault).  Destroy the symbolic handle afterwards. */
+int ipm_debug_add_dependency(ipm_sym_t sym, int supernode, int extra);
 
 /* ipm_solve — x = K^{-1} b with the factor: y = P b, L z = y, L^T w = z, x = P^T w.
  *   b [n], x [n] (may alias).  nrhs must be 1. */

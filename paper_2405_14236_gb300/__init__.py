@@ -26,19 +26,23 @@ I64 = ctypes.c_int64
 _SIGS = {
     "ipm_last_error_message": (ctypes.c_char_p, []),
     "ipm_symbolic": (I, [I, I, P, P, I, P, P, I, P, P]),
-    "ipm_symbolic_info": (I, [P, P, P, P, P, P]),
+    "ipm_symbolic_info": (I, [P, P, P, P, P, P, P]),
+    "ipm_launch_count": (ctypes.c_longlong, []),
     "ipm_symbolic_export": (I, [P, P, P, P, P, P]),
     "ipm_symbolic_export_panels": (I, [P, P, P, P]),
     "ipm_symbolic_destroy": (None, [P]),
     "ipm_num_create": (I, [P, I, P]),
     "ipm_num_destroy": (None, [P]),
     "ipm_num_export": (I, [P, P]),
+    "ipm_num_status": (I, [P, P]),
+    "ipm_set_spin_limit": (I, [ctypes.c_longlong]),
+    "ipm_debug_add_dependency": (I, [P, I, I]),
     "ipm_condense": (I, [P, P, P, P, P, P, D, P]),
     "ipm_factor": (I, [P, P, P, P]),
     "ipm_solve": (I, [P, P, P, P, I, P]),
     "ipm_aug_solve": (I, [P, P, P, P, P, P, D, P, P, P, P, I, D, P, P, P]),
     "hykkt_cg": (I, [P, P, I, P, P, D, P, P, D, I, P, P, P, P, P, P]),
-    "ipm_opf_create": (I, [I, I, I] + [P] * 14 + [P, P]),
+    "ipm_opf_create": (I, [I, I, I] + [P] * 13 + [P, P]),
     "ipm_opf_info": (I, [P, P, P, P, P, P]),
     "ipm_opf_patterns": (I, [P, P, P, P, P]),
     "ipm_opf_eval": (I, [P, P, P, P, D, P, P, P, P, P, P, P]),
@@ -63,6 +67,11 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched so far by the library's numeric entry points."""
+    return int(lib().ipm_launch_count())
 
 
 def exported_symbols():
@@ -104,9 +113,11 @@ class Symbolic:
                                   _stream(stream), ctypes.byref(h)), "ipm_symbolic")
         self.h = h
         self.n, self.m = n, m
-        ns, nnz, plen, nl, fl = I(), I64(), I64(), I(), D()
-        _check(lib().ipm_symbolic_info(h, ctypes.byref(ns), ctypes.byref(nnz), ctypes.byref(plen),
-                                       ctypes.byref(nl), ctypes.byref(fl)), "ipm_symbolic_info")
+        nk, ns, nnz, plen, nl, fl = I64(), I(), I64(), I64(), I(), D()
+        _check(lib().ipm_symbolic_info(h, ctypes.byref(nk), ctypes.byref(ns), ctypes.byref(nnz),
+                                       ctypes.byref(plen), ctypes.byref(nl), ctypes.byref(fl)),
+               "ipm_symbolic_info")
+        self.nnz_k = nk.value
         self.nsuper, self.nnz_offdiag, self.panel_len = ns.value, nnz.value, plen.value
         self.nlevels, self.flops = nl.value, fl.value
 
@@ -155,6 +166,21 @@ class Numeric:
         if getattr(self, "h", None) and _lib is not None:
             _lib.ipm_num_destroy(self.h)
             self.h = None
+
+
+def ipm_num_status(num):
+    st = I()
+    _check(lib().ipm_num_status(num.h, ctypes.byref(st)), "ipm_num_status")
+    return st.value
+
+
+def ipm_set_spin_limit(polls):
+    return _check(lib().ipm_set_spin_limit(int(polls)), "ipm_set_spin_limit")
+
+
+def ipm_debug_add_dependency(sym, supernode, extra=1):
+    return _check(lib().ipm_debug_add_dependency(sym.h, int(supernode), int(extra)),
+                  "ipm_debug_add_dependency")
 
 
 def ipm_condense(sym, num, W_val, sigma_x, J_val, d_row, delta_w, stream=None):

@@ -1,9 +1,13 @@
 // Error plumbing and device-wide prefix scans for libcondipm.
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
 
 namespace cipm {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static std::mutex g_err_mu;
 static std::string g_err;
@@ -138,6 +142,8 @@ int inclusive_max_scan_i32(const int *in, int *out, int64_t n, cudaStream_t s) {
 }
 
 }  // namespace cipm
+
+extern "C" long long ipm_launch_count(void) { return cipm::g_launches.load(); }
 
 extern "C" const char *ipm_last_error_message(void) {
   std::lock_guard<std::mutex> lk(cipm::g_err_mu);

@@ -12,6 +12,8 @@
 namespace cipm {
 
 void set_error(const char *where, cudaError_t e);
+// Counts kernel launches issued by the numeric entry points (reported by ipm_launch_count).
+void count_launches(long long k);
 void set_error_msg(const std::string &msg);
 
 #define CK(call)                              \

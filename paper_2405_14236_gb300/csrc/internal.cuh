@@ -35,13 +35,34 @@ struct ipm_sym_s {
   int *level_sn = nullptr;             // supernodes grouped by level
   std::vector<int> h_level_ptr;        // host copy, nlevels + 1 entries
   std::vector<int> h_level_maxld;      // max panel rows in each level
+  std::vector<int> h_level_maxw;       // max supernode width in each level
   double flops = 0.0;
+  int64_t nnz_k = 0;  // structural entries of tril(K)
+  // factorization task lists per level: panel tasks (supernode, row block) and update tasks
+  // (supernode, row block i, row block j <= i) of the rows below the diagonal block
+  int4 *panel_tasks = nullptr, *upd_tasks = nullptr;
+  int64_t *dptr = nullptr;  // offsets of the w x w diagonal factors L11 (separate array)
+  int64_t diag_len = 0;
+  // sync-free schedule: all factorization tasks in one topological order (x = supernode,
+  // y/z = row blocks, w = 0 panel / 1 update), dependency counts per supernode
+  int4 *ftasks = nullptr;
+  int nftasks = 0;
+  int *upd_need = nullptr;  // update tasks that scatter into each supernode
+  int *fwd_need = nullptr;  // supernodes whose rows below the diagonal reach each supernode
+  std::vector<int> h_panel_ptr, h_upd_ptr;  // per level, nlevels + 1 entries
 };
+
+#define CIPM_RB 32  // rows per block of the below-diagonal part of a panel
 
 struct ipm_num_s {
   ipm_sym_t sym = nullptr;
   int precision = 64;
   double *Lx = nullptr;  // panel values
+  double *Dx = nullptr;  // diagonal factors L11 of every supernode (column-major w x w)
+  bool factored = false;  // panels hold L21 and Dx holds L11 (else panels hold K)
+  // dependency counters of the sync-free kernels: [0,ns) update arrivals, [ns,2ns) panel
+  // tasks done, [2ns,3ns) forward arrivals, [3ns,4ns) backward done flags, then tickets/status
+  int *sync = nullptr;
   // workspaces (n or m sized), allocated once
   double *vn[8] = {nullptr};
   double *vm[6] = {nullptr};

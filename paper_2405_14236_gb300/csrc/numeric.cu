@@ -55,66 +55,10 @@ __device__ __forceinline__ int find_row(const int *rows, int ld, int i) {
 
 struct FactArgs {
   const int *level_sn, *sptr, *srow_ptr, *srow, *snode;
-  const int64_t *lptr;
-  double *Lx;
+  const int64_t *lptr, *dptr;
+  double *Lx, *Dx;
   int *info;
 };
-
-// One block per supernode of the level: dense right-looking Cholesky of the ld x w panel
-// (diagonal block and the rows below it), then the update -L21 L21^T scattered into the
-// ancestors' panels with FP64 atomics.
-__global__ void __launch_bounds__(256) k_factor_level(FactArgs A, int lvl_begin) {
-  const int s = A.level_sn[lvl_begin + blockIdx.x];
-  const int f = A.sptr[s], w = A.sptr[s + 1] - f;
-  const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
-  const int *rows = A.srow + rb;
-  double *P = A.Lx + A.lptr[s];
-  __shared__ double s_piv;
-  for (int k = 0; k < w; ++k) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double d = P[k + (int64_t)k * ld];
-      if (!(d > 0.0) || !isfinite(d)) {
-        atomicMin(A.info, f + k);
-        d = 1.0;
-      }
-      double piv = sqrt(d);
-      P[k + (int64_t)k * ld] = piv;
-      s_piv = piv;
-    }
-    __syncthreads();
-    const double inv = 1.0 / s_piv;
-    double *colk = P + (int64_t)k * ld;
-    for (int i = k + 1 + threadIdx.x; i < ld; i += blockDim.x) colk[i] *= inv;
-    __syncthreads();
-    const int nc = w - k - 1;
-    const int64_t tot = (int64_t)nc * ld;
-    for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
-      int j = k + 1 + (int)(t / ld);
-      int i = (int)(t - (int64_t)(j - k - 1) * ld);
-      if (i >= j) P[i + (int64_t)j * ld] -= colk[i] * colk[j];
-    }
-  }
-  __syncthreads();
-  const int B = ld - w;
-  if (B <= 0) return;
-  const int64_t npair = (int64_t)B * (B + 1) / 2;
-  for (int64_t t = threadIdx.x; t < npair; t += blockDim.x) {
-    // t -> (ii >= jj)
-    int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
-    while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
-    int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
-    const int i = w + ii, j = w + jj;
-    double v = 0.0;
-    for (int k = 0; k < w; ++k) v += P[i + (int64_t)k * ld] * P[j + (int64_t)k * ld];
-    const int col = rows[j], row = rows[i];
-    const int ts = A.snode[col];
-    const int tb = A.srow_ptr[ts], tld = A.srow_ptr[ts + 1] - tb;
-    const int r = find_row(A.srow + tb, tld, row);
-    atomicAdd(&A.Lx[A.lptr[ts] + (int64_t)(col - A.sptr[ts]) * tld + r], -v);
-  }
-}
 
 // ---------------------------------------------------------------- triangular solves
 __global__ void k_gather_perm(const int *perm, int n, const double *b, double *y) {
@@ -128,67 +72,318 @@ __global__ void k_scatter_perm(const int *perm, int n, const double *y, double *
 
 struct SolveArgs {
   const int *level_sn, *sptr, *srow_ptr, *srow;
-  const int64_t *lptr;
-  const double *Lx;
+  const int64_t *lptr, *dptr;
+  const double *Lx, *Dx;
   double *y;
 };
 
-// forward: y_s = L11^{-1} y_s, then y[rows below] -= L21 y_s
-__global__ void __launch_bounds__(128) k_fwd_level(SolveArgs A, int lvl_begin) {
-  const int s = A.level_sn[lvl_begin + blockIdx.x];
-  const int f = A.sptr[s], w = A.sptr[s + 1] - f;
-  const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
-  const int *rows = A.srow + rb;
-  const double *P = A.Lx + A.lptr[s];
-  __shared__ double ys[CIPM_SN_MAXW];
-  for (int k = threadIdx.x; k < w; k += blockDim.x) ys[k] = A.y[f + k];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int k = 0; k < w; ++k) {
-      if (lane == (k & 31)) ys[k] /= P[k + (int64_t)k * ld];
-      __syncwarp();
-      const double yk = ys[k];
-      for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= P[i + (int64_t)k * ld] * yk;
-      __syncwarp();
+// ---------------------------------------------------------------- sync-free scheduling
+// Persistent kernels take tasks in one topological order through an atomic ticket.  A task
+// waits (thread 0, bounded) until its dependency counter is complete, works, makes its writes
+// visible (every thread fences, then a barrier) and signals its dependents.  A block only
+// waits on tasks with smaller tickets, which running blocks already hold, so the schedule
+// cannot deadlock.  Data written inside the same launch is read through L2 (__ldcg).
+// A wait that exceeds the spin limit records IPM_ERR_TIMEOUT and raises an abort flag that
+// makes every block stop taking tasks.
+__device__ long long g_spin_limit = 1ll << 23;  // polls of ~0.2 us each before giving up
+
+struct SyncCtl {
+  int *cnt;      // per-supernode counters (layout in ipm_num_s::sync)
+  int *ticket;   // this kernel's ticket
+  int *abort_;   // shared abort flag
+  int *status;   // IPM_ERR_TIMEOUT on a timed-out wait
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// thread 0 only: wait until *p >= need; false when aborted or timed out
+__device__ bool spin_geq(const int *p, int need, const SyncCtl &C) {
+  long long it = 0;
+  while (ld_acquire(p) < need) {
+    if (ld_acquire(C.abort_)) return false;
+    if (++it > g_spin_limit) {
+      atomicExch(C.status, IPM_ERR_TIMEOUT);
+      atomicExch(C.abort_, 1);
+      return false;
     }
+    __nanosleep(128);
+  }
+  return true;
+}
+
+// every thread: make this thread's writes/atomics visible device-wide, then a barrier
+__device__ __forceinline__ void publish() {
+  __threadfence();
+  __syncthreads();
+}
+
+struct FactTaskArgs {
+  FactArgs F;
+  const int4 *tasks;
+  int ntasks;
+  const int *upd_need;
+  SyncCtl C;  // cnt: [0,ns) update arrivals, [ns,2ns) panel tasks done
+  int ns;
+};
+
+__device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm, int *s_ok) {
+  const FactArgs &A = T.F;
+  if (threadIdx.x == 0) *s_ok = spin_geq(T.C.cnt + s, T.upd_need[s], T.C);
+  __syncthreads();
+  if (!*s_ok) return;
+  const int f = A.sptr[s], w = A.sptr[s + 1] - f;
+  const int ld = A.srow_ptr[s + 1] - A.srow_ptr[s];
+  double *P = A.Lx + A.lptr[s];
+  double *sL = sm, *sR = sm + w * w;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int t = tid; t < w * w; t += bd) {
+    int k = t / w, i = t - k * w;
+    sL[t] = i >= k ? __ldcg(P + i + (int64_t)k * ld) : 0.0;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < w; k += blockDim.x) A.y[f + k] = ys[k];
-  for (int i = w + threadIdx.x; i < ld; i += blockDim.x) {
-    double t = 0.0;
-    for (int k = 0; k < w; ++k) t += P[i + (int64_t)k * ld] * ys[k];
-    atomicAdd(&A.y[rows[i]], -t);
+  for (int k = 0; k < w; ++k) {
+    if (tid == 0) {
+      double d = sL[k + k * w];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicMin(A.info, f + k);
+        d = 1.0;
+      }
+      sL[k + k * w] = sqrt(d);
+    }
+    __syncthreads();
+    const double inv = 1.0 / sL[k + k * w];
+    const int nr = w - k - 1;
+    for (int i = k + 1 + tid; i < w; i += bd) sL[i + k * w] *= inv;
+    __syncthreads();
+    // trailing update: thread (ii, jj) on a fixed 2-D layout, no divisions in the loop
+    for (int jj = tid / 32; jj < nr; jj += bd / 32) {
+      const int j = k + 1 + jj;
+      const double ljk = sL[j + k * w];
+      for (int i = j + (tid & 31); i < w; i += 32) sL[i + j * w] -= sL[i + k * w] * ljk;
+    }
+    __syncthreads();
+  }
+  if (rb == 0) {
+    double *Dd = A.Dx + A.dptr[s];
+    for (int t = tid; t < w * w; t += bd) Dd[t] = sL[t];
+  }
+  const int r0 = w + rb * CIPM_RB;
+  const int nrow = min(CIPM_RB, ld - r0);
+  if (nrow > 0) {
+    const int sw = w + 1;
+    for (int t = tid; t < nrow * w; t += bd) {
+      int k = t / nrow, r = t - k * nrow;
+      sR[r * sw + k] = __ldcg(P + (r0 + r) + (int64_t)k * ld);
+    }
+    __syncthreads();
+    // each warp owns rows r = warp, warp + nwarps, ...; lanes split the columns
+    const int warp = tid >> 5, lane = tid & 31, nw = bd >> 5;
+    for (int k = 0; k < w; ++k) {
+      const double inv = 1.0 / sL[k + k * w];
+      for (int r = warp; r < nrow; r += nw) {
+        double xk = sR[r * sw + k] * inv;
+        __syncwarp();
+        for (int j = k + 1 + lane; j < w; j += 32) sR[r * sw + j] -= xk * sL[j + k * w];
+        if (lane == 0) sR[r * sw + k] = xk;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nrow * w; t += bd) {
+      int k = t / nrow, r = t - k * nrow;
+      P[(r0 + r) + (int64_t)k * ld] = sR[r * sw + k];
+    }
+  }
+  publish();
+  if (tid == 0) atomicAdd(T.C.cnt + T.ns + s, 1);
+}
+
+__device__ void fact_update_task(const FactTaskArgs &T, int s, int ti, int tj, double *sm,
+                                 int *s_ok) {
+  const FactArgs &A = T.F;
+  const int f = A.sptr[s], w = A.sptr[s + 1] - f;
+  const int rbase = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rbase;
+  const int B = ld - w;
+  const int npanel = (B + CIPM_RB - 1) / CIPM_RB;
+  if (threadIdx.x == 0) *s_ok = spin_geq(T.C.cnt + T.ns + s, npanel, T.C);
+  __syncthreads();
+  if (!*s_ok) return;
+  const int *rows = A.srow + rbase;
+  const double *P = A.Lx + A.lptr[s];
+  const int sw = w + 1;
+  double *sI = sm, *sJ = sm + CIPM_RB * sw;
+  const int i0 = w + ti * CIPM_RB, ni = min(CIPM_RB, ld - i0);
+  const int j0 = w + tj * CIPM_RB, nj = min(CIPM_RB, ld - j0);
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int t = tid; t < ni * w; t += bd) {
+    int k = t / ni, r = t - k * ni;
+    sI[r * sw + k] = __ldcg(P + (i0 + r) + (int64_t)k * ld);
+  }
+  for (int t = tid; t < nj * w; t += bd) {
+    int k = t / nj, r = t - k * nj;
+    sJ[r * sw + k] = __ldcg(P + (j0 + r) + (int64_t)k * ld);
+  }
+  __syncthreads();
+  for (int p = tid; p < ni * nj; p += bd) {
+    const int ii = p / nj, jj = p - (p / nj) * nj;
+    const int i = i0 + ii, j = j0 + jj;
+    if (i < j) continue;
+    const double *a = sI + ii * sw, *b = sJ + jj * sw;
+    double v = 0.0;
+    for (int k = 0; k < w; ++k) v += a[k] * b[k];
+    const int col = rows[j], row = rows[i];
+    const int ts = A.snode[col];
+    const int tb = A.srow_ptr[ts], tld = A.srow_ptr[ts + 1] - tb;
+    const int r = find_row(A.srow + tb, tld, row);
+    atomicAdd(&A.Lx[A.lptr[ts] + (int64_t)(col - A.sptr[ts]) * tld + r], -v);
+  }
+  publish();
+  if (tid == 0) {
+    int last = -1;
+    for (int j = j0; j < j0 + nj; ++j) {
+      int t = A.snode[rows[j]];
+      if (t != last) atomicAdd(T.C.cnt + t, 1);
+      last = t;
+    }
   }
 }
 
-// backward: y_s = L11^{-T} (y_s - L21^T y[rows below])
-__global__ void __launch_bounds__(128) k_bwd_level(SolveArgs A, int lvl_begin) {
-  const int s = A.level_sn[lvl_begin + blockIdx.x];
-  const int f = A.sptr[s], w = A.sptr[s + 1] - f;
-  const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
-  const int *rows = A.srow + rb;
-  const double *P = A.Lx + A.lptr[s];
-  __shared__ double zs[CIPM_SN_MAXW];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < w; k += nw) {
-    double acc = 0.0;
-    for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * A.y[rows[i]];
-    acc = warp_sum(acc);
-    if (lane == 0) zs[k] = A.y[f + k] - acc;
+__global__ void __launch_bounds__(256) k_factor_dag(FactTaskArgs T) {
+  extern __shared__ double sm[];
+  __shared__ int s_t, s_ok;
+  while (true) {
+    if (threadIdx.x == 0) s_t = ld_acquire(T.C.abort_) ? T.ntasks : atomicAdd(T.C.ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    __syncthreads();
+    if (t >= T.ntasks) break;
+    const int4 tk = T.tasks[t];
+    if (tk.w == 0) fact_panel_task(T, tk.x, tk.y, sm, &s_ok);
+    else fact_update_task(T, tk.x, tk.y, tk.z, sm, &s_ok);
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    for (int k = w - 1; k >= 0; --k) {
-      if (lane == (k & 31)) zs[k] /= P[k + (int64_t)k * ld];
-      __syncwarp();
-      const double xk = zs[k];
-      for (int j = lane; j < k; j += 32) zs[j] -= P[k + (int64_t)j * ld] * xk;
-      __syncwarp();
+}
+
+struct SolveTaskArgs {
+  SolveArgs A;
+  const int *snode;
+  const int *fwd_need;
+  SyncCtl C;  // cnt: forward arrivals (fwd) or backward done flags (bwd)
+  int ns;
+};
+
+// forward solve, supernodes deepest level first: wait for every contribution into y_s
+__global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
+  extern __shared__ double sL[];
+  __shared__ double ys[CIPM_SN_MAXW];
+  __shared__ int s_t, s_ok;
+  const SolveArgs &A = T.A;
+  while (true) {
+    if (threadIdx.x == 0) s_t = ld_acquire(T.C.abort_) ? T.ns : atomicAdd(T.C.ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    __syncthreads();
+    if (t >= T.ns) break;
+    const int s = A.level_sn[t];
+    if (threadIdx.x == 0) s_ok = spin_geq(T.C.cnt + s, T.fwd_need[s], T.C);
+    __syncthreads();
+    if (!s_ok) continue;
+    const int f = A.sptr[s], w = A.sptr[s + 1] - f;
+    const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
+    const int *rows = A.srow + rb;
+    const double *P = A.Lx + A.lptr[s];
+    const double *Dd = A.Dx + A.dptr[s];
+    for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q] = Dd[q];
+    for (int k = threadIdx.x; k < w; k += blockDim.x) ys[k] = __ldcg(A.y + f + k);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int k = 0; k < w; ++k) {
+        if (lane == (k & 31)) ys[k] /= sL[k + k * w];
+        __syncwarp();
+        const double yk = ys[k];
+        for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= sL[i + k * w] * yk;
+        __syncwarp();
+      }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < w; k += blockDim.x) A.y[f + k] = ys[k];
+    for (int i = w + threadIdx.x; i < ld; i += blockDim.x) {
+      double acc = 0.0;
+      for (int k = 0; k < w; ++k) acc += P[i + (int64_t)k * ld] * ys[k];
+      atomicAdd(&A.y[rows[i]], -acc);
+    }
+    publish();
+    if (threadIdx.x == 0) {
+      int last = -1;
+      for (int i = w; i < ld; ++i) {
+        int tg = T.snode[rows[i]];
+        if (tg != last) atomicAdd(T.C.cnt + tg, 1);
+        last = tg;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < w; k += blockDim.x) A.y[f + k] = zs[k];
+}
+
+// backward solve, root first: wait until every supernode holding rows below s is done
+__global__ void __launch_bounds__(128) k_bwd_dag(SolveTaskArgs T) {
+  extern __shared__ double sL[];
+  __shared__ double zs[CIPM_SN_MAXW];
+  __shared__ int s_t, s_ok;
+  const SolveArgs &A = T.A;
+  while (true) {
+    if (threadIdx.x == 0) s_t = ld_acquire(T.C.abort_) ? T.ns : atomicAdd(T.C.ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    __syncthreads();
+    if (t >= T.ns) break;
+    const int s = A.level_sn[T.ns - 1 - t];
+    const int f = A.sptr[s], w = A.sptr[s + 1] - f;
+    const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
+    const int *rows = A.srow + rb;
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      int last = -1;
+      for (int i = w; i < ld && ok; ++i) {
+        int tg = T.snode[rows[i]];
+        if (tg != last) ok = spin_geq(T.C.cnt + tg, 1, T.C);
+        last = tg;
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) continue;
+    const double *P = A.Lx + A.lptr[s];
+    const double *Dd = A.Dx + A.dptr[s];
+    for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q] = Dd[q];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < w; k += nw) {
+      double acc = 0.0;
+      for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * __ldcg(A.y + rows[i]);
+      acc = warp_sum(acc);
+      if (lane == 0) zs[k] = __ldcg(A.y + f + k) - acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      for (int k = w - 1; k >= 0; --k) {
+        if (lane == (k & 31)) zs[k] /= sL[k + k * w];
+        __syncwarp();
+        const double xk = zs[k];
+        for (int j = lane; j < k; j += 32) zs[j] -= sL[k + j * w] * xk;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < w; k += blockDim.x) A.y[f + k] = zs[k];
+    publish();
+    if (threadIdx.x == 0) atomicExch(T.C.cnt + s, 1);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- sparse products
@@ -225,6 +420,24 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// max over the block of v, then one atomic per block (all threads must call)
+__device__ __forceinline__ void block_max_to(double *addr, double v, double *sh) {
+  v = warp_max(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    x = warp_max(x);
+    if (threadIdx.x == 0) atomic_max_nonneg(addr, x);
+  }
+  __syncthreads();
+}
+
 // partial[b] = sum over the block's range of x.y
 __global__ void k_dot_partial(const double *x, const double *y, int n, double *partial) {
   __shared__ double sh[32];
@@ -258,8 +471,10 @@ static constexpr int DOT_BLOCKS = 152;
 static int dot(const double *x, const double *y, int n, double *partial, double *out,
                cudaStream_t s) {
   k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(x, y, n, partial);
+  count_launches(1);
   CKL();
   k_dot_final<<<1, 256, 0, s>>>(partial, DOT_BLOCKS, out);
+  count_launches(1);
   CKL();
   return IPM_OK;
 }
@@ -282,55 +497,64 @@ struct AugArgs {
 };
 
 __global__ void k_aug_resid_x(AugArgs A) {
+  __shared__ double sh[32];
   int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= A.n) return;
-  double acc = (A.sigma[j] + A.dw) * A.sx[j];
-  double asum = 0.0;
-  double diag = A.sigma[j] + A.dw;
-  for (int p = A.W_rowptr[j]; p < A.W_rowptr[j + 1]; ++p) {
-    int c = A.W_colind[p];
-    acc += A.Wv[p] * A.sx[c];
-    if (c == j) diag += A.Wv[p];
-    else asum += fabs(A.Wv[p]);
+  double res = 0.0, solv = 0.0, rhsv = 0.0, asum = 0.0;
+  if (j < A.n) {
+    double acc = (A.sigma[j] + A.dw) * A.sx[j];
+    double diag = A.sigma[j] + A.dw;
+    for (int p = A.W_rowptr[j]; p < A.W_rowptr[j + 1]; ++p) {
+      int c = A.W_colind[p];
+      acc += A.Wv[p] * A.sx[c];
+      if (c == j) diag += A.Wv[p];
+      else asum += fabs(A.Wv[p]);
+    }
+    for (int t = A.WT_ptr[j]; t < A.WT_ptr[j + 1]; ++t) {
+      int e = A.WT_ent[t];
+      int r = A.W_rowidx[e];
+      if (r == j) continue;
+      acc += A.Wv[e] * A.sx[r];
+      asum += fabs(A.Wv[e]);
+    }
+    asum += fabs(diag);
+    for (int t = A.JT_ptr[j]; t < A.JT_ptr[j + 1]; ++t) {
+      int p = A.JT_ent[t];
+      acc += A.Jv[p] * A.sz[A.J_rowidx[p]];
+      asum += fabs(A.Jv[p]);
+    }
+    res = A.ra[j] - acc;
+    A.outx[j] = res;
+    solv = fabs(A.sx[j]);
+    rhsv = fabs(A.ra[j]);
   }
-  for (int t = A.WT_ptr[j]; t < A.WT_ptr[j + 1]; ++t) {
-    int e = A.WT_ent[t];
-    int r = A.W_rowidx[e];
-    if (r == j) continue;
-    acc += A.Wv[e] * A.sx[r];
-    asum += fabs(A.Wv[e]);
-  }
-  asum += fabs(diag);
-  for (int t = A.JT_ptr[j]; t < A.JT_ptr[j + 1]; ++t) {
-    int p = A.JT_ent[t];
-    acc += A.Jv[p] * A.sz[A.J_rowidx[p]];
-    asum += fabs(A.Jv[p]);
-  }
-  double res = A.ra[j] - acc;
-  A.outx[j] = res;
-  atomic_max_nonneg(&A.scal[0], fabs(res));
-  atomic_max_nonneg(&A.scal[1], fabs(A.sx[j]));
-  atomic_max_nonneg(&A.scal[2], fabs(A.ra[j]));
-  if (A.want_norm_a) atomic_max_nonneg(&A.scal[3], asum);
+  block_max_to(&A.scal[0], fabs(res), sh);
+  block_max_to(&A.scal[1], solv, sh);
+  block_max_to(&A.scal[2], rhsv, sh);
+  if (A.want_norm_a) block_max_to(&A.scal[3], asum, sh);
 }
 
 __global__ void k_aug_resid_z(AugArgs A) {
+  __shared__ double sh[32];
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= A.m) return;
-  double acc = 0.0, asum = 0.0;
-  for (int p = A.J_rowptr[r]; p < A.J_rowptr[r + 1]; ++p) {
-    acc += A.Jv[p] * A.sx[A.J_colind[p]];
-    asum += fabs(A.Jv[p]);
+  double res = 0.0, solv = 0.0, rhsv = 0.0, asum = 0.0;
+  if (r < A.m) {
+    double acc = 0.0;
+    for (int p = A.J_rowptr[r]; p < A.J_rowptr[r + 1]; ++p) {
+      acc += A.Jv[p] * A.sx[A.J_colind[p]];
+      asum += fabs(A.Jv[p]);
+    }
+    double e = r >= A.m_e ? 1.0 / A.d[r] : 0.0;
+    acc -= e * A.sz[r];
+    asum += fabs(e);
+    res = A.rb[r] - acc;
+    A.outz[r] = res;
+    solv = fabs(A.sz[r]);
+    rhsv = fabs(A.rb[r]);
   }
-  double e = r >= A.m_e ? 1.0 / A.d[r] : 0.0;
-  acc -= e * A.sz[r];
-  asum += fabs(e);
-  double res = A.rb[r] - acc;
-  A.outz[r] = res;
-  atomic_max_nonneg(&A.scal[0], fabs(res));
-  atomic_max_nonneg(&A.scal[1], fabs(A.sz[r]));
-  atomic_max_nonneg(&A.scal[2], fabs(A.rb[r]));
-  if (A.want_norm_a) atomic_max_nonneg(&A.scal[3], asum);
+  block_max_to(&A.scal[0], fabs(res), sh);
+  block_max_to(&A.scal[1], solv, sh);
+  block_max_to(&A.scal[2], rhsv, sh);
+  if (A.want_norm_a) block_max_to(&A.scal[3], asum, sh);
 }
 
 // elementwise helpers
@@ -366,13 +590,25 @@ __global__ void k_cg_update_p(int n, const double *scal, const double *r, double
 }
 __global__ void k_copy_scalar(const double *src, double *dst) { *dst = *src; }
 __global__ void k_info_set(int *info) { *info = INT_MAX; }
-__global__ void k_info_fix(int *info) {
-  if (*info == INT_MAX) *info = -1;
+__global__ void k_info_fix(int *info, const int *status) {
+  if (*status != 0) *info = -2;  // a bounded device wait gave up
+  else if (*info == INT_MAX) *info = -1;
 }
 
 }  // namespace cipm
 
 using namespace cipm;
+
+static int set_smem_limits() {
+  static bool done = false;
+  if (done) return IPM_OK;
+  const int big = 64 * 1024;
+  CK(cudaFuncSetAttribute(k_factor_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_fwd_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_bwd_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  done = true;
+  return IPM_OK;
+}
 
 extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
   if (!S || !out || precision != 64) {
@@ -380,10 +616,15 @@ extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
     return IPM_ERR_BAD_ARG;
   }
   *out = nullptr;
+  CKR(set_smem_limits());
   ipm_num_t N = new ipm_num_s();
   N->sym = S;
   N->precision = precision;
   int rc = dev_alloc(&N->Lx, S->panel_len);
+  if (rc == IPM_OK) rc = dev_alloc(&N->Dx, S->diag_len);
+  if (rc == IPM_OK) rc = dev_alloc(&N->sync, 4 * (int64_t)S->nsuper + 16);
+  if (rc == IPM_OK && cudaMemset(N->sync, 0, sizeof(int) * (4 * (size_t)S->nsuper + 16)) != cudaSuccess)
+    rc = IPM_ERR_CUDA;
   for (int k = 0; k < 8 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vn[k], S->n);
   for (int k = 0; k < 6 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vm[k], S->m > 0 ? S->m : 1);
   if (rc == IPM_OK) rc = dev_alloc(&N->scal, 64 + DOT_BLOCKS);
@@ -400,6 +641,8 @@ extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
 extern "C" void ipm_num_destroy(ipm_num_t N) {
   if (!N) return;
   if (N->Lx) cudaFree(N->Lx);
+  if (N->Dx) cudaFree(N->Dx);
+  if (N->sync) cudaFree(N->sync);
   for (auto *p : N->vn)
     if (p) cudaFree(p);
   for (auto *p : N->vm)
@@ -411,9 +654,56 @@ extern "C" void ipm_num_destroy(ipm_num_t N) {
 
 extern "C" int ipm_num_export(ipm_num_t N, double *Lx_host) {
   if (!N || !Lx_host) return IPM_ERR_BAD_ARG;
+  ipm_sym_t S = N->sym;
   CK(cudaDeviceSynchronize());
-  CK(cudaMemcpy(Lx_host, N->Lx, sizeof(double) * N->sym->panel_len, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(Lx_host, N->Lx, sizeof(double) * S->panel_len, cudaMemcpyDeviceToHost));
+  if (N->factored) {
+    // the factor keeps L11 in a separate array: put it into the panels' diagonal blocks
+    const int ns = S->nsuper;
+    std::vector<double> D(S->diag_len);
+    std::vector<int64_t> lp(ns + 1), dp(ns + 1);
+    std::vector<int> sp(ns + 1), rp(ns + 1);
+    CK(cudaMemcpy(D.data(), N->Dx, sizeof(double) * S->diag_len, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(lp.data(), S->lptr, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(dp.data(), S->dptr, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(sp.data(), S->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rp.data(), S->srow_ptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost));
+    for (int s = 0; s < ns; ++s) {
+      int w = sp[s + 1] - sp[s], ld = rp[s + 1] - rp[s];
+      for (int k = 0; k < w; ++k)
+        for (int i = 0; i < w; ++i)
+          Lx_host[lp[s] + (int64_t)k * ld + i] = i >= k ? D[dp[s] + (int64_t)k * w + i] : 0.0;
+    }
+  }
   return IPM_OK;
+}
+
+extern "C" int ipm_num_status(ipm_num_t N, int *status) {
+  if (!N || !status) return IPM_ERR_BAD_ARG;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(status, N->sync + 4 * N->sym->nsuper + 4, sizeof(int), cudaMemcpyDeviceToHost));
+  return IPM_OK;
+}
+
+extern "C" int ipm_set_spin_limit(long long polls) {
+  if (polls < 1) return IPM_ERR_BAD_ARG;
+  CK(cudaMemcpyToSymbol(g_spin_limit, &polls, sizeof(polls)));
+  return IPM_OK;
+}
+
+extern "C" int ipm_debug_add_dependency(ipm_sym_t S, int supernode, int extra) {
+  if (!S || supernode < 0 || supernode >= S->nsuper) return IPM_ERR_BAD_ARG;
+  int v = 0;
+  CK(cudaMemcpy(&v, S->upd_need + supernode, sizeof(int), cudaMemcpyDeviceToHost));
+  v += extra;
+  CK(cudaMemcpy(S->upd_need + supernode, &v, sizeof(int), cudaMemcpyHostToDevice));
+  return IPM_OK;
+}
+
+static int device_status(ipm_num_t N) {
+  int st = 0;
+  CK(cudaMemcpy(&st, N->sync + 4 * N->sym->nsuper + 4, sizeof(int), cudaMemcpyDeviceToHost));
+  return st;
 }
 
 extern "C" int ipm_condense(ipm_sym_t S, ipm_num_t N, const double *W_val, const double *sigma_x,
@@ -422,39 +712,86 @@ extern "C" int ipm_condense(ipm_sym_t S, ipm_num_t N, const double *W_val, const
   if (!S || !N || N->sym != S || !sigma_x || (S->nnzW && !W_val) || (S->nnzJ && (!J_val || !d_row)))
     return IPM_ERR_BAD_ARG;
   if (S->nsuper == 0) return IPM_OK;
+  N->factored = false;
   k_condense<<<S->nsuper, 128, 0, s>>>(S->sptr, S->srow_ptr, S->lptr, S->slot_ptr, S->items,
                                        S->J_rowidx, S->perm, W_val, sigma_x, J_val, d_row,
                                        delta_w, N->Lx);
+  count_launches(1);
   CKL();
   return IPM_OK;
 }
 
+static int persistent_grid(const void *kernel, int threads, size_t smem) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+  occ = std::max(1, std::min(occ, 4));
+  return nsm * occ;
+}
+
+static SyncCtl sync_ctl(ipm_sym_t S, ipm_num_t N, int region, int ticket) {
+  const int ns = S->nsuper;
+  int *tail = N->sync + 4 * ns;
+  return SyncCtl{N->sync + region * ns, tail + ticket, tail + 3, tail + 4};
+}
+
 extern "C" int ipm_factor(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s) {
   if (!S || !N || N->sym != S || !d_info) return IPM_ERR_BAD_ARG;
+  const int ns = S->nsuper;
+  // counters of the factorization (update arrivals, panel tasks done), its ticket, abort, status
+  CK(cudaMemsetAsync(N->sync, 0, sizeof(int) * 2 * ns, s));
+  CK(cudaMemsetAsync(N->sync + 4 * ns, 0, sizeof(int) * 8, s));
   k_info_set<<<1, 1, 0, s>>>(d_info);
+  count_launches(1);
   CKL();
-  FactArgs A{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->snode, S->lptr, N->Lx, d_info};
-  for (int L = 0; L < S->nlevels; ++L) {
-    int b = S->h_level_ptr[L], e = S->h_level_ptr[L + 1];
-    if (e > b) k_factor_level<<<e - b, 256, 0, s>>>(A, b);
+  FactTaskArgs T;
+  T.F = FactArgs{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->snode, S->lptr, S->dptr,
+                 N->Lx, N->Dx, d_info};
+  T.tasks = S->ftasks;
+  T.ntasks = S->nftasks;
+  T.upd_need = S->upd_need;
+  T.C = sync_ctl(S, N, 0, 0);
+  T.ns = ns;
+  const int w = S->max_w;
+  size_t sm = sizeof(double) * std::max((size_t)w * w + (size_t)CIPM_RB * (w + 1),
+                                        2 * (size_t)CIPM_RB * (w + 1));
+  if (T.ntasks > 0) {
+    k_factor_dag<<<persistent_grid((const void *)k_factor_dag, 256, sm), 256, sm, s>>>(T);
+    count_launches(1);
+    CKL();
   }
+  k_info_fix<<<1, 1, 0, s>>>(d_info, N->sync + 4 * ns + 4);
+  count_launches(1);
   CKL();
-  k_info_fix<<<1, 1, 0, s>>>(d_info);
-  CKL();
+  N->factored = true;
   return IPM_OK;
 }
 
 // y (permuted, length n) <- L^{-T} L^{-1} y in place
 static int solve_permuted(ipm_sym_t S, ipm_num_t N, double *y, cudaStream_t s) {
-  SolveArgs A{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, N->Lx, y};
-  for (int L = 0; L < S->nlevels; ++L) {
-    int b = S->h_level_ptr[L], e = S->h_level_ptr[L + 1];
-    if (e > b) k_fwd_level<<<e - b, 128, 0, s>>>(A, b);
-  }
-  for (int L = S->nlevels - 1; L >= 0; --L) {
-    int b = S->h_level_ptr[L], e = S->h_level_ptr[L + 1];
-    if (e > b) k_bwd_level<<<e - b, 128, 0, s>>>(A, b);
-  }
+  const int ns = S->nsuper;
+  if (ns == 0) return IPM_OK;
+  CK(cudaMemsetAsync(N->sync + 2 * ns, 0, sizeof(int) * 2 * ns, s));
+  CK(cudaMemsetAsync(N->sync + 4 * ns + 1, 0, sizeof(int) * 2, s));
+  SolveTaskArgs T;
+  T.A = SolveArgs{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr, N->Lx, N->Dx, y};
+  T.snode = S->snode;
+  T.fwd_need = S->fwd_need;
+  T.ns = ns;
+  size_t sm = sizeof(double) * (size_t)S->max_w * S->max_w;
+  T.C = sync_ctl(S, N, 2, 1);
+  k_fwd_dag<<<persistent_grid((const void *)k_fwd_dag, 128, sm), 128, sm, s>>>(T);
+  count_launches(1);
+  CKL();
+  T.C = sync_ctl(S, N, 3, 2);
+  k_bwd_dag<<<persistent_grid((const void *)k_bwd_dag, 128, sm), 128, sm, s>>>(T);
+  count_launches(1);
   CKL();
   return IPM_OK;
 }
@@ -463,9 +800,11 @@ static int solve_permuted(ipm_sym_t S, ipm_num_t N, double *y, cudaStream_t s) {
 static int solve_full(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStream_t s) {
   double *y = N->vn[7];
   k_gather_perm<<<grid_for(S->n, 256), 256, 0, s>>>(S->perm, S->n, b, y);
+  count_launches(1);
   CKL();
   CKR(solve_permuted(S, N, y, s));
   k_scatter_perm<<<grid_for(S->n, 256), 256, 0, s>>>(S->perm, S->n, y, x);
+  count_launches(1);
   CKL();
   return IPM_OK;
 }
@@ -484,11 +823,13 @@ static int aug_condensed(ipm_sym_t S, ipm_num_t N, const double *Jv, const doubl
   double *t = N->vn[6];
   k_jt_apply<<<grid_for(n, 256), 256, 0, s>>>(n, S->JT_ptr, S->JT_ent, S->J_rowidx, Jv, d, rb, 0,
                                               m, ra, 1.0, t);
+  count_launches(1);
   CKL();
   CKR(solve_full(S, N, t, dx, s));
   if (m > 0) {
     k_recover_dz<<<grid_for(m, 256), 256, 0, s>>>(0, m, S->J_rowptr, S->J_colind, Jv, d, dx, rb,
                                                   dz);
+    count_launches(1);
     CKL();
   }
   return IPM_OK;
@@ -537,8 +878,10 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
     A.want_norm_a = it == 0;
     CK(cudaMemsetAsync(N->scal, 0, sizeof(double) * (it == 0 ? 4 : 3), s));
     k_aug_resid_x<<<grid_for(n, 256), 256, 0, s>>>(A);
+    count_launches(1);
     CKL();
     if (m > 0) k_aug_resid_z<<<grid_for(m, 256), 256, 0, s>>>(A);
+    if (m > 0) count_launches(1);
     CKL();
     CK(cudaMemcpyAsync(N->h_scal, N->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -553,14 +896,17 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
     eta_prev = eta;
     CKR(aug_condensed(S, N, J_val, d_row, A.outx, A.outz, cx, cz, s));
     k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, 1.0, cx, dx);
+    count_launches(1);
     CKL();
     if (m > 0) k_axpy<<<grid_for(m, 256), 256, 0, s>>>(m, 1.0, cz, dz);
+    if (m > 0) count_launches(1);
     CKL();
     ++steps;
   }
   if (d_eta) CK(cudaMemcpyAsync(d_eta, &eta, sizeof(double), cudaMemcpyHostToDevice, s));
   if (d_steps) CK(cudaMemcpyAsync(d_steps, &steps, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
+  if (int st = device_status(N)) return st;
   if (!std::isfinite(eta)) return IPM_ERR_NONFINITE;
   return IPM_OK;
 }
@@ -580,6 +926,7 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
   // rhs1 = a + J^T (d o b)  ( = r1 + gamma G^T r2 with r1 = a + H^T D_H b_H, r2 = b_G )
   k_jt_apply<<<grid_for(n, 256), 256, 0, s>>>(n, S->JT_ptr, S->JT_ent, S->J_rowidx, J_val, d_row,
                                               b, 0, m, a, 1.0, rhs1);
+  count_launches(1);
   CKL();
   CKR(solve_full(S, N, rhs1, w, s));
   int iters = 0;
@@ -588,6 +935,7 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
   if (m_e > 0) {
     // r = G w - b_G ; dy = 0 ; p = r
     k_j_apply<<<grid_for(m_e, 256), 256, 0, s>>>(0, m_e, S->J_rowptr, S->J_colind, J_val, w, b, r);
+    count_launches(1);
     CKL();
     CK(cudaMemsetAsync(dy, 0, sizeof(double) * m_e, s));
     CK(cudaMemcpyAsync(p, r, sizeof(double) * m_e, cudaMemcpyDeviceToDevice, s));
@@ -601,18 +949,23 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
       // Sp = G K^{-1} G^T p
       k_jt_apply<<<grid_for(n, 256), 256, 0, s>>>(n, S->JT_ptr, S->JT_ent, S->J_rowidx, J_val,
                                                   nullptr, p, 0, m_e, nullptr, 1.0, u);
+      count_launches(1);
       CKL();
       CKR(solve_full(S, N, u, u, s));
       k_j_apply<<<grid_for(m_e, 256), 256, 0, s>>>(0, m_e, S->J_rowptr, S->J_colind, J_val, u,
                                                    nullptr, Sp);
+      count_launches(1);
       CKL();
       CKR(dot(p, Sp, m_e, partial, sc + 1, s));
       k_cg_update_xr<<<grid_for(m_e, 256), 256, 0, s>>>(m_e, sc, p, Sp, dy, r);
+      count_launches(1);
       CKL();
       CKR(dot(r, r, m_e, partial, sc + 2, s));
       k_cg_update_p<<<grid_for(m_e, 256), 256, 0, s>>>(m_e, sc, r, p);
+      count_launches(1);
       CKL();
       k_copy_scalar<<<1, 1, 0, s>>>(sc + 2, sc + 0);
+      count_launches(1);
       CKL();
       CK(cudaMemcpyAsync(N->h_scal, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -626,6 +979,7 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
     // dx = K^{-1}(rhs1 - G^T dy)
     k_jt_apply<<<grid_for(n, 256), 256, 0, s>>>(n, S->JT_ptr, S->JT_ent, S->J_rowidx, J_val,
                                                 nullptr, dy, 0, m_e, rhs1, -1.0, u);
+    count_launches(1);
     CKL();
     CKR(solve_full(S, N, u, dx, s));
   } else {
@@ -634,10 +988,12 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
   if (m > m_e) {
     k_recover_dz<<<grid_for(m - m_e, 256), 256, 0, s>>>(m_e, m, S->J_rowptr, S->J_colind, J_val,
                                                         d_row, dx, b, dz);
+    count_launches(1);
     CKL();
   }
   CK(cudaStreamSynchronize(s));
   if (h_iters) *h_iters = iters;
   if (h_relres) *h_relres = relres;
+  if (int st = device_status(N)) return st;
   return rc;
 }

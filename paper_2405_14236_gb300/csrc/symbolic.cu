@@ -755,6 +755,12 @@ static void free_sym(ipm_sym_t S) {
   if (S->colptr) cudaFree(S->colptr);
   if (S->lptr) cudaFree(S->lptr);
   if (S->items) cudaFree(S->items);
+  if (S->panel_tasks) cudaFree(S->panel_tasks);
+  if (S->dptr) cudaFree(S->dptr);
+  if (S->ftasks) cudaFree(S->ftasks);
+  if (S->upd_need) cudaFree(S->upd_need);
+  if (S->fwd_need) cudaFree(S->fwd_need);
+  if (S->upd_tasks) cudaFree(S->upd_tasks);
   delete S;
 }
 
@@ -805,6 +811,7 @@ static int symbolic_impl(ipm_sym_t S, const int *J_rowptr, const int *J_colind,
   int nadj = 0;
   CK(cudaMemcpy(&nadj, adj_ptr + n, sizeof(int), cudaMemcpyDeviceToHost));
   CKR(T.alloc(&adj, nadj));
+  S->nnz_k = (int64_t)nadj / 2 + n;
   k_graph_compact<<<n, 128, 0, s>>>(n, cand_ptr, cand, adj_ptr, adj);
   CKL();
 
@@ -1027,12 +1034,102 @@ static int symbolic_impl(ipm_sym_t S, const int *J_rowptr, const int *J_colind,
     CK(cudaMemcpy(hld.data(), ld, sizeof(int) * ns, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(hsp.data(), S->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost));
     S->h_level_maxld.assign(S->nlevels, 0);
+    S->h_level_maxw.assign(S->nlevels, 0);
     for (int k = 0; k < ns; ++k) {
       int L = md - hsd[k];
       S->h_level_maxld[L] = std::max(S->h_level_maxld[L], hld[k]);
+      S->h_level_maxw[L] = std::max(S->h_level_maxw[L], hsp[k + 1] - hsp[k]);
       S->max_ld = std::max(S->max_ld, hld[k]);
       S->max_w = std::max(S->max_w, hsp[k + 1] - hsp[k]);
     }
+    // factorization task lists (launch shapes of the numeric phase)
+    std::vector<int> hlsn(ns);
+    if (ns) CK(cudaMemcpy(hlsn.data(), S->level_sn, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+    std::vector<int4> pt, ut;
+    S->h_panel_ptr.assign(S->nlevels + 1, 0);
+    S->h_upd_ptr.assign(S->nlevels + 1, 0);
+    for (int L = 0; L < S->nlevels; ++L) {
+      S->h_panel_ptr[L] = (int)pt.size();
+      S->h_upd_ptr[L] = (int)ut.size();
+      for (int q = S->h_level_ptr[L]; q < S->h_level_ptr[L + 1]; ++q) {
+        int sn = hlsn[q];
+        int w = hsp[sn + 1] - hsp[sn];
+        int B = hld[sn] - w;
+        int T = B > 0 ? (B + CIPM_RB - 1) / CIPM_RB : 1;
+        for (int rb = 0; rb < T; ++rb) pt.push_back(make_int4(sn, rb, 0, 0));
+        if (B > 0)
+          for (int ti = 0; ti < T; ++ti)
+            for (int tj = 0; tj <= ti; ++tj) ut.push_back(make_int4(sn, ti, tj, 0));
+      }
+    }
+    S->h_panel_ptr[S->nlevels] = (int)pt.size();
+    // one topological order for the sync-free factorization: per level, its panel tasks then
+    // its update tasks; dependency counts from the row structure (rows are sorted, so the
+    // target supernodes of a row range appear in increasing runs)
+    {
+      std::vector<int> hsrp(ns + 1), hsrow(nsrow), hsn(n);
+      CK(cudaMemcpy(hsrp.data(), S->srow_ptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(hsrow.data(), S->srow, sizeof(int) * nsrow, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(hsn.data(), S->snode, sizeof(int) * n, cudaMemcpyDeviceToHost));
+      std::vector<int4> ft;
+      std::vector<int> updn(ns, 0), fwdn(ns, 0);
+      for (int L = 0; L < S->nlevels; ++L) {
+        for (int q = S->h_level_ptr[L]; q < S->h_level_ptr[L + 1]; ++q) {
+          int sn = hlsn[q];
+          int w = hsp[sn + 1] - hsp[sn];
+          int B = hld[sn] - w;
+          int T = B > 0 ? (B + CIPM_RB - 1) / CIPM_RB : 1;
+          for (int rb = 0; rb < T; ++rb) ft.push_back(make_int4(sn, rb, 0, 0));
+          int last = -1;
+          for (int i = w; i < w + B; ++i) {
+            int t = hsn[hsrow[hsrp[sn] + i]];
+            if (t != last) fwdn[t]++;
+            last = t;
+          }
+        }
+        for (int q = S->h_level_ptr[L]; q < S->h_level_ptr[L + 1]; ++q) {
+          int sn = hlsn[q];
+          int w = hsp[sn + 1] - hsp[sn];
+          int B = hld[sn] - w;
+          if (B <= 0) continue;
+          int T = (B + CIPM_RB - 1) / CIPM_RB;
+          for (int ti = 0; ti < T; ++ti)
+            for (int tj = 0; tj <= ti; ++tj) {
+              ft.push_back(make_int4(sn, ti, tj, 1));
+              int j0 = w + tj * CIPM_RB, j1 = std::min(w + B, j0 + CIPM_RB);
+              int last = -1;
+              for (int j = j0; j < j1; ++j) {
+                int t = hsn[hsrow[hsrp[sn] + j]];
+                if (t != last) updn[t]++;
+                last = t;
+              }
+            }
+        }
+      }
+      S->nftasks = (int)ft.size();
+      CKR(dev_alloc(&S->ftasks, (int64_t)ft.size()));
+      CKR(dev_alloc(&S->upd_need, ns));
+      CKR(dev_alloc(&S->fwd_need, ns));
+      if (!ft.empty())
+        CK(cudaMemcpy(S->ftasks, ft.data(), sizeof(int4) * ft.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(S->upd_need, updn.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(S->fwd_need, fwdn.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    }
+    S->h_upd_ptr[S->nlevels] = (int)ut.size();
+    std::vector<int64_t> hdp(ns + 1, 0);
+    for (int k = 0; k < ns; ++k) {
+      int64_t w = hsp[k + 1] - hsp[k];
+      hdp[k + 1] = hdp[k] + w * w;
+    }
+    S->diag_len = hdp[ns];
+    CKR(dev_alloc(&S->dptr, ns + 1));
+    CK(cudaMemcpy(S->dptr, hdp.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
+    CKR(dev_alloc(&S->panel_tasks, (int64_t)pt.size()));
+    CKR(dev_alloc(&S->upd_tasks, (int64_t)ut.size()));
+    if (!pt.empty())
+      CK(cudaMemcpy(S->panel_tasks, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));
+    if (!ut.empty())
+      CK(cudaMemcpy(S->upd_tasks, ut.data(), sizeof(int4) * ut.size(), cudaMemcpyHostToDevice));
     std::vector<int> hcc(n);
     CK(cudaMemcpy(hcc.data(), S->cc, sizeof(int) * n, cudaMemcpyDeviceToHost));
     double fl = 0;
@@ -1111,9 +1208,10 @@ extern "C" int ipm_symbolic(int n, int m, const int *J_rowptr, const int *J_coli
   return IPM_OK;
 }
 
-extern "C" int ipm_symbolic_info(ipm_sym_t S, int *nsuper, int64_t *nnz_offdiag,
+extern "C" int ipm_symbolic_info(ipm_sym_t S, int64_t *nnz_k, int *nsuper, int64_t *nnz_offdiag,
                                  int64_t *panel_len, int *nlevels, double *flops) {
   if (!S) return IPM_ERR_BAD_ARG;
+  if (nnz_k) *nnz_k = S->nnz_k;
   if (nsuper) *nsuper = S->nsuper;
   if (nnz_offdiag) *nnz_offdiag = S->nnz_offdiag;
   if (panel_len) *panel_len = S->panel_len;

@@ -228,3 +228,29 @@ def test_factor_reports_first_failing_pivot():
     F = Cholesky(K.condensed_matrix(c["Wf"], sigma, c["J"], c["d"], 0.0), c["solver"].sym)
     assert not F.ok
     assert int(info.item()) == F.fail
+
+
+def test_wait_timeout_reports_status_without_fault():
+    """A dependency that nothing satisfies ends in IPM_ERR_TIMEOUT, not a hang or a fault;
+    a fresh analysis of the same pattern factors normally afterwards."""
+    c = kkt_case("ring30")
+    S = gpu_sym(c["J"], c["Wl"])
+    N = cp.Numeric(S)
+    run_condense(c, S, N)
+    cp.ipm_set_spin_limit(20000)
+    try:
+        cp.ipm_debug_add_dependency(S, S.nsuper - 1, 1)
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        cp.ipm_factor(S, N, info)
+        torch.cuda.synchronize()
+        assert int(info.item()) == -2
+        assert cp.ipm_num_status(N) == cp.IPM_ERR_TIMEOUT
+    finally:
+        cp.ipm_set_spin_limit(1 << 23)
+    S2 = gpu_sym(c["J"], c["Wl"])
+    N2 = cp.Numeric(S2)
+    run_condense(c, S2, N2)
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cp.ipm_factor(S2, N2, info)
+    torch.cuda.synchronize()
+    assert int(info.item()) == -1 and cp.ipm_num_status(N2) == 0
