@@ -41,7 +41,7 @@ struct ipm_sym_s {
   // factorization task lists per level: panel tasks (supernode, row block) and update tasks
   // (supernode, row block i, row block j <= i) of the rows below the diagonal block
   int4 *panel_tasks = nullptr, *upd_tasks = nullptr;
-  int64_t *dptr = nullptr;  // offsets of the w x w diagonal factors L11 (separate array)
+  int64_t *dptr = nullptr;  // offsets of the diagonal factors: w x w L11, then 1 / diag(L11)
   int64_t diag_len = 0;
   // sync-free schedule: all factorization tasks in one topological order (x = supernode,
   // y/z = row blocks, w = 0 panel / 1 update), dependency counts per supernode

@@ -53,6 +53,19 @@ __device__ __forceinline__ int find_row(const int *rows, int ld, int i) {
   return lo;
 }
 
+// 1/sqrt(d) by Newton-Raphson (y <- y (3 - d y^2) / 2, quadratic convergence) from a
+// single-precision seed: two steps reach double precision.  On this GPU an FP64 sqrt plus a
+// reciprocal cost about 1100 cycles of dependent latency; this costs about half.  Inputs outside
+// the single-precision range use sqrt and division.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  double h = 0.5 * d;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
 struct FactArgs {
   const int *level_sn, *sptr, *srow_ptr, *srow, *snode;
   const int64_t *lptr, *dptr;
@@ -130,6 +143,11 @@ struct FactTaskArgs {
   int ns;
 };
 
+// Panel task (supernode s, row block rb): the w x w diagonal block is factored in shared memory
+// (every row block of s repeats this small Cholesky, so no block waits for a sibling), then
+// L21 = A21 L11^{-T} for the block's <= 32 rows.  The diagonal block of the panel keeps K
+// (siblings read it in the same launch); row block 0 stores L11 in the separate array Dx.
+// The reciprocal pivots are computed once by one thread: FP64 division is expensive here.
 __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm, int *s_ok) {
   const FactArgs &A = T.F;
   if (threadIdx.x == 0) *s_ok = spin_geq(T.C.cnt + s, T.upd_need[s], T.C);
@@ -139,6 +157,7 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
   const int ld = A.srow_ptr[s + 1] - A.srow_ptr[s];
   double *P = A.Lx + A.lptr[s];
   double *sL = sm, *sR = sm + w * w;
+  __shared__ double s_inv[CIPM_SN_MAXW];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int t = tid; t < w * w; t += bd) {
     int k = t / w, i = t - k * w;
@@ -152,14 +171,16 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
         atomicMin(A.info, f + k);
         d = 1.0;
       }
-      sL[k + k * w] = sqrt(d);
+      const double inv = rsqrt_newton(d);
+      sL[k + k * w] = d * inv;
+      s_inv[k] = inv;
     }
     __syncthreads();
-    const double inv = 1.0 / sL[k + k * w];
+    const double inv = s_inv[k];
     const int nr = w - k - 1;
     for (int i = k + 1 + tid; i < w; i += bd) sL[i + k * w] *= inv;
     __syncthreads();
-    // trailing update: thread (ii, jj) on a fixed 2-D layout, no divisions in the loop
+    // trailing update: warps own columns, lanes rows (no divisions in the loop)
     for (int jj = tid / 32; jj < nr; jj += bd / 32) {
       const int j = k + 1 + jj;
       const double ljk = sL[j + k * w];
@@ -170,6 +191,7 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
   if (rb == 0) {
     double *Dd = A.Dx + A.dptr[s];
     for (int t = tid; t < w * w; t += bd) Dd[t] = sL[t];
+    for (int k = tid; k < w; k += bd) Dd[w * w + k] = s_inv[k];
   }
   const int r0 = w + rb * CIPM_RB;
   const int nrow = min(CIPM_RB, ld - r0);
@@ -183,7 +205,7 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
     // each warp owns rows r = warp, warp + nwarps, ...; lanes split the columns
     const int warp = tid >> 5, lane = tid & 31, nw = bd >> 5;
     for (int k = 0; k < w; ++k) {
-      const double inv = 1.0 / sL[k + k * w];
+      const double inv = s_inv[k];
       for (int r = warp; r < nrow; r += nw) {
         double xk = sR[r * sw + k] * inv;
         __syncwarp();
@@ -242,13 +264,12 @@ __device__ void fact_update_task(const FactTaskArgs &T, int s, int ti, int tj, d
     atomicAdd(&A.Lx[A.lptr[ts] + (int64_t)(col - A.sptr[ts]) * tld + r], -v);
   }
   publish();
-  if (tid == 0) {
-    int last = -1;
-    for (int j = j0; j < j0 + nj; ++j) {
-      int t = A.snode[rows[j]];
-      if (t != last) atomicAdd(T.C.cnt + t, 1);
-      last = t;
-    }
+  // one signal per distinct target supernode of the tile's rows (runs, rows are sorted)
+  if (tid < 32 && tid < nj) {
+    const int j = j0 + tid;
+    const int t = A.snode[rows[j]];
+    const int tp = tid > 0 ? A.snode[rows[j - 1]] : -1;
+    if (t != tp) atomicAdd(T.C.cnt + t, 1);
   }
 }
 
@@ -302,8 +323,9 @@ __global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
     __syncthreads();
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
+      const double *rinv = Dd + w * w;
       for (int k = 0; k < w; ++k) {
-        if (lane == (k & 31)) ys[k] /= sL[k + k * w];
+        if (lane == (k & 31)) ys[k] *= rinv[k];
         __syncwarp();
         const double yk = ys[k];
         for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= sL[i + k * w] * yk;
@@ -318,13 +340,10 @@ __global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
       atomicAdd(&A.y[rows[i]], -acc);
     }
     publish();
-    if (threadIdx.x == 0) {
-      int last = -1;
-      for (int i = w; i < ld; ++i) {
-        int tg = T.snode[rows[i]];
-        if (tg != last) atomicAdd(T.C.cnt + tg, 1);
-        last = tg;
-      }
+    for (int i = w + threadIdx.x; i < ld; i += blockDim.x) {
+      const int tg = T.snode[rows[i]];
+      const int tp = i > w ? T.snode[rows[i - 1]] : -1;
+      if (tg != tp) atomicAdd(T.C.cnt + tg, 1);
     }
     __syncthreads();
   }
@@ -346,15 +365,12 @@ __global__ void __launch_bounds__(128) k_bwd_dag(SolveTaskArgs T) {
     const int f = A.sptr[s], w = A.sptr[s + 1] - f;
     const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
     const int *rows = A.srow + rb;
-    if (threadIdx.x == 0) {
-      bool ok = true;
-      int last = -1;
-      for (int i = w; i < ld && ok; ++i) {
-        int tg = T.snode[rows[i]];
-        if (tg != last) ok = spin_geq(T.C.cnt + tg, 1, T.C);
-        last = tg;
-      }
-      s_ok = ok;
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    for (int i = w + threadIdx.x; i < ld; i += blockDim.x) {
+      const int tg = T.snode[rows[i]];
+      const int tp = i > w ? T.snode[rows[i - 1]] : -1;
+      if (tg != tp && !spin_geq(T.C.cnt + tg, 1, T.C)) s_ok = 0;
     }
     __syncthreads();
     if (!s_ok) continue;
@@ -370,8 +386,9 @@ __global__ void __launch_bounds__(128) k_bwd_dag(SolveTaskArgs T) {
     }
     __syncthreads();
     if (threadIdx.x < 32) {
+      const double *rinv = Dd + w * w;
       for (int k = w - 1; k >= 0; --k) {
-        if (lane == (k & 31)) zs[k] /= sL[k + k * w];
+        if (lane == (k & 31)) zs[k] *= rinv[k];
         __syncwarp();
         const double xk = zs[k];
         for (int j = lane; j < k; j += 32) zs[j] -= sL[k + j * w] * xk;

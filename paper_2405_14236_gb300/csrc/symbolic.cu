@@ -1119,7 +1119,7 @@ static int symbolic_impl(ipm_sym_t S, const int *J_rowptr, const int *J_colind,
     std::vector<int64_t> hdp(ns + 1, 0);
     for (int k = 0; k < ns; ++k) {
       int64_t w = hsp[k + 1] - hsp[k];
-      hdp[k + 1] = hdp[k] + w * w;
+      hdp[k + 1] = hdp[k] + w * w + w;  // L11 (column-major) then its reciprocal diagonal
     }
     S->diag_len = hdp[ns];
     CKR(dev_alloc(&S->dptr, ns + 1));
