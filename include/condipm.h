@@ -151,6 +151,23 @@ int ipm_debug_add_dependency(ipm_sym_t sym, int supernode, int extra);
 int ipm_solve(ipm_sym_t sym, ipm_num_t num, const double *b, double *x, int nrhs,
               cudaStream_t stream);
 
+/* ipm_solve_noalloc — the solve of ipm_solve (x = K^{-1} b, same factor, same kernels) for
+ * callers that cannot allocate device memory when they call: a runtime that hands out all
+ * device memory itself at start-up, a process with a fixed memory budget, a latency-critical
+ * loop that must not enter the allocator.  The paper has no counterpart; this is a library
+ * convenience.  The call allocates nothing: its scratch (the permuted work vector and the
+ * dependency counters) is a static device array of the library, sized for n and the number of
+ * supernodes up to 262144 (2^18), which every GPU that loads the library holds until exit.
+ *   b [n], x [n] device (may alias); d_status: DEVICE int or NULL, receives IPM_OK or
+ *   IPM_ERR_TIMEOUT (a bounded wait gave up; x is then invalid).
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (the counters are cleared by each call); calls that overlap on the
+ * GPU (other streams, other threads) race on it — serialize them.
+ * IPM_ERR_BAD_ARG (with a message) when n or the supernode count exceeds 262144. */
+int ipm_solve_noalloc(ipm_sym_t sym, ipm_num_t num, const double *b, double *x, int *d_status,
+                      cudaStream_t stream);
+
 /* ipm_aug_solve — LiftedKKT solve (Section 3.2, Eq. (13)) of the augmented system with the
  * slack block eliminated (all rows inequality rows):
  *     [ W + Sigma_x + delta_w I   J^T      ] [dx]   [a]

@@ -40,6 +40,7 @@ _SIGS = {
     "ipm_condense": (I, [P, P, P, P, P, P, D, P]),
     "ipm_factor": (I, [P, P, P, P]),
     "ipm_solve": (I, [P, P, P, P, I, P]),
+    "ipm_solve_noalloc": (I, [P, P, P, P, P, P]),
     "ipm_aug_solve": (I, [P, P, P, P, P, P, D, P, P, P, P, I, D, P, P, P]),
     "hykkt_cg": (I, [P, P, I, P, P, D, P, P, D, I, P, P, P, P, P, P]),
     "ipm_opf_create": (I, [I, I, I] + [P] * 13 + [P, P]),
@@ -194,6 +195,12 @@ def ipm_factor(sym, num, d_info, stream=None):
 
 def ipm_solve(sym, num, b, x, stream=None):
     return _check(lib().ipm_solve(sym.h, num.h, _ptr(b), _ptr(x), 1, _stream(stream)), "ipm_solve")
+
+
+def ipm_solve_noalloc(sym, num, b, x, d_status=None, stream=None):
+    """Solve with the library's static scratch instead of the handle's workspace (no allocation)."""
+    return _check(lib().ipm_solve_noalloc(sym.h, num.h, _ptr(b), _ptr(x), _ptr(d_status),
+                                          _stream(stream)), "ipm_solve_noalloc")
 
 
 def ipm_aug_solve(sym, num, W_val, sigma_x, J_val, d_row, delta_w, a, b, dx, dz, d_eta, d_steps,

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -1013,4 +1014,81 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
   if (h_relres) *h_relres = relres;
   if (int st = device_status(N)) return st;
   return rc;
+}
+
+// ---------------------------------------------------------------- allocation-free solve
+// ipm_solve_noalloc: the same triangular solves as ipm_solve, for callers that may not allocate
+// device memory at call time (a runtime that owns all device memory up front, a process with a
+// fixed memory budget, code that must not call into the allocator from a latency-critical loop).
+// Its scratch (the permuted work vector and the dependency counters of the two sync-free
+// kernels) is this file-scope array, which every GPU that loads the library keeps until exit.
+// All calls share it: calls that overlap on the GPU race on it.
+#define CIPM_NOALLOC_MAX_N (1 << 18)        // largest n (and number of supernodes) accepted
+#define CIPM_NOALLOC_INTS (2 * CIPM_NOALLOC_MAX_N + 16)
+static __device__ __align__(256) double g_noalloc_scratch[CIPM_NOALLOC_MAX_N + CIPM_NOALLOC_INTS / 2 + 8];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64];  // device address of g_noalloc_scratch, per device ordinal
+
+__global__ void k_copy_status(const int *src, int *dst) { *dst = *src; }
+
+extern "C" int ipm_solve_noalloc(ipm_sym_t S, ipm_num_t N, const double *b, double *x,
+                                 int *d_status, cudaStream_t s) {
+  if (!S || !N || N->sym != S || !b || !x) {
+    set_error_msg("ipm_solve_noalloc: bad argument");
+    return IPM_ERR_BAD_ARG;
+  }
+  if (S->n > CIPM_NOALLOC_MAX_N || S->nsuper > CIPM_NOALLOC_MAX_N) {
+    set_error_msg("ipm_solve_noalloc: n = " + std::to_string(S->n) + " exceeds the static scratch limit " +
+                  std::to_string(CIPM_NOALLOC_MAX_N));
+    return IPM_ERR_BAD_ARG;
+  }
+  // set-up once per device (with that device current): the host cannot use the symbol's name as
+  // a device address, so look the address up and pass it to the kernels
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return IPM_ERR_BAD_ARG;
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  const int n = S->n, ns = S->nsuper;
+  double *y = (double *)base;
+  int *cnt = (int *)(y + CIPM_NOALLOC_MAX_N);  // [0,ns) forward, [ns,2ns) backward, then tail
+  int *tail = cnt + 2 * CIPM_NOALLOC_MAX_N;     // tickets (2), abort, status
+  // counters, tickets, abort flag and status must start at zero on every call
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)ns, s));
+  CK(cudaMemsetAsync(tail, 0, sizeof(int) * 8, s));
+  k_gather_perm<<<grid_for(n, 256), 256, 0, s>>>(S->perm, n, b, y);
+  count_launches(1);
+  CKL();
+  SolveTaskArgs T;
+  T.A = SolveArgs{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr, N->Lx, N->Dx, y};
+  T.snode = S->snode;
+  T.fwd_need = S->fwd_need;
+  T.ns = ns;
+  size_t sm = sizeof(double) * (size_t)S->max_w * S->max_w;
+  T.C = SyncCtl{cnt, tail + 0, tail + 2, tail + 3};
+  k_fwd_dag<<<persistent_grid((const void *)k_fwd_dag, 128, sm), 128, sm, s>>>(T);
+  count_launches(1);
+  CKL();
+  T.C = SyncCtl{cnt + ns, tail + 1, tail + 2, tail + 3};
+  k_bwd_dag<<<persistent_grid((const void *)k_bwd_dag, 128, sm), 128, sm, s>>>(T);
+  count_launches(1);
+  CKL();
+  k_scatter_perm<<<grid_for(n, 256), 256, 0, s>>>(S->perm, n, y, x);
+  count_launches(1);
+  CKL();
+  if (d_status) {
+    k_copy_status<<<1, 1, 0, s>>>(tail + 3, d_status);
+    count_launches(1);
+    CKL();
+  }
+  return IPM_OK;
 }
