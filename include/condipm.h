@@ -225,12 +225,53 @@ int ipm_opf_info(ipm_opf_t opf, int *n, int *m_e, int *m_i, int *nnzJ, int *nnzW
  * W_colind [nnzW]); columns increase within each row.  Synchronizes. */
 int ipm_opf_patterns(ipm_opf_t opf, int *J_rowptr, int *J_colind, int *W_rowptr, int *W_colind);
 /* Evaluates at x (device): f (device scalar, may be NULL), grad [n] (may be NULL),
- * g [m_e], h [m_i], J_val [nnzJ] and, when W_val is not NULL, W_val [nnzW] =
+ * g [m_e], h [m_i], J_val [nnzJ] (may be NULL) and, when W_val is not NULL, W_val [nnzW] =
  * sigma_f grad^2 f + sum y_i grad^2 g_i + sum z_j grad^2 h_j (y [m_e], z [m_i]). */
 int ipm_opf_eval(ipm_opf_t opf, const double *x, const double *y, const double *z,
                  double sigma_f, double *f, double *grad, double *g, double *h, double *J_val,
                  double *W_val, cudaStream_t stream);
 void ipm_opf_destroy(ipm_opf_t opf);
+
+/* ---------------------------------------------------------------------------------------
+ * Interior-point iterations on the GPU (Section 2: barrier problem (5), Newton step (K_3) solved
+ * in condensed form by LiftedKKT or HyKKT; Ipopt's filter line search, barrier update, inertia
+ * correction and multiplier safeguards as cited in Section 2.2).
+ */
+typedef struct {
+  int kkt;          /* 0 = LiftedKKT (Section 3.2), 1 = HyKKT (Section 3.1) */
+  double tol;       /* scaled KKT tolerance (e.g. 1e-6) */
+  double gamma;     /* HyKKT regularization gamma */
+  double tau;       /* LiftedKKT relaxation; <= 0 means tau = tol */
+  double mu0;       /* initial barrier parameter; <= 0 means 0.1 */
+  double cg_rtol;   /* HyKKT CG relative residual; <= 0 means 1e-10 */
+  int max_refine;   /* LiftedKKT refinement steps; < 0 means 10 */
+  int cg_maxit;     /* HyKKT CG iteration limit; <= 0 means m_e */
+} ipm_options;
+
+typedef struct {
+  int k;            /* iteration index */
+  int status;       /* 0 running, 1 converged, else an IPM_ERR_* code */
+  double mu, kkt_err, alpha, delta_w, obj, eta, theta;
+  int n_factor, cg_iters, refine_steps, ls_steps;
+} ipm_iter_info;
+
+typedef struct ipm_state_s *ipm_state_t;
+
+/* Creates the iterate for an OPF problem: flat start pushed inside the bounds, Ipopt gradient
+ * scaling of the objective and of each constraint row at the start, s = max(-h, 0.01), y = 0,
+ * z = v = 1, bound multipliers 1; runs ipm_symbolic on the model pattern and allocates every
+ * workspace.  The opf handle must outlive the state.  Synchronizes. */
+int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStream_t stream,
+                     ipm_state_t *out);
+/* One IPM iteration (or the convergence test that ends the solve): evaluate, test E_0 <= tol,
+ * update mu, inertia-corrected condensed KKT solve, fraction to the boundary, filter line search,
+ * update.  host_info (HOST) receives the iteration record; after convergence or a failure
+ * further calls return the final status without work.  Synchronizes.  Returns a negative code
+ * only on usage/CUDA errors (numerical failures are reported in host_info->status). */
+int ipm_step(ipm_state_t state, ipm_iter_info *host_info);
+/* Copies x [n] to a HOST buffer (NULL skipped) and the unscaled objective f(x) to *obj (HOST). */
+int ipm_state_export(ipm_state_t state, double *x, double *obj);
+void ipm_state_destroy(ipm_state_t state);
 
 #ifdef __cplusplus
 }

@@ -48,7 +48,28 @@ _SIGS = {
     "ipm_opf_patterns": (I, [P, P, P, P, P]),
     "ipm_opf_eval": (I, [P, P, P, P, D, P, P, P, P, P, P, P]),
     "ipm_opf_destroy": (None, [P]),
+    "ipm_state_create": (I, [P, P, P, P]),
+    "ipm_step": (I, [P, P]),
+    "ipm_state_export": (I, [P, P, P]),
+    "ipm_state_destroy": (None, [P]),
 }
+
+
+class IpmOptions(ctypes.Structure):
+    _fields_ = [("kkt", ctypes.c_int), ("tol", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("tau", ctypes.c_double), ("mu0", ctypes.c_double), ("cg_rtol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("cg_maxit", ctypes.c_int)]
+
+
+class IpmIterInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("status", ctypes.c_int), ("mu", ctypes.c_double),
+                ("kkt_err", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("delta_w", ctypes.c_double), ("obj", ctypes.c_double), ("eta", ctypes.c_double),
+                ("theta", ctypes.c_double), ("n_factor", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("ls_steps", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class CondipmError(RuntimeError):
@@ -261,3 +282,52 @@ class Opf:
         if getattr(self, "h", None) and _lib is not None:
             _lib.ipm_opf_destroy(self.h)
             self.h = None
+
+
+class IpmState:
+    """GPU interior-point iterate for an ``Opf`` problem (ipm_state_create / ipm_step)."""
+
+    def __init__(self, opf, kkt="lifted", tol=1e-6, gamma=1e6, tau=0.0, mu0=0.1, cg_rtol=1e-10,
+                 max_refine=10, cg_maxit=0, stream=None):
+        self.opf = opf
+        o = IpmOptions(0 if kkt == "lifted" else 1, tol, gamma, tau, mu0, cg_rtol, max_refine,
+                       cg_maxit)
+        h = ctypes.c_void_p()
+        _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream), ctypes.byref(h)),
+               "ipm_state_create")
+        self.h = h
+
+    def step(self):
+        info = IpmIterInfo()
+        _check(lib().ipm_step(self.h, ctypes.byref(info)), "ipm_step")
+        return info
+
+    def x(self):
+        out = np.zeros(self.opf.n)
+        _check(lib().ipm_state_export(self.h, out.ctypes.data_as(ctypes.c_void_p), None), "export")
+        return out
+
+    def objective(self):
+        v = D()
+        _check(lib().ipm_state_export(self.h, None, ctypes.byref(v)), "export")
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipm_state_destroy(self.h)
+            self.h = None
+
+
+def ipm_solve_opf(opf, max_iter=3000, **opts):
+    """Runs ipm_step until convergence, failure or max_iter; returns (status, iters, obj, history)."""
+    st = IpmState(opf, **opts)
+    hist = []
+    status = 0
+    for _ in range(max_iter + 1):
+        info = st.step()
+        hist.append(info.as_dict())
+        status = info.status
+        if status != 0:
+            break
+    iters = hist[-1]["k"]
+    return dict(status=status, iters=iters, obj=st.objective(), x=st.x(), history=hist, state=st)

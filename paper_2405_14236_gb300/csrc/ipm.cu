@@ -1,0 +1,881 @@
+// One primal-dual interior-point iteration on the GPU (ipm_step).
+//
+// Problem (2) of the paper with slacks h(x) + s = 0, s >= 0 and Ipopt-style variable bounds
+// (bound multipliers zl, zu eliminated into Sigma_x on the diagonal of K).  The Newton step
+// (K_2) is solved in condensed form, either
+//   LiftedKKT (Section 3.2): equalities relaxed to -tau <= g <= tau, i.e. rows g - tau <= 0 and
+//     -g - tau <= 0 in front of h <= 0; each pair of relaxed rows shares the pattern of its G
+//     row, so K_tau = W + Sigma_x + delta_w I + G^T (D1 + D2) G + H^T D_H H is condensed from
+//     J = [G; H] and the step is refined on the augmented system (ipm_aug_solve), or
+//   HyKKT (Section 3.1): K_gamma = K + gamma G^T G and CG on the Schur complement (hykkt_cg).
+// The line search, barrier update, inertia correction and safeguards are those of Ipopt
+// (Waechter & Biegler 2006, cited in Section 2.2), with its published constants.  Decisions
+// that need a few scalars (convergence, inertia, filter acceptance) read them back to the host.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+#include "opf.cuh"
+
+namespace cipm {
+
+static constexpr double KAPPA1 = 1e-2, KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5;
+static constexpr double TAU_MIN = 0.99, S_MAX = 100.0, GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-8;
+static constexpr double S_THETA = 1.1, S_PHI = 2.3, DELTA_SW = 1.0, ETA_PHI = 1e-8;
+static constexpr double GAMMA_ALPHA = 0.05, KAPPA_SIGMA = 1e10;
+
+// ------------------------------------------------------------------ reductions into R[]
+enum {
+  R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_MAX_SV, R_MAX_XL, R_MAX_XU,  // max |.|
+  R_SUM_Y, R_SUM_Z, R_SUM_V, R_SUM_ZL, R_SUM_ZU,                        // sums |.|
+  R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU,                          // theta / phi parts
+  R_GPHI_X, R_GPHI_S,                                                    // d phi
+  R_AMAX, R_AZ,                                                          // step bounds (min)
+  R_PD, R_QD, R_MAXGRAD,                                                 // set-up
+  R_COUNT
+};
+
+__device__ __forceinline__ void amax_nonneg(double *a, double v) {
+  atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void amin_nonneg(double *a, double v) {
+  atomicMin((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ double wmax(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double wmin(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// warp-level reduce then one atomic per warp (every lane of the warp must call)
+__device__ __forceinline__ void red_max(double *R, int k, double v) {
+  v = wmax(v);
+  if ((threadIdx.x & 31) == 0) amax_nonneg(R + k, v);
+}
+__device__ __forceinline__ void red_min(double *R, int k, double v) {
+  v = wmin(v);
+  if ((threadIdx.x & 31) == 0) amin_nonneg(R + k, v);
+}
+__device__ __forceinline__ void red_sum(double *R, int k, double v) {
+  v = wsum(v);
+  if ((threadIdx.x & 31) == 0) atomicAdd(R + k, v);
+}
+
+struct Dims {
+  int n, me0, mi0;  // model sizes: variables, equality rows g, inequality rows h
+  int me, mi;       // IPM sizes: equality rows (HyKKT: me0, Lifted: 0), slack rows
+  int lifted;
+};
+
+// ------------------------------------------------------------------ set-up kernels
+__global__ void k_setup_sums(int nb, const double *pd, const double *qd, double *R) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = i < nb ? pd[i] : 0.0, b = i < nb ? qd[i] : 0.0;
+  red_sum(R, R_PD, a);
+  red_sum(R, R_QD, b);
+}
+
+// flat start (|V| = 1, theta = 0, generators share the load equally), pushed inside the bounds
+__global__ void k_x0(int nb, int ng, const double *R, const double *xl, const double *xu,
+                     double *x) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 2 * nb + 2 * ng;
+  if (j >= n) return;
+  double v;
+  if (j < nb) v = 1.0;
+  else if (j < 2 * nb) v = 0.0;
+  else if (j < 2 * nb + ng) v = fmin(fmax(R[R_PD] / ng, xl[j]), xu[j]);
+  else v = fmin(fmax(R[R_QD] / ng, xl[j]), xu[j]);
+  const bool hl = isfinite(xl[j]), hu = isfinite(xu[j]);
+  double pl = hl ? KAPPA1 * fmax(1.0, fabs(xl[j])) : 0.0;
+  double pu = hu ? KAPPA1 * fmax(1.0, fabs(xu[j])) : 0.0;
+  if (hl && hu) {
+    pl = fmin(pl, KAPPA1 * (xu[j] - xl[j]));
+    pu = fmin(pu, KAPPA1 * (xu[j] - xl[j]));
+  }
+  if (hl) v = fmax(v, xl[j] + pl);
+  if (hu) v = fmin(v, xu[j] - pu);
+  x[j] = v;
+}
+
+// row scale d_r = min(1, 100 / max_j |J_rj|) (Ipopt gradient-based scaling)
+__global__ void k_row_scale(int m, const int *rowptr, const double *Jv, double *d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  double mx = 0.0;
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) mx = fmax(mx, fabs(Jv[p]));
+  d[r] = mx > 0.0 ? fmin(1.0, 100.0 / mx) : 1.0;
+}
+
+__global__ void k_max_abs(int n, const double *v, double *R, int k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  red_max(R, k, i < n ? fabs(v[i]) : 0.0);
+}
+
+// scale the model outputs: g~ = d_e g, h~ = d_i h, J~ rows by d
+__global__ void k_scale_rows(int m, const int *rowptr, const double *d, double *Jv) {
+  int r = blockIdx.x * blockDim.y + threadIdx.y;
+  if (r >= m) return;
+  const double dr = d[r];
+  for (int p = rowptr[r] + threadIdx.x; p < rowptr[r + 1]; p += blockDim.x) Jv[p] *= dr;
+}
+__global__ void k_scale_vec(int n, const double *d, double *v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= d[i];
+}
+
+// IPM constraint values from the scaled model: HyKKT  g' = g~, h' = h~;
+// Lifted  h' = [g~ - tau ; -g~ - tau ; h~]
+__global__ void k_ipm_rows(Dims D, double tau, const double *gs, const double *hs, double *geq,
+                           double *hin) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (D.lifted) {
+    if (k < D.me0) {
+      hin[k] = gs[k] - tau;
+      hin[D.me0 + k] = -gs[k] - tau;
+    }
+    if (k < D.mi0) hin[2 * D.me0 + k] = hs[k];
+  } else {
+    if (k < D.me0) geq[k] = gs[k];
+    if (k < D.mi0) hin[k] = hs[k];
+  }
+}
+
+// multipliers of the model rows: lambda = [lambda_g ; lambda_h] (unscaled-row weights)
+__global__ void k_lambda(Dims D, const double *y, const double *z, double *lam) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < D.me0) lam[k] = D.lifted ? z[k] - z[D.me0 + k] : y[k];
+  if (k < D.mi0) lam[D.me0 + k] = D.lifted ? z[2 * D.me0 + k] : z[k];
+}
+
+__global__ void k_mul(int n, const double *a, const double *b, double *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] * b[i];
+}
+
+// out_j = sum_p J~_pj u_row(p) (J^T u)
+__global__ void k_jtu(int n, const int *JT_ptr, const int *JT_ent, const int *rowidx,
+                      const double *Jv, const double *u, double *out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int t = JT_ptr[j]; t < JT_ptr[j + 1]; ++t) {
+    int p = JT_ent[t];
+    acc += Jv[p] * u[rowidx[p]];
+  }
+  out[j] = acc;
+}
+// out_r = (J~ v)_r
+__global__ void k_jv(int m, const int *rowptr, const int *colind, const double *Jv,
+                     const double *v, double *out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  double acc = 0.0;
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += Jv[p] * v[colind[p]];
+  out[r] = acc;
+}
+
+struct It {  // device pointers of the iterate and work vectors
+  double *x, *s, *y, *z, *v, *zl, *zu;
+  double *xl, *xu;
+  double *grad, *jtl;  // grad f, J~^T lambda
+  double *geq, *hin;   // IPM rows
+};
+
+// optimality error parts (Ipopt E_mu): maxima and 1-norm sums
+__global__ void k_errors(Dims D, It P, double sig, double mu, double *R) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double gl = 0, xl_c = 0, xu_c = 0, szl = 0, szu = 0;
+  if (i < D.n) {
+    double x = P.x[i];
+    gl = fabs(sig * P.grad[i] + P.jtl[i] - P.zl[i] + P.zu[i]);
+    if (isfinite(P.xl[i])) xl_c = fabs((x - P.xl[i]) * P.zl[i] - mu);
+    if (isfinite(P.xu[i])) xu_c = fabs((P.xu[i] - x) * P.zu[i] - mu);
+    szl = fabs(P.zl[i]);
+    szu = fabs(P.zu[i]);
+  }
+  double zv = 0, hs = 0, sv = 0, sz = 0, svv = 0;
+  if (i < D.mi) {
+    zv = fabs(P.z[i] - P.v[i]);
+    hs = fabs(P.hin[i] + P.s[i]);
+    sv = fabs(P.s[i] * P.v[i] - mu);
+    sz = fabs(P.z[i]);
+    svv = fabs(P.v[i]);
+  }
+  double ge = 0, sy = 0;
+  if (i < D.me) {
+    ge = fabs(P.geq[i]);
+    sy = fabs(P.y[i]);
+  }
+  red_max(R, R_MAX_GL, gl);
+  red_max(R, R_MAX_ZV, zv);
+  red_max(R, R_MAX_G, ge);
+  red_max(R, R_MAX_HS, hs);
+  red_max(R, R_MAX_SV, sv);
+  red_max(R, R_MAX_XL, xl_c);
+  red_max(R, R_MAX_XU, xu_c);
+  red_sum(R, R_SUM_Y, sy);
+  red_sum(R, R_SUM_Z, sz);
+  red_sum(R, R_SUM_V, svv);
+  red_sum(R, R_SUM_ZL, szl);
+  red_sum(R, R_SUM_ZU, szu);
+}
+
+// theta and phi parts at (x, s) with constraint rows geq/hin
+__global__ void k_merit(Dims D, const double *x, const double *s, const double *xl,
+                        const double *xu, const double *geq, const double *hin, double *R) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double tg = 0, th = 0, ls = 0, lxl = 0, lxu = 0;
+  if (i < D.me) tg = fabs(geq[i]);
+  if (i < D.mi) {
+    th = fabs(hin[i] + s[i]);
+    ls = log(s[i]);
+  }
+  if (i < D.n) {
+    if (isfinite(xl[i])) lxl = log(x[i] - xl[i]);
+    if (isfinite(xu[i])) lxu = log(xu[i] - x[i]);
+  }
+  red_sum(R, R_TH_G, tg);
+  red_sum(R, R_TH_H, th);
+  red_sum(R, R_LOG_S, ls);
+  red_sum(R, R_LOG_XL, lxl);
+  red_sum(R, R_LOG_XU, lxu);
+}
+
+// Newton right-hand sides and diagonals:
+//   sigma_x = zl/(x-xl) + zu/(xu-x); r1 = sig grad + J~^T lambda - mu/(x-xl) + mu/(xu-x)
+//   r2 = z - mu/s; r4 = h' + s; Ds = v/s
+__global__ void k_newton_rhs(Dims D, It P, double sig, double mu, double *sigma, double *r1,
+                             double *r2, double *r4, double *Ds) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < D.n) {
+    double sx = 0.0, r = sig * P.grad[i] + P.jtl[i];
+    if (isfinite(P.xl[i])) {
+      double dl = P.x[i] - P.xl[i];
+      sx += P.zl[i] / dl;
+      r -= mu / dl;
+    }
+    if (isfinite(P.xu[i])) {
+      double du = P.xu[i] - P.x[i];
+      sx += P.zu[i] / du;
+      r += mu / du;
+    }
+    sigma[i] = sx;
+    r1[i] = r;
+  }
+  if (i < D.mi) {
+    r2[i] = P.z[i] - mu / P.s[i];
+    r4[i] = P.hin[i] + P.s[i];
+    Ds[i] = P.v[i] / P.s[i];
+  }
+}
+
+// weights d and right-hand side b of the augmented system over the model rows [G; H]
+//   Lifted: G rows combine the relaxed pair (D1 = Ds_a + dw, D2 = Ds_b + dw):
+//           d = D1 + D2, b = (-D1 r4a + r2a + D2 r4b - r2b) / d;  H rows d = Ds + dw, b = -r4 + r2/d
+//   HyKKT:  G rows d = gamma, b = -r3;  H rows as above
+__global__ void k_aug_rhs(Dims D, double dw, double gamma, const double *r2, const double *r4,
+                          const double *Ds, const double *geq, double *d, double *b) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < D.me0) {
+    if (D.lifted) {
+      double d1 = Ds[k] + dw, d2 = Ds[D.me0 + k] + dw;
+      d[k] = d1 + d2;
+      b[k] = (-d1 * r4[k] + r2[k] + d2 * r4[D.me0 + k] - r2[D.me0 + k]) / (d1 + d2);
+    } else {
+      d[k] = gamma;
+      b[k] = -geq[k];
+    }
+  }
+  if (k < D.mi0) {
+    int ip = D.lifted ? 2 * D.me0 + k : k;
+    double dh = Ds[ip] + dw;
+    d[D.me0 + k] = dh;
+    b[D.me0 + k] = -r4[ip] + r2[ip] / dh;
+  }
+}
+
+__global__ void k_neg(int n, const double *a, double *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = -a[i];
+}
+
+// recover dz over the IPM slack rows from J~ dx (jdx over model rows) and ds, dv, dzl, dzu
+struct StepArgs {
+  Dims D;
+  It P;
+  double mu, dw;
+  const double *r2, *r4, *Ds, *jdx, *dx, *sigma;
+  const double *dzH;  // HyKKT: dz over H rows (from hykkt_cg)
+  double *dz, *ds, *dv, *dzl, *dzu;
+};
+__global__ void k_recover(StepArgs A) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const Dims &D = A.D;
+  if (i < D.mi) {
+    double dz;
+    if (D.lifted) {
+      double dh = A.Ds[i] + A.dw;
+      double hdx = i < D.me0 ? A.jdx[i] : (i < 2 * D.me0 ? -A.jdx[i - D.me0] : A.jdx[i - D.me0]);
+      dz = -A.r2[i] + dh * (hdx + A.r4[i]);
+    } else {
+      dz = A.dzH[i];
+    }
+    A.dz[i] = dz;
+    double ds = -(A.r2[i] + dz) / (A.Ds[i] + A.dw);
+    A.ds[i] = ds;
+    A.dv[i] = (A.mu - A.P.v[i] * ds) / A.P.s[i] - A.P.v[i];
+  }
+  if (i < D.n) {
+    double dx = A.dx[i];
+    if (isfinite(A.P.xl[i])) {
+      double dl = A.P.x[i] - A.P.xl[i];
+      A.dzl[i] = A.mu / dl - A.P.zl[i] - A.P.zl[i] / dl * dx;
+    } else {
+      A.dzl[i] = 0.0;
+    }
+    if (isfinite(A.P.xu[i])) {
+      double du = A.P.xu[i] - A.P.x[i];
+      A.dzu[i] = A.mu / du - A.P.zu[i] + A.P.zu[i] / du * dx;
+    } else {
+      A.dzu[i] = 0.0;
+    }
+  }
+}
+
+// fraction to the boundary (min over ratios) and the directional derivative of phi
+__global__ void k_ftb(StepArgs A, double tau, double sig, double *R) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const Dims &D = A.D;
+  double ap = 1.0, az = 1.0, gx = 0.0, gs = 0.0;
+  if (i < D.n) {
+    double x = A.P.x[i], dx = A.dx[i];
+    gx = sig * A.P.grad[i] * dx;
+    if (isfinite(A.P.xl[i])) {
+      double dl = x - A.P.xl[i];
+      if (dx < 0) ap = fmin(ap, -tau * dl / dx);
+      if (A.dzl[i] < 0) az = fmin(az, -tau * A.P.zl[i] / A.dzl[i]);
+      gx -= A.mu * dx / dl;
+    }
+    if (isfinite(A.P.xu[i])) {
+      double du = A.P.xu[i] - x;
+      if (dx > 0) ap = fmin(ap, tau * du / dx);
+      if (A.dzu[i] < 0) az = fmin(az, -tau * A.P.zu[i] / A.dzu[i]);
+      gx += A.mu * dx / du;
+    }
+  }
+  if (i < D.mi) {
+    if (A.ds[i] < 0) ap = fmin(ap, -tau * A.P.s[i] / A.ds[i]);
+    if (A.dv[i] < 0) az = fmin(az, -tau * A.P.v[i] / A.dv[i]);
+    gs = -A.mu * A.ds[i] / A.P.s[i];
+  }
+  red_min(R, R_AMAX, ap);
+  red_min(R, R_AZ, az);
+  red_sum(R, R_GPHI_X, gx);
+  red_sum(R, R_GPHI_S, gs);
+}
+
+__global__ void k_trial(int n, int mi, double a, const double *x, const double *dx,
+                        const double *s, const double *ds, double *xt, double *st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xt[i] = x[i] + a * dx[i];
+  if (i < mi) st[i] = s[i] + a * ds[i];
+}
+
+// accept the step: primal (x, s from the trial), y, z with alpha, bound duals with alpha_z, then
+// the bound-multiplier safeguard kappa_Sigma
+__global__ void k_accept(StepArgs A, double alpha, double az, const double *xt, const double *st,
+                         const double *dy) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const Dims &D = A.D;
+  const double mu = A.mu;
+  if (i < D.n) {
+    double x = xt[i];
+    A.P.x[i] = x;
+    if (isfinite(A.P.xl[i])) {
+      double dl = x - A.P.xl[i];
+      double zl = A.P.zl[i] + az * A.dzl[i];
+      A.P.zl[i] = fmin(fmax(zl, mu / (KAPPA_SIGMA * dl)), KAPPA_SIGMA * mu / dl);
+    } else {
+      A.P.zl[i] = 0.0;
+    }
+    if (isfinite(A.P.xu[i])) {
+      double du = A.P.xu[i] - x;
+      double zu = A.P.zu[i] + az * A.dzu[i];
+      A.P.zu[i] = fmin(fmax(zu, mu / (KAPPA_SIGMA * du)), KAPPA_SIGMA * mu / du);
+    } else {
+      A.P.zu[i] = 0.0;
+    }
+  }
+  if (i < D.mi) {
+    double s = st[i];
+    A.P.s[i] = s;
+    A.P.z[i] += alpha * A.dz[i];
+    double v = A.P.v[i] + az * A.dv[i];
+    A.P.v[i] = fmin(fmax(v, mu / (KAPPA_SIGMA * s)), KAPPA_SIGMA * mu / s);
+  }
+  if (i < D.me) A.P.y[i] += alpha * dy[i];
+}
+
+__global__ void k_init_duals(Dims D, It P, double *s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < D.mi) {
+    s[i] = fmax(-P.hin[i], KAPPA1);
+    P.z[i] = 1.0;
+    P.v[i] = 1.0;
+  }
+  if (i < D.me) P.y[i] = 0.0;
+  if (i < D.n) {
+    P.zl[i] = isfinite(P.xl[i]) ? 1.0 : 0.0;
+    P.zu[i] = isfinite(P.xu[i]) ? 1.0 : 0.0;
+  }
+}
+
+}  // namespace cipm
+
+using namespace cipm;
+
+struct ipm_state_s {
+  ipm_opf_t opf = nullptr;
+  ipm_options opt;
+  cudaStream_t stream = 0;
+  Dims D;
+  ipm_sym_t sym = nullptr;
+  ipm_num_t num = nullptr;
+  std::vector<double *> bufs;
+  It P;
+  double *dscale, *gs, *hs, *Jv, *Wv, *lam, *lamw, *f;
+  double *sigma, *r1, *r2, *r4, *Ds, *dcond, *baug, *a, *dx, *dy, *dzH, *dzc, *jdx;
+  double *dz, *ds, *dv, *dzl, *dzu, *xt, *st, *geqt, *hint, *gst, *hst, *ft;
+  double *R = nullptr, *hR = nullptr, *eta = nullptr;
+  int *info = nullptr, *steps = nullptr;
+  int nnzJ = 0, nnzW = 0, nb = 0, ng = 0;
+  // host-side algorithm state
+  double sig = 1.0, mu = 0.1, tau = 0.99, delta_last = 0.0;
+  double theta_max = 0, theta_min = 0;
+  bool have_theta0 = false;
+  std::vector<std::pair<double, double>> filter;
+  int k = 0;
+  int status = 0;  // 0 running, 1 converged, <0/IPM_ERR_* failure
+  int nl = 0, nu = 0;
+};
+
+static int grid1(int64_t n) { return grid_for(n > 0 ? n : 1, 256); }
+
+static int st_alloc(ipm_state_t S, double **p, int64_t n) {
+  CKR(dev_alloc(p, n > 0 ? n : 1));
+  S->bufs.push_back(*p);
+  return IPM_OK;
+}
+
+static int reduce_reset(ipm_state_t S, std::initializer_list<int> which, double init) {
+  for (int k : which) {
+    // +inf for min-reductions, 0 otherwise (bit patterns of non-negative doubles)
+    CK(cudaMemcpyAsync(S->R + k, &init, sizeof(double), cudaMemcpyHostToDevice, S->stream));
+  }
+  return IPM_OK;
+}
+
+static int read_R(ipm_state_t S) {
+  CK(cudaMemcpyAsync(S->hR, S->R, sizeof(double) * R_COUNT, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return IPM_OK;
+}
+
+// model evaluation at x (constraints scaled, IPM rows built); with_jac: also J~, grad, J~^T lambda
+static int eval_point(ipm_state_t S, const double *x, double *gs, double *hs, double *geq,
+                      double *hin, double *f, bool with_jac) {
+  const OpfData &M = S->opf->M;
+  cudaStream_t s = S->stream;
+  CKR(opf_eval(M, x, nullptr, nullptr, 1.0, f, with_jac ? S->P.grad : nullptr, gs, hs,
+               with_jac ? S->Jv : nullptr, nullptr, s));
+  k_scale_vec<<<grid1(S->D.me0), 256, 0, s>>>(S->D.me0, S->dscale, gs);
+  k_scale_vec<<<grid1(S->D.mi0), 256, 0, s>>>(S->D.mi0, S->dscale + S->D.me0, hs);
+  k_ipm_rows<<<grid1(std::max(S->D.me0, S->D.mi0)), 256, 0, s>>>(S->D, S->opt.tau, gs, hs, geq,
+                                                                 hin);
+  CKL();
+  if (with_jac) {
+    const int m = S->D.me0 + S->D.mi0;
+    dim3 blk(32, 8);
+    k_scale_rows<<<grid_for(m, 8), blk, 0, s>>>(m, M.J_rowptr, S->dscale, S->Jv);
+    CKL();
+  }
+  return IPM_OK;
+}
+
+static int jt_lambda(ipm_state_t S) {
+  cudaStream_t s = S->stream;
+  const int m = S->D.me0 + S->D.mi0;
+  k_lambda<<<grid1(std::max(S->D.me0, S->D.mi0)), 256, 0, s>>>(S->D, S->P.y, S->P.z, S->lam);
+  CKL();
+  k_jtu<<<grid1(S->D.n), 256, 0, s>>>(S->D.n, S->sym->JT_ptr, S->sym->JT_ent, S->sym->J_rowidx,
+                                      S->Jv, S->lam, S->P.jtl);
+  CKL();
+  (void)m;
+  return IPM_OK;
+}
+
+static int errors(ipm_state_t S, double mu, double *out) {
+  CKR(reduce_reset(S, {R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_MAX_SV, R_MAX_XL, R_MAX_XU,
+                       R_SUM_Y, R_SUM_Z, R_SUM_V, R_SUM_ZL, R_SUM_ZU}, 0.0));
+  int nmax = std::max({S->D.n, S->D.me, S->D.mi});
+  k_errors<<<grid1(nmax), 256, 0, S->stream>>>(S->D, S->P, S->sig, mu, S->R);
+  CKL();
+  CKR(read_R(S));
+  const double *h = S->hR;
+  const Dims &D = S->D;
+  double sd = std::max(S_MAX, (h[R_SUM_Y] + h[R_SUM_Z] + h[R_SUM_V] + h[R_SUM_ZL] + h[R_SUM_ZU]) /
+                                  std::max(D.me + 2 * D.mi + S->nl + S->nu, 1)) / S_MAX;
+  double sc = std::max(S_MAX, (h[R_SUM_V] + h[R_SUM_ZL] + h[R_SUM_ZU]) /
+                                  std::max(D.mi + S->nl + S->nu, 1)) / S_MAX;
+  double dual = std::max(h[R_MAX_GL], h[R_MAX_ZV]) / sd;
+  double prim = std::max(h[R_MAX_G], h[R_MAX_HS]);
+  double comp = std::max({h[R_MAX_SV], h[R_MAX_XL], h[R_MAX_XU]}) / sc;
+  *out = std::max({dual, prim, comp});
+  return IPM_OK;
+}
+
+// theta, phi at (x, s) with rows (geq, hin) and objective value *f (device)
+static int merit(ipm_state_t S, const double *x, const double *sv, const double *geq,
+                 const double *hin, const double *f, double mu, double *theta, double *phi) {
+  CKR(reduce_reset(S, {R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU}, 0.0));
+  int nmax = std::max({S->D.n, S->D.me, S->D.mi});
+  k_merit<<<grid1(nmax), 256, 0, S->stream>>>(S->D, x, sv, S->P.xl, S->P.xu, geq, hin, S->R);
+  CKL();
+  double fv = 0.0;
+  CK(cudaMemcpyAsync(&fv, f, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  CKR(read_R(S));
+  const double *h = S->hR;
+  *theta = h[R_TH_G] + h[R_TH_H];
+  *phi = S->sig * fv - mu * (h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU]);
+  return IPM_OK;
+}
+
+extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStream_t stream,
+                                ipm_state_t *out) {
+  if (!opf || !opt || !out || (opt->kkt != 0 && opt->kkt != 1) || !(opt->tol > 0)) {
+    set_error_msg("ipm_state_create: bad argument");
+    return IPM_ERR_BAD_ARG;
+  }
+  *out = nullptr;
+  ipm_state_t S = new ipm_state_s();
+  S->opf = opf;
+  S->opt = *opt;
+  if (!(S->opt.tau > 0)) S->opt.tau = S->opt.tol;
+  if (!(S->opt.mu0 > 0)) S->opt.mu0 = 0.1;
+  if (!(S->opt.cg_rtol > 0)) S->opt.cg_rtol = 1e-10;
+  if (S->opt.max_refine < 0) S->opt.max_refine = 10;
+  S->stream = stream;
+  const OpfData &M = opf->M;
+  Dims &D = S->D;
+  D.n = M.n;
+  D.me0 = M.me;
+  D.mi0 = M.mi;
+  D.lifted = opt->kkt == 0;
+  D.me = D.lifted ? 0 : M.me;
+  D.mi = D.lifted ? 2 * M.me + M.mi : M.mi;
+  S->nb = M.nb;
+  S->ng = M.ng;
+  S->nnzJ = M.nnzJ;
+  S->nnzW = M.nnzW;
+  const int n = D.n, m = M.me + M.mi;
+  int rc = IPM_OK;
+  auto A = [&](double **p, int64_t k) {
+    if (rc == IPM_OK) rc = st_alloc(S, p, k);
+  };
+  A(&S->P.x, n); A(&S->P.s, D.mi); A(&S->P.y, D.me); A(&S->P.z, D.mi); A(&S->P.v, D.mi);
+  A(&S->P.zl, n); A(&S->P.zu, n); A(&S->P.grad, n); A(&S->P.jtl, n);
+  A(&S->P.geq, D.me); A(&S->P.hin, D.mi);
+  A(&S->dscale, m); A(&S->gs, M.me); A(&S->hs, M.mi); A(&S->Jv, M.nnzJ); A(&S->Wv, M.nnzW);
+  A(&S->lam, m); A(&S->lamw, m); A(&S->f, 2);
+  A(&S->sigma, n); A(&S->r1, n); A(&S->r2, D.mi); A(&S->r4, D.mi); A(&S->Ds, D.mi);
+  A(&S->dcond, m); A(&S->baug, m); A(&S->a, n); A(&S->dx, n); A(&S->dy, M.me); A(&S->dzH, M.mi);
+  A(&S->dzc, m); A(&S->jdx, m);
+  A(&S->dz, D.mi); A(&S->ds, D.mi); A(&S->dv, D.mi); A(&S->dzl, n); A(&S->dzu, n);
+  A(&S->xt, n); A(&S->st, D.mi); A(&S->geqt, D.me); A(&S->hint, D.mi); A(&S->gst, M.me);
+  A(&S->hst, M.mi); A(&S->ft, 2); A(&S->R, R_COUNT); A(&S->eta, 1);
+  S->P.xl = M.xl;
+  S->P.xu = M.xu;
+  if (rc == IPM_OK) rc = dev_alloc(&S->info, 2);
+  if (rc == IPM_OK) rc = dev_alloc(&S->steps, 2);
+  if (rc == IPM_OK && cudaMallocHost((void **)&S->hR, sizeof(double) * R_COUNT) != cudaSuccess)
+    rc = IPM_ERR_OOM;
+  if (rc == IPM_OK) {
+    // bounds present
+    std::vector<double> hxl(n), hxu(n);
+    if (cudaMemcpy(hxl.data(), M.xl, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(hxu.data(), M.xu, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = IPM_ERR_CUDA;
+    for (int j = 0; j < n; ++j) {
+      S->nl += std::isfinite(hxl[j]);
+      S->nu += std::isfinite(hxu[j]);
+    }
+  }
+  if (rc == IPM_OK) rc = ipm_symbolic(n, m, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr,
+                                      M.W_colind, M.nnzW, stream, &S->sym);
+  if (rc == IPM_OK) rc = ipm_num_create(S->sym, 64, &S->num);
+  if (rc == IPM_OK) {
+    // starting point, objective scaling and row scaling at x0 (Ipopt gradient-based scaling)
+    cudaStream_t s = stream;
+    double zero = 0.0;
+    for (int k = 0; k < R_COUNT; ++k) cudaMemcpy(S->R + k, &zero, sizeof(double), cudaMemcpyHostToDevice);
+    k_setup_sums<<<grid1(M.nb), 256, 0, s>>>(M.nb, M.pd, M.qd, S->R);
+    k_x0<<<grid1(n), 256, 0, s>>>(M.nb, M.ng, S->R, M.xl, M.xu, S->P.x);
+    rc = opf_eval(M, S->P.x, nullptr, nullptr, 1.0, S->f, S->P.grad, S->gs, S->hs, S->Jv, nullptr, s);
+  }
+  if (rc == IPM_OK) {
+    cudaStream_t s = stream;
+    k_row_scale<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, S->Jv, S->dscale);
+    k_max_abs<<<grid1(n), 256, 0, s>>>(n, S->P.grad, S->R, R_MAXGRAD);
+    if (read_R(S) != IPM_OK) rc = IPM_ERR_CUDA;
+  }
+  if (rc == IPM_OK) {
+    S->sig = std::min(1.0, 100.0 / std::max(S->hR[R_MAXGRAD], 1e-300));
+    rc = eval_point(S, S->P.x, S->gs, S->hs, S->P.geq, S->P.hin, S->f, true);
+  }
+  if (rc == IPM_OK) {
+    k_init_duals<<<grid1(std::max({D.n, D.me, D.mi})), 256, 0, stream>>>(D, S->P, S->P.s);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) rc = IPM_ERR_CUDA;
+  }
+  S->mu = S->opt.mu0;
+  S->tau = std::max(TAU_MIN, 1.0 - S->mu);
+  if (rc != IPM_OK) {
+    ipm_state_destroy(S);
+    return rc;
+  }
+  *out = S;
+  return IPM_OK;
+}
+
+extern "C" void ipm_state_destroy(ipm_state_t S) {
+  if (!S) return;
+  for (double *p : S->bufs) cudaFree(p);
+  if (S->info) cudaFree(S->info);
+  if (S->steps) cudaFree(S->steps);
+  if (S->hR) cudaFreeHost(S->hR);
+  if (S->num) ipm_num_destroy(S->num);
+  if (S->sym) ipm_symbolic_destroy(S->sym);
+  delete S;
+}
+
+static int step_impl(ipm_state_t S, ipm_iter_info *info) {
+  cudaStream_t s = S->stream;
+  const Dims &D = S->D;
+  const OpfData &M = S->opf->M;
+  const int n = D.n, m = D.me0 + D.mi0;
+  const int nmax = std::max({D.n, D.me, D.mi, m});
+  *info = ipm_iter_info{};
+  info->k = S->k;
+  // ---- evaluate at the current iterate
+  CKR(eval_point(S, S->P.x, S->gs, S->hs, S->P.geq, S->P.hin, S->f, true));
+  CKR(jt_lambda(S));
+  double e0;
+  CKR(errors(S, 0.0, &e0));
+  double theta, phi;
+  if (!S->have_theta0) {
+    CKR(merit(S, S->P.x, S->P.s, S->P.geq, S->P.hin, S->f, S->mu, &theta, &phi));
+    S->theta_max = 1e4 * std::max(1.0, theta);
+    S->theta_min = 1e-4 * std::max(1.0, theta);
+    S->have_theta0 = true;
+  }
+  double fval = 0.0;
+  CK(cudaMemcpy(&fval, S->f, sizeof(double), cudaMemcpyDeviceToHost));
+  info->kkt_err = e0;
+  info->obj = fval;
+  info->mu = S->mu;
+  if (e0 <= S->opt.tol) {
+    S->status = 1;
+    info->status = 1;
+    return IPM_OK;
+  }
+  // ---- barrier update (repeated only in the first iteration)
+  bool first = true;
+  while (true) {
+    double emu;
+    CKR(errors(S, S->mu, &emu));
+    if (!(emu <= KAPPA_EPS * S->mu && (first || S->k == 0))) break;
+    S->mu = std::max(S->opt.tol / 10.0, std::min(KAPPA_MU * S->mu, std::pow(S->mu, THETA_MU)));
+    S->tau = std::max(TAU_MIN, 1.0 - S->mu);
+    S->filter.clear();
+    first = false;
+  }
+  const double mu = S->mu;
+  info->mu = mu;
+  // ---- Hessian with scaled multipliers, Newton right-hand sides
+  k_mul<<<grid1(m), 256, 0, s>>>(m, S->lam, S->dscale, S->lamw);
+  CKL();
+  CKR(opf_eval(M, S->P.x, S->lamw, S->lamw + D.me0, S->sig, S->ft, nullptr, S->gst, S->hst,
+               nullptr, S->Wv, s));
+  k_newton_rhs<<<grid1(nmax), 256, 0, s>>>(D, S->P, S->sig, mu, S->sigma, S->r1, S->r2, S->r4,
+                                           S->Ds);
+  k_neg<<<grid1(n), 256, 0, s>>>(n, S->r1, S->a);
+  CKL();
+  // ---- inertia correction: delta_w = 0, then delta_last/3 (x8) or 1e-4 (x100)
+  double dw = 0.0;
+  int nfac = 0;
+  bool ok = false;
+  double grow = S->delta_last > 0 ? 8.0 : 100.0;
+  double next = S->delta_last > 0 ? std::max(1e-20, S->delta_last / 3.0) : 1e-4;
+  for (int attempt = 0; attempt < 200; ++attempt) {
+    dw = attempt == 0 ? 0.0 : next;
+    if (attempt > 0) next *= grow;
+    if (dw >= 1e40) break;
+    k_aug_rhs<<<grid1(std::max(D.me0, D.mi0)), 256, 0, s>>>(D, dw, S->opt.gamma, S->r2, S->r4,
+                                                            S->Ds, S->P.geq, S->dcond, S->baug);
+    CKL();
+    CKR(ipm_condense(S->sym, S->num, S->Wv, S->sigma, S->Jv, S->dcond, dw, s));
+    CKR(ipm_factor(S->sym, S->num, S->info, s));
+    int hinfo = 0;
+    CK(cudaMemcpyAsync(&hinfo, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ++nfac;
+    if (hinfo == -2) return IPM_ERR_TIMEOUT;
+    if (hinfo == -1) {
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) return IPM_ERR_NOT_PD;
+  if (dw > 0) S->delta_last = dw;
+  info->delta_w = dw;
+  info->n_factor = nfac;
+  // ---- solve
+  StepArgs SA;
+  SA.D = D;
+  SA.P = S->P;
+  SA.mu = mu;
+  SA.dw = dw;
+  SA.r2 = S->r2;
+  SA.r4 = S->r4;
+  SA.Ds = S->Ds;
+  SA.jdx = S->jdx;
+  SA.dx = S->dx;
+  SA.sigma = S->sigma;
+  SA.dzH = S->dzH;
+  SA.dz = S->dz;
+  SA.ds = S->ds;
+  SA.dv = S->dv;
+  SA.dzl = S->dzl;
+  SA.dzu = S->dzu;
+  if (D.lifted) {
+    int st = ipm_aug_solve(S->sym, S->num, S->Wv, S->sigma, S->Jv, S->dcond, dw, S->a, S->baug,
+                           S->dx, S->dzc, S->opt.max_refine, 1e-10, S->eta, S->steps, s);
+    if (st < 0 || st == IPM_ERR_TIMEOUT || st == IPM_ERR_NONFINITE) return st;
+    double eta = 0;
+    int steps = 0;
+    CK(cudaMemcpy(&eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&steps, S->steps, sizeof(int), cudaMemcpyDeviceToHost));
+    info->eta = eta;
+    info->refine_steps = steps;
+    k_jv<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, M.J_colind, S->Jv, S->dx, S->jdx);
+    CKL();
+  } else {
+    int its = 0;
+    double rel = 0;
+    int st = hykkt_cg(S->sym, S->num, D.me0, S->Jv, S->dcond, S->opt.gamma, S->a, S->baug,
+                      S->opt.cg_rtol, S->opt.cg_maxit > 0 ? S->opt.cg_maxit : std::max(D.me0, 1),
+                      S->dx, S->dy, S->dzH, &its, &rel, s);
+    if (st < 0 || st == IPM_ERR_TIMEOUT) return st;
+    info->cg_iters = its;
+  }
+  k_recover<<<grid1(nmax), 256, 0, s>>>(SA);
+  CKL();
+  // ---- fraction to the boundary and d phi
+  CKR(reduce_reset(S, {R_AMAX, R_AZ}, 1.0));
+  CKR(reduce_reset(S, {R_GPHI_X, R_GPHI_S}, 0.0));
+  k_ftb<<<grid1(nmax), 256, 0, s>>>(SA, S->tau, S->sig, S->R);
+  CKL();
+  CKR(read_R(S));
+  const double amax = S->hR[R_AMAX], az = S->hR[R_AZ];
+  const double gphi = S->hR[R_GPHI_X] + S->hR[R_GPHI_S];
+  CKR(merit(S, S->P.x, S->P.s, S->P.geq, S->P.hin, S->f, mu, &theta, &phi));
+  double amin;
+  if (gphi < 0)
+    amin = GAMMA_ALPHA * std::min({GAMMA_THETA, GAMMA_PHI * theta / -gphi,
+                                   DELTA_SW * std::pow(theta, S_THETA) / std::pow(-gphi, S_PHI)});
+  else
+    amin = GAMMA_ALPHA * GAMMA_THETA;
+  // ---- backtracking filter line search
+  double alpha = amax;
+  bool accepted = false, ftype = false;
+  int ls = 0;
+  while (true) {
+    k_trial<<<grid1(std::max(n, D.mi)), 256, 0, s>>>(n, D.mi, alpha, S->P.x, S->dx, S->P.s, S->ds,
+                                                     S->xt, S->st);
+    CKL();
+    CKR(eval_point(S, S->xt, S->gst, S->hst, S->geqt, S->hint, S->ft, false));
+    double tht, pht;
+    CKR(merit(S, S->xt, S->st, S->geqt, S->hint, S->ft, mu, &tht, &pht));
+    bool okf = tht < S->theta_max;
+    for (auto &fp : S->filter)
+      if (!(tht < fp.first || pht < fp.second)) {
+        okf = false;
+        break;
+      }
+    if (okf && std::isfinite(pht)) {
+      bool switching = gphi < 0 && alpha * std::pow(-gphi, S_PHI) > DELTA_SW * std::pow(theta, S_THETA);
+      if (switching && theta <= S->theta_min) {
+        if (pht <= phi + ETA_PHI * alpha * gphi) {
+          accepted = true;
+          ftype = true;
+        }
+      } else if (tht <= (1 - GAMMA_THETA) * theta || pht <= phi - GAMMA_PHI * theta) {
+        accepted = true;
+        ftype = false;
+      }
+    }
+    if (accepted) break;
+    ++ls;
+    alpha *= 0.5;
+    if (alpha < amin) break;
+  }
+  info->ls_steps = ls;
+  info->alpha = alpha;
+  info->theta = theta;
+  if (!accepted) {
+    S->status = IPM_ERR_RESTORATION;
+    info->status = IPM_ERR_RESTORATION;
+    return IPM_OK;
+  }
+  if (!ftype) S->filter.push_back({(1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta});
+  k_accept<<<grid1(nmax), 256, 0, s>>>(SA, alpha, az, S->xt, S->st, S->dy);
+  CKL();
+  CK(cudaStreamSynchronize(s));
+  S->k++;
+  return IPM_OK;
+}
+
+extern "C" int ipm_step(ipm_state_t S, ipm_iter_info *info) {
+  if (!S || !info) return IPM_ERR_BAD_ARG;
+  if (S->status != 0) {
+    *info = ipm_iter_info{};
+    info->k = S->k;
+    info->status = S->status;
+    return IPM_OK;
+  }
+  int rc = step_impl(S, info);
+  if (rc != IPM_OK) {
+    S->status = rc;
+    info->status = rc;
+  }
+  return rc < 0 ? rc : IPM_OK;
+}
+
+extern "C" int ipm_state_export(ipm_state_t S, double *x, double *obj) {
+  if (!S) return IPM_ERR_BAD_ARG;
+  if (x) CK(cudaMemcpy(x, S->P.x, sizeof(double) * S->D.n, cudaMemcpyDeviceToHost));
+  if (obj) {
+    CKR(opf_eval(S->opf->M, S->P.x, nullptr, nullptr, 1.0, S->ft, nullptr, S->gst, S->hst,
+                 nullptr, nullptr, S->stream));
+    CK(cudaMemcpyAsync(obj, S->ft, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+  }
+  return IPM_OK;
+}

@@ -196,8 +196,10 @@ __global__ void k_eval_init(OpfDims D, const double *pd, const double *qd, const
     g[D.nb + i] = -qd[i];
   }
   if (i == 0) g[2 * D.nb] = x[D.nb + ref];
-  for (int p = i; p < nnzJ; p += gridDim.x * blockDim.x) Jv[p] = 0.0;
-  for (int p = i; p < nnzW; p += gridDim.x * blockDim.x) Wv[p] = 0.0;
+  if (Jv)
+    for (int p = i; p < nnzJ; p += gridDim.x * blockDim.x) Jv[p] = 0.0;
+  if (Wv)
+    for (int p = i; p < nnzW; p += gridDim.x * blockDim.x) Wv[p] = 0.0;
 }
 
 // one thread per branch end
@@ -228,11 +230,13 @@ __global__ void k_eval_branch(OpfDims D, OpfData M, const double *x, const doubl
   const int hrow = e;
   const double rt = M.rate[k];
   h[hrow] = P * P + Q * Q - rt * rt;
-  const int *je = M.jentry + 2 * D.ng + 12 * e;
-  for (int c = 0; c < 4; ++c) {
-    atomicAdd(&Jv[je[c]], -dP[c]);
-    atomicAdd(&Jv[je[4 + c]], -dQ[c]);
-    Jv[je[8 + c]] = 2 * P * dP[c] + 2 * Q * dQ[c];
+  if (Jv) {
+    const int *je = M.jentry + 2 * D.ng + 12 * e;
+    for (int c = 0; c < 4; ++c) {
+      atomicAdd(&Jv[je[c]], -dP[c]);
+      atomicAdd(&Jv[je[4 + c]], -dQ[c]);
+      Jv[je[8 + c]] = 2 * P * dP[c] + 2 * Q * dQ[c];
+    }
   }
   if (Wv) {
     const double yP = y[bus], yQ = y[D.nb + bus], zz = z[hrow];
@@ -255,8 +259,10 @@ __global__ void k_eval_gen(OpfDims D, OpfData M, const double *x, double sigma_f
     double pg = x[2 * D.nb + gi], qg = x[2 * D.nb + D.ng + gi];
     atomicAdd(&g[bus], pg);
     atomicAdd(&g[D.nb + bus], qg);
-    Jv[M.jentry[2 * gi]] = 1.0;
-    Jv[M.jentry[2 * gi + 1]] = 1.0;
+    if (Jv) {
+      Jv[M.jentry[2 * gi]] = 1.0;
+      Jv[M.jentry[2 * gi + 1]] = 1.0;
+    }
     double pm = pg * BASE;
     fc = M.c2[gi] * pm * pm + M.c1[gi] * pm;
     if (grad) {
@@ -282,7 +288,7 @@ __global__ void k_eval_finish(OpfDims D, OpfData M, const double *fpart, int npa
   if (grad)
     for (int k = i; k < 2 * D.nb; k += gridDim.x * blockDim.x) grad[k] = 0.0;
   if (i == 0) {
-    Jv[M.jentry[2 * D.ng + 24 * D.nbr]] = 1.0;
+    if (Jv) Jv[M.jentry[2 * D.ng + 24 * D.nbr]] = 1.0;
     if (f) {
       double s = 0.0;
       for (int p = 0; p < nparts; ++p) s += fpart[p];
@@ -296,8 +302,8 @@ int opf_eval(const OpfData &M, const double *x, const double *y, const double *z
              cudaStream_t s) {
   OpfDims D{M.nb, M.nbr, M.ng, M.n, M.me, M.mi};
   int nthreads = max(max(D.nb, 1), 256);
-  k_eval_init<<<grid_for(nthreads, 256), 256, 0, s>>>(D, M.pd, M.qd, x, M.ref, g, Jv, M.nnzJ,
-                                                      Wv, Wv ? M.nnzW : 0);
+  k_eval_init<<<grid_for(nthreads, 256), 256, 0, s>>>(D, M.pd, M.qd, x, M.ref, g, Jv,
+                                                      Jv ? M.nnzJ : 0, Wv, Wv ? M.nnzW : 0);
   CKL();
   if (D.nbr > 0) {
     k_eval_branch<<<grid_for(2 * D.nbr, 128), 128, 0, s>>>(D, M, x, y, z, g, h, Jv, Wv);
@@ -379,10 +385,6 @@ int opf_create(OpfData &M, int nb, int nbr, int ng, const int *f_bus, const int 
 
 using namespace cipm;
 
-struct ipm_opf_s {
-  OpfData M;
-};
-
 extern "C" int ipm_opf_create(int nb, int nbr, int ng, const int *f_bus, const int *t_bus,
                               const double *r, const double *x, const double *b,
                               const double *rate, const double *pd, const double *qd,
@@ -441,7 +443,7 @@ extern "C" int ipm_opf_patterns(ipm_opf_t P, int *J_rowptr, int *J_colind, int *
 extern "C" int ipm_opf_eval(ipm_opf_t P, const double *x, const double *y, const double *z,
                             double sigma_f, double *f, double *grad, double *g, double *h,
                             double *J_val, double *W_val, cudaStream_t s) {
-  if (!P || !x || !g || !h || !J_val || (W_val && (!y || !z))) return IPM_ERR_BAD_ARG;
+  if (!P || !x || !g || !h || (W_val && (!y || !z))) return IPM_ERR_BAD_ARG;
   return opf_eval(P->M, x, y, z, sigma_f, f, grad, g, h, J_val, W_val, s);
 }
 

@@ -26,3 +26,7 @@ int opf_eval(const OpfData &M, const double *x, const double *y, const double *z
              cudaStream_t s);
 
 }  // namespace cipm
+
+struct ipm_opf_s {
+  cipm::OpfData M;
+};
