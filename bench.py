@@ -250,6 +250,43 @@ def run_gpu(args, rank, world, local_rank):
         e3.synchronize()
         e_tot += e0.elapsed_time(e3)
     n_e2e = max(3, args.steps // 2)
+    # ---- precision row: FP32 condensation/factor/solves + FP64 preconditioned CG refinement
+    fp32 = None
+    if not args.no_fp32:
+        N32 = cp.Numeric(S, precision=32)
+        dx32, dz32 = torch.zeros(n, **f64), torch.zeros(m, **f64)
+        dw32 = dw
+        for k in range(40):  # the FP32 factor of the shifted matrix may need a larger delta_w
+            cp.ipm_condense(S, N32, Wv, sig, Jv, dd, dw32)
+            cp.ipm_factor(S, N32, info)
+            if int(info.item()) == -1:
+                break
+            dw32 = max(1e-4, dw32 * 100.0)
+        ph32 = []
+        st32 = 0
+        for k in range(args.warmup + max(3, args.steps // 2)):
+            flush.zero_()
+            e0.record(stream)
+            cp.ipm_condense(S, N32, Wv, sig, Jv, dd, dw32)
+            e1.record(stream)
+            cp.ipm_factor(S, N32, info)
+            e2.record(stream)
+            try:
+                st32 = cp.ipm_aug_solve(S, N32, Wv, sig, Jv, dd, dw32, a, bb, dx32, dz32, eta, steps_t)
+            except Exception as ex:  # reported, not fatal to the FP64 line
+                st32 = str(ex)
+            e3.record(stream)
+            e3.synchronize()
+            if k >= args.warmup:
+                ph32.append([e0.elapsed_time(e1), e1.elapsed_time(e2), e2.elapsed_time(e3)])
+        ph32 = np.array(ph32)
+        prec, pcg = cp.ipm_num_info(N32)
+        rel = float((dx32 - dx).abs().max().item() / dx.abs().max().item()) if dw32 == dw else None
+        fp32 = {"value": len(ph32) / (ph32.sum() / 1e3), "unit": UNIT,
+                "phases_ms": {nm: float(v) for nm, v in zip(["condense", "factor", "solve"],
+                                                            ph32.mean(axis=0))},
+                "delta_w": dw32, "pcg_iters": pcg, "backward_error": float(eta.item()),
+                "status": st32, "dx_rel_diff_vs_fp64": rel}
     clk = clocks.stop()
     h2d = 8 * (opf.nnzW + opf.nnzJ + n + m + n + m)
     d2h = 8 * (n + m)
@@ -307,11 +344,61 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": n_e2e / (e_tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "fp32": fp32,
         "clocks": clk,
     }
+    if not args.no_ipm and world == 1:
+        line["ipm"] = ipm_measure(include_oracle=not args.no_cpu_baseline)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+def ipm_measure(include_oracle=True):
+    """Full IPM solves to the 1e-6 scaled KKT tolerance on the GPU (ipm_step loop), with the
+    oracle IPM timed on the same problem (single thread) where it takes seconds."""
+    import torch
+    import paper_2405_14236_gb300 as cp
+    from synth import config_grid
+    out = {}
+    cases = [("planar1k", "lifted", 64), ("planar1k", "hykkt", 64), ("planar10k", "hykkt", 64),
+             ("planar1k", "lifted", 32), ("planar10k", "hykkt", 32)]
+    warm = cp.ipm_solve_opf(cp.Opf(config_grid("ring30")), kkt="hykkt")
+    del warm
+    for name, kkt, prec in cases:
+        g = config_grid(name)
+        opf = cp.Opf(g)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = cp.IpmState(opf, kkt=kkt, gamma=1e6, precision=prec)
+        torch.cuda.synchronize()
+        t_init = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hist = []
+        for _ in range(3001):
+            info = st.step()
+            hist.append(info)
+            if info.status != 0:
+                break
+        t_solve = time.perf_counter() - t0
+        rec = {"status": "converged" if hist[-1].status == 1 else f"status {hist[-1].status}",
+               "iters": hist[-1].k, "obj": st.objective(), "init_s": t_init, "solve_s": t_solve,
+               "ms_per_iter": 1e3 * t_solve / max(hist[-1].k, 1),
+               "ipm_solves_per_s": 1.0 / t_solve,
+               "factorizations": int(sum(h.n_factor for h in hist)),
+               "cg_iters": int(sum(h.cg_iters for h in hist)),
+               "fp32_iters": int(sum(1 for h in hist if h.precision == 32))}
+        if include_oracle and name == "planar1k" and prec == 64:
+            from oracle.opf import OPFModel
+            from oracle import ipm as oipm
+            t0 = time.perf_counter()
+            r = oipm.solve(OPFModel(g), oipm.Options(kkt=kkt, gamma=1e6))
+            el = time.perf_counter() - t0
+            rec["oracle_cpu"] = {"ipm_solves_per_s": 1.0 / el, "iters": r.iters, "obj": r.obj,
+                                 "cores": 1, "status": r.status}
+            rec["obj_rel_diff_vs_oracle"] = abs(rec["obj"] - r.obj) / abs(r.obj)
+        out[f"{name}-{kkt}" + ("-fp32" if prec == 32 else "")] = rec
+    return out
 
 
 def main():
@@ -321,6 +408,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ipm", action="store_true", help="skip the full-IPM measurement")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-factor variant")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

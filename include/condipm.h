@@ -101,9 +101,18 @@ int ipm_symbolic_export_panels(ipm_sym_t sym, int *srow_ptr, int *srow, int64_t 
 
 void ipm_symbolic_destroy(ipm_sym_t sym);
 
-/* Numeric storage for one pattern.  precision: 64 (FP64 factor).  Allocates the panel
- * values and every workspace the numeric calls need. */
+/* Numeric storage for one pattern.  precision: 64 (FP64 panels and factor) or 32 (the
+ * condensation sums are formed in FP64 and stored in FP32, the factorization runs in FP32, the
+ * triangular solves read the FP32 factor and compute in FP64; the factored matrix carries a
+ * relative diagonal shift of 2^-20).  ipm_aug_solve and hykkt_cg then reach FP64 accuracy by
+ * conjugate gradients in FP64 on K preconditioned by the FP32 factor, which converges while
+ * cond(K) * 2^-24 stays moderate; otherwise they return IPM_ERR_NOT_PD (the caller then
+ * switches to a precision-64 handle).  Allocates the panel values and every workspace. */
 int ipm_num_create(ipm_sym_t sym, int precision, ipm_num_t *out);
+
+/* HOST outputs: the handle's precision and the FP64 preconditioned-CG iterations spent by the
+ * last ipm_aug_solve / hykkt_cg on an FP32 factor (0 for FP64 handles). */
+int ipm_num_info(ipm_num_t num, int *precision, int *last_pcg_iters);
 void ipm_num_destroy(ipm_num_t num);
 
 /* Copies the panel values (panel_len doubles: the lower triangle of P K P^T after
@@ -118,7 +127,9 @@ int ipm_num_export(ipm_num_t num, double *Lx_host);
  *   J_val [nnzJ]    values of J in its pattern
  *   d_row [m]       per-row weight: gamma on HyKKT equality rows, D_H on inequality rows
  *   delta_w         primal regularization
- * Deterministic: each panel entry is one fixed-order sum, no atomics. */
+ * Deterministic: each panel entry is one fixed-order sum, no atomics.  The value pointers are
+ * kept: FP32 handles multiply by K in FP64 during ipm_aug_solve / hykkt_cg, so they must stay
+ * valid and unchanged until the solves that follow. */
 int ipm_condense(ipm_sym_t sym, ipm_num_t num, const double *W_val, const double *sigma_x,
                  const double *J_val, const double *d_row, double delta_w, cudaStream_t stream);
 
@@ -178,7 +189,10 @@ int ipm_solve_noalloc(ipm_sym_t sym, ipm_num_t num, const double *b, double *x, 
  * max_refine steps.  Requires a successful ipm_factor of the matching K.
  *   a [n], b [m], dx [n], dz [m];  d_eta (device double), d_steps (device int) receive the
  *   final backward error and the refinement steps taken.
- * Synchronizes once per refinement step (host decides whether to continue). */
+ * Synchronizes once per refinement step (host decides whether to continue).  With an FP32
+ * factor each condensed solve is FP64 conjugate gradients on K preconditioned by the factor;
+ * IPM_ERR_NOT_PD is returned when they meet negative curvature or reach neither a relative
+ * residual nor a normwise backward error of 1e-14 in 100 iterations (regularize more, as after a failed factorization). */
 int ipm_aug_solve(ipm_sym_t sym, ipm_num_t num, const double *W_val, const double *sigma_x,
                   const double *J_val, const double *d_row, double delta_w, const double *a,
                   const double *b, double *dx, double *dz, int max_refine, double tol,
@@ -197,7 +211,8 @@ int ipm_aug_solve(ipm_sym_t sym, ipm_num_t num, const double *W_val, const doubl
  *   d_row [m] as passed to ipm_condense (d_row[0..m_e) = gamma).
  *   a [n], b [m], dx [n], dy [m_e], dz [m - m_e]
  *   h_iters, h_relres: HOST outputs (CG iterations, final ||r||/||r_0||).
- * Returns IPM_ERR_CG_MAXIT if maxit was reached.  Synchronizes (convergence tests). */
+ * Returns IPM_ERR_CG_MAXIT if maxit was reached; with an FP32 factor, IPM_ERR_NOT_PD as for
+ * ipm_aug_solve.  Synchronizes (convergence tests). */
 int hykkt_cg(ipm_sym_t sym, ipm_num_t num, int m_e, const double *J_val, const double *d_row,
              double gamma, const double *a, const double *b, double rtol, int maxit, double *dx,
              double *dy, double *dz, int *h_iters, double *h_relres, cudaStream_t stream);
@@ -246,6 +261,10 @@ typedef struct {
   double cg_rtol;   /* HyKKT CG relative residual; <= 0 means 1e-10 */
   int max_refine;   /* LiftedKKT refinement steps; < 0 means 10 */
   int cg_maxit;     /* HyKKT CG iteration limit; <= 0 means m_e */
+  int precision;    /* factorization precision: 64 or 32; 0 means 64.  With 32 the state
+                       switches to an FP64 factor for good at the first iteration whose
+                       FP32-preconditioned FP64 refinement does not converge (late IPM
+                       iterations are too ill-conditioned for an FP32 factor) */
 } ipm_options;
 
 typedef struct {
@@ -253,6 +272,7 @@ typedef struct {
   int status;       /* 0 running, 1 converged, else an IPM_ERR_* code */
   double mu, kkt_err, alpha, delta_w, obj, eta, theta;
   int n_factor, cg_iters, refine_steps, ls_steps;
+  int precision;    /* factorization precision used by this iteration (32 or 64) */
 } ipm_iter_info;
 
 typedef struct ipm_state_s *ipm_state_t;

@@ -35,6 +35,7 @@ _SIGS = {
     "ipm_num_destroy": (None, [P]),
     "ipm_num_export": (I, [P, P]),
     "ipm_num_status": (I, [P, P]),
+    "ipm_num_info": (I, [P, P, P]),
     "ipm_set_spin_limit": (I, [ctypes.c_longlong]),
     "ipm_debug_add_dependency": (I, [P, I, I]),
     "ipm_condense": (I, [P, P, P, P, P, P, D, P]),
@@ -58,7 +59,8 @@ _SIGS = {
 class IpmOptions(ctypes.Structure):
     _fields_ = [("kkt", ctypes.c_int), ("tol", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("tau", ctypes.c_double), ("mu0", ctypes.c_double), ("cg_rtol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("cg_maxit", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("cg_maxit", ctypes.c_int),
+                ("precision", ctypes.c_int)]
 
 
 class IpmIterInfo(ctypes.Structure):
@@ -66,7 +68,8 @@ class IpmIterInfo(ctypes.Structure):
                 ("kkt_err", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("delta_w", ctypes.c_double), ("obj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("theta", ctypes.c_double), ("n_factor", ctypes.c_int), ("cg_iters", ctypes.c_int),
-                ("refine_steps", ctypes.c_int), ("ls_steps", ctypes.c_int)]
+                ("refine_steps", ctypes.c_int), ("ls_steps", ctypes.c_int),
+                ("precision", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -190,6 +193,12 @@ class Numeric:
             self.h = None
 
 
+def ipm_num_info(num):
+    prec, its = I(), I()
+    _check(lib().ipm_num_info(num.h, ctypes.byref(prec), ctypes.byref(its)), "ipm_num_info")
+    return prec.value, its.value
+
+
 def ipm_num_status(num):
     st = I()
     _check(lib().ipm_num_status(num.h, ctypes.byref(st)), "ipm_num_status")
@@ -288,10 +297,10 @@ class IpmState:
     """GPU interior-point iterate for an ``Opf`` problem (ipm_state_create / ipm_step)."""
 
     def __init__(self, opf, kkt="lifted", tol=1e-6, gamma=1e6, tau=0.0, mu0=0.1, cg_rtol=1e-10,
-                 max_refine=10, cg_maxit=0, stream=None):
+                 max_refine=10, cg_maxit=0, precision=64, stream=None):
         self.opf = opf
         o = IpmOptions(0 if kkt == "lifted" else 1, tol, gamma, tau, mu0, cg_rtol, max_refine,
-                       cg_maxit)
+                       cg_maxit, precision)
         h = ctypes.c_void_p()
         _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream), ctypes.byref(h)),
                "ipm_state_create")

@@ -57,14 +57,19 @@ struct ipm_sym_s {
 struct ipm_num_s {
   ipm_sym_t sym = nullptr;
   int precision = 64;
-  double *Lx = nullptr;  // panel values
-  double *Dx = nullptr;  // diagonal factors L11 of every supernode (column-major w x w)
+  void *Lx = nullptr;  // panel values (double or float, by precision)
+  void *Dx = nullptr;  // diagonal factors L11 + reciprocal pivots of every supernode
+  void *tJ = nullptr;     // d_row(p) J_p per J entry (condensation workspace)
+  // values of the last ipm_condense (caller-owned): the FP32 path multiplies by K in FP64
+  const double *cW = nullptr, *cSig = nullptr, *cJ = nullptr, *cD = nullptr;
+  double cDw = 0.0;
+  int last_pcg_iters = 0;
   bool factored = false;  // panels hold L21 and Dx holds L11 (else panels hold K)
   // dependency counters of the sync-free kernels: [0,ns) update arrivals, [ns,2ns) panel
   // tasks done, [2ns,3ns) forward arrivals, [3ns,4ns) backward done flags, then tickets/status
   int *sync = nullptr;
   // workspaces (n or m sized), allocated once
-  double *vn[8] = {nullptr};
+  double *vn[12] = {nullptr};
   double *vm[6] = {nullptr};
   double *scal = nullptr;  // device scalars
   double *h_scal = nullptr;  // pinned host mirror

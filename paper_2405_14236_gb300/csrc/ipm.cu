@@ -448,7 +448,8 @@ struct ipm_state_s {
   cudaStream_t stream = 0;
   Dims D;
   ipm_sym_t sym = nullptr;
-  ipm_num_t num = nullptr;
+  ipm_num_t num = nullptr;    // the factor in use
+  ipm_num_t num32 = nullptr;  // FP32 factor while it serves (precision 32), else null
   std::vector<double *> bufs;
   It P;
   double *dscale, *gs, *hs, *Jv, *Wv, *lam, *lamw, *f;
@@ -621,6 +622,7 @@ extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStrea
   if (rc == IPM_OK) rc = ipm_symbolic(n, m, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr,
                                       M.W_colind, M.nnzW, stream, &S->sym);
   if (rc == IPM_OK) rc = ipm_num_create(S->sym, 64, &S->num);
+  if (rc == IPM_OK && S->opt.precision == 32) rc = ipm_num_create(S->sym, 32, &S->num32);
   if (rc == IPM_OK) {
     // starting point, objective scaling and row scaling at x0 (Ipopt gradient-based scaling)
     cudaStream_t s = stream;
@@ -661,6 +663,7 @@ extern "C" void ipm_state_destroy(ipm_state_t S) {
   if (S->steps) cudaFree(S->steps);
   if (S->hR) cudaFreeHost(S->hR);
   if (S->num) ipm_num_destroy(S->num);
+  if (S->num32) ipm_num_destroy(S->num32);
   if (S->sym) ipm_symbolic_destroy(S->sym);
   delete S;
 }
@@ -717,41 +720,18 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
                                            S->Ds);
   k_neg<<<grid1(n), 256, 0, s>>>(n, S->r1, S->a);
   CKL();
-  // ---- inertia correction: delta_w = 0, then delta_last/3 (x8) or 1e-4 (x100)
+  // ---- inertia correction: delta_w = 0, then delta_last/3 (x8) or 1e-4 (x100).  A failed
+  // factorization, or (FP32 factor) a solve whose FP64 refinement meets negative curvature or
+  // does not converge, counts as wrong inertia.
   double dw = 0.0;
   int nfac = 0;
   bool ok = false;
   double grow = S->delta_last > 0 ? 8.0 : 100.0;
   double next = S->delta_last > 0 ? std::max(1e-20, S->delta_last / 3.0) : 1e-4;
-  for (int attempt = 0; attempt < 200; ++attempt) {
-    dw = attempt == 0 ? 0.0 : next;
-    if (attempt > 0) next *= grow;
-    if (dw >= 1e40) break;
-    k_aug_rhs<<<grid1(std::max(D.me0, D.mi0)), 256, 0, s>>>(D, dw, S->opt.gamma, S->r2, S->r4,
-                                                            S->Ds, S->P.geq, S->dcond, S->baug);
-    CKL();
-    CKR(ipm_condense(S->sym, S->num, S->Wv, S->sigma, S->Jv, S->dcond, dw, s));
-    CKR(ipm_factor(S->sym, S->num, S->info, s));
-    int hinfo = 0;
-    CK(cudaMemcpyAsync(&hinfo, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    ++nfac;
-    if (hinfo == -2) return IPM_ERR_TIMEOUT;
-    if (hinfo == -1) {
-      ok = true;
-      break;
-    }
-  }
-  if (!ok) return IPM_ERR_NOT_PD;
-  if (dw > 0) S->delta_last = dw;
-  info->delta_w = dw;
-  info->n_factor = nfac;
-  // ---- solve
   StepArgs SA;
   SA.D = D;
   SA.P = S->P;
   SA.mu = mu;
-  SA.dw = dw;
   SA.r2 = S->r2;
   SA.r4 = S->r4;
   SA.Ds = S->Ds;
@@ -764,10 +744,56 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   SA.dv = S->dv;
   SA.dzl = S->dzl;
   SA.dzu = S->dzu;
-  if (D.lifted) {
-    int st = ipm_aug_solve(S->sym, S->num, S->Wv, S->sigma, S->Jv, S->dcond, dw, S->a, S->baug,
-                           S->dx, S->dzc, S->opt.max_refine, 1e-10, S->eta, S->steps, s);
+  for (int attempt = 0; attempt < 200; ++attempt) {
+    dw = attempt == 0 ? 0.0 : next;
+    if (attempt > 0) next *= grow;
+    if (dw >= 1e40) break;
+    ipm_num_t num = S->num32 ? S->num32 : S->num;
+    k_aug_rhs<<<grid1(std::max(D.me0, D.mi0)), 256, 0, s>>>(D, dw, S->opt.gamma, S->r2, S->r4,
+                                                            S->Ds, S->P.geq, S->dcond, S->baug);
+    CKL();
+    CKR(ipm_condense(S->sym, num, S->Wv, S->sigma, S->Jv, S->dcond, dw, s));
+    CKR(ipm_factor(S->sym, num, S->info, s));
+    int hinfo = 0;
+    CK(cudaMemcpyAsync(&hinfo, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ++nfac;
+    if (hinfo == -2) return IPM_ERR_TIMEOUT;
+    if (hinfo != -1) continue;
+    // ---- solve
+    int st;
+    if (D.lifted) {
+      st = ipm_aug_solve(S->sym, num, S->Wv, S->sigma, S->Jv, S->dcond, dw, S->a, S->baug,
+                         S->dx, S->dzc, S->opt.max_refine, 1e-10, S->eta, S->steps, s);
+    } else {
+      int its = 0;
+      double rel = 0;
+      st = hykkt_cg(S->sym, num, D.me0, S->Jv, S->dcond, S->opt.gamma, S->a, S->baug,
+                    S->opt.cg_rtol, S->opt.cg_maxit > 0 ? S->opt.cg_maxit : std::max(D.me0, 1),
+                    S->dx, S->dy, S->dzH, &its, &rel, s);
+      info->cg_iters = its;
+    }
     if (st < 0 || st == IPM_ERR_TIMEOUT || st == IPM_ERR_NONFINITE) return st;
+    if (st == IPM_ERR_NOT_PD && num == S->num32) {
+      // the FP32 factor no longer preconditions K to FP64 accuracy: FP64 factor from now on,
+      // redoing this inertia search from delta_w = 0
+      ipm_num_destroy(S->num32);
+      S->num32 = nullptr;
+      attempt = -1;
+      next = S->delta_last > 0 ? std::max(1e-20, S->delta_last / 3.0) : 1e-4;
+      continue;
+    }
+    if (st == IPM_ERR_NOT_PD) continue;
+    ok = true;
+    info->precision = num == S->num32 ? 32 : 64;
+    break;
+  }
+  if (!ok) return IPM_ERR_NOT_PD;
+  if (dw > 0) S->delta_last = dw;
+  info->delta_w = dw;
+  info->n_factor = nfac;
+  SA.dw = dw;
+  if (D.lifted) {
     double eta = 0;
     int steps = 0;
     CK(cudaMemcpy(&eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost));
@@ -776,14 +802,6 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     info->refine_steps = steps;
     k_jv<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, M.J_colind, S->Jv, S->dx, S->jdx);
     CKL();
-  } else {
-    int its = 0;
-    double rel = 0;
-    int st = hykkt_cg(S->sym, S->num, D.me0, S->Jv, S->dcond, S->opt.gamma, S->a, S->baug,
-                      S->opt.cg_rtol, S->opt.cg_maxit > 0 ? S->opt.cg_maxit : std::max(D.me0, 1),
-                      S->dx, S->dy, S->dzH, &its, &rel, s);
-    if (st < 0 || st == IPM_ERR_TIMEOUT) return st;
-    info->cg_iters = its;
   }
   k_recover<<<grid1(nmax), 256, 0, s>>>(SA);
   CKL();

@@ -17,12 +17,23 @@
 namespace cipm {
 
 // ---------------------------------------------------------------- condensation
-// K = W + diag(sigma_x) + delta_w I + J^T diag(d) J.  One block per supernode writes every slot
-// of its panel as a fixed-order sum over the slot's items (sorted-pattern condensation).
+// K = W + diag(sigma_x) + delta_w I + J^T diag(d) J.  First t_p = d_row(p) J_p for every J entry
+// (one FP64 multiply per entry), then one block per supernode writes every slot of its panel as a
+// fixed-order sum over the slot's items t_p J_q (one FP64 FMA per item; on this GPU every FP64
+// warp instruction costs the same, so the per-item instruction count is what matters).
+__global__ void k_scale_jv(int nnz, const int *J_rowidx, const double *Jv, const double *d,
+                           double *t) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnz) t[p] = d[J_rowidx[p]] * Jv[p];
+}
+
+// The sums are formed in FP64 (they cancel heavily when D spans many orders of magnitude) and
+// stored as T (T = float for the FP32 factorization path).
+template <typename T>
 __global__ void k_condense(const int *sptr, const int *srow_ptr, const int64_t *lptr,
-                           const int *slot_ptr, const int2 *items, const int *J_rowidx,
-                           const int *perm, const double *Wv, const double *sigma,
-                           const double *Jv, const double *d, double dw, double *Lx) {
+                           const int *slot_ptr, const int2 *items, const int *perm,
+                           const double *Wv, const double *sigma, const double *Jv,
+                           const double *tJ, double dw, T *Lx) {
   int s = blockIdx.x;
   int f = sptr[s], w = sptr[s + 1] - f;
   int ld = srow_ptr[s + 1] - srow_ptr[s];
@@ -36,11 +47,14 @@ __global__ void k_condense(const int *sptr, const int *srow_ptr, const int64_t *
       if (r == c) v = sigma[perm[f + c]] + dw;
       for (int it = slot_ptr[slot]; it < slot_ptr[slot + 1]; ++it) {
         int2 pq = items[it];
-        if (pq.y < 0) v += Wv[pq.x];
-        else v += d[J_rowidx[pq.x]] * Jv[pq.x] * Jv[pq.y];
+        v = pq.y < 0 ? v + Wv[pq.x] : fma(tJ[pq.x], Jv[pq.y], v);
       }
+      // single precision: the factored matrix gets a relative diagonal shift of 2^-20 so that
+      // rounding K to FP32 cannot make a positive definite K indefinite; the FP64 refinement
+      // multiplies by the unshifted K, so the shift only changes the preconditioner
+      if (sizeof(T) == 4 && r == c) v += v * 9.5367431640625e-07;
     }
-    Lx[slot] = v;
+    Lx[slot] = (T)v;
   }
 }
 
@@ -67,10 +81,23 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
+// single precision: hardware rsqrt plus one Newton step
+__device__ __forceinline__ float rsqrt_newton(float d) {
+  float y = rsqrtf(d);
+  return y * fmaf(-0.5f * d * y, y, 1.5f);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
 struct FactArgs {
   const int *level_sn, *sptr, *srow_ptr, *srow, *snode;
   const int64_t *lptr, *dptr;
-  double *Lx, *Dx;
+  T *Lx, *Dx;
   int *info;
 };
 
@@ -84,10 +111,13 @@ __global__ void k_scatter_perm(const int *perm, int n, const double *y, double *
   if (k < n) x[perm[k]] = y[k];
 }
 
+// Triangular solves read factors stored as T and compute in FP64: with an FP32 factor the
+// preconditioner (L L^T)^{-1} is then applied exactly, as preconditioned CG requires.
+template <typename T>
 struct SolveArgs {
   const int *level_sn, *sptr, *srow_ptr, *srow;
   const int64_t *lptr, *dptr;
-  const double *Lx, *Dx;
+  const T *Lx, *Dx;
   double *y;
 };
 
@@ -135,8 +165,9 @@ __device__ __forceinline__ void publish() {
   __syncthreads();
 }
 
+template <typename T>
 struct FactTaskArgs {
-  FactArgs F;
+  FactArgs<T> F;
   const int4 *tasks;
   int ntasks;
   const int *upd_need;
@@ -149,16 +180,17 @@ struct FactTaskArgs {
 // L21 = A21 L11^{-T} for the block's <= 32 rows.  The diagonal block of the panel keeps K
 // (siblings read it in the same launch); row block 0 stores L11 in the separate array Dx.
 // The reciprocal pivots are computed once by one thread: FP64 division is expensive here.
-__device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm, int *s_ok) {
-  const FactArgs &A = T.F;
+template <typename V>
+__device__ void fact_panel_task(const FactTaskArgs<V> &T, int s, int rb, V *sm, int *s_ok) {
+  const FactArgs<V> &A = T.F;
   if (threadIdx.x == 0) *s_ok = spin_geq(T.C.cnt + s, T.upd_need[s], T.C);
   __syncthreads();
   if (!*s_ok) return;
   const int f = A.sptr[s], w = A.sptr[s + 1] - f;
   const int ld = A.srow_ptr[s + 1] - A.srow_ptr[s];
-  double *P = A.Lx + A.lptr[s];
-  double *sL = sm, *sR = sm + w * w;
-  __shared__ double s_inv[CIPM_SN_MAXW];
+  V *P = A.Lx + A.lptr[s];
+  V *sL = sm, *sR = sm + w * w;
+  __shared__ V s_inv[CIPM_SN_MAXW];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int t = tid; t < w * w; t += bd) {
     int k = t / w, i = t - k * w;
@@ -167,30 +199,30 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
   __syncthreads();
   for (int k = 0; k < w; ++k) {
     if (tid == 0) {
-      double d = sL[k + k * w];
+      V d = sL[k + k * w];
       if (!(d > 0.0) || !isfinite(d)) {
         atomicMin(A.info, f + k);
         d = 1.0;
       }
-      const double inv = rsqrt_newton(d);
+      const V inv = rsqrt_newton(d);
       sL[k + k * w] = d * inv;
       s_inv[k] = inv;
     }
     __syncthreads();
-    const double inv = s_inv[k];
+    const V inv = s_inv[k];
     const int nr = w - k - 1;
     for (int i = k + 1 + tid; i < w; i += bd) sL[i + k * w] *= inv;
     __syncthreads();
     // trailing update: warps own columns, lanes rows (no divisions in the loop)
     for (int jj = tid / 32; jj < nr; jj += bd / 32) {
       const int j = k + 1 + jj;
-      const double ljk = sL[j + k * w];
+      const V ljk = sL[j + k * w];
       for (int i = j + (tid & 31); i < w; i += 32) sL[i + j * w] -= sL[i + k * w] * ljk;
     }
     __syncthreads();
   }
   if (rb == 0) {
-    double *Dd = A.Dx + A.dptr[s];
+    V *Dd = A.Dx + A.dptr[s];
     for (int t = tid; t < w * w; t += bd) Dd[t] = sL[t];
     for (int k = tid; k < w; k += bd) Dd[w * w + k] = s_inv[k];
   }
@@ -206,9 +238,9 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
     // each warp owns rows r = warp, warp + nwarps, ...; lanes split the columns
     const int warp = tid >> 5, lane = tid & 31, nw = bd >> 5;
     for (int k = 0; k < w; ++k) {
-      const double inv = s_inv[k];
+      const V inv = s_inv[k];
       for (int r = warp; r < nrow; r += nw) {
-        double xk = sR[r * sw + k] * inv;
+        V xk = sR[r * sw + k] * inv;
         __syncwarp();
         for (int j = k + 1 + lane; j < w; j += 32) sR[r * sw + j] -= xk * sL[j + k * w];
         if (lane == 0) sR[r * sw + k] = xk;
@@ -225,9 +257,10 @@ __device__ void fact_panel_task(const FactTaskArgs &T, int s, int rb, double *sm
   if (tid == 0) atomicAdd(T.C.cnt + T.ns + s, 1);
 }
 
-__device__ void fact_update_task(const FactTaskArgs &T, int s, int ti, int tj, double *sm,
+template <typename V>
+__device__ void fact_update_task(const FactTaskArgs<V> &T, int s, int ti, int tj, V *sm,
                                  int *s_ok) {
-  const FactArgs &A = T.F;
+  const FactArgs<V> &A = T.F;
   const int f = A.sptr[s], w = A.sptr[s + 1] - f;
   const int rbase = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rbase;
   const int B = ld - w;
@@ -236,9 +269,9 @@ __device__ void fact_update_task(const FactTaskArgs &T, int s, int ti, int tj, d
   __syncthreads();
   if (!*s_ok) return;
   const int *rows = A.srow + rbase;
-  const double *P = A.Lx + A.lptr[s];
+  const V *P = A.Lx + A.lptr[s];
   const int sw = w + 1;
-  double *sI = sm, *sJ = sm + CIPM_RB * sw;
+  V *sI = sm, *sJ = sm + CIPM_RB * sw;
   const int i0 = w + ti * CIPM_RB, ni = min(CIPM_RB, ld - i0);
   const int j0 = w + tj * CIPM_RB, nj = min(CIPM_RB, ld - j0);
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -255,8 +288,8 @@ __device__ void fact_update_task(const FactTaskArgs &T, int s, int ti, int tj, d
     const int ii = p / nj, jj = p - (p / nj) * nj;
     const int i = i0 + ii, j = j0 + jj;
     if (i < j) continue;
-    const double *a = sI + ii * sw, *b = sJ + jj * sw;
-    double v = 0.0;
+    const V *a = sI + ii * sw, *b = sJ + jj * sw;
+    V v = 0.0;
     for (int k = 0; k < w; ++k) v += a[k] * b[k];
     const int col = rows[j], row = rows[i];
     const int ts = A.snode[col];
@@ -274,8 +307,10 @@ __device__ void fact_update_task(const FactTaskArgs &T, int s, int ti, int tj, d
   }
 }
 
-__global__ void __launch_bounds__(256) k_factor_dag(FactTaskArgs T) {
-  extern __shared__ double sm[];
+template <typename V>
+__global__ void __launch_bounds__(256) k_factor_dag(FactTaskArgs<V> T) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  V *sm = reinterpret_cast<V *>(sm_raw);
   __shared__ int s_t, s_ok;
   while (true) {
     if (threadIdx.x == 0) s_t = ld_acquire(T.C.abort_) ? T.ntasks : atomicAdd(T.C.ticket, 1);
@@ -290,8 +325,9 @@ __global__ void __launch_bounds__(256) k_factor_dag(FactTaskArgs T) {
   }
 }
 
+template <typename V>
 struct SolveTaskArgs {
-  SolveArgs A;
+  SolveArgs<V> A;
   const int *snode;
   const int *fwd_need;
   SyncCtl C;  // cnt: forward arrivals (fwd) or backward done flags (bwd)
@@ -299,11 +335,13 @@ struct SolveTaskArgs {
 };
 
 // forward solve, supernodes deepest level first: wait for every contribution into y_s
-__global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
-  extern __shared__ double sL[];
+template <typename V>
+__global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs<V> T) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *sL = reinterpret_cast<double *>(sm_raw);
   __shared__ double ys[CIPM_SN_MAXW];
   __shared__ int s_t, s_ok;
-  const SolveArgs &A = T.A;
+  const SolveArgs<V> &A = T.A;
   while (true) {
     if (threadIdx.x == 0) s_t = ld_acquire(T.C.abort_) ? T.ns : atomicAdd(T.C.ticket, 1);
     __syncthreads();
@@ -317,16 +355,16 @@ __global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
     const int f = A.sptr[s], w = A.sptr[s + 1] - f;
     const int rb = A.srow_ptr[s], ld = A.srow_ptr[s + 1] - rb;
     const int *rows = A.srow + rb;
-    const double *P = A.Lx + A.lptr[s];
-    const double *Dd = A.Dx + A.dptr[s];
-    for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q] = Dd[q];
+    const V *P = A.Lx + A.lptr[s];
+    const V *Dd = A.Dx + A.dptr[s];
+    for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q] = (double)Dd[q];
     for (int k = threadIdx.x; k < w; k += blockDim.x) ys[k] = __ldcg(A.y + f + k);
     __syncthreads();
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
-      const double *rinv = Dd + w * w;
+      const V *rinv = Dd + w * w;
       for (int k = 0; k < w; ++k) {
-        if (lane == (k & 31)) ys[k] *= rinv[k];
+        if (lane == (k & 31)) ys[k] *= (double)rinv[k];
         __syncwarp();
         const double yk = ys[k];
         for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= sL[i + k * w] * yk;
@@ -337,7 +375,7 @@ __global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
     for (int k = threadIdx.x; k < w; k += blockDim.x) A.y[f + k] = ys[k];
     for (int i = w + threadIdx.x; i < ld; i += blockDim.x) {
       double acc = 0.0;
-      for (int k = 0; k < w; ++k) acc += P[i + (int64_t)k * ld] * ys[k];
+      for (int k = 0; k < w; ++k) acc += (double)P[i + (int64_t)k * ld] * ys[k];
       atomicAdd(&A.y[rows[i]], -acc);
     }
     publish();
@@ -351,11 +389,13 @@ __global__ void __launch_bounds__(128) k_fwd_dag(SolveTaskArgs T) {
 }
 
 // backward solve, root first: wait until every supernode holding rows below s is done
-__global__ void __launch_bounds__(128) k_bwd_dag(SolveTaskArgs T) {
-  extern __shared__ double sL[];
+template <typename V>
+__global__ void __launch_bounds__(128) k_bwd_dag(SolveTaskArgs<V> T) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *sL = reinterpret_cast<double *>(sm_raw);
   __shared__ double zs[CIPM_SN_MAXW];
   __shared__ int s_t, s_ok;
-  const SolveArgs &A = T.A;
+  const SolveArgs<V> &A = T.A;
   while (true) {
     if (threadIdx.x == 0) s_t = ld_acquire(T.C.abort_) ? T.ns : atomicAdd(T.C.ticket, 1);
     __syncthreads();
@@ -375,21 +415,21 @@ __global__ void __launch_bounds__(128) k_bwd_dag(SolveTaskArgs T) {
     }
     __syncthreads();
     if (!s_ok) continue;
-    const double *P = A.Lx + A.lptr[s];
-    const double *Dd = A.Dx + A.dptr[s];
-    for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q] = Dd[q];
+    const V *P = A.Lx + A.lptr[s];
+    const V *Dd = A.Dx + A.dptr[s];
+    for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q] = (double)Dd[q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = warp; k < w; k += nw) {
       double acc = 0.0;
-      for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * __ldcg(A.y + rows[i]);
+      for (int i = w + lane; i < ld; i += 32) acc += (double)P[i + (int64_t)k * ld] * __ldcg(A.y + rows[i]);
       acc = warp_sum(acc);
       if (lane == 0) zs[k] = __ldcg(A.y + f + k) - acc;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-      const double *rinv = Dd + w * w;
+      const V *rinv = Dd + w * w;
       for (int k = w - 1; k >= 0; --k) {
-        if (lane == (k & 31)) zs[k] *= rinv[k];
+        if (lane == (k & 31)) zs[k] *= (double)rinv[k];
         __syncwarp();
         const double xk = zs[k];
         for (int j = lane; j < k; j += 32) zs[j] -= sL[k + j * w] * xk;
@@ -617,20 +657,27 @@ __global__ void k_info_fix(int *info, const int *status) {
 
 using namespace cipm;
 
+template <typename V>
+static int set_smem_limits_t() {
+  const int big = 64 * 1024;
+  CK(cudaFuncSetAttribute(k_factor_dag<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_fwd_dag<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_bwd_dag<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return IPM_OK;
+}
+
 static int set_smem_limits() {
   static bool done = false;
   if (done) return IPM_OK;
-  const int big = 64 * 1024;
-  CK(cudaFuncSetAttribute(k_factor_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_fwd_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_bwd_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CKR(set_smem_limits_t<double>());
+  CKR(set_smem_limits_t<float>());
   done = true;
   return IPM_OK;
 }
 
 extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
-  if (!S || !out || precision != 64) {
-    set_error_msg("ipm_num_create: bad argument (precision must be 64)");
+  if (!S || !out || (precision != 64 && precision != 32)) {
+    set_error_msg("ipm_num_create: bad argument (precision must be 64 or 32)");
     return IPM_ERR_BAD_ARG;
   }
   *out = nullptr;
@@ -638,12 +685,20 @@ extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
   ipm_num_t N = new ipm_num_s();
   N->sym = S;
   N->precision = precision;
-  int rc = dev_alloc(&N->Lx, S->panel_len);
-  if (rc == IPM_OK) rc = dev_alloc(&N->Dx, S->diag_len);
+  const size_t es = precision == 64 ? sizeof(double) : sizeof(float);
+  int rc = IPM_OK;
+  auto bytes = [&](void **p, int64_t count) {
+    if (rc == IPM_OK && cudaMalloc(p, es * (size_t)std::max<int64_t>(count, 1)) != cudaSuccess)
+      rc = IPM_ERR_OOM;
+  };
+  bytes(&N->Lx, S->panel_len);
+  bytes(&N->Dx, S->diag_len);
+  if (rc == IPM_OK && cudaMalloc(&N->tJ, sizeof(double) * (size_t)std::max(S->nnzJ, 1)) != cudaSuccess)
+    rc = IPM_ERR_OOM;
   if (rc == IPM_OK) rc = dev_alloc(&N->sync, 4 * (int64_t)S->nsuper + 16);
   if (rc == IPM_OK && cudaMemset(N->sync, 0, sizeof(int) * (4 * (size_t)S->nsuper + 16)) != cudaSuccess)
     rc = IPM_ERR_CUDA;
-  for (int k = 0; k < 8 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vn[k], S->n);
+  for (int k = 0; k < 12 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vn[k], S->n);
   for (int k = 0; k < 6 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vm[k], S->m > 0 ? S->m : 1);
   if (rc == IPM_OK) rc = dev_alloc(&N->scal, 64 + DOT_BLOCKS);
   if (rc == IPM_OK && cudaMallocHost((void **)&N->h_scal, sizeof(double) * 64) != cudaSuccess)
@@ -660,6 +715,7 @@ extern "C" void ipm_num_destroy(ipm_num_t N) {
   if (!N) return;
   if (N->Lx) cudaFree(N->Lx);
   if (N->Dx) cudaFree(N->Dx);
+  if (N->tJ) cudaFree(N->tJ);
   if (N->sync) cudaFree(N->sync);
   for (auto *p : N->vn)
     if (p) cudaFree(p);
@@ -670,18 +726,32 @@ extern "C" void ipm_num_destroy(ipm_num_t N) {
   delete N;
 }
 
+template <typename V>
+static int copy_to_double(std::vector<double> &out, const void *src, int64_t count) {
+  std::vector<V> tmp(count);
+  if (count) CK(cudaMemcpy(tmp.data(), src, sizeof(V) * count, cudaMemcpyDeviceToHost));
+  out.assign(tmp.begin(), tmp.end());
+  return IPM_OK;
+}
+
 extern "C" int ipm_num_export(ipm_num_t N, double *Lx_host) {
   if (!N || !Lx_host) return IPM_ERR_BAD_ARG;
   ipm_sym_t S = N->sym;
   CK(cudaDeviceSynchronize());
-  CK(cudaMemcpy(Lx_host, N->Lx, sizeof(double) * S->panel_len, cudaMemcpyDeviceToHost));
+  std::vector<double> L, D;
+  if (N->precision == 64) {
+    CKR(copy_to_double<double>(L, N->Lx, S->panel_len));
+    CKR(copy_to_double<double>(D, N->Dx, S->diag_len));
+  } else {
+    CKR(copy_to_double<float>(L, N->Lx, S->panel_len));
+    CKR(copy_to_double<float>(D, N->Dx, S->diag_len));
+  }
+  std::copy(L.begin(), L.end(), Lx_host);
   if (N->factored) {
     // the factor keeps L11 in a separate array: put it into the panels' diagonal blocks
     const int ns = S->nsuper;
-    std::vector<double> D(S->diag_len);
     std::vector<int64_t> lp(ns + 1), dp(ns + 1);
     std::vector<int> sp(ns + 1), rp(ns + 1);
-    CK(cudaMemcpy(D.data(), N->Dx, sizeof(double) * S->diag_len, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(lp.data(), S->lptr, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(dp.data(), S->dptr, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(sp.data(), S->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost));
@@ -693,6 +763,13 @@ extern "C" int ipm_num_export(ipm_num_t N, double *Lx_host) {
           Lx_host[lp[s] + (int64_t)k * ld + i] = i >= k ? D[dp[s] + (int64_t)k * w + i] : 0.0;
     }
   }
+  return IPM_OK;
+}
+
+extern "C" int ipm_num_info(ipm_num_t N, int *precision, int *last_pcg_iters) {
+  if (!N) return IPM_ERR_BAD_ARG;
+  if (precision) *precision = N->precision;
+  if (last_pcg_iters) *last_pcg_iters = N->last_pcg_iters;
   return IPM_OK;
 }
 
@@ -724,19 +801,37 @@ static int device_status(ipm_num_t N) {
   return st;
 }
 
+template <typename V>
+static int condense_t(ipm_sym_t S, ipm_num_t N, const double *W_val, const double *sigma_x,
+                      const double *J_val, const double *d_row, double delta_w, cudaStream_t s) {
+  double *tJ = (double *)N->tJ;
+  if (S->nnzJ > 0) {
+    k_scale_jv<<<grid_for(S->nnzJ, 256), 256, 0, s>>>(S->nnzJ, S->J_rowidx, J_val, d_row, tJ);
+    count_launches(1);
+    CKL();
+  }
+  k_condense<V><<<S->nsuper, 128, 0, s>>>(S->sptr, S->srow_ptr, S->lptr, S->slot_ptr, S->items,
+                                          S->perm, W_val, sigma_x, J_val, tJ, delta_w,
+                                          (V *)N->Lx);
+  count_launches(1);
+  CKL();
+  return IPM_OK;
+}
+
 extern "C" int ipm_condense(ipm_sym_t S, ipm_num_t N, const double *W_val, const double *sigma_x,
                             const double *J_val, const double *d_row, double delta_w,
                             cudaStream_t s) {
   if (!S || !N || N->sym != S || !sigma_x || (S->nnzW && !W_val) || (S->nnzJ && (!J_val || !d_row)))
     return IPM_ERR_BAD_ARG;
+  N->cW = W_val;
+  N->cSig = sigma_x;
+  N->cJ = J_val;
+  N->cD = d_row;
+  N->cDw = delta_w;
   if (S->nsuper == 0) return IPM_OK;
   N->factored = false;
-  k_condense<<<S->nsuper, 128, 0, s>>>(S->sptr, S->srow_ptr, S->lptr, S->slot_ptr, S->items,
-                                       S->J_rowidx, S->perm, W_val, sigma_x, J_val, d_row,
-                                       delta_w, N->Lx);
-  count_launches(1);
-  CKL();
-  return IPM_OK;
+  return N->precision == 64 ? condense_t<double>(S, N, W_val, sigma_x, J_val, d_row, delta_w, s)
+                            : condense_t<float>(S, N, W_val, sigma_x, J_val, d_row, delta_w, s);
 }
 
 static int persistent_grid(const void *kernel, int threads, size_t smem) {
@@ -759,6 +854,27 @@ static SyncCtl sync_ctl(ipm_sym_t S, ipm_num_t N, int region, int ticket) {
   return SyncCtl{N->sync + region * ns, tail + ticket, tail + 3, tail + 4};
 }
 
+template <typename V>
+static int factor_t(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s) {
+  FactTaskArgs<V> T;
+  T.F = FactArgs<V>{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->snode, S->lptr, S->dptr,
+                    (V *)N->Lx, (V *)N->Dx, d_info};
+  T.tasks = S->ftasks;
+  T.ntasks = S->nftasks;
+  T.upd_need = S->upd_need;
+  T.C = sync_ctl(S, N, 0, 0);
+  T.ns = S->nsuper;
+  const int w = S->max_w;
+  size_t sm = sizeof(V) * std::max((size_t)w * w + (size_t)CIPM_RB * (w + 1),
+                                   2 * (size_t)CIPM_RB * (w + 1));
+  if (T.ntasks > 0) {
+    k_factor_dag<V><<<persistent_grid((const void *)k_factor_dag<V>, 256, sm), 256, sm, s>>>(T);
+    count_launches(1);
+    CKL();
+  }
+  return IPM_OK;
+}
+
 extern "C" int ipm_factor(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s) {
   if (!S || !N || N->sym != S || !d_info) return IPM_ERR_BAD_ARG;
   const int ns = S->nsuper;
@@ -768,22 +884,7 @@ extern "C" int ipm_factor(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s)
   k_info_set<<<1, 1, 0, s>>>(d_info);
   count_launches(1);
   CKL();
-  FactTaskArgs T;
-  T.F = FactArgs{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->snode, S->lptr, S->dptr,
-                 N->Lx, N->Dx, d_info};
-  T.tasks = S->ftasks;
-  T.ntasks = S->nftasks;
-  T.upd_need = S->upd_need;
-  T.C = sync_ctl(S, N, 0, 0);
-  T.ns = ns;
-  const int w = S->max_w;
-  size_t sm = sizeof(double) * std::max((size_t)w * w + (size_t)CIPM_RB * (w + 1),
-                                        2 * (size_t)CIPM_RB * (w + 1));
-  if (T.ntasks > 0) {
-    k_factor_dag<<<persistent_grid((const void *)k_factor_dag, 256, sm), 256, sm, s>>>(T);
-    count_launches(1);
-    CKL();
-  }
+  CKR(N->precision == 64 ? factor_t<double>(S, N, d_info, s) : factor_t<float>(S, N, d_info, s));
   k_info_fix<<<1, 1, 0, s>>>(d_info, N->sync + 4 * ns + 4);
   count_launches(1);
   CKL();
@@ -791,46 +892,230 @@ extern "C" int ipm_factor(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s)
   return IPM_OK;
 }
 
-// y (permuted, length n) <- L^{-T} L^{-1} y in place
-static int solve_permuted(ipm_sym_t S, ipm_num_t N, double *y, cudaStream_t s) {
-  const int ns = S->nsuper;
-  if (ns == 0) return IPM_OK;
-  CK(cudaMemsetAsync(N->sync + 2 * ns, 0, sizeof(int) * 2 * ns, s));
-  CK(cudaMemsetAsync(N->sync + 4 * ns + 1, 0, sizeof(int) * 2, s));
-  SolveTaskArgs T;
-  T.A = SolveArgs{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr, N->Lx, N->Dx, y};
+// y (permuted, length n, value type V) <- L^{-T} L^{-1} y in place, counters in C_fwd / C_bwd
+template <typename V>
+static int solve_permuted_t(ipm_sym_t S, ipm_num_t N, double *y, SyncCtl C_fwd, SyncCtl C_bwd,
+                            cudaStream_t s) {
+  SolveTaskArgs<V> T;
+  T.A = SolveArgs<V>{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr,
+                     (const V *)N->Lx, (const V *)N->Dx, y};
   T.snode = S->snode;
   T.fwd_need = S->fwd_need;
-  T.ns = ns;
+  T.ns = S->nsuper;
   size_t sm = sizeof(double) * (size_t)S->max_w * S->max_w;
-  T.C = sync_ctl(S, N, 2, 1);
-  k_fwd_dag<<<persistent_grid((const void *)k_fwd_dag, 128, sm), 128, sm, s>>>(T);
+  T.C = C_fwd;
+  k_fwd_dag<V><<<persistent_grid((const void *)k_fwd_dag<V>, 128, sm), 128, sm, s>>>(T);
   count_launches(1);
   CKL();
-  T.C = sync_ctl(S, N, 3, 2);
-  k_bwd_dag<<<persistent_grid((const void *)k_bwd_dag, 128, sm), 128, sm, s>>>(T);
+  T.C = C_bwd;
+  k_bwd_dag<V><<<persistent_grid((const void *)k_bwd_dag<V>, 128, sm), 128, sm, s>>>(T);
   count_launches(1);
   CKL();
   return IPM_OK;
 }
 
-// x = K^{-1} b (b, x of length n in the original order; may alias)
-static int solve_full(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStream_t s) {
-  double *y = N->vn[7];
+// x = (L L^T)^{-1} b with the factor, any precision (b, x: double, original order; may alias);
+// y_work: n doubles of scratch; cnt: 2 nsuper counters, tail: tickets (2), abort, status
+template <typename V>
+static int factor_solve_t(ipm_sym_t S, ipm_num_t N, const double *b, double *x, void *y_work,
+                          int *cnt, int *tail, cudaStream_t s) {
+  const int ns = S->nsuper;
+  double *y = (double *)y_work;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)ns, s));
+  CK(cudaMemsetAsync(tail, 0, sizeof(int) * 2, s));
   k_gather_perm<<<grid_for(S->n, 256), 256, 0, s>>>(S->perm, S->n, b, y);
   count_launches(1);
   CKL();
-  CKR(solve_permuted(S, N, y, s));
+  if (ns > 0)
+    CKR(solve_permuted_t<V>(S, N, y, SyncCtl{cnt, tail + 0, tail + 2, tail + 3},
+                            SyncCtl{cnt + ns, tail + 1, tail + 2, tail + 3}, s));
   k_scatter_perm<<<grid_for(S->n, 256), 256, 0, s>>>(S->perm, S->n, y, x);
   count_launches(1);
   CKL();
   return IPM_OK;
 }
 
+// x = K^{-1} b with the handle's factor and workspace
+static int solve_full(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStream_t s) {
+  const int ns = S->nsuper;
+  int *cnt = N->sync + 2 * ns, *tail = N->sync + 4 * ns + 1;
+  return N->precision == 64 ? factor_solve_t<double>(S, N, b, x, N->vn[7], cnt, tail, s)
+                            : factor_solve_t<float>(S, N, b, x, N->vn[7], cnt, tail, s);
+}
+
 extern "C" int ipm_solve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, int nrhs,
                          cudaStream_t s) {
   if (!S || !N || N->sym != S || !b || !x || nrhs != 1) return IPM_ERR_BAD_ARG;
   return solve_full(S, N, b, x, s);
+}
+
+// --- K x = b solved to FP64 accuracy with an FP32 factor: conjugate gradients in FP64 on K
+// (K p = (W + Sigma_x + delta_w I) p + J^T (d o (J p)) from the condensation inputs),
+// preconditioned by the FP32 factor (L L^T)^{-1}.
+__global__ void k_kmat_rows(int m, const int *J_rowptr, const int *J_colind, const double *Jv,
+                            const double *d, const double *p, double *t) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  double acc = 0.0;
+  for (int q = J_rowptr[r]; q < J_rowptr[r + 1]; ++q) acc += Jv[q] * p[J_colind[q]];
+  t[r] = d[r] * acc;
+}
+__global__ void k_kmat_cols(int n, const int *W_rowptr, const int *W_colind, const int *W_rowidx,
+                            const int *WT_ptr, const int *WT_ent, const double *Wv,
+                            const double *sigma, double dw, const int *JT_ptr, const int *JT_ent,
+                            const int *J_rowidx, const double *Jv, const double *t,
+                            const double *p, double *out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = (sigma[j] + dw) * p[j];
+  for (int q = W_rowptr[j]; q < W_rowptr[j + 1]; ++q) acc += Wv[q] * p[W_colind[q]];
+  for (int u = WT_ptr[j]; u < WT_ptr[j + 1]; ++u) {
+    int e = WT_ent[u];
+    int r = W_rowidx[e];
+    if (r != j) acc += Wv[e] * p[r];
+  }
+  for (int u = JT_ptr[j]; u < JT_ptr[j + 1]; ++u) {
+    int q = JT_ent[u];
+    acc += Jv[q] * t[J_rowidx[q]];
+  }
+  out[j] = acc;
+}
+__global__ void k_pcg_xr(int n, const double *sc, const double *p, const double *Ap, double *x,
+                         double *r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double alpha = sc[0] / sc[1];  // rz / pAp
+  x[i] += alpha * p[i];
+  r[i] -= alpha * Ap[i];
+}
+__global__ void k_pcg_p(int n, const double *sc, const double *z, double *p) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] = z[i] + (sc[2] / sc[0]) * p[i];  // beta = rz_new / rz
+}
+
+__global__ void k_absmax(int n, const double *v, double *out) {
+  __shared__ double sh[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  block_max_to(out, i < n ? fabs(v[i]) : 0.0, sh);
+}
+
+// max over rows of the row sums of |W + Sigma_x + delta_w I| + |J|^T |d| |J| (an upper bound of
+// ||K||_inf used by the normwise stopping test)
+__global__ void k_knorm(int n, const int *W_rowptr, const int *W_colind, const int *W_rowidx,
+                        const int *WT_ptr, const int *WT_ent, const double *Wv,
+                        const double *sigma, double dw, const int *JT_ptr, const int *JT_ent,
+                        const int *J_rowidx, const int *J_rowptr, const double *Jv,
+                        const double *d, double *out) {
+  __shared__ double sh[32];
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (j < n) {
+    double diag = sigma[j] + dw;
+    for (int q = W_rowptr[j]; q < W_rowptr[j + 1]; ++q) {
+      if (W_colind[q] == j) diag += Wv[q];
+      else acc += fabs(Wv[q]);
+    }
+    for (int u = WT_ptr[j]; u < WT_ptr[j + 1]; ++u) {
+      int e = WT_ent[u];
+      if (W_rowidx[e] != j) acc += fabs(Wv[e]);
+    }
+    acc += fabs(diag);
+    for (int u = JT_ptr[j]; u < JT_ptr[j + 1]; ++u) {
+      int q = JT_ent[u];
+      int r = J_rowidx[q];
+      double rs = 0.0;
+      for (int t = J_rowptr[r]; t < J_rowptr[r + 1]; ++t) rs += fabs(Jv[t]);
+      acc += fabs(d[r]) * fabs(Jv[q]) * rs;
+    }
+  }
+  block_max_to(out, acc, sh);
+}
+
+static int kmat(ipm_sym_t S, ipm_num_t N, const double *p, double *out, cudaStream_t s) {
+  double *t = N->vm[5];
+  if (S->m > 0) {
+    k_kmat_rows<<<grid_for(S->m, 256), 256, 0, s>>>(S->m, S->J_rowptr, S->J_colind, N->cJ, N->cD, p,
+                                                    t);
+    count_launches(1);
+  }
+  k_kmat_cols<<<grid_for(S->n, 256), 256, 0, s>>>(S->n, S->W_rowptr, S->W_colind, S->W_rowidx,
+                                                  S->WT_ptr, S->WT_ent, N->cW, N->cSig, N->cDw,
+                                                  S->JT_ptr, S->JT_ent, S->J_rowidx, N->cJ, t, p,
+                                                  out);
+  count_launches(1);
+  CKL();
+  return IPM_OK;
+}
+
+// FP64 accuracy from the factor of any precision; FP64 factors solve directly
+static int ksolve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStream_t s) {
+  if (N->precision == 64) return solve_full(S, N, b, x, s);
+  const int n = S->n;
+  double *r = N->vn[8], *z = N->vn[9], *p = N->vn[10], *Ap = N->vn[11];
+  double *sc = N->scal + 8, *partial = N->scal + 64;
+  CKR(dot(b, b, n, partial, sc + 4, s));
+  CK(cudaMemcpyAsync(N->h_scal + 4, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+  // ||K||_inf bound, ||b||_inf for the normwise backward error of K x = b
+  CK(cudaMemsetAsync(sc + 5, 0, sizeof(double) * 3, s));
+  k_knorm<<<grid_for(n, 256), 256, 0, s>>>(n, S->W_rowptr, S->W_colind, S->W_rowidx, S->WT_ptr,
+                                           S->WT_ent, N->cW, N->cSig, N->cDw, S->JT_ptr,
+                                           S->JT_ent, S->J_rowidx, S->J_rowptr, N->cJ, N->cD,
+                                           sc + 5);
+  count_launches(1);
+  k_absmax<<<grid_for(n, 256), 256, 0, s>>>(n, b, sc + 6);
+  count_launches(1);
+  CKL();
+  CKR(solve_full(S, N, b, x, s));  // x0 = M^{-1} b
+  CKR(kmat(S, N, x, Ap, s));
+  CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, -1.0, Ap, r);
+  count_launches(1);
+  CKR(solve_full(S, N, r, z, s));
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CKR(dot(r, z, n, partial, sc + 0, s));
+  CK(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(N->h_scal[4]);
+  int it = 0;
+  bool converged = false;
+  for (; it < 100; ++it) {
+    CKR(dot(r, r, n, partial, sc + 3, s));
+    CK(cudaMemsetAsync(sc + 7, 0, sizeof(double) * 2, s));
+    k_absmax<<<grid_for(n, 256), 256, 0, s>>>(n, r, sc + 7);
+    k_absmax<<<grid_for(n, 256), 256, 0, s>>>(n, x, sc + 8);
+    count_launches(2);
+    CK(cudaMemcpyAsync(N->h_scal + 3, sc + 3, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double rn = std::sqrt(N->h_scal[3]);
+    if (!std::isfinite(rn)) return IPM_ERR_NONFINITE;
+    // stop at a relative residual of 1e-14 or a normwise backward error of K x = b of 1e-14
+    const double knorm = N->h_scal[5], binf = N->h_scal[6], rinf = N->h_scal[7], xinf = N->h_scal[8];
+    if (rn <= 1e-14 * bnorm || rinf <= 1e-14 * (knorm * xinf + binf)) {
+      converged = true;
+      break;
+    }
+    CKR(kmat(S, N, p, Ap, s));
+    CKR(dot(p, Ap, n, partial, sc + 1, s));
+    CK(cudaMemcpyAsync(N->h_scal + 1, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(N->h_scal[1] > 0.0)) {  // negative curvature: K is not positive definite
+      N->last_pcg_iters += it;
+      return IPM_ERR_NOT_PD;
+    }
+    k_pcg_xr<<<grid_for(n, 256), 256, 0, s>>>(n, sc, p, Ap, x, r);
+    count_launches(1);
+    CKR(solve_full(S, N, r, z, s));
+    CKR(dot(r, z, n, partial, sc + 2, s));
+    k_pcg_p<<<grid_for(n, 256), 256, 0, s>>>(n, sc, z, p);
+    count_launches(1);
+    k_copy_scalar<<<1, 1, 0, s>>>(sc + 2, sc + 0);
+    count_launches(1);
+    CKL();
+  }
+  N->last_pcg_iters += it;
+  // an FP32 factor that does not precondition K to FP64 accuracy within the iteration limit is
+  // reported like a failed factorization: the caller regularizes more (larger delta_w)
+  return converged ? IPM_OK : IPM_ERR_NOT_PD;
 }
 
 // condensed solve of the augmented system: dx = K^{-1}(ra + J^T (d o rb)), dz = d o (J dx - rb)
@@ -843,7 +1128,7 @@ static int aug_condensed(ipm_sym_t S, ipm_num_t N, const double *Jv, const doubl
                                               m, ra, 1.0, t);
   count_launches(1);
   CKL();
-  CKR(solve_full(S, N, t, dx, s));
+  CKR(ksolve(S, N, t, dx, s));  // (IPM_ERR_NOT_PD on an FP32 factor that fails to precondition)
   if (m > 0) {
     k_recover_dz<<<grid_for(m, 256), 256, 0, s>>>(0, m, S->J_rowptr, S->J_colind, Jv, d, dx, rb,
                                                   dz);
@@ -862,6 +1147,7 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
       max_refine < 0)
     return IPM_ERR_BAD_ARG;
   const int n = S->n, m = S->m;
+  N->last_pcg_iters = 0;
   CKR(aug_condensed(S, N, J_val, d_row, a, b, dx, dz, s));
   AugArgs A;
   A.n = n;
@@ -946,7 +1232,8 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
                                               b, 0, m, a, 1.0, rhs1);
   count_launches(1);
   CKL();
-  CKR(solve_full(S, N, rhs1, w, s));
+  N->last_pcg_iters = 0;
+  CKR(ksolve(S, N, rhs1, w, s));
   int iters = 0;
   double relres = 0.0;
   int rc = IPM_OK;
@@ -969,9 +1256,9 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
                                                   nullptr, p, 0, m_e, nullptr, 1.0, u);
       count_launches(1);
       CKL();
-      CKR(solve_full(S, N, u, u, s));
-      k_j_apply<<<grid_for(m_e, 256), 256, 0, s>>>(0, m_e, S->J_rowptr, S->J_colind, J_val, u,
-                                                   nullptr, Sp);
+      CKR(ksolve(S, N, u, N->vn[6], s));
+      k_j_apply<<<grid_for(m_e, 256), 256, 0, s>>>(0, m_e, S->J_rowptr, S->J_colind, J_val,
+                                                   N->vn[6], nullptr, Sp);
       count_launches(1);
       CKL();
       CKR(dot(p, Sp, m_e, partial, sc + 1, s));
@@ -999,7 +1286,7 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
                                                 nullptr, dy, 0, m_e, rhs1, -1.0, u);
     count_launches(1);
     CKL();
-    CKR(solve_full(S, N, u, dx, s));
+    CKR(ksolve(S, N, u, dx, s));
   } else {
     CK(cudaMemcpyAsync(dx, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
@@ -1058,33 +1345,13 @@ extern "C" int ipm_solve_noalloc(ipm_sym_t S, ipm_num_t N, const double *b, doub
     }
     base = g_noalloc_addr[dev];
   }
-  const int n = S->n, ns = S->nsuper;
   double *y = (double *)base;
   int *cnt = (int *)(y + CIPM_NOALLOC_MAX_N);  // [0,ns) forward, [ns,2ns) backward, then tail
   int *tail = cnt + 2 * CIPM_NOALLOC_MAX_N;     // tickets (2), abort, status
   // counters, tickets, abort flag and status must start at zero on every call
-  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (size_t)ns, s));
   CK(cudaMemsetAsync(tail, 0, sizeof(int) * 8, s));
-  k_gather_perm<<<grid_for(n, 256), 256, 0, s>>>(S->perm, n, b, y);
-  count_launches(1);
-  CKL();
-  SolveTaskArgs T;
-  T.A = SolveArgs{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr, N->Lx, N->Dx, y};
-  T.snode = S->snode;
-  T.fwd_need = S->fwd_need;
-  T.ns = ns;
-  size_t sm = sizeof(double) * (size_t)S->max_w * S->max_w;
-  T.C = SyncCtl{cnt, tail + 0, tail + 2, tail + 3};
-  k_fwd_dag<<<persistent_grid((const void *)k_fwd_dag, 128, sm), 128, sm, s>>>(T);
-  count_launches(1);
-  CKL();
-  T.C = SyncCtl{cnt + ns, tail + 1, tail + 2, tail + 3};
-  k_bwd_dag<<<persistent_grid((const void *)k_bwd_dag, 128, sm), 128, sm, s>>>(T);
-  count_launches(1);
-  CKL();
-  k_scatter_perm<<<grid_for(n, 256), 256, 0, s>>>(S->perm, n, y, x);
-  count_launches(1);
-  CKL();
+  CKR(N->precision == 64 ? factor_solve_t<double>(S, N, b, x, y, cnt, tail, s)
+                         : factor_solve_t<float>(S, N, b, x, y, cnt, tail, s));
   if (d_status) {
     k_copy_status<<<1, 1, 0, s>>>(tail + 3, d_status);
     count_launches(1);
