@@ -36,6 +36,8 @@ enum {
   IPM_ERR_NONFINITE = 3,    /* NaN/Inf in inputs or results */
   IPM_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
   IPM_ERR_RESTORATION = 5,  /* line search failed: feasibility restoration needed */
+  IPM_ERR_INERTIA = 6,      /* inertia correction failed: delta_w reached 1e40 */
+  IPM_ERR_MAXITER = 7,      /* iteration limit reached before convergence (batched solves) */
   IPM_ERR_BAD_ARG = -1,
   IPM_ERR_OOM = -2,
   IPM_ERR_CUDA = -3
@@ -269,7 +271,8 @@ typedef struct {
 
 typedef struct {
   int k;            /* iteration index */
-  int status;       /* 0 running, 1 converged, else an IPM_ERR_* code */
+  int status;       /* 0 running, 1 converged, else an IPM_ERR_* code among IPM_ERR_INERTIA,
+                       IPM_ERR_RESTORATION, IPM_ERR_TIMEOUT and IPM_ERR_NONFINITE */
   double mu, kkt_err, alpha, delta_w, obj, eta, theta;
   int n_factor, cg_iters, refine_steps, ls_steps;
   int precision;    /* factorization precision used by this iteration (32 or 64) */
@@ -292,6 +295,48 @@ int ipm_step(ipm_state_t state, ipm_iter_info *host_info);
 /* Copies x [n] to a HOST buffer (NULL skipped) and the unscaled objective f(x) to *obj (HOST). */
 int ipm_state_export(ipm_state_t state, double *x, double *obj);
 void ipm_state_destroy(ipm_state_t state);
+
+/* ---------------------------------------------------------------- batched interior-point solves
+ * Many OPF instances advanced together (LiftedKKT, FP64): the batched form of the method.
+ * Instances whose model patterns (J and lower W) are equal share one symbolic analysis (the
+ * paper reuses the analysis of a pattern across iterations, Section 5); instances may have
+ * different sizes.  Each launch of the condensation, the sync-free factorization and the
+ * triangular solves covers every instance that is in that step; the per-instance control of the
+ * algorithm of ipm_step (convergence test, barrier update, inertia correction, refinement,
+ * fraction to the boundary, filter line search) runs on the device, so a sweep of the method is
+ * one CUDA graph and every instance follows the single-problem iteration exactly. */
+typedef struct ipm_batch_s *ipm_batch_t;
+
+/* Creates the batch over count model handles (HOST array of handles that must outlive the batch;
+ * the same handle may not appear twice).  opt: kkt must be 0 (LiftedKKT), precision 0 or 64; the
+ * remaining fields as in ipm_options.  Runs one ipm_symbolic per distinct pattern, allocates one
+ * device pool for every instance's iterate, factor and workspace, and sets every instance to the
+ * starting point of ipm_state_create.  Synchronizes.  IPM_ERR_BAD_ARG on a bad argument,
+ * IPM_ERR_OOM when the pool does not fit. */
+int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_options *opt,
+                     cudaStream_t stream, ipm_batch_t *out);
+/* Number of distinct patterns, bytes of the instance pool, kernel launches per sweep (after the
+ * first ipm_batch_run).  Pointers may be NULL. */
+int ipm_batch_info(ipm_batch_t batch, int *npatterns, int64_t *device_bytes,
+                   int *launches_per_sweep);
+/* Puts every instance back at its starting point (as after ipm_batch_create).  Stream-ordered. */
+int ipm_batch_reset(ipm_batch_t batch);
+/* Runs sweeps until every instance has converged (status 1) or stopped: IPM_ERR_INERTIA,
+ * IPM_ERR_RESTORATION, IPM_ERR_NONFINITE, IPM_ERR_TIMEOUT, or IPM_ERR_MAXITER after max_iter
+ * iterations (or when max_sweeps sweeps end first).  use_graph != 0 replays one captured CUDA
+ * graph per sweep, else the sweep's kernels are launched one by one.  Reads one int back per
+ * sweep.  Synchronizes. */
+int ipm_batch_run(ipm_batch_t batch, int max_iter, int max_sweeps, int use_graph);
+/* Per-instance results into HOST arrays [count] (any may be NULL): status, iterations, objective
+ * f(x) at the last evaluated iterate, scaled KKT error there, factorizations, backtracking
+ * steps.  Synchronizes. */
+int ipm_batch_results(ipm_batch_t batch, int *status, int *iters, double *obj, double *kkt_err,
+                      int *n_factor, int *ls_steps);
+/* Copies instance i's x [n] into a HOST buffer.  Synchronizes. */
+int ipm_batch_export(ipm_batch_t batch, int i, double *x);
+/* Sweeps run since creation or the last reset. */
+int ipm_batch_sweeps(ipm_batch_t batch);
+void ipm_batch_destroy(ipm_batch_t batch);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ from .build import LIB
 _lib = None
 
 IPM_OK, IPM_ERR_NOT_PD, IPM_ERR_CG_MAXIT, IPM_ERR_NONFINITE = 0, 1, 2, 3
-IPM_ERR_TIMEOUT, IPM_ERR_RESTORATION = 4, 5
+IPM_ERR_TIMEOUT, IPM_ERR_RESTORATION, IPM_ERR_INERTIA, IPM_ERR_MAXITER = 4, 5, 6, 7
 
 P = ctypes.c_void_p
 I = ctypes.c_int
@@ -53,6 +53,14 @@ _SIGS = {
     "ipm_step": (I, [P, P]),
     "ipm_state_export": (I, [P, P, P]),
     "ipm_state_destroy": (None, [P]),
+    "ipm_batch_create": (I, [I, P, P, P, P]),
+    "ipm_batch_info": (I, [P, P, P, P]),
+    "ipm_batch_reset": (I, [P]),
+    "ipm_batch_run": (I, [P, I, I, I]),
+    "ipm_batch_results": (I, [P, P, P, P, P, P, P]),
+    "ipm_batch_export": (I, [P, I, P]),
+    "ipm_batch_sweeps": (I, [P]),
+    "ipm_batch_destroy": (None, [P]),
 }
 
 
@@ -340,3 +348,54 @@ def ipm_solve_opf(opf, max_iter=3000, **opts):
             break
     iters = hist[-1]["k"]
     return dict(status=status, iters=iters, obj=st.objective(), x=st.x(), history=hist, state=st)
+
+
+class Batch:
+    """Batched LiftedKKT interior-point solves over ``Opf`` handles (ipm_batch_*): one symbolic
+    analysis per distinct pattern, every instance advanced by the same launches."""
+
+    def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, stream=None):
+        self.opfs = list(opfs)
+        arr = (ctypes.c_void_p * len(self.opfs))(*[o.h.value for o in self.opfs])
+        o = IpmOptions(0, tol, 0.0, tau, mu0, 1e-10, max_refine, 0, 64)
+        h = ctypes.c_void_p()
+        _check(lib().ipm_batch_create(len(self.opfs), arr, ctypes.byref(o), _stream(stream),
+                                      ctypes.byref(h)), "ipm_batch_create")
+        self.h = h
+        self.count = len(self.opfs)
+
+    def info(self):
+        npat, nbytes, nl = I(), I64(), I()
+        _check(lib().ipm_batch_info(self.h, ctypes.byref(npat), ctypes.byref(nbytes),
+                                    ctypes.byref(nl)), "ipm_batch_info")
+        return dict(patterns=npat.value, device_bytes=nbytes.value, launches_per_sweep=nl.value)
+
+    def reset(self):
+        _check(lib().ipm_batch_reset(self.h), "ipm_batch_reset")
+
+    def run(self, max_iter=3000, max_sweeps=None, use_graph=True):
+        ms = 4 * max_iter + 100 if max_sweeps is None else max_sweeps
+        _check(lib().ipm_batch_run(self.h, int(max_iter), int(ms), int(bool(use_graph))),
+               "ipm_batch_run")
+
+    def results(self):
+        n = self.count
+        st, it, nf, ls = (np.zeros(n, np.int32) for _ in range(4))
+        obj, err = np.zeros(n), np.zeros(n)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_batch_results(self.h, p(st), p(it), p(obj), p(err), p(nf), p(ls)),
+               "ipm_batch_results")
+        return dict(status=st, iters=it, obj=obj, kkt_err=err, n_factor=nf, ls_steps=ls,
+                    sweeps=lib().ipm_batch_sweeps(self.h))
+
+    def x(self, i):
+        out = np.zeros(self.opfs[i].n)
+        _check(lib().ipm_batch_export(self.h, int(i), out.ctypes.data_as(ctypes.c_void_p)),
+               "ipm_batch_export")
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipm_batch_destroy(self.h)
+            self.h = None
+

@@ -1,0 +1,1345 @@
+// Batched interior-point solves: many AC-OPF instances, with equal or different sparsity
+// patterns, advanced together by the same launches (the batched form of the method; the paper
+// reuses one symbolic analysis across iterations of a pattern, Section 5, and motivates batched
+// solves of many related problems in Section 1).
+//
+// * One symbolic analysis per distinct pattern; instances with the same pattern share it.
+// * Numeric data of every instance sits in one device pool; the persistent factorization and
+//   triangular-solve kernels take tasks from one ticket range per launch that lists every
+//   instance's tasks instance after instance (each instance's tasks in its own topological
+//   order, so a block only waits on smaller tickets and the schedule cannot deadlock).
+// * The interior-point control (convergence test, barrier update, inertia correction, Richardson
+//   refinement, fraction to the boundary, filter line search) runs on the device as a per-instance
+//   phase machine: every kernel acts on the instances in its phase and a one-thread-per-instance
+//   control kernel moves them on.  One sweep (evaluate, build, two inertia rounds, solve, three
+//   refinement rounds, step, two line-search trials, accept) is captured once as a CUDA graph and
+//   replayed; an instance that needs more rounds than a sweep holds continues in the next sweep
+//   from the phase it is in, so every instance follows exactly the single-problem algorithm.
+// LiftedKKT (Section 3.2) in FP64.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <type_traits>
+#include <vector>
+
+#include "ipm_core.cuh"
+#include "numeric_dev.cuh"
+#include "opf_dev.cuh"
+
+namespace cipm {
+
+enum Phase { PH_EVAL = 0, PH_BUILD, PH_FACT, PH_SOLVE, PH_REFINE, PH_STEP, PH_LS, PH_ACC, PH_DONE };
+
+static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2;
+static constexpr int B_BLOCK = 256;
+
+// per-instance control record (device)
+struct BCtl {
+  int ph, status, k, nfac, ls, ftype, have_theta0, ref_it, ref_steps, nfilter;
+  int total_fac, total_ls, total_ref;
+  double mu, tau, sig, delta_last, theta_max, theta_min;
+  double dw, next, grow;
+  double alpha, az, amax, amin, gphi, theta, phi, logsum, obj, e0, eta, eta_prev, normA;
+};
+
+// per-instance descriptor (device): pattern and model pointers, iterate and work vectors
+struct BI {
+  Dims D;
+  It P;
+  StepArgs SA;  // mu and dw are taken from the control record
+  OpfData M;
+  int nl, nu, m;  // finite lower / upper bounds; model rows m = me0 + mi0
+  double *dscale, *gs, *hs, *Jv, *Wv, *lam, *lamw, *f, *fpart;
+  double *r1, *dcond, *baug, *a, *dx, *dzc;
+  double *xt, *st, *geqt, *hint, *gst, *hst, *ft;
+  double *R, *filter;
+  // numeric
+  const int *sptr, *srow_ptr, *slot_ptr, *perm, *J_rowidx, *JT_ptr, *JT_ent;
+  const int64_t *lptr;
+  const int2 *items;
+  int ns;
+  double *tJ, *Lx, *Dx;
+  int *info, *sync;  // sync: [0,2ns) factor, [2ns,3ns) forward, [3ns,4ns) backward, then tail
+  double *y, *t, *cx, *cz, *outx, *outz, *scal;
+  AugArgs aug;
+};
+
+__device__ __forceinline__ int *sync_abort(const BI &I) { return I.sync + 4 * I.ns + 1; }
+__device__ __forceinline__ int *sync_status(const BI &I) { return I.sync + 4 * I.ns + 2; }
+
+#define B_PROLOGUE(want)                 \
+  const int b = blockIdx.y;              \
+  if (ctl[b].ph != (want)) return;       \
+  const BI &I = bi[b];                   \
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x; \
+  const int gstride = gridDim.x * blockDim.x;
+
+// ------------------------------------------------------------------ control helpers
+__global__ void k_b_rreset(const BI *bi, const BCtl *ctl, int phase, int k0, int k1, double v) {
+  const int b = blockIdx.x;
+  if (ctl[b].ph != phase) return;
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) bi[b].R[k] = v;
+}
+
+__global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  BCtl c;
+  memset(&c, 0, sizeof(c));
+  c.ph = PH_EVAL;
+  c.mu = mu0;
+  c.tau = fmax(TAU_MIN, 1.0 - mu0);
+  c.sig = 1.0;
+  c.eta = c.eta_prev = INFINITY;
+  ctl[b] = c;
+  for (int k = 0; k < R_COUNT; ++k) bi[b].R[k] = 0.0;
+}
+
+// ------------------------------------------------------------------ model evaluation
+// mode 0: at x with J and grad f (phase EVAL); mode 1: W at x with the scaled multipliers
+// (phase BUILD); mode 2: at the trial point, values only (phase LS)
+struct EvalPtrs {
+  const double *x, *y, *z;
+  double sigf, *f, *grad, *g, *h, *Jv, *Wv;
+};
+__device__ __forceinline__ EvalPtrs eval_ptrs(const BI &I, const BCtl &c, int mode) {
+  EvalPtrs E;
+  if (mode == 0) {
+    E = EvalPtrs{I.P.x, nullptr, nullptr, 1.0, I.f, I.P.grad, I.gs, I.hs, I.Jv, nullptr};
+  } else if (mode == 1) {
+    E = EvalPtrs{I.P.x, I.lamw, I.lamw + I.D.me0, c.sig, I.ft, nullptr, I.gst, I.hst, nullptr,
+                 I.Wv};
+  } else {
+    E = EvalPtrs{I.xt, nullptr, nullptr, 1.0, I.ft, nullptr, I.gst, I.hst, nullptr, nullptr};
+  }
+  return E;
+}
+__device__ __forceinline__ OpfDims opf_dims(const OpfData &M) {
+  return OpfDims{M.nb, M.nbr, M.ng, M.n, M.me, M.mi};
+}
+
+__global__ void k_b_eval_init(const BI *bi, const BCtl *ctl, int phase, int mode) {
+  B_PROLOGUE(phase);
+  const EvalPtrs E = eval_ptrs(I, ctl[b], mode);
+  const OpfData &M = I.M;
+  eval_init_at(opf_dims(M), M.pd, M.qd, E.x, M.ref, E.g, E.Jv, E.Jv ? M.nnzJ : 0, E.Wv,
+               E.Wv ? M.nnzW : 0, gtid, gstride);
+}
+__global__ void k_b_eval_branch(const BI *bi, const BCtl *ctl, int phase, int mode) {
+  B_PROLOGUE(phase);
+  const EvalPtrs E = eval_ptrs(I, ctl[b], mode);
+  const OpfDims D = opf_dims(I.M);
+  for (int e = gtid; e < 2 * D.nbr; e += gstride)
+    eval_branch_at(D, I.M, E.x, E.y, E.z, E.g, E.h, E.Jv, E.Wv, e);
+}
+// one generator per thread (the grid covers the largest generator count): per-block cost parts
+__global__ void k_b_eval_gen(const BI *bi, const BCtl *ctl, int phase, int mode) {
+  __shared__ double sh[32];
+  const int b = blockIdx.y;
+  if (ctl[b].ph != phase) return;
+  const BI &I = bi[b];
+  const EvalPtrs E = eval_ptrs(I, ctl[b], mode);
+  const OpfDims D = opf_dims(I.M);
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  double fc = gi < D.ng ? eval_gen_at(D, I.M, E.x, E.sigf, E.g, E.grad, E.Jv, E.Wv, gi) : 0.0;
+  block_sum_to(I.fpart + blockIdx.x, fc, sh);
+}
+__global__ void k_b_eval_finish(const BI *bi, const BCtl *ctl, int phase, int mode, int nparts) {
+  B_PROLOGUE(phase);
+  const EvalPtrs E = eval_ptrs(I, ctl[b], mode);
+  eval_finish_at(opf_dims(I.M), I.M, I.fpart, nparts, E.f, E.grad, E.Jv, gtid, gstride);
+}
+
+// constraint scaling of the model outputs and the IPM rows; mode 0 also scales J
+__global__ void k_b_scale_model(const BI *bi, const BCtl *ctl, int phase, int mode,
+                                double relax_tau) {
+  B_PROLOGUE(phase);
+  const Dims &D = I.D;
+  double *gs = mode == 0 ? I.gs : I.gst, *hs = mode == 0 ? I.hs : I.hst;
+  double *geq = mode == 0 ? I.P.geq : I.geqt, *hin = mode == 0 ? I.P.hin : I.hint;
+  const int nrow = max(D.me0, D.mi0);
+  for (int k = gtid; k < nrow; k += gstride) {
+    if (k < D.me0) gs[k] *= I.dscale[k];
+    if (k < D.mi0) hs[k] *= I.dscale[D.me0 + k];
+    ipm_rows_at(D, relax_tau, gs, hs, geq, hin, k);
+  }
+  if (mode == 0)
+    for (int p = gtid; p < I.M.nnzJ; p += gstride) I.Jv[p] *= I.dscale[I.J_rowidx[p]];
+}
+
+// ------------------------------------------------------------------ set-up
+__global__ void k_b_setup_sums(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  double a = 0.0, q = 0.0;
+  for (int i = gtid; i < I.M.nb; i += gstride) {
+    a += I.M.pd[i];
+    q += I.M.qd[i];
+  }
+  red_sum(I.R, R_PD, a);
+  red_sum(I.R, R_QD, q);
+}
+__global__ void k_b_x0(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  for (int j = gtid; j < I.D.n; j += gstride)
+    I.P.x[j] = x0_at(I.M.nb, I.M.ng, I.R[R_PD], I.R[R_QD], I.P.xl, I.P.xu, j);
+}
+__global__ void k_b_row_scale(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  for (int r = gtid; r < I.m; r += gstride) {
+    double mx = 0.0;
+    for (int p = I.M.J_rowptr[r]; p < I.M.J_rowptr[r + 1]; ++p) mx = fmax(mx, fabs(I.Jv[p]));
+    I.dscale[r] = mx > 0.0 ? fmin(1.0, 100.0 / mx) : 1.0;
+  }
+  double g = 0.0;
+  for (int j = gtid; j < I.D.n; j += gstride) g = fmax(g, fabs(I.P.grad[j]));
+  red_max(I.R, R_MAXGRAD, g);
+}
+__global__ void k_b_ctl_sig(const BI *bi, BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  ctl[b].sig = fmin(1.0, 100.0 / fmax(bi[b].R[R_MAXGRAD], 1e-300));
+}
+__global__ void k_b_init_duals(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  const int nmax = max(I.D.n, max(I.D.me, I.D.mi));
+  for (int i = gtid; i < nmax; i += gstride) init_duals_at(I.D, I.P, I.P.s, i);
+}
+
+// ------------------------------------------------------------------ evaluation phase
+__global__ void k_b_lambda(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  const int nrow = max(I.D.me0, I.D.mi0);
+  for (int k = gtid; k < nrow; k += gstride) lambda_at(I.D, I.P.y, I.P.z, I.lam, k);
+}
+__global__ void k_b_jtu(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    double acc = 0.0;
+    for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+      int p = I.JT_ent[t];
+      acc += I.Jv[p] * I.lam[I.J_rowidx[p]];
+    }
+    I.P.jtl[j] = acc;
+  }
+}
+// optimality error parts (mu-independent maxima, sums, min / max of the complementarity
+// products) and the merit parts at (x, s)
+__global__ void k_b_errors(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  const Dims &D = I.D;
+  const double sig = ctl[b].sig;
+  double gl = 0, zv = 0, ge = 0, hs = 0, sy = 0, sz = 0, svv = 0, szl = 0, szu = 0;
+  double svmin = INFINITY, svmax = 0, clmin = INFINITY, clmax = 0, cumin = INFINITY, cumax = 0;
+  double tg = 0, th = 0, ls = 0, lxl = 0, lxu = 0;
+  const int nmax = max(D.n, max(D.me, D.mi));
+  for (int i = gtid; i < nmax; i += gstride) {
+    const ErrParts E = errors_at(D, I.P, sig, 0.0, i);
+    gl = fmax(gl, E.gl);
+    zv = fmax(zv, E.zv);
+    ge = fmax(ge, E.ge);
+    hs = fmax(hs, E.hs);
+    sy += E.sy;
+    sz += E.sz;
+    svv += E.svv;
+    szl += E.szl;
+    szu += E.szu;
+    if (E.csv >= 0) { svmin = fmin(svmin, E.csv); svmax = fmax(svmax, E.csv); }
+    if (E.ccl >= 0) { clmin = fmin(clmin, E.ccl); clmax = fmax(clmax, E.ccl); }
+    if (E.ccu >= 0) { cumin = fmin(cumin, E.ccu); cumax = fmax(cumax, E.ccu); }
+    const MeritParts Mp = merit_at(D, I.P.x, I.P.s, I.P.xl, I.P.xu, I.P.geq, I.P.hin, i);
+    tg += Mp.tg;
+    th += Mp.th;
+    ls += Mp.ls;
+    lxl += Mp.lxl;
+    lxu += Mp.lxu;
+  }
+  double *R = I.R;
+  red_max(R, R_MAX_GL, gl);
+  red_max(R, R_MAX_ZV, zv);
+  red_max(R, R_MAX_G, ge);
+  red_max(R, R_MAX_HS, hs);
+  red_sum(R, R_SUM_Y, sy);
+  red_sum(R, R_SUM_Z, sz);
+  red_sum(R, R_SUM_V, svv);
+  red_sum(R, R_SUM_ZL, szl);
+  red_sum(R, R_SUM_ZU, szu);
+  red_min(R, R_SV_MIN, svmin);
+  red_max(R, R_SV_MAX, svmax);
+  red_min(R, R_CL_MIN, clmin);
+  red_max(R, R_CL_MAX, clmax);
+  red_min(R, R_CU_MIN, cumin);
+  red_max(R, R_CU_MAX, cumax);
+  red_sum(R, R_TH_G, tg);
+  red_sum(R, R_TH_H, th);
+  red_sum(R, R_LOG_S, ls);
+  red_sum(R, R_LOG_XL, lxl);
+  red_sum(R, R_LOG_XU, lxu);
+}
+
+__device__ __forceinline__ double comp_mu(const double *h, double mu) {
+  double c = 0.0;
+  c = fmax(c, fmax(h[R_SV_MAX] - mu, mu - h[R_SV_MIN]));
+  c = fmax(c, fmax(h[R_CL_MAX] - mu, mu - h[R_CL_MIN]));
+  c = fmax(c, fmax(h[R_CU_MAX] - mu, mu - h[R_CU_MIN]));
+  return c;
+}
+
+// convergence test, iteration limit, barrier update (repeated in the first iteration)
+__global__ void k_b_ctl_eval(const BI *bi, BCtl *ctl, int count, double tol, int max_iter) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_EVAL) return;
+  const BI &I = bi[b];
+  BCtl c = ctl[b];
+  const double *h = I.R;
+  c.obj = *I.f;
+  c.theta = h[R_TH_G] + h[R_TH_H];
+  c.logsum = h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU];
+  const double e0 = kkt_error(h, I.D, I.nl, I.nu, fmax(h[R_SV_MAX], fmax(h[R_CL_MAX], h[R_CU_MAX])));
+  c.e0 = e0;
+  if (!c.have_theta0) {
+    c.theta_max = 1e4 * fmax(1.0, c.theta);
+    c.theta_min = 1e-4 * fmax(1.0, c.theta);
+    c.have_theta0 = 1;
+  }
+  if (e0 <= tol) {
+    c.status = 1;
+    c.ph = PH_DONE;
+  } else if (!isfinite(e0)) {
+    c.status = IPM_ERR_NONFINITE;
+    c.ph = PH_DONE;
+  } else if (c.k >= max_iter) {
+    c.status = IPM_ERR_MAXITER;
+    c.ph = PH_DONE;
+  } else {
+    bool first = true;
+    for (int rep = 0; rep < 200; ++rep) {
+      const double emu = kkt_error(h, I.D, I.nl, I.nu, comp_mu(h, c.mu));
+      if (!(emu <= KAPPA_EPS * c.mu && (first || c.k == 0))) break;
+      c.mu = fmax(tol / 10.0, fmin(KAPPA_MU * c.mu, pow(c.mu, THETA_MU)));
+      c.tau = fmax(TAU_MIN, 1.0 - c.mu);
+      c.nfilter = 0;
+      first = false;
+    }
+    c.ph = PH_BUILD;
+  }
+  ctl[b] = c;
+}
+
+// ------------------------------------------------------------------ build phase
+__global__ void k_b_lamw(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_BUILD);
+  for (int r = gtid; r < I.m; r += gstride) I.lamw[r] = I.lam[r] * I.dscale[r];
+}
+__global__ void k_b_newton_rhs(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_BUILD);
+  const Dims &D = I.D;
+  const int nmax = max(D.n, D.mi);
+  for (int i = gtid; i < nmax; i += gstride) {
+    newton_rhs_at(D, I.P, ctl[b].sig, ctl[b].mu, (double *)I.SA.sigma, I.r1, (double *)I.SA.r2,
+                  (double *)I.SA.r4, (double *)I.SA.Ds, i);
+    if (i < D.n) I.a[i] = -I.r1[i];
+  }
+}
+// inertia search start: delta_w = 0, then delta_last / 3 (x8) or 1e-4 (x100)
+__global__ void k_b_ctl_build(BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_BUILD) return;
+  BCtl &c = ctl[b];
+  c.dw = 0.0;
+  c.nfac = 0;
+  c.grow = c.delta_last > 0 ? 8.0 : 100.0;
+  c.next = c.delta_last > 0 ? fmax(1e-20, c.delta_last / 3.0) : 1e-4;
+  c.ph = PH_FACT;
+}
+
+// ------------------------------------------------------------------ inertia rounds
+__global__ void k_b_aug_rhs(const BI *bi, const BCtl *ctl, double gamma) {
+  B_PROLOGUE(PH_FACT);
+  const int nrow = max(I.D.me0, I.D.mi0);
+  for (int k = gtid; k < nrow; k += gstride)
+    aug_rhs_at(I.D, ctl[b].dw, gamma, I.SA.r2, I.SA.r4, I.SA.Ds, I.P.geq, I.dcond, I.baug, k);
+}
+__global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_FACT);
+  for (int p = gtid; p < I.M.nnzJ; p += gstride) I.tJ[p] = I.dcond[I.J_rowidx[p]] * I.Jv[p];
+}
+__global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
+  const int b = blockIdx.y;
+  if (ctl[b].ph != PH_FACT) return;
+  const BI &I = bi[b];
+  for (int s = blockIdx.x; s < I.ns; s += gridDim.x)
+    condense_block<double>(s, I.sptr, I.srow_ptr, I.lptr, I.slot_ptr, I.items, I.perm, I.Wv,
+                           I.SA.sigma, I.Jv, I.tJ, ctl[b].dw, I.Lx);
+}
+// counters of the factorization, abort and status flags, failing-pivot slot
+__global__ void k_b_fact_reset(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_FACT);
+  for (int k = gtid; k < 2 * I.ns; k += gstride) I.sync[k] = 0;
+  if (gtid == 0) {
+    *sync_abort(I) = 0;
+    *sync_status(I) = 0;
+    *I.info = INT_MAX;
+  }
+}
+
+__device__ __forceinline__ int find_inst(const int *start, int count, int t) {
+  int lo = 0, hi = count - 1;  // largest i with start[i] <= t
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// thread 0: next ticket of an instance in the phase (instances outside it are jumped over)
+__device__ __forceinline__ void grab_ticket(const int *start, int count, const BCtl *ctl,
+                                            int phase, int *ticket, int *s_t, int *s_inst) {
+  const int total = start[count];
+  int t, inst;
+  while (true) {
+    t = atomicAdd(ticket, 1);
+    if (t >= total) {
+      inst = -1;
+      break;
+    }
+    inst = find_inst(start, count, t);
+    if (ctl[inst].ph == phase) break;
+    atomicMax(ticket, start[inst + 1]);
+  }
+  *s_t = t;
+  *s_inst = inst;
+}
+
+template <typename A>
+__device__ __forceinline__ void load_args(A *dst, const A *src) {
+  static_assert(sizeof(A) % 4 == 0, "argument block size");
+  const int *s = reinterpret_cast<const int *>(src);
+  int *d = reinterpret_cast<int *>(dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(A) / 4); k += blockDim.x) d[k] = s[k];
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_b_factor(const FactTaskArgs<V> *FA, const int *start,
+                                                  int count, const BCtl *ctl, int *ticket) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  V *sm = reinterpret_cast<V *>(sm_raw);
+  __shared__ FactTaskArgs<V> sT;
+  __shared__ int s_t, s_inst, s_cur, s_ok;
+  if (threadIdx.x == 0) s_cur = -1;
+  __syncthreads();
+  while (true) {
+    if (threadIdx.x == 0) grab_ticket(start, count, ctl, PH_FACT, ticket, &s_t, &s_inst);
+    __syncthreads();
+    const int t = s_t, inst = s_inst;
+    const bool reload = inst >= 0 && inst != s_cur;
+    __syncthreads();
+    if (inst < 0) break;
+    if (reload) {
+      load_args(&sT, FA + inst);
+      if (threadIdx.x == 0) s_cur = inst;
+    }
+    __syncthreads();
+    const int4 tk = sT.tasks[t - start[inst]];
+    if (tk.w == 0) fact_panel_task(sT, tk.x, tk.y, sm, &s_ok);
+    else fact_update_task(sT, tk.x, tk.y, tk.z, sm, &s_ok);
+    __syncthreads();
+  }
+}
+
+// factor outcome: success -> solve; wrong inertia -> next delta_w
+__global__ void k_b_ctl_fact(const BI *bi, BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_FACT) return;
+  const BI &I = bi[b];
+  BCtl &c = ctl[b];
+  ++c.nfac;
+  ++c.total_fac;
+  if (*sync_status(I) != 0) {
+    c.status = IPM_ERR_TIMEOUT;
+    c.ph = PH_DONE;
+    return;
+  }
+  if (*I.info == INT_MAX) {
+    if (c.dw > 0) c.delta_last = c.dw;
+    c.ph = PH_SOLVE;
+    return;
+  }
+  c.dw = c.next;
+  c.next *= c.grow;
+  if (c.dw >= 1e40) {
+    c.status = IPM_ERR_INERTIA;
+    c.ph = PH_DONE;
+  }
+}
+
+// ------------------------------------------------------------------ condensed solve
+// phase SOLVE: dx = K^{-1}(a + J^T (d o b)), dz = d o (J dx - b);
+// phase REFINE: the same for the residual (outx, outz) into (cx, cz)
+__global__ void k_b_jt_rhs(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  const double *u = phase == PH_SOLVE ? I.baug : I.outz;
+  const double *base = phase == PH_SOLVE ? I.a : I.outx;
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    double acc = 0.0;
+    for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+      int p = I.JT_ent[t];
+      int r = I.J_rowidx[p];
+      double v = I.Jv[p] * u[r];
+      v *= I.dcond[r];
+      acc += v;
+    }
+    I.t[j] = base[j] + acc;
+  }
+}
+__global__ void k_b_gather(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  for (int k = gtid; k < I.D.n; k += gstride) I.y[k] = I.t[I.perm[k]];
+  for (int k = gtid; k < 2 * I.ns; k += gstride) I.sync[2 * I.ns + k] = 0;
+}
+template <typename V, bool Fwd>
+__global__ void __launch_bounds__(128) k_b_solve(const SolveTaskArgs<V> *SA, const int *start,
+                                                 int count, const BCtl *ctl, int phase,
+                                                 int *ticket) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *sL = reinterpret_cast<double *>(sm_raw);
+  __shared__ double ys[CIPM_SN_MAXW];
+  __shared__ SolveTaskArgs<V> sT;
+  __shared__ int s_t, s_inst, s_cur, s_ok;
+  if (threadIdx.x == 0) s_cur = -1;
+  __syncthreads();
+  while (true) {
+    if (threadIdx.x == 0) grab_ticket(start, count, ctl, phase, ticket, &s_t, &s_inst);
+    __syncthreads();
+    const int t = s_t, inst = s_inst;
+    const bool reload = inst >= 0 && inst != s_cur;
+    __syncthreads();
+    if (inst < 0) break;
+    if (reload) {
+      load_args(&sT, SA + inst);
+      if (threadIdx.x == 0) s_cur = inst;
+    }
+    __syncthreads();
+    const int local = t - start[inst];
+    if (Fwd) fwd_task(sT, sT.A.level_sn[local], sL, ys, &s_ok);
+    else bwd_task(sT, sT.A.level_sn[sT.ns - 1 - local], sL, ys, &s_ok);
+    __syncthreads();
+  }
+}
+__global__ void k_b_scatter_dz(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  double *x = phase == PH_SOLVE ? I.dx : I.cx;
+  for (int k = gtid; k < I.D.n; k += gstride) x[I.perm[k]] = I.y[k];
+}
+__global__ void k_b_recover_dz(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  const double *x = phase == PH_SOLVE ? I.dx : I.cx;
+  const double *rb = phase == PH_SOLVE ? I.baug : I.outz;
+  double *dz = phase == PH_SOLVE ? I.dzc : I.cz;
+  for (int r = gtid; r < I.m; r += gstride) {
+    double acc = 0.0;
+    for (int p = I.M.J_rowptr[r]; p < I.M.J_rowptr[r + 1]; ++p) acc += I.Jv[p] * x[I.M.J_colind[p]];
+    dz[r] = I.dcond[r] * (acc - rb[r]);
+  }
+}
+__global__ void k_b_ctl_solved(const BI *bi, BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_SOLVE) return;
+  BCtl &c = ctl[b];
+  if (*sync_status(bi[b]) != 0) {
+    c.status = IPM_ERR_TIMEOUT;
+    c.ph = PH_DONE;
+    return;
+  }
+  c.ref_it = 0;
+  c.ref_steps = 0;
+  c.eta = c.eta_prev = INFINITY;
+  c.ph = PH_REFINE;
+}
+
+// ------------------------------------------------------------------ refinement rounds
+__global__ void k_b_resid(const BI *bi, const BCtl *ctl) {
+  __shared__ double sh[32];
+  B_PROLOGUE(PH_REFINE);
+  AugArgs A = I.aug;
+  A.dw = ctl[b].dw;
+  double res = 0.0, solv = 0.0, rhsv = 0.0, asum = 0.0;
+  for (int i = gtid; i < A.n + A.m; i += gstride) {
+    double as = 0.0, r;
+    if (i < A.n) {
+      r = aug_resid_x_at(A, i, &as);
+      A.outx[i] = r;
+      solv = fmax(solv, fabs(A.sx[i]));
+      rhsv = fmax(rhsv, fabs(A.ra[i]));
+    } else {
+      const int q = i - A.n;
+      r = aug_resid_z_at(A, q, &as);
+      A.outz[q] = r;
+      solv = fmax(solv, fabs(A.sz[q]));
+      rhsv = fmax(rhsv, fabs(A.rb[q]));
+    }
+    res = fmax(res, fabs(r));
+    asum = fmax(asum, as);
+  }
+  block_max_to(&A.scal[0], res, sh);
+  block_max_to(&A.scal[1], solv, sh);
+  block_max_to(&A.scal[2], rhsv, sh);
+  block_max_to(&A.scal[3], asum, sh);
+}
+// Richardson test: stop at eta <= 1e-10, after max_refine corrections, or when eta stops
+// halving; otherwise one more correction
+__global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_REFINE) return;
+  const BI &I = bi[b];
+  BCtl &c = ctl[b];
+  const double *sc = I.scal;
+  if (*sync_status(I) != 0) {
+    c.status = IPM_ERR_TIMEOUT;
+    c.ph = PH_DONE;
+    return;
+  }
+  if (c.ref_it == 0) c.normA = sc[3];
+  const double den = c.normA * sc[1] + sc[2];
+  const double eta = den > 0 ? sc[0] / den : 0.0;
+  c.eta = eta;
+  bool stop;
+  if (!isfinite(eta)) {
+    c.status = IPM_ERR_NONFINITE;
+    c.ph = PH_DONE;
+    return;
+  }
+  stop = eta <= 1e-10 || c.ref_it >= max_refine || (c.ref_it > 0 && eta > 0.5 * c.eta_prev);
+  ++c.ref_it;
+  if (stop) {
+    c.ph = PH_STEP;
+    return;
+  }
+  c.eta_prev = eta;
+  ++c.ref_steps;
+  ++c.total_ref;
+}
+__global__ void k_b_scal_zero(const BI *bi, const BCtl *ctl) {
+  const int b = blockIdx.x;
+  if (ctl[b].ph != PH_REFINE) return;
+  if (threadIdx.x < 4) bi[b].scal[threadIdx.x] = 0.0;
+}
+__global__ void k_b_axpy(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_REFINE);
+  for (int j = gtid; j < I.D.n; j += gstride) I.dx[j] += I.cx[j];
+  for (int r = gtid; r < I.m; r += gstride) I.dzc[r] += I.cz[r];
+}
+
+// ------------------------------------------------------------------ step
+__global__ void k_b_jv(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_STEP);
+  for (int r = gtid; r < I.m; r += gstride) {
+    double acc = 0.0;
+    for (int p = I.M.J_rowptr[r]; p < I.M.J_rowptr[r + 1]; ++p) acc += I.Jv[p] * I.dx[I.M.J_colind[p]];
+    ((double *)I.SA.jdx)[r] = acc;
+  }
+}
+__global__ void k_b_recover(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_STEP);
+  StepArgs A = I.SA;
+  A.mu = ctl[b].mu;
+  A.dw = ctl[b].dw;
+  const int nmax = max(I.D.n, I.D.mi);
+  for (int i = gtid; i < nmax; i += gstride) recover_at(A, i);
+}
+__global__ void k_b_ftb(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_STEP);
+  StepArgs A = I.SA;
+  A.mu = ctl[b].mu;
+  A.dw = ctl[b].dw;
+  double ap = 1.0, az = 1.0, gx = 0.0, gs = 0.0;
+  const int nmax = max(I.D.n, I.D.mi);
+  for (int i = gtid; i < nmax; i += gstride) {
+    const FtbParts F = ftb_at(A, ctl[b].tau, ctl[b].sig, i);
+    ap = fmin(ap, F.ap);
+    az = fmin(az, F.az);
+    gx += F.gx;
+    gs += F.gs;
+  }
+  red_min(I.R, R_AMAX, ap);
+  red_min(I.R, R_AZ, az);
+  red_sum(I.R, R_GPHI_X, gx);
+  red_sum(I.R, R_GPHI_S, gs);
+}
+__global__ void k_b_ctl_ls0(const BI *bi, BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_STEP) return;
+  const double *h = bi[b].R;
+  BCtl &c = ctl[b];
+  c.amax = h[R_AMAX];
+  c.az = h[R_AZ];
+  c.gphi = h[R_GPHI_X] + h[R_GPHI_S];
+  c.phi = c.sig * c.obj - c.mu * c.logsum;
+  const double theta = c.theta, gphi = c.gphi;
+  if (gphi < 0)
+    c.amin = GAMMA_ALPHA * fmin(GAMMA_THETA, fmin(GAMMA_PHI * theta / -gphi,
+                                                  DELTA_SW * pow(theta, S_THETA) / pow(-gphi, S_PHI)));
+  else
+    c.amin = GAMMA_ALPHA * GAMMA_THETA;
+  c.alpha = c.amax;
+  c.ls = 0;
+  c.ph = PH_LS;
+}
+
+// ------------------------------------------------------------------ line search
+__global__ void k_b_trial(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_LS);
+  const int nmax = max(I.D.n, I.D.mi);
+  for (int i = gtid; i < nmax; i += gstride)
+    trial_at(I.D.n, I.D.mi, ctl[b].alpha, I.P.x, I.dx, I.P.s, I.SA.ds, I.xt, I.st, i);
+}
+__global__ void k_b_merit_trial(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_LS);
+  const Dims &D = I.D;
+  double tg = 0, th = 0, ls = 0, lxl = 0, lxu = 0;
+  const int nmax = max(D.n, max(D.me, D.mi));
+  for (int i = gtid; i < nmax; i += gstride) {
+    const MeritParts Mp = merit_at(D, I.xt, I.st, I.P.xl, I.P.xu, I.geqt, I.hint, i);
+    tg += Mp.tg;
+    th += Mp.th;
+    ls += Mp.ls;
+    lxl += Mp.lxl;
+    lxu += Mp.lxu;
+  }
+  red_sum(I.R, R_TH_G, tg);
+  red_sum(I.R, R_TH_H, th);
+  red_sum(I.R, R_LOG_S, ls);
+  red_sum(I.R, R_LOG_XL, lxl);
+  red_sum(I.R, R_LOG_XU, lxu);
+}
+// filter acceptance (Ipopt: switching condition with the Armijo test on phi, else sufficient
+// decrease in theta or phi against the filter); backtrack by halves down to alpha_min
+__global__ void k_b_ctl_ls(const BI *bi, BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_LS) return;
+  const BI &I = bi[b];
+  BCtl &c = ctl[b];
+  const double *h = I.R;
+  const double tht = h[R_TH_G] + h[R_TH_H];
+  const double pht = c.sig * (*I.ft) - c.mu * (h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU]);
+  const double theta = c.theta, phi = c.phi, gphi = c.gphi, alpha = c.alpha;
+  bool okf = tht < c.theta_max;
+  for (int q = 0; q < c.nfilter && okf; ++q)
+    if (!(tht < I.filter[2 * q] || pht < I.filter[2 * q + 1])) okf = false;
+  bool accepted = false;
+  int ftype = 0;
+  if (okf && isfinite(pht)) {
+    const bool switching = gphi < 0 && alpha * pow(-gphi, S_PHI) > DELTA_SW * pow(theta, S_THETA);
+    if (switching && theta <= c.theta_min) {
+      if (pht <= phi + ETA_PHI * alpha * gphi) {
+        accepted = true;
+        ftype = 1;
+      }
+    } else if (tht <= (1 - GAMMA_THETA) * theta || pht <= phi - GAMMA_PHI * theta) {
+      accepted = true;
+    }
+  }
+  if (accepted) {
+    c.ftype = ftype;
+    c.ph = PH_ACC;
+    return;
+  }
+  ++c.ls;
+  ++c.total_ls;
+  c.alpha = alpha * 0.5;
+  if (c.alpha < c.amin) {
+    c.status = IPM_ERR_RESTORATION;
+    c.ph = PH_DONE;
+  }
+}
+
+// ------------------------------------------------------------------ accept
+__global__ void k_b_accept(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_ACC);
+  StepArgs A = I.SA;
+  A.mu = ctl[b].mu;
+  A.dw = ctl[b].dw;
+  const int nmax = max(I.D.n, max(I.D.me, I.D.mi));
+  for (int i = gtid; i < nmax; i += gstride)
+    accept_at(A, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.dx, i);
+}
+__global__ void k_b_ctl_acc(const BI *bi, BCtl *ctl, int count, int fmax_entries) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_ACC) return;
+  BCtl &c = ctl[b];
+  if (!c.ftype) {
+    double *F = bi[b].filter;
+    if (c.nfilter < fmax_entries) {
+      F[2 * c.nfilter] = (1 - GAMMA_THETA) * c.theta;
+      F[2 * c.nfilter + 1] = c.phi - GAMMA_PHI * c.theta;
+      ++c.nfilter;
+    } else {
+      // full: replace the entry that is dominated the most (largest theta), keeping a valid
+      // (conservative) filter
+      int q = 0;
+      for (int k = 1; k < c.nfilter; ++k)
+        if (F[2 * k] > F[2 * q]) q = k;
+      F[2 * q] = fmin(F[2 * q], (1 - GAMMA_THETA) * c.theta);
+      F[2 * q + 1] = fmin(F[2 * q + 1], c.phi - GAMMA_PHI * c.theta);
+    }
+  }
+  ++c.k;
+  c.ph = PH_EVAL;
+}
+
+__global__ void k_b_count(const BCtl *ctl, int count, int *active) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = b < count && ctl[b].ph != PH_DONE;
+  a = __syncthreads_count(a);
+  if (threadIdx.x == 0 && a) atomicAdd(active, a);
+}
+__global__ void k_b_finish_unfinished(BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < count && ctl[b].ph != PH_DONE) {
+    ctl[b].status = IPM_ERR_MAXITER;
+    ctl[b].ph = PH_DONE;
+  }
+}
+
+}  // namespace cipm
+
+using namespace cipm;
+
+// ------------------------------------------------------------------ host side
+struct ipm_batch_s {
+  int count = 0;
+  ipm_options opt;
+  cudaStream_t stream = 0;
+  std::vector<ipm_opf_t> opf;
+  std::vector<ipm_sym_t> syms;  // one per distinct pattern
+  std::vector<int> pat;         // instance -> pattern
+  double *dpool = nullptr;
+  int *ipool = nullptr;
+  size_t dpool_len = 0, ipool_len = 0;
+  BI *d_bi = nullptr;
+  BCtl *d_ctl = nullptr;
+  FactTaskArgs<double> *d_fa = nullptr;
+  SolveTaskArgs<double> *d_fw = nullptr, *d_bw = nullptr;
+  int *d_fstart = nullptr, *d_sstart = nullptr;  // ticket ranges [count + 1]
+  int *d_tickets = nullptr;                      // 16 ticket counters, then the active count
+  int *h_active = nullptr;                       // pinned
+  int gx = 1, gx_gen = 1, max_ns = 1, fmax_entries = 0;
+  size_t fact_smem = 0, solve_smem = 0;
+  int grid_fact = 0, grid_solve = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches_per_sweep = 0;
+  int sweeps = 0;
+  int max_iter = 3000;  // iteration limit of the captured sweep
+};
+
+namespace {
+
+struct Bump {
+  size_t n = 0;
+  size_t take(size_t k) {
+    size_t o = n;
+    n += (std::max<size_t>(k, 1) + 31) & ~size_t(31);
+    return o;
+  }
+};
+
+int pattern_of(const OpfData &M, std::vector<int> &out) {
+  const int m = M.me + M.mi;
+  out.resize(4 + (m + 1) + M.nnzJ + (M.n + 1) + M.nnzW);
+  int *o = out.data();
+  o[0] = M.n;
+  o[1] = M.me;
+  o[2] = M.mi;
+  o[3] = M.nnzJ;
+  o += 4;
+  CK(cudaMemcpy(o, M.J_rowptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost));
+  o += m + 1;
+  CK(cudaMemcpy(o, M.J_colind, sizeof(int) * M.nnzJ, cudaMemcpyDeviceToHost));
+  o += M.nnzJ;
+  CK(cudaMemcpy(o, M.W_rowptr, sizeof(int) * (M.n + 1), cudaMemcpyDeviceToHost));
+  o += M.n + 1;
+  CK(cudaMemcpy(o, M.W_colind, sizeof(int) * M.nnzW, cudaMemcpyDeviceToHost));
+  return IPM_OK;
+}
+
+int b_smem_limits() {
+  static bool done = false;
+  if (done) return IPM_OK;
+  const int big = 64 * 1024;
+  CK(cudaFuncSetAttribute(k_b_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_b_solve<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_b_solve<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  done = true;
+  return IPM_OK;
+}
+
+int b_persistent_grid(const void *kernel, int threads, size_t smem) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+  return std::max(1, nsm) * std::max(1, std::min(occ, 4));
+}
+
+// every kernel of one sweep, in order; returns the number of launches
+int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
+  const int C = B->count;
+  const dim3 g2(B->gx, C), blk(B_BLOCK);
+  const int gc = grid_for(C, 128);
+  const double tol = B->opt.tol, relax = B->opt.tau;
+  BI *bi = B->d_bi;
+  BCtl *ctl = B->d_ctl;
+  int n = 0;
+  auto L = [&](int k) { n += k; };
+  auto rreset = [&](int phase, int k0, int k1, double v) {
+    k_b_rreset<<<C, 32, 0, s>>>(bi, ctl, phase, k0, k1, v);
+    L(1);
+  };
+  auto eval = [&](int phase, int mode) {
+    k_b_eval_init<<<g2, blk, 0, s>>>(bi, ctl, phase, mode);
+    k_b_eval_branch<<<g2, blk, 0, s>>>(bi, ctl, phase, mode);
+    k_b_eval_gen<<<dim3(B->gx_gen, C), blk, 0, s>>>(bi, ctl, phase, mode);
+    k_b_eval_finish<<<g2, blk, 0, s>>>(bi, ctl, phase, mode, B->gx_gen);
+    L(4);
+  };
+  auto solve = [&](int phase) {
+    k_b_jt_rhs<<<g2, blk, 0, s>>>(bi, ctl, phase);
+    k_b_gather<<<g2, blk, 0, s>>>(bi, ctl, phase);
+    L(2);
+    CK(cudaMemsetAsync(B->d_tickets + 2, 0, sizeof(int) * 2, s));
+    k_b_solve<double, true><<<B->grid_solve, 128, B->solve_smem, s>>>(
+        B->d_fw, B->d_sstart, C, ctl, phase, B->d_tickets + 2);
+    k_b_solve<double, false><<<B->grid_solve, 128, B->solve_smem, s>>>(
+        B->d_bw, B->d_sstart, C, ctl, phase, B->d_tickets + 3);
+    k_b_scatter_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
+    k_b_recover_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
+    L(4);
+    return IPM_OK;
+  };
+  // evaluate at x, optimality error, convergence, barrier update
+  eval(PH_EVAL, 0);
+  k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0, relax);
+  k_b_lambda<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_jtu<<<g2, blk, 0, s>>>(bi, ctl);
+  L(3);
+  rreset(PH_EVAL, 0, R_COUNT, 0.0);
+  rreset(PH_EVAL, R_SV_MIN, R_SV_MIN + 1, INFINITY);
+  rreset(PH_EVAL, R_CL_MIN, R_CL_MIN + 1, INFINITY);
+  rreset(PH_EVAL, R_CU_MIN, R_CU_MIN + 1, INFINITY);
+  k_b_errors<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_ctl_eval<<<gc, 128, 0, s>>>(bi, ctl, C, tol, B->max_iter);
+  L(2);
+  // Hessian with the scaled multipliers, Newton right-hand sides
+  k_b_lamw<<<g2, blk, 0, s>>>(bi, ctl);
+  L(1);
+  eval(PH_BUILD, 1);
+  k_b_newton_rhs<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_ctl_build<<<gc, 128, 0, s>>>(ctl, C);
+  L(2);
+  // inertia rounds: condense + factor with the current delta_w
+  for (int r = 0; r < B_FACT_ROUNDS; ++r) {
+    k_b_aug_rhs<<<g2, blk, 0, s>>>(bi, ctl, B->opt.gamma);
+    k_b_scale_jv<<<g2, blk, 0, s>>>(bi, ctl);
+    k_b_condense<<<dim3(B->max_ns, C), 128, 0, s>>>(bi, ctl);
+    k_b_fact_reset<<<g2, blk, 0, s>>>(bi, ctl);
+    L(4);
+    CK(cudaMemsetAsync(B->d_tickets + 0, 0, sizeof(int), s));
+    k_b_factor<double><<<B->grid_fact, 256, B->fact_smem, s>>>(B->d_fa, B->d_fstart, C, ctl,
+                                                               B->d_tickets + 0);
+    k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
+    L(2);
+  }
+  // condensed solve, then Richardson refinement on the augmented system
+  CKR(solve(PH_SOLVE));
+  k_b_ctl_solved<<<gc, 128, 0, s>>>(bi, ctl, C);
+  L(1);
+  for (int r = 0; r < B_REFINE_ROUNDS; ++r) {
+    k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl);
+    k_b_resid<<<g2, blk, 0, s>>>(bi, ctl);
+    k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine);
+    L(3);
+    CKR(solve(PH_REFINE));
+    k_b_axpy<<<g2, blk, 0, s>>>(bi, ctl);
+    L(1);
+  }
+  // step recovery, fraction to the boundary, line-search set-up
+  k_b_jv<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_recover<<<g2, blk, 0, s>>>(bi, ctl);
+  L(2);
+  rreset(PH_STEP, R_AMAX, R_AZ + 1, 1.0);
+  rreset(PH_STEP, R_GPHI_X, R_GPHI_S + 1, 0.0);
+  k_b_ftb<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_ctl_ls0<<<gc, 128, 0, s>>>(bi, ctl, C);
+  L(2);
+  // line-search trials
+  for (int r = 0; r < B_LS_ROUNDS; ++r) {
+    k_b_trial<<<g2, blk, 0, s>>>(bi, ctl);
+    L(1);
+    eval(PH_LS, 2);
+    k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_LS, 2, relax);
+    L(1);
+    rreset(PH_LS, R_TH_G, R_LOG_XU + 1, 0.0);
+    k_b_merit_trial<<<g2, blk, 0, s>>>(bi, ctl);
+    k_b_ctl_ls<<<gc, 128, 0, s>>>(bi, ctl, C);
+    L(2);
+  }
+  k_b_accept<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_ctl_acc<<<gc, 128, 0, s>>>(bi, ctl, C, B->fmax_entries);
+  L(2);
+  CK(cudaMemsetAsync(B->d_tickets + 8, 0, sizeof(int), s));
+  k_b_count<<<gc, 128, 0, s>>>(ctl, C, B->d_tickets + 8);
+  L(1);
+  CK(cudaMemcpyAsync(B->h_active, B->d_tickets + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKL();
+  B->launches_per_sweep = n;
+  return IPM_OK;
+}
+
+// starting point, scaling and multipliers of every instance (Ipopt: see ipm_state_create)
+int init_instances(ipm_batch_t B) {
+  const int C = B->count;
+  cudaStream_t s = B->stream;
+  const dim3 g2(B->gx, C), blk(B_BLOCK);
+  BI *bi = B->d_bi;
+  BCtl *ctl = B->d_ctl;
+  const double mu0 = B->opt.mu0;
+  k_b_ctl_init<<<grid_for(C, 128), 128, 0, s>>>(bi, ctl, C, mu0);
+  k_b_setup_sums<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_x0<<<g2, blk, 0, s>>>(bi, ctl);
+  auto eval0 = [&]() {
+    k_b_eval_init<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0);
+    k_b_eval_branch<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0);
+    k_b_eval_gen<<<dim3(B->gx_gen, C), blk, 0, s>>>(bi, ctl, PH_EVAL, 0);
+    k_b_eval_finish<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0, B->gx_gen);
+  };
+  eval0();
+  k_b_row_scale<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_ctl_sig<<<grid_for(C, 128), 128, 0, s>>>(bi, ctl, C);
+  eval0();
+  k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0, B->opt.tau);
+  k_b_init_duals<<<g2, blk, 0, s>>>(bi, ctl);
+  CKL();
+  count_launches(15);
+  return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_options *opt,
+                                cudaStream_t stream, ipm_batch_t *out) {
+  if (count <= 0 || !opfs || !opt || !out || opt->kkt != 0 || !(opt->tol > 0)) {
+    set_error_msg("ipm_batch_create: bad argument (count > 0, kkt = 0 (LiftedKKT), tol > 0)");
+    return IPM_ERR_BAD_ARG;
+  }
+  if (opt->precision != 0 && opt->precision != 64) {
+    set_error_msg("ipm_batch_create: batched solves factor in FP64 (precision 0 or 64)");
+    return IPM_ERR_BAD_ARG;
+  }
+  for (int i = 0; i < count; ++i)
+    if (!opfs[i]) {
+      set_error_msg("ipm_batch_create: null model handle");
+      return IPM_ERR_BAD_ARG;
+    }
+  *out = nullptr;
+  CKR(b_smem_limits());
+  ipm_batch_t B = new ipm_batch_s();
+  auto fail = [&](int rc) {
+    ipm_batch_destroy(B);
+    return rc;
+  };
+  B->count = count;
+  B->opt = *opt;
+  if (!(B->opt.tau > 0)) B->opt.tau = B->opt.tol;
+  if (!(B->opt.mu0 > 0)) B->opt.mu0 = 0.1;
+  if (B->opt.max_refine < 0) B->opt.max_refine = 10;
+  B->stream = stream;
+  B->opf.assign(opfs, opfs + count);
+  // ---- one symbolic analysis per distinct pattern
+  {
+    std::map<std::vector<int>, int> seen;
+    std::vector<int> key;
+    B->pat.resize(count);
+    for (int i = 0; i < count; ++i) {
+      int rc = pattern_of(opfs[i]->M, key);
+      if (rc != IPM_OK) return fail(rc);
+      auto it = seen.find(key);
+      if (it != seen.end()) {
+        B->pat[i] = it->second;
+        continue;
+      }
+      const OpfData &M = opfs[i]->M;
+      ipm_sym_t S = nullptr;
+      rc = ipm_symbolic(M.n, M.me + M.mi, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr, M.W_colind,
+                        M.nnzW, stream, &S);
+      if (rc != IPM_OK) return fail(rc);
+      B->pat[i] = (int)B->syms.size();
+      B->syms.push_back(S);
+      seen.emplace(key, B->pat[i]);
+    }
+  }
+  // ---- sizes and pool layout
+  struct Off {
+    size_t x, s, y, z, v, zl, zu, grad, jtl, geq, hin, dscale, gs, hs, Jv, Wv, lam, lamw, f, fpart;
+    size_t sigma, r1, r2, r4, Ds, dcond, baug, a, dx, dzc, jdx, dz, ds, dv, dzl, dzu;
+    size_t xt, st, geqt, hint, gst, hst, ft, R, filter, tJ, Lx, Dx, y_s, t, cx, cz, outx, outz,
+        scal;
+    size_t sync, info;
+  };
+  std::vector<Off> off(count);
+  Bump dp, ip;
+  int max_elems = 1, max_ng = 1;
+  B->fmax_entries = 512;
+  for (int i = 0; i < count; ++i) max_ng = std::max(max_ng, opfs[i]->M.ng);
+  B->gx_gen = grid_for(max_ng, B_BLOCK);
+  for (int i = 0; i < count; ++i) {
+    const OpfData &M = opfs[i]->M;
+    ipm_sym_t S = B->syms[B->pat[i]];
+    const size_t n = M.n, me0 = M.me, mi0 = M.mi, m = me0 + mi0, mi = 2 * me0 + mi0;
+    Off &o = off[i];
+    o.x = dp.take(n); o.s = dp.take(mi); o.y = dp.take(1); o.z = dp.take(mi); o.v = dp.take(mi);
+    o.zl = dp.take(n); o.zu = dp.take(n); o.grad = dp.take(n); o.jtl = dp.take(n);
+    o.geq = dp.take(1); o.hin = dp.take(mi); o.dscale = dp.take(m); o.gs = dp.take(me0);
+    o.hs = dp.take(mi0); o.Jv = dp.take(M.nnzJ); o.Wv = dp.take(M.nnzW); o.lam = dp.take(m);
+    o.lamw = dp.take(m); o.f = dp.take(2); o.fpart = dp.take(B->gx_gen);
+    o.sigma = dp.take(n); o.r1 = dp.take(n); o.r2 = dp.take(mi); o.r4 = dp.take(mi);
+    o.Ds = dp.take(mi); o.dcond = dp.take(m); o.baug = dp.take(m); o.a = dp.take(n);
+    o.dx = dp.take(n); o.dzc = dp.take(m); o.jdx = dp.take(m); o.dz = dp.take(mi);
+    o.ds = dp.take(mi); o.dv = dp.take(mi); o.dzl = dp.take(n); o.dzu = dp.take(n);
+    o.xt = dp.take(n); o.st = dp.take(mi); o.geqt = dp.take(1); o.hint = dp.take(mi);
+    o.gst = dp.take(me0); o.hst = dp.take(mi0); o.ft = dp.take(2); o.R = dp.take(R_COUNT);
+    o.filter = dp.take(2 * (size_t)B->fmax_entries); o.tJ = dp.take(M.nnzJ);
+    o.Lx = dp.take(S->panel_len); o.Dx = dp.take(S->diag_len); o.y_s = dp.take(n);
+    o.t = dp.take(n); o.cx = dp.take(n); o.cz = dp.take(m); o.outx = dp.take(n);
+    o.outz = dp.take(m); o.scal = dp.take(8);
+    o.sync = ip.take(4 * (size_t)S->nsuper + 16);
+    o.info = ip.take(1);
+    max_elems = std::max({max_elems, M.n, (int)mi, (int)m, M.nnzJ, M.nnzW, 2 * M.nbr});
+    B->max_ns = std::max(B->max_ns, S->nsuper);
+  }
+  B->dpool_len = dp.n;
+  B->ipool_len = ip.n;
+  // about 8 elements per thread keep every instance's loop short without idle blocks
+  B->gx = std::max(1, std::min(grid_for(max_elems, B_BLOCK * 8), 64));
+  if (cudaMalloc(&B->dpool, sizeof(double) * B->dpool_len) != cudaSuccess ||
+      cudaMalloc(&B->ipool, sizeof(int) * B->ipool_len) != cudaSuccess) {
+    set_error_msg("ipm_batch_create: out of device memory for the instance pool");
+    return fail(IPM_ERR_OOM);
+  }
+  if (cudaMemset(B->dpool, 0, sizeof(double) * B->dpool_len) != cudaSuccess ||
+      cudaMemset(B->ipool, 0, sizeof(int) * B->ipool_len) != cudaSuccess)
+    return fail(IPM_ERR_CUDA);
+  // ---- descriptors, task-argument blocks and ticket ranges
+  std::vector<BI> hbi(count);
+  std::vector<FactTaskArgs<double>> hfa(count);
+  std::vector<SolveTaskArgs<double>> hfw(count), hbw(count);
+  std::vector<int> fstart(count + 1, 0), sstart(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    const OpfData &M = opfs[i]->M;
+    ipm_sym_t S = B->syms[B->pat[i]];
+    const Off &o = off[i];
+    double *d = B->dpool;
+    BI &I = hbi[i];
+    memset(&I, 0, sizeof(I));
+    I.D = Dims{M.n, M.me, M.mi, 0, 2 * M.me + M.mi, 1};
+    I.P.x = d + o.x; I.P.s = d + o.s; I.P.y = d + o.y; I.P.z = d + o.z; I.P.v = d + o.v;
+    I.P.zl = d + o.zl; I.P.zu = d + o.zu; I.P.xl = M.xl; I.P.xu = M.xu;
+    I.P.grad = d + o.grad; I.P.jtl = d + o.jtl; I.P.geq = d + o.geq; I.P.hin = d + o.hin;
+    I.SA.D = I.D;
+    I.SA.P = I.P;
+    I.SA.r2 = d + o.r2; I.SA.r4 = d + o.r4; I.SA.Ds = d + o.Ds; I.SA.jdx = d + o.jdx;
+    I.SA.dx = d + o.dx; I.SA.sigma = d + o.sigma; I.SA.dzH = nullptr;
+    I.SA.dz = d + o.dz; I.SA.ds = d + o.ds; I.SA.dv = d + o.dv; I.SA.dzl = d + o.dzl;
+    I.SA.dzu = d + o.dzu;
+    I.M = M;
+    I.m = M.me + M.mi;
+    I.dscale = d + o.dscale; I.gs = d + o.gs; I.hs = d + o.hs; I.Jv = d + o.Jv; I.Wv = d + o.Wv;
+    I.lam = d + o.lam; I.lamw = d + o.lamw; I.f = d + o.f; I.fpart = d + o.fpart;
+    I.r1 = d + o.r1; I.dcond = d + o.dcond; I.baug = d + o.baug; I.a = d + o.a; I.dx = d + o.dx;
+    I.dzc = d + o.dzc; I.xt = d + o.xt; I.st = d + o.st; I.geqt = d + o.geqt; I.hint = d + o.hint;
+    I.gst = d + o.gst; I.hst = d + o.hst; I.ft = d + o.ft; I.R = d + o.R; I.filter = d + o.filter;
+    I.sptr = S->sptr; I.srow_ptr = S->srow_ptr; I.slot_ptr = S->slot_ptr; I.perm = S->perm;
+    I.J_rowidx = S->J_rowidx; I.JT_ptr = S->JT_ptr; I.JT_ent = S->JT_ent; I.lptr = S->lptr;
+    I.items = S->items; I.ns = S->nsuper;
+    I.tJ = d + o.tJ; I.Lx = d + o.Lx; I.Dx = d + o.Dx;
+    I.sync = B->ipool + o.sync; I.info = B->ipool + o.info;
+    I.y = d + o.y_s; I.t = d + o.t; I.cx = d + o.cx; I.cz = d + o.cz; I.outx = d + o.outx;
+    I.outz = d + o.outz; I.scal = d + o.scal;
+    AugArgs &A = I.aug;
+    A.n = M.n; A.m = I.m; A.m_e = 0;
+    A.J_rowptr = S->J_rowptr; A.J_colind = S->J_colind; A.J_rowidx = S->J_rowidx;
+    A.JT_ptr = S->JT_ptr; A.JT_ent = S->JT_ent;
+    A.W_rowptr = S->W_rowptr; A.W_colind = S->W_colind; A.W_rowidx = S->W_rowidx;
+    A.WT_ptr = S->WT_ptr; A.WT_ent = S->WT_ent;
+    A.Wv = I.Wv; A.sigma = I.SA.sigma; A.Jv = I.Jv; A.d = I.dcond; A.dw = 0.0;
+    A.sx = I.dx; A.sz = I.dzc; A.ra = I.a; A.rb = I.baug; A.outx = I.outx; A.outz = I.outz;
+    A.scal = I.scal; A.want_norm_a = 1;
+    // the model pattern arrays of the handle and of the symbolic analysis are equal; the
+    // products use the model's (rows of J by row pointer), the symbolic's transposes
+    const int ns = S->nsuper;
+    int *tail = I.sync + 4 * ns;
+    FactTaskArgs<double> &F = hfa[i];
+    F.F = FactArgs<double>{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->snode, S->lptr,
+                           S->dptr, I.Lx, I.Dx, I.info};
+    F.tasks = S->ftasks;
+    F.ntasks = S->nftasks;
+    F.upd_need = S->upd_need;
+    F.C = SyncCtl{I.sync, nullptr, tail + 1, tail + 2};
+    F.ns = ns;
+    for (SolveTaskArgs<double> *T : {&hfw[i], &hbw[i]}) {
+      T->A = SolveArgs<double>{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr,
+                               I.Lx, I.Dx, I.y};
+      T->snode = S->snode;
+      T->fwd_need = S->fwd_need;
+      T->ns = ns;
+    }
+    hfw[i].C = SyncCtl{I.sync + 2 * ns, nullptr, tail + 1, tail + 2};
+    hbw[i].C = SyncCtl{I.sync + 3 * ns, nullptr, tail + 1, tail + 2};
+    fstart[i + 1] = fstart[i] + S->nftasks;
+    sstart[i + 1] = sstart[i] + ns;
+  }
+  int rc = IPM_OK;
+  auto up = [&](auto **dst, const auto &v) {
+    using T = std::remove_reference_t<decltype(v[0])>;
+    if (rc != IPM_OK) return;
+    if (cudaMalloc((void **)dst, sizeof(T) * v.size()) != cudaSuccess) {
+      rc = IPM_ERR_OOM;
+      return;
+    }
+    if (cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = IPM_ERR_CUDA;
+  };
+  up(&B->d_bi, hbi);
+  up(&B->d_fa, hfa);
+  up(&B->d_fw, hfw);
+  up(&B->d_bw, hbw);
+  up(&B->d_fstart, fstart);
+  up(&B->d_sstart, sstart);
+  if (rc == IPM_OK && cudaMalloc(&B->d_ctl, sizeof(BCtl) * count) != cudaSuccess) rc = IPM_ERR_OOM;
+  if (rc == IPM_OK && cudaMalloc(&B->d_tickets, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_OOM;
+  if (rc == IPM_OK && cudaMemset(B->d_tickets, 0, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_CUDA;
+  if (rc == IPM_OK && cudaMallocHost((void **)&B->h_active, sizeof(int)) != cudaSuccess) rc = IPM_ERR_OOM;
+  if (rc != IPM_OK) return fail(rc);
+  int max_w = 1;
+  for (ipm_sym_t S : B->syms) max_w = std::max(max_w, S->max_w);
+  B->fact_smem = sizeof(double) * std::max((size_t)max_w * max_w + (size_t)CIPM_RB * (max_w + 1),
+                                           2 * (size_t)CIPM_RB * (max_w + 1));
+  B->solve_smem = sizeof(double) * (size_t)max_w * max_w;
+  B->grid_fact = b_persistent_grid((const void *)k_b_factor<double>, 256, B->fact_smem);
+  B->grid_solve = b_persistent_grid((const void *)k_b_solve<double, true>, 128, B->solve_smem);
+  rc = init_instances(B);
+  if (rc == IPM_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = IPM_ERR_CUDA;
+  if (rc != IPM_OK) return fail(rc);
+  *out = B;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_info(ipm_batch_t B, int *npatterns, int64_t *device_bytes,
+                              int *launches_per_sweep) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  if (npatterns) *npatterns = (int)B->syms.size();
+  if (device_bytes)
+    *device_bytes = (int64_t)(sizeof(double) * B->dpool_len + sizeof(int) * B->ipool_len);
+  if (launches_per_sweep) *launches_per_sweep = B->launches_per_sweep;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_reset(ipm_batch_t B) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  CKR(init_instances(B));
+  B->sweeps = 0;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int use_graph) {
+  if (!B || max_iter < 0 || max_sweeps < 1) return IPM_ERR_BAD_ARG;
+  cudaStream_t s = B->stream;
+  if (B->max_iter != max_iter && B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+  }
+  B->max_iter = max_iter;
+  if (use_graph && !B->exec) {
+    // sweeps are captured on a private stream: legacy default streams cannot be captured
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = IPM_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = IPM_ERR_CUDA;
+    if (rc == IPM_OK) rc = enqueue_sweep(B, cs);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess && rc == IPM_OK) rc = IPM_ERR_CUDA;
+    cudaStreamDestroy(cs);
+    if (rc != IPM_OK) {
+      if (g) cudaGraphDestroy(g);
+      set_error_msg("ipm_batch_run: capturing the sweep failed");
+      return rc;
+    }
+    B->graph = g;
+    CK(cudaGraphInstantiate(&B->exec, g, 0));
+  }
+  int rc = IPM_OK;
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    if (use_graph) {
+      CK(cudaGraphLaunch(B->exec, s));
+    } else {
+      CKR(enqueue_sweep(B, s));
+    }
+    count_launches(B->launches_per_sweep);
+    ++B->sweeps;
+    CK(cudaStreamSynchronize(s));
+    if (*B->h_active == 0) break;
+  }
+  k_b_finish_unfinished<<<grid_for(B->count, 128), 128, 0, s>>>(B->d_ctl, B->count);
+  count_launches(1);
+  CKL();
+  CK(cudaStreamSynchronize(s));
+  return rc;
+}
+
+extern "C" int ipm_batch_results(ipm_batch_t B, int *status, int *iters, double *obj,
+                                 double *kkt_err, int *n_factor, int *ls_steps) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  std::vector<BCtl> h(B->count);
+  CK(cudaMemcpy(h.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < B->count; ++i) {
+    if (status) status[i] = h[i].status;
+    if (iters) iters[i] = h[i].k;
+    if (obj) obj[i] = h[i].obj;
+    if (kkt_err) kkt_err[i] = h[i].e0;
+    if (n_factor) n_factor[i] = h[i].total_fac;
+    if (ls_steps) ls_steps[i] = h[i].total_ls;
+  }
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_export(ipm_batch_t B, int i, double *x) {
+  if (!B || i < 0 || i >= B->count || !x) return IPM_ERR_BAD_ARG;
+  BI h;
+  CK(cudaMemcpy(&h, B->d_bi + i, sizeof(BI), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(x, h.P.x, sizeof(double) * h.D.n, cudaMemcpyDeviceToHost));
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_sweeps(ipm_batch_t B) { return B ? B->sweeps : 0; }
+
+extern "C" void ipm_batch_destroy(ipm_batch_t B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (ipm_sym_t S : B->syms) ipm_symbolic_destroy(S);
+  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_fa, B->d_fw, B->d_bw,
+                B->d_fstart, B->d_sstart, B->d_tickets};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  if (B->h_active) cudaFreeHost(B->h_active);
+  delete B;
+}
+
+// the batched kernels keep their own copy of the spin limit
+int batch_set_spin_limit(long long polls) {
+  CK(cudaMemcpyToSymbol(g_spin_limit, &polls, sizeof(polls)));
+  return IPM_OK;
+}

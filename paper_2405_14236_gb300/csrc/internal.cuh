@@ -74,3 +74,6 @@ struct ipm_num_s {
   double *scal = nullptr;  // device scalars
   double *h_scal = nullptr;  // pinned host mirror
 };
+
+// the batched kernels (batch.cu) keep their own copy of the device spin limit
+int batch_set_spin_limit(long long polls);

@@ -16,63 +16,10 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "ipm_core.cuh"
 #include "opf.cuh"
 
 namespace cipm {
-
-static constexpr double KAPPA1 = 1e-2, KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5;
-static constexpr double TAU_MIN = 0.99, S_MAX = 100.0, GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-8;
-static constexpr double S_THETA = 1.1, S_PHI = 2.3, DELTA_SW = 1.0, ETA_PHI = 1e-8;
-static constexpr double GAMMA_ALPHA = 0.05, KAPPA_SIGMA = 1e10;
-
-// ------------------------------------------------------------------ reductions into R[]
-enum {
-  R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_MAX_SV, R_MAX_XL, R_MAX_XU,  // max |.|
-  R_SUM_Y, R_SUM_Z, R_SUM_V, R_SUM_ZL, R_SUM_ZU,                        // sums |.|
-  R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU,                          // theta / phi parts
-  R_GPHI_X, R_GPHI_S,                                                    // d phi
-  R_AMAX, R_AZ,                                                          // step bounds (min)
-  R_PD, R_QD, R_MAXGRAD,                                                 // set-up
-  R_COUNT
-};
-
-__device__ __forceinline__ void amax_nonneg(double *a, double v) {
-  atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
-}
-__device__ __forceinline__ void amin_nonneg(double *a, double v) {
-  atomicMin((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
-}
-__device__ __forceinline__ double wmax(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double wmin(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double wsum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-// warp-level reduce then one atomic per warp (every lane of the warp must call)
-__device__ __forceinline__ void red_max(double *R, int k, double v) {
-  v = wmax(v);
-  if ((threadIdx.x & 31) == 0) amax_nonneg(R + k, v);
-}
-__device__ __forceinline__ void red_min(double *R, int k, double v) {
-  v = wmin(v);
-  if ((threadIdx.x & 31) == 0) amin_nonneg(R + k, v);
-}
-__device__ __forceinline__ void red_sum(double *R, int k, double v) {
-  v = wsum(v);
-  if ((threadIdx.x & 31) == 0) atomicAdd(R + k, v);
-}
-
-struct Dims {
-  int n, me0, mi0;  // model sizes: variables, equality rows g, inequality rows h
-  int me, mi;       // IPM sizes: equality rows (HyKKT: me0, Lifted: 0), slack rows
-  int lifted;
-};
 
 // ------------------------------------------------------------------ set-up kernels
 __global__ void k_setup_sums(int nb, const double *pd, const double *qd, double *R) {
@@ -82,36 +29,21 @@ __global__ void k_setup_sums(int nb, const double *pd, const double *qd, double 
   red_sum(R, R_QD, b);
 }
 
-// flat start (|V| = 1, theta = 0, generators share the load equally), pushed inside the bounds
 __global__ void k_x0(int nb, int ng, const double *R, const double *xl, const double *xu,
                      double *x) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int n = 2 * nb + 2 * ng;
-  if (j >= n) return;
-  double v;
-  if (j < nb) v = 1.0;
-  else if (j < 2 * nb) v = 0.0;
-  else if (j < 2 * nb + ng) v = fmin(fmax(R[R_PD] / ng, xl[j]), xu[j]);
-  else v = fmin(fmax(R[R_QD] / ng, xl[j]), xu[j]);
-  const bool hl = isfinite(xl[j]), hu = isfinite(xu[j]);
-  double pl = hl ? KAPPA1 * fmax(1.0, fabs(xl[j])) : 0.0;
-  double pu = hu ? KAPPA1 * fmax(1.0, fabs(xu[j])) : 0.0;
-  if (hl && hu) {
-    pl = fmin(pl, KAPPA1 * (xu[j] - xl[j]));
-    pu = fmin(pu, KAPPA1 * (xu[j] - xl[j]));
-  }
-  if (hl) v = fmax(v, xl[j] + pl);
-  if (hu) v = fmin(v, xu[j] - pu);
-  x[j] = v;
+  if (j < 2 * nb + 2 * ng) x[j] = x0_at(nb, ng, R[R_PD], R[R_QD], xl, xu, j);
 }
 
 // row scale d_r = min(1, 100 / max_j |J_rj|) (Ipopt gradient-based scaling)
-__global__ void k_row_scale(int m, const int *rowptr, const double *Jv, double *d) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= m) return;
+__device__ __forceinline__ double row_scale_at(const int *rowptr, const double *Jv, int r) {
   double mx = 0.0;
   for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) mx = fmax(mx, fabs(Jv[p]));
-  d[r] = mx > 0.0 ? fmin(1.0, 100.0 / mx) : 1.0;
+  return mx > 0.0 ? fmin(1.0, 100.0 / mx) : 1.0;
+}
+__global__ void k_row_scale(int m, const int *rowptr, const double *Jv, double *d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < m) d[r] = row_scale_at(rowptr, Jv, r);
 }
 
 __global__ void k_max_abs(int n, const double *v, double *R, int k) {
@@ -131,28 +63,13 @@ __global__ void k_scale_vec(int n, const double *d, double *v) {
   if (i < n) v[i] *= d[i];
 }
 
-// IPM constraint values from the scaled model: HyKKT  g' = g~, h' = h~;
-// Lifted  h' = [g~ - tau ; -g~ - tau ; h~]
 __global__ void k_ipm_rows(Dims D, double tau, const double *gs, const double *hs, double *geq,
                            double *hin) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (D.lifted) {
-    if (k < D.me0) {
-      hin[k] = gs[k] - tau;
-      hin[D.me0 + k] = -gs[k] - tau;
-    }
-    if (k < D.mi0) hin[2 * D.me0 + k] = hs[k];
-  } else {
-    if (k < D.me0) geq[k] = gs[k];
-    if (k < D.mi0) hin[k] = hs[k];
-  }
+  ipm_rows_at(D, tau, gs, hs, geq, hin, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// multipliers of the model rows: lambda = [lambda_g ; lambda_h] (unscaled-row weights)
 __global__ void k_lambda(Dims D, const double *y, const double *z, double *lam) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < D.me0) lam[k] = D.lifted ? z[k] - z[D.me0 + k] : y[k];
-  if (k < D.mi0) lam[D.me0 + k] = D.lifted ? z[2 * D.me0 + k] : z[k];
+  lambda_at(D, y, z, lam, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_mul(int n, const double *a, const double *b, double *out) {
@@ -161,145 +78,67 @@ __global__ void k_mul(int n, const double *a, const double *b, double *out) {
 }
 
 // out_j = sum_p J~_pj u_row(p) (J^T u)
-__global__ void k_jtu(int n, const int *JT_ptr, const int *JT_ent, const int *rowidx,
-                      const double *Jv, const double *u, double *out) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+__device__ __forceinline__ double jtu_at(const int *JT_ptr, const int *JT_ent, const int *rowidx,
+                                         const double *Jv, const double *u, int j) {
   double acc = 0.0;
   for (int t = JT_ptr[j]; t < JT_ptr[j + 1]; ++t) {
     int p = JT_ent[t];
     acc += Jv[p] * u[rowidx[p]];
   }
-  out[j] = acc;
+  return acc;
+}
+__global__ void k_jtu(int n, const int *JT_ptr, const int *JT_ent, const int *rowidx,
+                      const double *Jv, const double *u, double *out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = jtu_at(JT_ptr, JT_ent, rowidx, Jv, u, j);
 }
 // out_r = (J~ v)_r
+__device__ __forceinline__ double jv_at(const int *rowptr, const int *colind, const double *Jv,
+                                        const double *v, int r) {
+  double acc = 0.0;
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += Jv[p] * v[colind[p]];
+  return acc;
+}
 __global__ void k_jv(int m, const int *rowptr, const int *colind, const double *Jv,
                      const double *v, double *out) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= m) return;
-  double acc = 0.0;
-  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += Jv[p] * v[colind[p]];
-  out[r] = acc;
+  if (r < m) out[r] = jv_at(rowptr, colind, Jv, v, r);
 }
 
-struct It {  // device pointers of the iterate and work vectors
-  double *x, *s, *y, *z, *v, *zl, *zu;
-  double *xl, *xu;
-  double *grad, *jtl;  // grad f, J~^T lambda
-  double *geq, *hin;   // IPM rows
-};
-
-// optimality error parts (Ipopt E_mu): maxima and 1-norm sums
 __global__ void k_errors(Dims D, It P, double sig, double mu, double *R) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double gl = 0, xl_c = 0, xu_c = 0, szl = 0, szu = 0;
-  if (i < D.n) {
-    double x = P.x[i];
-    gl = fabs(sig * P.grad[i] + P.jtl[i] - P.zl[i] + P.zu[i]);
-    if (isfinite(P.xl[i])) xl_c = fabs((x - P.xl[i]) * P.zl[i] - mu);
-    if (isfinite(P.xu[i])) xu_c = fabs((P.xu[i] - x) * P.zu[i] - mu);
-    szl = fabs(P.zl[i]);
-    szu = fabs(P.zu[i]);
-  }
-  double zv = 0, hs = 0, sv = 0, sz = 0, svv = 0;
-  if (i < D.mi) {
-    zv = fabs(P.z[i] - P.v[i]);
-    hs = fabs(P.hin[i] + P.s[i]);
-    sv = fabs(P.s[i] * P.v[i] - mu);
-    sz = fabs(P.z[i]);
-    svv = fabs(P.v[i]);
-  }
-  double ge = 0, sy = 0;
-  if (i < D.me) {
-    ge = fabs(P.geq[i]);
-    sy = fabs(P.y[i]);
-  }
-  red_max(R, R_MAX_GL, gl);
-  red_max(R, R_MAX_ZV, zv);
-  red_max(R, R_MAX_G, ge);
-  red_max(R, R_MAX_HS, hs);
-  red_max(R, R_MAX_SV, sv);
-  red_max(R, R_MAX_XL, xl_c);
-  red_max(R, R_MAX_XU, xu_c);
-  red_sum(R, R_SUM_Y, sy);
-  red_sum(R, R_SUM_Z, sz);
-  red_sum(R, R_SUM_V, svv);
-  red_sum(R, R_SUM_ZL, szl);
-  red_sum(R, R_SUM_ZU, szu);
+  const ErrParts E = errors_at(D, P, sig, mu, blockIdx.x * blockDim.x + threadIdx.x);
+  red_max(R, R_MAX_GL, E.gl);
+  red_max(R, R_MAX_ZV, E.zv);
+  red_max(R, R_MAX_G, E.ge);
+  red_max(R, R_MAX_HS, E.hs);
+  red_max(R, R_MAX_SV, E.sv);
+  red_max(R, R_MAX_XL, E.xl);
+  red_max(R, R_MAX_XU, E.xu);
+  red_sum(R, R_SUM_Y, E.sy);
+  red_sum(R, R_SUM_Z, E.sz);
+  red_sum(R, R_SUM_V, E.svv);
+  red_sum(R, R_SUM_ZL, E.szl);
+  red_sum(R, R_SUM_ZU, E.szu);
 }
 
-// theta and phi parts at (x, s) with constraint rows geq/hin
 __global__ void k_merit(Dims D, const double *x, const double *s, const double *xl,
                         const double *xu, const double *geq, const double *hin, double *R) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double tg = 0, th = 0, ls = 0, lxl = 0, lxu = 0;
-  if (i < D.me) tg = fabs(geq[i]);
-  if (i < D.mi) {
-    th = fabs(hin[i] + s[i]);
-    ls = log(s[i]);
-  }
-  if (i < D.n) {
-    if (isfinite(xl[i])) lxl = log(x[i] - xl[i]);
-    if (isfinite(xu[i])) lxu = log(xu[i] - x[i]);
-  }
-  red_sum(R, R_TH_G, tg);
-  red_sum(R, R_TH_H, th);
-  red_sum(R, R_LOG_S, ls);
-  red_sum(R, R_LOG_XL, lxl);
-  red_sum(R, R_LOG_XU, lxu);
+  const MeritParts M = merit_at(D, x, s, xl, xu, geq, hin, blockIdx.x * blockDim.x + threadIdx.x);
+  red_sum(R, R_TH_G, M.tg);
+  red_sum(R, R_TH_H, M.th);
+  red_sum(R, R_LOG_S, M.ls);
+  red_sum(R, R_LOG_XL, M.lxl);
+  red_sum(R, R_LOG_XU, M.lxu);
 }
 
-// Newton right-hand sides and diagonals:
-//   sigma_x = zl/(x-xl) + zu/(xu-x); r1 = sig grad + J~^T lambda - mu/(x-xl) + mu/(xu-x)
-//   r2 = z - mu/s; r4 = h' + s; Ds = v/s
 __global__ void k_newton_rhs(Dims D, It P, double sig, double mu, double *sigma, double *r1,
                              double *r2, double *r4, double *Ds) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D.n) {
-    double sx = 0.0, r = sig * P.grad[i] + P.jtl[i];
-    if (isfinite(P.xl[i])) {
-      double dl = P.x[i] - P.xl[i];
-      sx += P.zl[i] / dl;
-      r -= mu / dl;
-    }
-    if (isfinite(P.xu[i])) {
-      double du = P.xu[i] - P.x[i];
-      sx += P.zu[i] / du;
-      r += mu / du;
-    }
-    sigma[i] = sx;
-    r1[i] = r;
-  }
-  if (i < D.mi) {
-    r2[i] = P.z[i] - mu / P.s[i];
-    r4[i] = P.hin[i] + P.s[i];
-    Ds[i] = P.v[i] / P.s[i];
-  }
+  newton_rhs_at(D, P, sig, mu, sigma, r1, r2, r4, Ds, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// weights d and right-hand side b of the augmented system over the model rows [G; H]
-//   Lifted: G rows combine the relaxed pair (D1 = Ds_a + dw, D2 = Ds_b + dw):
-//           d = D1 + D2, b = (-D1 r4a + r2a + D2 r4b - r2b) / d;  H rows d = Ds + dw, b = -r4 + r2/d
-//   HyKKT:  G rows d = gamma, b = -r3;  H rows as above
 __global__ void k_aug_rhs(Dims D, double dw, double gamma, const double *r2, const double *r4,
                           const double *Ds, const double *geq, double *d, double *b) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < D.me0) {
-    if (D.lifted) {
-      double d1 = Ds[k] + dw, d2 = Ds[D.me0 + k] + dw;
-      d[k] = d1 + d2;
-      b[k] = (-d1 * r4[k] + r2[k] + d2 * r4[D.me0 + k] - r2[D.me0 + k]) / (d1 + d2);
-    } else {
-      d[k] = gamma;
-      b[k] = -geq[k];
-    }
-  }
-  if (k < D.mi0) {
-    int ip = D.lifted ? 2 * D.me0 + k : k;
-    double dh = Ds[ip] + dw;
-    d[D.me0 + k] = dh;
-    b[D.me0 + k] = -r4[ip] + r2[ip] / dh;
-  }
+  aug_rhs_at(D, dw, gamma, r2, r4, Ds, geq, d, b, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_neg(int n, const double *a, double *out) {
@@ -307,135 +146,28 @@ __global__ void k_neg(int n, const double *a, double *out) {
   if (i < n) out[i] = -a[i];
 }
 
-// recover dz over the IPM slack rows from J~ dx (jdx over model rows) and ds, dv, dzl, dzu
-struct StepArgs {
-  Dims D;
-  It P;
-  double mu, dw;
-  const double *r2, *r4, *Ds, *jdx, *dx, *sigma;
-  const double *dzH;  // HyKKT: dz over H rows (from hykkt_cg)
-  double *dz, *ds, *dv, *dzl, *dzu;
-};
-__global__ void k_recover(StepArgs A) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const Dims &D = A.D;
-  if (i < D.mi) {
-    double dz;
-    if (D.lifted) {
-      double dh = A.Ds[i] + A.dw;
-      double hdx = i < D.me0 ? A.jdx[i] : (i < 2 * D.me0 ? -A.jdx[i - D.me0] : A.jdx[i - D.me0]);
-      dz = -A.r2[i] + dh * (hdx + A.r4[i]);
-    } else {
-      dz = A.dzH[i];
-    }
-    A.dz[i] = dz;
-    double ds = -(A.r2[i] + dz) / (A.Ds[i] + A.dw);
-    A.ds[i] = ds;
-    A.dv[i] = (A.mu - A.P.v[i] * ds) / A.P.s[i] - A.P.v[i];
-  }
-  if (i < D.n) {
-    double dx = A.dx[i];
-    if (isfinite(A.P.xl[i])) {
-      double dl = A.P.x[i] - A.P.xl[i];
-      A.dzl[i] = A.mu / dl - A.P.zl[i] - A.P.zl[i] / dl * dx;
-    } else {
-      A.dzl[i] = 0.0;
-    }
-    if (isfinite(A.P.xu[i])) {
-      double du = A.P.xu[i] - A.P.x[i];
-      A.dzu[i] = A.mu / du - A.P.zu[i] + A.P.zu[i] / du * dx;
-    } else {
-      A.dzu[i] = 0.0;
-    }
-  }
-}
+__global__ void k_recover(StepArgs A) { recover_at(A, blockIdx.x * blockDim.x + threadIdx.x); }
 
-// fraction to the boundary (min over ratios) and the directional derivative of phi
 __global__ void k_ftb(StepArgs A, double tau, double sig, double *R) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const Dims &D = A.D;
-  double ap = 1.0, az = 1.0, gx = 0.0, gs = 0.0;
-  if (i < D.n) {
-    double x = A.P.x[i], dx = A.dx[i];
-    gx = sig * A.P.grad[i] * dx;
-    if (isfinite(A.P.xl[i])) {
-      double dl = x - A.P.xl[i];
-      if (dx < 0) ap = fmin(ap, -tau * dl / dx);
-      if (A.dzl[i] < 0) az = fmin(az, -tau * A.P.zl[i] / A.dzl[i]);
-      gx -= A.mu * dx / dl;
-    }
-    if (isfinite(A.P.xu[i])) {
-      double du = A.P.xu[i] - x;
-      if (dx > 0) ap = fmin(ap, tau * du / dx);
-      if (A.dzu[i] < 0) az = fmin(az, -tau * A.P.zu[i] / A.dzu[i]);
-      gx += A.mu * dx / du;
-    }
-  }
-  if (i < D.mi) {
-    if (A.ds[i] < 0) ap = fmin(ap, -tau * A.P.s[i] / A.ds[i]);
-    if (A.dv[i] < 0) az = fmin(az, -tau * A.P.v[i] / A.dv[i]);
-    gs = -A.mu * A.ds[i] / A.P.s[i];
-  }
-  red_min(R, R_AMAX, ap);
-  red_min(R, R_AZ, az);
-  red_sum(R, R_GPHI_X, gx);
-  red_sum(R, R_GPHI_S, gs);
+  const FtbParts F = ftb_at(A, tau, sig, blockIdx.x * blockDim.x + threadIdx.x);
+  red_min(R, R_AMAX, F.ap);
+  red_min(R, R_AZ, F.az);
+  red_sum(R, R_GPHI_X, F.gx);
+  red_sum(R, R_GPHI_S, F.gs);
 }
 
 __global__ void k_trial(int n, int mi, double a, const double *x, const double *dx,
                         const double *s, const double *ds, double *xt, double *st) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) xt[i] = x[i] + a * dx[i];
-  if (i < mi) st[i] = s[i] + a * ds[i];
+  trial_at(n, mi, a, x, dx, s, ds, xt, st, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// accept the step: primal (x, s from the trial), y, z with alpha, bound duals with alpha_z, then
-// the bound-multiplier safeguard kappa_Sigma
 __global__ void k_accept(StepArgs A, double alpha, double az, const double *xt, const double *st,
                          const double *dy) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const Dims &D = A.D;
-  const double mu = A.mu;
-  if (i < D.n) {
-    double x = xt[i];
-    A.P.x[i] = x;
-    if (isfinite(A.P.xl[i])) {
-      double dl = x - A.P.xl[i];
-      double zl = A.P.zl[i] + az * A.dzl[i];
-      A.P.zl[i] = fmin(fmax(zl, mu / (KAPPA_SIGMA * dl)), KAPPA_SIGMA * mu / dl);
-    } else {
-      A.P.zl[i] = 0.0;
-    }
-    if (isfinite(A.P.xu[i])) {
-      double du = A.P.xu[i] - x;
-      double zu = A.P.zu[i] + az * A.dzu[i];
-      A.P.zu[i] = fmin(fmax(zu, mu / (KAPPA_SIGMA * du)), KAPPA_SIGMA * mu / du);
-    } else {
-      A.P.zu[i] = 0.0;
-    }
-  }
-  if (i < D.mi) {
-    double s = st[i];
-    A.P.s[i] = s;
-    A.P.z[i] += alpha * A.dz[i];
-    double v = A.P.v[i] + az * A.dv[i];
-    A.P.v[i] = fmin(fmax(v, mu / (KAPPA_SIGMA * s)), KAPPA_SIGMA * mu / s);
-  }
-  if (i < D.me) A.P.y[i] += alpha * dy[i];
+  accept_at(A, alpha, az, xt, st, dy, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_init_duals(Dims D, It P, double *s) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D.mi) {
-    s[i] = fmax(-P.hin[i], KAPPA1);
-    P.z[i] = 1.0;
-    P.v[i] = 1.0;
-  }
-  if (i < D.me) P.y[i] = 0.0;
-  if (i < D.n) {
-    P.zl[i] = isfinite(P.xl[i]) ? 1.0 : 0.0;
-    P.zu[i] = isfinite(P.xu[i]) ? 1.0 : 0.0;
-  }
+  init_duals_at(D, P, s, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 }  // namespace cipm
@@ -531,15 +263,7 @@ static int errors(ipm_state_t S, double mu, double *out) {
   CKL();
   CKR(read_R(S));
   const double *h = S->hR;
-  const Dims &D = S->D;
-  double sd = std::max(S_MAX, (h[R_SUM_Y] + h[R_SUM_Z] + h[R_SUM_V] + h[R_SUM_ZL] + h[R_SUM_ZU]) /
-                                  std::max(D.me + 2 * D.mi + S->nl + S->nu, 1)) / S_MAX;
-  double sc = std::max(S_MAX, (h[R_SUM_V] + h[R_SUM_ZL] + h[R_SUM_ZU]) /
-                                  std::max(D.mi + S->nl + S->nu, 1)) / S_MAX;
-  double dual = std::max(h[R_MAX_GL], h[R_MAX_ZV]) / sd;
-  double prim = std::max(h[R_MAX_G], h[R_MAX_HS]);
-  double comp = std::max({h[R_MAX_SV], h[R_MAX_XL], h[R_MAX_XU]}) / sc;
-  *out = std::max({dual, prim, comp});
+  *out = kkt_error(h, S->D, S->nl, S->nu, std::max({h[R_MAX_SV], h[R_MAX_XL], h[R_MAX_XU]}));
   return IPM_OK;
 }
 
@@ -788,7 +512,7 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     info->precision = num == S->num32 ? 32 : 64;
     break;
   }
-  if (!ok) return IPM_ERR_NOT_PD;
+  if (!ok) return IPM_ERR_INERTIA;
   if (dw > 0) S->delta_last = dw;
   info->delta_w = dw;
   info->n_factor = nfac;

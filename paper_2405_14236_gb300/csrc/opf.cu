@@ -11,34 +11,18 @@
 
 #include "internal.cuh"
 #include "opf.cuh"
+#include "opf_dev.cuh"
 
 namespace cipm {
 
-static constexpr double BASE = 100.0;
 static constexpr int SORT_CAP2 = 1024;
 
 // --- pattern construction: every model term lists its (row, col) coordinates in a fixed
 // order; rows are then sorted/uniqued and each term records the entry it writes.
-struct OpfDims {
-  int nb, nbr, ng, n, me, mi;
-};
-
 // J terms: per gen 2, per branch end 12 (4 P-balance, 4 Q-balance, 4 thermal), theta_ref 1
 __device__ __forceinline__ int jterm_count(const OpfDims &D) { return 2 * D.ng + 24 * D.nbr + 1; }
 // W terms: per gen 1, per branch end 10 (lower 4x4 block)
 __device__ __forceinline__ int wterm_count(const OpfDims &D) { return D.ng + 20 * D.nbr; }
-
-__device__ __forceinline__ void end_vars(const OpfDims &D, const int *f_bus, const int *t_bus,
-                                         int e, int *bus, int *vars) {
-  int k = e % D.nbr;
-  bool to = e >= D.nbr;
-  int a = to ? t_bus[k] : f_bus[k], b = to ? f_bus[k] : t_bus[k];
-  *bus = a;
-  vars[0] = a;           // Va
-  vars[1] = b;           // Vb
-  vars[2] = D.nb + a;    // theta_a
-  vars[3] = D.nb + b;    // theta_b
-}
 
 __device__ __forceinline__ void jterm(const OpfDims &D, const int *f_bus, const int *t_bus,
                                       const int *gen_bus, int ref, int t, int *row, int *col) {
@@ -68,9 +52,6 @@ __device__ __forceinline__ void jterm(const OpfDims &D, const int *f_bus, const 
   *row = 2 * D.nb;
   *col = D.nb + ref;
 }
-
-__device__ __constant__ int c_lowpairs[10][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1},
-                                                 {2, 2}, {3, 0}, {3, 1}, {3, 2}, {3, 3}};
 
 __device__ __forceinline__ void wterm(const OpfDims &D, const int *f_bus, const int *t_bus, int t,
                                       int *row, int *col) {
@@ -190,111 +171,29 @@ __global__ void k_branch_admittance(int nbr, const double *r, const double *x, c
 
 __global__ void k_eval_init(OpfDims D, const double *pd, const double *qd, const double *x,
                             int ref, double *g, double *Jv, int nnzJ, double *Wv, int nnzW) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D.nb) {
-    g[i] = -pd[i];
-    g[D.nb + i] = -qd[i];
-  }
-  if (i == 0) g[2 * D.nb] = x[D.nb + ref];
-  if (Jv)
-    for (int p = i; p < nnzJ; p += gridDim.x * blockDim.x) Jv[p] = 0.0;
-  if (Wv)
-    for (int p = i; p < nnzW; p += gridDim.x * blockDim.x) Wv[p] = 0.0;
+  eval_init_at(D, pd, qd, x, ref, g, Jv, nnzJ, Wv, nnzW, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
 }
 
 // one thread per branch end
 __global__ void k_eval_branch(OpfDims D, OpfData M, const double *x, const double *y,
                               const double *z, double *g, double *h, double *Jv, double *Wv) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 2 * D.nbr) return;
-  int k = e % D.nbr;
-  int bus, v[4];
-  end_vars(D, M.f_bus, M.t_bus, e, &bus, v);
-  double4_32a ad = M.adm[k];
-  const double G1 = ad.x, B1 = ad.y, G2 = ad.z, B2 = ad.w;
-  const double Va = x[v[0]], Vb = x[v[1]], ta = x[v[2]], tb = x[v[3]];
-  double sn, cs;
-  sincos(ta - tb, &sn, &cs);
-  const double A = G2 * cs + B2 * sn, Bq = G2 * sn - B2 * cs;
-  const double P = G1 * Va * Va + Va * Vb * A;
-  const double Q = -B1 * Va * Va + Va * Vb * Bq;
-  double dP[4] = {2 * G1 * Va + Vb * A, Va * A, -Va * Vb * Bq, Va * Vb * Bq};
-  double dQ[4] = {-2 * B1 * Va + Vb * Bq, Va * Bq, Va * Vb * A, -Va * Vb * A};
-  // lower-triangle second derivatives in the order of c_lowpairs
-  double hP[10] = {2 * G1, A, 0.0, -Vb * Bq, -Va * Bq, -Va * Vb * A, Vb * Bq, Va * Bq, Va * Vb * A,
-                   -Va * Vb * A};
-  double hQ[10] = {-2 * B1, Bq, 0.0, Vb * A, Va * A, -Va * Vb * Bq, -Vb * A, -Va * A, Va * Vb * Bq,
-                   -Va * Vb * Bq};
-  atomicAdd(&g[bus], -P);
-  atomicAdd(&g[D.nb + bus], -Q);
-  const int hrow = e;
-  const double rt = M.rate[k];
-  h[hrow] = P * P + Q * Q - rt * rt;
-  if (Jv) {
-    const int *je = M.jentry + 2 * D.ng + 12 * e;
-    for (int c = 0; c < 4; ++c) {
-      atomicAdd(&Jv[je[c]], -dP[c]);
-      atomicAdd(&Jv[je[4 + c]], -dQ[c]);
-      Jv[je[8 + c]] = 2 * P * dP[c] + 2 * Q * dQ[c];
-    }
-  }
-  if (Wv) {
-    const double yP = y[bus], yQ = y[D.nb + bus], zz = z[hrow];
-    const int *we = M.wentry + D.ng + 10 * e;
-    for (int t = 0; t < 10; ++t) {
-      int a = c_lowpairs[t][0], b = c_lowpairs[t][1];
-      double hh = 2 * (dP[a] * dP[b] + P * hP[t] + dQ[a] * dQ[b] + Q * hQ[t]);
-      atomicAdd(&Wv[we[t]], -yP * hP[t] - yQ * hQ[t] + zz * hh);
-    }
-  }
+  if (e < 2 * D.nbr) eval_branch_at(D, M, x, y, z, g, h, Jv, Wv, e);
 }
 
 __global__ void k_eval_gen(OpfDims D, OpfData M, const double *x, double sigma_f, double *g,
                            double *grad, double *Jv, double *Wv, double *fpart) {
   __shared__ double sh[32];
   int gi = blockIdx.x * blockDim.x + threadIdx.x;
-  double fc = 0.0;
-  if (gi < D.ng) {
-    int bus = M.gen_bus[gi];
-    double pg = x[2 * D.nb + gi], qg = x[2 * D.nb + D.ng + gi];
-    atomicAdd(&g[bus], pg);
-    atomicAdd(&g[D.nb + bus], qg);
-    if (Jv) {
-      Jv[M.jentry[2 * gi]] = 1.0;
-      Jv[M.jentry[2 * gi + 1]] = 1.0;
-    }
-    double pm = pg * BASE;
-    fc = M.c2[gi] * pm * pm + M.c1[gi] * pm;
-    if (grad) {
-      grad[2 * D.nb + gi] = BASE * (2 * M.c2[gi] * pm + M.c1[gi]);
-      grad[2 * D.nb + D.ng + gi] = 0.0;
-    }
-    if (Wv) atomicAdd(&Wv[M.wentry[gi]], sigma_f * 2 * M.c2[gi] * BASE * BASE);
-  }
-  fc = warp_sum(fc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = fc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) fpart[blockIdx.x] = v;
-  }
+  double fc = gi < D.ng ? eval_gen_at(D, M, x, sigma_f, g, grad, Jv, Wv, gi) : 0.0;
+  block_sum_to(fpart + blockIdx.x, fc, sh);
 }
 
 __global__ void k_eval_finish(OpfDims D, OpfData M, const double *fpart, int nparts, double *f,
                               double *grad, double *Jv) {
-  // theta_ref row entry and the zero gradient on V and theta
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (grad)
-    for (int k = i; k < 2 * D.nb; k += gridDim.x * blockDim.x) grad[k] = 0.0;
-  if (i == 0) {
-    if (Jv) Jv[M.jentry[2 * D.ng + 24 * D.nbr]] = 1.0;
-    if (f) {
-      double s = 0.0;
-      for (int p = 0; p < nparts; ++p) s += fpart[p];
-      *f = s;
-    }
-  }
+  eval_finish_at(D, M, fpart, nparts, f, grad, Jv, blockIdx.x * blockDim.x + threadIdx.x,
+                 gridDim.x * blockDim.x);
 }
 
 int opf_eval(const OpfData &M, const double *x, const double *y, const double *z, double sigma_f,

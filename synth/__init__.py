@@ -4,8 +4,8 @@ This package only draws random numbers and builds grid topologies and
 parameters; it holds none of the interior-point or KKT arithmetic.  Both the
 CPU oracle and the CUDA path consume what it produces.
 """
-from .grid import (Grid, make_grid, ring_grid, planar_grid, scale_loads,
+from .grid import (Grid, make_grid, ring_grid, planar_grid, scale_loads, mixed_grid, batch_grids,
                    kkt_point, CONFIGS, config_grid)
 
-__all__ = ["Grid", "make_grid", "ring_grid", "planar_grid", "scale_loads",
+__all__ = ["Grid", "make_grid", "ring_grid", "planar_grid", "scale_loads", "mixed_grid", "batch_grids",
            "kkt_point", "CONFIGS", "config_grid"]

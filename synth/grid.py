@@ -210,6 +210,22 @@ def config_grid(name: str) -> Grid:
     return make_grid(c["nb"], c["seed"])
 
 
+def mixed_grid(seed: int, lo: int = 118, hi: int = 2000) -> Grid:
+    """A grid of the mixed batch: N_b log-uniform in [lo, hi] drawn from the seed, then the
+    planar generator with the same seed."""
+    rng = np.random.default_rng(seed)
+    nb = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+    return make_grid(nb, seed)
+
+
+def batch_grids(n_scen: int = 256, n_mixed: int = 64, base: str = "planar1k"):
+    """The batched workload: n_scen load scenarios of the base grid (per-bus scaling U[0.8, 1.2],
+    seeds 1000, 1001, ...) followed by n_mixed grids of 118-2000 buses (seeds 2000, 2001, ...)."""
+    g = config_grid(base)
+    return ([scale_loads(g, 1000 + k) for k in range(n_scen)] +
+            [mixed_grid(2000 + k) for k in range(n_mixed)])
+
+
 def kkt_point(grid: Grid, seed: int, log_range: float = 8.0):
     """A late-iteration-shaped KKT point: primal x inside the bounds, multipliers
     y, z ~ U[-1, 1], barrier diagonals Sigma_x and D_s log-uniform in
