@@ -1,15 +1,18 @@
-"""Benchmark: condensed KKT solves on one GB300 (or N independent replicas).
+"""Benchmark: batched interior-point solves on one GB300 (or N GPUs, one set per GPU).
 
-Workload (default, "kkt10k-lifted"): one LiftedKKT KKT solve of a seeded synthetic
-10,000-bus AC-OPF grid (24,000 primal variables, 46,001 relaxed rows) at a late-iteration
-shaped point: Sigma_x and D_H log-uniform in [1e-8, 1e8].  One step = condensation of
-K = W + Sigma_x + delta_w I + J^T D_H J, supernodal Cholesky, and the FP64-refined solve of
-the augmented system (backward error <= 1e-10).  W and J are evaluated once by the GPU
-model kernels at setup; the symbolic analysis is done once (reported as symbolic_s, like
-the paper's "init").  L2 is flushed between timed steps.
+Headline workload ("batch320-lifted"): 256 load scenarios of a seeded synthetic 1,000-bus
+AC-OPF grid (per-bus load scaling U[0.8, 1.2]) plus 64 seeded grids of 118-2,000 buses, solved
+together by the batched LiftedKKT FP64 interior-point method to the 1e-6 scaled KKT tolerance.
+One step = set every instance back to its starting point and run sweeps until every instance has
+converged or stopped; value = converged instances / step time (symbolic analyses, once per
+pattern at batch creation, are reported separately as init_s, like the paper's "init").  The
+instance pool (~0.7 GB) is larger than L2, so no flush is needed between steps.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the same
-workload instead.
+Also reported: the single-problem GPU IPM on a sample of the same instances ("plain"), the
+condensed KKT solve kernel at 10,000 buses with its own roofline ("kkt10k"), full single-problem
+IPM solves of several grids and forms ("ipm"), and the CPU oracle ("cpu_baseline").
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the same workload.
 """
 from __future__ import annotations
 
@@ -27,9 +30,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IPM solves/s at 1e-6 KKT tol, plain vs batched/warm-start; factor GB/s"
-UNIT = "KKT solves/s"
-WORKLOAD = ("kkt10k-lifted: LiftedKKT condensed KKT solve (condense + supernodal Cholesky + "
-            "FP64-refined solve) on a seeded synthetic 10,000-bus grid, Sigma log-uniform [1e-8,1e8]")
+UNIT = "IPM solves/s"
+KKT_UNIT = "KKT solves/s"
+WORKLOAD = ("batch320-lifted: 256 load scenarios of a seeded 1,000-bus grid + 64 seeded grids of "
+            "118-2,000 buses, batched LiftedKKT FP64 IPM to 1e-6 scaled KKT tolerance")
+KKT_WORKLOAD = ("kkt10k-lifted: LiftedKKT condensed KKT solve (condense + supernodal Cholesky + "
+                "FP64-refined solve) on a seeded synthetic 10,000-bus grid, Sigma log-uniform "
+                "[1e-8,1e8]")
+MAX_ITER = 300
+# FP64 peak from unit counts: 4 SMSPs x 0.5 FP64 FMA per cycle (one FP64 warp instruction per 64
+# cycles, measured) x 2 flops x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 0.5 * 2 * 2.07e9 / 1e12
 
 
 def measured_peaks():
@@ -126,7 +137,7 @@ def oracle_step(o):
     return hist[-1]
 
 
-def cpu_baseline(budget_s=12.0, min_solves=3):
+def kkt_cpu_baseline(budget_s=8.0, min_solves=3):
     o = oracle_setup()
     oracle_step(o)  # warm
     t0 = time.perf_counter()
@@ -137,38 +148,109 @@ def cpu_baseline(budget_s=12.0, min_solves=3):
         if k >= 200:
             break
     el = time.perf_counter() - t0
-    return {"value": k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": k / el, "unit": KKT_UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{k} full KKT solves of the same workload in {el:.1f} s "
                       f"(scipy condensation + plain C up-looking Cholesky + numpy refinement, "
                       f"single thread; host has {os.cpu_count()} cores)"}
 
 
+def _oracle_solve(grid):
+    from oracle.opf import OPFModel
+    from oracle import ipm as oipm
+    r = oipm.solve(OPFModel(grid), oipm.Options(kkt="lifted"))
+    return r.status == "converged", r.iters
+
+
+def _oracle_solve_seed(spec):
+    """Pool worker (spawned process): rebuild the instance from its seeds and solve it."""
+    sys.path.insert(0, ROOT)
+    from synth import config_grid, scale_loads, mixed_grid
+    kind, seed = spec
+    g = scale_loads(config_grid("planar1k"), seed) if kind == "scen" else mixed_grid(seed)
+    return _oracle_solve(g)
+
+
+def sample_specs(k, part=0):
+    """k instances of the batched workload, alternating scenarios and mixed grids."""
+    o = 100000 * part
+    out = []
+    for i in range(k):
+        out.append(("scen", o + 1000 + i // 2) if i % 2 == 0 else ("mixed", o + 2000 + i // 2))
+    return out
+
+
+def batch_cpu_baseline(budget_s=10.0, pool=True):
+    """The oracle IPM (plain FP64 CPU, simple sparse LDL^T) on a bounded sample of the batched
+    workload: one thread, then (pool) one problem per host core in spawned processes."""
+    from synth import config_grid, scale_loads, mixed_grid
+    specs = sample_specs(64)
+    t0 = time.perf_counter()
+    k = conv = 0
+    while k < 2 or (time.perf_counter() - t0 < budget_s and k < len(specs)):
+        kind, seed = specs[k]
+        g = scale_loads(config_grid("planar1k"), seed) if kind == "scen" else mixed_grid(seed)
+        ok, _ = _oracle_solve(g)
+        conv += ok
+        k += 1
+    el = time.perf_counter() - t0
+    out = {"value": conv / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{k} instances of the batched workload (alternating 1,000-bus scenarios and "
+                     f"mixed grids), {conv} converged, {el:.1f} s, one thread; host has "
+                     f"{os.cpu_count()} cores"}
+    if pool:
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        specs = sample_specs(2 * cores)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as P:
+            P.map(_oracle_solve_seed, specs[:cores])  # start-up and imports, untimed
+            t0 = time.perf_counter()
+            res = P.map(_oracle_solve_seed, specs)
+            el = time.perf_counter() - t0
+        c2 = sum(ok for ok, _ in res)
+        out["pool"] = {"value": c2 / el, "unit": UNIT, "cores": cores,
+                       "sample": f"{len(specs)} instances, one per core at a time, {c2} converged, "
+                                 f"{el:.1f} s"}
+    return out
+
+
 def run_reference(args, rank, world):
+    """The oracle on the batched workload: each step solves one instance (cycling through a
+    sample of scenarios and mixed grids) with the plain CPU IPM, single thread."""
     if rank != 0:
         return
-    o = oracle_setup()
-    for _ in range(args.warmup):
-        oracle_step(o)
+    from synth import config_grid, scale_loads, mixed_grid
+    specs = sample_specs(max(8, args.steps + args.warmup))
+    grids = [scale_loads(config_grid("planar1k"), s_) if k_ == "scen" else mixed_grid(s_)
+             for k_, s_ in specs]
+    for i in range(args.warmup):
+        _oracle_solve(grids[i])
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(o)
+    conv = 0
+    for i in range(args.steps):
+        ok, _ = _oracle_solve(grids[args.warmup + i])
+        conv += ok
     el = time.perf_counter() - t0
-    v = args.steps / el
+    v = conv / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "one instance per step, one thread"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full KKT solves, single thread"},
+                             "sample": f"{args.steps} instances of the batched workload, "
+                                       f"{conv} converged, single thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
-def run_gpu(args, rank, world, local_rank):
+def kkt_measure(args):
+    """The condensed KKT solve at 10,000 buses (condense + factor + FP64-refined solve), with the
+    FP32-factor variant, its own roofline, e2e and oracle timing (one GPU)."""
     import torch
     import paper_2405_14236_gb300 as cp
-    torch.cuda.set_device(local_rank)
+    world, rank, local_rank = 1, 0, torch.cuda.current_device()
     stream = torch.cuda.current_stream()
     f64 = dict(dtype=torch.float64, device="cuda")
     g, p, d, b = build_inputs()
@@ -282,7 +364,7 @@ def run_gpu(args, rank, world, local_rank):
         ph32 = np.array(ph32)
         prec, pcg = cp.ipm_num_info(N32)
         rel = float((dx32 - dx).abs().max().item() / dx.abs().max().item()) if dw32 == dw else None
-        fp32 = {"value": len(ph32) / (ph32.sum() / 1e3), "unit": UNIT,
+        fp32 = {"value": len(ph32) / (ph32.sum() / 1e3), "unit": KKT_UNIT,
                 "phases_ms": {nm: float(v) for nm, v in zip(["condense", "factor", "solve"],
                                                             ph32.mean(axis=0))},
                 "delta_w": dw32, "pcg_iters": pcg, "backward_error": float(eta.item()),
@@ -325,10 +407,9 @@ def run_gpu(args, rank, world, local_rank):
             traffic = None
     ach = bytes_[names[dom]] / (mean[dom] / 1e3) / 1e9
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "m": m, "nnzJ": opf.nnzJ, "nnzW": opf.nnzW,
+        "value": value, "unit": KKT_UNIT, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()),
+        "config": {"workload": KKT_WORKLOAD, "n": n, "m": m, "nnzJ": opf.nnzJ, "nnzW": opf.nnzW,
                    "nnzK_lower": S.nnz_k, "nnzL": nnzL, "nsuper": S.nsuper,
                    "nlevels": S.nlevels, "factor_flops": S.flops, "delta_w": dw,
                    "l2": "flushed between timed steps (256 MiB write)",
@@ -341,16 +422,191 @@ def run_gpu(args, rank, world, local_rank):
                    "GFLOP_s": S.flops / (mean[1] / 1e3) / 1e9},
         "backward_error": eta_v, "refine_steps": refine, "factor_ok": ok,
         "symbolic_s": symbolic_s,
-        "e2e": {"value": n_e2e / (e_tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": n_e2e / (e_tot / 1e3), "unit": KKT_UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "fp32": fp32,
         "clocks": clk,
     }
-    if not args.no_ipm and world == 1:
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = kkt_cpu_baseline()
+    return line
+
+
+def plain_measure(grids):
+    """Single-problem GPU IPM (ipm_step loop, LiftedKKT FP64) on the given instances, one after
+    another; time of the iterations (the per-problem symbolic analysis excluded, as for the
+    batch)."""
+    import torch
+    import paper_2405_14236_gb300 as cp
+    conv, t_tot, iters = 0, 0.0, []
+    for g in grids:
+        st = cp.IpmState(cp.Opf(g), kkt="lifted")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(MAX_ITER + 1):
+            info = st.step()
+            if info.status != 0:
+                break
+        t_tot += time.perf_counter() - t0
+        conv += info.status == 1
+        iters.append(info.k)
+    return {"value": conv / t_tot, "unit": UNIT, "instances": len(grids), "converged": int(conv),
+            "mean_iters": float(np.mean(iters)),
+            "sample": "single-problem GPU IPM (one instance at a time) on alternating "
+                      "1,000-bus scenarios and mixed grids of the batched workload"}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2405_14236_gb300 as cp
+    from synth import batch_grids
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    # ---- instances of this GPU (weak scaling: one full set per GPU)
+    grids = batch_grids(256, 64, part=rank)
+    t0 = time.perf_counter()
+    opfs = [cp.Opf(g) for g in grids]
+    B = cp.Batch(opfs)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    info = B.info()
+    B.set_timing(True)
+    for _ in range(args.warmup):
+        B.reset()
+        B.run(max_iter=MAX_ITER)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, conv, iters_mean, iters_max, sweeps = [], [], [], [], []
+    fact_ms = solve_ms = 0.0
+    n_sw = 0
+    nfac = 0
+    w = B.work()
+    fl_inst = w["factor_flops"] + w["condense_flops"]
+    fl_tot = by_tot = 0.0
+    l0 = cp.launch_count()
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        B.reset()
+        B.run(max_iter=MAX_ITER)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        r = B.results()
+        kt = B.kernel_time()
+        fact_ms += kt["fact_ms"]
+        solve_ms += kt["solve_ms"]
+        n_sw += kt["sweeps"]
+        nfac += int(r["n_factor"].sum())
+        fl_tot += float(np.sum(fl_inst * r["n_factor"]))
+        by_tot += float(np.sum(w["bytes"] * r["n_factor"]))
+        conv.append(int((r["status"] == 1).sum()))
+        iters_mean.append(float(r["iters"].mean()))
+        iters_max.append(int(r["iters"].max()))
+        sweeps.append(int(r["sweeps"]))
+    launches = cp.launch_count() - l0
+    clk = clocks.stop()
+    t_tot = float(np.sum(step_ms))
+    tot_conv = float(np.sum(conv))
+    if world > 1:
+        tt = torch.tensor([t_tot, tot_conv], dtype=torch.float64, device="cuda")
+        t_max = tt[:1].clone()
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+        c_sum = tt[1:].clone()
+        torch.distributed.all_reduce(c_sum, op=torch.distributed.ReduceOp.SUM)
+        t_tot, tot_conv = float(t_max.item()), float(c_sum.item())
+    value = tot_conv / (t_tot / 1e3)
+    # ---- e2e through the public API with host data: new loads for every scenario from host
+    # memory, solve, every x back to host memory
+    host_pd = [np.ascontiguousarray(g.pd, dtype=np.float64) for g in grids]
+    host_qd = [np.ascontiguousarray(g.qd, dtype=np.float64) for g in grids]
+    x_host = np.zeros(sum(o.n for o in opfs))
+    n_e2e = max(2, args.steps // 3)
+    e_ms, e_conv = 0.0, 0
+    B.set_timing(False)
+    for _ in range(n_e2e):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for o, pd, qd in zip(opfs, host_pd, host_qd):
+            o.set_loads(pd, qd)
+        B.reset()
+        B.run(max_iter=MAX_ITER)
+        B.x_all(x_host)
+        e_ms += 1e3 * (time.perf_counter() - t0)
+        e_conv += int((B.results()["status"] == 1).sum())
+    h2d = int(sum(16 * g.nb for g in grids))
+    d2h = int(8 * x_host.size)
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel: fused condensation + factorization (FP64 arithmetic,
+    # latency-bound on these small supernodes): algorithmic FP64 flops per launch / its duration
+    flops_all = float(np.sum(fl_inst))
+    bytes_all = float(np.sum(w["bytes"]))
+    # every factorization of every instance over the timed steps against the summed duration of
+    # the factorization launches (two per sweep)
+    launches_fact = 2 * max(n_sw, 1)
+    fact_avg_ms = fact_ms / launches_fact
+    ach_tf = fl_tot / (fact_ms / 1e3) / 1e12
+    fl_per_fact = fl_tot
+    by_per_fact = by_tot
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            import hashlib
+            tr = json.load(open(tfile))
+            h = hashlib.sha256(open(os.path.join(ROOT, "paper_2405_14236_gb300", "csrc",
+                                                  "batch.cu"), "rb").read()).hexdigest()[:16]
+            if tr.get("batch_cu_sha") == h:
+                traffic = tr.get("k_b_fact_inst_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances": len(grids), "patterns": info["patterns"],
+                   "tol": 1e-6, "max_iter": MAX_ITER, "pool_bytes": info["device_bytes"],
+                   "l2": "not flushed: the instance pool (%.2f GB) exceeds L2"
+                         % (info["device_bytes"] / 1e9),
+                   "parallelism": f"dp{world}: one instance set per GPU" if world > 1
+                   else "single GPU"},
+        "converged_per_step": conv, "iters_mean": float(np.mean(iters_mean)),
+        "iters_max": iters_max, "sweeps_per_step": sweeps,
+        "launches_per_sweep": B.info()["launches_per_sweep"], "init_s": init_s,
+        "roofline": {"kernel": "k_b_fact_inst (condensation + factorization, every instance)",
+                     "bound": "alu", "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach_tf / FP64_PEAK_TFLOPS,
+                     "peak_source": "FP64 from unit counts and the 2070 MHz clock",
+                     "traffic": traffic,
+                     "algorithmic_flops_per_launch": fl_per_fact / launches_fact,
+                     "algorithmic_bytes_per_launch": by_per_fact / launches_fact,
+                     "avg_launch_ms": fact_avg_ms, "factorizations": nfac},
+        "kernels_ms_per_sweep": {"factor_both_rounds": fact_ms / max(n_sw, 1),
+                                 "solve_first": solve_ms / max(n_sw, 1)},
+        "factor": {"GB_s": by_tot / (fact_ms / 1e3) / 1e9,
+                   "work_per_batch_factorization": {"flops": flops_all, "bytes": bytes_all}},
+        "e2e": {"value": e_conv / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_plain:
+        line["plain"] = plain_measure([grids[i] if i % 2 == 0 else grids[256 + i // 2]
+                                       for i in range(4)])
+        line["plain"]["batched_speedup"] = value / line["plain"]["value"]
+    if not args.no_kkt:
+        line["kkt10k"] = kkt_measure(args)
+    if not args.no_ipm:
         line["ipm"] = ipm_measure(include_oracle=not args.no_cpu_baseline)
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline()
     print(json.dumps(line), flush=True)
 
 
@@ -404,12 +660,14 @@ def ipm_measure(include_oracle=True):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ipm", action="store_true", help="skip the full-IPM measurement")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-factor variant")
+    ap.add_argument("--no-kkt", action="store_true", help="skip the 10k KKT-solve kernel line")
+    ap.add_argument("--no-plain", action="store_true", help="skip the single-problem GPU IPM")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

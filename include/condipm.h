@@ -247,6 +247,9 @@ int ipm_opf_patterns(ipm_opf_t opf, int *J_rowptr, int *J_colind, int *W_rowptr,
 int ipm_opf_eval(ipm_opf_t opf, const double *x, const double *y, const double *z,
                  double sigma_f, double *f, double *grad, double *g, double *h, double *J_val,
                  double *W_val, cudaStream_t stream);
+/* Replaces the loads (pd, qd: nb values each, HOST or device; MW / 100 per bus) of a model, for
+ * a new scenario of the same grid.  Stream-ordered. */
+int ipm_opf_set_loads(ipm_opf_t opf, const double *pd, const double *qd, cudaStream_t stream);
 void ipm_opf_destroy(ipm_opf_t opf);
 
 /* ---------------------------------------------------------------------------------------
@@ -336,6 +339,21 @@ int ipm_batch_results(ipm_batch_t batch, int *status, int *iters, double *obj, d
 int ipm_batch_export(ipm_batch_t batch, int i, double *x);
 /* Sweeps run since creation or the last reset. */
 int ipm_batch_sweeps(ipm_batch_t batch);
+/* Copies every instance's x, concatenated in instance order, into a HOST buffer of sum(n)
+ * doubles (one gather kernel and one device-to-host copy).  Synchronizes. */
+int ipm_batch_export_all(ipm_batch_t batch, double *x_host);
+/* on != 0: record CUDA events around every factorization launch (condensation + factorization
+ * of the instances in that step) and the first solve launch of every sweep (event nodes inside
+ * the captured graph) and accumulate their durations; ipm_batch_kernel_time reports the sums
+ * (ms) and the number of sweeps since the last reset. */
+int ipm_batch_set_timing(ipm_batch_t batch, int on);
+int ipm_batch_kernel_time(ipm_batch_t batch, double *fact_ms, double *solve_ms, int *sweeps);
+/* Algorithmic work of one condensation + factorization of each instance, into HOST arrays
+ * [count] (any may be NULL): textbook factorization flops sum_j eta_j (eta_j + 3), condensation
+ * flops (2 per J^T D J product), and bytes (8 (nnz(J) + m + nnz(W) + n) read, 8 per panel value
+ * written). */
+int ipm_batch_work(ipm_batch_t batch, double *factor_flops, double *condense_flops,
+                   double *bytes);
 void ipm_batch_destroy(ipm_batch_t batch);
 
 #ifdef __cplusplus

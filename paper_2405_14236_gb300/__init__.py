@@ -61,6 +61,11 @@ _SIGS = {
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
     "ipm_batch_destroy": (None, [P]),
+    "ipm_batch_export_all": (I, [P, P]),
+    "ipm_batch_set_timing": (I, [P, I]),
+    "ipm_batch_kernel_time": (I, [P, P, P, P]),
+    "ipm_batch_work": (I, [P, P, P, P]),
+    "ipm_opf_set_loads": (I, [P, P, P, P]),
 }
 
 
@@ -290,6 +295,12 @@ class Opf:
         self.J_colind = self.J_colind[:self.nnzJ]
         self.W_colind = self.W_colind[:self.nnzW]
 
+    def set_loads(self, pd, qd, stream=None):
+        """New loads (numpy float64 host arrays or CUDA tensors, nb values each)."""
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if isinstance(a, np.ndarray) else _ptr(a)
+        _check(lib().ipm_opf_set_loads(self.h, ptr(pd), ptr(qd), _stream(stream)),
+               "ipm_opf_set_loads")
+
     def eval(self, x, y, z, sigma_f, f, grad, g, h, J_val, W_val, stream=None):
         return _check(lib().ipm_opf_eval(self.h, _ptr(x), _ptr(y), _ptr(z), float(sigma_f), _ptr(f),
                                          _ptr(grad), _ptr(g), _ptr(h), _ptr(J_val), _ptr(W_val),
@@ -387,6 +398,30 @@ class Batch:
                "ipm_batch_results")
         return dict(status=st, iters=it, obj=obj, kkt_err=err, n_factor=nf, ls_steps=ls,
                     sweeps=lib().ipm_batch_sweeps(self.h))
+
+    def x_all(self, out=None):
+        """Every instance's x, concatenated (one gather and one copy); out: float64 numpy array."""
+        if out is None:
+            out = np.zeros(sum(o.n for o in self.opfs))
+        _check(lib().ipm_batch_export_all(self.h, out.ctypes.data_as(ctypes.c_void_p)),
+               "ipm_batch_export_all")
+        return out
+
+    def set_timing(self, on=True):
+        _check(lib().ipm_batch_set_timing(self.h, int(bool(on))), "ipm_batch_set_timing")
+
+    def kernel_time(self):
+        f, s_, n = D(), D(), I()
+        _check(lib().ipm_batch_kernel_time(self.h, ctypes.byref(f), ctypes.byref(s_),
+                                           ctypes.byref(n)), "ipm_batch_kernel_time")
+        return dict(fact_ms=f.value, solve_ms=s_.value, sweeps=n.value)
+
+    def work(self):
+        n = self.count
+        ff, cf, by = np.zeros(n), np.zeros(n), np.zeros(n)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_batch_work(self.h, p(ff), p(cf), p(by)), "ipm_batch_work")
+        return dict(factor_flops=ff, condense_flops=cf, bytes=by)
 
     def x(self, i):
         out = np.zeros(self.opfs[i].n)

@@ -24,6 +24,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "ipm_core.cuh"
 #include "numeric_dev.cuh"
 #include "opf_dev.cuh"
@@ -57,17 +59,19 @@ struct BI {
   double *R, *filter;
   // numeric
   const int *sptr, *srow_ptr, *slot_ptr, *perm, *J_rowidx, *JT_ptr, *JT_ent;
-  const int64_t *lptr;
+  const int *srow, *snode, *level_sn, *lvl_ptr;  // lvl_ptr: level offsets into level_sn
+  // update pairs of each supernode (precomputed per pattern): pair_ptr[s].. pair_ptr[s + 1],
+  // rows (i << 16 | j) of the panel, i >= j >= w, and the target value slot in the panels
+  const int *pair_ptr, *pair_ij, *pair_tgt;
+  const int64_t *lptr, *dptr;
   const int2 *items;
-  int ns;
+  int ns, nlevels;
   double *tJ, *Lx, *Dx;
-  int *info, *sync;  // sync: [0,2ns) factor, [2ns,3ns) forward, [3ns,4ns) backward, then tail
+  int *info;
   double *y, *t, *cx, *cz, *outx, *outz, *scal;
   AugArgs aug;
 };
 
-__device__ __forceinline__ int *sync_abort(const BI &I) { return I.sync + 4 * I.ns + 1; }
-__device__ __forceinline__ int *sync_status(const BI &I) { return I.sync + 4 * I.ns + 2; }
 
 #define B_PROLOGUE(want)                 \
   const int b = blockIdx.y;              \
@@ -169,6 +173,31 @@ __global__ void k_b_scale_model(const BI *bi, const BCtl *ctl, int phase, int mo
     for (int p = gtid; p < I.M.nnzJ; p += gstride) I.Jv[p] *= I.dscale[I.J_rowidx[p]];
 }
 
+// block-wide reduction of NQ values (op 0 sum, 1 max, 2 min; max / min values non-negative)
+// with one atomic per value per block; every thread of the block (<= 256) must call
+enum { OP_SUM = 0, OP_MAX = 1, OP_MIN = 2 };
+template <int NQ>
+__device__ __forceinline__ void block_reduce_atomic(double *R, const int (&slot)[NQ],
+                                                    const int (&op)[NQ], double (&v)[NQ]) {
+  __shared__ double sh[8][NQ];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double x = op[q] == OP_SUM ? wsum(v[q]) : op[q] == OP_MAX ? wmax(v[q]) : wmin(v[q]);
+    if (lane == 0) sh[w][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    const int q = threadIdx.x;
+    double a = sh[0][q];
+    for (int k = 1; k < nw; ++k)
+      a = op[q] == OP_SUM ? a + sh[k][q] : op[q] == OP_MAX ? fmax(a, sh[k][q]) : fmin(a, sh[k][q]);
+    if (op[q] == OP_SUM) atomicAdd(R + slot[q], a);
+    else if (op[q] == OP_MAX) amax_nonneg(R + slot[q], a);
+    else amin_nonneg(R + slot[q], a);
+  }
+}
+
 // ------------------------------------------------------------------ set-up
 __global__ void k_b_setup_sums(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
@@ -255,27 +284,15 @@ __global__ void k_b_errors(const BI *bi, const BCtl *ctl) {
     lxl += Mp.lxl;
     lxu += Mp.lxu;
   }
-  double *R = I.R;
-  red_max(R, R_MAX_GL, gl);
-  red_max(R, R_MAX_ZV, zv);
-  red_max(R, R_MAX_G, ge);
-  red_max(R, R_MAX_HS, hs);
-  red_sum(R, R_SUM_Y, sy);
-  red_sum(R, R_SUM_Z, sz);
-  red_sum(R, R_SUM_V, svv);
-  red_sum(R, R_SUM_ZL, szl);
-  red_sum(R, R_SUM_ZU, szu);
-  red_min(R, R_SV_MIN, svmin);
-  red_max(R, R_SV_MAX, svmax);
-  red_min(R, R_CL_MIN, clmin);
-  red_max(R, R_CL_MAX, clmax);
-  red_min(R, R_CU_MIN, cumin);
-  red_max(R, R_CU_MAX, cumax);
-  red_sum(R, R_TH_G, tg);
-  red_sum(R, R_TH_H, th);
-  red_sum(R, R_LOG_S, ls);
-  red_sum(R, R_LOG_XL, lxl);
-  red_sum(R, R_LOG_XU, lxu);
+  const int slot[20] = {R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_SUM_Y, R_SUM_Z, R_SUM_V,
+                       R_SUM_ZL, R_SUM_ZU, R_SV_MIN, R_SV_MAX, R_CL_MIN, R_CL_MAX, R_CU_MIN,
+                       R_CU_MAX, R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU};
+  const int op[20] = {OP_MAX, OP_MAX, OP_MAX, OP_MAX, OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM,
+                      OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_SUM, OP_SUM, OP_SUM,
+                      OP_SUM, OP_SUM};
+  double v[20] = {gl, zv, ge, hs, sy, sz, svv, szl, szu, svmin, svmax, clmin, clmax,
+                  cumin, cumax, tg, th, ls, lxl, lxu};
+  block_reduce_atomic<20>(I.R, slot, op, v);
 }
 
 __device__ __forceinline__ double comp_mu(const double *h, double mu) {
@@ -365,87 +382,287 @@ __global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_FACT);
   for (int p = gtid; p < I.M.nnzJ; p += gstride) I.tJ[p] = I.dcond[I.J_rowidx[p]] * I.Jv[p];
 }
-__global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
-  const int b = blockIdx.y;
-  if (ctl[b].ph != PH_FACT) return;
-  const BI &I = bi[b];
-  for (int s = blockIdx.x; s < I.ns; s += gridDim.x)
-    condense_block<double>(s, I.sptr, I.srow_ptr, I.lptr, I.slot_ptr, I.items, I.perm, I.Wv,
-                           I.SA.sigma, I.Jv, I.tJ, ctl[b].dw, I.Lx);
-}
-// counters of the factorization, abort and status flags, failing-pivot slot
-__global__ void k_b_fact_reset(const BI *bi, const BCtl *ctl) {
-  B_PROLOGUE(PH_FACT);
-  for (int k = gtid; k < 2 * I.ns; k += gstride) I.sync[k] = 0;
-  if (gtid == 0) {
-    *sync_abort(I) = 0;
-    *sync_status(I) = 0;
-    *I.info = INT_MAX;
+
+// ------------------------------------------------------------------ per-instance numeric kernels
+// One block per instance, level by level through the supernodal elimination tree (deepest level
+// first for the factorization and the forward solve, root first for the backward solve): the
+// supernodes of a level are independent, so a barrier between levels is the only
+// synchronization.  Narrow supernodes (w <= B_WS) take one warp each; wider ones use the whole
+// block.  Contributions into other supernodes' panels (and into y) from one level are added
+// atomically, since supernodes of a level may share targets.  No waits on other blocks.
+static constexpr int B_WS = 16;
+static constexpr int B_NT = 512;  // threads of the per-instance kernels
+
+// Update of supernode s into its ancestors: entry (i, j), i >= j >= w, of L21 L21^T is
+// subtracted from the panel of the supernode owning column rows[j], at row rows[i].  The pairs
+// and their target slots are listed per pattern, so threads take pairs (full lanes, no searches).
+__device__ __forceinline__ void scatter_update(const BI &I, int s, int ld, int w, const double *P,
+                                               int tid, int nthreads) {
+  const int p0 = I.pair_ptr[s], np = I.pair_ptr[s + 1] - p0;
+  for (int t = tid; t < np; t += nthreads) {
+    const int ij = I.pair_ij[p0 + t];
+    const int i = ij >> 16, j = ij & 0xffff;
+    double v = 0.0;
+    for (int k = 0; k < w; ++k) v += P[i + (int64_t)k * ld] * P[j + (int64_t)k * ld];
+    atomicAdd(&I.Lx[I.pair_tgt[p0 + t]], -v);
   }
 }
 
-__device__ __forceinline__ int find_inst(const int *start, int count, int t) {
-  int lo = 0, hi = count - 1;  // largest i with start[i] <= t
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (start[mid] <= t) lo = mid; else hi = mid - 1;
+// warp path: diagonal block, reciprocal pivots, L21 = A21 L11^{-T}, then the outer product of the
+// rows below scattered into the target panels.  D: w*w doubles, inv: w doubles (this warp's).
+__device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
+  const int lane = threadIdx.x & 31;
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
+  double *P = I.Lx + I.lptr[s];
+  for (int t = lane; t < w * w; t += 32) {
+    const int k = t / w, i = t - k * w;
+    D[t] = i >= k ? P[i + (int64_t)k * ld] : 0.0;
   }
-  return lo;
-}
-
-// thread 0: next ticket of an instance in the phase (instances outside it are jumped over)
-__device__ __forceinline__ void grab_ticket(const int *start, int count, const BCtl *ctl,
-                                            int phase, int *ticket, int *s_t, int *s_inst) {
-  const int total = start[count];
-  int t, inst;
-  while (true) {
-    t = atomicAdd(ticket, 1);
-    if (t >= total) {
-      inst = -1;
-      break;
+  __syncwarp();
+  for (int k = 0; k < w; ++k) {
+    if (lane == 0) {
+      double d = D[k + k * w];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicMin(I.info, f + k);
+        d = 1.0;
+      }
+      const double iv = rsqrt_newton(d);
+      D[k + k * w] = d * iv;
+      inv[k] = iv;
     }
-    inst = find_inst(start, count, t);
-    if (ctl[inst].ph == phase) break;
-    atomicMax(ticket, start[inst + 1]);
+    __syncwarp();
+    const double iv = inv[k];
+    for (int i = k + 1 + lane; i < w; i += 32) D[i + k * w] *= iv;
+    __syncwarp();
+    const int nr = w - k - 1;
+    for (int t = lane; t < nr * nr; t += 32) {
+      const int j = k + 1 + t / nr, i = k + 1 + t % nr;
+      if (i >= j) D[i + j * w] -= D[i + k * w] * D[j + k * w];
+    }
+    __syncwarp();
   }
-  *s_t = t;
-  *s_inst = inst;
+  double *Dd = I.Dx + I.dptr[s];
+  for (int t = lane; t < w * w; t += 32) Dd[t] = D[t];
+  for (int k = lane; k < w; k += 32) Dd[w * w + k] = inv[k];
+  // rows below: forward substitution with L11 per row (lane-owned rows, registers)
+  for (int r = w + lane; r < ld; r += 32) {
+    double x[B_WS];
+#pragma unroll
+    for (int k = 0; k < B_WS; ++k)
+      if (k < w) x[k] = P[r + (int64_t)k * ld];
+#pragma unroll
+    for (int k = 0; k < B_WS; ++k) {
+      if (k < w) {
+        double v = x[k];
+#pragma unroll
+        for (int j = 0; j < B_WS; ++j)
+          if (j < k) v -= x[j] * D[k + j * w];
+        x[k] = v * inv[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B_WS; ++k)
+      if (k < w) P[r + (int64_t)k * ld] = x[k];
+  }
+  __syncwarp();
+  scatter_update(I, s, ld, w, P, lane, 32);
 }
 
-template <typename A>
-__device__ __forceinline__ void load_args(A *dst, const A *src) {
-  static_assert(sizeof(A) % 4 == 0, "argument block size");
-  const int *s = reinterpret_cast<const int *>(src);
-  int *d = reinterpret_cast<int *>(dst);
-  for (int k = threadIdx.x; k < (int)(sizeof(A) / 4); k += blockDim.x) d[k] = s[k];
-}
-
-template <typename V>
-__global__ void __launch_bounds__(256) k_b_factor(const FactTaskArgs<V> *FA, const int *start,
-                                                  int count, const BCtl *ctl, int *ticket) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  V *sm = reinterpret_cast<V *>(sm_raw);
-  __shared__ FactTaskArgs<V> sT;
-  __shared__ int s_t, s_inst, s_cur, s_ok;
-  if (threadIdx.x == 0) s_cur = -1;
+// block path for a wide supernode (every thread of the block calls); sm: w*w + 32*(w+1) doubles
+__device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
+  double *P = I.Lx + I.lptr[s];
+  double *sL = sm, *sR = sm + w * w;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int t = tid; t < w * w; t += bd) {
+    const int k = t / w, i = t - k * w;
+    sL[t] = i >= k ? P[i + (int64_t)k * ld] : 0.0;
+  }
   __syncthreads();
-  while (true) {
-    if (threadIdx.x == 0) grab_ticket(start, count, ctl, PH_FACT, ticket, &s_t, &s_inst);
-    __syncthreads();
-    const int t = s_t, inst = s_inst;
-    const bool reload = inst >= 0 && inst != s_cur;
-    __syncthreads();
-    if (inst < 0) break;
-    if (reload) {
-      load_args(&sT, FA + inst);
-      if (threadIdx.x == 0) s_cur = inst;
+  for (int k = 0; k < w; ++k) {
+    if (tid == 0) {
+      double d = sL[k + k * w];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicMin(I.info, f + k);
+        d = 1.0;
+      }
+      const double iv = rsqrt_newton(d);
+      sL[k + k * w] = d * iv;
+      s_inv[k] = iv;
     }
     __syncthreads();
-    const int4 tk = sT.tasks[t - start[inst]];
-    if (tk.w == 0) fact_panel_task(sT, tk.x, tk.y, sm, &s_ok);
-    else fact_update_task(sT, tk.x, tk.y, tk.z, sm, &s_ok);
+    const double iv = s_inv[k];
+    const int nr = w - k - 1;
+    for (int i = k + 1 + tid; i < w; i += bd) sL[i + k * w] *= iv;
+    __syncthreads();
+    for (int jj = tid / 32; jj < nr; jj += bd / 32) {
+      const int j = k + 1 + jj;
+      const double ljk = sL[j + k * w];
+      for (int i = j + (tid & 31); i < w; i += 32) sL[i + j * w] -= sL[i + k * w] * ljk;
+    }
     __syncthreads();
   }
+  double *Dd = I.Dx + I.dptr[s];
+  for (int t = tid; t < w * w; t += bd) Dd[t] = sL[t];
+  for (int k = tid; k < w; k += bd) Dd[w * w + k] = s_inv[k];
+  // rows below in blocks of 32: each warp owns rows, lanes split the columns
+  const int sw = w + 1;
+  const int warp = tid >> 5, lane = tid & 31, nw = bd >> 5;
+  for (int r0 = w; r0 < ld; r0 += 32) {
+    const int nrow = min(32, ld - r0);
+    __syncthreads();
+    for (int t = tid; t < nrow * w; t += bd) {
+      const int k = t / nrow, r = t - k * nrow;
+      sR[r * sw + k] = P[(r0 + r) + (int64_t)k * ld];
+    }
+    __syncthreads();
+    for (int k = 0; k < w; ++k) {
+      const double iv = s_inv[k];
+      for (int r = warp; r < nrow; r += nw) {
+        const double xk = sR[r * sw + k] * iv;
+        __syncwarp();
+        for (int j = k + 1 + lane; j < w; j += 32) sR[r * sw + j] -= xk * sL[j + k * w];
+        if (lane == 0) sR[r * sw + k] = xk;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nrow * w; t += bd) {
+      const int k = t / nrow, r = t - k * nrow;
+      P[(r0 + r) + (int64_t)k * ld] = sR[r * sw + k];
+    }
+  }
+  __syncthreads();
+  scatter_update(I, s, ld, w, P, tid, bd);
+  __syncthreads();
+}
+
+// condensation of every panel, then the factorization, of each instance in the FACT phase: one
+// thread-block cluster of B_CL blocks per instance.  Warps of the whole cluster share the
+// narrow supernodes of a level; each block collects the wide ones its warps met and factors them
+// with all its threads; a cluster barrier (release / acquire) separates the levels.
+static constexpr int B_CL = 1;
+static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
+
+__global__ void __cluster_dims__(B_CL, 1, 1) __launch_bounds__(B_NT)
+    k_b_fact_inst(const BI *bi, const BCtl *ctl) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double *sm = reinterpret_cast<double *>(sm_raw);
+  __shared__ double s_inv[CIPM_SN_MAXW];
+  __shared__ int s_wide[B_WIDE_CAP], s_nwide;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int b = blockIdx.x / B_CL;
+  if (ctl[b].ph != PH_FACT) return;  // the same for every block of the cluster
+  const BI &I = bi[b];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int gw = crank * nw + warp, gnw = B_CL * nw;
+  const double dw = ctl[b].dw;
+  if (crank == 0 && threadIdx.x == 0) *I.info = INT_MAX;
+  for (int s = gw; s < I.ns; s += gnw)
+    condense_block<double>(s, I.sptr, I.srow_ptr, I.lptr, I.slot_ptr, I.items, I.perm, I.Wv,
+                           I.SA.sigma, I.Jv, I.tJ, dw, I.Lx, lane, 32);
+  cluster.sync();
+  double *D = sm + warp * (B_WS * B_WS + B_WS), *inv = D + B_WS * B_WS;
+  for (int L = 0; L < I.nlevels; ++L) {
+    if (threadIdx.x == 0) s_nwide = 0;
+    __syncthreads();
+    const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
+    for (int q = q0 + gw; q < q1; q += gnw) {
+      const int s = I.level_sn[q];
+      if (I.sptr[s + 1] - I.sptr[s] <= B_WS) {
+        warp_factor_sn(I, s, D, inv);
+      } else if (lane == 0) {
+        s_wide[atomicAdd(&s_nwide, 1)] = s;
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < s_nwide; ++k) block_factor_sn(I, s_wide[k], sm, s_inv);
+    cluster.sync();
+  }
+}
+
+// y <- L^{-T} L^{-1} y for one supernode, one warp (ys: w doubles of this warp's shared memory)
+__device__ void warp_fwd_sn(const BI &I, int s, double *ys) {
+  const int lane = threadIdx.x & 31;
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
+  const int *rows = I.srow + rb;
+  const double *P = I.Lx + I.lptr[s];
+  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
+  for (int k = lane; k < w; k += 32) ys[k] = I.y[f + k];
+  __syncwarp();
+  for (int k = 0; k < w; ++k) {
+    if (lane == (k & 31)) ys[k] *= rinv[k];
+    __syncwarp();
+    const double yk = ys[k];
+    for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= Dd[i + k * w] * yk;
+    __syncwarp();
+  }
+  for (int k = lane; k < w; k += 32) I.y[f + k] = ys[k];
+  for (int i = w + lane; i < ld; i += 32) {
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc += P[i + (int64_t)k * ld] * ys[k];
+    atomicAdd(&I.y[rows[i]], -acc);
+  }
+  __syncwarp();
+}
+
+__device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
+  const int lane = threadIdx.x & 31;
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
+  const int *rows = I.srow + rb;
+  const double *P = I.Lx + I.lptr[s];
+  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
+  for (int k = 0; k < w; ++k) {
+    double acc = 0.0;
+    for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * I.y[rows[i]];
+    acc = warp_sum(acc);
+    if (lane == 0) zs[k] = I.y[f + k] - acc;
+  }
+  __syncwarp();
+  for (int k = w - 1; k >= 0; --k) {
+    if (lane == (k & 31)) zs[k] *= rinv[k];
+    __syncwarp();
+    const double xk = zs[k];
+    for (int j = lane; j < k; j += 32) zs[j] -= Dd[k + j * w] * xk;
+    __syncwarp();
+  }
+  for (int k = lane; k < w; k += 32) I.y[f + k] = zs[k];
+  __syncwarp();
+}
+
+// phase SOLVE: dx = K^{-1} t; phase REFINE: cx = K^{-1} t (t from k_b_jt_rhs), one cluster per
+// instance: gather by the ordering, forward levels, backward levels, scatter
+__global__ void __cluster_dims__(B_CL, 1, 1) __launch_bounds__(B_NT)
+    k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase) {
+  __shared__ double s_y[(B_NT / 32) * CIPM_SN_MAXW];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
+  const int b = blockIdx.x / B_CL;
+  if (ctl[b].ph != phase) return;  // the same for every block of the cluster
+  const BI &I = bi[b];
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gw = crank * nw + warp, gnw = B_CL * nw;
+  const int gt = crank * blockDim.x + threadIdx.x, gnt = B_CL * blockDim.x;
+  double *ys = s_y + warp * CIPM_SN_MAXW;
+  for (int k = gt; k < I.D.n; k += gnt) I.y[k] = I.t[I.perm[k]];
+  cluster.sync();
+  for (int L = 0; L < I.nlevels; ++L) {
+    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_fwd_sn(I, I.level_sn[q], ys);
+    cluster.sync();
+  }
+  for (int L = I.nlevels - 1; L >= 0; --L) {
+    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_bwd_sn(I, I.level_sn[q], ys);
+    cluster.sync();
+  }
+  double *x = phase == PH_SOLVE ? I.dx : I.cx;
+  for (int k = gt; k < I.D.n; k += gnt) x[I.perm[k]] = I.y[k];
 }
 
 // factor outcome: success -> solve; wrong inertia -> next delta_w
@@ -456,11 +673,6 @@ __global__ void k_b_ctl_fact(const BI *bi, BCtl *ctl, int count) {
   BCtl &c = ctl[b];
   ++c.nfac;
   ++c.total_fac;
-  if (*sync_status(I) != 0) {
-    c.status = IPM_ERR_TIMEOUT;
-    c.ph = PH_DONE;
-    return;
-  }
   if (*I.info == INT_MAX) {
     if (c.dw > 0) c.delta_last = c.dw;
     c.ph = PH_SOLVE;
@@ -493,45 +705,7 @@ __global__ void k_b_jt_rhs(const BI *bi, const BCtl *ctl, int phase) {
     I.t[j] = base[j] + acc;
   }
 }
-__global__ void k_b_gather(const BI *bi, const BCtl *ctl, int phase) {
-  B_PROLOGUE(phase);
-  for (int k = gtid; k < I.D.n; k += gstride) I.y[k] = I.t[I.perm[k]];
-  for (int k = gtid; k < 2 * I.ns; k += gstride) I.sync[2 * I.ns + k] = 0;
-}
-template <typename V, bool Fwd>
-__global__ void __launch_bounds__(128) k_b_solve(const SolveTaskArgs<V> *SA, const int *start,
-                                                 int count, const BCtl *ctl, int phase,
-                                                 int *ticket) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  double *sL = reinterpret_cast<double *>(sm_raw);
-  __shared__ double ys[CIPM_SN_MAXW];
-  __shared__ SolveTaskArgs<V> sT;
-  __shared__ int s_t, s_inst, s_cur, s_ok;
-  if (threadIdx.x == 0) s_cur = -1;
-  __syncthreads();
-  while (true) {
-    if (threadIdx.x == 0) grab_ticket(start, count, ctl, phase, ticket, &s_t, &s_inst);
-    __syncthreads();
-    const int t = s_t, inst = s_inst;
-    const bool reload = inst >= 0 && inst != s_cur;
-    __syncthreads();
-    if (inst < 0) break;
-    if (reload) {
-      load_args(&sT, SA + inst);
-      if (threadIdx.x == 0) s_cur = inst;
-    }
-    __syncthreads();
-    const int local = t - start[inst];
-    if (Fwd) fwd_task(sT, sT.A.level_sn[local], sL, ys, &s_ok);
-    else bwd_task(sT, sT.A.level_sn[sT.ns - 1 - local], sL, ys, &s_ok);
-    __syncthreads();
-  }
-}
-__global__ void k_b_scatter_dz(const BI *bi, const BCtl *ctl, int phase) {
-  B_PROLOGUE(phase);
-  double *x = phase == PH_SOLVE ? I.dx : I.cx;
-  for (int k = gtid; k < I.D.n; k += gstride) x[I.perm[k]] = I.y[k];
-}
+
 __global__ void k_b_recover_dz(const BI *bi, const BCtl *ctl, int phase) {
   B_PROLOGUE(phase);
   const double *x = phase == PH_SOLVE ? I.dx : I.cx;
@@ -547,11 +721,6 @@ __global__ void k_b_ctl_solved(const BI *bi, BCtl *ctl, int count) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count || ctl[b].ph != PH_SOLVE) return;
   BCtl &c = ctl[b];
-  if (*sync_status(bi[b]) != 0) {
-    c.status = IPM_ERR_TIMEOUT;
-    c.ph = PH_DONE;
-    return;
-  }
   c.ref_it = 0;
   c.ref_steps = 0;
   c.eta = c.eta_prev = INFINITY;
@@ -595,11 +764,6 @@ __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine) 
   const BI &I = bi[b];
   BCtl &c = ctl[b];
   const double *sc = I.scal;
-  if (*sync_status(I) != 0) {
-    c.status = IPM_ERR_TIMEOUT;
-    c.ph = PH_DONE;
-    return;
-  }
   if (c.ref_it == 0) c.normA = sc[3];
   const double den = c.normA * sc[1] + sc[2];
   const double eta = den > 0 ? sc[0] / den : 0.0;
@@ -662,10 +826,10 @@ __global__ void k_b_ftb(const BI *bi, const BCtl *ctl) {
     gx += F.gx;
     gs += F.gs;
   }
-  red_min(I.R, R_AMAX, ap);
-  red_min(I.R, R_AZ, az);
-  red_sum(I.R, R_GPHI_X, gx);
-  red_sum(I.R, R_GPHI_S, gs);
+  const int slot[4] = {R_AMAX, R_AZ, R_GPHI_X, R_GPHI_S};
+  const int op[4] = {OP_MIN, OP_MIN, OP_SUM, OP_SUM};
+  double v[4] = {ap, az, gx, gs};
+  block_reduce_atomic<4>(I.R, slot, op, v);
 }
 __global__ void k_b_ctl_ls0(const BI *bi, BCtl *ctl, int count) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -707,11 +871,10 @@ __global__ void k_b_merit_trial(const BI *bi, const BCtl *ctl) {
     lxl += Mp.lxl;
     lxu += Mp.lxu;
   }
-  red_sum(I.R, R_TH_G, tg);
-  red_sum(I.R, R_TH_H, th);
-  red_sum(I.R, R_LOG_S, ls);
-  red_sum(I.R, R_LOG_XL, lxl);
-  red_sum(I.R, R_LOG_XU, lxu);
+  const int slot[5] = {R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU};
+  const int op[5] = {OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM};
+  double v[5] = {tg, th, ls, lxl, lxu};
+  block_reduce_atomic<5>(I.R, slot, op, v);
 }
 // filter acceptance (Ipopt: switching condition with the Armijo test on phi, else sufficient
 // decrease in theta or phi against the filter); backtrack by halves down to alpha_min
@@ -819,19 +982,25 @@ struct ipm_batch_s {
   size_t dpool_len = 0, ipool_len = 0;
   BI *d_bi = nullptr;
   BCtl *d_ctl = nullptr;
-  FactTaskArgs<double> *d_fa = nullptr;
-  SolveTaskArgs<double> *d_fw = nullptr, *d_bw = nullptr;
-  int *d_fstart = nullptr, *d_sstart = nullptr;  // ticket ranges [count + 1]
+  std::vector<void *> bufs;  // per-pattern level offsets
   int *d_tickets = nullptr;                      // 16 ticket counters, then the active count
   int *h_active = nullptr;                       // pinned
   int gx = 1, gx_gen = 1, max_ns = 1, fmax_entries = 0;
-  size_t fact_smem = 0, solve_smem = 0;
-  int grid_fact = 0, grid_solve = 0;
+  size_t fact_smem = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches_per_sweep = 0;
   int sweeps = 0;
   int max_iter = 3000;  // iteration limit of the captured sweep
+  // kernel timing (ipm_batch_set_timing): events around both factorization launches and the
+  // first solve of every sweep, recorded inside the sweep (graph event nodes when captured)
+  bool timing = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double t_fact_ms = 0.0, t_solve_ms = 0.0;
+  int t_n = 0;
+  double *x_stage = nullptr;  // all instances' x, contiguous (ipm_batch_export_all)
+  std::vector<int64_t> x_off;
+  int64_t x_total = 0;
 };
 
 namespace {
@@ -867,21 +1036,11 @@ int pattern_of(const OpfData &M, std::vector<int> &out) {
 int b_smem_limits() {
   static bool done = false;
   if (done) return IPM_OK;
-  const int big = 64 * 1024;
-  CK(cudaFuncSetAttribute(k_b_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_b_solve<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  CK(cudaFuncSetAttribute(k_b_solve<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  CK(cudaFuncSetAttribute(k_b_fact_inst, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   done = true;
   return IPM_OK;
 }
 
-int b_persistent_grid(const void *kernel, int threads, size_t smem) {
-  int dev = 0, nsm = 0, occ = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
-  return std::max(1, nsm) * std::max(1, std::min(occ, 4));
-}
 
 // every kernel of one sweep, in order; returns the number of launches
 int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
@@ -904,18 +1063,17 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_eval_finish<<<g2, blk, 0, s>>>(bi, ctl, phase, mode, B->gx_gen);
     L(4);
   };
-  auto solve = [&](int phase) {
+  auto rec = [&](int k) -> int {
+    if (B->timing) CK(cudaEventRecordWithFlags(B->ev[k], s, cudaEventRecordExternal));
+    return IPM_OK;
+  };
+  auto solve = [&](int phase) -> int {
     k_b_jt_rhs<<<g2, blk, 0, s>>>(bi, ctl, phase);
-    k_b_gather<<<g2, blk, 0, s>>>(bi, ctl, phase);
-    L(2);
-    CK(cudaMemsetAsync(B->d_tickets + 2, 0, sizeof(int) * 2, s));
-    k_b_solve<double, true><<<B->grid_solve, 128, B->solve_smem, s>>>(
-        B->d_fw, B->d_sstart, C, ctl, phase, B->d_tickets + 2);
-    k_b_solve<double, false><<<B->grid_solve, 128, B->solve_smem, s>>>(
-        B->d_bw, B->d_sstart, C, ctl, phase, B->d_tickets + 3);
-    k_b_scatter_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
+    if (phase == PH_SOLVE) CKR(rec(2));
+    k_b_solve_inst<<<C * B_CL, B_NT, 0, s>>>(bi, ctl, phase);
+    if (phase == PH_SOLVE) CKR(rec(3));
     k_b_recover_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
-    L(4);
+    L(3);
     return IPM_OK;
   };
   // evaluate at x, optimality error, convergence, barrier update
@@ -942,14 +1100,11 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   for (int r = 0; r < B_FACT_ROUNDS; ++r) {
     k_b_aug_rhs<<<g2, blk, 0, s>>>(bi, ctl, B->opt.gamma);
     k_b_scale_jv<<<g2, blk, 0, s>>>(bi, ctl);
-    k_b_condense<<<dim3(B->max_ns, C), 128, 0, s>>>(bi, ctl);
-    k_b_fact_reset<<<g2, blk, 0, s>>>(bi, ctl);
-    L(4);
-    CK(cudaMemsetAsync(B->d_tickets + 0, 0, sizeof(int), s));
-    k_b_factor<double><<<B->grid_fact, 256, B->fact_smem, s>>>(B->d_fa, B->d_fstart, C, ctl,
-                                                               B->d_tickets + 0);
+    CKR(rec(r == 0 ? 0 : 4));
+    k_b_fact_inst<<<C * B_CL, B_NT, B->fact_smem, s>>>(bi, ctl);
+    CKR(rec(r == 0 ? 1 : 5));
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
-    L(2);
+    L(4);
   }
   // condensed solve, then Richardson refinement on the augmented system
   CKR(solve(PH_SOLVE));
@@ -1085,7 +1240,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     size_t sigma, r1, r2, r4, Ds, dcond, baug, a, dx, dzc, jdx, dz, ds, dv, dzl, dzu;
     size_t xt, st, geqt, hint, gst, hst, ft, R, filter, tJ, Lx, Dx, y_s, t, cx, cz, outx, outz,
         scal;
-    size_t sync, info;
+    size_t info;
   };
   std::vector<Off> off(count);
   Bump dp, ip;
@@ -1113,7 +1268,6 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     o.Lx = dp.take(S->panel_len); o.Dx = dp.take(S->diag_len); o.y_s = dp.take(n);
     o.t = dp.take(n); o.cx = dp.take(n); o.cz = dp.take(m); o.outx = dp.take(n);
     o.outz = dp.take(m); o.scal = dp.take(8);
-    o.sync = ip.take(4 * (size_t)S->nsuper + 16);
     o.info = ip.take(1);
     max_elems = std::max({max_elems, M.n, (int)mi, (int)m, M.nnzJ, M.nnzW, 2 * M.nbr});
     B->max_ns = std::max(B->max_ns, S->nsuper);
@@ -1132,9 +1286,78 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     return fail(IPM_ERR_CUDA);
   // ---- descriptors, task-argument blocks and ticket ranges
   std::vector<BI> hbi(count);
-  std::vector<FactTaskArgs<double>> hfa(count);
-  std::vector<SolveTaskArgs<double>> hfw(count), hbw(count);
-  std::vector<int> fstart(count + 1, 0), sstart(count + 1, 0);
+  // wide supernodes of one level must fit the per-block list of the factorization kernel
+  for (ipm_sym_t S : B->syms) {
+    std::vector<int> sp(S->nsuper + 1), ls(S->nsuper);
+    if (cudaMemcpy(sp.data(), S->sptr, sizeof(int) * (S->nsuper + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(ls.data(), S->level_sn, sizeof(int) * S->nsuper, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
+    for (int L = 0; L < S->nlevels; ++L) {
+      int wide = 0;
+      for (int q = S->h_level_ptr[L]; q < S->h_level_ptr[L + 1]; ++q)
+        wide += sp[ls[q] + 1] - sp[ls[q]] > B_WS;
+      if (wide > B_WIDE_CAP) {
+        set_error_msg("ipm_batch_create: a level holds more wide supernodes than the batched "
+                      "factorization takes (" + std::to_string(B_WIDE_CAP) + ")");
+        return fail(IPM_ERR_BAD_ARG);
+      }
+    }
+  }
+  // update pairs of every pattern: for each supernode, the pairs (i, j) of its rows below the
+  // diagonal block and the slot of the target panel that entry (i, j) of L21 L21^T updates
+  std::vector<int *> pptr(B->syms.size()), pij(B->syms.size()), ptgt(B->syms.size());
+  for (size_t q = 0; q < B->syms.size(); ++q) {
+    ipm_sym_t S = B->syms[q];
+    const int ns = S->nsuper;
+    std::vector<int> sp(ns + 1), rp(ns + 1), sn(S->n);
+    std::vector<int64_t> lp(ns + 1);
+    if (cudaMemcpy(sp.data(), S->sptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(rp.data(), S->srow_ptr, sizeof(int) * (ns + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(sn.data(), S->snode, sizeof(int) * S->n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(lp.data(), S->lptr, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
+    std::vector<int> rows(rp[ns]);
+    if (rp[ns] && cudaMemcpy(rows.data(), S->srow, sizeof(int) * rp[ns], cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
+    if (S->panel_len >= INT_MAX) return fail(IPM_ERR_BAD_ARG);
+    std::vector<int> hp(ns + 1, 0), hij, htg;
+    for (int sn_ = 0; sn_ < ns; ++sn_) {
+      const int w = sp[sn_ + 1] - sp[sn_], rb = rp[sn_], ld = rp[sn_ + 1] - rb;
+      if (ld >= 65536) return fail(IPM_ERR_BAD_ARG);
+      for (int j = w; j < ld; ++j) {
+        const int col = rows[rb + j], ts = sn[col];
+        const int tb = rp[ts], tld = rp[ts + 1] - tb;
+        const int *tr = rows.data() + tb;
+        for (int i = j; i < ld; ++i) {
+          const int r = (int)(std::lower_bound(tr, tr + tld, rows[rb + i]) - tr);
+          hij.push_back(i << 16 | j);
+          htg.push_back((int)(lp[ts] + (int64_t)(col - sp[ts]) * tld + r));
+        }
+      }
+      hp[sn_ + 1] = (int)hij.size();
+    }
+    auto upi = [&](int **dst, const std::vector<int> &v) -> int {
+      if (cudaMalloc((void **)dst, sizeof(int) * std::max<size_t>(v.size(), 1)) != cudaSuccess)
+        return IPM_ERR_OOM;
+      B->bufs.push_back(*dst);
+      if (!v.empty() && cudaMemcpy(*dst, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return IPM_ERR_CUDA;
+      return IPM_OK;
+    };
+    int r1 = upi(&pptr[q], hp);
+    if (r1 == IPM_OK) r1 = upi(&pij[q], hij);
+    if (r1 == IPM_OK) r1 = upi(&ptgt[q], htg);
+    if (r1 != IPM_OK) return fail(r1);
+  }
+  // level offsets of each pattern's supernode schedule, on the device
+  std::vector<int *> lvl(B->syms.size(), nullptr);
+  for (size_t q = 0; q < B->syms.size(); ++q) {
+    const std::vector<int> &h = B->syms[q]->h_level_ptr;
+    if (cudaMalloc((void **)&lvl[q], sizeof(int) * h.size()) != cudaSuccess) return fail(IPM_ERR_OOM);
+    B->bufs.push_back(lvl[q]);
+    if (cudaMemcpy(lvl[q], h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
+  }
   for (int i = 0; i < count; ++i) {
     const OpfData &M = opfs[i]->M;
     ipm_sym_t S = B->syms[B->pat[i]];
@@ -1163,7 +1386,13 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.J_rowidx = S->J_rowidx; I.JT_ptr = S->JT_ptr; I.JT_ent = S->JT_ent; I.lptr = S->lptr;
     I.items = S->items; I.ns = S->nsuper;
     I.tJ = d + o.tJ; I.Lx = d + o.Lx; I.Dx = d + o.Dx;
-    I.sync = B->ipool + o.sync; I.info = B->ipool + o.info;
+    I.info = B->ipool + o.info;
+    I.srow = S->srow; I.snode = S->snode; I.level_sn = S->level_sn; I.dptr = S->dptr;
+    I.nlevels = S->nlevels;
+    I.lvl_ptr = lvl[B->pat[i]];
+    I.pair_ptr = pptr[B->pat[i]];
+    I.pair_ij = pij[B->pat[i]];
+    I.pair_tgt = ptgt[B->pat[i]];
     I.y = d + o.y_s; I.t = d + o.t; I.cx = d + o.cx; I.cz = d + o.cz; I.outx = d + o.outx;
     I.outz = d + o.outz; I.scal = d + o.scal;
     AugArgs &A = I.aug;
@@ -1175,29 +1404,6 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     A.Wv = I.Wv; A.sigma = I.SA.sigma; A.Jv = I.Jv; A.d = I.dcond; A.dw = 0.0;
     A.sx = I.dx; A.sz = I.dzc; A.ra = I.a; A.rb = I.baug; A.outx = I.outx; A.outz = I.outz;
     A.scal = I.scal; A.want_norm_a = 1;
-    // the model pattern arrays of the handle and of the symbolic analysis are equal; the
-    // products use the model's (rows of J by row pointer), the symbolic's transposes
-    const int ns = S->nsuper;
-    int *tail = I.sync + 4 * ns;
-    FactTaskArgs<double> &F = hfa[i];
-    F.F = FactArgs<double>{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->snode, S->lptr,
-                           S->dptr, I.Lx, I.Dx, I.info};
-    F.tasks = S->ftasks;
-    F.ntasks = S->nftasks;
-    F.upd_need = S->upd_need;
-    F.C = SyncCtl{I.sync, nullptr, tail + 1, tail + 2};
-    F.ns = ns;
-    for (SolveTaskArgs<double> *T : {&hfw[i], &hbw[i]}) {
-      T->A = SolveArgs<double>{S->level_sn, S->sptr, S->srow_ptr, S->srow, S->lptr, S->dptr,
-                               I.Lx, I.Dx, I.y};
-      T->snode = S->snode;
-      T->fwd_need = S->fwd_need;
-      T->ns = ns;
-    }
-    hfw[i].C = SyncCtl{I.sync + 2 * ns, nullptr, tail + 1, tail + 2};
-    hbw[i].C = SyncCtl{I.sync + 3 * ns, nullptr, tail + 1, tail + 2};
-    fstart[i + 1] = fstart[i] + S->nftasks;
-    sstart[i + 1] = sstart[i] + ns;
   }
   int rc = IPM_OK;
   auto up = [&](auto **dst, const auto &v) {
@@ -1211,11 +1417,6 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
       rc = IPM_ERR_CUDA;
   };
   up(&B->d_bi, hbi);
-  up(&B->d_fa, hfa);
-  up(&B->d_fw, hfw);
-  up(&B->d_bw, hbw);
-  up(&B->d_fstart, fstart);
-  up(&B->d_sstart, sstart);
   if (rc == IPM_OK && cudaMalloc(&B->d_ctl, sizeof(BCtl) * count) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMalloc(&B->d_tickets, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMemset(B->d_tickets, 0, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_CUDA;
@@ -1223,11 +1424,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   if (rc != IPM_OK) return fail(rc);
   int max_w = 1;
   for (ipm_sym_t S : B->syms) max_w = std::max(max_w, S->max_w);
-  B->fact_smem = sizeof(double) * std::max((size_t)max_w * max_w + (size_t)CIPM_RB * (max_w + 1),
-                                           2 * (size_t)CIPM_RB * (max_w + 1));
-  B->solve_smem = sizeof(double) * (size_t)max_w * max_w;
-  B->grid_fact = b_persistent_grid((const void *)k_b_factor<double>, 256, B->fact_smem);
-  B->grid_solve = b_persistent_grid((const void *)k_b_solve<double, true>, 128, B->solve_smem);
+  B->fact_smem = sizeof(double) *
+                 std::max((size_t)max_w * max_w + (size_t)32 * (max_w + 1),
+                          (size_t)(B_NT / 32) * (B_WS * B_WS + B_WS));
   rc = init_instances(B);
   if (rc == IPM_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = IPM_ERR_CUDA;
   if (rc != IPM_OK) return fail(rc);
@@ -1249,6 +1448,8 @@ extern "C" int ipm_batch_reset(ipm_batch_t B) {
   if (!B) return IPM_ERR_BAD_ARG;
   CKR(init_instances(B));
   B->sweeps = 0;
+  B->t_fact_ms = B->t_solve_ms = 0.0;
+  B->t_n = 0;
   return IPM_OK;
 }
 
@@ -1290,6 +1491,15 @@ extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int us
     count_launches(B->launches_per_sweep);
     ++B->sweeps;
     CK(cudaStreamSynchronize(s));
+    if (B->timing) {
+      float a = 0.f, a2 = 0.f, c = 0.f;
+      CK(cudaEventElapsedTime(&a, B->ev[0], B->ev[1]));
+      CK(cudaEventElapsedTime(&a2, B->ev[4], B->ev[5]));
+      CK(cudaEventElapsedTime(&c, B->ev[2], B->ev[3]));
+      B->t_fact_ms += a + a2;
+      B->t_solve_ms += c;
+      ++B->t_n;
+    }
     if (*B->h_active == 0) break;
   }
   k_b_finish_unfinished<<<grid_for(B->count, 128), 128, 0, s>>>(B->d_ctl, B->count);
@@ -1330,12 +1540,83 @@ extern "C" void ipm_batch_destroy(ipm_batch_t B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   for (ipm_sym_t S : B->syms) ipm_symbolic_destroy(S);
-  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_fa, B->d_fw, B->d_bw,
-                B->d_fstart, B->d_sstart, B->d_tickets};
+  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_tickets};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (B->h_active) cudaFreeHost(B->h_active);
+  for (void *p : B->bufs) cudaFree(p);
+  for (cudaEvent_t e : B->ev)
+    if (e) cudaEventDestroy(e);
+  if (B->x_stage) cudaFree(B->x_stage);
   delete B;
+}
+
+extern "C" int ipm_batch_work(ipm_batch_t B, double *factor_flops, double *condense_flops,
+                              double *bytes) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  for (int i = 0; i < B->count; ++i) {
+    ipm_sym_t S = B->syms[B->pat[i]];
+    const OpfData &M = B->opf[i]->M;
+    if (factor_flops) factor_flops[i] = S->flops;
+    if (condense_flops) condense_flops[i] = 2.0 * (double)S->nitems;
+    if (bytes)
+      bytes[i] = 8.0 * ((double)M.nnzJ + M.me + M.mi + M.nnzW + M.n) + 8.0 * (double)S->panel_len;
+  }
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_set_timing(ipm_batch_t B, int on) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  if ((on != 0) == B->timing) return IPM_OK;
+  if (on && !B->ev[0])
+    for (cudaEvent_t &e : B->ev) CK(cudaEventCreate(&e));
+  B->timing = on != 0;
+  if (B->exec) {  // the captured sweep changes: capture again at the next run
+    cudaGraphExecDestroy(B->exec);
+    cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+  }
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_kernel_time(ipm_batch_t B, double *fact_ms, double *solve_ms,
+                                     int *sweeps) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  if (fact_ms) *fact_ms = B->t_fact_ms;
+  if (solve_ms) *solve_ms = B->t_solve_ms;
+  if (sweeps) *sweeps = B->t_n;
+  return IPM_OK;
+}
+
+__global__ void k_b_gather_x(const BI *bi, const int64_t *off, double *out) {
+  const int b = blockIdx.y;
+  const BI &I = bi[b];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.D.n; j += gridDim.x * blockDim.x)
+    out[off[b] + j] = I.P.x[j];
+}
+
+extern "C" int ipm_batch_export_all(ipm_batch_t B, double *x_host) {
+  if (!B || !x_host) return IPM_ERR_BAD_ARG;
+  if (!B->x_stage) {
+    std::vector<BI> h(B->count);
+    CK(cudaMemcpy(h.data(), B->d_bi, sizeof(BI) * B->count, cudaMemcpyDeviceToHost));
+    B->x_off.assign(B->count + 1, 0);
+    for (int i = 0; i < B->count; ++i) B->x_off[i + 1] = B->x_off[i] + h[i].D.n;
+    B->x_total = B->x_off[B->count];
+    CK(cudaMalloc(&B->x_stage, sizeof(double) * (B->x_total + B->count + 1)));
+    // the offsets live after the staged values
+    CK(cudaMemcpy(B->x_stage + B->x_total, B->x_off.data(), sizeof(int64_t) * (B->count + 1),
+                  cudaMemcpyHostToDevice));
+  }
+  k_b_gather_x<<<dim3(B->gx, B->count), B_BLOCK, 0, B->stream>>>(
+      B->d_bi, (const int64_t *)(B->x_stage + B->x_total), B->x_stage);
+  count_launches(1);
+  CKL();
+  CK(cudaMemcpyAsync(x_host, B->x_stage, sizeof(double) * B->x_total, cudaMemcpyDeviceToHost,
+                     B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  return IPM_OK;
 }
 
 // the batched kernels keep their own copy of the spin limit

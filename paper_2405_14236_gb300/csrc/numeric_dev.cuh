@@ -35,12 +35,12 @@ __device__ __forceinline__ void condense_block(int s, const int *sptr, const int
                                                const int2 *items, const int *perm,
                                                const double *Wv, const double *sigma,
                                                const double *Jv, const double *tJ, double dw,
-                                               T *Lx) {
+                                               T *Lx, int tid, int nthreads) {
   int f = sptr[s], w = sptr[s + 1] - f;
   int ld = srow_ptr[s + 1] - srow_ptr[s];
   int64_t base = lptr[s];
   int64_t area = (int64_t)ld * w;
-  for (int64_t t = threadIdx.x; t < area; t += blockDim.x) {
+  for (int64_t t = tid; t < area; t += nthreads) {
     int c = (int)(t / ld), r = (int)(t - (int64_t)c * ld);
     int64_t slot = base + t;
     double v = 0.0;
@@ -65,7 +65,7 @@ __global__ void k_condense(const int *sptr, const int *srow_ptr, const int64_t *
                            const double *Wv, const double *sigma, const double *Jv,
                            const double *tJ, double dw, T *Lx) {
   condense_block<T>(blockIdx.x, sptr, srow_ptr, lptr, slot_ptr, items, perm, Wv, sigma, Jv, tJ,
-                    dw, Lx);
+                    dw, Lx, threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------- factorization

@@ -346,6 +346,15 @@ extern "C" int ipm_opf_eval(ipm_opf_t P, const double *x, const double *y, const
   return opf_eval(P->M, x, y, z, sigma_f, f, grad, g, h, J_val, W_val, s);
 }
 
+extern "C" int ipm_opf_set_loads(ipm_opf_t P, const double *pd, const double *qd,
+                                 cudaStream_t s) {
+  if (!P || !pd || !qd) return IPM_ERR_BAD_ARG;
+  const OpfData &M = P->M;
+  CK(cudaMemcpyAsync(M.pd, pd, sizeof(double) * M.nb, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(M.qd, qd, sizeof(double) * M.nb, cudaMemcpyDefault, s));
+  return IPM_OK;
+}
+
 extern "C" void ipm_opf_destroy(ipm_opf_t P) {
   if (!P) return;
   opf_free(P->M);

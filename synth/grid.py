@@ -218,12 +218,15 @@ def mixed_grid(seed: int, lo: int = 118, hi: int = 2000) -> Grid:
     return make_grid(nb, seed)
 
 
-def batch_grids(n_scen: int = 256, n_mixed: int = 64, base: str = "planar1k"):
+def batch_grids(n_scen: int = 256, n_mixed: int = 64, base: str = "planar1k", part: int = 0):
     """The batched workload: n_scen load scenarios of the base grid (per-bus scaling U[0.8, 1.2],
-    seeds 1000, 1001, ...) followed by n_mixed grids of 118-2000 buses (seeds 2000, 2001, ...)."""
+    seeds 1000, 1001, ...) followed by n_mixed grids of 118-2000 buses (seeds 2000, 2001, ...).
+    part > 0 draws another set of the same shape (scenario seeds from 1000 + 100000 part, mixed
+    seeds from 2000 + 100000 part), e.g. one set per GPU."""
     g = config_grid(base)
-    return ([scale_loads(g, 1000 + k) for k in range(n_scen)] +
-            [mixed_grid(2000 + k) for k in range(n_mixed)])
+    o = 100000 * part
+    return ([scale_loads(g, o + 1000 + k) for k in range(n_scen)] +
+            [mixed_grid(o + 2000 + k) for k in range(n_mixed)])
 
 
 def kkt_point(grid: Grid, seed: int, log_range: float = 8.0):
