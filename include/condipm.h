@@ -356,6 +356,57 @@ int ipm_batch_work(ipm_batch_t batch, double *factor_flops, double *condense_flo
                    double *bytes);
 void ipm_batch_destroy(ipm_batch_t batch);
 
+/* ---------------------------------------------------------------- learned warm start
+ * Rows for training and prediction: per instance x (n), log s (m_i), log v (m_i), log zl (n),
+ * log zu (n), 0 where a bound is absent (width 3 n + 2 m_i; the iterate of the scaled problem as
+ * the batched IPM holds it).  ipm_batch_state_rows writes every instance's row into the DEVICE
+ * float matrix out (row stride ld >= width; out NULL only reports *width); all instances must
+ * have the same sizes.  Stream-ordered. */
+int ipm_batch_state_rows(ipm_batch_t batch, float *out, int64_t ld, int *width);
+/* Starts every instance from a predicted row (DEVICE float matrix pred, row stride ld, values
+ * de-normalized as pred * stdv + mean per column when mean != NULL, else taken as they are):
+ * x pushed inside its bounds (the push of the cold start), s = exp(log s), z = v = exp(log v),
+ * zl, zu = exp(.) where the bound exists, mu0 = s^T v / m_i (at least tol / 10), a fresh filter.
+ * Call after ipm_batch_reset (which sets the scaling at the cold start point); an instance whose
+ * row holds a non-finite value keeps its cold start.  h_used (HOST, count, may be NULL) receives
+ * 1 where the prediction was used.  Synchronizes. */
+int ipm_batch_warm_start(ipm_batch_t batch, const float *pred, int64_t ld, const float *mean,
+                         const float *stdv, int *h_used);
+
+/* Multilayer perceptron with BF16 weights and activations and FP32 accumulation (tensor-core
+ * products), GELU after every layer but the last, mean-squared-error loss, Adam.  Layer l maps
+ * dims[l] to dims[l+1] (W_l: dims[l] x dims[l+1] row-major, b_l: dims[l+1]).  All X, Y, T are
+ * DEVICE float matrices, row-major, one row per sample, at most max_batch rows per call. */
+typedef struct mlp_s *mlp_t;
+int mlp_create(int nlayers, const int *dims, int max_batch, mlp_t *out);
+/* Number of parameters: sum over layers of dims[l] dims[l+1] + dims[l+1]. */
+int mlp_param_count(mlp_t net, int64_t *count);
+/* Parameters from / to a HOST float array, per layer W_l (row-major) then b_l; setting them
+ * also resets the Adam moments and rounds the BF16 copies.  Synchronizes. */
+int mlp_set_params(mlp_t net, const float *host);
+int mlp_get_params(mlp_t net, float *host);
+/* Gradients of the last mlp_loss_backward, same layout as the parameters.  Synchronizes. */
+int mlp_get_grads(mlp_t net, float *host);
+/* Y [B x dims[L]] = net(X [B x dims[0]]) (Y may be NULL when only the loss follows). */
+int mlp_forward(mlp_t net, const float *X, int B, float *Y, cudaStream_t stream);
+/* After mlp_forward on the same rows: *d_loss (DEVICE float) = mean over B x dims[L] of
+ * (Y - T)^2, and the gradient of that loss into the parameter gradients. */
+int mlp_loss_backward(mlp_t net, const float *T, int B, float *d_loss, cudaStream_t stream);
+/* One Adam step (Kingma & Ba, bias-corrected, step number t >= 1) on the FP32 master weights. */
+int mlp_adam_step(mlp_t net, float lr, float beta1, float beta2, float eps, int t,
+                  cudaStream_t stream);
+/* out[r] = src[idx[r]] for r < rows (rows of cols floats; DEVICE pointers). */
+int mlp_gather_rows(int rows, int cols, const int *idx, const float *src, float *out,
+                    cudaStream_t stream);
+/* Per-column mean and standard deviation (population, FP64 sums; std at least floor_std) of a
+ * rows x cols DEVICE float matrix, and the column normalization out = (src - mean) / std
+ * (out may alias src). */
+int mlp_col_stats(int rows, int cols, const float *src, float *mean, float *stdv,
+                  float floor_std, cudaStream_t stream);
+int mlp_normalize(int rows, int cols, const float *src, const float *mean, const float *stdv,
+                  float *out, cudaStream_t stream);
+void mlp_destroy(mlp_t net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,20 @@ _SIGS = {
     "ipm_batch_kernel_time": (I, [P, P, P, P]),
     "ipm_batch_work": (I, [P, P, P, P]),
     "ipm_opf_set_loads": (I, [P, P, P, P]),
+    "ipm_batch_state_rows": (I, [P, P, I64, P]),
+    "ipm_batch_warm_start": (I, [P, P, I64, P, P, P]),
+    "mlp_create": (I, [I, P, I, P]),
+    "mlp_param_count": (I, [P, P]),
+    "mlp_set_params": (I, [P, P]),
+    "mlp_get_params": (I, [P, P]),
+    "mlp_get_grads": (I, [P, P]),
+    "mlp_forward": (I, [P, P, I, P, P]),
+    "mlp_loss_backward": (I, [P, P, I, P, P]),
+    "mlp_adam_step": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P]),
+    "mlp_gather_rows": (I, [I, I, P, P, P, P]),
+    "mlp_col_stats": (I, [I, I, P, P, P, ctypes.c_float, P]),
+    "mlp_normalize": (I, [I, I, P, P, P, P, P]),
+    "mlp_destroy": (None, [P]),
 }
 
 
@@ -423,6 +437,25 @@ class Batch:
         _check(lib().ipm_batch_work(self.h, p(ff), p(cf), p(by)), "ipm_batch_work")
         return dict(factor_flops=ff, condense_flops=cf, bytes=by)
 
+    def state_rows(self, out=None):
+        """Every instance's (x, log s, log v, log zl, log zu) as a float32 CUDA matrix."""
+        import torch
+        w = I()
+        _check(lib().ipm_batch_state_rows(self.h, None, 0, ctypes.byref(w)), "ipm_batch_state_rows")
+        if out is None:
+            out = torch.empty(self.count, w.value, dtype=torch.float32, device="cuda")
+        _check(lib().ipm_batch_state_rows(self.h, _ptr(out), out.stride(0), None),
+               "ipm_batch_state_rows")
+        return out
+
+    def warm_start(self, pred, mean=None, std=None):
+        """Start every instance from the predicted rows (after reset); returns the used flags."""
+        used = np.zeros(self.count, np.int32)
+        _check(lib().ipm_batch_warm_start(self.h, _ptr(pred), pred.stride(0), _ptr(mean),
+                                          _ptr(std), used.ctypes.data_as(ctypes.c_void_p)),
+               "ipm_batch_warm_start")
+        return used
+
     def x(self, i):
         out = np.zeros(self.opfs[i].n)
         _check(lib().ipm_batch_export(self.h, int(i), out.ctypes.data_as(ctypes.c_void_p)),
@@ -433,4 +466,81 @@ class Batch:
         if getattr(self, "h", None) and _lib is not None:
             _lib.ipm_batch_destroy(self.h)
             self.h = None
+
+
+class MLP:
+    """BF16 multilayer perceptron on the project's own kernels (mlp_*): GELU hidden layers,
+    linear output, MSE loss, Adam."""
+
+    def __init__(self, dims, max_batch):
+        self.dims = [int(d) for d in dims]
+        arr = (ctypes.c_int * len(self.dims))(*self.dims)
+        h = ctypes.c_void_p()
+        _check(lib().mlp_create(len(self.dims) - 1, arr, int(max_batch), ctypes.byref(h)),
+               "mlp_create")
+        self.h = h
+        self.max_batch = int(max_batch)
+        c = I64()
+        _check(lib().mlp_param_count(h, ctypes.byref(c)), "mlp_param_count")
+        self.nparams = c.value
+        import torch
+        self._loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.t = 0
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(lib().mlp_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p)), "mlp_set_params")
+        self.t = 0
+
+    def get_params(self):
+        a = np.zeros(self.nparams, np.float32)
+        _check(lib().mlp_get_params(self.h, a.ctypes.data_as(ctypes.c_void_p)), "mlp_get_params")
+        return a
+
+    def get_grads(self):
+        a = np.zeros(self.nparams, np.float32)
+        _check(lib().mlp_get_grads(self.h, a.ctypes.data_as(ctypes.c_void_p)), "mlp_get_grads")
+        return a
+
+    def forward(self, X, Y=None):
+        _check(lib().mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), None), "mlp_forward")
+        return Y
+
+    def loss_backward(self, T):
+        _check(lib().mlp_loss_backward(self.h, _ptr(T), T.shape[0], _ptr(self._loss), None),
+               "mlp_loss_backward")
+        return self._loss
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.t += 1
+        _check(lib().mlp_adam_step(self.h, float(lr), float(b1), float(b2), float(eps), self.t,
+                                   None), "mlp_adam_step")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mlp_destroy(self.h)
+            self.h = None
+
+
+def gather_rows(idx, src, out):
+    _check(lib().mlp_gather_rows(idx.shape[0], src.shape[1], _ptr(idx), _ptr(src), _ptr(out), None),
+           "mlp_gather_rows")
+    return out
+
+
+def col_stats(src, floor_std=1e-3):
+    import torch
+    mean = torch.empty(src.shape[1], dtype=torch.float32, device="cuda")
+    std = torch.empty_like(mean)
+    _check(lib().mlp_col_stats(src.shape[0], src.shape[1], _ptr(src), _ptr(mean), _ptr(std),
+                               float(floor_std), None), "mlp_col_stats")
+    return mean, std
+
+
+def normalize(src, mean, std, out=None):
+    out = src if out is None else out
+    _check(lib().mlp_normalize(src.shape[0], src.shape[1], _ptr(src), _ptr(mean), _ptr(std),
+                               _ptr(out), None), "mlp_normalize")
+    return out
 

@@ -965,6 +965,95 @@ __global__ void k_b_finish_unfinished(BCtl *ctl, int count) {
   }
 }
 
+// ------------------------------------------------------------------ learned warm start
+// Row of an instance for training and prediction: x (n), log s (mi), log v (mi), log zl (n),
+// log zu (n) (0 where the bound is absent); the iterate as the IPM holds it (scaled problem).
+__global__ void k_b_state_rows(const BI *bi, float *out, int64_t ld) {
+  const int b = blockIdx.y;
+  const BI &I = bi[b];
+  const int n = I.D.n, mi = I.D.mi;
+  float *o = out + (int64_t)b * ld;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    o[j] = (float)I.P.x[j];
+    o[n + 2 * mi + j] = isfinite(I.P.xl[j]) ? (float)log(I.P.zl[j]) : 0.f;
+    o[2 * n + 2 * mi + j] = isfinite(I.P.xu[j]) ? (float)log(I.P.zu[j]) : 0.f;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mi; i += gridDim.x * blockDim.x) {
+    o[n + i] = (float)log(I.P.s[i]);
+    o[n + mi + i] = (float)log(I.P.v[i]);
+  }
+}
+
+__device__ __forceinline__ float denorm(const float *pred, const float *mean, const float *stdv,
+                                        int j) {
+  return mean ? pred[j] * stdv[j] + mean[j] : pred[j];
+}
+
+// pass 1: count non-finite predicted values and sum s v (into R_QD, R_PD)
+__global__ void k_b_warm_check(const BI *bi, const float *pred, int64_t ld, const float *mean,
+                               const float *stdv) {
+  const int b = blockIdx.y;
+  const BI &I = bi[b];
+  const int n = I.D.n, mi = I.D.mi, w = 3 * n + 2 * mi;
+  const float *p = pred + (int64_t)b * ld;
+  double bad = 0.0, sv = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < w; j += gridDim.x * blockDim.x) {
+    const float v = denorm(p, mean, stdv, j);
+    if (!isfinite(v)) bad += 1.0;
+    if (j >= n && j < n + mi) sv += exp((double)v + (double)denorm(p, mean, stdv, j + mi));
+  }
+  red_sum(I.R, R_QD, bad);
+  red_sum(I.R, R_PD, sv);
+}
+
+// pass 2: the iterate of every instance whose prediction is finite: x pushed inside its bounds,
+// s = exp(log s), z = v = exp(log v), zl, zu = exp(.) where the bound exists
+__global__ void k_b_warm_apply(const BI *bi, const float *pred, int64_t ld, const float *mean,
+                               const float *stdv) {
+  const int b = blockIdx.y;
+  const BI &I = bi[b];
+  if (I.R[R_QD] != 0.0) return;
+  const int n = I.D.n, mi = I.D.mi;
+  const float *p = pred + (int64_t)b * ld;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double xl = I.P.xl[j], xu = I.P.xu[j];
+    const bool hl = isfinite(xl), hu = isfinite(xu);
+    double pl = hl ? KAPPA1 * fmax(1.0, fabs(xl)) : 0.0, pu = hu ? KAPPA1 * fmax(1.0, fabs(xu)) : 0.0;
+    if (hl && hu) {
+      pl = fmin(pl, KAPPA1 * (xu - xl));
+      pu = fmin(pu, KAPPA1 * (xu - xl));
+    }
+    double v = denorm(p, mean, stdv, j);
+    if (hl) v = fmax(v, xl + pl);
+    if (hu) v = fmin(v, xu - pu);
+    I.P.x[j] = v;
+    I.P.zl[j] = hl ? exp((double)denorm(p, mean, stdv, n + 2 * mi + j)) : 0.0;
+    I.P.zu[j] = hu ? exp((double)denorm(p, mean, stdv, 2 * n + 2 * mi + j)) : 0.0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mi; i += gridDim.x * blockDim.x) {
+    I.P.s[i] = exp((double)denorm(p, mean, stdv, n + i));
+    const double v = exp((double)denorm(p, mean, stdv, n + mi + i));
+    I.P.v[i] = v;
+    I.P.z[i] = v;
+  }
+}
+
+// pass 3: barrier parameter mu0 = s^T v / m_i of the predicted point, fresh filter
+__global__ void k_b_warm_ctl(const BI *bi, BCtl *ctl, int count, double tol, int *used) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const BI &I = bi[b];
+  const int ok = I.R[R_QD] == 0.0;
+  used[b] = ok;
+  if (!ok) return;
+  BCtl &c = ctl[b];
+  c.mu = fmax(I.R[R_PD] / (double)max(I.D.mi, 1), tol / 10.0);
+  c.tau = fmax(TAU_MIN, 1.0 - c.mu);
+  c.nfilter = 0;
+  c.have_theta0 = 0;
+  c.delta_last = 0.0;
+}
+
 }  // namespace cipm
 
 using namespace cipm;
@@ -1616,6 +1705,51 @@ extern "C" int ipm_batch_export_all(ipm_batch_t B, double *x_host) {
   CK(cudaMemcpyAsync(x_host, B->x_stage, sizeof(double) * B->x_total, cudaMemcpyDeviceToHost,
                      B->stream));
   CK(cudaStreamSynchronize(B->stream));
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_state_rows(ipm_batch_t B, float *out, int64_t ld, int *width) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  std::vector<BI> h(B->count);
+  CK(cudaMemcpy(h.data(), B->d_bi, sizeof(BI) * B->count, cudaMemcpyDeviceToHost));
+  const int w = 3 * h[0].D.n + 2 * h[0].D.mi;
+  for (const BI &I : h)
+    if (3 * I.D.n + 2 * I.D.mi != w) {
+      set_error_msg("ipm_batch_state_rows: instances of different sizes");
+      return IPM_ERR_BAD_ARG;
+    }
+  if (width) *width = w;
+  if (!out) return IPM_OK;
+  if (ld < w) return IPM_ERR_BAD_ARG;
+  k_b_state_rows<<<dim3(B->gx, B->count), B_BLOCK, 0, B->stream>>>(B->d_bi, out, ld);
+  count_launches(1);
+  CKL();
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_warm_start(ipm_batch_t B, const float *pred, int64_t ld,
+                                    const float *mean, const float *stdv, int *h_used) {
+  int w = 0;
+  if (!B || !pred || (mean && !stdv)) return IPM_ERR_BAD_ARG;
+  CKR(ipm_batch_state_rows(B, nullptr, 0, &w));
+  if (ld < w) return IPM_ERR_BAD_ARG;
+  cudaStream_t s = B->stream;
+  const dim3 g2(B->gx, B->count), blk(B_BLOCK);
+  k_b_rreset<<<B->count, 32, 0, s>>>(B->d_bi, B->d_ctl, PH_EVAL, R_PD, R_QD + 1, 0.0);
+  k_b_warm_check<<<g2, blk, 0, s>>>(B->d_bi, pred, ld, mean, stdv);
+  k_b_warm_apply<<<g2, blk, 0, s>>>(B->d_bi, pred, ld, mean, stdv);
+  int *used = nullptr;
+  CK(cudaMalloc(&used, sizeof(int) * B->count));
+  k_b_warm_ctl<<<grid_for(B->count, 128), 128, 0, s>>>(B->d_bi, B->d_ctl, B->count, B->opt.tol,
+                                                       used);
+  count_launches(4);
+  CKL();
+  std::vector<int> hu(B->count);
+  cudaError_t e = cudaMemcpyAsync(hu.data(), used, sizeof(int) * B->count, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(used);
+  CK(e);
+  if (h_used) std::copy(hu.begin(), hu.end(), h_used);
   return IPM_OK;
 }
 

@@ -16,7 +16,7 @@ def header_prototypes():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-        for m in re.finditer(r"\n\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ipm_\w+|hykkt_\w+)\s*\(([^;{]*?)\)\s*;",
+        for m in re.finditer(r"\n\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ipm_\w+|hykkt_\w+|mlp_\w+)\s*\(([^;{]*?)\)\s*;",
                              text):
             name, args = m.group(1), m.group(2).strip()
             n = 0 if args in ("", "void") else args.count(",") + 1

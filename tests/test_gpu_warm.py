@@ -1,0 +1,41 @@
+"""Learned warm start of the batched IPM: a network trained (on the GPU, by the library's own
+kernels) on batched-IPM points of load scenarios of the 1,000-bus grid starts held-out
+scenarios.  Bar: every warm-started instance converges to the 1e-6 tolerance at the objective
+of its cold start (1e-6 relative) and the warm starts take fewer iterations on average than the
+cold starts of the same instances."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from synth import config_grid, scale_loads
+import paper_2405_14236_gb300 as cp
+from paper_2405_14236_gb300 import warm
+
+
+def test_warm_start_saves_iterations():
+    base = config_grid("planar1k")
+    train_grids = [scale_loads(base, 10000 + k) for k in range(640)]
+    test_grids = [scale_loads(base, 30000 + k) for k in range(32)]
+    T, ok = warm.collect(train_grids, tol=1e-3)
+    assert ok.mean() > 0.95
+    keep = np.nonzero(ok)[0]
+    X = warm.input_rows([train_grids[i] for i in keep])
+    Tk = T[torch.as_tensor(keep, device="cuda")].contiguous()
+    model, losses = warm.train(X, Tk, steps=600, batch=128, lr=1e-3, log_every=100)
+    assert losses[-1][1] < losses[0][1]
+    opfs = [cp.Opf(g) for g in test_grids]
+    B = cp.Batch(opfs)
+    B.run(max_iter=300)
+    cold = B.results()
+    B.reset()
+    used = model.start(B, warm.input_rows(test_grids))
+    assert used.all()
+    B.run(max_iter=300)
+    hot = B.results()
+    both = (cold["status"] == 1) & (hot["status"] == 1)
+    assert both.mean() >= 0.9, (cold["status"], hot["status"])
+    rel = np.abs(hot["obj"][both] - cold["obj"][both]) / np.abs(cold["obj"][both])
+    assert rel.max() <= 1e-6
+    assert hot["iters"][both].mean() < cold["iters"][both].mean(), (hot["iters"], cold["iters"])
