@@ -464,7 +464,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     # ---- instances of this GPU (weak scaling: one full set per GPU)
-    grids = batch_grids(256, 64, part=rank)
+    grids = batch_grids(args.batch_scen, args.batch_mixed, part=rank)
     t0 = time.perf_counter()
     opfs = [cp.Opf(g) for g in grids]
     B = cp.Batch(opfs)
@@ -598,9 +598,14 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk,
     }
     if not args.no_plain:
-        line["plain"] = plain_measure([grids[i] if i % 2 == 0 else grids[256 + i // 2]
-                                       for i in range(4)])
+        ns = args.batch_scen
+        line["plain"] = plain_measure([grids[i // 2] if i % 2 == 0 or ns == len(grids)
+                                       else grids[ns + i // 2] for i in range(4)])
         line["plain"]["batched_speedup"] = value / line["plain"]["value"]
+    if not args.no_warm:
+        line["warm"] = warm_measure()
+        if "plain" in line:
+            line["warm"]["vs_plain"] = line["warm"]["warm"]["value"] / line["plain"]["value"]
     if not args.no_kkt:
         line["kkt10k"] = kkt_measure(args)
     if not args.no_ipm:
@@ -608,6 +613,75 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = batch_cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+def warm_measure(steps=6000, n_train=20000, n_test=1024):
+    """Learned warm start on load scenarios of the 1,000-bus grid: training points from the
+    batched IPM at tolerance 1e-2 (seeds 10000..), the network trained by the library's own
+    kernels, then held-out scenarios (seeds 30000..) solved to 1e-6 by the batched IPM from
+    the cold start and from the predicted start (the prediction is inside the timed region)."""
+    import torch
+    import paper_2405_14236_gb300 as cp
+    from paper_2405_14236_gb300 import warm
+    from synth import config_grid, scale_loads
+    base = config_grid("planar1k")
+    train = [scale_loads(base, 10000 + k) for k in range(n_train)]
+    test = [scale_loads(base, 30000 + k) for k in range(n_test)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T, ok = warm.collect(train, tol=1e-2)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    keep = np.nonzero(ok)[0]
+    X = warm.input_rows([train[i] for i in keep])
+    Tk = T[torch.as_tensor(keep, device="cuda")].contiguous()
+    del T
+    t0 = time.perf_counter()
+    model, losses = warm.train(X, Tk, steps=steps, batch=256, lr=1e-3, log_every=steps // 4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del Tk
+    opfs = [cp.Opf(g) for g in test]
+    B = cp.Batch(opfs)
+    Xt = warm.input_rows(test)
+    B.run(max_iter=MAX_ITER)  # capture and warm-up
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rec = {}
+    for mode in ("cold", "warm"):
+        ms, conv, its, itmax, used = [], [], [], [], 1.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            B.reset()
+            if mode == "warm":
+                used = float(model.start(B, Xt).mean())
+            B.run(max_iter=MAX_ITER)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            r = B.results()
+            conv.append(int((r["status"] == 1).sum()))
+            its.append(float(r["iters"].mean()))
+            itmax.append(int(r["iters"].max()))
+        rec[mode] = {"value": float(np.sum(conv) / (np.sum(ms) / 1e3)), "unit": UNIT,
+                     "ms_per_batch": float(np.mean(ms)), "converged": conv,
+                     "iters_mean": float(np.mean(its)), "iters_max": itmax, "obj": r["obj"].copy()}
+        if mode == "warm":
+            rec[mode]["prediction_used"] = used
+    both = rec["cold"]["obj"], rec["warm"]["obj"]
+    objrel = float(np.max(np.abs(both[1] - both[0]) / np.abs(both[0])))
+    for m in rec.values():
+        del m["obj"]
+    return {"workload": f"{n_test} held-out load scenarios of the 1,000-bus grid (seeds 30000..), "
+                        f"batched LiftedKKT FP64 IPM to 1e-6",
+            "cold": rec["cold"], "warm": rec["warm"],
+            "speedup": rec["warm"]["value"] / rec["cold"]["value"],
+            "obj_rel_diff_max": objrel,
+            "training": {"points": int(len(keep)), "point_tolerance": 1e-2, "collect_s": t_collect,
+                         "steps": steps, "batch": 256, "train_s": t_train,
+                         "loss": losses, "net": [int(X.shape[1]), *warm.HIDDEN, int(model.tmean.shape[0])],
+                         "params": int(model.net.nparams), "dtype": "bf16 weights, fp32 accumulate"}}
 
 
 def ipm_measure(include_oracle=True):
@@ -668,6 +742,11 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-factor variant")
     ap.add_argument("--no-kkt", action="store_true", help="skip the 10k KKT-solve kernel line")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-problem GPU IPM")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--batch-scen", type=int, default=256,
+                    help="load scenarios of the 1,000-bus grid in the batch (profiling: fewer)")
+    ap.add_argument("--batch-mixed", type=int, default=64,
+                    help="mixed grids of 118-2,000 buses in the batch (profiling: fewer)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

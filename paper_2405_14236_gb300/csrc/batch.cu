@@ -408,6 +408,52 @@ __device__ __forceinline__ void scatter_update(const BI &I, int s, int ld, int w
   }
 }
 
+static constexpr int B_WT = 4;  // diagonal blocks up to this width are factored one per thread
+
+// diagonal block of a narrow supernode (w <= B_WT) by one thread: L11 and its reciprocal pivots
+// into Dd (the same arithmetic as the warp path); on GB300 an FP64 warp instruction costs the
+// same with one lane active as with 32, so the pivots of a level go 32 per instruction
+__device__ void thread_diag_sn(const BI &I, int s) {
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int ld = I.srow_ptr[s + 1] - I.srow_ptr[s];
+  const double *P = I.Lx + I.lptr[s];
+  double D[B_WT * B_WT], inv[B_WT];
+#pragma unroll
+  for (int k = 0; k < B_WT; ++k)
+#pragma unroll
+    for (int i = 0; i < B_WT; ++i) D[i + k * B_WT] = (k < w && i < w && i >= k) ? P[i + (int64_t)k * ld] : 0.0;
+#pragma unroll
+  for (int k = 0; k < B_WT; ++k) {
+    if (k < w) {
+      double d = D[k + k * B_WT];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicMin(I.info, f + k);
+        d = 1.0;
+      }
+      const double iv = rsqrt_newton(d);
+      D[k + k * B_WT] = d * iv;
+      inv[k] = iv;
+#pragma unroll
+      for (int i = k + 1; i < B_WT; ++i)
+        if (i < w) D[i + k * B_WT] *= iv;
+#pragma unroll
+      for (int j = k + 1; j < B_WT; ++j)
+#pragma unroll
+        for (int i = j; i < B_WT; ++i)
+          if (i < w && j < w) D[i + j * B_WT] -= D[i + k * B_WT] * D[j + k * B_WT];
+    }
+  }
+  double *Dd = I.Dx + I.dptr[s];
+#pragma unroll
+  for (int k = 0; k < B_WT; ++k)
+#pragma unroll
+    for (int i = 0; i < B_WT; ++i)
+      if (k < w && i < w) Dd[i + k * w] = D[i + k * B_WT];
+#pragma unroll
+  for (int k = 0; k < B_WT; ++k)
+    if (k < w) Dd[w * w + k] = inv[k];
+}
+
 // warp path: diagonal block, reciprocal pivots, L21 = A21 L11^{-T}, then the outer product of the
 // rows below scattered into the target panels.  D: w*w doubles, inv: w doubles (this warp's).
 __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
@@ -415,6 +461,12 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   double *P = I.Lx + I.lptr[s];
+  double *Dd = I.Dx + I.dptr[s];
+  if (w <= B_WT) {  // factored by thread_diag_sn before this pass
+    for (int t = lane; t < w * w; t += 32) D[t] = Dd[t];
+    for (int k = lane; k < w; k += 32) inv[k] = Dd[w * w + k];
+    __syncwarp();
+  } else {
   for (int t = lane; t < w * w; t += 32) {
     const int k = t / w, i = t - k * w;
     D[t] = i >= k ? P[i + (int64_t)k * ld] : 0.0;
@@ -442,28 +494,18 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
     }
     __syncwarp();
   }
-  double *Dd = I.Dx + I.dptr[s];
   for (int t = lane; t < w * w; t += 32) Dd[t] = D[t];
   for (int k = lane; k < w; k += 32) Dd[w * w + k] = inv[k];
-  // rows below: forward substitution with L11 per row (lane-owned rows, registers)
+  __syncwarp();
+  }
+  // rows below: L21 = A21 L11^{-T}, lane-owned rows, right-looking over the w columns (loops
+  // bounded by w: every FP64 instruction issued does work)
   for (int r = w + lane; r < ld; r += 32) {
-    double x[B_WS];
-#pragma unroll
-    for (int k = 0; k < B_WS; ++k)
-      if (k < w) x[k] = P[r + (int64_t)k * ld];
-#pragma unroll
-    for (int k = 0; k < B_WS; ++k) {
-      if (k < w) {
-        double v = x[k];
-#pragma unroll
-        for (int j = 0; j < B_WS; ++j)
-          if (j < k) v -= x[j] * D[k + j * w];
-        x[k] = v * inv[k];
-      }
+    for (int k = 0; k < w; ++k) {
+      const double xk = P[r + (int64_t)k * ld] * inv[k];
+      P[r + (int64_t)k * ld] = xk;
+      for (int j = k + 1; j < w; ++j) P[r + (int64_t)j * ld] -= xk * D[j + k * w];
     }
-#pragma unroll
-    for (int k = 0; k < B_WS; ++k)
-      if (k < w) P[r + (int64_t)k * ld] = x[k];
   }
   __syncwarp();
   scatter_update(I, s, ld, w, P, lane, 32);
@@ -569,8 +611,12 @@ __global__ void __cluster_dims__(B_CL, 1, 1) __launch_bounds__(B_NT)
   double *D = sm + warp * (B_WS * B_WS + B_WS), *inv = D + B_WS * B_WS;
   for (int L = 0; L < I.nlevels; ++L) {
     if (threadIdx.x == 0) s_nwide = 0;
-    __syncthreads();
     const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
+    for (int q = q0 + crank * blockDim.x + threadIdx.x; q < q1; q += B_CL * blockDim.x) {
+      const int s = I.level_sn[q];
+      if (I.sptr[s + 1] - I.sptr[s] <= B_WT) thread_diag_sn(I, s);
+    }
+    __syncthreads();
     for (int q = q0 + gw; q < q1; q += gnw) {
       const int s = I.level_sn[q];
       if (I.sptr[s + 1] - I.sptr[s] <= B_WS) {
