@@ -433,6 +433,20 @@ def kkt_measure(args):
     return line
 
 
+def aggregate_ranks(t_ms, converged, world, device):
+    """Whole-job figures of a run on `world` ranks: the slowest rank's time and the sum of the
+    converged instances (each rank solves its own instance set)."""
+    if world == 1:
+        return t_ms, converged
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    c = torch.tensor([converged], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def plain_measure(grids):
     """Single-problem GPU IPM (ipm_step loop, LiftedKKT FP64) on the given instances, one after
     another; time of the iterations (the per-problem symbolic analysis excluded, as for the
@@ -512,15 +526,7 @@ def run_gpu(args, rank, world, local_rank):
         sweeps.append(int(r["sweeps"]))
     launches = cp.launch_count() - l0
     clk = clocks.stop()
-    t_tot = float(np.sum(step_ms))
-    tot_conv = float(np.sum(conv))
-    if world > 1:
-        tt = torch.tensor([t_tot, tot_conv], dtype=torch.float64, device="cuda")
-        t_max = tt[:1].clone()
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-        c_sum = tt[1:].clone()
-        torch.distributed.all_reduce(c_sum, op=torch.distributed.ReduceOp.SUM)
-        t_tot, tot_conv = float(t_max.item()), float(c_sum.item())
+    t_tot, tot_conv = aggregate_ranks(float(np.sum(step_ms)), float(np.sum(conv)), world, "cuda")
     value = tot_conv / (t_tot / 1e3)
     # ---- e2e through the public API with host data: new loads for every scenario from host
     # memory, solve, every x back to host memory
