@@ -569,8 +569,10 @@ def run_gpu(args, rank, world, local_rank):
             tr = json.load(open(tfile))
             h = hashlib.sha256(open(os.path.join(ROOT, "paper_2405_14236_gb300", "csrc",
                                                   "batch.cu"), "rb").read()).hexdigest()[:16]
-            if tr.get("batch_cu_sha") == h:
-                traffic = tr.get("k_b_fact_inst_bytes_per_launch")
+            if tr.get("batch_cu_sha") == h and tr.get("k_b_fact_inst_traffic_over_algorithmic"):
+                # measured DRAM bytes / algorithmic bytes of a 40-instance launch, scaled to this
+                # launch's algorithmic bytes (traffic grows with the instances factored)
+                traffic = tr["k_b_fact_inst_traffic_over_algorithmic"] * by_per_fact / launches_fact
         except Exception:
             traffic = None
     line = {
