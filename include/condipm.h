@@ -258,9 +258,13 @@ void ipm_opf_destroy(ipm_opf_t opf);
  * correction and multiplier safeguards as cited in Section 2.2).
  */
 typedef struct {
-  int kkt;          /* 0 = LiftedKKT (Section 3.2), 1 = HyKKT (Section 3.1) */
+  int kkt;          /* 0 = LiftedKKT (Section 3.2), 1 = HyKKT (Section 3.1), 2 = dual-regularized
+                       condensed form with delta_c = 1/gamma (Remark in Section 3): one condensed
+                       solve of K + G^T G / delta_c refined on the regularized augmented system */
   double tol;       /* scaled KKT tolerance (e.g. 1e-6) */
-  double gamma;     /* HyKKT regularization gamma */
+  double gamma;     /* gamma of forms 1 and 2; <= 0: ||K||_inf / ||G||_inf^2 every iteration
+                       (Golub & Greif, recommended in Section 3.1), ||K|| bounded by the row sums
+                       of |W + Sigma_x| + |H|^T |D_s| |H| */
   double tau;       /* LiftedKKT relaxation; <= 0 means tau = tol */
   double mu0;       /* initial barrier parameter; <= 0 means 0.1 */
   double cg_rtol;   /* HyKKT CG relative residual; <= 0 means 1e-10 */
@@ -279,6 +283,7 @@ typedef struct {
   double mu, kkt_err, alpha, delta_w, obj, eta, theta;
   int n_factor, cg_iters, refine_steps, ls_steps;
   int precision;    /* factorization precision used by this iteration (32 or 64) */
+  double gamma;     /* gamma used by this iteration (forms 1 and 2) */
 } ipm_iter_info;
 
 typedef struct ipm_state_s *ipm_state_t;

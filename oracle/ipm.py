@@ -39,9 +39,9 @@ KAPPA_SIGMA = 1e10
 
 @dataclasses.dataclass
 class Options:
-    kkt: str = "lifted"          # "lifted" | "hykkt"
+    kkt: str = "lifted"          # "lifted" | "hykkt" | "regularized"
     tol: float = 1e-6
-    gamma: float = 1e6           # HyKKT
+    gamma: float = 1e6           # HyKKT gamma; "regularized": delta_c = 1 / gamma; <= 0: automatic
     tau: float | None = None     # LiftedKKT relaxation; None -> tol
     max_iter: int = 3000
     mu0: float = 0.1
@@ -150,6 +150,18 @@ def _push(x, xl, xu):
     return x
 
 
+def auto_gamma(W, sigma_x, G, H, Ds):
+    """gamma = ||K|| / ||G||^2 (Golub & Greif, recommended in Sec. 3.1), infinity norms, with
+    ||K|| bounded by the row sums of |W + Sigma_x| + |H|^T |D_s| |H| (delta_w = 0)."""
+    import scipy.sparse as sps
+    ones = np.ones(W.shape[0])
+    full = abs(W + sps.diags(sigma_x)) @ ones
+    rows = np.asarray(abs(H) @ np.ones(H.shape[1])).ravel()
+    kn = float(np.max(full + abs(H).T @ (np.abs(Ds) * rows)))
+    gn = float(np.max(np.asarray(abs(G) @ np.ones(G.shape[1])).ravel())) if G.shape[0] else 0.0
+    return kn / (gn * gn) if gn > 0 else 1.0
+
+
 def solve(model, opt: Options | None = None, x0=None):
     opt = opt or Options()
     base = model
@@ -236,9 +248,11 @@ def solve(model, opt: Options | None = None, x0=None):
         r3 = g
         r4 = h + s
 
+        gamma = opt.gamma if opt.gamma > 0 else auto_gamma(W, sigma_x, G, H, Ds)
+
         def kmat(dw):
             dh = Ds + dw
-            d = np.concatenate([np.full(me, opt.gamma), dh]) if opt.kkt == "hykkt" else dh
+            d = np.concatenate([np.full(me, gamma), dh]) if opt.kkt != "lifted" else dh
             return K.condensed_matrix(W, sigma_x, J, d, dw)
 
         dw, F, nfac = K.inertia_schedule(kmat, solver, delta_last)
@@ -250,10 +264,20 @@ def solve(model, opt: Options | None = None, x0=None):
         cg_its = 0
         if opt.kkt == "hykkt":
             b = np.concatenate([-r3, bH])
-            dx, dy, dz, cg_its, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, opt.gamma, a, b,
+            dx, dy, dz, cg_its, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, gamma, a, b,
                                                    rtol=opt.cg_rtol)
             eta = K.backward_error(K.aug_matrix(W, sigma_x, J, dh, me, dw),
                                    np.concatenate([dx, dy, dz]), np.concatenate([a, b]))
+        elif opt.kkt == "regularized":
+            # dual regularization delta_c = 1/gamma (Remark in Sec. 3): one condensed solve of
+            # (K + G^T G / delta_c) dx = r1bar + G^T r2bar / delta_c, dy = (G dx - r2bar) / delta_c,
+            # refined on the augmented system with -delta_c I in the equality block
+            b = np.concatenate([-r3, bH])
+            d = np.concatenate([np.full(me, gamma), dh])
+            A = K.aug_matrix(W, sigma_x, J, d, 0, dw)
+            dx, dzall, eh = K.lifted_solve(F, A, J, d, a, b, max_refine=opt.max_refine)
+            dy, dz = dzall[:me], dzall[me:]
+            eta = eh[-1]
         else:
             A = K.aug_matrix(W, sigma_x, J, dh, 0, dw)
             dx, dz, eh = K.lifted_solve(F, A, J, dh, a, bH, max_refine=opt.max_refine)
@@ -325,7 +349,7 @@ def solve(model, opt: Options | None = None, x0=None):
         zu = np.where(hu, np.clip(zu, mu / (KAPPA_SIGMA * dxu), KAPPA_SIGMA * mu / dxu), 0.0)
         v = np.clip(v, mu / (KAPPA_SIGMA * s), KAPPA_SIGMA * mu / s)
         hist.append(dict(k=it, mu=mu, e0=e0, alpha=alpha, delta_w=dw, nfac=nfac, cg=cg_its,
-                         eta=eta, ls=ls, obj=model.objective(x)))
+                         eta=eta, ls=ls, obj=model.objective(x), gamma=gamma))
         if opt.verbose:
             print(f"{it:4d} mu={mu:.1e} E0={e0:.2e} a={alpha:.2e} dw={dw:.1e} cg={cg_its} eta={eta:.1e}")
     g, h = model.cons(x)

@@ -96,7 +96,7 @@ class IpmIterInfo(ctypes.Structure):
                 ("delta_w", ctypes.c_double), ("obj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("theta", ctypes.c_double), ("n_factor", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("ls_steps", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("gamma", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -332,8 +332,8 @@ class IpmState:
     def __init__(self, opf, kkt="lifted", tol=1e-6, gamma=1e6, tau=0.0, mu0=0.1, cg_rtol=1e-10,
                  max_refine=10, cg_maxit=0, precision=64, stream=None):
         self.opf = opf
-        o = IpmOptions(0 if kkt == "lifted" else 1, tol, gamma, tau, mu0, cg_rtol, max_refine,
-                       cg_maxit, precision)
+        o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
+                       cg_rtol, max_refine, cg_maxit, precision)
         h = ctypes.c_void_p()
         _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream), ctypes.byref(h)),
                "ipm_state_create")

@@ -166,6 +166,43 @@ __global__ void k_accept(StepArgs A, double alpha, double az, const double *xt, 
   accept_at(A, alpha, az, xt, st, dy, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// ||K|| bound for the automatic gamma: per column j the row sum of |W + Sigma_x| plus
+// sum over H rows r of |Ds_r| |J_rj| sum_t |J_rt| (delta_w = 0), max-reduced into R[k_out];
+// and max over G rows of sum |G_rj| into R[g_out]
+__global__ void k_gamma_norms(Dims D, const int *W_rowptr, const int *W_colind,
+                              const int *W_rowidx, const int *WT_ptr, const int *WT_ent,
+                              const double *Wv, const double *sigma, const int *JT_ptr,
+                              const int *JT_ent, const int *J_rowidx, const int *J_rowptr,
+                              const double *Jv, const double *Ds, double *R, int k_out,
+                              int g_out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0, gr = 0.0;
+  if (j < D.n) {
+    double diag = sigma[j];
+    for (int q = W_rowptr[j]; q < W_rowptr[j + 1]; ++q) {
+      if (W_colind[q] == j) diag += Wv[q];
+      else acc += fabs(Wv[q]);
+    }
+    for (int u = WT_ptr[j]; u < WT_ptr[j + 1]; ++u) {
+      const int e = WT_ent[u];
+      if (W_rowidx[e] != j) acc += fabs(Wv[e]);
+    }
+    acc += fabs(diag);
+    for (int u = JT_ptr[j]; u < JT_ptr[j + 1]; ++u) {
+      const int q = JT_ent[u];
+      const int r = J_rowidx[q];
+      if (r < D.me0) continue;
+      double rs = 0.0;
+      for (int t = J_rowptr[r]; t < J_rowptr[r + 1]; ++t) rs += fabs(Jv[t]);
+      acc += fabs(Ds[r - D.me0]) * fabs(Jv[q]) * rs;
+    }
+  }
+  if (j < D.me0)
+    for (int t = J_rowptr[j]; t < J_rowptr[j + 1]; ++t) gr += fabs(Jv[t]);
+  red_max(R, k_out, acc);
+  red_max(R, g_out, gr);
+}
+
 __global__ void k_init_duals(Dims D, It P, double *s) {
   init_duals_at(D, P, s, blockIdx.x * blockDim.x + threadIdx.x);
 }
@@ -285,7 +322,7 @@ static int merit(ipm_state_t S, const double *x, const double *sv, const double 
 
 extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStream_t stream,
                                 ipm_state_t *out) {
-  if (!opf || !opt || !out || (opt->kkt != 0 && opt->kkt != 1) || !(opt->tol > 0)) {
+  if (!opf || !opt || !out || opt->kkt < 0 || opt->kkt > 2 || !(opt->tol > 0)) {
     set_error_msg("ipm_state_create: bad argument");
     return IPM_ERR_BAD_ARG;
   }
@@ -303,7 +340,7 @@ extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStrea
   D.n = M.n;
   D.me0 = M.me;
   D.mi0 = M.mi;
-  D.lifted = opt->kkt == 0;
+  D.lifted = opt->kkt == 0;  // HyKKT (1) and the dual-regularized form (2) keep the equalities
   D.me = D.lifted ? 0 : M.me;
   D.mi = D.lifted ? 2 * M.me + M.mi : M.mi;
   S->nb = M.nb;
@@ -447,6 +484,20 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   // ---- inertia correction: delta_w = 0, then delta_last/3 (x8) or 1e-4 (x100).  A failed
   // factorization, or (FP32 factor) a solve whose FP64 refinement meets negative curvature or
   // does not converge, counts as wrong inertia.
+  // gamma: the option, or (<= 0) ||K|| / ||G||^2 of this iteration (Golub & Greif, Sec. 3.1)
+  double gamma = S->opt.gamma;
+  if (!D.lifted && !(gamma > 0)) {
+    CKR(reduce_reset(S, {R_PD, R_QD}, 0.0));
+    k_gamma_norms<<<grid1(n), 256, 0, s>>>(D, M.W_rowptr, M.W_colind, S->sym->W_rowidx,
+                                           S->sym->WT_ptr, S->sym->WT_ent, S->Wv, S->sigma,
+                                           S->sym->JT_ptr, S->sym->JT_ent, S->sym->J_rowidx,
+                                           M.J_rowptr, S->Jv, S->Ds, S->R, R_PD, R_QD);
+    CKL();
+    CKR(read_R(S));
+    const double gn = S->hR[R_QD];
+    gamma = gn > 0 ? S->hR[R_PD] / (gn * gn) : 1.0;
+  }
+  info->gamma = gamma;
   double dw = 0.0;
   int nfac = 0;
   bool ok = false;
@@ -473,7 +524,7 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     if (attempt > 0) next *= grow;
     if (dw >= 1e40) break;
     ipm_num_t num = S->num32 ? S->num32 : S->num;
-    k_aug_rhs<<<grid1(std::max(D.me0, D.mi0)), 256, 0, s>>>(D, dw, S->opt.gamma, S->r2, S->r4,
+    k_aug_rhs<<<grid1(std::max(D.me0, D.mi0)), 256, 0, s>>>(D, dw, gamma, S->r2, S->r4,
                                                             S->Ds, S->P.geq, S->dcond, S->baug);
     CKL();
     CKR(ipm_condense(S->sym, num, S->Wv, S->sigma, S->Jv, S->dcond, dw, s));
@@ -486,13 +537,15 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     if (hinfo != -1) continue;
     // ---- solve
     int st;
-    if (D.lifted) {
+    if (S->opt.kkt != 1) {
+      // LiftedKKT, or the dual-regularized form (delta_c = 1/gamma, Remark in Sec. 3): one
+      // condensed solve refined on the augmented system whose equality block is -delta_c I
       st = ipm_aug_solve(S->sym, num, S->Wv, S->sigma, S->Jv, S->dcond, dw, S->a, S->baug,
                          S->dx, S->dzc, S->opt.max_refine, 1e-10, S->eta, S->steps, s);
     } else {
       int its = 0;
       double rel = 0;
-      st = hykkt_cg(S->sym, num, D.me0, S->Jv, S->dcond, S->opt.gamma, S->a, S->baug,
+      st = hykkt_cg(S->sym, num, D.me0, S->Jv, S->dcond, gamma, S->a, S->baug,
                     S->opt.cg_rtol, S->opt.cg_maxit > 0 ? S->opt.cg_maxit : std::max(D.me0, 1),
                     S->dx, S->dy, S->dzH, &its, &rel, s);
       info->cg_iters = its;
@@ -517,15 +570,22 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   info->delta_w = dw;
   info->n_factor = nfac;
   SA.dw = dw;
-  if (D.lifted) {
+  const double *dy_step = S->dy;
+  if (S->opt.kkt == 2) {  // dy = dz over the G rows, dz over the H rows
+    SA.dzH = S->dzc + D.me0;
+    dy_step = S->dzc;
+  }
+  if (S->opt.kkt != 1) {
     double eta = 0;
     int steps = 0;
     CK(cudaMemcpy(&eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&steps, S->steps, sizeof(int), cudaMemcpyDeviceToHost));
     info->eta = eta;
     info->refine_steps = steps;
-    k_jv<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, M.J_colind, S->Jv, S->dx, S->jdx);
-    CKL();
+    if (D.lifted) {
+      k_jv<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, M.J_colind, S->Jv, S->dx, S->jdx);
+      CKL();
+    }
   }
   k_recover<<<grid1(nmax), 256, 0, s>>>(SA);
   CKL();
@@ -587,7 +647,7 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     return IPM_OK;
   }
   if (!ftype) S->filter.push_back({(1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta});
-  k_accept<<<grid1(nmax), 256, 0, s>>>(SA, alpha, az, S->xt, S->st, S->dy);
+  k_accept<<<grid1(nmax), 256, 0, s>>>(SA, alpha, az, S->xt, S->st, dy_step);
   CKL();
   CK(cudaStreamSynchronize(s));
   S->k++;

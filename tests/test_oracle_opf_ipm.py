@@ -131,3 +131,31 @@ def test_lifted_optimum_within_tau_of_hykkt():
     rl = ipm.solve(OPFModel(g), ipm.Options(kkt="lifted"))
     tau = 1e-6
     assert abs(rl.obj - rh.obj) <= 1e3 * tau * max(1.0, abs(rh.obj))
+
+
+def test_auto_gamma_is_the_norm_ratio_when_the_bound_is_exact():
+    # H with one entry per row, W + Sigma diagonal and non-negative, D >= 0: the row-sum bound of
+    # ||K||_inf is the exact infinity norm of K = W + Sigma + H^T D H
+    import scipy.sparse as sp
+    from oracle.ipm import auto_gamma
+    rng = np.random.default_rng(7)
+    n = 6
+    W = sp.diags(rng.uniform(0.5, 2.0, n)).tocsr()
+    sig = rng.uniform(0, 1, n)
+    H = sp.csr_matrix((rng.normal(size=4), ([0, 1, 2, 3], [0, 2, 2, 5])), shape=(4, n))
+    Ds = rng.uniform(0.1, 3.0, 4)
+    G = sp.csr_matrix(rng.normal(size=(2, n)))
+    Kd = W.toarray() + np.diag(sig) + H.toarray().T @ np.diag(Ds) @ H.toarray()
+    expect = np.linalg.norm(Kd, np.inf) / np.linalg.norm(G.toarray(), np.inf) ** 2
+    assert np.isclose(auto_gamma(W, sig, G, H, Ds), expect, rtol=1e-14)
+
+
+def test_dual_regularized_form_converges_near_hykkt():
+    from synth import config_grid
+    g = config_grid("ring30")
+    hy = ipm.solve(OPFModel(g), ipm.Options(kkt="hykkt", gamma=1e6))
+    for gam in (1e6, 0.0):
+        r = ipm.solve(OPFModel(g), ipm.Options(kkt="regularized", gamma=gam))
+        assert r.status == "converged"
+        # delta_c = 1/gamma perturbs the dual update only: same optimum to O(delta_c)
+        assert abs(r.obj - hy.obj) <= 1e-6 * abs(hy.obj)
