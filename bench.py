@@ -618,6 +618,7 @@ def run_gpu(args, rank, world, local_rank):
         line["kkt10k"] = kkt_measure(args)
     if not args.no_ipm:
         line["ipm"] = ipm_measure(include_oracle=not args.no_cpu_baseline)
+        line["sweeps"] = sweep_measure()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = batch_cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -692,6 +693,39 @@ def warm_measure(steps=6000, n_train=20000, n_test=1024):
                          "params": int(model.net.nparams), "dtype": "bf16 weights, fp32 accumulate"}}
 
 
+def sweep_measure():
+    """gamma and tolerance sweeps on the 1,000-bus grid (the paper's experiments on gamma and on
+    epsilon_tol): single-problem GPU IPM status, iterations, CG iterations, time, objective and
+    the largest equality violation of the result."""
+    import torch
+    import paper_2405_14236_gb300 as cp
+    from synth import config_grid
+    from oracle.opf import OPFModel
+    g = config_grid("planar1k")
+    opf = cp.Opf(g)
+    model = OPFModel(g)
+
+    def run(**kw):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = cp.ipm_solve_opf(opf, max_iter=MAX_ITER, **kw)
+        el = time.perf_counter() - t0
+        gx, _ = model.cons(r["x"])
+        return {"status": int(r["status"]), "iters": int(r["iters"]), "s": el,
+                "cg_iters": int(sum(h["cg_iters"] for h in r["history"])),
+                "gamma_last": float(r["history"][-1]["gamma"]), "obj": float(r["obj"]),
+                "max_abs_g": float(np.abs(gx).max())}
+    out = {"grid": "planar1k (1,000 buses)", "hykkt_gamma": {}, "regularized_gamma": {},
+           "lifted_tol": {}}
+    for gam in (1e4, 1e5, 1e6, 1e7, 1e8, 0.0):
+        out["hykkt_gamma"]["auto" if gam == 0 else f"{gam:g}"] = run(kkt="hykkt", gamma=gam)
+    for gam in (1e4, 1e6, 1e8, 0.0):
+        out["regularized_gamma"]["auto" if gam == 0 else f"{gam:g}"] = run(kkt="regularized", gamma=gam)
+    for tol in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+        out["lifted_tol"][f"{tol:g}"] = run(kkt="lifted", tol=tol)
+    return out
+
+
 def ipm_measure(include_oracle=True):
     """Full IPM solves to the 1e-6 scaled KKT tolerance on the GPU (ipm_step loop), with the
     oracle IPM timed on the same problem (single thread) where it takes seconds."""
@@ -751,6 +785,8 @@ def main():
     ap.add_argument("--no-kkt", action="store_true", help="skip the 10k KKT-solve kernel line")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-problem GPU IPM")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--kkt-only", action="store_true",
+                    help="print only the 10k-bus KKT-solve leg (profiling)")
     ap.add_argument("--batch-scen", type=int, default=256,
                     help="load scenarios of the 1,000-bus grid in the batch (profiling: fewer)")
     ap.add_argument("--batch-mixed", type=int, default=64,
@@ -763,6 +799,9 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.kkt_only:
+        print(json.dumps(kkt_measure(args)), flush=True)
         return
     if world > 1:
         import torch
