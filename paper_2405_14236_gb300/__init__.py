@@ -16,6 +16,7 @@ from .build import LIB
 _lib = None
 
 IPM_OK, IPM_ERR_NOT_PD, IPM_ERR_CG_MAXIT, IPM_ERR_NONFINITE = 0, 1, 2, 3
+IPM_ERR_BAD_ARG, IPM_ERR_OOM, IPM_ERR_CUDA = -1, -2, -3
 IPM_ERR_TIMEOUT, IPM_ERR_RESTORATION, IPM_ERR_INERTIA, IPM_ERR_MAXITER = 4, 5, 6, 7
 
 P = ctypes.c_void_p

@@ -79,3 +79,36 @@ def test_batch_iteration_limit_reported():
     r = B.results()
     assert np.all(r["status"] == cp.IPM_ERR_MAXITER)
     assert np.all(r["iters"] == 3)
+
+
+def test_single_instance_and_repeated_grid():
+    g = config_grid("ring30")
+    ref = oipm.solve(OPFModel(g), oipm.Options(kkt="lifted"))
+    B1 = cp.Batch([cp.Opf(g)])
+    B1.run(max_iter=200)
+    r1 = B1.results()
+    assert r1["status"][0] == 1 and abs(r1["obj"][0] - ref.obj) <= 1e-6 * abs(ref.obj)
+    # the same grid twice: one pattern, two identical solves
+    B2 = cp.Batch([cp.Opf(g), cp.Opf(g)])
+    assert B2.info()["patterns"] == 1
+    B2.run(max_iter=200)
+    r2 = B2.results()
+    assert (r2["status"] == 1).all() and np.allclose(r2["obj"], ref.obj, rtol=1e-6)
+
+
+def test_batch_argument_errors():
+    import ctypes
+    g = config_grid("ring30")
+    o = cp.Opf(g)
+    arr = (ctypes.c_void_p * 1)(o.h.value)
+    h = ctypes.c_void_p()
+    for kkt, prec in ((1, 64), (0, 32)):  # HyKKT and FP32 are not batched
+        opt = cp.IpmOptions(kkt, 1e-6, 1e6, 0.0, 0.1, 1e-10, 10, 0, prec)
+        rc = cp.lib().ipm_batch_create(1, arr, ctypes.byref(opt), None, ctypes.byref(h))
+        assert rc == cp.IPM_ERR_BAD_ARG
+    opt = cp.IpmOptions(0, 1e-6, 1e6, 0.0, 0.1, 1e-10, 10, 0, 64)
+    assert cp.lib().ipm_batch_create(0, arr, ctypes.byref(opt), None, ctypes.byref(h)) == cp.IPM_ERR_BAD_ARG
+    # state rows need equal sizes
+    B = cp.Batch([o, cp.Opf(config_grid("planar1k"))])
+    w = ctypes.c_int()
+    assert cp.lib().ipm_batch_state_rows(B.h, None, 0, ctypes.byref(w)) == cp.IPM_ERR_BAD_ARG

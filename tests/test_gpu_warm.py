@@ -39,3 +39,23 @@ def test_warm_start_saves_iterations():
     rel = np.abs(hot["obj"][both] - cold["obj"][both]) / np.abs(cold["obj"][both])
     assert rel.max() <= 1e-6
     assert hot["iters"][both].mean() < cold["iters"][both].mean(), (hot["iters"], cold["iters"])
+
+
+def test_non_finite_prediction_keeps_the_cold_start():
+    base = config_grid("planar1k")
+    grids = [scale_loads(base, 30100 + k) for k in range(3)]
+    B = cp.Batch([cp.Opf(g) for g in grids])
+    B.run(max_iter=300)
+    cold = B.results()
+    rows = B.state_rows()  # the solutions themselves as "predictions" (unnormalized)
+    rows[1, 5] = float("nan")
+    B.reset()
+    used = B.warm_start(rows)
+    assert used.tolist() == [1, 0, 1]
+    B.run(max_iter=300)
+    hot = B.results()
+    assert (hot["status"] == 1).all()
+    # instance 1 repeats its cold solve; the others start at their own solution
+    assert hot["iters"][1] == cold["iters"][1] or abs(hot["iters"][1] - cold["iters"][1]) <= 3
+    assert hot["iters"][0] < cold["iters"][0] and hot["iters"][2] < cold["iters"][2]
+    assert np.allclose(hot["obj"], cold["obj"], rtol=1e-6)
