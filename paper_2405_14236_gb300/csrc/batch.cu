@@ -582,26 +582,27 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
 }
 
 // condensation of every panel, then the factorization, of each instance in the FACT phase: one
-// thread-block cluster of B_CL blocks per instance.  Warps of the whole cluster share the
-// narrow supernodes of a level; each block collects the wide ones its warps met and factors them
-// with all its threads; a cluster barrier (release / acquire) separates the levels.
-static constexpr int B_CL = 1;
+// block, or one thread-block cluster (big instances, launched with a cluster size), per
+// instance.  Warps of the whole cluster share the narrow supernodes of a level; each block
+// collects the wide ones its warps met and factors them with all its threads; a cluster barrier
+// (release / acquire) separates the levels.
+static constexpr int B_CL_BIG = 4;       // cluster size of the big instances
 static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
 
-__global__ void __cluster_dims__(B_CL, 1, 1) __launch_bounds__(B_NT)
-    k_b_fact_inst(const BI *bi, const BCtl *ctl) {
+__global__ void __launch_bounds__(B_NT, 3)
+    k_b_fact_inst(const BI *bi, const BCtl *ctl, const int *order) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double *sm = reinterpret_cast<double *>(sm_raw);
   __shared__ double s_inv[CIPM_SN_MAXW];
   __shared__ int s_wide[B_WIDE_CAP], s_nwide;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  const int crank = (int)cluster.block_rank();
-  const int b = blockIdx.x / B_CL;
+  const int crank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
+  const int b = order[blockIdx.x / ncl];
   if (ctl[b].ph != PH_FACT) return;  // the same for every block of the cluster
   const BI &I = bi[b];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int gw = crank * nw + warp, gnw = B_CL * nw;
+  const int gw = crank * nw + warp, gnw = ncl * nw;
   const double dw = ctl[b].dw;
   if (crank == 0 && threadIdx.x == 0) *I.info = INT_MAX;
   for (int s = gw; s < I.ns; s += gnw)
@@ -612,11 +613,11 @@ __global__ void __cluster_dims__(B_CL, 1, 1) __launch_bounds__(B_NT)
   for (int L = 0; L < I.nlevels; ++L) {
     if (threadIdx.x == 0) s_nwide = 0;
     const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
-    for (int q = q0 + crank * blockDim.x + threadIdx.x; q < q1; q += B_CL * blockDim.x) {
+    for (int q = q0 + crank * blockDim.x + threadIdx.x; q < q1; q += ncl * blockDim.x) {
       const int s = I.level_sn[q];
       if (I.sptr[s + 1] - I.sptr[s] <= B_WT) thread_diag_sn(I, s);
     }
-    __syncthreads();
+    cluster.sync();  // warps of any block of the cluster read these pivots
     for (int q = q0 + gw; q < q1; q += gnw) {
       const int s = I.level_sn[q];
       if (I.sptr[s + 1] - I.sptr[s] <= B_WS) {
@@ -684,18 +685,18 @@ __device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
 
 // phase SOLVE: dx = K^{-1} t; phase REFINE: cx = K^{-1} t (t from k_b_jt_rhs), one cluster per
 // instance: gather by the ordering, forward levels, backward levels, scatter
-__global__ void __cluster_dims__(B_CL, 1, 1) __launch_bounds__(B_NT)
-    k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase) {
+__global__ void __launch_bounds__(B_NT)
+    k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase, const int *order) {
   __shared__ double s_y[(B_NT / 32) * CIPM_SN_MAXW];
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  const int crank = (int)cluster.block_rank();
-  const int b = blockIdx.x / B_CL;
+  const int crank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
+  const int b = order[blockIdx.x / ncl];
   if (ctl[b].ph != phase) return;  // the same for every block of the cluster
   const BI &I = bi[b];
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int gw = crank * nw + warp, gnw = B_CL * nw;
-  const int gt = crank * blockDim.x + threadIdx.x, gnt = B_CL * blockDim.x;
+  const int gw = crank * nw + warp, gnw = ncl * nw;
+  const int gt = crank * blockDim.x + threadIdx.x, gnt = ncl * blockDim.x;
   double *ys = s_y + warp * CIPM_SN_MAXW;
   for (int k = gt; k < I.D.n; k += gnt) I.y[k] = I.t[I.perm[k]];
   cluster.sync();
@@ -1118,7 +1119,11 @@ struct ipm_batch_s {
   BI *d_bi = nullptr;
   BCtl *d_ctl = nullptr;
   std::vector<void *> bufs;  // per-pattern level offsets
-  int *d_tickets = nullptr;                      // 16 ticket counters, then the active count
+  int *d_tickets = nullptr;                      // scratch counters (active count at [8])
+  int *d_order = nullptr;  // small instances by decreasing supernode count, then the big ones
+  int n_small = 0, n_big = 0;
+  cudaStream_t side = nullptr;  // second branch of the sweep: the big instances
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *h_active = nullptr;                       // pinned
   int gx = 1, gx_gen = 1, max_ns = 1, fmax_entries = 0;
   size_t fact_smem = 0;
@@ -1202,13 +1207,45 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     if (B->timing) CK(cudaEventRecordWithFlags(B->ev[k], s, cudaEventRecordExternal));
     return IPM_OK;
   };
+  // one launch for the one-block instances on s and, in a concurrent branch, one cluster launch
+  // for the big ones (order: small instances first, then big)
+  auto split = [&](auto kernel, size_t smem, auto... args) -> int {
+    if (B->n_big) {
+      CK(cudaEventRecord(B->ev_fork, s));
+      CK(cudaStreamWaitEvent(B->side, B->ev_fork, 0));
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = B_CL_BIG;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(B->n_big * B_CL_BIG);
+      cfg.blockDim = dim3(B_NT);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = B->side;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      CK(cudaLaunchKernelEx(&cfg, kernel, bi, ctl, args..., (const int *)(B->d_order + B->n_small)));
+      L(1);
+    }
+    if (B->n_small) {
+      kernel<<<B->n_small, B_NT, smem, s>>>(bi, ctl, args..., (const int *)B->d_order);
+      L(1);
+    }
+    CKL();
+    if (B->n_big) {
+      CK(cudaEventRecord(B->ev_join, B->side));
+      CK(cudaStreamWaitEvent(s, B->ev_join, 0));
+    }
+    return IPM_OK;
+  };
   auto solve = [&](int phase) -> int {
     k_b_jt_rhs<<<g2, blk, 0, s>>>(bi, ctl, phase);
     if (phase == PH_SOLVE) CKR(rec(2));
-    k_b_solve_inst<<<C * B_CL, B_NT, 0, s>>>(bi, ctl, phase);
+    CKR(split(k_b_solve_inst, (size_t)0, phase));
     if (phase == PH_SOLVE) CKR(rec(3));
     k_b_recover_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
-    L(3);
+    L(2);
     return IPM_OK;
   };
   // evaluate at x, optimality error, convergence, barrier update
@@ -1236,10 +1273,10 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_aug_rhs<<<g2, blk, 0, s>>>(bi, ctl, B->opt.gamma);
     k_b_scale_jv<<<g2, blk, 0, s>>>(bi, ctl);
     CKR(rec(r == 0 ? 0 : 4));
-    k_b_fact_inst<<<C * B_CL, B_NT, B->fact_smem, s>>>(bi, ctl);
+    CKR(split(k_b_fact_inst, B->fact_smem));
     CKR(rec(r == 0 ? 1 : 5));
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
-    L(4);
+    L(3);
   }
   // condensed solve, then Richardson refinement on the augmented system
   CKR(solve(PH_SOLVE));
@@ -1552,10 +1589,32 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
       rc = IPM_ERR_CUDA;
   };
   up(&B->d_bi, hbi);
+  {
+    // instances whose supernode count exceeds 1.5x the median are "big": their factorization and
+    // solves run on a cluster of B_CL_BIG blocks in a second branch of the sweep, concurrently
+    // with the one-block instances, so that they do not set the length of every sweep
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
+      return B->syms[B->pat[a]]->nsuper > B->syms[B->pat[b2]]->nsuper;
+    });
+    const int med = B->syms[B->pat[order[count / 2]]]->nsuper;
+    int nbig = 0;
+    while (nbig < count && B->syms[B->pat[order[nbig]]]->nsuper * 2 > 3 * med) ++nbig;
+    std::vector<int> ord2(order.begin() + nbig, order.end());  // small ones, biggest first
+    ord2.insert(ord2.end(), order.begin(), order.begin() + nbig);
+    B->n_big = nbig;
+    B->n_small = count - nbig;
+    up(&B->d_order, ord2);
+  }
   if (rc == IPM_OK && cudaMalloc(&B->d_ctl, sizeof(BCtl) * count) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMalloc(&B->d_tickets, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMemset(B->d_tickets, 0, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_CUDA;
   if (rc == IPM_OK && cudaMallocHost((void **)&B->h_active, sizeof(int)) != cudaSuccess) rc = IPM_ERR_OOM;
+  if (rc == IPM_OK && (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = IPM_ERR_CUDA;
   if (rc != IPM_OK) return fail(rc);
   int max_w = 1;
   for (ipm_sym_t S : B->syms) max_w = std::max(max_w, S->max_w);
@@ -1675,7 +1734,7 @@ extern "C" void ipm_batch_destroy(ipm_batch_t B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   for (ipm_sym_t S : B->syms) ipm_symbolic_destroy(S);
-  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_tickets};
+  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_tickets, B->d_order};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (B->h_active) cudaFreeHost(B->h_active);
@@ -1683,6 +1742,9 @@ extern "C" void ipm_batch_destroy(ipm_batch_t B) {
   for (cudaEvent_t e : B->ev)
     if (e) cudaEventDestroy(e);
   if (B->x_stage) cudaFree(B->x_stage);
+  if (B->side) cudaStreamDestroy(B->side);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->ev_join) cudaEventDestroy(B->ev_join);
   delete B;
 }
 
