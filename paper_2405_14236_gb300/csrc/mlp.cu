@@ -7,6 +7,7 @@
 // FP32 master weights are updated by Adam and rounded to the BF16 copies the products read.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -19,84 +20,156 @@ using bf16 = __nv_bfloat16;
 
 // C[M x N] (FP32, row-major, ldc) = opA[M x K] opB[K x N] with BF16 operands.
 // TA: A is stored K x M (row-major, lda), else M x K.  TB: B is stored N x K, else K x N.
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const bf16 *A, int lda,
-                                                   const bf16 *B, int ldb, float *C, int ldc) {
-  constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-  __shared__ __align__(16) bf16 As[BM][BK + PAD];
-  __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, 32 x 32 each
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
+// 128 x 128 x 32 block tiles, 8 warps of 64 x 32, mma.sync m16n8k16 with ldmatrix fragment
+// loads from shared memory (A as [m][k], B as [n][k]); the next k-tile is fetched into registers
+// (16-byte loads where the row is aligned and in bounds, element loads at the edges) while the
+// current one is multiplied, then stored to the other shared buffer.
+constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8, GLD = GBK + GPAD;
+
+// 8 consecutive bf16 of a row (contiguous in memory) starting at column c0, zero beyond len
+__device__ __forceinline__ uint4 load8(const bf16 *row, int c0, int len, bool aligned) {
+  if (aligned && c0 + 8 <= len) return *reinterpret_cast<const uint4 *>(row + c0);
+  union {
+    uint4 v;
+    bf16 h[8];
+  } u;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 8; ++i) u.h[i] = c0 + i < len ? row[c0 + i] : __float2bfloat16(0.f);
+  return u.v;
+}
+
+// one operand tile (128 rows of the [row][k] smem layout x 32 k) as two 16-byte chunks per
+// thread.  Contiguous-k storage: chunk = (row, 8 k).  Transposed storage (contiguous along
+// rows): chunk = (8 rows, k), scattered to the smem layout at store time.
+template <bool KCONTIG>
+__device__ __forceinline__ void tile_load(const bf16 *X, int ldx, int rows, int K, int r0, int k0,
+                                          bool aligned, uint4 (&buf)[2]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int c = threadIdx.x + q * 256;
+    if (KCONTIG) {
+      const int r = c >> 2, kk = (c & 3) * 8;
+      buf[q] = r0 + r < rows ? load8(X + (size_t)(r0 + r) * ldx, k0 + kk, K, aligned)
+                             : make_uint4(0, 0, 0, 0);
+    } else {
+      const int kk = c >> 4, r = (c & 15) * 8;
+      buf[q] = k0 + kk < K ? load8(X + (size_t)(k0 + kk) * ldx, r0 + r, rows, aligned)
+                           : make_uint4(0, 0, 0, 0);
+    }
+  }
+}
+
+template <bool KCONTIG>
+__device__ __forceinline__ void tile_store(bf16 (*S)[GLD], const uint4 (&buf)[2]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int c = threadIdx.x + q * 256;
+    if (KCONTIG) {
+      const int r = c >> 2, kk = (c & 3) * 8;
+      *reinterpret_cast<uint4 *>(&S[r][kk]) = buf[q];
+    } else {
+      const int kk = c >> 4, r = (c & 15) * 8;
+      union {
+        uint4 v;
+        bf16 h[8];
+      } u;
+      u.v = buf[q];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) S[r + i][kk] = u.h[i];
+    }
+  }
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16 *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// split K: block z multiplies k-tiles [z kchunk, (z + 1) kchunk) and adds its partial sums into
+// C (zeroed by the caller) when gridDim.z > 1
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, const bf16 *A, int lda,
+                                                   const bf16 *B, int ldb, float *C, int ldc,
+                                                   int kchunk) {
+  __shared__ __align__(16) bf16 As[2][GBM][GLD];
+  __shared__ __align__(16) bf16 Bs[2][GBN][GLD];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps of 64 x 32
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  // A rows are m (contiguous k unless TA), B rows are n (contiguous k when TB)
+  const bool a_al = (lda % 8) == 0 && ((uintptr_t)A % 16) == 0;
+  const bool b_al = (ldb % 8) == 0 && ((uintptr_t)B % 16) == 0;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  const bf16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 128) {
-      int m, k;
-      if (TA) { m = e % BM; k = e / BM; } else { k = e % BK; m = e / BK; }
-      const int gm = m0 + m, gk = k0 + k;
-      bf16 v = zero;
-      if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-      As[m][k] = v;
+  uint4 ra[2], rb[2];
+  const int t0 = blockIdx.z * kchunk;
+  const int nk = min((K + GBK - 1) / GBK, t0 + kchunk);
+  if (t0 >= nk) return;
+  tile_load<!TA>(A, lda, M, K, m0, t0 * GBK, a_al, ra);
+  tile_load<TB>(B, ldb, N, K, n0, t0 * GBK, b_al, rb);
+  tile_store<!TA>(As[0], ra);
+  tile_store<TB>(Bs[0], rb);
+  __syncthreads();
+  for (int t = t0; t < nk; ++t) {
+    const int cur = (t - t0) & 1;
+    if (t + 1 < nk) {
+      tile_load<!TA>(A, lda, M, K, m0, (t + 1) * GBK, a_al, ra);
+      tile_load<TB>(B, ldb, N, K, n0, (t + 1) * GBK, b_al, rb);
     }
-    for (int e = tid; e < BN * BK; e += 128) {
-      int n, k;
-      if (TB) { k = e % BK; n = e / BK; } else { n = e % BN; k = e / BN; }
-      const int gn = n0 + n, gk = k0 + k;
-      bf16 v = zero;
-      if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-      Bs[n][k] = v;
-    }
-    __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t a[2][4], b[4][2];
+    for (int kk = 0; kk < GBK; kk += 16) {
+      uint32_t af[4][4], bfr[2][4];
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm * 32 + i * 16 + g;
-        a[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + t * 2]);
-        a[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + t * 2]);
-        a[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + t * 2 + 8]);
-        a[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + t * 2 + 8]);
-      }
+      for (int i = 0; i < 4; ++i)
+        ldsm_x4(af[i], &As[cur][wm * 64 + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn * 32 + j * 8 + g;
-        b[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + t * 2]);
-        b[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + t * 2 + 8]);
-      }
+      for (int j = 0; j < 2; ++j)
+        ldsm_x4(bfr[j], &Bs[cur][wn * 32 + j * 16 + (lane & 7) + ((lane >> 4) << 3)]
+                            [kk + ((lane >> 3) & 1) * 8]);
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t b0 = bfr[j >> 1][(j & 1) * 2], b1 = bfr[j >> 1][(j & 1) * 2 + 1];
           asm volatile(
               "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
               "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
               : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]),
-                "r"(b[j][1]));
+              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(b0), "r"(b1));
+        }
+    }
+    if (t + 1 < nk) {
+      tile_store<!TA>(As[cur ^ 1], ra);
+      tile_store<TB>(Bs[cur ^ 1], rb);
     }
     __syncthreads();
   }
+  const int g = lane >> 2, q4 = lane & 3;
+  const bool split = gridDim.z > 1;
+  auto put = [&](int r, int c, float v) {
+    float *p = C + (size_t)r * ldc + c;
+    if (split) atomicAdd(p, v);
+    else *p = v;
+  };
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int r = m0 + wm * 32 + i * 16 + g, c = n0 + wn * 32 + j * 8 + t * 2;
+      const int r = m0 + wm * 64 + i * 16 + g, c = n0 + wn * 32 + j * 8 + q4 * 2;
       if (r < M) {
-        if (c < N) C[(size_t)r * ldc + c] = acc[i][j][0];
-        if (c + 1 < N) C[(size_t)r * ldc + c + 1] = acc[i][j][1];
+        if (c < N) put(r, c, acc[i][j][0]);
+        if (c + 1 < N) put(r, c + 1, acc[i][j][1]);
       }
       if (r + 8 < M) {
-        if (c < N) C[(size_t)(r + 8) * ldc + c] = acc[i][j][2];
-        if (c + 1 < N) C[(size_t)(r + 8) * ldc + c + 1] = acc[i][j][3];
+        if (c < N) put(r + 8, c, acc[i][j][2]);
+        if (c + 1 < N) put(r + 8, c + 1, acc[i][j][3]);
       }
     }
 }
@@ -315,8 +388,15 @@ extern "C" int mlp_get_grads(mlp_t P, float *host) {
 template <bool TA, bool TB>
 static int gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, float *C,
                 int ldc, cudaStream_t s) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+  // too few output tiles for 152 SMs and a long K: split K over blocks (partial sums added)
+  const int nk = (K + GBK - 1) / GBK, tiles = grid.x * grid.y;
+  int split = 1;
+  if (tiles < 2 * 152 && nk >= 8) split = std::min((2 * 152 + tiles - 1) / tiles, nk / 4);
+  const int kchunk = (nk + split - 1) / split;
+  grid.z = (nk + kchunk - 1) / kchunk;
+  if (grid.z > 1) CK(cudaMemsetAsync(C, 0, sizeof(float) * ((size_t)(M - 1) * ldc + N), s));
+  k_gemm_bf16<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, kchunk);
   count_launches(1);
   CKL();
   return IPM_OK;
