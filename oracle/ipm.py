@@ -260,33 +260,40 @@ def solve(model, opt: Options | None = None, x0=None):
             delta_last = dw
         dh = Ds + dw
         a = -r1
-        bH = -r4 + r2 / dh
-        cg_its = 0
-        if opt.kkt == "hykkt":
-            b = np.concatenate([-r3, bH])
-            dx, dy, dz, cg_its, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, gamma, a, b,
-                                                   rtol=opt.cg_rtol)
-            eta = K.backward_error(K.aug_matrix(W, sigma_x, J, dh, me, dw),
-                                   np.concatenate([dx, dy, dz]), np.concatenate([a, b]))
-        elif opt.kkt == "regularized":
-            # dual regularization delta_c = 1/gamma (Remark in Sec. 3): one condensed solve of
-            # (K + G^T G / delta_c) dx = r1bar + G^T r2bar / delta_c, dy = (G dx - r2bar) / delta_c,
-            # refined on the augmented system with -delta_c I in the equality block
-            b = np.concatenate([-r3, bH])
-            d = np.concatenate([np.full(me, gamma), dh])
-            A = K.aug_matrix(W, sigma_x, J, d, 0, dw)
-            dx, dzall, eh = K.lifted_solve(F, A, J, d, a, b, max_refine=opt.max_refine)
-            dy, dz = dzall[:me], dzall[me:]
-            eta = eh[-1]
-        else:
-            A = K.aug_matrix(W, sigma_x, J, dh, 0, dw)
-            dx, dz, eh = K.lifted_solve(F, A, J, dh, a, bH, max_refine=opt.max_refine)
-            dy = np.zeros(0)
-            eta = eh[-1]
-        ds = -(r2 + dz) / dh
-        dv = (mu - v * ds) / s - v
-        dzl = np.where(hl, mu / dxl - zl - zl / dxl * dx, 0.0)
-        dzu = np.where(hu, mu / dxu - zu + zu / dxu * dx, 0.0)
+
+        def direction(r3_, r4_):
+            """Newton direction for the constraint residuals (r3_, r4_) with the factor of this
+            iteration."""
+            bH = -r4_ + r2 / dh
+            cg_its_ = 0
+            if opt.kkt == "hykkt":
+                b = np.concatenate([-r3_, bH])
+                dx_, dy_, dz_, cg_its_, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, gamma, a, b,
+                                                          rtol=opt.cg_rtol)
+                eta_ = K.backward_error(K.aug_matrix(W, sigma_x, J, dh, me, dw),
+                                        np.concatenate([dx_, dy_, dz_]), np.concatenate([a, b]))
+            elif opt.kkt == "regularized":
+                # dual regularization delta_c = 1/gamma (Remark in Sec. 3): one condensed solve
+                # of (K + G^T G / delta_c) dx = r1bar + G^T r2bar / delta_c, dy = (G dx - r2bar)
+                # / delta_c, refined on the augmented system with -delta_c I in the equality block
+                b = np.concatenate([-r3_, bH])
+                d = np.concatenate([np.full(me, gamma), dh])
+                A = K.aug_matrix(W, sigma_x, J, d, 0, dw)
+                dx_, dzall, eh = K.lifted_solve(F, A, J, d, a, b, max_refine=opt.max_refine)
+                dy_, dz_ = dzall[:me], dzall[me:]
+                eta_ = eh[-1]
+            else:
+                A = K.aug_matrix(W, sigma_x, J, dh, 0, dw)
+                dx_, dz_, eh = K.lifted_solve(F, A, J, dh, a, bH, max_refine=opt.max_refine)
+                dy_ = np.zeros(0)
+                eta_ = eh[-1]
+            ds_ = -(r2 + dz_) / dh
+            dv_ = (mu - v * ds_) / s - v
+            dzl_ = np.where(hl, mu / dxl - zl - zl / dxl * dx_, 0.0)
+            dzu_ = np.where(hu, mu / dxu - zu + zu / dxu * dx_, 0.0)
+            return dx_, dy_, dz_, ds_, dv_, dzl_, dzu_, cg_its_, eta_
+
+        dx, dy, dz, ds, dv, dzl, dzu, cg_its, eta = direction(r3, r4)
 
         # fraction to the boundary
         def ftb(val, dval):
@@ -310,20 +317,23 @@ def solve(model, opt: Options | None = None, x0=None):
         alpha = amax
         accepted = False
         ls = 0
+
+        def acceptable(tht, pht, alpha_):
+            ok_f = tht < theta_max and all(tht < tf or pht < pf for tf, pf in filt)
+            if not (ok_f and np.isfinite(pht)):
+                return False, False
+            switching = gphi < 0 and alpha_ * (-gphi) ** S_PHI > DELTA * theta ** S_THETA
+            if switching and theta <= theta_min:
+                return pht <= phi + ETA_PHI * alpha_ * gphi, True
+            return tht <= (1 - GAMMA_THETA) * theta or pht <= phi - GAMMA_PHI * theta, False
+
         while True:
             xt = x + alpha * dx
             st = s + alpha * ds
             gt, ht = model.cons(xt)
             tht = theta_of(gt, ht, st)
             pht = phi_of(xt, st, mu)
-            ok_f = tht < theta_max and all(tht < tf or pht < pf for tf, pf in filt)
-            if ok_f and np.isfinite(pht):
-                switching = gphi < 0 and alpha * (-gphi) ** S_PHI > DELTA * theta ** S_THETA
-                if switching and theta <= theta_min:
-                    if pht <= phi + ETA_PHI * alpha * gphi:
-                        accepted, ftype = True, True
-                elif tht <= (1 - GAMMA_THETA) * theta or pht <= phi - GAMMA_PHI * theta:
-                    accepted, ftype = True, False
+            accepted, ftype = acceptable(tht, pht, alpha)
             if accepted:
                 break
             ls += 1
