@@ -1446,8 +1446,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   }
   B->dpool_len = dp.n;
   B->ipool_len = ip.n;
-  // about 8 elements per thread keep every instance's loop short without idle blocks
-  B->gx = std::max(1, std::min(grid_for(max_elems, B_BLOCK * 8), 64));
+  // up to 32 elements per thread and at most 16 blocks per instance: phase-masked launches stay
+  // cheap (a masked block only checks its instance's phase) while each instance keeps 4,096 threads
+  B->gx = std::max(1, std::min(grid_for(max_elems, B_BLOCK * 32), 16));
   if (cudaMalloc(&B->dpool, sizeof(double) * B->dpool_len) != cudaSuccess ||
       cudaMalloc(&B->ipool, sizeof(int) * B->ipool_len) != cudaSuccess) {
     set_error_msg("ipm_batch_create: out of device memory for the instance pool");
