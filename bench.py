@@ -734,7 +734,8 @@ def ipm_measure(include_oracle=True):
     from synth import config_grid
     out = {}
     cases = [("planar1k", "lifted", 64), ("planar1k", "hykkt", 64), ("planar10k", "hykkt", 64),
-             ("planar1k", "lifted", 32), ("planar10k", "hykkt", 32)]
+             ("planar10k", "lifted", 64), ("planar1k", "lifted", 32), ("planar10k", "hykkt", 32),
+             ("planar80k", "lifted", 64), ("planar80k", "hykkt", 32)]
     warm = cp.ipm_solve_opf(cp.Opf(config_grid("ring30")), kkt="hykkt")
     del warm
     for name, kkt, prec in cases:
@@ -742,7 +743,9 @@ def ipm_measure(include_oracle=True):
         opf = cp.Opf(g)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = cp.IpmState(opf, kkt=kkt, gamma=1e6, precision=prec)
+        # the 80,000-bus HyKKT case is the large configuration: gamma = 1e7, FP32 factor
+        gam = 1e7 if name == "planar80k" else 1e6
+        st = cp.IpmState(opf, kkt=kkt, gamma=gam, precision=prec)
         torch.cuda.synchronize()
         t_init = time.perf_counter() - t0
         t0 = time.perf_counter()
@@ -759,7 +762,7 @@ def ipm_measure(include_oracle=True):
                "ipm_solves_per_s": 1.0 / t_solve,
                "factorizations": int(sum(h.n_factor for h in hist)),
                "cg_iters": int(sum(h.cg_iters for h in hist)),
-               "fp32_iters": int(sum(1 for h in hist if h.precision == 32))}
+               "fp32_iters": int(sum(1 for h in hist if h.precision == 32)), "gamma": gam}
         if include_oracle and name == "planar1k" and prec == 64:
             from oracle.opf import OPFModel
             from oracle import ipm as oipm
