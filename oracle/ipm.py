@@ -112,7 +112,11 @@ class ScaledModel:
         return g * self.de, h * self.di
 
     def jacobian(self, x):
-        return sp.diags(self.d) @ self.base.jacobian(x)
+        # row scaling on the stored values: the structure (explicit zeros included) must stay the
+        # pattern the symbolic analysis was made for
+        J = self.base.jacobian(x).tocsr(copy=True)
+        J.data *= np.repeat(self.d, np.diff(J.indptr))
+        return J
 
     def hessian(self, x, y, z, sigma_f=1.0):
         return self.base.hessian(x, y * self.de, z * self.di, sigma_f)

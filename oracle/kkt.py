@@ -80,6 +80,12 @@ class CondensedSolver:
         self.sym = Symbolic(self.P)
 
     def factor(self, K):
+        # the C factorization writes only the columns the analysis allocated: an entry of K
+        # outside the analysed pattern is a caller error, reported here
+        Kp = sp.csr_matrix((np.ones(K.nnz), K.indices, K.indptr), shape=K.shape)
+        Pp = sp.csr_matrix((np.ones(self.P.nnz), self.P.indices, self.P.indptr), shape=self.P.shape)
+        if (Kp - Kp.multiply(Pp)).count_nonzero():
+            raise ValueError("K has entries outside the analysed pattern")
         return Cholesky(K, self.sym)
 
 

@@ -184,3 +184,121 @@ class OPFModel:
                           shape=(self.n, self.n)).tocsr()
         W.sum_duplicates()
         return W
+
+
+class FlowOPFModel:
+    """The same AC-OPF with branch-flow variables (the formulation whose sizes the paper's
+    instances have: n = 2 N_b + 2 N_g + 4 N_br, m_e = 2 N_b + 1 + 4 N_br):
+      x = [V | theta | Pg | Qg | p_end (2 N_br) | q_end (2 N_br)], ends = from ends then to ends
+      g = [P balance (with -p_end) | Q balance (with -q_end) | theta_ref |
+           p_end - P_end(V, theta) | q_end - Q_end(V, theta)]
+      h = [p_end^2 + q_end^2 - rate^2]  (one row per branch end, h <= 0)
+    Flow variables are free.  Its feasible set projects onto the compact model's, so both have
+    the same optimum."""
+
+    def __init__(self, grid):
+        self.grid = grid
+        nb, nbr, ng = grid.nb, grid.nbr, grid.ng
+        self.nc = 2 * nb + 2 * ng
+        self.n = self.nc + 4 * nbr
+        self.m_e = 2 * nb + 1 + 4 * nbr
+        self.m_i = 2 * nbr
+        self.base = OPFModel(grid)
+        lo, hi = grid.bounds()
+        self.xl = np.concatenate([lo, np.full(4 * nbr, -np.inf)])
+        self.xu = np.concatenate([hi, np.full(4 * nbr, np.inf)])
+        self.op = self.nc                # p_end block
+        self.oq = self.nc + 2 * nbr      # q_end block
+        self.rp = 2 * nb + 1             # p definition rows
+        self.rq = 2 * nb + 1 + 2 * nbr   # q definition rows
+
+    def x0(self):
+        """Compact flat start; each flow variable at the flow the start voltages give."""
+        xc = self.base.x0()
+        P = np.concatenate([fl[2] for fl in self.base._flows(xc)])
+        Q = np.concatenate([fl[3] for fl in self.base._flows(xc)])
+        return np.concatenate([xc, P, Q])
+
+    def objective(self, x):
+        return self.base.objective(x[:self.nc])
+
+    def grad(self, x):
+        return np.concatenate([self.base.grad(x[:self.nc]), np.zeros(4 * self.grid.nbr)])
+
+    def cons(self, x):
+        g = self.grid
+        nb, nbr = g.nb, g.nbr
+        xc = x[:self.nc]
+        p, q = x[self.op:self.op + 2 * nbr], x[self.oq:self.oq + 2 * nbr]
+        ge = np.zeros(self.m_e)
+        np.add.at(ge, g.gen_bus, xc[2 * nb:2 * nb + g.ng])
+        np.add.at(ge, nb + g.gen_bus, xc[2 * nb + g.ng:])
+        ge[:nb] -= g.pd
+        ge[nb:2 * nb] -= g.qd
+        buses = np.concatenate([g.f_bus, g.t_bus])
+        np.add.at(ge, buses, -p)
+        np.add.at(ge, nb + buses, -q)
+        ge[2 * nb] = xc[nb + g.ref_bus]
+        flows = self.base._flows(xc)
+        P = np.concatenate([fl[2] for fl in flows])
+        Q = np.concatenate([fl[3] for fl in flows])
+        ge[self.rp:self.rp + 2 * nbr] = p - P
+        ge[self.rq:self.rq + 2 * nbr] = q - Q
+        hi = p ** 2 + q ** 2 - np.concatenate([g.rate, g.rate]) ** 2
+        return ge, hi
+
+    def jacobian(self, x):
+        g = self.grid
+        nb, nbr, ng = g.nb, g.nbr, g.ng
+        rows, cols, vals = [], [], []
+        gi = np.arange(ng)
+        rows += [g.gen_bus, nb + g.gen_bus]
+        cols += [2 * nb + gi, 2 * nb + ng + gi]
+        vals += [np.ones(ng), np.ones(ng)]
+        ends = np.arange(2 * nbr)
+        buses = np.concatenate([g.f_bus, g.t_bus])
+        pv, qv = self.op + ends, self.oq + ends
+        rows += [buses, nb + buses, self.rp + ends, self.rq + ends]
+        cols += [pv, qv, pv, qv]
+        vals += [-np.ones(2 * nbr), -np.ones(2 * nbr), np.ones(2 * nbr), np.ones(2 * nbr)]
+        flows = self.base._flows(x[:self.nc])
+        for e, (bus, idx, P, Q, dP, dQ, _hP, _hQ) in enumerate(flows):
+            sl = np.arange(e * nbr, (e + 1) * nbr)
+            for k in range(4):
+                rows += [self.rp + sl, self.rq + sl]
+                cols += [idx[:, k], idx[:, k]]
+                vals += [-dP[:, k], -dQ[:, k]]
+        hrow = self.m_e + ends
+        rows += [hrow, hrow, np.array([2 * nb])]
+        cols += [pv, qv, np.array([nb + g.ref_bus])]
+        vals += [2 * x[pv], 2 * x[qv], np.array([1.0])]
+        J = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.m_e + self.m_i, self.n)).tocsr()
+        J.sum_duplicates()
+        return J
+
+    def hessian(self, x, y, z, sigma_f=1.0):
+        g = self.grid
+        nb, nbr, ng = g.nb, g.nbr, g.ng
+        rows, cols, vals = [], [], []
+        gi = np.arange(ng)
+        rows.append(2 * nb + gi)
+        cols.append(2 * nb + gi)
+        vals.append(sigma_f * 2 * g.c2 * BASE * BASE)
+        flows = self.base._flows(x[:self.nc])
+        for e, (bus, idx, P, Q, dP, dQ, hP, hQ) in enumerate(flows):
+            sl = np.arange(e * nbr, (e + 1) * nbr)
+            yp, yq = y[self.rp + sl], y[self.rq + sl]
+            for a in range(4):
+                for b in range(4):
+                    rows.append(idx[:, a])
+                    cols.append(idx[:, b])
+                    vals.append(-yp * hP[:, a, b] - yq * hQ[:, a, b])
+        ends = np.arange(2 * nbr)
+        rows += [self.op + ends, self.oq + ends]
+        cols += [self.op + ends, self.oq + ends]
+        vals += [2 * z, 2 * z]
+        W = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.n, self.n)).tocsr()
+        W.sum_duplicates()
+        return W

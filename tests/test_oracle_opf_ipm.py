@@ -159,3 +159,46 @@ def test_dual_regularized_form_converges_near_hykkt():
         assert r.status == "converged"
         # delta_c = 1/gamma perturbs the dual update only: same optimum to O(delta_c)
         assert abs(r.obj - hy.obj) <= 1e-6 * abs(hy.obj)
+
+
+def test_flow_model_derivatives_by_finite_differences():
+    from oracle.opf import FlowOPFModel
+    g = config_grid("ring30")
+    m = FlowOPFModel(g)
+    rng = np.random.default_rng(3)
+    x = m.x0() + rng.normal(0, 0.02, m.n)
+    y, z = rng.normal(size=m.m_e), rng.normal(size=m.m_i)
+    J = m.jacobian(x).toarray()
+    h = 1e-6
+    fd = np.zeros_like(J)
+    for j in range(m.n):
+        e = np.zeros(m.n)
+        e[j] = h
+        gp, hp = m.cons(x + e)
+        gm, hm = m.cons(x - e)
+        fd[:, j] = (np.concatenate([gp, hp]) - np.concatenate([gm, hm])) / (2 * h)
+    assert np.allclose(J, fd, atol=1e-6)
+
+    def lag_grad(xx):
+        return 0.7 * m.grad(xx) + m.jacobian(xx).T @ np.concatenate([y, z])
+    W = m.hessian(x, y, z, 0.7).toarray()
+    fdw = np.zeros_like(W)
+    for j in range(m.n):
+        e = np.zeros(m.n)
+        e[j] = h
+        fdw[:, j] = (lag_grad(x + e) - lag_grad(x - e)) / (2 * h)
+    assert np.allclose(W, fdw, atol=1e-5)
+    assert np.allclose(W, W.T)
+
+
+def test_flow_model_has_the_compact_optimum():
+    # the flow variables only name the branch flows: the same feasible set after projection,
+    # so HyKKT (exact equalities) reaches the same objective on both formulations
+    from oracle.opf import FlowOPFModel
+    g = config_grid("ring30")
+    a = ipm.solve(OPFModel(g), ipm.Options(kkt="hykkt", gamma=1e6))
+    b = ipm.solve(FlowOPFModel(g), ipm.Options(kkt="hykkt", gamma=1e6))
+    assert a.status == b.status == "converged"
+    assert abs(a.obj - b.obj) <= 1e-6 * abs(a.obj)
+    m = FlowOPFModel(g)
+    assert (m.n, m.m_e, m.m_i) == (2 * g.nb + 2 * g.ng + 4 * g.nbr, 2 * g.nb + 1 + 4 * g.nbr, 2 * g.nbr)
