@@ -236,6 +236,18 @@ int ipm_opf_create(int nb, int nbr, int ng, const int *f_bus, const int *t_bus, 
                    const double *x, const double *b, const double *rate, const double *pd,
                    const double *qd, const int *gen_bus, const double *c2, const double *c1,
                    const double *xl, const double *xu, cudaStream_t stream, ipm_opf_t *out);
+/* The same grid in the flow-variable formulation (the shape of the paper's instances): branch
+ * flows p_end, q_end (2 nbr each, from ends then to ends) are free variables after [V | theta |
+ * Pg | Qg]; equalities [P balance | Q balance | theta_ref | p_end - P_end(V, theta) |
+ * q_end - Q_end(V, theta)], inequalities p_end^2 + q_end^2 - rate^2 <= 0.  n = 2 nb + 2 ng +
+ * 4 nbr, m_e = 2 nb + 1 + 4 nbr, m_i = 2 nbr.  Arguments as for ipm_opf_create (xl, xu: the
+ * 2 nb + 2 ng compact bounds).  The IPM starts every flow variable at the flow of its start
+ * voltages. */
+int ipm_opf_create_flow(int nb, int nbr, int ng, const int *f_bus, const int *t_bus,
+                        const double *r, const double *x, const double *b, const double *rate,
+                        const double *pd, const double *qd, const int *gen_bus, const double *c2,
+                        const double *c1, const double *xl, const double *xu,
+                        cudaStream_t stream, ipm_opf_t *out);
 int ipm_opf_info(ipm_opf_t opf, int *n, int *m_e, int *m_i, int *nnzJ, int *nnzW);
 /* Copies the handle's patterns into caller buffers (host or device; NULLs skipped): CSR of J
  * (J_rowptr [m_e+m_i+1], J_colind [nnzJ]) and CSR of the lower triangle of W (W_rowptr [n+1],

@@ -46,6 +46,7 @@ _SIGS = {
     "ipm_aug_solve": (I, [P, P, P, P, P, P, D, P, P, P, P, I, D, P, P, P]),
     "hykkt_cg": (I, [P, P, I, P, P, D, P, P, D, I, P, P, P, P, P, P]),
     "ipm_opf_create": (I, [I, I, I] + [P] * 13 + [P, P]),
+    "ipm_opf_create_flow": (I, [I, I, I] + [P] * 13 + [P, P]),
     "ipm_opf_info": (I, [P, P, P, P, P, P]),
     "ipm_opf_patterns": (I, [P, P, P, P, P]),
     "ipm_opf_eval": (I, [P, P, P, P, D, P, P, P, P, P, P, P]),
@@ -283,7 +284,8 @@ def hykkt_cg(sym, num, m_e, J_val, d_row, gamma, a, b, dx, dy, dz, rtol=1e-10, m
 class Opf:
     """ipm_opf handle for one synthetic grid (``synth.Grid``); patterns as int32 CUDA tensors."""
 
-    def __init__(self, grid, stream=None):
+    def __init__(self, grid, stream=None, form="compact"):
+        """form "compact" (x = [V | theta | Pg | Qg]) or "flow" (plus branch-flow variables)."""
         import torch
         c = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
         self._keep = [c(grid.f_bus, np.int32), c(grid.t_bus, np.int32), c(grid.r, np.float64),
@@ -294,8 +296,9 @@ class Opf:
         self._keep += [c(lo, np.float64), c(hi, np.float64)]
         ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in self._keep]
         h = ctypes.c_void_p()
-        _check(lib().ipm_opf_create(grid.nb, grid.nbr, grid.ng, *ptrs, _stream(stream),
-                                    ctypes.byref(h)), "ipm_opf_create")
+        create = lib().ipm_opf_create_flow if form == "flow" else lib().ipm_opf_create
+        _check(create(grid.nb, grid.nbr, grid.ng, *ptrs, _stream(stream), ctypes.byref(h)),
+               "ipm_opf_create")
         self.h = h
         n, me, mi, nj, nw = I(), I(), I(), I(), I()
         _check(lib().ipm_opf_info(h, *(ctypes.byref(v) for v in (n, me, mi, nj, nw))), "ipm_opf_info")

@@ -121,7 +121,7 @@ __device__ __forceinline__ EvalPtrs eval_ptrs(const BI &I, const BCtl &c, int mo
   return E;
 }
 __device__ __forceinline__ OpfDims opf_dims(const OpfData &M) {
-  return OpfDims{M.nb, M.nbr, M.ng, M.n, M.me, M.mi};
+  return OpfDims{M.nb, M.nbr, M.ng, M.n, M.me, M.mi, M.form};
 }
 
 __global__ void k_b_eval_init(const BI *bi, const BCtl *ctl, int phase, int mode) {
@@ -211,8 +211,15 @@ __global__ void k_b_setup_sums(const BI *bi, const BCtl *ctl) {
 }
 __global__ void k_b_x0(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
-  for (int j = gtid; j < I.D.n; j += gstride)
+  for (int j = gtid; j < 2 * I.M.nb + 2 * I.M.ng; j += gstride)
     I.P.x[j] = x0_at(I.M.nb, I.M.ng, I.R[R_PD], I.R[R_QD], I.P.xl, I.P.xu, j);
+}
+// flow-variable form: each flow variable at the flow of the start voltages
+__global__ void k_b_flow_start(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  if (!I.M.form) return;
+  const OpfDims D = opf_dims(I.M);
+  for (int e = gtid; e < 2 * D.nbr; e += gstride) flow_start_at(D, I.M, I.P.x, e);
 }
 __global__ void k_b_row_scale(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
@@ -1335,6 +1342,7 @@ int init_instances(ipm_batch_t B) {
   k_b_ctl_init<<<grid_for(C, 128), 128, 0, s>>>(bi, ctl, C, mu0);
   k_b_setup_sums<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_x0<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_flow_start<<<g2, blk, 0, s>>>(bi, ctl);
   auto eval0 = [&]() {
     k_b_eval_init<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0);
     k_b_eval_branch<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0);
@@ -1348,7 +1356,7 @@ int init_instances(ipm_batch_t B) {
   k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0, B->opt.tau);
   k_b_init_duals<<<g2, blk, 0, s>>>(bi, ctl);
   CKL();
-  count_launches(15);
+  count_launches(16);
   return IPM_OK;
 }
 

@@ -391,7 +391,10 @@ extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStrea
     for (int k = 0; k < R_COUNT; ++k) cudaMemcpy(S->R + k, &zero, sizeof(double), cudaMemcpyHostToDevice);
     k_setup_sums<<<grid1(M.nb), 256, 0, s>>>(M.nb, M.pd, M.qd, S->R);
     k_x0<<<grid1(n), 256, 0, s>>>(M.nb, M.ng, S->R, M.xl, M.xu, S->P.x);
-    rc = opf_eval(M, S->P.x, nullptr, nullptr, 1.0, S->f, S->P.grad, S->gs, S->hs, S->Jv, nullptr, s);
+    rc = opf_flow_start(M, S->P.x, s);
+    if (rc == IPM_OK)
+      rc = opf_eval(M, S->P.x, nullptr, nullptr, 1.0, S->f, S->P.grad, S->gs, S->hs, S->Jv,
+                    nullptr, s);
   }
   if (rc == IPM_OK) {
     cudaStream_t s = stream;

@@ -8,6 +8,7 @@
 // Branch pi-model: series 1/(r + j x), shunt j b/2 per end, unit tap.  Cost on MW (base 100).
 #include <climits>
 #include <cmath>
+#include <vector>
 
 #include "internal.cuh"
 #include "opf.cuh"
@@ -19,10 +20,15 @@ static constexpr int SORT_CAP2 = 1024;
 
 // --- pattern construction: every model term lists its (row, col) coordinates in a fixed
 // order; rows are then sorted/uniqued and each term records the entry it writes.
-// J terms: per gen 2, per branch end 12 (4 P-balance, 4 Q-balance, 4 thermal), theta_ref 1
-__device__ __forceinline__ int jterm_count(const OpfDims &D) { return 2 * D.ng + 24 * D.nbr + 1; }
-// W terms: per gen 1, per branch end 10 (lower 4x4 block)
-__device__ __forceinline__ int wterm_count(const OpfDims &D) { return D.ng + 20 * D.nbr; }
+// J terms: per gen 2, per branch end 12 (compact: 4 P-balance, 4 Q-balance, 4 thermal) or 14
+// (flow form: balance P and Q, p and q definitions with 5 each, thermal 2), theta_ref 1
+__host__ __device__ __forceinline__ int jterm_count(const OpfDims &D) {
+  return 2 * D.ng + 2 * jterms_per_end(D) * D.nbr + 1;
+}
+// W terms: per gen 1, per branch end 10 (lower 4x4 block) or 12 (plus p_end, q_end diagonals)
+__host__ __device__ __forceinline__ int wterm_count(const OpfDims &D) {
+  return D.ng + 2 * wterms_per_end(D) * D.nbr;
+}
 
 __device__ __forceinline__ void jterm(const OpfDims &D, const int *f_bus, const int *t_bus,
                                       const int *gen_bus, int ref, int t, int *row, int *col) {
@@ -38,7 +44,22 @@ __device__ __forceinline__ void jterm(const OpfDims &D, const int *f_bus, const 
     return;
   }
   t -= 2 * D.ng;
-  if (t < 24 * D.nbr) {
+  if (D.form && t < 28 * D.nbr) {
+    const int e = t / 14, k = t % 14;
+    int bus, v[4];
+    end_vars(D, f_bus, t_bus, e, &bus, v);
+    const int pv = flow_pvar(D, e), qv = flow_qvar(D, e);
+    const int rp = flow_prow(D, e), rq = flow_qrow(D, e);
+    if (k == 0) { *row = bus; *col = pv; }
+    else if (k == 1) { *row = D.nb + bus; *col = qv; }
+    else if (k == 2) { *row = rp; *col = pv; }
+    else if (k < 7) { *row = rp; *col = v[k - 3]; }
+    else if (k == 7) { *row = rq; *col = qv; }
+    else if (k < 12) { *row = rq; *col = v[k - 8]; }
+    else { *row = D.me + e; *col = k == 12 ? pv : qv; }
+    return;
+  }
+  if (!D.form && t < 24 * D.nbr) {
     int e = t / 12, k = t % 12;
     int bus, v[4];
     end_vars(D, f_bus, t_bus, e, &bus, v);
@@ -60,7 +81,12 @@ __device__ __forceinline__ void wterm(const OpfDims &D, const int *f_bus, const 
     return;
   }
   t -= D.ng;
-  int e = t / 10, k = t % 10;
+  const int per = wterms_per_end(D);
+  int e = t / per, k = t % per;
+  if (k >= 10) {  // flow form: (p_end, p_end), (q_end, q_end)
+    *row = *col = k == 10 ? flow_pvar(D, e) : flow_qvar(D, e);
+    return;
+  }
   int bus, v[4];
   end_vars(D, f_bus, t_bus, e, &bus, v);
   int a = v[c_lowpairs[k][0]], b = v[c_lowpairs[k][1]];
@@ -123,7 +149,7 @@ __global__ void k_term_entry(int nt, const int *trow, const int *tcol, const int
 static int build_pattern(bool isJ, const OpfDims &D, const OpfData &M, int nrows, int **rowptr,
                          int **colind, int **entry, int *nnz, cudaStream_t s) {
   DevTemp T;
-  int nt = isJ ? 2 * D.ng + 24 * D.nbr + 1 : D.ng + 20 * D.nbr;
+  int nt = isJ ? jterm_count(D) : wterm_count(D);
   int *trow, *tcol, *cnt, *ptr, *fill, *cand, *ucnt;
   CKR(T.alloc(&trow, nt));
   CKR(T.alloc(&tcol, nt));
@@ -199,7 +225,7 @@ __global__ void k_eval_finish(OpfDims D, OpfData M, const double *fpart, int npa
 int opf_eval(const OpfData &M, const double *x, const double *y, const double *z, double sigma_f,
              double *f, double *grad, double *g, double *h, double *Jv, double *Wv,
              cudaStream_t s) {
-  OpfDims D{M.nb, M.nbr, M.ng, M.n, M.me, M.mi};
+  OpfDims D{M.nb, M.nbr, M.ng, M.n, M.me, M.mi, M.form};
   int nthreads = max(max(D.nb, 1), 256);
   k_eval_init<<<grid_for(nthreads, 256), 256, 0, s>>>(D, M.pd, M.qd, x, M.ref, g, Jv,
                                                       Jv ? M.nnzJ : 0, Wv, Wv ? M.nnzW : 0);
@@ -216,6 +242,19 @@ int opf_eval(const OpfData &M, const double *x, const double *y, const double *z
   return IPM_OK;
 }
 
+__global__ void k_flow_start(OpfDims D, OpfData M, double *x) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 2 * D.nbr) flow_start_at(D, M, x, e);
+}
+
+int opf_flow_start(const OpfData &M, double *x, cudaStream_t s) {
+  if (!M.form || M.nbr == 0) return IPM_OK;
+  OpfDims D{M.nb, M.nbr, M.ng, M.n, M.me, M.mi, M.form};
+  k_flow_start<<<grid_for(2 * M.nbr, 128), 128, 0, s>>>(D, M, x);
+  CKL();
+  return IPM_OK;
+}
+
 void opf_free(OpfData &M) {
   void *ps[] = {M.f_bus, M.t_bus, M.gen_bus, M.adm, M.rate, M.pd, M.qd, M.c2, M.c1, M.xl, M.xu,
                 M.J_rowptr, M.J_colind, M.W_rowptr, M.W_colind, M.jentry, M.wentry, M.fpart};
@@ -226,14 +265,16 @@ void opf_free(OpfData &M) {
 int opf_create(OpfData &M, int nb, int nbr, int ng, const int *f_bus, const int *t_bus,
                const double *r, const double *x, const double *b, const double *rate,
                const double *pd, const double *qd, const int *gen_bus, const double *c2,
-               const double *c1, const double *xl, const double *xu, cudaStream_t s) {
+               const double *c1, const double *xl, const double *xu, cudaStream_t s, int form) {
   M.nb = nb;
   M.nbr = nbr;
   M.ng = ng;
-  M.n = 2 * nb + 2 * ng;
-  M.me = 2 * nb + 1;
+  M.form = form;
+  M.n = 2 * nb + 2 * ng + (form ? 4 * nbr : 0);
+  M.me = 2 * nb + 1 + (form ? 4 * nbr : 0);
   M.mi = 2 * nbr;
   const int n = M.n;
+  const int nc = 2 * nb + 2 * ng;  // the caller's bounds cover the compact variables
   CKR(dev_alloc(&M.f_bus, nbr));
   CKR(dev_alloc(&M.t_bus, nbr));
   CKR(dev_alloc(&M.gen_bus, ng));
@@ -266,14 +307,19 @@ int opf_create(OpfData &M, int nb, int nbr, int ng, const int *f_bus, const int 
   CKR(up(M.qd, qd, sizeof(double) * nb));
   CKR(up(M.c2, c2, sizeof(double) * ng));
   CKR(up(M.c1, c1, sizeof(double) * ng));
-  CKR(up(M.xl, xl, sizeof(double) * n));
-  CKR(up(M.xu, xu, sizeof(double) * n));
+  CKR(up(M.xl, xl, sizeof(double) * nc));
+  CKR(up(M.xu, xu, sizeof(double) * nc));
+  if (n > nc) {  // flow variables are free
+    std::vector<double> lo(n - nc, -INFINITY), hi(n - nc, INFINITY);
+    CK(cudaMemcpy(M.xl + nc, lo.data(), sizeof(double) * (n - nc), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(M.xu + nc, hi.data(), sizeof(double) * (n - nc), cudaMemcpyHostToDevice));
+  }
   M.ref = gen_bus[0];
   if (nbr > 0) {
     k_branch_admittance<<<grid_for(nbr, 256), 256, 0, s>>>(nbr, dr, dx, db, M.adm);
     CKL();
   }
-  OpfDims D{nb, nbr, ng, M.n, M.me, M.mi};
+  OpfDims D{nb, nbr, ng, M.n, M.me, M.mi, M.form};
   CKR(build_pattern(true, D, M, M.me + M.mi, &M.J_rowptr, &M.J_colind, &M.jentry, &M.nnzJ, s));
   CKR(build_pattern(false, D, M, n, &M.W_rowptr, &M.W_colind, &M.wentry, &M.nnzW, s));
   CK(cudaStreamSynchronize(s));
@@ -284,12 +330,37 @@ int opf_create(OpfData &M, int nb, int nbr, int ng, const int *f_bus, const int 
 
 using namespace cipm;
 
+static int opf_create_form(int form, int nb, int nbr, int ng, const int *f_bus,
+                           const int *t_bus, const double *r, const double *x, const double *b,
+                           const double *rate, const double *pd, const double *qd,
+                           const int *gen_bus, const double *c2, const double *c1,
+                           const double *xl, const double *xu, cudaStream_t s, ipm_opf_t *out);
+
 extern "C" int ipm_opf_create(int nb, int nbr, int ng, const int *f_bus, const int *t_bus,
                               const double *r, const double *x, const double *b,
                               const double *rate, const double *pd, const double *qd,
                               const int *gen_bus, const double *c2, const double *c1,
                               const double *xl, const double *xu, cudaStream_t s,
                               ipm_opf_t *out) {
+  return opf_create_form(0, nb, nbr, ng, f_bus, t_bus, r, x, b, rate, pd, qd, gen_bus, c2, c1,
+                         xl, xu, s, out);
+}
+
+extern "C" int ipm_opf_create_flow(int nb, int nbr, int ng, const int *f_bus, const int *t_bus,
+                                   const double *r, const double *x, const double *b,
+                                   const double *rate, const double *pd, const double *qd,
+                                   const int *gen_bus, const double *c2, const double *c1,
+                                   const double *xl, const double *xu, cudaStream_t s,
+                                   ipm_opf_t *out) {
+  return opf_create_form(1, nb, nbr, ng, f_bus, t_bus, r, x, b, rate, pd, qd, gen_bus, c2, c1,
+                         xl, xu, s, out);
+}
+
+static int opf_create_form(int form, int nb, int nbr, int ng, const int *f_bus,
+                           const int *t_bus, const double *r, const double *x, const double *b,
+                           const double *rate, const double *pd, const double *qd,
+                           const int *gen_bus, const double *c2, const double *c1,
+                           const double *xl, const double *xu, cudaStream_t s, ipm_opf_t *out) {
   if (!out || nb <= 0 || nbr < 0 || ng <= 0 || !f_bus || !t_bus || !r || !x || !b || !rate ||
       !pd || !qd || !gen_bus || !c2 || !c1 || !xl || !xu) {
     set_error_msg("ipm_opf_create: bad argument");
@@ -308,7 +379,7 @@ extern "C" int ipm_opf_create(int nb, int nbr, int ng, const int *f_bus, const i
   *out = nullptr;
   ipm_opf_t P = new ipm_opf_s();
   int rc = opf_create(P->M, nb, nbr, ng, f_bus, t_bus, r, x, b, rate, pd, qd, gen_bus, c2, c1, xl,
-                      xu, s);
+                      xu, s, form);
   if (rc != IPM_OK) {
     opf_free(P->M);
     delete P;

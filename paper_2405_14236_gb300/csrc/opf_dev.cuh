@@ -1,8 +1,11 @@
 // Device side of the AC-OPF model evaluation (per branch end, per generator), shared by the
 // single-problem kernels (opf.cu) and the batched ones (batch.cu).
 //
-// Layout: x = [V (nb) | theta (nb) | Pg (ng) | Qg (ng)];
+// Compact form (0): x = [V (nb) | theta (nb) | Pg (ng) | Qg (ng)];
 // g = [P balance (nb) | Q balance (nb) | theta_ref]; h = [|S_from|^2 - rate^2 | |S_to|^2 - rate^2].
+// Flow-variable form (1): x adds p_end (2 nbr) | q_end (2 nbr) (ends: from ends, then to ends),
+// g = [P balance with -p_end | Q balance with -q_end | theta_ref | p_end - P_end(V, theta) |
+// q_end - Q_end(V, theta)], h = [p_end^2 + q_end^2 - rate^2].
 // Branch pi-model: series 1/(r + j x), shunt j b/2 per end, unit tap.  Cost on MW (base 100).
 #pragma once
 #include "opf.cuh"
@@ -13,7 +16,23 @@ static constexpr double BASE = 100.0;
 
 struct OpfDims {
   int nb, nbr, ng, n, me, mi;
+  int form;
 };
+
+// per-end term counts and offsets of the two forms (J: 12 or 14 terms per end after 2 per
+// generator; W: 10 or 12 per end after 1 per generator)
+__host__ __device__ __forceinline__ int jterms_per_end(const OpfDims &D) { return D.form ? 14 : 12; }
+__host__ __device__ __forceinline__ int wterms_per_end(const OpfDims &D) { return D.form ? 12 : 10; }
+__host__ __device__ __forceinline__ int flow_pvar(const OpfDims &D, int e) {
+  return 2 * D.nb + 2 * D.ng + e;
+}
+__host__ __device__ __forceinline__ int flow_qvar(const OpfDims &D, int e) {
+  return 2 * D.nb + 2 * D.ng + 2 * D.nbr + e;
+}
+__host__ __device__ __forceinline__ int flow_prow(const OpfDims &D, int e) { return 2 * D.nb + 1 + e; }
+__host__ __device__ __forceinline__ int flow_qrow(const OpfDims &D, int e) {
+  return 2 * D.nb + 1 + 2 * D.nbr + e;
+}
 
 __device__ __forceinline__ void end_vars(const OpfDims &D, const int *f_bus, const int *t_bus,
                                          int e, int *bus, int *vars) {
@@ -58,12 +77,89 @@ __device__ __forceinline__ void eval_init_at(const OpfDims &D, const double *pd,
     for (int p = i; p < nnzW; p += stride) Wv[p] = 0.0;
 }
 
+// flow leaving bus a on branch end e and its derivatives / second derivatives in the local
+// variable order (Va, Vb, theta_a, theta_b); lower-triangle second derivatives follow c_lowpairs
+struct EndFlow {
+  int bus, v[4];
+  double P, Q, dP[4], dQ[4], hP[10], hQ[10];
+};
+__device__ __forceinline__ void end_flow_at(const OpfDims &D, const OpfData &M, const double *x,
+                                            int e, EndFlow &F) {
+  const int k = e % D.nbr;
+  end_vars(D, M.f_bus, M.t_bus, e, &F.bus, F.v);
+  double4_32a ad = M.adm[k];
+  const double G1 = ad.x, B1 = ad.y, G2 = ad.z, B2 = ad.w;
+  const double Va = x[F.v[0]], Vb = x[F.v[1]], ta = x[F.v[2]], tb = x[F.v[3]];
+  double sn, cs;
+  sincos(ta - tb, &sn, &cs);
+  const double A = G2 * cs + B2 * sn, Bq = G2 * sn - B2 * cs;
+  F.P = G1 * Va * Va + Va * Vb * A;
+  F.Q = -B1 * Va * Va + Va * Vb * Bq;
+  const double dP[4] = {2 * G1 * Va + Vb * A, Va * A, -Va * Vb * Bq, Va * Vb * Bq};
+  const double dQ[4] = {-2 * B1 * Va + Vb * Bq, Va * Bq, Va * Vb * A, -Va * Vb * A};
+  const double hP[10] = {2 * G1, A, 0.0, -Vb * Bq, -Va * Bq, -Va * Vb * A, Vb * Bq, Va * Bq,
+                         Va * Vb * A, -Va * Vb * A};
+  const double hQ[10] = {-2 * B1, Bq, 0.0, Vb * A, Va * A, -Va * Vb * Bq, -Vb * A, -Va * A,
+                         Va * Vb * Bq, -Va * Vb * Bq};
+  for (int c = 0; c < 4; ++c) {
+    F.dP[c] = dP[c];
+    F.dQ[c] = dQ[c];
+  }
+  for (int t = 0; t < 10; ++t) {
+    F.hP[t] = hP[t];
+    F.hQ[t] = hQ[t];
+  }
+}
+
+// flow-variable form, branch end e (term order per end: balance P, balance Q, p definition
+// (p_end, Va, Vb, theta_a, theta_b), q definition (q_end, ...), thermal (p_end, q_end); W: the 10
+// lower pairs of the definition rows, then (p_end, p_end), (q_end, q_end))
+__device__ __forceinline__ void eval_branch_flow_at(const OpfDims &D, const OpfData &M,
+                                                    const double *x, const double *y,
+                                                    const double *z, double *g, double *h,
+                                                    double *Jv, double *Wv, int e) {
+  EndFlow F;
+  end_flow_at(D, M, x, e, F);
+  const int pv = flow_pvar(D, e), qv = flow_qvar(D, e);
+  const double p = x[pv], q = x[qv];
+  atomicAdd(&g[F.bus], -p);
+  atomicAdd(&g[D.nb + F.bus], -q);
+  g[flow_prow(D, e)] = p - F.P;
+  g[flow_qrow(D, e)] = q - F.Q;
+  const double rt = M.rate[e % D.nbr];
+  h[e] = p * p + q * q - rt * rt;
+  if (Jv) {
+    const int *je = M.jentry + 2 * D.ng + 14 * e;
+    Jv[je[0]] = -1.0;
+    Jv[je[1]] = -1.0;
+    Jv[je[2]] = 1.0;
+    Jv[je[7]] = 1.0;
+    for (int c = 0; c < 4; ++c) {
+      Jv[je[3 + c]] = -F.dP[c];
+      Jv[je[8 + c]] = -F.dQ[c];
+    }
+    Jv[je[12]] = 2 * p;
+    Jv[je[13]] = 2 * q;
+  }
+  if (Wv) {
+    const double yp = y[flow_prow(D, e)], yq = y[flow_qrow(D, e)], zz = z[e];
+    const int *we = M.wentry + D.ng + 12 * e;
+    for (int t = 0; t < 10; ++t) atomicAdd(&Wv[we[t]], -yp * F.hP[t] - yq * F.hQ[t]);
+    Wv[we[10]] = 2 * zz;
+    Wv[we[11]] = 2 * zz;
+  }
+}
+
 // branch end e: flows into the balance rows, thermal row, their derivatives, and the weighted
 // second derivatives (y on the balance rows, z on the thermal row) into W
 __device__ __forceinline__ void eval_branch_at(const OpfDims &D, const OpfData &M,
                                                const double *x, const double *y, const double *z,
                                                double *g, double *h, double *Jv, double *Wv,
                                                int e) {
+  if (D.form) {
+    eval_branch_flow_at(D, M, x, y, z, g, h, Jv, Wv, e);
+    return;
+  }
   int k = e % D.nbr;
   int bus, v[4];
   end_vars(D, M.f_bus, M.t_bus, e, &bus, v);
@@ -134,13 +230,21 @@ __device__ __forceinline__ void eval_finish_at(const OpfDims &D, const OpfData &
   if (grad)
     for (int k = i; k < 2 * D.nb; k += stride) grad[k] = 0.0;
   if (i == 0) {
-    if (Jv) Jv[M.jentry[2 * D.ng + 24 * D.nbr]] = 1.0;
+    if (Jv) Jv[M.jentry[2 * D.ng + 2 * jterms_per_end(D) * D.nbr]] = 1.0;
     if (f) {
       double s = 0.0;
       for (int p = 0; p < nparts; ++p) s += fpart[p];
       *f = s;
     }
   }
+}
+
+// flow-variable start: p_end, q_end = the flows of the voltages already in x
+__device__ __forceinline__ void flow_start_at(const OpfDims &D, const OpfData &M, double *x, int e) {
+  EndFlow F;
+  end_flow_at(D, M, x, e, F);
+  x[flow_pvar(D, e)] = F.P;
+  x[flow_qvar(D, e)] = F.Q;
 }
 
 }  // namespace cipm
