@@ -447,6 +447,33 @@ def aggregate_ranks(t_ms, converged, world, device):
     return float(t.item()), float(c.item())
 
 
+def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3):
+    """The headline's instances solved by another batched form (the dual-regularized condensed
+    form: equality rows kept, delta_c = 1/gamma)."""
+    import torch
+    import paper_2405_14236_gb300 as cp
+    opfs = [cp.Opf(g) for g in grids]
+    B = cp.Batch(opfs, kkt=kkt, gamma=gamma)
+    B.run(max_iter=MAX_ITER)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, conv, its = [], [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        B.reset()
+        B.run(max_iter=MAX_ITER)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        r = B.results()
+        conv.append(int((r["status"] == 1).sum()))
+        its.append(float(r["iters"].mean()))
+    return {"kkt": kkt, "gamma": gamma, "value": float(np.sum(conv) / (np.sum(ms) / 1e3)),
+            "unit": UNIT, "converged_per_step": conv, "iters_mean": float(np.mean(its)),
+            "ms_per_step": float(np.mean(ms))}
+
+
 def plain_measure(grids):
     """Single-problem GPU IPM (ipm_step loop, LiftedKKT FP64) on the given instances, one after
     another; time of the iterations (the per-problem symbolic analysis excluded, as for the
@@ -610,6 +637,7 @@ def run_gpu(args, rank, world, local_rank):
         line["plain"] = plain_measure([grids[i // 2] if i % 2 == 0 or ns == len(grids)
                                        else grids[ns + i // 2] for i in range(4)])
         line["plain"]["batched_speedup"] = value / line["plain"]["value"]
+    line["batch_regularized"] = batch_form_measure(grids)
     if not args.no_warm:
         line["warm"] = warm_measure()
         if "plain" in line:
@@ -735,16 +763,19 @@ def ipm_measure(include_oracle=True):
     out = {}
     cases = [("planar1k", "lifted", 64), ("planar1k", "hykkt", 64), ("planar10k", "hykkt", 64),
              ("planar10k", "lifted", 64), ("planar1k", "lifted", 32), ("planar10k", "hykkt", 32),
-             ("planar80k", "lifted", 64), ("planar80k", "hykkt", 32)]
+             ("planar80k", "lifted", 64), ("planar80k", "hykkt", 32),
+             ("planar10k-flow", "hykkt", 64), ("planar10k-flow", "lifted", 64)]
     warm = cp.ipm_solve_opf(cp.Opf(config_grid("ring30")), kkt="hykkt")
     del warm
     for name, kkt, prec in cases:
-        g = config_grid(name)
-        opf = cp.Opf(g)
+        # "-flow": the flow-variable formulation (the shape of the paper's instances)
+        g = config_grid(name.replace("-flow", ""))
+        opf = cp.Opf(g, form="flow" if name.endswith("-flow") else "compact")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         # the 80,000-bus HyKKT case is the large configuration: gamma = 1e7, FP32 factor
         gam = 1e7 if name == "planar80k" else 1e6
+        sizes = {"n": opf.n, "m_e": opf.m_e, "m_i": opf.m_i}
         st = cp.IpmState(opf, kkt=kkt, gamma=gam, precision=prec)
         torch.cuda.synchronize()
         t_init = time.perf_counter() - t0
@@ -762,7 +793,8 @@ def ipm_measure(include_oracle=True):
                "ipm_solves_per_s": 1.0 / t_solve,
                "factorizations": int(sum(h.n_factor for h in hist)),
                "cg_iters": int(sum(h.cg_iters for h in hist)),
-               "fp32_iters": int(sum(1 for h in hist if h.precision == 32)), "gamma": gam}
+               "fp32_iters": int(sum(1 for h in hist if h.precision == 32)), "gamma": gam,
+               **sizes}
         if include_oracle and name == "planar1k" and prec == 64:
             from oracle.opf import OPFModel
             from oracle import ipm as oipm

@@ -328,8 +328,8 @@ void ipm_state_destroy(ipm_state_t state);
 typedef struct ipm_batch_s *ipm_batch_t;
 
 /* Creates the batch over count model handles (HOST array of handles that must outlive the batch;
- * the same handle may not appear twice).  opt: kkt must be 0 (LiftedKKT), precision 0 or 64; the
- * remaining fields as in ipm_options.  Runs one ipm_symbolic per distinct pattern, allocates one
+ * the same handle may not appear twice).  opt: kkt 0 (LiftedKKT) or 2 (dual-regularized form,
+ * gamma > 0), precision 0 or 64; the remaining fields as in ipm_options.  Runs one ipm_symbolic per distinct pattern, allocates one
  * device pool for every instance's iterate, factor and workspace, and sets every instance to the
  * starting point of ipm_state_create.  Synchronizes.  IPM_ERR_BAD_ARG on a bad argument,
  * IPM_ERR_OOM when the pool does not fit. */
@@ -378,7 +378,7 @@ void ipm_batch_destroy(ipm_batch_t batch);
  * log zu (n), 0 where a bound is absent (width 3 n + 2 m_i; the iterate of the scaled problem as
  * the batched IPM holds it).  ipm_batch_state_rows writes every instance's row into the DEVICE
  * float matrix out (row stride ld >= width; out NULL only reports *width); all instances must
- * have the same sizes.  Stream-ordered. */
+ * have the same sizes; LiftedKKT batches only (IPM_ERR_BAD_ARG otherwise).  Stream-ordered. */
 int ipm_batch_state_rows(ipm_batch_t batch, float *out, int64_t ld, int *width);
 /* Starts every instance from a predicted row (DEVICE float matrix pred, row stride ld, values
  * de-normalized as pred * stdv + mean per column when mean != NULL, else taken as they are):

@@ -383,10 +383,12 @@ class Batch:
     """Batched LiftedKKT interior-point solves over ``Opf`` handles (ipm_batch_*): one symbolic
     analysis per distinct pattern, every instance advanced by the same launches."""
 
-    def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, stream=None):
+    def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, kkt="lifted", gamma=1e6,
+                 stream=None):
         self.opfs = list(opfs)
         arr = (ctypes.c_void_p * len(self.opfs))(*[o.h.value for o in self.opfs])
-        o = IpmOptions(0, tol, 0.0, tau, mu0, 1e-10, max_refine, 0, 64)
+        o = IpmOptions({"lifted": 0, "regularized": 2}[kkt], tol, gamma, tau, mu0, 1e-10,
+                       max_refine, 0, 64)
         h = ctypes.c_void_p()
         _check(lib().ipm_batch_create(len(self.opfs), arr, ctypes.byref(o), _stream(stream),
                                       ctypes.byref(h)), "ipm_batch_create")

@@ -979,7 +979,7 @@ __global__ void k_b_accept(const BI *bi, const BCtl *ctl) {
   A.dw = ctl[b].dw;
   const int nmax = max(I.D.n, max(I.D.me, I.D.mi));
   for (int i = gtid; i < nmax; i += gstride)
-    accept_at(A, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.dx, i);
+    accept_at(A, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.dzc, i);  // dy: dz over the G rows
 }
 __global__ void k_b_ctl_acc(const BI *bi, BCtl *ctl, int count, int fmax_entries) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1364,8 +1364,10 @@ int init_instances(ipm_batch_t B) {
 
 extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_options *opt,
                                 cudaStream_t stream, ipm_batch_t *out) {
-  if (count <= 0 || !opfs || !opt || !out || opt->kkt != 0 || !(opt->tol > 0)) {
-    set_error_msg("ipm_batch_create: bad argument (count > 0, kkt = 0 (LiftedKKT), tol > 0)");
+  if (count <= 0 || !opfs || !opt || !out || (opt->kkt != 0 && opt->kkt != 2) ||
+      !(opt->tol > 0) || (opt->kkt == 2 && !(opt->gamma > 0))) {
+    set_error_msg("ipm_batch_create: bad argument (count > 0, kkt = 0 (LiftedKKT) or 2 "
+                  "(dual-regularized, gamma > 0), tol > 0)");
     return IPM_ERR_BAD_ARG;
   }
   if (opt->precision != 0 && opt->precision != 64) {
@@ -1431,18 +1433,20 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   for (int i = 0; i < count; ++i) {
     const OpfData &M = opfs[i]->M;
     ipm_sym_t S = B->syms[B->pat[i]];
-    const size_t n = M.n, me0 = M.me, mi0 = M.mi, m = me0 + mi0, mi = 2 * me0 + mi0;
+    const bool lifted = B->opt.kkt == 0;
+    const size_t n = M.n, me0 = M.me, mi0 = M.mi, m = me0 + mi0;
+    const size_t mi = lifted ? 2 * me0 + mi0 : mi0, me = lifted ? 0 : me0;
     Off &o = off[i];
-    o.x = dp.take(n); o.s = dp.take(mi); o.y = dp.take(1); o.z = dp.take(mi); o.v = dp.take(mi);
+    o.x = dp.take(n); o.s = dp.take(mi); o.y = dp.take(me); o.z = dp.take(mi); o.v = dp.take(mi);
     o.zl = dp.take(n); o.zu = dp.take(n); o.grad = dp.take(n); o.jtl = dp.take(n);
-    o.geq = dp.take(1); o.hin = dp.take(mi); o.dscale = dp.take(m); o.gs = dp.take(me0);
+    o.geq = dp.take(me); o.hin = dp.take(mi); o.dscale = dp.take(m); o.gs = dp.take(me0);
     o.hs = dp.take(mi0); o.Jv = dp.take(M.nnzJ); o.Wv = dp.take(M.nnzW); o.lam = dp.take(m);
     o.lamw = dp.take(m); o.f = dp.take(2); o.fpart = dp.take(B->gx_gen);
     o.sigma = dp.take(n); o.r1 = dp.take(n); o.r2 = dp.take(mi); o.r4 = dp.take(mi);
     o.Ds = dp.take(mi); o.dcond = dp.take(m); o.baug = dp.take(m); o.a = dp.take(n);
     o.dx = dp.take(n); o.dzc = dp.take(m); o.jdx = dp.take(m); o.dz = dp.take(mi);
     o.ds = dp.take(mi); o.dv = dp.take(mi); o.dzl = dp.take(n); o.dzu = dp.take(n);
-    o.xt = dp.take(n); o.st = dp.take(mi); o.geqt = dp.take(1); o.hint = dp.take(mi);
+    o.xt = dp.take(n); o.st = dp.take(mi); o.geqt = dp.take(me); o.hint = dp.take(mi);
     o.gst = dp.take(me0); o.hst = dp.take(mi0); o.ft = dp.take(2); o.R = dp.take(R_COUNT);
     o.filter = dp.take(2 * (size_t)B->fmax_entries); o.tJ = dp.take(M.nnzJ);
     o.Lx = dp.take(S->panel_len); o.Dx = dp.take(S->diag_len); o.y_s = dp.take(n);
@@ -1546,14 +1550,17 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     double *d = B->dpool;
     BI &I = hbi[i];
     memset(&I, 0, sizeof(I));
-    I.D = Dims{M.n, M.me, M.mi, 0, 2 * M.me + M.mi, 1};
+    // LiftedKKT: equalities relaxed into slack rows; form 2: equalities kept (y), delta_c = 1/gamma
+    I.D = B->opt.kkt == 0 ? Dims{M.n, M.me, M.mi, 0, 2 * M.me + M.mi, 1}
+                          : Dims{M.n, M.me, M.mi, M.me, M.mi, 0};
     I.P.x = d + o.x; I.P.s = d + o.s; I.P.y = d + o.y; I.P.z = d + o.z; I.P.v = d + o.v;
     I.P.zl = d + o.zl; I.P.zu = d + o.zu; I.P.xl = M.xl; I.P.xu = M.xu;
     I.P.grad = d + o.grad; I.P.jtl = d + o.jtl; I.P.geq = d + o.geq; I.P.hin = d + o.hin;
     I.SA.D = I.D;
     I.SA.P = I.P;
     I.SA.r2 = d + o.r2; I.SA.r4 = d + o.r4; I.SA.Ds = d + o.Ds; I.SA.jdx = d + o.jdx;
-    I.SA.dx = d + o.dx; I.SA.sigma = d + o.sigma; I.SA.dzH = nullptr;
+    I.SA.dx = d + o.dx; I.SA.sigma = d + o.sigma;
+    I.SA.dzH = B->opt.kkt == 0 ? nullptr : d + o.dzc + M.me;  // form 2: dz over the H rows
     I.SA.dz = d + o.dz; I.SA.ds = d + o.ds; I.SA.dv = d + o.dv; I.SA.dzl = d + o.dzl;
     I.SA.dzu = d + o.dzu;
     I.M = M;
@@ -1827,6 +1834,10 @@ extern "C" int ipm_batch_export_all(ipm_batch_t B, double *x_host) {
 
 extern "C" int ipm_batch_state_rows(ipm_batch_t B, float *out, int64_t ld, int *width) {
   if (!B) return IPM_ERR_BAD_ARG;
+  if (B->opt.kkt != 0) {
+    set_error_msg("ipm_batch_state_rows: learned warm starts are for LiftedKKT batches");
+    return IPM_ERR_BAD_ARG;
+  }
   std::vector<BI> h(B->count);
   CK(cudaMemcpy(h.data(), B->d_bi, sizeof(BI) * B->count, cudaMemcpyDeviceToHost));
   const int w = 3 * h[0].D.n + 2 * h[0].D.mi;

@@ -112,3 +112,17 @@ def test_batch_argument_errors():
     B = cp.Batch([o, cp.Opf(config_grid("planar1k"))])
     w = ctypes.c_int()
     assert cp.lib().ipm_batch_state_rows(B.h, None, 0, ctypes.byref(w)) == cp.IPM_ERR_BAD_ARG
+
+
+def test_batch_dual_regularized_form_matches_oracle():
+    """Form 2 (delta_c = 1/gamma) batched: equality rows kept with their multipliers y."""
+    base = config_grid("planar1k")
+    grids = [scale_loads(base, 1000 + k) for k in range(3)] + [config_grid("ring30")]
+    B = cp.Batch([cp.Opf(g) for g in grids], kkt="regularized", gamma=1e6)
+    B.run(max_iter=300)
+    r = B.results()
+    for i, g in enumerate(grids):
+        ref = oipm.solve(OPFModel(g), oipm.Options(kkt="regularized", gamma=1e6))
+        assert r["status"][i] == 1, (i, r["status"][i])
+        assert abs(r["obj"][i] - ref.obj) <= 1e-6 * abs(ref.obj), i
+        assert abs(r["iters"][i] - ref.iters) <= max(3, ref.iters // 5), (r["iters"][i], ref.iters)
