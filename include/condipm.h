@@ -317,7 +317,8 @@ int ipm_state_export(ipm_state_t state, double *x, double *obj);
 void ipm_state_destroy(ipm_state_t state);
 
 /* ---------------------------------------------------------------- batched interior-point solves
- * Many OPF instances advanced together (LiftedKKT, FP64): the batched form of the method.
+ * Many OPF instances advanced together (LiftedKKT, HyKKT or the dual-regularized form; FP64): the
+ * batched form of the method.
  * Instances whose model patterns (J and lower W) are equal share one symbolic analysis (the
  * paper reuses the analysis of a pattern across iterations, Section 5); instances may have
  * different sizes.  Each launch of the condensation, the sync-free factorization and the
@@ -328,8 +329,10 @@ void ipm_state_destroy(ipm_state_t state);
 typedef struct ipm_batch_s *ipm_batch_t;
 
 /* Creates the batch over count model handles (HOST array of handles that must outlive the batch;
- * the same handle may not appear twice).  opt: kkt 0 (LiftedKKT) or 2 (dual-regularized form,
- * gamma > 0), precision 0 or 64; the remaining fields as in ipm_options.  Runs one ipm_symbolic per distinct pattern, allocates one
+ * the same handle may not appear twice).  opt: kkt 0 (LiftedKKT), 1 (HyKKT: CG on the Schur
+ * complement of K_gamma, cg_rtol and cg_maxit as in ipm_options, gamma > 0) or 2 (dual-regularized
+ * form, gamma > 0), precision 0 or 64; the remaining fields as in ipm_options.  Runs one
+ * ipm_symbolic per distinct pattern, allocates one
  * device pool for every instance's iterate, factor and workspace, and sets every instance to the
  * starting point of ipm_state_create.  Synchronizes.  IPM_ERR_BAD_ARG on a bad argument,
  * IPM_ERR_OOM when the pool does not fit. */
@@ -352,6 +355,9 @@ int ipm_batch_run(ipm_batch_t batch, int max_iter, int max_sweeps, int use_graph
  * steps.  Synchronizes. */
 int ipm_batch_results(ipm_batch_t batch, int *status, int *iters, double *obj, double *kkt_err,
                       int *n_factor, int *ls_steps);
+/* HyKKT batches: CG iterations per instance since creation or the last reset into a HOST array
+ * [count] (0 for the other forms).  Synchronizes. */
+int ipm_batch_cg_iters(ipm_batch_t batch, int *cg_iters);
 /* Copies instance i's x [n] into a HOST buffer.  Synchronizes. */
 int ipm_batch_export(ipm_batch_t batch, int i, double *x);
 /* Sweeps run since creation or the last reset. */

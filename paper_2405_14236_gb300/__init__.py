@@ -60,6 +60,7 @@ _SIGS = {
     "ipm_batch_reset": (I, [P]),
     "ipm_batch_run": (I, [P, I, I, I]),
     "ipm_batch_results": (I, [P, P, P, P, P, P, P]),
+    "ipm_batch_cg_iters": (I, [P, P]),
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
     "ipm_batch_destroy": (None, [P]),
@@ -380,15 +381,16 @@ def ipm_solve_opf(opf, max_iter=3000, **opts):
 
 
 class Batch:
-    """Batched LiftedKKT interior-point solves over ``Opf`` handles (ipm_batch_*): one symbolic
-    analysis per distinct pattern, every instance advanced by the same launches."""
+    """Batched interior-point solves over ``Opf`` handles (ipm_batch_*): one symbolic analysis
+    per distinct pattern, every instance advanced by the same launches.  kkt: "lifted",
+    "hykkt" (CG on the Schur complement of K_gamma) or "regularized"."""
 
     def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, kkt="lifted", gamma=1e6,
-                 stream=None):
+                 cg_rtol=1e-10, cg_maxit=0, stream=None):
         self.opfs = list(opfs)
         arr = (ctypes.c_void_p * len(self.opfs))(*[o.h.value for o in self.opfs])
-        o = IpmOptions({"lifted": 0, "regularized": 2}[kkt], tol, gamma, tau, mu0, 1e-10,
-                       max_refine, 0, 64)
+        o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
+                       cg_rtol, max_refine, cg_maxit, 64)
         h = ctypes.c_void_p()
         _check(lib().ipm_batch_create(len(self.opfs), arr, ctypes.byref(o), _stream(stream),
                                       ctypes.byref(h)), "ipm_batch_create")
@@ -416,8 +418,10 @@ class Batch:
         p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(lib().ipm_batch_results(self.h, p(st), p(it), p(obj), p(err), p(nf), p(ls)),
                "ipm_batch_results")
+        cg = np.zeros(n, np.int32)
+        _check(lib().ipm_batch_cg_iters(self.h, p(cg)), "ipm_batch_cg_iters")
         return dict(status=st, iters=it, obj=obj, kkt_err=err, n_factor=nf, ls_steps=ls,
-                    sweeps=lib().ipm_batch_sweeps(self.h))
+                    cg_iters=cg, sweeps=lib().ipm_batch_sweeps(self.h))
 
     def x_all(self, out=None):
         """Every instance's x, concatenated (one gather and one copy); out: float64 numpy array."""

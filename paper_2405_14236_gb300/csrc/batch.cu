@@ -32,9 +32,13 @@
 
 namespace cipm {
 
-enum Phase { PH_EVAL = 0, PH_BUILD, PH_FACT, PH_SOLVE, PH_REFINE, PH_STEP, PH_LS, PH_ACC, PH_DONE };
+// PH_CGI, PH_CG, PH_CGX: HyKKT's Schur-complement CG (start, iterations, primal back-solve)
+enum Phase {
+  PH_EVAL = 0, PH_BUILD, PH_FACT, PH_SOLVE, PH_REFINE, PH_STEP, PH_LS, PH_ACC, PH_DONE,
+  PH_CGI, PH_CG, PH_CGX
+};
 
-static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2;
+static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2, B_CG_ROUNDS = 6;
 static constexpr int B_BLOCK = 256;
 
 // per-instance control record (device)
@@ -44,6 +48,9 @@ struct BCtl {
   double mu, tau, sig, delta_last, theta_max, theta_min;
   double dw, next, grow;
   double alpha, az, amax, amin, gphi, theta, phi, logsum, obj, e0, eta, eta_prev, normA;
+  // HyKKT CG: r.r, stopping threshold, step scalars, iterations (this IPM step, in total)
+  double cg_rr, cg_stop, cg_alpha, cg_beta;
+  int cg_it, cg_total, cg_maxit, pad_;
 };
 
 // per-instance descriptor (device): pattern and model pointers, iterate and work vectors
@@ -69,6 +76,8 @@ struct BI {
   double *tJ, *Lx, *Dx;
   int *info;
   double *y, *t, *cx, *cz, *outx, *outz, *scal;
+  double *cg_r, *cg_p, *cg_sp, *cg_dy, *cg_rhs1, *cg_v;  // HyKKT CG vectors
+  const double *dystep;  // dy of the step: cg_dy (HyKKT), dz over the G rows (form 2)
   AugArgs aug;
 };
 
@@ -87,7 +96,9 @@ __global__ void k_b_rreset(const BI *bi, const BCtl *ctl, int phase, int k0, int
   for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) bi[b].R[k] = v;
 }
 
-__global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0) {
+// cg_maxit: HyKKT CG iteration limit (<= 0: m_e of the instance); 0 in the record = no CG
+__global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0, int hykkt,
+                             int cg_maxit) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count) return;
   BCtl c;
@@ -97,6 +108,7 @@ __global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0) {
   c.tau = fmax(TAU_MIN, 1.0 - mu0);
   c.sig = 1.0;
   c.eta = c.eta_prev = INFINITY;
+  if (hykkt) c.cg_maxit = cg_maxit > 0 ? cg_maxit : max(bi[b].D.me0, 1);
   ctl[b] = c;
   for (int k = 0; k < R_COUNT; ++k) bi[b].R[k] = 0.0;
 }
@@ -715,8 +727,161 @@ __global__ void __launch_bounds__(B_NT)
     for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_bwd_sn(I, I.level_sn[q], ys);
     cluster.sync();
   }
-  double *x = phase == PH_SOLVE ? I.dx : I.cx;
+  double *x = phase == PH_SOLVE || phase == PH_CGI || phase == PH_CGX ? I.dx
+              : phase == PH_CG ? I.cg_v : I.cx;
   for (int k = gt; k < I.D.n; k += gnt) x[I.perm[k]] = I.y[k];
+}
+
+// ------------------------------------------------------------------ HyKKT CG (Eq. (10))
+// CGI: t = a + J^T (d o b) = r1 + gamma G^T r2 (kept as rhs1), w = K_gamma^{-1} t (into dx);
+// then r = G w - b_G, p = r, dy = 0, r.r.  CG: t = G^T p, v = K_gamma^{-1} t, Sp = G v,
+// alpha = r.r / p.Sp, dy += alpha p, r -= alpha Sp, beta = r.r_new / r.r, p = r + beta p.
+// CGX: t = rhs1 - G^T dy, dx = K_gamma^{-1} t, dz_H = d_H o (H dx - b_H).
+__global__ void k_b_cgi_rhs(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CGI);
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    double acc = 0.0;
+    for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+      const int p = I.JT_ent[t];
+      const int r = I.J_rowidx[p];
+      double v = I.Jv[p] * I.baug[r];
+      v *= I.dcond[r];
+      acc += v;
+    }
+    const double v = I.a[j] + acc;
+    I.t[j] = v;
+    I.cg_rhs1[j] = v;
+  }
+}
+__device__ __forceinline__ double g_row_dot(const BI &I, int r, const double *x) {
+  double acc = 0.0;
+  for (int p = I.M.J_rowptr[r]; p < I.M.J_rowptr[r + 1]; ++p) acc += I.Jv[p] * x[I.M.J_colind[p]];
+  return acc;
+}
+__global__ void k_b_cgi_start(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CGI);
+  double rr = 0.0;
+  for (int r = gtid; r < I.D.me0; r += gstride) {
+    const double v = g_row_dot(I, r, I.dx) - I.baug[r];
+    I.cg_r[r] = v;
+    I.cg_p[r] = v;
+    I.cg_dy[r] = 0.0;
+    rr += v * v;
+  }
+  const int slot[1] = {R_CG_A};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {rr};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+__global__ void k_b_ctl_cgi(const BI *bi, BCtl *ctl, int count, double rtol) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_CGI) return;
+  BCtl &c = ctl[b];
+  c.cg_rr = bi[b].R[R_CG_A];
+  bi[b].R[R_CG_B] = 0.0;
+  const double r0 = sqrt(c.cg_rr);
+  c.cg_stop = fmax(rtol * r0, 1e-14);
+  c.cg_it = 0;
+  c.ph = r0 > c.cg_stop ? PH_CG : PH_CGX;
+}
+// t = G^T p (G = the first me0 rows of J)
+__global__ void k_b_cg_u(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CG);
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    double acc = 0.0;
+    for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+      const int p = I.JT_ent[t];
+      const int r = I.J_rowidx[p];
+      if (r < I.D.me0) acc += I.Jv[p] * I.cg_p[r];
+    }
+    I.t[j] = acc;
+  }
+}
+__global__ void k_b_cg_sp(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CG);
+  double psp = 0.0;
+  for (int r = gtid; r < I.D.me0; r += gstride) {
+    const double v = g_row_dot(I, r, I.cg_v);
+    I.cg_sp[r] = v;
+    psp += I.cg_p[r] * v;
+  }
+  const int slot[1] = {R_CG_B};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {psp};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+__global__ void k_b_ctl_cg_alpha(const BI *bi, BCtl *ctl, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_CG) return;
+  BCtl &c = ctl[b];
+  const double alpha = c.cg_rr / bi[b].R[R_CG_B];
+  bi[b].R[R_CG_A] = 0.0;
+  if (!isfinite(alpha)) {  // p.S p = 0: breakdown, as a non-finite step in hykkt_cg
+    c.status = IPM_ERR_NONFINITE;
+    c.ph = PH_DONE;
+    return;
+  }
+  c.cg_alpha = alpha;
+}
+__global__ void k_b_cg_xr(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CG);
+  const double al = ctl[b].cg_alpha;
+  double rr = 0.0;
+  for (int r = gtid; r < I.D.me0; r += gstride) {
+    I.cg_dy[r] += al * I.cg_p[r];
+    const double v = I.cg_r[r] - al * I.cg_sp[r];
+    I.cg_r[r] = v;
+    rr += v * v;
+  }
+  const int slot[1] = {R_CG_A};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {rr};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+__global__ void k_b_ctl_cg_beta(const BI *bi, BCtl *ctl, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_CG) return;
+  BCtl &c = ctl[b];
+  const double rr = bi[b].R[R_CG_A];
+  bi[b].R[R_CG_B] = 0.0;
+  c.cg_beta = rr / c.cg_rr;
+  c.cg_rr = rr;
+  ++c.cg_it;
+  ++c.cg_total;
+  if (!isfinite(rr)) {
+    c.status = IPM_ERR_NONFINITE;
+    c.ph = PH_DONE;
+  } else if (sqrt(rr) <= c.cg_stop || c.cg_it >= c.cg_maxit) {
+    c.ph = PH_CGX;  // at the iteration limit the step goes on inexact, as in hykkt_cg
+  }
+}
+__global__ void k_b_cg_p(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CG);
+  const double be = ctl[b].cg_beta;
+  for (int r = gtid; r < I.D.me0; r += gstride) I.cg_p[r] = I.cg_r[r] + be * I.cg_p[r];
+}
+__global__ void k_b_cgx_rhs(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CGX);
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    double acc = 0.0;
+    for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+      const int p = I.JT_ent[t];
+      const int r = I.J_rowidx[p];
+      if (r < I.D.me0) acc += I.Jv[p] * I.cg_dy[r];
+    }
+    I.t[j] = I.cg_rhs1[j] - acc;
+  }
+}
+// dz over the H rows (into dzc after the G rows, as the recovery of form 2 reads it)
+__global__ void k_b_cgx_dz(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_CGX);
+  for (int r = I.D.me0 + gtid; r < I.m; r += gstride)
+    I.dzc[r] = I.dcond[r] * (g_row_dot(I, r, I.dx) - I.baug[r]);
+}
+__global__ void k_b_ctl_cgx(BCtl *ctl, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_CGX) return;
+  ctl[b].ph = PH_STEP;
 }
 
 // factor outcome: success -> solve; wrong inertia -> next delta_w
@@ -729,7 +894,12 @@ __global__ void k_b_ctl_fact(const BI *bi, BCtl *ctl, int count) {
   ++c.total_fac;
   if (*I.info == INT_MAX) {
     if (c.dw > 0) c.delta_last = c.dw;
-    c.ph = PH_SOLVE;
+    if (c.cg_maxit > 0) {  // HyKKT
+      I.R[R_CG_A] = 0.0;
+      c.ph = PH_CGI;
+    } else {
+      c.ph = PH_SOLVE;
+    }
     return;
   }
   c.dw = c.next;
@@ -979,7 +1149,7 @@ __global__ void k_b_accept(const BI *bi, const BCtl *ctl) {
   A.dw = ctl[b].dw;
   const int nmax = max(I.D.n, max(I.D.me, I.D.mi));
   for (int i = gtid; i < nmax; i += gstride)
-    accept_at(A, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.dzc, i);  // dy: dz over the G rows
+    accept_at(A, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.dystep, i);
 }
 __global__ void k_b_ctl_acc(const BI *bi, BCtl *ctl, int count, int fmax_entries) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1285,18 +1455,48 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(3);
   }
-  // condensed solve, then Richardson refinement on the augmented system
-  CKR(solve(PH_SOLVE));
-  k_b_ctl_solved<<<gc, 128, 0, s>>>(bi, ctl, C);
-  L(1);
-  for (int r = 0; r < B_REFINE_ROUNDS; ++r) {
-    k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl);
-    k_b_resid<<<g2, blk, 0, s>>>(bi, ctl);
-    k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine);
-    L(3);
-    CKR(solve(PH_REFINE));
-    k_b_axpy<<<g2, blk, 0, s>>>(bi, ctl);
+  if (B->opt.kkt == 1) {
+    // HyKKT: CG on the Schur complement of K_gamma (Eq. (10)), one K_gamma solve per iteration;
+    // an instance whose CG needs more than B_CG_ROUNDS iterations goes on in the next sweep
+    k_b_cgi_rhs<<<g2, blk, 0, s>>>(bi, ctl);
     L(1);
+    CKR(rec(2));
+    CKR(split(k_b_solve_inst, (size_t)0, (int)PH_CGI));
+    CKR(rec(3));
+    k_b_cgi_start<<<g2, blk, 0, s>>>(bi, ctl);
+    k_b_ctl_cgi<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.cg_rtol);
+    L(2);
+    for (int r = 0; r < B_CG_ROUNDS; ++r) {
+      k_b_cg_u<<<g2, blk, 0, s>>>(bi, ctl);
+      L(1);
+      CKR(split(k_b_solve_inst, (size_t)0, (int)PH_CG));
+      k_b_cg_sp<<<g2, blk, 0, s>>>(bi, ctl);
+      k_b_ctl_cg_alpha<<<gc, 128, 0, s>>>(bi, ctl, C);
+      k_b_cg_xr<<<g2, blk, 0, s>>>(bi, ctl);
+      k_b_ctl_cg_beta<<<gc, 128, 0, s>>>(bi, ctl, C);
+      k_b_cg_p<<<g2, blk, 0, s>>>(bi, ctl);
+      L(5);
+    }
+    k_b_cgx_rhs<<<g2, blk, 0, s>>>(bi, ctl);
+    L(1);
+    CKR(split(k_b_solve_inst, (size_t)0, (int)PH_CGX));
+    k_b_cgx_dz<<<g2, blk, 0, s>>>(bi, ctl);
+    k_b_ctl_cgx<<<gc, 128, 0, s>>>(ctl, C);
+    L(2);
+  } else {
+    // condensed solve, then Richardson refinement on the augmented system
+    CKR(solve(PH_SOLVE));
+    k_b_ctl_solved<<<gc, 128, 0, s>>>(bi, ctl, C);
+    L(1);
+    for (int r = 0; r < B_REFINE_ROUNDS; ++r) {
+      k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl);
+      k_b_resid<<<g2, blk, 0, s>>>(bi, ctl);
+      k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine);
+      L(3);
+      CKR(solve(PH_REFINE));
+      k_b_axpy<<<g2, blk, 0, s>>>(bi, ctl);
+      L(1);
+    }
   }
   // step recovery, fraction to the boundary, line-search set-up
   k_b_jv<<<g2, blk, 0, s>>>(bi, ctl);
@@ -1339,7 +1539,8 @@ int init_instances(ipm_batch_t B) {
   BI *bi = B->d_bi;
   BCtl *ctl = B->d_ctl;
   const double mu0 = B->opt.mu0;
-  k_b_ctl_init<<<grid_for(C, 128), 128, 0, s>>>(bi, ctl, C, mu0);
+  k_b_ctl_init<<<grid_for(C, 128), 128, 0, s>>>(bi, ctl, C, mu0, B->opt.kkt == 1,
+                                                B->opt.cg_maxit);
   k_b_setup_sums<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_x0<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_flow_start<<<g2, blk, 0, s>>>(bi, ctl);
@@ -1364,10 +1565,10 @@ int init_instances(ipm_batch_t B) {
 
 extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_options *opt,
                                 cudaStream_t stream, ipm_batch_t *out) {
-  if (count <= 0 || !opfs || !opt || !out || (opt->kkt != 0 && opt->kkt != 2) ||
-      !(opt->tol > 0) || (opt->kkt == 2 && !(opt->gamma > 0))) {
-    set_error_msg("ipm_batch_create: bad argument (count > 0, kkt = 0 (LiftedKKT) or 2 "
-                  "(dual-regularized, gamma > 0), tol > 0)");
+  if (count <= 0 || !opfs || !opt || !out || opt->kkt < 0 || opt->kkt > 2 ||
+      !(opt->tol > 0) || (opt->kkt != 0 && !(opt->gamma > 0))) {
+    set_error_msg("ipm_batch_create: bad argument (count > 0, kkt = 0 (LiftedKKT), 1 (HyKKT, "
+                  "gamma > 0) or 2 (dual-regularized, gamma > 0), tol > 0)");
     return IPM_ERR_BAD_ARG;
   }
   if (opt->precision != 0 && opt->precision != 64) {
@@ -1391,6 +1592,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   if (!(B->opt.tau > 0)) B->opt.tau = B->opt.tol;
   if (!(B->opt.mu0 > 0)) B->opt.mu0 = 0.1;
   if (B->opt.max_refine < 0) B->opt.max_refine = 10;
+  if (!(B->opt.cg_rtol > 0)) B->opt.cg_rtol = 1e-10;
   B->stream = stream;
   B->opf.assign(opfs, opfs + count);
   // ---- one symbolic analysis per distinct pattern
@@ -1422,6 +1624,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     size_t sigma, r1, r2, r4, Ds, dcond, baug, a, dx, dzc, jdx, dz, ds, dv, dzl, dzu;
     size_t xt, st, geqt, hint, gst, hst, ft, R, filter, tJ, Lx, Dx, y_s, t, cx, cz, outx, outz,
         scal;
+    size_t cg_r, cg_p, cg_sp, cg_dy, cg_rhs1, cg_v;
     size_t info;
   };
   std::vector<Off> off(count);
@@ -1452,6 +1655,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     o.Lx = dp.take(S->panel_len); o.Dx = dp.take(S->diag_len); o.y_s = dp.take(n);
     o.t = dp.take(n); o.cx = dp.take(n); o.cz = dp.take(m); o.outx = dp.take(n);
     o.outz = dp.take(m); o.scal = dp.take(8);
+    const size_t ncg = B->opt.kkt == 1 ? n : 0, mcg = B->opt.kkt == 1 ? me0 : 0;
+    o.cg_r = dp.take(mcg); o.cg_p = dp.take(mcg); o.cg_sp = dp.take(mcg); o.cg_dy = dp.take(mcg);
+    o.cg_rhs1 = dp.take(ncg); o.cg_v = dp.take(ncg);
     o.info = ip.take(1);
     max_elems = std::max({max_elems, M.n, (int)mi, (int)m, M.nnzJ, M.nnzW, 2 * M.nbr});
     B->max_ns = std::max(B->max_ns, S->nsuper);
@@ -1550,7 +1756,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     double *d = B->dpool;
     BI &I = hbi[i];
     memset(&I, 0, sizeof(I));
-    // LiftedKKT: equalities relaxed into slack rows; form 2: equalities kept (y), delta_c = 1/gamma
+    // LiftedKKT: equalities relaxed into slack rows; HyKKT and form 2 (delta_c = 1/gamma): equalities
+    // kept (y)
     I.D = B->opt.kkt == 0 ? Dims{M.n, M.me, M.mi, 0, 2 * M.me + M.mi, 1}
                           : Dims{M.n, M.me, M.mi, M.me, M.mi, 0};
     I.P.x = d + o.x; I.P.s = d + o.s; I.P.y = d + o.y; I.P.z = d + o.z; I.P.v = d + o.v;
@@ -1560,7 +1767,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.SA.P = I.P;
     I.SA.r2 = d + o.r2; I.SA.r4 = d + o.r4; I.SA.Ds = d + o.Ds; I.SA.jdx = d + o.jdx;
     I.SA.dx = d + o.dx; I.SA.sigma = d + o.sigma;
-    I.SA.dzH = B->opt.kkt == 0 ? nullptr : d + o.dzc + M.me;  // form 2: dz over the H rows
+    I.SA.dzH = B->opt.kkt == 0 ? nullptr : d + o.dzc + M.me;  // dz over the H rows
     I.SA.dz = d + o.dz; I.SA.ds = d + o.ds; I.SA.dv = d + o.dv; I.SA.dzl = d + o.dzl;
     I.SA.dzu = d + o.dzu;
     I.M = M;
@@ -1583,6 +1790,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.pair_tgt = ptgt[B->pat[i]];
     I.y = d + o.y_s; I.t = d + o.t; I.cx = d + o.cx; I.cz = d + o.cz; I.outx = d + o.outx;
     I.outz = d + o.outz; I.scal = d + o.scal;
+    I.cg_r = d + o.cg_r; I.cg_p = d + o.cg_p; I.cg_sp = d + o.cg_sp; I.cg_dy = d + o.cg_dy;
+    I.cg_rhs1 = d + o.cg_rhs1; I.cg_v = d + o.cg_v;
+    I.dystep = B->opt.kkt == 1 ? I.cg_dy : I.dzc;
     AugArgs &A = I.aug;
     A.n = M.n; A.m = I.m; A.m_e = 0;
     A.J_rowptr = S->J_rowptr; A.J_colind = S->J_colind; A.J_rowidx = S->J_rowidx;
@@ -1732,6 +1942,14 @@ extern "C" int ipm_batch_results(ipm_batch_t B, int *status, int *iters, double 
     if (n_factor) n_factor[i] = h[i].total_fac;
     if (ls_steps) ls_steps[i] = h[i].total_ls;
   }
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_cg_iters(ipm_batch_t B, int *cg_iters) {
+  if (!B || !cg_iters) return IPM_ERR_BAD_ARG;
+  std::vector<BCtl> h(B->count);
+  CK(cudaMemcpy(h.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < B->count; ++i) cg_iters[i] = h[i].cg_total;
   return IPM_OK;
 }
 

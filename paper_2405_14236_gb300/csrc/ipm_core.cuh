@@ -28,6 +28,7 @@ enum {
   // mu, max_i |c_i - mu| = max(cmax - mu, mu - cmin) exactly (rounding is monotone), so the
   // barrier test can try several mu without another pass over the vectors.
   R_SV_MIN, R_SV_MAX, R_CL_MIN, R_CL_MAX, R_CU_MIN, R_CU_MAX,
+  R_CG_A, R_CG_B,  // batched HyKKT CG: r.r and p.S p
   R_COUNT
 };
 

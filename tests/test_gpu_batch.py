@@ -102,8 +102,9 @@ def test_batch_argument_errors():
     o = cp.Opf(g)
     arr = (ctypes.c_void_p * 1)(o.h.value)
     h = ctypes.c_void_p()
-    for kkt, prec in ((1, 64), (0, 32)):  # HyKKT and FP32 are not batched
-        opt = cp.IpmOptions(kkt, 1e-6, 1e6, 0.0, 0.1, 1e-10, 10, 0, prec)
+    # FP32 is not batched; HyKKT and form 2 need gamma > 0; kkt outside 0..2
+    for kkt, gam, prec in ((0, 1e6, 32), (1, 0.0, 64), (2, -1.0, 64), (3, 1e6, 64)):
+        opt = cp.IpmOptions(kkt, 1e-6, gam, 0.0, 0.1, 1e-10, 10, 0, prec)
         rc = cp.lib().ipm_batch_create(1, arr, ctypes.byref(opt), None, ctypes.byref(h))
         assert rc == cp.IPM_ERR_BAD_ARG
     opt = cp.IpmOptions(0, 1e-6, 1e6, 0.0, 0.1, 1e-10, 10, 0, 64)
@@ -126,3 +127,33 @@ def test_batch_dual_regularized_form_matches_oracle():
         assert r["status"][i] == 1, (i, r["status"][i])
         assert abs(r["obj"][i] - ref.obj) <= 1e-6 * abs(ref.obj), i
         assert abs(r["iters"][i] - ref.iters) <= max(3, ref.iters // 5), (r["iters"][i], ref.iters)
+
+
+def test_batch_hykkt_matches_oracle_and_single_problem():
+    """HyKKT batched: CG on the Schur complement of K_gamma (Eq. (10)) inside the sweeps, an
+    instance whose CG runs past one sweep's rounds going on in the next.  Objectives against the
+    oracle's HyKKT solve; iterations and CG iterations against the single-problem path."""
+    base = config_grid("planar1k")
+    grids = [scale_loads(base, 1000 + k) for k in range(3)] + [config_grid("ring30")]
+    B = cp.Batch([cp.Opf(g) for g in grids], kkt="hykkt", gamma=1e6)
+    B.run(max_iter=300)
+    r = B.results()
+    for i, g in enumerate(grids):
+        ref = oipm.solve(OPFModel(g), oipm.Options(kkt="hykkt", gamma=1e6))
+        assert ref.status == "converged"
+        assert r["status"][i] == 1, (i, r["status"][i])
+        assert abs(r["obj"][i] - ref.obj) <= 1e-6 * abs(ref.obj), i
+        assert abs(r["iters"][i] - ref.iters) <= max(3, ref.iters // 5), (r["iters"][i], ref.iters)
+        single = cp.ipm_solve_opf(cp.Opf(g), max_iter=300, kkt="hykkt", gamma=1e6)
+        assert abs(r["iters"][i] - single["iters"]) <= 3
+        cg_single = sum(h["cg_iters"] for h in single["history"])
+        assert r["cg_iters"][i] > 0
+        assert abs(int(r["cg_iters"][i]) - cg_single) <= max(5, cg_single // 5), (r["cg_iters"][i], cg_single)
+    # a CG that needs several sweeps per IPM step reaches the same optimum
+    B2 = cp.Batch([cp.Opf(grids[0])], kkt="hykkt", gamma=1e2)
+    B2.run(max_iter=300)
+    r2 = B2.results()
+    ref2 = oipm.solve(OPFModel(grids[0]), oipm.Options(kkt="hykkt", gamma=1e2))
+    if ref2.status == "converged":
+        assert r2["status"][0] == 1
+        assert abs(r2["obj"][0] - ref2.obj) <= 1e-6 * abs(ref2.obj)
