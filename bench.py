@@ -448,8 +448,9 @@ def aggregate_ranks(t_ms, converged, world, device):
 
 
 def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3):
-    """The headline's instances solved by another batched form (the dual-regularized condensed
-    form: equality rows kept, delta_c = 1/gamma)."""
+    """The headline's instances solved by another batched form: "regularized" (the
+    dual-regularized condensed form: equality rows kept, delta_c = 1/gamma) or "hykkt" (CG on
+    the Schur complement of K_gamma, Section 3.1)."""
     import torch
     import paper_2405_14236_gb300 as cp
     opfs = [cp.Opf(g) for g in grids]
@@ -469,9 +470,12 @@ def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3):
         r = B.results()
         conv.append(int((r["status"] == 1).sum()))
         its.append(float(r["iters"].mean()))
-    return {"kkt": kkt, "gamma": gamma, "value": float(np.sum(conv) / (np.sum(ms) / 1e3)),
-            "unit": UNIT, "converged_per_step": conv, "iters_mean": float(np.mean(its)),
-            "ms_per_step": float(np.mean(ms))}
+    out = {"kkt": kkt, "gamma": gamma, "value": float(np.sum(conv) / (np.sum(ms) / 1e3)),
+           "unit": UNIT, "converged_per_step": conv, "iters_mean": float(np.mean(its)),
+           "ms_per_step": float(np.mean(ms)), "sweeps": int(r["sweeps"])}
+    if kkt == "hykkt":
+        out["cg_iters_per_ipm_iter"] = float(r["cg_iters"].sum() / max(1, r["iters"].sum()))
+    return out
 
 
 def plain_measure(grids):
@@ -638,6 +642,7 @@ def run_gpu(args, rank, world, local_rank):
                                        else grids[ns + i // 2] for i in range(4)])
         line["plain"]["batched_speedup"] = value / line["plain"]["value"]
     line["batch_regularized"] = batch_form_measure(grids)
+    line["batch_hykkt"] = batch_form_measure(grids, kkt="hykkt")
     if not args.no_warm:
         line["warm"] = warm_measure()
         if "plain" in line:

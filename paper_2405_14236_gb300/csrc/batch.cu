@@ -67,9 +67,17 @@ struct BI {
   // numeric
   const int *sptr, *srow_ptr, *slot_ptr, *perm, *J_rowidx, *JT_ptr, *JT_ent;
   const int *srow, *snode, *level_sn, *lvl_ptr;  // lvl_ptr: level offsets into level_sn
-  // update pairs of each supernode (precomputed per pattern): pair_ptr[s].. pair_ptr[s + 1],
-  // rows (i << 16 | j) of the panel, i >= j >= w, and the target value slot in the panels
-  const int *pair_ptr, *pair_ij, *pair_tgt;
+  // update pairs (precomputed per pattern), stored level by level: level L owns entries
+  // lpair_ptr[L] .. lpair_ptr[L + 1]; each pair: its supernode, rows (i << 16 | j) of that
+  // panel (i >= j >= w) and the target value slot in the panels
+  const int *lpair_ptr, *pair_sn, *pair_ij, *pair_tgt;
+  // condensation order (per pattern): the lower panel slots of every supernode sorted by their
+  // number of items (ccol: the column of a diagonal slot, else -1); the items of each group of
+  // 32 slots are interleaved (item k of lane l at cgptr[g] + 32 k + l, padded with y = -2) so
+  // that a warp's item loads are coalesced and its lanes loop over equal counts
+  const int *cslot, *ccol, *cgptr;
+  const int2 *citems;
+  int ncslot;
   const int64_t *lptr, *dptr;
   const int2 *items;
   int ns, nlevels;
@@ -412,18 +420,52 @@ __global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
 static constexpr int B_WS = 16;
 static constexpr int B_NT = 512;  // threads of the per-instance kernels
 
-// Update of supernode s into its ancestors: entry (i, j), i >= j >= w, of L21 L21^T is
-// subtracted from the panel of the supernode owning column rows[j], at row rows[i].  The pairs
-// and their target slots are listed per pattern, so threads take pairs (full lanes, no searches).
-__device__ __forceinline__ void scatter_update(const BI &I, int s, int ld, int w, const double *P,
-                                               int tid, int nthreads) {
-  const int p0 = I.pair_ptr[s], np = I.pair_ptr[s + 1] - p0;
-  for (int t = tid; t < np; t += nthreads) {
-    const int ij = I.pair_ij[p0 + t];
+// Updates of the supernodes of level L into their ancestors, every pair of the level spread over
+// all threads of the cluster: entry (i, j), i >= j >= w, of L21 L21^T of supernode s is
+// subtracted from the panel of the supernode owning column rows[j], at row rows[i].
+__device__ __forceinline__ void level_updates(const BI &I, int L, int tid, int nthreads) {
+  const int p1 = I.lpair_ptr[L + 1];
+  for (int t = I.lpair_ptr[L] + tid; t < p1; t += nthreads) {
+    const int s = I.pair_sn[t];
+    const int w = I.sptr[s + 1] - I.sptr[s], ld = I.srow_ptr[s + 1] - I.srow_ptr[s];
+    const double *P = I.Lx + I.lptr[s];
+    const int ij = I.pair_ij[t];
     const int i = ij >> 16, j = ij & 0xffff;
     double v = 0.0;
-    for (int k = 0; k < w; ++k) v += P[i + (int64_t)k * ld] * P[j + (int64_t)k * ld];
-    atomicAdd(&I.Lx[I.pair_tgt[p0 + t]], -v);
+    int k = 0;
+    for (; k + 4 <= w; k += 4) {  // four independent load pairs in flight
+      double a[4], c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = P[i + (int64_t)(k + u) * ld];
+        c[u] = P[j + (int64_t)(k + u) * ld];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v += a[u] * c[u];
+    }
+    for (; k < w; ++k) v += P[i + (int64_t)k * ld] * P[j + (int64_t)k * ld];
+    atomicAdd(&I.Lx[I.pair_tgt[t]], -v);
+  }
+}
+
+// rows below the diagonal block of a narrow supernode of width W: L21 = A21 L11^{-T}, one row per
+// lane held in registers (one load and one store per entry; the right-looking column loop then
+// runs on registers instead of re-reading the panel)
+template <int W>
+__device__ __forceinline__ void rows_below(double *P, int ld, const double *D, const double *inv,
+                                           int lane) {
+  for (int r = W + lane; r < ld; r += 32) {
+    double x[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) x[k] = P[r + (int64_t)k * ld];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      x[k] *= inv[k];
+#pragma unroll
+      for (int j = k + 1; j < W; ++j) x[j] -= x[k] * D[j + k * W];
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) P[r + (int64_t)k * ld] = x[k];
   }
 }
 
@@ -445,7 +487,7 @@ __device__ void thread_diag_sn(const BI &I, int s) {
   for (int k = 0; k < B_WT; ++k) {
     if (k < w) {
       double d = D[k + k * B_WT];
-      if (!(d > 0.0) || !isfinite(d)) {
+      if (!pivot_ok(d)) {
         atomicMin(I.info, f + k);
         d = 1.0;
       }
@@ -494,7 +536,7 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
   for (int k = 0; k < w; ++k) {
     if (lane == 0) {
       double d = D[k + k * w];
-      if (!(d > 0.0) || !isfinite(d)) {
+      if (!pivot_ok(d)) {
         atomicMin(I.info, f + k);
         d = 1.0;
       }
@@ -517,17 +559,25 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
   for (int k = lane; k < w; k += 32) Dd[w * w + k] = inv[k];
   __syncwarp();
   }
-  // rows below: L21 = A21 L11^{-T}, lane-owned rows, right-looking over the w columns (loops
-  // bounded by w: every FP64 instruction issued does work)
-  for (int r = w + lane; r < ld; r += 32) {
-    for (int k = 0; k < w; ++k) {
-      const double xk = P[r + (int64_t)k * ld] * inv[k];
-      P[r + (int64_t)k * ld] = xk;
-      for (int j = k + 1; j < w; ++j) P[r + (int64_t)j * ld] -= xk * D[j + k * w];
-    }
+  // rows below: L21 = A21 L11^{-T}, lane-owned rows (the updates they cause run in the level's
+  // update pass)
+  switch (w) {
+#define CIPM_RB_CASE(W) case W: rows_below<W>(P, ld, D, inv, lane); break;
+    CIPM_RB_CASE(1) CIPM_RB_CASE(2) CIPM_RB_CASE(3) CIPM_RB_CASE(4) CIPM_RB_CASE(5)
+    CIPM_RB_CASE(6) CIPM_RB_CASE(7) CIPM_RB_CASE(8)
+#undef CIPM_RB_CASE
+    default:  // 8 < w <= B_WS: the row in a thread-private array
+      for (int r = w + lane; r < ld; r += 32) {
+        double x[B_WS];
+        for (int k = 0; k < w; ++k) x[k] = P[r + (int64_t)k * ld];
+        for (int k = 0; k < w; ++k) {
+          x[k] *= inv[k];
+          for (int j = k + 1; j < w; ++j) x[j] -= x[k] * D[j + k * w];
+        }
+        for (int k = 0; k < w; ++k) P[r + (int64_t)k * ld] = x[k];
+      }
   }
   __syncwarp();
-  scatter_update(I, s, ld, w, P, lane, 32);
 }
 
 // block path for a wide supernode (every thread of the block calls); sm: w*w + 32*(w+1) doubles
@@ -545,7 +595,7 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
   for (int k = 0; k < w; ++k) {
     if (tid == 0) {
       double d = sL[k + k * w];
-      if (!(d > 0.0) || !isfinite(d)) {
+      if (!pivot_ok(d)) {
         atomicMin(I.info, f + k);
         d = 1.0;
       }
@@ -596,8 +646,6 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
     }
   }
   __syncthreads();
-  scatter_update(I, s, ld, w, P, tid, bd);
-  __syncthreads();
 }
 
 // condensation of every panel, then the factorization, of each instance in the FACT phase: one
@@ -624,9 +672,37 @@ __global__ void __launch_bounds__(B_NT, 3)
   const int gw = crank * nw + warp, gnw = ncl * nw;
   const double dw = ctl[b].dw;
   if (crank == 0 && threadIdx.x == 0) *I.info = INT_MAX;
-  for (int s = gw; s < I.ns; s += gnw)
-    condense_block<double>(s, I.sptr, I.srow_ptr, I.lptr, I.slot_ptr, I.items, I.perm, I.Wv,
-                           I.SA.sigma, I.Jv, I.tJ, dw, I.Lx, lane, 32);
+  // K = W + Sigma_x + delta_w I + J^T D J into the lower slots of the panels (the diagonal
+  // block's upper triangle is never read); the W item of a slot is taken as W * 1 so that every
+  // lane issues the same fused multiply-add
+  for (int t = crank * blockDim.x + threadIdx.x; t < I.ncslot; t += ncl * blockDim.x) {
+    const int slot = I.cslot[t], j = I.ccol[t], g = t >> 5;
+    double v = j >= 0 ? I.SA.sigma[I.perm[j]] + dw : 0.0;
+    const int2 *it = I.citems + I.cgptr[g] + (t & 31);
+    const int cnt = (I.cgptr[g + 1] - I.cgptr[g]) >> 5;
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {  // four items' loads in flight, summed in list order
+      double a[4], m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int2 q = it[(k + u) * 32];
+        const bool wv = q.y < 0;
+        a[u] = wv ? I.Wv[q.x] : I.tJ[q.x];
+        m[u] = wv ? 1.0 : I.Jv[q.y];
+        if (q.y == -2) a[u] = m[u] = 0.0;  // padding
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v = fma(a[u], m[u], v);
+    }
+    for (; k < cnt; ++k) {
+      const int2 q = it[k * 32];
+      const bool wv = q.y < 0;
+      double a = wv ? I.Wv[q.x] : I.tJ[q.x], m = wv ? 1.0 : I.Jv[q.y];
+      if (q.y == -2) a = m = 0.0;
+      v = fma(a, m, v);
+    }
+    I.Lx[slot] = v;
+  }
   cluster.sync();
   double *D = sm + warp * (B_WS * B_WS + B_WS), *inv = D + B_WS * B_WS;
   for (int L = 0; L < I.nlevels; ++L) {
@@ -647,6 +723,8 @@ __global__ void __launch_bounds__(B_NT, 3)
     }
     __syncthreads();
     for (int k = 0; k < s_nwide; ++k) block_factor_sn(I, s_wide[k], sm, s_inv);
+    cluster.sync();
+    level_updates(I, L, crank * blockDim.x + threadIdx.x, ncl * blockDim.x);
     cluster.sync();
   }
 }
@@ -684,11 +762,24 @@ __device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
   const int *rows = I.srow + rb;
   const double *P = I.Lx + I.lptr[s];
   const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
-  for (int k = 0; k < w; ++k) {
+  if (w <= 32) {
+    // zs = y_own - L21^T y_below: lane = g * W2 + k takes column k over the rows i = w + g
+    // (mod G), then a shuffle tree over the G row groups (W2 = w rounded up to a power of two)
+    int W2 = 1;
+    while (W2 < w) W2 <<= 1;
+    const int k = lane & (W2 - 1), g = lane / W2, G = 32 / W2;
     double acc = 0.0;
-    for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * I.y[rows[i]];
-    acc = warp_sum(acc);
-    if (lane == 0) zs[k] = I.y[f + k] - acc;
+    if (k < w)
+      for (int i = w + g; i < ld; i += G) acc += P[i + (int64_t)k * ld] * I.y[rows[i]];
+    for (int o = W2; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (g == 0 && k < w) zs[k] = I.y[f + k] - acc;
+  } else {
+    for (int k = 0; k < w; ++k) {
+      double acc = 0.0;
+      for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * I.y[rows[i]];
+      acc = warp_sum(acc);
+      if (lane == 0) zs[k] = I.y[f + k] - acc;
+    }
   }
   __syncwarp();
   for (int k = w - 1; k >= 0; --k) {
@@ -702,9 +793,73 @@ __device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
   __syncwarp();
 }
 
+// Narrow supernodes with few rows below are solved one per thread (the many width-1 to width-4
+// supernodes of the deep levels: one FP64 warp instruction then serves up to 32 supernodes
+// instead of one).  The same arithmetic as the warp path, in registers.
+static constexpr int B_TS = 4, B_TR = 48;
+__device__ __forceinline__ bool thread_solved(const BI &I, int s) {
+  const int w = I.sptr[s + 1] - I.sptr[s];
+  return w <= B_TS && I.srow_ptr[s + 1] - I.srow_ptr[s] - w <= B_TR;
+}
+__device__ void thread_fwd_sn(const BI &I, int s) {
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
+  const int *rows = I.srow + rb;
+  const double *P = I.Lx + I.lptr[s];
+  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
+  double ys[B_TS];
+#pragma unroll
+  for (int k = 0; k < B_TS; ++k) ys[k] = k < w ? I.y[f + k] : 0.0;
+#pragma unroll
+  for (int k = 0; k < B_TS; ++k)
+    if (k < w) {
+      ys[k] *= rinv[k];
+#pragma unroll
+      for (int i = k + 1; i < B_TS; ++i)
+        if (i < w) ys[i] -= Dd[i + k * w] * ys[k];
+    }
+#pragma unroll
+  for (int k = 0; k < B_TS; ++k)
+    if (k < w) I.y[f + k] = ys[k];
+  for (int i = w; i < ld; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < B_TS; ++k)
+      if (k < w) acc += P[i + (int64_t)k * ld] * ys[k];
+    atomicAdd(&I.y[rows[i]], -acc);
+  }
+}
+__device__ void thread_bwd_sn(const BI &I, int s) {
+  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
+  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
+  const int *rows = I.srow + rb;
+  const double *P = I.Lx + I.lptr[s];
+  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
+  double zs[B_TS] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = w; i < ld; ++i) {
+    const double yi = I.y[rows[i]];
+#pragma unroll
+    for (int k = 0; k < B_TS; ++k)
+      if (k < w) zs[k] += P[i + (int64_t)k * ld] * yi;
+  }
+#pragma unroll
+  for (int k = 0; k < B_TS; ++k)
+    if (k < w) zs[k] = I.y[f + k] - zs[k];
+#pragma unroll
+  for (int k = B_TS - 1; k >= 0; --k)
+    if (k < w) {
+      zs[k] *= rinv[k];
+#pragma unroll
+      for (int j = 0; j < k; ++j) zs[j] -= Dd[k + j * w] * zs[k];
+    }
+#pragma unroll
+  for (int k = 0; k < B_TS; ++k)
+    if (k < w) I.y[f + k] = zs[k];
+}
+
 // phase SOLVE: dx = K^{-1} t; phase REFINE: cx = K^{-1} t (t from k_b_jt_rhs), one cluster per
 // instance: gather by the ordering, forward levels, backward levels, scatter
-__global__ void __launch_bounds__(B_NT)
+__global__ void __launch_bounds__(B_NT, 3)
     k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase, const int *order) {
   __shared__ double s_y[(B_NT / 32) * CIPM_SN_MAXW];
   namespace cg = cooperative_groups;
@@ -720,11 +875,19 @@ __global__ void __launch_bounds__(B_NT)
   for (int k = gt; k < I.D.n; k += gnt) I.y[k] = I.t[I.perm[k]];
   cluster.sync();
   for (int L = 0; L < I.nlevels; ++L) {
-    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_fwd_sn(I, I.level_sn[q], ys);
+    const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
+    for (int q = q0 + gt; q < q1; q += gnt)
+      if (thread_solved(I, I.level_sn[q])) thread_fwd_sn(I, I.level_sn[q]);
+    for (int q = q0 + gw; q < q1; q += gnw)
+      if (!thread_solved(I, I.level_sn[q])) warp_fwd_sn(I, I.level_sn[q], ys);
     cluster.sync();
   }
   for (int L = I.nlevels - 1; L >= 0; --L) {
-    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_bwd_sn(I, I.level_sn[q], ys);
+    const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
+    for (int q = q0 + gt; q < q1; q += gnt)
+      if (thread_solved(I, I.level_sn[q])) thread_bwd_sn(I, I.level_sn[q]);
+    for (int q = q0 + gw; q < q1; q += gnw)
+      if (!thread_solved(I, I.level_sn[q])) warp_bwd_sn(I, I.level_sn[q], ys);
     cluster.sync();
   }
   double *x = phase == PH_SOLVE || phase == PH_CGI || phase == PH_CGX ? I.dx
@@ -1696,7 +1859,11 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   }
   // update pairs of every pattern: for each supernode, the pairs (i, j) of its rows below the
   // diagonal block and the slot of the target panel that entry (i, j) of L21 L21^T updates
-  std::vector<int *> pptr(B->syms.size()), pij(B->syms.size()), ptgt(B->syms.size());
+  std::vector<int *> pptr(B->syms.size()), psn(B->syms.size()), pij(B->syms.size()),
+      ptgt(B->syms.size());
+  std::vector<int *> cslot(B->syms.size()), ccol(B->syms.size()), cgp(B->syms.size());
+  std::vector<int2 *> citm(B->syms.size());
+  std::vector<int> ncslot(B->syms.size());
   for (size_t q = 0; q < B->syms.size(); ++q) {
     ipm_sym_t S = B->syms[q];
     const int ns = S->nsuper;
@@ -1711,21 +1878,28 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     if (rp[ns] && cudaMemcpy(rows.data(), S->srow, sizeof(int) * rp[ns], cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(IPM_ERR_CUDA);
     if (S->panel_len >= INT_MAX) return fail(IPM_ERR_BAD_ARG);
-    std::vector<int> hp(ns + 1, 0), hij, htg;
-    for (int sn_ = 0; sn_ < ns; ++sn_) {
-      const int w = sp[sn_ + 1] - sp[sn_], rb = rp[sn_], ld = rp[sn_ + 1] - rb;
-      if (ld >= 65536) return fail(IPM_ERR_BAD_ARG);
-      for (int j = w; j < ld; ++j) {
-        const int col = rows[rb + j], ts = sn[col];
-        const int tb = rp[ts], tld = rp[ts + 1] - tb;
-        const int *tr = rows.data() + tb;
-        for (int i = j; i < ld; ++i) {
-          const int r = (int)(std::lower_bound(tr, tr + tld, rows[rb + i]) - tr);
-          hij.push_back(i << 16 | j);
-          htg.push_back((int)(lp[ts] + (int64_t)(col - sp[ts]) * tld + r));
+    std::vector<int> lsn(ns);
+    if (ns && cudaMemcpy(lsn.data(), S->level_sn, sizeof(int) * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
+    std::vector<int> hp(S->nlevels + 1, 0), hsn, hij, htg;
+    for (int L = 0; L < S->nlevels; ++L) {
+      for (int qq = S->h_level_ptr[L]; qq < S->h_level_ptr[L + 1]; ++qq) {
+        const int sn_ = lsn[qq];
+        const int w = sp[sn_ + 1] - sp[sn_], rb = rp[sn_], ld = rp[sn_ + 1] - rb;
+        if (ld >= 65536) return fail(IPM_ERR_BAD_ARG);
+        for (int j = w; j < ld; ++j) {
+          const int col = rows[rb + j], ts = sn[col];
+          const int tb = rp[ts], tld = rp[ts + 1] - tb;
+          const int *tr = rows.data() + tb;
+          for (int i = j; i < ld; ++i) {
+            const int r = (int)(std::lower_bound(tr, tr + tld, rows[rb + i]) - tr);
+            hsn.push_back(sn_);
+            hij.push_back(i << 16 | j);
+            htg.push_back((int)(lp[ts] + (int64_t)(col - sp[ts]) * tld + r));
+          }
         }
       }
-      hp[sn_ + 1] = (int)hij.size();
+      hp[L + 1] = (int)hij.size();
     }
     auto upi = [&](int **dst, const std::vector<int> &v) -> int {
       if (cudaMalloc((void **)dst, sizeof(int) * std::max<size_t>(v.size(), 1)) != cudaSuccess)
@@ -1735,10 +1909,64 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
         return IPM_ERR_CUDA;
       return IPM_OK;
     };
+    // condensation order: lower slots by descending item count (then by slot)
+    std::vector<int> sptr_items(S->panel_len + 1);
+    std::vector<int2> items(std::max<int64_t>(S->nitems, 1));
+    if (cudaMemcpy(sptr_items.data(), S->slot_ptr, sizeof(int) * (S->panel_len + 1),
+                   cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (S->nitems && cudaMemcpy(items.data(), S->items, sizeof(int2) * S->nitems,
+                                 cudaMemcpyDeviceToHost) != cudaSuccess))
+      return fail(IPM_ERR_CUDA);
+    std::vector<std::pair<int, int>> order;  // (-count, slot)
+    std::vector<int> diagcol(S->panel_len, -1);
+    for (int sn_ = 0; sn_ < ns; ++sn_) {
+      const int w = sp[sn_ + 1] - sp[sn_], ld = rp[sn_ + 1] - rp[sn_];
+      for (int c = 0; c < w; ++c)
+        for (int r = c; r < ld; ++r) {
+          const int slot = (int)(lp[sn_] + (int64_t)c * ld + r);
+          order.push_back({-(sptr_items[slot + 1] - sptr_items[slot]), slot});
+          if (r == c) diagcol[slot] = sp[sn_] + c;
+        }
+    }
+    std::sort(order.begin(), order.end());
+    std::vector<int> hcs(order.size()), hcc(order.size());
+    for (size_t t = 0; t < order.size(); ++t) {
+      hcs[t] = order[t].second;
+      hcc[t] = diagcol[order[t].second];
+    }
+    ncslot[q] = (int)order.size();
+    const size_t ngrp = (order.size() + 31) / 32;
+    std::vector<int> hgp(ngrp + 1, 0);
+    std::vector<int2> hci;
+    for (size_t g = 0; g < ngrp; ++g) {
+      const int cnt = -order[g * 32].first;  // the largest count of the group (sorted)
+      if ((int64_t)hci.size() + 32 * (int64_t)cnt >= INT_MAX) return fail(IPM_ERR_BAD_ARG);
+      for (int k = 0; k < cnt; ++k)
+        for (int l = 0; l < 32; ++l) {
+          const size_t t = g * 32 + l;
+          int2 v = make_int2(0, -2);
+          if (t < order.size()) {
+            const int slot = order[t].second;
+            if (k < sptr_items[slot + 1] - sptr_items[slot]) v = items[sptr_items[slot] + k];
+          }
+          hci.push_back(v);
+        }
+      hgp[g + 1] = (int)hci.size();
+    }
     int r1 = upi(&pptr[q], hp);
+    if (r1 == IPM_OK) r1 = upi(&psn[q], hsn);
     if (r1 == IPM_OK) r1 = upi(&pij[q], hij);
     if (r1 == IPM_OK) r1 = upi(&ptgt[q], htg);
+    if (r1 == IPM_OK) r1 = upi(&cslot[q], hcs);
+    if (r1 == IPM_OK) r1 = upi(&ccol[q], hcc);
+    if (r1 == IPM_OK) r1 = upi(&cgp[q], hgp);
     if (r1 != IPM_OK) return fail(r1);
+    if (cudaMalloc((void **)&citm[q], sizeof(int2) * std::max<size_t>(hci.size(), 1)) != cudaSuccess)
+      return fail(IPM_ERR_OOM);
+    B->bufs.push_back(citm[q]);
+    if (!hci.empty() && cudaMemcpy(citm[q], hci.data(), sizeof(int2) * hci.size(),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
   }
   // level offsets of each pattern's supernode schedule, on the device
   std::vector<int *> lvl(B->syms.size(), nullptr);
@@ -1785,9 +2013,15 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.srow = S->srow; I.snode = S->snode; I.level_sn = S->level_sn; I.dptr = S->dptr;
     I.nlevels = S->nlevels;
     I.lvl_ptr = lvl[B->pat[i]];
-    I.pair_ptr = pptr[B->pat[i]];
+    I.lpair_ptr = pptr[B->pat[i]];
+    I.pair_sn = psn[B->pat[i]];
     I.pair_ij = pij[B->pat[i]];
     I.pair_tgt = ptgt[B->pat[i]];
+    I.cslot = cslot[B->pat[i]];
+    I.ccol = ccol[B->pat[i]];
+    I.cgptr = cgp[B->pat[i]];
+    I.citems = citm[B->pat[i]];
+    I.ncslot = ncslot[B->pat[i]];
     I.y = d + o.y_s; I.t = d + o.t; I.cx = d + o.cx; I.cz = d + o.cz; I.outx = d + o.outx;
     I.outz = d + o.outz; I.scal = d + o.scal;
     I.cg_r = d + o.cg_r; I.cg_p = d + o.cg_p; I.cg_sp = d + o.cg_sp; I.cg_dy = d + o.cg_dy;
