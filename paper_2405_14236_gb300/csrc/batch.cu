@@ -68,11 +68,12 @@ struct BI {
   const int *sptr, *srow_ptr, *slot_ptr, *perm, *J_rowidx, *JT_ptr, *JT_ent;
   const int *srow, *snode, *level_sn, *lvl_ptr;  // lvl_ptr: level offsets into level_sn
   // update pairs (precomputed per pattern), stored level by level: level L owns entries
-  // lpair_ptr[L] .. lpair_ptr[L + 1]; each pair: its supernode, rows (i << 16 | j) of that
-  // panel (i >= j >= w) and the target value slot in the panels
-  const int *lpair_ptr, *pair_sn, *pair_ij, *pair_tgt;
+  // lpair_ptr[L] .. lpair_ptr[L + 1]; each pair: the panel slots of rows i and j (i >= j >= w)
+  // in column 0 of its supernode, ld << 8 | w of that panel, and the target value slot
+  const int *lpair_ptr, *pair_a, *pair_b, *pair_m, *pair_tgt;
   // condensation order (per pattern): the lower panel slots of every supernode sorted by their
-  // number of items (ccol: the column of a diagonal slot, else -1); the items of each group of
+  // number of items (ccol: the variable of a diagonal slot, whose Sigma_x entry it takes, else
+  // -1); the items of each group of
   // 32 slots are interleaved (item k of lane l at cgptr[g] + 32 k + l, padded with y = -2) so
   // that a warp's item loads are coalesced and its lanes loop over equal counts
   const int *cslot, *ccol, *cgptr;
@@ -282,44 +283,55 @@ __global__ void k_b_jtu(const BI *bi, const BCtl *ctl) {
 }
 // optimality error parts (mu-independent maxima, sums, min / max of the complementarity
 // products) and the merit parts at (x, s)
+// Maxima and minima of non-negative values are kept on their bit patterns (integer compares,
+// which order like the numbers and keep a NaN as the largest), the barrier logs in a LogSum
+// (their total goes to R_LOG_S): both keep FP64 instructions for the sums.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
 __global__ void k_b_errors(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
   const Dims &D = I.D;
   const double sig = ctl[b].sig;
-  double gl = 0, zv = 0, ge = 0, hs = 0, sy = 0, sz = 0, svv = 0, szl = 0, szu = 0;
-  double svmin = INFINITY, svmax = 0, clmin = INFINITY, clmax = 0, cumin = INFINITY, cumax = 0;
-  double tg = 0, th = 0, ls = 0, lxl = 0, lxu = 0;
+  long long gl = 0, zv = 0, ge = 0, hs = 0;
+  const long long inf = dbits(INFINITY);
+  long long svmin = inf, svmax = 0, clmin = inf, clmax = 0, cumin = inf, cumax = 0;
+  double sy = 0, sz = 0, svv = 0, szl = 0, szu = 0, tg = 0, th = 0;
+  LogSum lg;
   const int nmax = max(D.n, max(D.me, D.mi));
   for (int i = gtid; i < nmax; i += gstride) {
     const ErrParts E = errors_at(D, I.P, sig, 0.0, i);
-    gl = fmax(gl, E.gl);
-    zv = fmax(zv, E.zv);
-    ge = fmax(ge, E.ge);
-    hs = fmax(hs, E.hs);
+    gl = max(gl, dbits(E.gl));
+    zv = max(zv, dbits(E.zv));
+    ge = max(ge, dbits(E.ge));
+    hs = max(hs, dbits(E.hs));
     sy += E.sy;
     sz += E.sz;
     svv += E.svv;
     szl += E.szl;
     szu += E.szu;
-    if (E.csv >= 0) { svmin = fmin(svmin, E.csv); svmax = fmax(svmax, E.csv); }
-    if (E.ccl >= 0) { clmin = fmin(clmin, E.ccl); clmax = fmax(clmax, E.ccl); }
-    if (E.ccu >= 0) { cumin = fmin(cumin, E.ccu); cumax = fmax(cumax, E.ccu); }
-    const MeritParts Mp = merit_at(D, I.P.x, I.P.s, I.P.xl, I.P.xu, I.P.geq, I.P.hin, i);
-    tg += Mp.tg;
-    th += Mp.th;
-    ls += Mp.ls;
-    lxl += Mp.lxl;
-    lxu += Mp.lxu;
+    // absent products are -1: a negative bit pattern
+    const long long cs = dbits(E.csv), cl = dbits(E.ccl), cu = dbits(E.ccu);
+    if (cs >= 0) { svmin = min(svmin, cs); svmax = max(svmax, cs); }
+    if (cl >= 0) { clmin = min(clmin, cl); clmax = max(clmax, cl); }
+    if (cu >= 0) { cumin = min(cumin, cu); cumax = max(cumax, cu); }
+    if (i < D.me) tg += fabs(I.P.geq[i]);
+    if (i < D.mi) {
+      th += fabs(I.P.hin[i] + I.P.s[i]);
+      lg.add(I.P.s[i]);
+    }
+    if (i < D.n) {
+      if (isfinite(I.P.xl[i])) lg.add(I.P.x[i] - I.P.xl[i]);
+      if (isfinite(I.P.xu[i])) lg.add(I.P.xu[i] - I.P.x[i]);
+    }
   }
-  const int slot[20] = {R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_SUM_Y, R_SUM_Z, R_SUM_V,
-                       R_SUM_ZL, R_SUM_ZU, R_SV_MIN, R_SV_MAX, R_CL_MIN, R_CL_MAX, R_CU_MIN,
-                       R_CU_MAX, R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU};
-  const int op[20] = {OP_MAX, OP_MAX, OP_MAX, OP_MAX, OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM,
-                      OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_SUM, OP_SUM, OP_SUM,
-                      OP_SUM, OP_SUM};
-  double v[20] = {gl, zv, ge, hs, sy, sz, svv, szl, szu, svmin, svmax, clmin, clmax,
-                  cumin, cumax, tg, th, ls, lxl, lxu};
-  block_reduce_atomic<20>(I.R, slot, op, v);
+  const int slot[18] = {R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_SUM_Y, R_SUM_Z, R_SUM_V,
+                        R_SUM_ZL, R_SUM_ZU, R_SV_MIN, R_SV_MAX, R_CL_MIN, R_CL_MAX, R_CU_MIN,
+                        R_CU_MAX, R_TH_G, R_TH_H, R_LOG_S};
+  const int op[18] = {OP_MAX, OP_MAX, OP_MAX, OP_MAX, OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM,
+                      OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_SUM, OP_SUM, OP_SUM};
+  auto d = [](long long x) { return __longlong_as_double(x); };
+  double v[18] = {d(gl), d(zv), d(ge), d(hs), sy, sz, svv, szl, szu, d(svmin), d(svmax),
+                  d(clmin), d(clmax), d(cumin), d(cumax), tg, th, lg.value()};
+  block_reduce_atomic<18>(I.R, slot, op, v);
 }
 
 __device__ __forceinline__ double comp_mu(const double *h, double mu) {
@@ -410,6 +422,45 @@ __global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
   for (int p = gtid; p < I.M.nnzJ; p += gstride) I.tJ[p] = I.dcond[I.J_rowidx[p]] * I.Jv[p];
 }
 
+// ------------------------------------------------------------------ condensation
+// K = W + Sigma_x + delta_w I + J^T D J into the lower slots of every panel of the instances in
+// the FACT phase (the diagonal block's upper triangle is never read), all slots of all instances
+// in one launch (slots are independent); the W item of a slot is taken as W * 1 so that every
+// lane issues the same fused multiply-add.  Also resets the factorization status.
+__global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_FACT);
+  if (gtid == 0) *I.info = INT_MAX;
+  const double dw = ctl[b].dw;
+  for (int t = gtid; t < I.ncslot; t += gstride) {
+    const int slot = I.cslot[t], j = I.ccol[t], g = t >> 5;
+    double v = j >= 0 ? I.SA.sigma[j] + dw : 0.0;
+    const int2 *it = I.citems + I.cgptr[g] + (t & 31);
+    const int cnt = (I.cgptr[g + 1] - I.cgptr[g]) >> 5;
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {  // four items' loads in flight, summed in list order
+      double a[4], m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int2 q = it[(k + u) * 32];
+        const bool wv = q.y < 0;
+        a[u] = wv ? I.Wv[q.x] : I.tJ[q.x];
+        m[u] = wv ? 1.0 : I.Jv[q.y];
+        if (q.y == -2) a[u] = m[u] = 0.0;  // padding
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v = fma(a[u], m[u], v);
+    }
+    for (; k < cnt; ++k) {
+      const int2 q = it[k * 32];
+      const bool wv = q.y < 0;
+      double a = wv ? I.Wv[q.x] : I.tJ[q.x], m = wv ? 1.0 : I.Jv[q.y];
+      if (q.y == -2) a = m = 0.0;
+      v = fma(a, m, v);
+    }
+    I.Lx[slot] = v;
+  }
+}
+
 // ------------------------------------------------------------------ per-instance numeric kernels
 // One block per instance, level by level through the supernodal elimination tree (deepest level
 // first for the factorization and the forward solve, root first for the backward solve): the
@@ -418,7 +469,8 @@ __global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
 // block.  Contributions into other supernodes' panels (and into y) from one level are added
 // atomically, since supernodes of a level may share targets.  No waits on other blocks.
 static constexpr int B_WS = 16;
-static constexpr int B_NT = 512;  // threads of the per-instance kernels
+static constexpr int B_NT = 512;    // threads of the per-instance solve kernel
+static constexpr int B_NT_F = 512;  // threads of the per-instance factorization kernel
 
 // Updates of the supernodes of level L into their ancestors, every pair of the level spread over
 // all threads of the cluster: entry (i, j), i >= j >= w, of L21 L21^T of supernode s is
@@ -426,24 +478,22 @@ static constexpr int B_NT = 512;  // threads of the per-instance kernels
 __device__ __forceinline__ void level_updates(const BI &I, int L, int tid, int nthreads) {
   const int p1 = I.lpair_ptr[L + 1];
   for (int t = I.lpair_ptr[L] + tid; t < p1; t += nthreads) {
-    const int s = I.pair_sn[t];
-    const int w = I.sptr[s + 1] - I.sptr[s], ld = I.srow_ptr[s + 1] - I.srow_ptr[s];
-    const double *P = I.Lx + I.lptr[s];
-    const int ij = I.pair_ij[t];
-    const int i = ij >> 16, j = ij & 0xffff;
+    const int m = I.pair_m[t];
+    const int w = m & 0xff, ld = m >> 8;
+    const double *Pi = I.Lx + I.pair_a[t], *Pj = I.Lx + I.pair_b[t];
     double v = 0.0;
     int k = 0;
     for (; k + 4 <= w; k += 4) {  // four independent load pairs in flight
       double a[4], c[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        a[u] = P[i + (int64_t)(k + u) * ld];
-        c[u] = P[j + (int64_t)(k + u) * ld];
+        a[u] = Pi[(int64_t)(k + u) * ld];
+        c[u] = Pj[(int64_t)(k + u) * ld];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) v += a[u] * c[u];
     }
-    for (; k < w; ++k) v += P[i + (int64_t)k * ld] * P[j + (int64_t)k * ld];
+    for (; k < w; ++k) v += Pi[(int64_t)k * ld] * Pj[(int64_t)k * ld];
     atomicAdd(&I.Lx[I.pair_tgt[t]], -v);
   }
 }
@@ -648,7 +698,7 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
   __syncthreads();
 }
 
-// condensation of every panel, then the factorization, of each instance in the FACT phase: one
+// factorization of each instance in the FACT phase (panels condensed by k_b_condense): one
 // block, or one thread-block cluster (big instances, launched with a cluster size), per
 // instance.  Warps of the whole cluster share the narrow supernodes of a level; each block
 // collects the wide ones its warps met and factors them with all its threads; a cluster barrier
@@ -656,7 +706,7 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
 static constexpr int B_CL_BIG = 4;       // cluster size of the big instances
 static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
 
-__global__ void __launch_bounds__(B_NT, 3)
+__global__ void __launch_bounds__(B_NT_F, 3)
     k_b_fact_inst(const BI *bi, const BCtl *ctl, const int *order) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double *sm = reinterpret_cast<double *>(sm_raw);
@@ -670,40 +720,6 @@ __global__ void __launch_bounds__(B_NT, 3)
   const BI &I = bi[b];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int gw = crank * nw + warp, gnw = ncl * nw;
-  const double dw = ctl[b].dw;
-  if (crank == 0 && threadIdx.x == 0) *I.info = INT_MAX;
-  // K = W + Sigma_x + delta_w I + J^T D J into the lower slots of the panels (the diagonal
-  // block's upper triangle is never read); the W item of a slot is taken as W * 1 so that every
-  // lane issues the same fused multiply-add
-  for (int t = crank * blockDim.x + threadIdx.x; t < I.ncslot; t += ncl * blockDim.x) {
-    const int slot = I.cslot[t], j = I.ccol[t], g = t >> 5;
-    double v = j >= 0 ? I.SA.sigma[I.perm[j]] + dw : 0.0;
-    const int2 *it = I.citems + I.cgptr[g] + (t & 31);
-    const int cnt = (I.cgptr[g + 1] - I.cgptr[g]) >> 5;
-    int k = 0;
-    for (; k + 4 <= cnt; k += 4) {  // four items' loads in flight, summed in list order
-      double a[4], m[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int2 q = it[(k + u) * 32];
-        const bool wv = q.y < 0;
-        a[u] = wv ? I.Wv[q.x] : I.tJ[q.x];
-        m[u] = wv ? 1.0 : I.Jv[q.y];
-        if (q.y == -2) a[u] = m[u] = 0.0;  // padding
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v = fma(a[u], m[u], v);
-    }
-    for (; k < cnt; ++k) {
-      const int2 q = it[k * 32];
-      const bool wv = q.y < 0;
-      double a = wv ? I.Wv[q.x] : I.tJ[q.x], m = wv ? 1.0 : I.Jv[q.y];
-      if (q.y == -2) a = m = 0.0;
-      v = fma(a, m, v);
-    }
-    I.Lx[slot] = v;
-  }
-  cluster.sync();
   double *D = sm + warp * (B_WS * B_WS + B_WS), *inv = D + B_WS * B_WS;
   for (int L = 0; L < I.nlevels; ++L) {
     if (threadIdx.x == 0) s_nwide = 0;
@@ -730,14 +746,25 @@ __global__ void __launch_bounds__(B_NT, 3)
 }
 
 // y <- L^{-T} L^{-1} y for one supernode, one warp (ys: w doubles of this warp's shared memory)
-__device__ void warp_fwd_sn(const BI &I, int s, double *ys) {
+// L11 and the reciprocal pivots of a supernode of width w <= B_WS copied to this warp's shared
+// staging area with one load per lane (the triangular loops then read shared memory instead of
+// issuing one global round trip per column); wider supernodes read them in place
+__device__ __forceinline__ const double *stage_diag(const double *Dd, int w, double *stage,
+                                                    int lane) {
+  if (w > B_WS) return Dd;
+  for (int t = lane; t < w * w + w; t += 32) stage[t] = Dd[t];
+  __syncwarp();
+  return stage;
+}
+
+__device__ void warp_fwd_sn(const BI &I, double *Y, int s, double *ys) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   const int *rows = I.srow + rb;
   const double *P = I.Lx + I.lptr[s];
-  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
-  for (int k = lane; k < w; k += 32) ys[k] = I.y[f + k];
+  const double *Dd = stage_diag(I.Dx + I.dptr[s], w, ys + CIPM_SN_MAXW, lane), *rinv = Dd + w * w;
+  for (int k = lane; k < w; k += 32) ys[k] = Y[f + k];
   __syncwarp();
   for (int k = 0; k < w; ++k) {
     if (lane == (k & 31)) ys[k] *= rinv[k];
@@ -746,22 +773,30 @@ __device__ void warp_fwd_sn(const BI &I, int s, double *ys) {
     for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= Dd[i + k * w] * yk;
     __syncwarp();
   }
-  for (int k = lane; k < w; k += 32) I.y[f + k] = ys[k];
+  for (int k = lane; k < w; k += 32) Y[f + k] = ys[k];
   for (int i = w + lane; i < ld; i += 32) {
     double acc = 0.0;
-    for (int k = 0; k < w; ++k) acc += P[i + (int64_t)k * ld] * ys[k];
-    atomicAdd(&I.y[rows[i]], -acc);
+    int k = 0;
+    for (; k + 4 <= w; k += 4) {  // four loads in flight
+      double p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p[u] = P[i + (int64_t)(k + u) * ld];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += p[u] * ys[k + u];
+    }
+    for (; k < w; ++k) acc += P[i + (int64_t)k * ld] * ys[k];
+    atomicAdd(&Y[rows[i]], -acc);
   }
   __syncwarp();
 }
 
-__device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
+__device__ void warp_bwd_sn(const BI &I, double *Y, int s, double *zs) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   const int *rows = I.srow + rb;
   const double *P = I.Lx + I.lptr[s];
-  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
+  const double *Dd = stage_diag(I.Dx + I.dptr[s], w, zs + CIPM_SN_MAXW, lane), *rinv = Dd + w * w;
   if (w <= 32) {
     // zs = y_own - L21^T y_below: lane = g * W2 + k takes column k over the rows i = w + g
     // (mod G), then a shuffle tree over the G row groups (W2 = w rounded up to a power of two)
@@ -770,15 +805,15 @@ __device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
     const int k = lane & (W2 - 1), g = lane / W2, G = 32 / W2;
     double acc = 0.0;
     if (k < w)
-      for (int i = w + g; i < ld; i += G) acc += P[i + (int64_t)k * ld] * I.y[rows[i]];
+      for (int i = w + g; i < ld; i += G) acc += P[i + (int64_t)k * ld] * Y[rows[i]];
     for (int o = W2; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (g == 0 && k < w) zs[k] = I.y[f + k] - acc;
+    if (g == 0 && k < w) zs[k] = Y[f + k] - acc;
   } else {
     for (int k = 0; k < w; ++k) {
       double acc = 0.0;
-      for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * I.y[rows[i]];
+      for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * Y[rows[i]];
       acc = warp_sum(acc);
-      if (lane == 0) zs[k] = I.y[f + k] - acc;
+      if (lane == 0) zs[k] = Y[f + k] - acc;
     }
   }
   __syncwarp();
@@ -789,7 +824,7 @@ __device__ void warp_bwd_sn(const BI &I, int s, double *zs) {
     for (int j = lane; j < k; j += 32) zs[j] -= Dd[k + j * w] * xk;
     __syncwarp();
   }
-  for (int k = lane; k < w; k += 32) I.y[f + k] = zs[k];
+  for (int k = lane; k < w; k += 32) Y[f + k] = zs[k];
   __syncwarp();
 }
 
@@ -801,7 +836,7 @@ __device__ __forceinline__ bool thread_solved(const BI &I, int s) {
   const int w = I.sptr[s + 1] - I.sptr[s];
   return w <= B_TS && I.srow_ptr[s + 1] - I.srow_ptr[s] - w <= B_TR;
 }
-__device__ void thread_fwd_sn(const BI &I, int s) {
+__device__ void thread_fwd_sn(const BI &I, double *Y, int s) {
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   const int *rows = I.srow + rb;
@@ -809,7 +844,7 @@ __device__ void thread_fwd_sn(const BI &I, int s) {
   const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
   double ys[B_TS];
 #pragma unroll
-  for (int k = 0; k < B_TS; ++k) ys[k] = k < w ? I.y[f + k] : 0.0;
+  for (int k = 0; k < B_TS; ++k) ys[k] = k < w ? Y[f + k] : 0.0;
 #pragma unroll
   for (int k = 0; k < B_TS; ++k)
     if (k < w) {
@@ -820,31 +855,59 @@ __device__ void thread_fwd_sn(const BI &I, int s) {
     }
 #pragma unroll
   for (int k = 0; k < B_TS; ++k)
-    if (k < w) I.y[f + k] = ys[k];
-  for (int i = w; i < ld; ++i) {
+    if (k < w) Y[f + k] = ys[k];
+  // rows four at a time: their loads are in flight together
+  int i = w;
+  for (; i + 4 <= ld; i += 4) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < B_TS; ++k)
+      if (k < w) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += P[i + u + (int64_t)k * ld] * ys[k];
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) atomicAdd(&Y[rows[i + u]], -acc[u]);
+  }
+  for (; i < ld; ++i) {
     double acc = 0.0;
 #pragma unroll
     for (int k = 0; k < B_TS; ++k)
       if (k < w) acc += P[i + (int64_t)k * ld] * ys[k];
-    atomicAdd(&I.y[rows[i]], -acc);
+    atomicAdd(&Y[rows[i]], -acc);
   }
 }
-__device__ void thread_bwd_sn(const BI &I, int s) {
+__device__ void thread_bwd_sn(const BI &I, double *Y, int s) {
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   const int *rows = I.srow + rb;
   const double *P = I.Lx + I.lptr[s];
   const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
   double zs[B_TS] = {0.0, 0.0, 0.0, 0.0};
-  for (int i = w; i < ld; ++i) {
-    const double yi = I.y[rows[i]];
+  int i = w;
+  for (; i + 4 <= ld; i += 4) {  // four rows' loads in flight, summed in row order
+    double yi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) yi[u] = Y[rows[i + u]];
+#pragma unroll
+    for (int k = 0; k < B_TS; ++k)
+      if (k < w) {
+        double p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = P[i + u + (int64_t)k * ld];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) zs[k] += p[u] * yi[u];
+      }
+  }
+  for (; i < ld; ++i) {
+    const double yi = Y[rows[i]];
 #pragma unroll
     for (int k = 0; k < B_TS; ++k)
       if (k < w) zs[k] += P[i + (int64_t)k * ld] * yi;
   }
 #pragma unroll
   for (int k = 0; k < B_TS; ++k)
-    if (k < w) zs[k] = I.y[f + k] - zs[k];
+    if (k < w) zs[k] = Y[f + k] - zs[k];
 #pragma unroll
   for (int k = B_TS - 1; k >= 0; --k)
     if (k < w) {
@@ -854,14 +917,16 @@ __device__ void thread_bwd_sn(const BI &I, int s) {
     }
 #pragma unroll
   for (int k = 0; k < B_TS; ++k)
-    if (k < w) I.y[f + k] = zs[k];
+    if (k < w) Y[f + k] = zs[k];
 }
 
 // phase SOLVE: dx = K^{-1} t; phase REFINE: cx = K^{-1} t (t from k_b_jt_rhs), one cluster per
 // instance: gather by the ordering, forward levels, backward levels, scatter
 __global__ void __launch_bounds__(B_NT, 3)
-    k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase, const int *order) {
-  __shared__ double s_y[(B_NT / 32) * CIPM_SN_MAXW];
+    k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase, int ycap, const int *order) {
+  constexpr int kArea = CIPM_SN_MAXW + B_WS * B_WS + B_WS;  // per warp: ys, then L11 stage
+  __shared__ double s_y[(B_NT / 32) * kArea];
+  extern __shared__ __align__(16) double s_vec[];
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
@@ -871,28 +936,31 @@ __global__ void __launch_bounds__(B_NT, 3)
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gw = crank * nw + warp, gnw = ncl * nw;
   const int gt = crank * blockDim.x + threadIdx.x, gnt = ncl * blockDim.x;
-  double *ys = s_y + warp * CIPM_SN_MAXW;
-  for (int k = gt; k < I.D.n; k += gnt) I.y[k] = I.t[I.perm[k]];
+  double *ys = s_y + warp * kArea;
+  // the permuted right-hand side lives in this block's shared memory when the instance has
+  // one block and n fits (ycap doubles): its loads and atomic updates then stay on the SM
+  double *Y = ncl == 1 && I.D.n <= ycap ? s_vec : I.y;
+  for (int k = gt; k < I.D.n; k += gnt) Y[k] = I.t[I.perm[k]];
   cluster.sync();
   for (int L = 0; L < I.nlevels; ++L) {
     const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
     for (int q = q0 + gt; q < q1; q += gnt)
-      if (thread_solved(I, I.level_sn[q])) thread_fwd_sn(I, I.level_sn[q]);
+      if (thread_solved(I, I.level_sn[q])) thread_fwd_sn(I, Y, I.level_sn[q]);
     for (int q = q0 + gw; q < q1; q += gnw)
-      if (!thread_solved(I, I.level_sn[q])) warp_fwd_sn(I, I.level_sn[q], ys);
+      if (!thread_solved(I, I.level_sn[q])) warp_fwd_sn(I, Y, I.level_sn[q], ys);
     cluster.sync();
   }
   for (int L = I.nlevels - 1; L >= 0; --L) {
     const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
     for (int q = q0 + gt; q < q1; q += gnt)
-      if (thread_solved(I, I.level_sn[q])) thread_bwd_sn(I, I.level_sn[q]);
+      if (thread_solved(I, I.level_sn[q])) thread_bwd_sn(I, Y, I.level_sn[q]);
     for (int q = q0 + gw; q < q1; q += gnw)
-      if (!thread_solved(I, I.level_sn[q])) warp_bwd_sn(I, I.level_sn[q], ys);
+      if (!thread_solved(I, I.level_sn[q])) warp_bwd_sn(I, Y, I.level_sn[q], ys);
     cluster.sync();
   }
   double *x = phase == PH_SOLVE || phase == PH_CGI || phase == PH_CGX ? I.dx
               : phase == PH_CG ? I.cg_v : I.cx;
-  for (int k = gt; k < I.D.n; k += gnt) x[I.perm[k]] = I.y[k];
+  for (int k = gt; k < I.D.n; k += gnt) x[I.perm[k]] = Y[k];
 }
 
 // ------------------------------------------------------------------ HyKKT CG (Eq. (10))
@@ -1248,20 +1316,24 @@ __global__ void k_b_trial(const BI *bi, const BCtl *ctl) {
 __global__ void k_b_merit_trial(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_LS);
   const Dims &D = I.D;
-  double tg = 0, th = 0, ls = 0, lxl = 0, lxu = 0;
+  double tg = 0, th = 0;
+  LogSum lg;  // the barrier logs (total into R_LOG_S)
   const int nmax = max(D.n, max(D.me, D.mi));
   for (int i = gtid; i < nmax; i += gstride) {
-    const MeritParts Mp = merit_at(D, I.xt, I.st, I.P.xl, I.P.xu, I.geqt, I.hint, i);
-    tg += Mp.tg;
-    th += Mp.th;
-    ls += Mp.ls;
-    lxl += Mp.lxl;
-    lxu += Mp.lxu;
+    if (i < D.me) tg += fabs(I.geqt[i]);
+    if (i < D.mi) {
+      th += fabs(I.hint[i] + I.st[i]);
+      lg.add(I.st[i]);
+    }
+    if (i < D.n) {
+      if (isfinite(I.P.xl[i])) lg.add(I.xt[i] - I.P.xl[i]);
+      if (isfinite(I.P.xu[i])) lg.add(I.P.xu[i] - I.xt[i]);
+    }
   }
-  const int slot[5] = {R_TH_G, R_TH_H, R_LOG_S, R_LOG_XL, R_LOG_XU};
-  const int op[5] = {OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM};
-  double v[5] = {tg, th, ls, lxl, lxu};
-  block_reduce_atomic<5>(I.R, slot, op, v);
+  const int slot[3] = {R_TH_G, R_TH_H, R_LOG_S};
+  const int op[3] = {OP_SUM, OP_SUM, OP_SUM};
+  double v[3] = {tg, th, lg.value()};
+  block_reduce_atomic<3>(I.R, slot, op, v);
 }
 // filter acceptance (Ipopt: switching condition with the Armijo test on phi, else sufficient
 // decrease in theta or phi against the filter); backtrack by halves down to alpha_min
@@ -1467,6 +1539,9 @@ struct ipm_batch_s {
   int *h_active = nullptr;                       // pinned
   int gx = 1, gx_gen = 1, max_ns = 1, fmax_entries = 0;
   size_t fact_smem = 0;
+  int gx_cond = 1;  // blocks per instance of the condensation
+  size_t solve_smem = 0;  // dynamic shared memory of the solve launches: the right-hand side
+  int solve_ycap = 0;     // doubles of it
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches_per_sweep = 0;
@@ -1517,6 +1592,7 @@ int b_smem_limits() {
   static bool done = false;
   if (done) return IPM_OK;
   CK(cudaFuncSetAttribute(k_b_fact_inst, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  CK(cudaFuncSetAttribute(k_b_solve_inst, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   done = true;
   return IPM_OK;
 }
@@ -1549,7 +1625,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   };
   // one launch for the one-block instances on s and, in a concurrent branch, one cluster launch
   // for the big ones (order: small instances first, then big)
-  auto split = [&](auto kernel, size_t smem, auto... args) -> int {
+  auto split = [&](auto kernel, int nt, size_t smem, auto... args) -> int {
     if (B->n_big) {
       CK(cudaEventRecord(B->ev_fork, s));
       CK(cudaStreamWaitEvent(B->side, B->ev_fork, 0));
@@ -1560,7 +1636,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(B->n_big * B_CL_BIG);
-      cfg.blockDim = dim3(B_NT);
+      cfg.blockDim = dim3(nt);
       cfg.dynamicSmemBytes = smem;
       cfg.stream = B->side;
       cfg.attrs = at;
@@ -1569,7 +1645,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
       L(1);
     }
     if (B->n_small) {
-      kernel<<<B->n_small, B_NT, smem, s>>>(bi, ctl, args..., (const int *)B->d_order);
+      kernel<<<B->n_small, nt, smem, s>>>(bi, ctl, args..., (const int *)B->d_order);
       L(1);
     }
     CKL();
@@ -1582,7 +1658,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   auto solve = [&](int phase) -> int {
     k_b_jt_rhs<<<g2, blk, 0, s>>>(bi, ctl, phase);
     if (phase == PH_SOLVE) CKR(rec(2));
-    CKR(split(k_b_solve_inst, (size_t)0, phase));
+    CKR(split(k_b_solve_inst, B_NT, B->solve_smem, phase, B->solve_ycap));
     if (phase == PH_SOLVE) CKR(rec(3));
     k_b_recover_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
     L(2);
@@ -1613,7 +1689,9 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_aug_rhs<<<g2, blk, 0, s>>>(bi, ctl, B->opt.gamma);
     k_b_scale_jv<<<g2, blk, 0, s>>>(bi, ctl);
     CKR(rec(r == 0 ? 0 : 4));
-    CKR(split(k_b_fact_inst, B->fact_smem));
+    k_b_condense<<<dim3(B->gx_cond, C), blk, 0, s>>>(bi, ctl);
+    L(1);
+    CKR(split(k_b_fact_inst, B_NT_F, B->fact_smem));
     CKR(rec(r == 0 ? 1 : 5));
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(3);
@@ -1624,7 +1702,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_cgi_rhs<<<g2, blk, 0, s>>>(bi, ctl);
     L(1);
     CKR(rec(2));
-    CKR(split(k_b_solve_inst, (size_t)0, (int)PH_CGI));
+    CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CGI, B->solve_ycap));
     CKR(rec(3));
     k_b_cgi_start<<<g2, blk, 0, s>>>(bi, ctl);
     k_b_ctl_cgi<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.cg_rtol);
@@ -1632,7 +1710,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     for (int r = 0; r < B_CG_ROUNDS; ++r) {
       k_b_cg_u<<<g2, blk, 0, s>>>(bi, ctl);
       L(1);
-      CKR(split(k_b_solve_inst, (size_t)0, (int)PH_CG));
+      CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CG, B->solve_ycap));
       k_b_cg_sp<<<g2, blk, 0, s>>>(bi, ctl);
       k_b_ctl_cg_alpha<<<gc, 128, 0, s>>>(bi, ctl, C);
       k_b_cg_xr<<<g2, blk, 0, s>>>(bi, ctl);
@@ -1642,7 +1720,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     }
     k_b_cgx_rhs<<<g2, blk, 0, s>>>(bi, ctl);
     L(1);
-    CKR(split(k_b_solve_inst, (size_t)0, (int)PH_CGX));
+    CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CGX, B->solve_ycap));
     k_b_cgx_dz<<<g2, blk, 0, s>>>(bi, ctl);
     k_b_ctl_cgx<<<gc, 128, 0, s>>>(ctl, C);
     L(2);
@@ -1825,6 +1903,14 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     max_elems = std::max({max_elems, M.n, (int)mi, (int)m, M.nnzJ, M.nnzW, 2 * M.nbr});
     B->max_ns = std::max(B->max_ns, S->nsuper);
   }
+  {
+    int64_t max_slots = 1;
+    for (int i = 0; i < count; ++i) {
+      ipm_sym_t S = B->syms[B->pat[i]];
+      max_slots = std::max<int64_t>(max_slots, S->panel_len);
+    }
+    B->gx_cond = std::max(1, std::min(64, (int)((max_slots + B_BLOCK * 4 - 1) / (B_BLOCK * 4))));
+  }
   B->dpool_len = dp.n;
   B->ipool_len = ip.n;
   // up to 32 elements per thread and at most 16 blocks per instance: phase-masked launches stay
@@ -1859,8 +1945,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   }
   // update pairs of every pattern: for each supernode, the pairs (i, j) of its rows below the
   // diagonal block and the slot of the target panel that entry (i, j) of L21 L21^T updates
-  std::vector<int *> pptr(B->syms.size()), psn(B->syms.size()), pij(B->syms.size()),
-      ptgt(B->syms.size());
+  std::vector<int *> pptr(B->syms.size()), pa(B->syms.size()), pb(B->syms.size()),
+      pm(B->syms.size()), ptgt(B->syms.size());
   std::vector<int *> cslot(B->syms.size()), ccol(B->syms.size()), cgp(B->syms.size());
   std::vector<int2 *> citm(B->syms.size());
   std::vector<int> ncslot(B->syms.size());
@@ -1881,25 +1967,26 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     std::vector<int> lsn(ns);
     if (ns && cudaMemcpy(lsn.data(), S->level_sn, sizeof(int) * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(IPM_ERR_CUDA);
-    std::vector<int> hp(S->nlevels + 1, 0), hsn, hij, htg;
+    std::vector<int> hp(S->nlevels + 1, 0), ha, hb, hm, htg;
     for (int L = 0; L < S->nlevels; ++L) {
       for (int qq = S->h_level_ptr[L]; qq < S->h_level_ptr[L + 1]; ++qq) {
         const int sn_ = lsn[qq];
         const int w = sp[sn_ + 1] - sp[sn_], rb = rp[sn_], ld = rp[sn_ + 1] - rb;
-        if (ld >= 65536) return fail(IPM_ERR_BAD_ARG);
+        if (ld >= (1 << 23) || w > 255) return fail(IPM_ERR_BAD_ARG);
         for (int j = w; j < ld; ++j) {
           const int col = rows[rb + j], ts = sn[col];
           const int tb = rp[ts], tld = rp[ts + 1] - tb;
           const int *tr = rows.data() + tb;
           for (int i = j; i < ld; ++i) {
             const int r = (int)(std::lower_bound(tr, tr + tld, rows[rb + i]) - tr);
-            hsn.push_back(sn_);
-            hij.push_back(i << 16 | j);
+            ha.push_back((int)(lp[sn_] + i));
+            hb.push_back((int)(lp[sn_] + j));
+            hm.push_back(ld << 8 | w);
             htg.push_back((int)(lp[ts] + (int64_t)(col - sp[ts]) * tld + r));
           }
         }
       }
-      hp[L + 1] = (int)hij.size();
+      hp[L + 1] = (int)ha.size();
     }
     auto upi = [&](int **dst, const std::vector<int> &v) -> int {
       if (cudaMalloc((void **)dst, sizeof(int) * std::max<size_t>(v.size(), 1)) != cudaSuccess)
@@ -1917,6 +2004,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
         (S->nitems && cudaMemcpy(items.data(), S->items, sizeof(int2) * S->nitems,
                                  cudaMemcpyDeviceToHost) != cudaSuccess))
       return fail(IPM_ERR_CUDA);
+    std::vector<int> hperm(S->n);
+    if (cudaMemcpy(hperm.data(), S->perm, sizeof(int) * S->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IPM_ERR_CUDA);
     std::vector<std::pair<int, int>> order;  // (-count, slot)
     std::vector<int> diagcol(S->panel_len, -1);
     for (int sn_ = 0; sn_ < ns; ++sn_) {
@@ -1925,7 +2015,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
         for (int r = c; r < ld; ++r) {
           const int slot = (int)(lp[sn_] + (int64_t)c * ld + r);
           order.push_back({-(sptr_items[slot + 1] - sptr_items[slot]), slot});
-          if (r == c) diagcol[slot] = sp[sn_] + c;
+          if (r == c) diagcol[slot] = hperm[sp[sn_] + c];
         }
     }
     std::sort(order.begin(), order.end());
@@ -1954,8 +2044,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
       hgp[g + 1] = (int)hci.size();
     }
     int r1 = upi(&pptr[q], hp);
-    if (r1 == IPM_OK) r1 = upi(&psn[q], hsn);
-    if (r1 == IPM_OK) r1 = upi(&pij[q], hij);
+    if (r1 == IPM_OK) r1 = upi(&pa[q], ha);
+    if (r1 == IPM_OK) r1 = upi(&pb[q], hb);
+    if (r1 == IPM_OK) r1 = upi(&pm[q], hm);
     if (r1 == IPM_OK) r1 = upi(&ptgt[q], htg);
     if (r1 == IPM_OK) r1 = upi(&cslot[q], hcs);
     if (r1 == IPM_OK) r1 = upi(&ccol[q], hcc);
@@ -2014,8 +2105,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.nlevels = S->nlevels;
     I.lvl_ptr = lvl[B->pat[i]];
     I.lpair_ptr = pptr[B->pat[i]];
-    I.pair_sn = psn[B->pat[i]];
-    I.pair_ij = pij[B->pat[i]];
+    I.pair_a = pa[B->pat[i]];
+    I.pair_b = pb[B->pat[i]];
+    I.pair_m = pm[B->pat[i]];
     I.pair_tgt = ptgt[B->pat[i]];
     I.cslot = cslot[B->pat[i]];
     I.ccol = ccol[B->pat[i]];
@@ -2080,7 +2172,17 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   for (ipm_sym_t S : B->syms) max_w = std::max(max_w, S->max_w);
   B->fact_smem = sizeof(double) *
                  std::max((size_t)max_w * max_w + (size_t)32 * (max_w + 1),
-                          (size_t)(B_NT / 32) * (B_WS * B_WS + B_WS));
+                          (size_t)(B_NT_F / 32) * (B_WS * B_WS + B_WS));
+  // the solves keep the right-hand side in shared memory for instances with n <= 3,800 (with
+  // the 43 KB of per-warp staging, three blocks of the solve kernel per SM still fit); larger
+  // instances use global memory
+  {
+    int max_n = 0;
+    for (int i = 0; i < count; ++i)
+      if (opfs[i]->M.n <= 3800) max_n = std::max(max_n, opfs[i]->M.n);
+    B->solve_ycap = max_n;
+    B->solve_smem = sizeof(double) * (size_t)B->solve_ycap;
+  }
   rc = init_instances(B);
   if (rc == IPM_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = IPM_ERR_CUDA;
   if (rc != IPM_OK) return fail(rc);

@@ -190,6 +190,35 @@ __device__ __forceinline__ MeritParts merit_at(const Dims &D, const double *x, c
   return M;
 }
 
+// Sum of logarithms taken as the logarithm of a product: each factor is split on its bits into
+// a mantissa in [1, 2) and an exponent, the mantissas are multiplied (one FP64 multiply per
+// factor, the product renormalized on its bits) and the exponents added as integers; value()
+// returns e ln 2 + log(m) (ln 2 in two parts, the first with 21 significant bits so that e times
+// it is exact).  One log per thread instead of one per factor: on this GPU a double log is a
+// few dozen FP64 instructions at 64 cycles each per warp.  A factor that is not a positive
+// normal number adds its log directly.
+struct LogSum {
+  double m = 1.0, direct = 0.0;
+  long long e = 0;
+  __device__ __forceinline__ void add(double v) {
+    const long long b = __double_as_longlong(v);
+    const long long ex = b >> 52;  // includes the sign bit: negative v gives ex < 0
+    if (ex <= 0 || ex >= 0x7ff) {
+      direct += log(v);
+      return;
+    }
+    m *= __longlong_as_double((b & 0xfffffffffffffLL) | 0x3ff0000000000000LL);
+    const long long bm = __double_as_longlong(m);
+    e += ex - 1023 + ((bm >> 52) - 1023);
+    m = __longlong_as_double((bm & 0xfffffffffffffLL) | 0x3ff0000000000000LL);
+  }
+  __device__ __forceinline__ double value() const {
+    const double ln2_hi = 0x1.62e42p-1, ln2_lo = 0x1.fdf473de6af28p-22;
+    const double fe = (double)e;
+    return fe * ln2_hi + (fe * ln2_lo + log(m)) + direct;
+  }
+};
+
 // Newton right-hand sides and diagonals:
 //   sigma_x = zl/(x-xl) + zu/(xu-x); r1 = sig grad + J~^T lambda - mu/(x-xl) + mu/(xu-x)
 //   r2 = z - mu/s; r4 = h' + s; Ds = v/s
