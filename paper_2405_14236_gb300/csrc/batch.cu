@@ -828,98 +828,6 @@ __device__ void warp_bwd_sn(const BI &I, double *Y, int s, double *zs) {
   __syncwarp();
 }
 
-// Narrow supernodes with few rows below are solved one per thread (the many width-1 to width-4
-// supernodes of the deep levels: one FP64 warp instruction then serves up to 32 supernodes
-// instead of one).  The same arithmetic as the warp path, in registers.
-static constexpr int B_TS = 4, B_TR = 48;
-__device__ __forceinline__ bool thread_solved(const BI &I, int s) {
-  const int w = I.sptr[s + 1] - I.sptr[s];
-  return w <= B_TS && I.srow_ptr[s + 1] - I.srow_ptr[s] - w <= B_TR;
-}
-__device__ void thread_fwd_sn(const BI &I, double *Y, int s) {
-  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
-  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
-  const int *rows = I.srow + rb;
-  const double *P = I.Lx + I.lptr[s];
-  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
-  double ys[B_TS];
-#pragma unroll
-  for (int k = 0; k < B_TS; ++k) ys[k] = k < w ? Y[f + k] : 0.0;
-#pragma unroll
-  for (int k = 0; k < B_TS; ++k)
-    if (k < w) {
-      ys[k] *= rinv[k];
-#pragma unroll
-      for (int i = k + 1; i < B_TS; ++i)
-        if (i < w) ys[i] -= Dd[i + k * w] * ys[k];
-    }
-#pragma unroll
-  for (int k = 0; k < B_TS; ++k)
-    if (k < w) Y[f + k] = ys[k];
-  // rows four at a time: their loads are in flight together
-  int i = w;
-  for (; i + 4 <= ld; i += 4) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < B_TS; ++k)
-      if (k < w) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] += P[i + u + (int64_t)k * ld] * ys[k];
-      }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) atomicAdd(&Y[rows[i + u]], -acc[u]);
-  }
-  for (; i < ld; ++i) {
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < B_TS; ++k)
-      if (k < w) acc += P[i + (int64_t)k * ld] * ys[k];
-    atomicAdd(&Y[rows[i]], -acc);
-  }
-}
-__device__ void thread_bwd_sn(const BI &I, double *Y, int s) {
-  const int f = I.sptr[s], w = I.sptr[s + 1] - f;
-  const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
-  const int *rows = I.srow + rb;
-  const double *P = I.Lx + I.lptr[s];
-  const double *Dd = I.Dx + I.dptr[s], *rinv = Dd + w * w;
-  double zs[B_TS] = {0.0, 0.0, 0.0, 0.0};
-  int i = w;
-  for (; i + 4 <= ld; i += 4) {  // four rows' loads in flight, summed in row order
-    double yi[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) yi[u] = Y[rows[i + u]];
-#pragma unroll
-    for (int k = 0; k < B_TS; ++k)
-      if (k < w) {
-        double p[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) p[u] = P[i + u + (int64_t)k * ld];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) zs[k] += p[u] * yi[u];
-      }
-  }
-  for (; i < ld; ++i) {
-    const double yi = Y[rows[i]];
-#pragma unroll
-    for (int k = 0; k < B_TS; ++k)
-      if (k < w) zs[k] += P[i + (int64_t)k * ld] * yi;
-  }
-#pragma unroll
-  for (int k = 0; k < B_TS; ++k)
-    if (k < w) zs[k] = Y[f + k] - zs[k];
-#pragma unroll
-  for (int k = B_TS - 1; k >= 0; --k)
-    if (k < w) {
-      zs[k] *= rinv[k];
-#pragma unroll
-      for (int j = 0; j < k; ++j) zs[j] -= Dd[k + j * w] * zs[k];
-    }
-#pragma unroll
-  for (int k = 0; k < B_TS; ++k)
-    if (k < w) Y[f + k] = zs[k];
-}
-
 // phase SOLVE: dx = K^{-1} t; phase REFINE: cx = K^{-1} t (t from k_b_jt_rhs), one cluster per
 // instance: gather by the ordering, forward levels, backward levels, scatter
 __global__ void __launch_bounds__(B_NT, 3)
@@ -943,19 +851,11 @@ __global__ void __launch_bounds__(B_NT, 3)
   for (int k = gt; k < I.D.n; k += gnt) Y[k] = I.t[I.perm[k]];
   cluster.sync();
   for (int L = 0; L < I.nlevels; ++L) {
-    const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
-    for (int q = q0 + gt; q < q1; q += gnt)
-      if (thread_solved(I, I.level_sn[q])) thread_fwd_sn(I, Y, I.level_sn[q]);
-    for (int q = q0 + gw; q < q1; q += gnw)
-      if (!thread_solved(I, I.level_sn[q])) warp_fwd_sn(I, Y, I.level_sn[q], ys);
+    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_fwd_sn(I, Y, I.level_sn[q], ys);
     cluster.sync();
   }
   for (int L = I.nlevels - 1; L >= 0; --L) {
-    const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
-    for (int q = q0 + gt; q < q1; q += gnt)
-      if (thread_solved(I, I.level_sn[q])) thread_bwd_sn(I, Y, I.level_sn[q]);
-    for (int q = q0 + gw; q < q1; q += gnw)
-      if (!thread_solved(I, I.level_sn[q])) warp_bwd_sn(I, Y, I.level_sn[q], ys);
+    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_bwd_sn(I, Y, I.level_sn[q], ys);
     cluster.sync();
   }
   double *x = phase == PH_SOLVE || phase == PH_CGI || phase == PH_CGX ? I.dx
@@ -2142,7 +2042,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   };
   up(&B->d_bi, hbi);
   {
-    // instances whose supernode count exceeds 1.5x the median are "big": their factorization and
+    // instances whose supernode count exceeds 1.2x the median are "big": their factorization and
     // solves run on a cluster of B_CL_BIG blocks in a second branch of the sweep, concurrently
     // with the one-block instances, so that they do not set the length of every sweep
     std::vector<int> order(count);
@@ -2152,7 +2052,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     });
     const int med = B->syms[B->pat[order[count / 2]]]->nsuper;
     int nbig = 0;
-    while (nbig < count && B->syms[B->pat[order[nbig]]]->nsuper * 2 > 3 * med) ++nbig;
+    while (nbig < count && B->syms[B->pat[order[nbig]]]->nsuper * 5 > 6 * med) ++nbig;
     std::vector<int> ord2(order.begin() + nbig, order.end());  // small ones, biggest first
     ord2.insert(ord2.end(), order.begin(), order.begin() + nbig);
     B->n_big = nbig;
