@@ -641,8 +641,9 @@ def run_gpu(args, rank, world, local_rank):
         line["plain"] = plain_measure([grids[i // 2] if i % 2 == 0 or ns == len(grids)
                                        else grids[ns + i // 2] for i in range(4)])
         line["plain"]["batched_speedup"] = value / line["plain"]["value"]
-    line["batch_regularized"] = batch_form_measure(grids)
-    line["batch_hykkt"] = batch_form_measure(grids, kkt="hykkt")
+    if not args.no_forms:
+        line["batch_regularized"] = batch_form_measure(grids)
+        line["batch_hykkt"] = batch_form_measure(grids, kkt="hykkt")
     if not args.no_warm:
         line["warm"] = warm_measure()
         if "plain" in line:
@@ -825,6 +826,8 @@ def main():
     ap.add_argument("--no-kkt", action="store_true", help="skip the 10k KKT-solve kernel line")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-problem GPU IPM")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other batched KKT forms (dual-regularized, HyKKT)")
     ap.add_argument("--kkt-only", action="store_true",
                     help="print only the 10k-bus KKT-solve leg (profiling)")
     ap.add_argument("--batch-scen", type=int, default=256,
