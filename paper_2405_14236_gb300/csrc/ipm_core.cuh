@@ -14,7 +14,7 @@ namespace cipm {
 static constexpr double KAPPA1 = 1e-2, KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5;
 static constexpr double TAU_MIN = 0.99, S_MAX = 100.0, GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-8;
 static constexpr double S_THETA = 1.1, S_PHI = 2.3, DELTA_SW = 1.0, ETA_PHI = 1e-8;
-static constexpr double GAMMA_ALPHA = 0.05, KAPPA_SIGMA = 1e10;
+static constexpr double GAMMA_ALPHA = 0.05, KAPPA_SIGMA = 1e10, KAPPA_SIGMA_INV = 1.0 / KAPPA_SIGMA;
 
 // ------------------------------------------------------------------ reductions into R[]
 enum {
@@ -222,28 +222,31 @@ struct LogSum {
 // Newton right-hand sides and diagonals:
 //   sigma_x = zl/(x-xl) + zu/(xu-x); r1 = sig grad + J~^T lambda - mu/(x-xl) + mu/(xu-x)
 //   r2 = z - mu/s; r4 = h' + s; Ds = v/s
+// A denominator used twice is inverted once (an FP64 division is a chain of about ten FP64
+// instructions here, a multiply one).
 __device__ __forceinline__ void newton_rhs_at(const Dims &D, const It &P, double sig, double mu,
                                               double *sigma, double *r1, double *r2, double *r4,
                                               double *Ds, int i) {
   if (i < D.n) {
     double sx = 0.0, r = sig * P.grad[i] + P.jtl[i];
     if (isfinite(P.xl[i])) {
-      double dl = P.x[i] - P.xl[i];
-      sx += P.zl[i] / dl;
-      r -= mu / dl;
+      const double il = 1.0 / (P.x[i] - P.xl[i]);
+      sx += P.zl[i] * il;
+      r -= mu * il;
     }
     if (isfinite(P.xu[i])) {
-      double du = P.xu[i] - P.x[i];
-      sx += P.zu[i] / du;
-      r += mu / du;
+      const double iu = 1.0 / (P.xu[i] - P.x[i]);
+      sx += P.zu[i] * iu;
+      r += mu * iu;
     }
     sigma[i] = sx;
     r1[i] = r;
   }
   if (i < D.mi) {
-    r2[i] = P.z[i] - mu / P.s[i];
+    const double is = 1.0 / P.s[i];
+    r2[i] = P.z[i] - mu * is;
     r4[i] = P.hin[i] + P.s[i];
-    Ds[i] = P.v[i] / P.s[i];
+    Ds[i] = P.v[i] * is;
   }
 }
 
@@ -291,22 +294,25 @@ __device__ __forceinline__ void recover_at(const StepArgs &A, int i) {
   }
   if (i < D.n) {
     double dx = A.dx[i];
+    // dzl = (mu - zl dx) / (x - xl) - zl, dzu = (mu + zu dx) / (xu - x) - zu: one division each
     if (isfinite(A.P.xl[i])) {
-      double dl = A.P.x[i] - A.P.xl[i];
-      A.dzl[i] = A.mu / dl - A.P.zl[i] - A.P.zl[i] / dl * dx;
+      const double dl = A.P.x[i] - A.P.xl[i];
+      A.dzl[i] = fma(-A.P.zl[i], dx, A.mu) / dl - A.P.zl[i];
     } else {
       A.dzl[i] = 0.0;
     }
     if (isfinite(A.P.xu[i])) {
-      double du = A.P.xu[i] - A.P.x[i];
-      A.dzu[i] = A.mu / du - A.P.zu[i] + A.P.zu[i] / du * dx;
+      const double du = A.P.xu[i] - A.P.x[i];
+      A.dzu[i] = fma(A.P.zu[i], dx, A.mu) / du - A.P.zu[i];
     } else {
       A.dzu[i] = 0.0;
     }
   }
 }
 
-// fraction to the boundary (ratios) and the directional derivative of phi, element i
+// fraction to the boundary (ratios) and the directional derivative of phi, element i.  A ratio
+// tau u / |d| only matters below 1 (the step bounds start at 1): it is divided out only when
+// tau u < |d|, which near convergence leaves most elements without a division.
 struct FtbParts {
   double ap, az, gx, gs;
 };
@@ -314,25 +320,30 @@ __device__ __forceinline__ FtbParts ftb_at(const StepArgs &A, double tau, double
   const Dims &D = A.D;
   FtbParts F{1.0, 1.0, 0.0, 0.0};
   if (i < D.n) {
-    double x = A.P.x[i], dx = A.dx[i];
+    const double x = A.P.x[i], dx = A.dx[i];
     F.gx = sig * A.P.grad[i] * dx;
-    if (isfinite(A.P.xl[i])) {
-      double dl = x - A.P.xl[i];
-      if (dx < 0) F.ap = fmin(F.ap, -tau * dl / dx);
-      if (A.dzl[i] < 0) F.az = fmin(F.az, -tau * A.P.zl[i] / A.dzl[i]);
-      F.gx -= A.mu * dx / dl;
+    const bool hl = isfinite(A.P.xl[i]), hu = isfinite(A.P.xu[i]);
+    const double dl = hl ? x - A.P.xl[i] : 1.0, du = hu ? A.P.xu[i] - x : 1.0;
+    if (hl) {
+      if (dx < 0 && tau * dl < -dx) F.ap = fmin(F.ap, -tau * dl / dx);
+      const double dz = A.dzl[i];
+      if (dz < 0 && tau * A.P.zl[i] < -dz) F.az = fmin(F.az, -tau * A.P.zl[i] / dz);
     }
-    if (isfinite(A.P.xu[i])) {
-      double du = A.P.xu[i] - x;
-      if (dx > 0) F.ap = fmin(F.ap, tau * du / dx);
-      if (A.dzu[i] < 0) F.az = fmin(F.az, -tau * A.P.zu[i] / A.dzu[i]);
-      F.gx += A.mu * dx / du;
+    if (hu) {
+      if (dx > 0 && tau * du < dx) F.ap = fmin(F.ap, tau * du / dx);
+      const double dz = A.dzu[i];
+      if (dz < 0 && tau * A.P.zu[i] < -dz) F.az = fmin(F.az, -tau * A.P.zu[i] / dz);
     }
+    // mu dx (1/du - 1/dl) with one division when both bounds exist
+    if (hl && hu) F.gx += A.mu * dx * ((dl - du) / (dl * du));
+    else if (hl) F.gx -= A.mu * dx / dl;
+    else if (hu) F.gx += A.mu * dx / du;
   }
   if (i < D.mi) {
-    if (A.ds[i] < 0) F.ap = fmin(F.ap, -tau * A.P.s[i] / A.ds[i]);
-    if (A.dv[i] < 0) F.az = fmin(F.az, -tau * A.P.v[i] / A.dv[i]);
-    F.gs = -A.mu * A.ds[i] / A.P.s[i];
+    const double ds = A.ds[i], dv = A.dv[i];
+    if (ds < 0 && tau * A.P.s[i] < -ds) F.ap = fmin(F.ap, -tau * A.P.s[i] / ds);
+    if (dv < 0 && tau * A.P.v[i] < -dv) F.az = fmin(F.az, -tau * A.P.v[i] / dv);
+    F.gs = -A.mu * ds / A.P.s[i];
   }
   return F;
 }
@@ -354,27 +365,29 @@ __device__ __forceinline__ void accept_at(const StepArgs &A, double alpha, doubl
   if (i < D.n) {
     double x = xt[i];
     A.P.x[i] = x;
+    // the kappa_Sigma band [mu / (kappa c), kappa mu / c] from one division mu / c
     if (isfinite(A.P.xl[i])) {
-      double dl = x - A.P.xl[i];
-      double zl = A.P.zl[i] + az * A.dzl[i];
-      A.P.zl[i] = fmin(fmax(zl, mu / (KAPPA_SIGMA * dl)), KAPPA_SIGMA * mu / dl);
+      const double q = mu / (x - A.P.xl[i]);
+      const double zl = A.P.zl[i] + az * A.dzl[i];
+      A.P.zl[i] = fmin(fmax(zl, q * KAPPA_SIGMA_INV), KAPPA_SIGMA * q);
     } else {
       A.P.zl[i] = 0.0;
     }
     if (isfinite(A.P.xu[i])) {
-      double du = A.P.xu[i] - x;
-      double zu = A.P.zu[i] + az * A.dzu[i];
-      A.P.zu[i] = fmin(fmax(zu, mu / (KAPPA_SIGMA * du)), KAPPA_SIGMA * mu / du);
+      const double q = mu / (A.P.xu[i] - x);
+      const double zu = A.P.zu[i] + az * A.dzu[i];
+      A.P.zu[i] = fmin(fmax(zu, q * KAPPA_SIGMA_INV), KAPPA_SIGMA * q);
     } else {
       A.P.zu[i] = 0.0;
     }
   }
   if (i < D.mi) {
-    double s = st[i];
+    const double s = st[i];
     A.P.s[i] = s;
     A.P.z[i] += alpha * A.dz[i];
-    double v = A.P.v[i] + az * A.dv[i];
-    A.P.v[i] = fmin(fmax(v, mu / (KAPPA_SIGMA * s)), KAPPA_SIGMA * mu / s);
+    const double q = mu / s;
+    const double v = A.P.v[i] + az * A.dv[i];
+    A.P.v[i] = fmin(fmax(v, q * KAPPA_SIGMA_INV), KAPPA_SIGMA * q);
   }
   if (i < D.me) A.P.y[i] += alpha * dy[i];
 }
