@@ -462,12 +462,14 @@ __global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
 }
 
 // ------------------------------------------------------------------ per-instance numeric kernels
-// One block per instance, level by level through the supernodal elimination tree (deepest level
-// first for the factorization and the forward solve, root first for the backward solve): the
-// supernodes of a level are independent, so a barrier between levels is the only
-// synchronization.  Narrow supernodes (w <= B_WS) take one warp each; wider ones use the whole
-// block.  Contributions into other supernodes' panels (and into y) from one level are added
-// atomically, since supernodes of a level may share targets.  No waits on other blocks.
+// One block per instance (a cluster of blocks for the big instances), level by level through the
+// supernodal elimination tree (deepest level first for the factorization and the forward solve,
+// root first for the backward solve): the supernodes of a level are independent, so a barrier
+// between levels (block or cluster barrier) is the only synchronization.  In the factorization
+// narrow supernodes (w <= B_WS) take one warp each and wider ones the whole block; in the solves
+// every supernode takes one warp.  Contributions into other supernodes' panels (and into y) from
+// one level are added atomically, since supernodes of a level may share targets.  No waits on
+// blocks outside the instance's cluster.
 static constexpr int B_WS = 16;
 static constexpr int B_NT = 512;    // threads of the per-instance solve kernel
 static constexpr int B_NT_F = 512;  // threads of the per-instance factorization kernel
@@ -745,7 +747,6 @@ __global__ void __launch_bounds__(B_NT_F, 3)
   }
 }
 
-// y <- L^{-T} L^{-1} y for one supernode, one warp (ys: w doubles of this warp's shared memory)
 // L11 and the reciprocal pivots of a supernode of width w <= B_WS copied to this warp's shared
 // staging area with one load per lane (the triangular loops then read shared memory instead of
 // issuing one global round trip per column); wider supernodes read them in place
@@ -757,6 +758,8 @@ __device__ __forceinline__ const double *stage_diag(const double *Dd, int w, dou
   return stage;
 }
 
+// forward step of one supernode, one warp: y_own <- L11^{-1} y_own, y_below -= L21 y_own (ys:
+// this warp's shared staging, w doubles, then L11 for w <= B_WS)
 __device__ void warp_fwd_sn(const BI &I, double *Y, int s, double *ys) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
@@ -790,6 +793,7 @@ __device__ void warp_fwd_sn(const BI &I, double *Y, int s, double *ys) {
   __syncwarp();
 }
 
+// backward step of one supernode, one warp: y_own <- L11^{-T} (y_own - L21^T y_below)
 __device__ void warp_bwd_sn(const BI &I, double *Y, int s, double *zs) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
