@@ -123,8 +123,8 @@ __global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0, int
 }
 
 // ------------------------------------------------------------------ model evaluation
-// mode 0: at x with J and grad f (phase EVAL); mode 1: W at x with the scaled multipliers
-// (phase BUILD); mode 2: at the trial point, values only (phase LS)
+// mode 0: at x with J and grad f (the set-up); mode 1: J, grad f and W (with the scaled
+// multipliers) at x (phase EVAL); mode 2: at the trial point, values only (phase LS)
 struct EvalPtrs {
   const double *x, *y, *z;
   double sigf, *f, *grad, *g, *h, *Jv, *Wv;
@@ -134,8 +134,7 @@ __device__ __forceinline__ EvalPtrs eval_ptrs(const BI &I, const BCtl &c, int mo
   if (mode == 0) {
     E = EvalPtrs{I.P.x, nullptr, nullptr, 1.0, I.f, I.P.grad, I.gs, I.hs, I.Jv, nullptr};
   } else if (mode == 1) {
-    E = EvalPtrs{I.P.x, I.lamw, I.lamw + I.D.me0, c.sig, I.ft, nullptr, I.gst, I.hst, nullptr,
-                 I.Wv};
+    E = EvalPtrs{I.P.x, I.lamw, I.lamw + I.D.me0, c.sig, I.f, I.P.grad, I.gs, I.hs, I.Jv, I.Wv};
   } else {
     E = EvalPtrs{I.xt, nullptr, nullptr, 1.0, I.ft, nullptr, I.gst, I.hst, nullptr, nullptr};
   }
@@ -265,10 +264,23 @@ __global__ void k_b_init_duals(const BI *bi, const BCtl *ctl) {
 }
 
 // ------------------------------------------------------------------ evaluation phase
+// multipliers of the model rows and their scaled copy (the weights of the constraint Hessians
+// in W); they depend only on the iterate, so W is evaluated together with J at x
 __global__ void k_b_lambda(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
   const int nrow = max(I.D.me0, I.D.mi0);
-  for (int k = gtid; k < nrow; k += gstride) lambda_at(I.D, I.P.y, I.P.z, I.lam, k);
+  for (int k = gtid; k < nrow; k += gstride) {
+    lambda_at(I.D, I.P.y, I.P.z, I.lam, k);
+    if (k < I.D.me0) I.lamw[k] = I.lam[k] * I.dscale[k];
+    if (k < I.D.mi0) I.lamw[I.D.me0 + k] = I.lam[I.D.me0 + k] * I.dscale[I.D.me0 + k];
+  }
+}
+// the reduction slots of the EVAL phase: sums and maxima from 0, minima from +infinity
+__global__ void k_b_rinit_eval(const BI *bi, const BCtl *ctl) {
+  const int b = blockIdx.x;
+  if (ctl[b].ph != PH_EVAL) return;
+  for (int k = threadIdx.x; k < R_COUNT; k += blockDim.x)
+    bi[b].R[k] = (k == R_SV_MIN || k == R_CL_MIN || k == R_CU_MIN) ? INFINITY : 0.0;
 }
 __global__ void k_b_jtu(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
@@ -384,10 +396,6 @@ __global__ void k_b_ctl_eval(const BI *bi, BCtl *ctl, int count, double tol, int
 }
 
 // ------------------------------------------------------------------ build phase
-__global__ void k_b_lamw(const BI *bi, const BCtl *ctl) {
-  B_PROLOGUE(PH_BUILD);
-  for (int r = gtid; r < I.m; r += gstride) I.lamw[r] = I.lam[r] * I.dscale[r];
-}
 __global__ void k_b_newton_rhs(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_BUILD);
   const Dims &D = I.D;
@@ -1568,23 +1576,18 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     L(2);
     return IPM_OK;
   };
-  // evaluate at x, optimality error, convergence, barrier update
-  eval(PH_EVAL, 0);
-  k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0, relax);
+  // evaluate f, grad f, g, h, J and W at x, optimality error, convergence, barrier update
   k_b_lambda<<<g2, blk, 0, s>>>(bi, ctl);
+  L(1);
+  eval(PH_EVAL, 1);
+  k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_EVAL, 0, relax);
   k_b_jtu<<<g2, blk, 0, s>>>(bi, ctl);
+  k_b_rinit_eval<<<C, 32, 0, s>>>(bi, ctl);
   L(3);
-  rreset(PH_EVAL, 0, R_COUNT, 0.0);
-  rreset(PH_EVAL, R_SV_MIN, R_SV_MIN + 1, INFINITY);
-  rreset(PH_EVAL, R_CL_MIN, R_CL_MIN + 1, INFINITY);
-  rreset(PH_EVAL, R_CU_MIN, R_CU_MIN + 1, INFINITY);
   k_b_errors<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_ctl_eval<<<gc, 128, 0, s>>>(bi, ctl, C, tol, B->max_iter);
   L(2);
-  // Hessian with the scaled multipliers, Newton right-hand sides
-  k_b_lamw<<<g2, blk, 0, s>>>(bi, ctl);
-  L(1);
-  eval(PH_BUILD, 1);
+  // Newton right-hand sides
   k_b_newton_rhs<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_ctl_build<<<gc, 128, 0, s>>>(ctl, C);
   L(2);
