@@ -515,6 +515,15 @@ def run_gpu(args, rank, world, local_rank):
     B = cp.Batch(opfs)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
+    # launch shapes chosen by measurement (outside the timed steps, like the symbolic analyses)
+    shape, autotune_s = None, 0.0
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune = B.autotune(sweeps=8)
+        autotune_s = time.perf_counter() - t0
+        best = tune["candidates"][tune["best"]]
+        shape = {k: best[k] for k in ("cluster", "threshold", "blocks_per_instance")}
+        shape["candidates"] = len(tune["candidates"])
     info = B.info()
     B.set_timing(True)
     for _ in range(args.warmup):
@@ -619,6 +628,7 @@ def run_gpu(args, rank, world, local_rank):
         "converged_per_step": conv, "iters_mean": float(np.mean(iters_mean)),
         "iters_max": iters_max, "sweeps_per_step": sweeps,
         "launches_per_sweep": B.info()["launches_per_sweep"], "init_s": init_s,
+        "launch_shape": shape, "autotune_s": autotune_s,
         "roofline": {"kernel": "k_b_fact_inst (condensation + factorization, every instance)",
                      "bound": "alu", "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": ach_tf / FP64_PEAK_TFLOPS,
@@ -826,6 +836,8 @@ def main():
     ap.add_argument("--no-kkt", action="store_true", help="skip the 10k KKT-solve kernel line")
     ap.add_argument("--no-plain", action="store_true", help="skip the single-problem GPU IPM")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes of the batched kernels")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other batched KKT forms (dual-regularized, HyKKT)")
     ap.add_argument("--kkt-only", action="store_true",

@@ -355,6 +355,16 @@ int ipm_batch_run(ipm_batch_t batch, int max_iter, int max_sweeps, int use_graph
  * steps.  Synchronizes. */
 int ipm_batch_results(ipm_batch_t batch, int *status, int *iters, double *obj, double *kkt_err,
                       int *n_factor, int *ls_steps);
+/* Autotuner of the batched launch shapes: for each candidate (cluster size 1, 2, 4 or 8 blocks for
+ * the big instances; "big" = supernode count above 1.5x or 1.2x the median; 0.5x, 1x or 2x the
+ * default blocks per instance of the element kernels) the sweep graph is captured, every instance
+ * is reset and `sweeps` sweeps are timed with CUDA events; the fastest shape is kept and every
+ * instance is put back at its starting point.  HOST outputs (any may be NULL when max_results is
+ * 0): *n_results = number of candidates; for the first max_results of them cfg[4 k .. 4 k + 3] =
+ * (cluster size, threshold numerator, denominator, blocks per instance) and ms_per_sweep[k];
+ * *best = index of the chosen one.  Synchronizes.  Returns IPM_ERR_BAD_ARG for sweeps < 1. */
+int ipm_batch_autotune(ipm_batch_t batch, int sweeps, int max_results, int *n_results, int *cfg,
+                       double *ms_per_sweep, int *best);
 /* HyKKT batches: CG iterations per instance since creation or the last reset into a HOST array
  * [count] (0 for the other forms).  Synchronizes. */
 int ipm_batch_cg_iters(ipm_batch_t batch, int *cg_iters);

@@ -61,6 +61,7 @@ _SIGS = {
     "ipm_batch_run": (I, [P, I, I, I]),
     "ipm_batch_results": (I, [P, P, P, P, P, P, P]),
     "ipm_batch_cg_iters": (I, [P, P]),
+    "ipm_batch_autotune": (I, [P, I, I, P, P, P, P]),
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
     "ipm_batch_destroy": (None, [P]),
@@ -422,6 +423,23 @@ class Batch:
         _check(lib().ipm_batch_cg_iters(self.h, p(cg)), "ipm_batch_cg_iters")
         return dict(status=st, iters=it, obj=obj, kkt_err=err, n_factor=nf, ls_steps=ls,
                     cg_iters=cg, sweeps=lib().ipm_batch_sweeps(self.h))
+
+    def autotune(self, sweeps=8):
+        """Times the candidate launch shapes (ipm_batch_autotune) and keeps the fastest; every
+        instance is back at its starting point afterwards.  Returns the candidates as dicts
+        (cluster, threshold, blocks_per_instance, ms_per_sweep) and the chosen index."""
+        cap = 64
+        cfg = np.zeros(4 * cap, np.int32)
+        ms = np.zeros(cap)
+        n, best = I(), I()
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_batch_autotune(self.h, int(sweeps), cap, ctypes.byref(n), p(cfg), p(ms),
+                                        ctypes.byref(best)), "ipm_batch_autotune")
+        out = [dict(cluster=int(cfg[4 * k]), threshold=(float(cfg[4 * k + 1]) / cfg[4 * k + 2]
+                                                         if cfg[4 * k + 2] else None),
+                    blocks_per_instance=int(cfg[4 * k + 3]), ms_per_sweep=float(ms[k]))
+               for k in range(min(n.value, cap))]
+        return dict(candidates=out, best=best.value)
 
     def x_all(self, out=None):
         """Every instance's x, concatenated (one gather and one copy); out: float64 numpy array."""

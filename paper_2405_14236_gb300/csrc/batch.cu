@@ -713,7 +713,6 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
 // instance.  Warps of the whole cluster share the narrow supernodes of a level; each block
 // collects the wide ones its warps met and factors them with all its threads; a cluster barrier
 // (release / acquire) separates the levels.
-static constexpr int B_CL_BIG = 4;       // cluster size of the big instances
 static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
 
 __global__ void __launch_bounds__(B_NT_F, 3)
@@ -1446,6 +1445,10 @@ struct ipm_batch_s {
   int *d_tickets = nullptr;                      // scratch counters (active count at [8])
   int *d_order = nullptr;  // small instances by decreasing supernode count, then the big ones
   int n_small = 0, n_big = 0;
+  // launch shapes (ipm_batch_autotune): cluster size of the big instances, "big" = supernode
+  // count above big_num / big_den times the median (big_den = 0: none), blocks per instance of
+  // the element kernels
+  int cl_big = 4, big_num = 6, big_den = 5;
   cudaStream_t side = nullptr;  // second branch of the sweep: the big instances
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *h_active = nullptr;                       // pinned
@@ -1544,10 +1547,10 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = B_CL_BIG;
+      at[0].val.clusterDim.x = B->cl_big;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(B->n_big * B_CL_BIG);
+      cfg.gridDim = dim3(B->n_big * B->cl_big);
       cfg.blockDim = dim3(nt);
       cfg.dynamicSmemBytes = smem;
       cfg.stream = B->side;
@@ -1677,6 +1680,40 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   CKL();
   B->launches_per_sweep = n;
   return IPM_OK;
+}
+
+// Instances whose supernode count exceeds big_num / big_den times the median are "big": their
+// factorization and solves run on a cluster of cl_big blocks in a second branch of the sweep,
+// concurrently with the one-block instances, so that they do not set the length of every sweep.
+// Writes the launch order (one-block instances by decreasing supernode count, then the big ones).
+int set_order(ipm_batch_t B) {
+  const int count = B->count;
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
+    return B->syms[B->pat[a]]->nsuper > B->syms[B->pat[b2]]->nsuper;
+  });
+  const int64_t med = B->syms[B->pat[order[count / 2]]]->nsuper;
+  int nbig = 0;
+  if (B->big_den > 0 && B->cl_big > 1)
+    while (nbig < count &&
+           (int64_t)B->syms[B->pat[order[nbig]]]->nsuper * B->big_den > B->big_num * med)
+      ++nbig;
+  std::vector<int> ord2(order.begin() + nbig, order.end());
+  ord2.insert(ord2.end(), order.begin(), order.begin() + nbig);
+  B->n_big = nbig;
+  B->n_small = count - nbig;
+  CK(cudaMemcpy(B->d_order, ord2.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+  return IPM_OK;
+}
+
+void drop_graph(ipm_batch_t B) {
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+  }
 }
 
 // starting point, scaling and multipliers of every instance (Ipopt: see ipm_state_create)
@@ -2048,24 +2085,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
       rc = IPM_ERR_CUDA;
   };
   up(&B->d_bi, hbi);
-  {
-    // instances whose supernode count exceeds 1.2x the median are "big": their factorization and
-    // solves run on a cluster of B_CL_BIG blocks in a second branch of the sweep, concurrently
-    // with the one-block instances, so that they do not set the length of every sweep
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
-      return B->syms[B->pat[a]]->nsuper > B->syms[B->pat[b2]]->nsuper;
-    });
-    const int med = B->syms[B->pat[order[count / 2]]]->nsuper;
-    int nbig = 0;
-    while (nbig < count && B->syms[B->pat[order[nbig]]]->nsuper * 5 > 6 * med) ++nbig;
-    std::vector<int> ord2(order.begin() + nbig, order.end());  // small ones, biggest first
-    ord2.insert(ord2.end(), order.begin(), order.begin() + nbig);
-    B->n_big = nbig;
-    B->n_small = count - nbig;
-    up(&B->d_order, ord2);
-  }
+  if (rc == IPM_OK && cudaMalloc(&B->d_order, sizeof(int) * count) != cudaSuccess) rc = IPM_ERR_OOM;
+  if (rc == IPM_OK) rc = set_order(B);
   if (rc == IPM_OK && cudaMalloc(&B->d_ctl, sizeof(BCtl) * count) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMalloc(&B->d_tickets, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMemset(B->d_tickets, 0, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_CUDA;
@@ -2170,6 +2191,77 @@ extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int us
   CKL();
   CK(cudaStreamSynchronize(s));
   return rc;
+}
+
+extern "C" int ipm_batch_autotune(ipm_batch_t B, int sweeps, int max_results, int *n_results,
+                                  int *cfg, double *ms_per_sweep, int *best) {
+  if (!B || sweeps < 1 || max_results < 0 || (max_results > 0 && (!cfg || !ms_per_sweep)))
+    return IPM_ERR_BAD_ARG;
+  struct Shape { int cl, num, den, gx; };
+  std::vector<Shape> cand;
+  const int gx0 = B->gx;
+  for (int gx : {std::max(1, gx0 / 2), gx0, std::min(16, 2 * gx0)}) {
+    if (!cand.empty() && cand.back().gx == gx) continue;
+    cand.push_back({1, 0, 0, gx});  // no clusters
+    for (int cl : {2, 4, 8})
+      for (int th : {0, 1}) cand.push_back({cl, th ? 3 : 6, th ? 2 : 5, gx});  // 1.5x, 1.2x
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool timing = B->timing;
+  B->timing = false;
+  int rc = IPM_OK, ibest = -1;
+  double tbest = INFINITY;
+  std::vector<double> times(cand.size(), INFINITY);
+  auto apply = [&](const Shape &c) -> int {
+    B->cl_big = c.cl;
+    B->big_num = c.num;
+    B->big_den = c.den;
+    B->gx = c.gx;
+    drop_graph(B);
+    return set_order(B);
+  };
+  for (size_t k = 0; k < cand.size() && rc == IPM_OK; ++k) {
+    rc = apply(cand[k]);
+    // first run captures the sweep graph; the second, from the starting point, is timed
+    if (rc == IPM_OK) rc = ipm_batch_reset(B);
+    if (rc == IPM_OK) rc = ipm_batch_run(B, B->max_iter, 1, 1);
+    if (rc == IPM_OK) rc = ipm_batch_reset(B);
+    if (rc != IPM_OK) break;
+    if (cudaEventRecord(e0, B->stream) != cudaSuccess) { rc = IPM_ERR_CUDA; break; }
+    rc = ipm_batch_run(B, B->max_iter, sweeps, 1);
+    if (rc != IPM_OK) break;
+    if (cudaEventRecord(e1, B->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = IPM_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const int done = std::max(1, B->sweeps);
+    times[k] = ms / done;
+    if (times[k] < tbest) {
+      tbest = times[k];
+      ibest = (int)k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B->timing = timing;
+  if (rc == IPM_OK && ibest >= 0) rc = apply(cand[ibest]);
+  if (rc == IPM_OK) rc = ipm_batch_reset(B);
+  if (rc != IPM_OK) return rc;
+  const int n = std::min((int)cand.size(), max_results);
+  for (int k = 0; k < n; ++k) {
+    cfg[4 * k] = cand[k].cl;
+    cfg[4 * k + 1] = cand[k].num;
+    cfg[4 * k + 2] = cand[k].den;
+    cfg[4 * k + 3] = cand[k].gx;
+    ms_per_sweep[k] = times[k];
+  }
+  if (n_results) *n_results = (int)cand.size();
+  if (best) *best = ibest;
+  return IPM_OK;
 }
 
 extern "C" int ipm_batch_results(ipm_batch_t B, int *status, int *iters, double *obj,

@@ -186,3 +186,27 @@ def test_batch_large_instances_follow_single_problem():
     # the path to the optimum may differ (this grid's iteration count moves with rounding-level
     # differences of the reductions); the final scaled KKT error is the method's own test
     assert (r2["kkt_err"] <= 1e-6).all() and r1["kkt_err"][0] <= 1e-6
+
+
+def test_batch_autotune_keeps_results():
+    """The launch-shape autotuner times every candidate (cluster sizes 1-8, both thresholds,
+    three element-kernel grids), keeps the fastest and leaves every instance at its starting
+    point: the solves after tuning reach the objectives of the solves before it."""
+    base = config_grid("planar1k")
+    grids = [scale_loads(base, 1000 + k) for k in range(6)] + [mixed_grid(2025)]
+    B = cp.Batch([cp.Opf(g) for g in grids])
+    B.run(max_iter=300)
+    ref = B.results()
+    t = B.autotune(sweeps=3)
+    c = t["candidates"]
+    assert len(c) >= 7 and 0 <= t["best"] < len(c)
+    ms = np.array([x["ms_per_sweep"] for x in c])
+    assert np.isfinite(ms).all() and (ms > 0).all() and ms[t["best"]] == ms.min()
+    assert {x["cluster"] for x in c} == {1, 2, 4, 8}
+    assert B.results()["iters"].max() == 0  # back at the starting point
+    B.run(max_iter=300)
+    r = B.results()
+    for i in range(len(grids)):
+        if ref["status"][i] == 1:
+            assert r["status"][i] == 1, i
+            assert abs(r["obj"][i] - ref["obj"][i]) <= 1e-6 * abs(ref["obj"][i]), i
