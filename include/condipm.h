@@ -321,11 +321,13 @@ void ipm_state_destroy(ipm_state_t state);
  * batched form of the method.
  * Instances whose model patterns (J and lower W) are equal share one symbolic analysis (the
  * paper reuses the analysis of a pattern across iterations, Section 5); instances may have
- * different sizes.  Each launch of the condensation, the sync-free factorization and the
- * triangular solves covers every instance that is in that step; the per-instance control of the
- * algorithm of ipm_step (convergence test, barrier update, inertia correction, refinement,
- * fraction to the boundary, filter line search) runs on the device, so a sweep of the method is
- * one CUDA graph and every instance follows the single-problem iteration exactly. */
+ * different sizes.  Each launch of the condensation, the factorization (level by level through
+ * each instance's elimination tree: one block, or one thread-block cluster for the big
+ * instances, per instance) and the triangular solves covers every instance that is in that step;
+ * the per-instance control of the algorithm of ipm_step (convergence test, barrier update,
+ * inertia correction, refinement or CG, fraction to the boundary, filter line search) runs on the
+ * device, so a sweep of the method is one CUDA graph and every instance follows the
+ * single-problem iteration up to the order of floating-point additions. */
 typedef struct ipm_batch_s *ipm_batch_t;
 
 /* Creates the batch over count model handles (HOST array of handles that must outlive the batch;
