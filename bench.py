@@ -508,8 +508,16 @@ def run_gpu(args, rank, world, local_rank):
     from synth import batch_grids
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
-    # ---- instances of this GPU (weak scaling: one full set per GPU)
-    grids = batch_grids(args.batch_scen, args.batch_mixed, part=rank)
+    # ---- instances of this GPU: weak scaling (one full set per GPU), or --split: one set split
+    # across the GPUs by size (strong scaling; results gathered on the host)
+    split = bool(args.split) and world > 1
+    if split:
+        from paper_2405_14236_gb300.shard import partition_by_cost
+        all_grids = batch_grids(args.batch_scen, args.batch_mixed, part=0)
+        share = partition_by_cost([2 * g.nb + 2 * g.ng for g in all_grids], world)[rank]
+        grids = [all_grids[i] for i in share]
+    else:
+        grids = batch_grids(args.batch_scen, args.batch_mixed, part=rank)
     t0 = time.perf_counter()
     opfs = [cp.Opf(g) for g in grids]
     B = cp.Batch(opfs)
@@ -568,6 +576,12 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     t_tot, tot_conv = aggregate_ranks(float(np.sum(step_ms)), float(np.sum(conv)), world, "cuda")
     value = tot_conv / (t_tot / 1e3)
+    gathered = None
+    if split:
+        from paper_2405_14236_gb300.shard import gather_results
+        r = B.results()
+        gathered = gather_results({"status": r["status"], "obj": r["obj"]}, share,
+                                  len(all_grids), world)
     # ---- e2e through the public API with host data: new loads for every scenario from host
     # memory, solve, every x back to host memory
     host_pd = [np.ascontiguousarray(g.pd, dtype=np.float64) for g in grids]
@@ -618,14 +632,22 @@ def run_gpu(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "instances": len(grids), "patterns": info["patterns"],
+        "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD,
+                   "instances": len(all_grids) if split else len(grids),
+                   "patterns": info["patterns"],
                    "tol": 1e-6, "max_iter": MAX_ITER, "pool_bytes": info["device_bytes"],
                    "l2": "not flushed: the instance pool (%.2f GB) exceeds L2"
                          % (info["device_bytes"] / 1e9),
-                   "parallelism": f"dp{world}: one instance set per GPU" if world > 1
-                   else "single GPU"},
-        "converged_per_step": conv, "iters_mean": float(np.mean(iters_mean)),
+                   "parallelism": (f"split{world}: one instance set split by size across "
+                                   "the GPUs" if split else
+                                   f"dp{world}: one instance set per GPU" if world > 1
+                                   else "single GPU")},
+        "converged_per_step": conv, "instances_per_step": len(grids) * world if not split
+        else len(all_grids),
+        "gathered_converged": None if gathered is None else int((gathered["status"] == 1).sum()),
+        "iters_mean": float(np.mean(iters_mean)),
         "iters_max": iters_max, "sweeps_per_step": sweeps,
         "launches_per_sweep": B.info()["launches_per_sweep"], "init_s": init_s,
         "launch_shape": shape, "autotune_s": autotune_s,
@@ -846,6 +868,9 @@ def main():
                     help="load scenarios of the 1,000-bus grid in the batch (profiling: fewer)")
     ap.add_argument("--batch-mixed", type=int, default=64,
                     help="mixed grids of 118-2,000 buses in the batch (profiling: fewer)")
+    ap.add_argument("--split", action="store_true",
+                    help="N > 1: split one instance set across the GPUs by size (strong scaling) "
+                         "instead of one set per GPU")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -171,8 +171,9 @@ int ipm_solve(ipm_sym_t sym, ipm_num_t num, const double *b, double *x, int nrhs
  * convenience.  The call allocates nothing: its scratch (the permuted work vector and the
  * dependency counters) is a static device array of the library, sized for n and the number of
  * supernodes up to 262144 (2^18), which every GPU that loads the library holds until exit.
- *   b [n], x [n] device (may alias); d_status: DEVICE int or NULL, receives IPM_OK or
- *   IPM_ERR_TIMEOUT (a bounded wait gave up; x is then invalid).
+ *   b [n], x [n] device (may alias); d_status: DEVICE int, receives IPM_OK or IPM_ERR_TIMEOUT
+ *   (a bounded wait gave up; x is then invalid) in stream order, and the call returns without
+ *   waiting; or NULL: the call then synchronizes the stream and returns that status itself.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress),
  * so make that first call before any stream capture.  All calls share the array and it keeps
  * the last call's contents (the counters are cleared by each call); calls that overlap on the
@@ -209,10 +210,16 @@ int ipm_aug_solve(ipm_sym_t sym, ipm_num_t num, const double *W_val, const doubl
  * (ipm_condense with d_row = [gamma..., D_H...]): r1 = a + H^T D_H b_H, r2 = b_G,
  * CG from dy = 0 on (G K_gamma^{-1} G^T) dy = G K_gamma^{-1}(r1 + gamma G^T r2) - r2 until
  * ||r_k||_2 <= max(rtol ||r_0||_2, 1e-14) or maxit; then
- * dx = K_gamma^{-1}(r1 + gamma G^T r2 - G^T dy) and dz = D_H (H dx - b_H).
+ * dx = K_gamma^{-1}(r1 + gamma G^T r2 - G^T dy) and dz = D_H (H dx - b_H).  When the normwise
+ * backward error of (dx, dy, dz) on the augmented system above exceeds 1e-10, the solution is
+ * refined on that system (Sec. 2.2): the residual is solved by the same procedure and added, at
+ * most three times, until the error is below 1e-10 or stops halving.  The refinement reads
+ * W_val, sigma_x and delta_w as passed to the last ipm_condense on num: those device arrays must
+ * still hold the values they held then.
  *   d_row [m] as passed to ipm_condense (d_row[0..m_e) = gamma).
  *   a [n], b [m], dx [n], dy [m_e], dz [m - m_e]
- *   h_iters, h_relres: HOST outputs (CG iterations, final ||r||/||r_0||).
+ *   h_iters, h_relres: HOST outputs (CG iterations of all solves, final ||r||/||r_0|| of the
+ *   first CG).
  * Returns IPM_ERR_CG_MAXIT if maxit was reached; with an FP32 factor, IPM_ERR_NOT_PD as for
  * ipm_aug_solve.  Synchronizes (convergence tests). */
 int hykkt_cg(ipm_sym_t sym, ipm_num_t num, int m_e, const double *J_val, const double *d_row,
@@ -314,6 +321,21 @@ int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStream_t stream,
 int ipm_step(ipm_state_t state, ipm_iter_info *host_info);
 /* Copies x [n] to a HOST buffer (NULL skipped) and the unscaled objective f(x) to *obj (HOST). */
 int ipm_state_export(ipm_state_t state, double *x, double *obj);
+/* Copies the KKT system that the last completed ipm_step solved, and its solution, to HOST
+ * buffers (any pointer may be NULL).  The system is the augmented system (K_2) with the slack
+ * block eliminated (Sec. 2.2, the system that iterative refinement runs on; Sec. 3.1-3.2):
+ *   [ W + Sigma_x + delta_w I   J^T ] [dx ]   [a]
+ *   [ J                         -E  ] [dyz] = [b],   E = diag(1 / d_row) on condensed rows,
+ * E = 0 on the first *m_e rows (HyKKT keeps the equalities; *m_e = 0 for the other forms).
+ * W_val [nnzW]: lower-triangular Hessian values in the model's W pattern (scaled multipliers and
+ * objective); sigma [n]; J_val [nnzJ]: the scaled Jacobian in the model's J pattern (rows
+ * [G; H], m = m_e0 + m_i0); d_row [m]: the row weights the condensed matrix was built with
+ * (LiftedKKT: the two relaxed rows of an equality merged, D1 + D2; HyKKT: gamma on G rows);
+ * *delta_w; a [n], b [m]: right-hand sides; dx [n], dyz [m]: the refined solution (HyKKT: dy
+ * over the G rows, then dz).  Returns IPM_ERR_BAD_ARG before the first step.  Synchronizes. */
+int ipm_state_export_kkt(ipm_state_t state, double *W_val, double *sigma, double *J_val,
+                         double *d_row, double *delta_w, double *a, double *b, double *dx,
+                         double *dyz, int *m_e);
 void ipm_state_destroy(ipm_state_t state);
 
 /* ---------------------------------------------------------------- batched interior-point solves
@@ -374,6 +396,28 @@ int ipm_batch_cg_iters(ipm_batch_t batch, int *cg_iters);
 int ipm_batch_export(ipm_batch_t batch, int i, double *x);
 /* Sweeps run since creation or the last reset. */
 int ipm_batch_sweeps(ipm_batch_t batch);
+/* Sets a launch shape (the candidates of ipm_batch_autotune): instances whose supernode count
+ * exceeds big_num / big_den times the median (big_den = 0: none) factor and solve on thread-block
+ * clusters of `cluster` blocks (1, 2, 4 or 8), and the element kernels take gx blocks per
+ * instance (1..16; gx <= 0 keeps the current value).  *n_big (HOST, may be NULL) = instances on
+ * clusters.  Keeps every instance's state. */
+int ipm_batch_set_shape(ipm_batch_t batch, int cluster, int big_num, int big_den, int gx,
+                        int *n_big);
+/* Holds every instance right after the KKT solve (and refinement, or CG) of its iteration k:
+ * such instances stop advancing, and ipm_batch_run returns once every instance is held or done.
+ * k = -1 (the state after creation) holds none.  The hold lets ipm_batch_export_kkt read a solved
+ * system whose values the next phase would overwrite.  Synchronizes. */
+int ipm_batch_pause_at(ipm_batch_t batch, int k);
+/* Releases the held instances; the next ipm_batch_run continues them from their step
+ * (fraction to the boundary, line search).  Synchronizes. */
+int ipm_batch_resume(ipm_batch_t batch);
+/* Instance i's KKT system and refined solution while it is held (ipm_batch_pause_at), to HOST
+ * buffers, in the layout of ipm_state_export_kkt (the augmented system (K_2) with the slack
+ * block eliminated, Sec. 2.2; HyKKT: dy over the G rows then dz, and *m_e = the G rows).
+ * Returns IPM_ERR_BAD_ARG when the instance is not held.  Synchronizes. */
+int ipm_batch_export_kkt(ipm_batch_t batch, int i, double *W_val, double *sigma, double *J_val,
+                         double *d_row, double *delta_w, double *a, double *b, double *dx,
+                         double *dyz, int *m_e);
 /* Copies every instance's x, concatenated in instance order, into a HOST buffer of sum(n)
  * doubles (one gather kernel and one device-to-host copy).  Synchronizes. */
 int ipm_batch_export_all(ipm_batch_t batch, double *x_host);

@@ -35,6 +35,39 @@ S_THETA, S_PHI, DELTA = 1.1, 2.3, 1.0
 ETA_PHI = 1e-8
 GAMMA_ALPHA = 0.05
 KAPPA_SIGMA = 1e10
+# rounding margin of barrier-function comparisons: phi is known only to about
+# 10 eps_mach |phi|, so a trial whose phi differs by less than that counts as equal
+PHI_MARGIN = 10.0 * np.finfo(np.float64).eps
+
+
+def filter_accept(theta, phi, gphi, alpha, tht, pht, filt, theta_min, theta_max):
+    """Acceptance of a trial point in the filter line search (Waechter & Biegler 2006,
+    Sec. 2.3-2.4, cited in Sec. 2.2 of the paper).
+
+    theta, phi: constraint violation and barrier function at the current iterate; gphi: the
+    directional derivative of phi along the step; (tht, pht): the trial point at step alpha;
+    filt: list of filter entries (theta_f, phi_f).  Returns (accepted, f_type): f_type is True
+    when the trial was accepted by the Armijo condition in the switching case (such steps do
+    not augment the filter).  Every comparison of barrier-function values allows the rounding
+    margin PHI_MARGIN * |phi| (a reading: the paper is silent; Ipopt relaxes its Armijo and
+    sufficient-decrease tests in the same way, applied here to the filter entries as well).
+    """
+    margin = PHI_MARGIN * abs(phi)
+    if not (tht < theta_max and np.isfinite(pht)):
+        return False, False
+    for tf, pf in filt:
+        if not (tht < tf or pht - pf < margin):
+            return False, False
+    switching = bool(gphi < 0 and alpha * (-gphi) ** S_PHI > DELTA * theta ** S_THETA)
+    if switching and theta <= theta_min:
+        return bool(pht - phi <= ETA_PHI * alpha * gphi + margin), True
+    return bool(tht <= (1 - GAMMA_THETA) * theta or pht - phi <= -GAMMA_PHI * theta + margin), False
+
+
+def barrier_update(mu, tol):
+    """Monotone barrier decrease mu+ = max(tol / 10, min(kappa_mu mu, mu^theta_mu))
+    (Waechter & Biegler 2006, Eq. (7))."""
+    return max(tol / 10.0, min(KAPPA_MU * mu, mu ** THETA_MU))
 
 
 @dataclasses.dataclass
@@ -237,7 +270,7 @@ def solve(model, opt: Options | None = None, x0=None):
             break
         first = True
         while errors(gradf, J, g, h, mu) <= KAPPA_EPS * mu and (first or it == 0):
-            mu = max(opt.tol / 10.0, min(KAPPA_MU * mu, mu ** THETA_MU))
+            mu = barrier_update(mu, opt.tol)
             tau = max(TAU_MIN, 1.0 - mu)
             filt = []
             first = False
@@ -322,22 +355,14 @@ def solve(model, opt: Options | None = None, x0=None):
         accepted = False
         ls = 0
 
-        def acceptable(tht, pht, alpha_):
-            ok_f = tht < theta_max and all(tht < tf or pht < pf for tf, pf in filt)
-            if not (ok_f and np.isfinite(pht)):
-                return False, False
-            switching = gphi < 0 and alpha_ * (-gphi) ** S_PHI > DELTA * theta ** S_THETA
-            if switching and theta <= theta_min:
-                return pht <= phi + ETA_PHI * alpha_ * gphi, True
-            return tht <= (1 - GAMMA_THETA) * theta or pht <= phi - GAMMA_PHI * theta, False
-
         while True:
             xt = x + alpha * dx
             st = s + alpha * ds
             gt, ht = model.cons(xt)
             tht = theta_of(gt, ht, st)
             pht = phi_of(xt, st, mu)
-            accepted, ftype = acceptable(tht, pht, alpha)
+            accepted, ftype = filter_accept(theta, phi, gphi, alpha, tht, pht, filt, theta_min,
+                                            theta_max)
             if accepted:
                 break
             ls += 1

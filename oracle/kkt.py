@@ -26,7 +26,7 @@ and dz = D_H (H dx - b_H).
 Readings where the paper is silent (also listed in the design notes):
   CG starts at dy = 0 and stops when ||r_k||_2 <= max(rtol ||r_0||_2, atol);
   refinement stops at backward error <= 1e-10, when the error stops halving,
-  or after 10 steps.
+  or after 10 steps (LiftedKKT) or 3 HyKKT re-solves (HyKKT).
 """
 from __future__ import annotations
 
@@ -127,14 +127,60 @@ def lifted_solve(F, A, J, d, a, b, max_refine=10, tol=1e-10):
         if eta <= tol:
             break
         res = rhs - A @ sol
-        sol = sol + csolve(res[:n], res[n:])
-        eta_new = backward_error(A, sol, rhs)
+        corr = csolve(res[:n], res[n:])
+        eta_new = backward_error(A, sol + corr, rhs)
         hist.append(eta_new)
-        if eta_new > 0.5 * eta:
-            eta = eta_new
+        if not eta_new <= eta:      # the correction made it worse: keep the previous solution
             break
+        sol = sol + corr
+        stalled = eta_new > 0.5 * eta
         eta = eta_new
+        if stalled:
+            break
+    if np.isfinite(eta) and eta > tol and max_refine > 0:
+        # Richardson stagnated: conjugate gradients on K dx = a + J^T (d o b) preconditioned by
+        # the factor, from the refined dx; dz = d o (J dx - b); the better solution is kept
+        x = pcg_condensed(F, A[:n, :n], J, d, a + J.T @ (d * b), sol[:n].copy(), 50,
+                          normwise=False)
+        alt = np.concatenate([x, d * (J @ x - b)])
+        eta_alt = backward_error(A, alt, rhs)
+        hist.append(eta_alt)
+        if eta_alt < eta:
+            sol = alt
     return sol[:n], sol[n:], hist
+
+
+def pcg_condensed(F, Axx, J, d, t, x, maxit, normwise=True):
+    """Preconditioned CG on K x = t, K v = Axx v + J^T (d o (J v)), M^{-1} = the factor F,
+    from the given x; stops at ||r||_2 <= 1e-14 ||t||_2 or (normwise) a normwise backward error
+    ||r||_inf <= 1e-14 (||K||_inf ||x||_inf + ||t||_inf) (||K||_inf bounded by the row sums of
+    |Axx| + |J|^T |d| |J|), after maxit iterations, or at negative curvature.  After stagnating
+    refinement the normwise test is off: with large d it is far looser than the backward error
+    of the augmented system."""
+    kv = lambda v: Axx @ v + J.T @ (d * (J @ v))
+    knorm = float(np.max(abs(Axx) @ np.ones(Axx.shape[0]) +
+                         abs(J).T @ (np.abs(d) * (abs(J) @ np.ones(J.shape[1])))))
+    tn, tinf = np.linalg.norm(t), np.abs(t).max()
+    r = t - kv(x)
+    z = F.solve(r)
+    p = z.copy()
+    rz = float(r @ z)
+    for _ in range(maxit):
+        if (np.linalg.norm(r) <= 1e-14 * tn or
+                (normwise and np.abs(r).max() <= 1e-14 * (knorm * np.abs(x).max() + tinf))):
+            break
+        Ap = kv(p)
+        pap = float(p @ Ap)
+        if not pap > 0:
+            break
+        al = rz / pap
+        x = x + al * p
+        r = r - al * Ap
+        z = F.solve(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x
 
 
 def hykkt_cg(F, G, gamma, r1bar, r2bar, rtol=1e-10, atol=1e-14, maxit=None):
@@ -165,12 +211,43 @@ def hykkt_cg(F, G, gamma, r1bar, r2bar, rtol=1e-10, atol=1e-14, maxit=None):
     return dx, dy, it, float(np.sqrt(rr) / max(r0, 1e-300))
 
 
-def hykkt_solve(F, W, sigma_x, J, d_h, m_e, delta_w, gamma, a, b, **cg):
-    """HyKKT solve of (AUG): condense H, CG on the Schur complement, recover dz."""
+def hykkt_solve(F, W, sigma_x, J, d_h, m_e, delta_w, gamma, a, b, max_refine=3, tol=1e-10,
+                **cg):
+    """HyKKT solve of (AUG): condense H, CG on the Schur complement, recover dz; then, while the
+    backward error on (AUG) exceeds tol, Richardson refinement on (AUG) with the same HyKKT
+    procedure solving for the residual (Section 2.2, iterative refinement on the original
+    system; at most max_refine corrections, stopping when the error fails to halve).
+    Returns dx, dy, dz, the CG iterations of all solves, and the first CG's final relative
+    residual."""
     G = J[:m_e]
     H = J[m_e:]
-    r1bar = a + H.T @ (d_h * b[m_e:])
-    r2bar = b[:m_e]
-    dx, dy, it, rel = hykkt_cg(F, G, gamma, r1bar, r2bar, **cg)
-    dz = d_h * (H @ dx - b[m_e:])
-    return dx, dy, dz, it, rel
+    n = J.shape[1]
+
+    def once(ra, rb):
+        r1bar = ra + H.T @ (d_h * rb[m_e:])
+        dx_, dy_, it_, rel_ = hykkt_cg(F, G, gamma, r1bar, rb[:m_e], **cg)
+        dz_ = d_h * (H @ dx_ - rb[m_e:])
+        return np.concatenate([dx_, dy_, dz_]), it_, rel_
+
+    A = aug_matrix(W, sigma_x, J, d_h, m_e, delta_w)
+    rhs = np.concatenate([a, b])
+    sol, it, rel = once(a, b)
+    eta = backward_error(A, sol, rhs)
+    for _ in range(max_refine):
+        if eta <= tol:
+            break
+        res = rhs - A @ sol
+        # solve for the residual scaled to unit size (the CG's absolute floor must not end the
+        # correction early), then scale the correction back
+        sc = float(np.abs(res).max()) or 1.0
+        corr, it2, _ = once(res[:n] / sc, res[n:] / sc)
+        it += it2
+        eta_new = backward_error(A, sol + sc * corr, rhs)
+        if not eta_new <= eta:      # worse: keep the previous solution
+            break
+        sol = sol + sc * corr
+        stalled = eta_new > 0.5 * eta
+        eta = eta_new
+        if stalled:
+            break
+    return sol[:n], sol[n:n + m_e], sol[n + m_e:], it, rel

@@ -24,9 +24,15 @@
  * The elimination tree and the column structures of L follow their definitions
  * (symbolic elimination): struct(L_j) = {i > j : A_ij != 0} united with
  * struct(L_c) minus {j} over the children c of j; parent(j) = min struct(L_j).
- * Supernodes: column j+1 continues the supernode of column j when parent(j) = j+1,
- * |struct(L_j)| = |struct(L_{j+1})| + 1 and the supernode has fewer than SN_MAXW
- * columns.
+ * Supernodes (relaxed): a supernode is a run of consecutive columns f..l in which
+ * parent(k) = k+1 for f <= k < l (a chain of the elimination tree).  Its panel holds, in
+ * every column k, the rows k..l and the rows of struct(L_l); the entries of the panel that are
+ * not in struct(L_k) are explicit zeros.  Scanning the columns in order, column l+1 joins the
+ * supernode f..l when parent(l) = l+1, the width l+2-f stays <= SN_MAXW, and either that width
+ * is <= SN_RELAX_W or the explicit zeros are at most 1/SN_RELAX_DEN of the panel's entries
+ * (E = w(w+1)/2 + w |struct(L_{l+1})|, zeros = E - sum_k |L_k|); otherwise l+1 starts a new
+ * supernode.  Fundamental supernodes (no explicit zero) are the special case where every
+ * extension adds none.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -35,6 +41,8 @@
 #define LEAF 64
 #define REROOT 4
 #define SN_MAXW 64
+#define SN_RELAX_W 8   /* always merge up to this width */
+#define SN_RELAX_DEN 5 /* otherwise explicit zeros <= entries / SN_RELAX_DEN */
 
 typedef struct {
   int n;
@@ -305,12 +313,23 @@ osym *osym_analyze(int n, const int *ap, const int *ai) {
   free(nxt);
   free(tmp);
 
-  /* supernodes */
+  /* supernodes (relaxed, see the header) */
   int ns = 0;
+  int64_t nzsum = 0; /* sum of |L_k| (diagonal included) over the current supernode */
   for (int j = 0; j < n; ++j) {
-    int cont = j > 0 && s->parent[j - 1] == j && s->cc[j - 1] == s->cc[j] + 1 &&
-               (j - s->sptr[ns - 1]) < SN_MAXW;
-    if (!cont) s->sptr[ns++] = j;
+    int join = 0;
+    if (j > 0 && s->parent[j - 1] == j) {
+      int64_t w = j - s->sptr[ns - 1] + 1; /* width with column j */
+      int64_t below = s->cc[j] - 1;        /* |struct(L_j)|: the rows below the panel */
+      int64_t entries = w * (w + 1) / 2 + w * below;
+      int64_t zeros = entries - (nzsum + s->cc[j]);
+      join = w <= SN_MAXW && (w <= SN_RELAX_W || SN_RELAX_DEN * zeros <= entries);
+    }
+    if (!join) {
+      s->sptr[ns++] = j;
+      nzsum = 0;
+    }
+    nzsum += s->cc[j];
   }
   s->sptr[ns] = n;
   s->nsuper = ns;

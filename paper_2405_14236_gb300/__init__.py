@@ -54,6 +54,7 @@ _SIGS = {
     "ipm_state_create": (I, [P, P, P, P]),
     "ipm_step": (I, [P, P]),
     "ipm_state_export": (I, [P, P, P]),
+    "ipm_state_export_kkt": (I, [P] * 11),
     "ipm_state_destroy": (None, [P]),
     "ipm_batch_create": (I, [I, P, P, P, P]),
     "ipm_batch_info": (I, [P, P, P, P]),
@@ -64,6 +65,10 @@ _SIGS = {
     "ipm_batch_autotune": (I, [P, I, I, P, P, P, P]),
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
+    "ipm_batch_pause_at": (I, [P, I]),
+    "ipm_batch_set_shape": (I, [P, I, I, I, I, P]),
+    "ipm_batch_resume": (I, [P]),
+    "ipm_batch_export_kkt": (I, [P, I] + [P] * 10),
     "ipm_batch_destroy": (None, [P]),
     "ipm_batch_export_all": (I, [P, P]),
     "ipm_batch_set_timing": (I, [P, I]),
@@ -246,8 +251,12 @@ def ipm_debug_add_dependency(sym, supernode, extra=1):
 
 
 def ipm_condense(sym, num, W_val, sigma_x, J_val, d_row, delta_w, stream=None):
-    return _check(lib().ipm_condense(sym.h, num.h, _ptr(W_val), _ptr(sigma_x), _ptr(J_val),
-                                     _ptr(d_row), float(delta_w), _stream(stream)), "ipm_condense")
+    rc = _check(lib().ipm_condense(sym.h, num.h, _ptr(W_val), _ptr(sigma_x), _ptr(J_val),
+                                   _ptr(d_row), float(delta_w), _stream(stream)), "ipm_condense")
+    # the library keeps these pointers for the FP64 products of later solves on this handle
+    # (refinement, the FP32 factor's CG): the tensors live as long as the handle refers to them
+    num._condense_inputs = (W_val, sigma_x, J_val, d_row)
+    return rc
 
 
 def ipm_factor(sym, num, d_info, stream=None):
@@ -359,6 +368,22 @@ class IpmState:
         v = D()
         _check(lib().ipm_state_export(self.h, None, ctypes.byref(v)), "export")
         return v.value
+
+    def export_kkt(self):
+        """The augmented KKT system of the last step and its refined solution
+        (ipm_state_export_kkt), as host arrays."""
+        o = self.opf
+        m = o.m_e + o.m_i
+        out = dict(W_val=np.zeros(o.nnzW), sigma=np.zeros(o.n), J_val=np.zeros(o.nnzJ),
+                   d_row=np.zeros(m), a=np.zeros(o.n), b=np.zeros(m), dx=np.zeros(o.n),
+                   dyz=np.zeros(m))
+        dw, me = D(), I()
+        p = lambda k: out[k].ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_state_export_kkt(self.h, p("W_val"), p("sigma"), p("J_val"), p("d_row"),
+                                          ctypes.byref(dw), p("a"), p("b"), p("dx"), p("dyz"),
+                                          ctypes.byref(me)), "ipm_state_export_kkt")
+        out["delta_w"], out["m_e"] = dw.value, me.value
+        return out
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -488,6 +513,36 @@ class Batch:
         out = np.zeros(self.opfs[i].n)
         _check(lib().ipm_batch_export(self.h, int(i), out.ctypes.data_as(ctypes.c_void_p)),
                "ipm_batch_export")
+        return out
+
+    def set_shape(self, cluster, big_num, big_den, gx):
+        """Launch shape (ipm_batch_set_shape); returns the number of instances on clusters."""
+        nb = I()
+        _check(lib().ipm_batch_set_shape(self.h, int(cluster), int(big_num), int(big_den), int(gx),
+                                         ctypes.byref(nb)), "ipm_batch_set_shape")
+        return nb.value
+
+    def pause_at(self, k):
+        """Hold every instance after the KKT solve of its iteration k (-1: none)."""
+        _check(lib().ipm_batch_pause_at(self.h, int(k)), "ipm_batch_pause_at")
+
+    def resume(self):
+        _check(lib().ipm_batch_resume(self.h), "ipm_batch_resume")
+
+    def export_kkt(self, i):
+        """Instance i's KKT system and refined solution while it is held (dict of host arrays,
+        the layout of IpmState.export_kkt)."""
+        o = self.opfs[i]
+        m = o.m_e + o.m_i
+        out = dict(W_val=np.zeros(o.nnzW), sigma=np.zeros(o.n), J_val=np.zeros(o.nnzJ),
+                   d_row=np.zeros(m), a=np.zeros(o.n), b=np.zeros(m), dx=np.zeros(o.n),
+                   dyz=np.zeros(m))
+        dw, me = D(), I()
+        p = lambda k: out[k].ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_batch_export_kkt(self.h, int(i), p("W_val"), p("sigma"), p("J_val"),
+                                          p("d_row"), ctypes.byref(dw), p("a"), p("b"), p("dx"),
+                                          p("dyz"), ctypes.byref(me)), "ipm_batch_export_kkt")
+        out["delta_w"], out["m_e"] = dw.value, me.value
         return out
 
     def __del__(self):

@@ -32,10 +32,12 @@
 
 namespace cipm {
 
-// PH_CGI, PH_CG, PH_CGX: HyKKT's Schur-complement CG (start, iterations, primal back-solve)
+// PH_CGI, PH_CG, PH_CGX: HyKKT's Schur-complement CG (start, iterations, primal back-solve);
+// PH_PAUSE: held after the KKT solve of the iteration named by ipm_batch_pause_at (the solved
+// system and its solution stay in the instance's buffers until ipm_batch_resume)
 enum Phase {
   PH_EVAL = 0, PH_BUILD, PH_FACT, PH_SOLVE, PH_REFINE, PH_STEP, PH_LS, PH_ACC, PH_DONE,
-  PH_CGI, PH_CG, PH_CGX
+  PH_CGI, PH_CG, PH_CGX, PH_PAUSE
 };
 
 static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2, B_CG_ROUNDS = 6;
@@ -1020,10 +1022,10 @@ __global__ void k_b_cgx_dz(const BI *bi, const BCtl *ctl) {
   for (int r = I.D.me0 + gtid; r < I.m; r += gstride)
     I.dzc[r] = I.dcond[r] * (g_row_dot(I, r, I.dx) - I.baug[r]);
 }
-__global__ void k_b_ctl_cgx(BCtl *ctl, int count) {
+__global__ void k_b_ctl_cgx(BCtl *ctl, int count, const int *pause_k) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count || ctl[b].ph != PH_CGX) return;
-  ctl[b].ph = PH_STEP;
+  ctl[b].ph = ctl[b].k == *pause_k ? PH_PAUSE : PH_STEP;
 }
 
 // factor outcome: success -> solve; wrong inertia -> next delta_w
@@ -1124,7 +1126,8 @@ __global__ void k_b_resid(const BI *bi, const BCtl *ctl) {
 }
 // Richardson test: stop at eta <= 1e-10, after max_refine corrections, or when eta stops
 // halving; otherwise one more correction
-__global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine) {
+__global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine,
+                            const int *pause_k) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count || ctl[b].ph != PH_REFINE) return;
   const BI &I = bi[b];
@@ -1143,7 +1146,7 @@ __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine) 
   stop = eta <= 1e-10 || c.ref_it >= max_refine || (c.ref_it > 0 && eta > 0.5 * c.eta_prev);
   ++c.ref_it;
   if (stop) {
-    c.ph = PH_STEP;
+    c.ph = c.k == *pause_k ? PH_PAUSE : PH_STEP;
     return;
   }
   c.eta_prev = eta;
@@ -1257,22 +1260,9 @@ __global__ void k_b_ctl_ls(const BI *bi, BCtl *ctl, int count) {
   const double tht = h[R_TH_G] + h[R_TH_H];
   const double pht = c.sig * (*I.ft) - c.mu * (h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU]);
   const double theta = c.theta, phi = c.phi, gphi = c.gphi, alpha = c.alpha;
-  bool okf = tht < c.theta_max;
-  for (int q = 0; q < c.nfilter && okf; ++q)
-    if (!(tht < I.filter[2 * q] || pht < I.filter[2 * q + 1])) okf = false;
-  bool accepted = false;
   int ftype = 0;
-  if (okf && isfinite(pht)) {
-    const bool switching = gphi < 0 && alpha * pow(-gphi, S_PHI) > DELTA_SW * pow(theta, S_THETA);
-    if (switching && theta <= c.theta_min) {
-      if (pht <= phi + ETA_PHI * alpha * gphi) {
-        accepted = true;
-        ftype = 1;
-      }
-    } else if (tht <= (1 - GAMMA_THETA) * theta || pht <= phi - GAMMA_PHI * theta) {
-      accepted = true;
-    }
-  }
+  const bool accepted = filter_accept(theta, phi, gphi, alpha, tht, pht, I.filter, c.nfilter,
+                                      c.theta_min, c.theta_max, &ftype);
   if (accepted) {
     c.ftype = ftype;
     c.ph = PH_ACC;
@@ -1323,13 +1313,17 @@ __global__ void k_b_ctl_acc(const BI *bi, BCtl *ctl, int count, int fmax_entries
 
 __global__ void k_b_count(const BCtl *ctl, int count, int *active) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
-  int a = b < count && ctl[b].ph != PH_DONE;
+  int a = b < count && ctl[b].ph != PH_DONE && ctl[b].ph != PH_PAUSE;
   a = __syncthreads_count(a);
   if (threadIdx.x == 0 && a) atomicAdd(active, a);
 }
+__global__ void k_b_resume(BCtl *ctl, int count) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < count && ctl[b].ph == PH_PAUSE) ctl[b].ph = PH_STEP;
+}
 __global__ void k_b_finish_unfinished(BCtl *ctl, int count) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < count && ctl[b].ph != PH_DONE) {
+  if (b < count && ctl[b].ph != PH_DONE && ctl[b].ph != PH_PAUSE) {
     ctl[b].status = IPM_ERR_MAXITER;
     ctl[b].ph = PH_DONE;
   }
@@ -1442,7 +1436,7 @@ struct ipm_batch_s {
   BI *d_bi = nullptr;
   BCtl *d_ctl = nullptr;
   std::vector<void *> bufs;  // per-pattern level offsets
-  int *d_tickets = nullptr;                      // scratch counters (active count at [8])
+  int *d_tickets = nullptr;  // scratch counters: active count at [8], pause iteration at [12]
   int *d_order = nullptr;  // small instances by decreasing supernode count, then the big ones
   int n_small = 0, n_big = 0;
   // launch shapes (ipm_batch_autotune): cluster size of the big instances, "big" = supernode
@@ -1632,7 +1626,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     L(1);
     CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CGX, B->solve_ycap));
     k_b_cgx_dz<<<g2, blk, 0, s>>>(bi, ctl);
-    k_b_ctl_cgx<<<gc, 128, 0, s>>>(ctl, C);
+    k_b_ctl_cgx<<<gc, 128, 0, s>>>(ctl, C, B->d_tickets + 12);
     L(2);
   } else {
     // condensed solve, then Richardson refinement on the augmented system
@@ -1642,7 +1636,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     for (int r = 0; r < B_REFINE_ROUNDS; ++r) {
       k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl);
       k_b_resid<<<g2, blk, 0, s>>>(bi, ctl);
-      k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine);
+      k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine, B->d_tickets + 12);
       L(3);
       CKR(solve(PH_REFINE));
       k_b_axpy<<<g2, blk, 0, s>>>(bi, ctl);
@@ -2090,6 +2084,11 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   if (rc == IPM_OK && cudaMalloc(&B->d_ctl, sizeof(BCtl) * count) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMalloc(&B->d_tickets, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMemset(B->d_tickets, 0, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_CUDA;
+  if (rc == IPM_OK) {
+    const int no_pause = -1;
+    if (cudaMemcpy(B->d_tickets + 12, &no_pause, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = IPM_ERR_CUDA;
+  }
   if (rc == IPM_OK && cudaMallocHost((void **)&B->h_active, sizeof(int)) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -2437,5 +2436,74 @@ extern "C" int ipm_batch_warm_start(ipm_batch_t B, const float *pred, int64_t ld
 // the batched kernels keep their own copy of the spin limit
 int batch_set_spin_limit(long long polls) {
   CK(cudaMemcpyToSymbol(g_spin_limit, &polls, sizeof(polls)));
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_pause_at(ipm_batch_t B, int k) {
+  if (!B || k < -1) return IPM_ERR_BAD_ARG;
+  CK(cudaMemcpy(B->d_tickets + 12, &k, sizeof(int), cudaMemcpyHostToDevice));
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_resume(ipm_batch_t B) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  k_b_resume<<<grid_for(B->count, 128), 128, 0, B->stream>>>(B->d_ctl, B->count);
+  count_launches(1);
+  CKL();
+  CK(cudaStreamSynchronize(B->stream));
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_export_kkt(ipm_batch_t B, int i, double *W_val, double *sigma,
+                                    double *J_val, double *d_row, double *delta_w, double *a,
+                                    double *b, double *dx, double *dyz, int *m_e) {
+  if (!B || i < 0 || i >= B->count) return IPM_ERR_BAD_ARG;
+  CK(cudaStreamSynchronize(B->stream));
+  BI I;
+  BCtl c;
+  CK(cudaMemcpy(&I, B->d_bi + i, sizeof(BI), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&c, B->d_ctl + i, sizeof(BCtl), cudaMemcpyDeviceToHost));
+  if (c.ph != PH_PAUSE) {
+    set_error_msg("ipm_batch_export_kkt: instance " + std::to_string(i) +
+                  " is not held after a KKT solve (ipm_batch_pause_at)");
+    return IPM_ERR_BAD_ARG;
+  }
+  const int n = I.D.n, me0 = I.D.me0, m = I.m;
+  auto get = [&](double *dst, const double *src, int64_t count) -> int {
+    if (dst && count > 0)
+      CK(cudaMemcpy(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    return IPM_OK;
+  };
+  CKR(get(W_val, I.Wv, I.M.nnzW));
+  CKR(get(sigma, I.SA.sigma, n));
+  CKR(get(J_val, I.Jv, I.M.nnzJ));
+  CKR(get(d_row, I.dcond, m));
+  CKR(get(a, I.a, n));
+  CKR(get(b, I.baug, m));
+  CKR(get(dx, I.dx, n));
+  const bool hykkt = B->opt.kkt == 1;
+  if (hykkt) {
+    CKR(get(dyz, I.cg_dy, me0));
+    CKR(get(dyz ? dyz + me0 : nullptr, I.dzc + me0, m - me0));
+  } else {
+    CKR(get(dyz, I.dzc, m));
+  }
+  if (delta_w) *delta_w = c.dw;
+  if (m_e) *m_e = hykkt ? me0 : 0;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_set_shape(ipm_batch_t B, int cluster, int big_num, int big_den, int gx,
+                                   int *n_big) {
+  if (!B || (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) || big_num < 0 ||
+      big_den < 0 || gx > 16)
+    return IPM_ERR_BAD_ARG;
+  B->cl_big = cluster;
+  B->big_num = big_num;
+  B->big_den = big_den;
+  if (gx > 0) B->gx = gx;
+  drop_graph(B);
+  CKR(set_order(B));
+  if (n_big) *n_big = B->n_big;
   return IPM_OK;
 }

@@ -64,13 +64,14 @@ struct ipm_num_s {
   const double *cW = nullptr, *cSig = nullptr, *cJ = nullptr, *cD = nullptr;
   double cDw = 0.0;
   int last_pcg_iters = 0;
+  double last_eta = 0.0;  // backward error of the last hykkt_cg solve on the augmented system
   bool factored = false;  // panels hold L21 and Dx holds L11 (else panels hold K)
   // dependency counters of the sync-free kernels: [0,ns) update arrivals, [ns,2ns) panel
   // tasks done, [2ns,3ns) forward arrivals, [3ns,4ns) backward done flags, then tickets/status
   int *sync = nullptr;
   // workspaces (n or m sized), allocated once
   double *vn[12] = {nullptr};
-  double *vm[6] = {nullptr};
+  double *vm[8] = {nullptr};
   double *scal = nullptr;  // device scalars
   double *h_scal = nullptr;  // pinned host mirror
 };

@@ -231,10 +231,12 @@ struct ipm_state_s {
   double sig = 1.0, mu = 0.1, tau = 0.99, delta_last = 0.0;
   double theta_max = 0, theta_min = 0;
   bool have_theta0 = false;
-  std::vector<std::pair<double, double>> filter;
+  std::vector<double> filter;  // interleaved (theta, phi) entries
   int k = 0;
   int status = 0;  // 0 running, 1 converged, <0/IPM_ERR_* failure
   int nl = 0, nu = 0;
+  bool have_kkt = false;  // a KKT solve has completed (ipm_state_export_kkt)
+  double last_dw = 0.0;
 };
 
 static int grid1(int64_t n) { return grid_for(n > 0 ? n : 1, 256); }
@@ -566,9 +568,12 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     if (st == IPM_ERR_NOT_PD) continue;
     ok = true;
     info->precision = num == S->num32 ? 32 : 64;
+    if (S->opt.kkt == 1) info->eta = num->last_eta;
     break;
   }
   if (!ok) return IPM_ERR_INERTIA;
+  S->have_kkt = true;
+  S->last_dw = dw;
   if (dw > 0) S->delta_last = dw;
   info->delta_w = dw;
   info->n_factor = nfac;
@@ -618,24 +623,10 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     CKR(eval_point(S, S->xt, S->gst, S->hst, S->geqt, S->hint, S->ft, false));
     double tht, pht;
     CKR(merit(S, S->xt, S->st, S->geqt, S->hint, S->ft, mu, &tht, &pht));
-    bool okf = tht < S->theta_max;
-    for (auto &fp : S->filter)
-      if (!(tht < fp.first || pht < fp.second)) {
-        okf = false;
-        break;
-      }
-    if (okf && std::isfinite(pht)) {
-      bool switching = gphi < 0 && alpha * std::pow(-gphi, S_PHI) > DELTA_SW * std::pow(theta, S_THETA);
-      if (switching && theta <= S->theta_min) {
-        if (pht <= phi + ETA_PHI * alpha * gphi) {
-          accepted = true;
-          ftype = true;
-        }
-      } else if (tht <= (1 - GAMMA_THETA) * theta || pht <= phi - GAMMA_PHI * theta) {
-        accepted = true;
-        ftype = false;
-      }
-    }
+    int ft = 0;
+    accepted = filter_accept(theta, phi, gphi, alpha, tht, pht, S->filter.data(),
+                             (int)(S->filter.size() / 2), S->theta_min, S->theta_max, &ft);
+    ftype = ft != 0;
     if (accepted) break;
     ++ls;
     alpha *= 0.5;
@@ -649,7 +640,10 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     info->status = IPM_ERR_RESTORATION;
     return IPM_OK;
   }
-  if (!ftype) S->filter.push_back({(1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta});
+  if (!ftype) {
+    S->filter.push_back((1 - GAMMA_THETA) * theta);
+    S->filter.push_back(phi - GAMMA_PHI * theta);
+  }
   k_accept<<<grid1(nmax), 256, 0, s>>>(SA, alpha, az, S->xt, S->st, dy_step);
   CKL();
   CK(cudaStreamSynchronize(s));
@@ -682,5 +676,37 @@ extern "C" int ipm_state_export(ipm_state_t S, double *x, double *obj) {
     CK(cudaMemcpyAsync(obj, S->ft, sizeof(double), cudaMemcpyDeviceToHost, S->stream));
     CK(cudaStreamSynchronize(S->stream));
   }
+  return IPM_OK;
+}
+
+extern "C" int ipm_state_export_kkt(ipm_state_t S, double *W_val, double *sigma, double *J_val,
+                                    double *d_row, double *delta_w, double *a, double *b,
+                                    double *dx, double *dyz, int *m_e) {
+  if (!S || !S->have_kkt) {
+    set_error_msg("ipm_state_export_kkt: no KKT solve has completed");
+    return IPM_ERR_BAD_ARG;
+  }
+  const int n = S->D.n, me0 = S->D.me0, mi0 = S->D.mi0, m = me0 + mi0;
+  CK(cudaStreamSynchronize(S->stream));
+  auto get = [&](double *dst, const double *src, int64_t count) -> int {
+    if (dst && count > 0)
+      CK(cudaMemcpy(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    return IPM_OK;
+  };
+  CKR(get(W_val, S->Wv, S->nnzW));
+  CKR(get(sigma, S->sigma, n));
+  CKR(get(J_val, S->Jv, S->nnzJ));
+  CKR(get(d_row, S->dcond, m));
+  CKR(get(a, S->a, n));
+  CKR(get(b, S->baug, m));
+  CKR(get(dx, S->dx, n));
+  if (S->opt.kkt == 1) {
+    CKR(get(dyz, S->dy, me0));
+    CKR(get(dyz ? dyz + me0 : nullptr, S->dzH, mi0));
+  } else {
+    CKR(get(dyz, S->dzc, m));
+  }
+  if (delta_w) *delta_w = S->last_dw;
+  if (m_e) *m_e = S->opt.kkt == 1 ? me0 : 0;
   return IPM_OK;
 }

@@ -15,6 +15,32 @@ static constexpr double KAPPA1 = 1e-2, KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_M
 static constexpr double TAU_MIN = 0.99, S_MAX = 100.0, GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-8;
 static constexpr double S_THETA = 1.1, S_PHI = 2.3, DELTA_SW = 1.0, ETA_PHI = 1e-8;
 static constexpr double GAMMA_ALPHA = 0.05, KAPPA_SIGMA = 1e10, KAPPA_SIGMA_INV = 1.0 / KAPPA_SIGMA;
+// rounding margin of barrier-function comparisons: phi is known to about 10 eps_mach |phi|, so
+// values closer than that compare as equal (the Armijo test, the sufficient decrease and the
+// filter entries alike)
+static constexpr double PHI_MARGIN = 10.0 * 2.220446049250313e-16;
+
+// Filter acceptance of a trial point (tht, pht) at step alpha from (theta, phi) with directional
+// derivative gphi (Waechter & Biegler 2006, Sec. 2.3-2.4): the filter (nfilter interleaved
+// (theta, phi) pairs) and theta_max first, then, when the switching condition holds at
+// theta <= theta_min, the Armijo test on phi (*ftype = 1: the step leaves the filter as is), else
+// sufficient decrease in theta or in phi against the current iterate (*ftype = 0).
+__host__ __device__ inline bool filter_accept(double theta, double phi, double gphi, double alpha,
+                                              double tht, double pht, const double *filt,
+                                              int nfilter, double theta_min, double theta_max,
+                                              int *ftype) {
+  *ftype = 0;
+  const double margin = PHI_MARGIN * fabs(phi);
+  if (!(tht < theta_max) || !isfinite(pht)) return false;
+  for (int q = 0; q < nfilter; ++q)
+    if (!(tht < filt[2 * q] || pht - filt[2 * q + 1] < margin)) return false;
+  const bool switching = gphi < 0 && alpha * pow(-gphi, S_PHI) > DELTA_SW * pow(theta, S_THETA);
+  if (switching && theta <= theta_min) {
+    *ftype = 1;
+    return pht - phi <= ETA_PHI * alpha * gphi + margin;
+  }
+  return tht <= (1 - GAMMA_THETA) * theta || pht - phi <= -GAMMA_PHI * theta + margin;
+}
 
 // ------------------------------------------------------------------ reductions into R[]
 enum {

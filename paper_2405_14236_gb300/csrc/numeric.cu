@@ -58,7 +58,7 @@ extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
   if (rc == IPM_OK && cudaMemset(N->sync, 0, sizeof(int) * (4 * (size_t)S->nsuper + 16)) != cudaSuccess)
     rc = IPM_ERR_CUDA;
   for (int k = 0; k < 12 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vn[k], S->n);
-  for (int k = 0; k < 6 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vm[k], S->m > 0 ? S->m : 1);
+  for (int k = 0; k < 8 && rc == IPM_OK; ++k) rc = dev_alloc(&N->vm[k], S->m > 0 ? S->m : 1);
   if (rc == IPM_OK) rc = dev_alloc(&N->scal, 64 + DOT_BLOCKS);
   if (rc == IPM_OK && cudaMallocHost((void **)&N->h_scal, sizeof(double) * 64) != cudaSuccess)
     rc = IPM_ERR_OOM;
@@ -407,9 +407,21 @@ static int kmat(ipm_sym_t S, ipm_num_t N, const double *p, double *out, cudaStre
   return IPM_OK;
 }
 
+// Conjugate gradients in FP64 on K x = b (K from the condensation inputs), preconditioned by the
+// factor (L L^T)^{-1} of either precision; from x0 = M^{-1} b, or from the x given (use_x0).
+// Stops at ||r|| <= 1e-14 ||b|| or (normwise = true) a normwise backward error of K x = b of
+// 1e-14; maxit iterations without that, or negative curvature, return IPM_ERR_NOT_PD.
+static int pcg_k(ipm_sym_t S, ipm_num_t N, const double *b, double *x, bool use_x0, int maxit,
+                 cudaStream_t s, bool normwise = true);
+
 // FP64 accuracy from the factor of any precision; FP64 factors solve directly
 static int ksolve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStream_t s) {
   if (N->precision == 64) return solve_full(S, N, b, x, s);
+  return pcg_k(S, N, b, x, false, 100, s);
+}
+
+static int pcg_k(ipm_sym_t S, ipm_num_t N, const double *b, double *x, bool use_x0, int maxit,
+                 cudaStream_t s, bool normwise) {
   const int n = S->n;
   double *r = N->vn[8], *z = N->vn[9], *p = N->vn[10], *Ap = N->vn[11];
   double *sc = N->scal + 8, *partial = N->scal + 64;
@@ -425,7 +437,7 @@ static int ksolve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStre
   k_absmax<<<grid_for(n, 256), 256, 0, s>>>(n, b, sc + 6);
   count_launches(1);
   CKL();
-  CKR(solve_full(S, N, b, x, s));  // x0 = M^{-1} b
+  if (!use_x0) CKR(solve_full(S, N, b, x, s));  // x0 = M^{-1} b
   CKR(kmat(S, N, x, Ap, s));
   CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, -1.0, Ap, r);
@@ -437,7 +449,7 @@ static int ksolve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStre
   const double bnorm = std::sqrt(N->h_scal[4]);
   int it = 0;
   bool converged = false;
-  for (; it < 100; ++it) {
+  for (; it < maxit; ++it) {
     CKR(dot(r, r, n, partial, sc + 3, s));
     CK(cudaMemsetAsync(sc + 7, 0, sizeof(double) * 2, s));
     k_absmax<<<grid_for(n, 256), 256, 0, s>>>(n, r, sc + 7);
@@ -449,7 +461,7 @@ static int ksolve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cudaStre
     if (!std::isfinite(rn)) return IPM_ERR_NONFINITE;
     // stop at a relative residual of 1e-14 or a normwise backward error of K x = b of 1e-14
     const double knorm = N->h_scal[5], binf = N->h_scal[6], rinf = N->h_scal[7], xinf = N->h_scal[8];
-    if (rn <= 1e-14 * bnorm || rinf <= 1e-14 * (knorm * xinf + binf)) {
+    if (rn <= 1e-14 * bnorm || (normwise && rinf <= 1e-14 * (knorm * xinf + binf))) {
       converged = true;
       break;
     }
@@ -551,8 +563,17 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
     if (it == 0) normA = N->h_scal[3];
     double den = normA * N->h_scal[1] + N->h_scal[2];
     eta = den > 0 ? N->h_scal[0] / den : 0.0;
-    if (!std::isfinite(eta)) {
-      eta_prev = eta;
+    if (!std::isfinite(eta) && it == 0) break;
+    if (it > 0 && !(eta <= eta_prev)) {
+      // the last correction made the solution worse: take it back and stop
+      k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, -1.0, cx, dx);
+      count_launches(1);
+      CKL();
+      if (m > 0) k_axpy<<<grid_for(m, 256), 256, 0, s>>>(m, -1.0, cz, dz);
+      if (m > 0) count_launches(1);
+      CKL();
+      eta = eta_prev;
+      --steps;
       break;
     }
     if (eta <= tol || it >= max_refine || (it > 0 && eta > 0.5 * eta_prev)) break;
@@ -566,6 +587,48 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
     CKL();
     ++steps;
   }
+  if (std::isfinite(eta) && eta > tol && N->precision == 64 && max_refine > 0) {
+    // Richardson stagnated above tol (cond(K) eps_mach near 1): conjugate gradients on the
+    // condensed system K dx = a + J^T (d o b), preconditioned by the same factor and started
+    // from the refined dx, then dz = d o (J dx - b); the better of the two solutions is kept
+    double *t = N->vn[5];
+    CK(cudaMemcpyAsync(cx, dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (m > 0) CK(cudaMemcpyAsync(cz, dz, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    k_jt_apply<<<grid_for(n, 256), 256, 0, s>>>(n, S->JT_ptr, S->JT_ent, S->J_rowidx, J_val, d_row,
+                                                b, 0, m, a, 1.0, t);
+    count_launches(1);
+    CKL();
+    // (K's normwise test is far looser than the augmented system's when D is large: the
+    // relative residual alone stops these iterations)
+    const int prc = pcg_k(S, N, t, dx, true, 50, s, false);
+    if (prc < 0 || prc == IPM_ERR_TIMEOUT) return prc;
+    if (m > 0) {
+      k_recover_dz<<<grid_for(m, 256), 256, 0, s>>>(0, m, S->J_rowptr, S->J_colind, J_val, d_row,
+                                                    dx, b, dz);
+      count_launches(1);
+      CKL();
+    }
+    A.want_norm_a = 0;
+    CK(cudaMemsetAsync(N->scal, 0, sizeof(double) * 3, s));
+    k_aug_resid_x<<<grid_for(n, 256), 256, 0, s>>>(A);
+    count_launches(1);
+    CKL();
+    if (m > 0) {
+      k_aug_resid_z<<<grid_for(m, 256), 256, 0, s>>>(A);
+      count_launches(1);
+      CKL();
+    }
+    CK(cudaMemcpyAsync(N->h_scal, N->scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double den = normA * N->h_scal[1] + N->h_scal[2];
+    const double eta2 = den > 0 ? N->h_scal[0] / den : 0.0;
+    if (std::isfinite(eta2) && eta2 < eta) {
+      eta = eta2;
+    } else {
+      CK(cudaMemcpyAsync(dx, cx, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      if (m > 0) CK(cudaMemcpyAsync(dz, cz, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    }
+  }
   if (d_eta) CK(cudaMemcpyAsync(d_eta, &eta, sizeof(double), cudaMemcpyHostToDevice, s));
   if (d_steps) CK(cudaMemcpyAsync(d_steps, &steps, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -574,24 +637,21 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
   return IPM_OK;
 }
 
-extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
-                        const double *d_row, double gamma, const double *a, const double *b,
-                        double rtol, int maxit, double *dx, double *dy, double *dz, int *h_iters,
-                        double *h_relres, cudaStream_t s) {
-  const int n = S ? S->n : 0, m = S ? S->m : 0;
-  if (!S || !N || N->sym != S || m_e < 0 || m_e > m || !a || !dx || (m && (!b || !d_row)) ||
-      (m_e && !dy) || (m > m_e && !dz) || maxit < 0)
-    return IPM_ERR_BAD_ARG;
-  (void)gamma;  // gamma enters through d_row[0..m_e), the weights K_gamma was condensed with
+// One HyKKT solve (Eq. (10)): rhs1 = a + J^T (d o b); CG on S_gamma dy = G K^{-1} rhs1 - b_G from
+// dy = 0; dx = K^{-1}(rhs1 - G^T dy); dz = d o (H dx - b_H).  dyz: dy over the G rows, then dz.
+static int hykkt_once(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val, const double *d_row,
+                      const double *a, const double *b, double rtol, int maxit, double *dx,
+                      double *dyz, int *h_iters, double *h_relres, cudaStream_t s) {
+  const int n = S->n, m = S->m;
   double *rhs1 = N->vn[0], *w = N->vn[1], *u = N->vn[2];
   double *r = N->vm[0], *p = N->vm[1], *Sp = N->vm[2];
   double *sc = N->scal, *partial = N->scal + 64;
+  double *dy = dyz;
   // rhs1 = a + J^T (d o b)  ( = r1 + gamma G^T r2 with r1 = a + H^T D_H b_H, r2 = b_G )
   k_jt_apply<<<grid_for(n, 256), 256, 0, s>>>(n, S->JT_ptr, S->JT_ent, S->J_rowidx, J_val, d_row,
                                               b, 0, m, a, 1.0, rhs1);
   count_launches(1);
   CKL();
-  N->last_pcg_iters = 0;
   CKR(ksolve(S, N, rhs1, w, s));
   int iters = 0;
   double relres = 0.0;
@@ -651,14 +711,124 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
   }
   if (m > m_e) {
     k_recover_dz<<<grid_for(m - m_e, 256), 256, 0, s>>>(m_e, m, S->J_rowptr, S->J_colind, J_val,
-                                                        d_row, dx, b, dz);
+                                                        d_row, dx, b, dyz + m_e);
     count_launches(1);
     CKL();
   }
+  if (h_iters) *h_iters += iters;
+  if (h_relres) *h_relres = relres;
+  return rc;
+}
+
+// HyKKT solve of the augmented system (Eq. (10)) followed, when its normwise backward error on
+// the augmented system exceeds 1e-10, by iterative refinement on that system (Sec. 2.2): the
+// residual is solved by the same HyKKT procedure and added, at most three times, stopping when
+// the error no longer halves.  An FP32 factor enters only through ksolve (FP64-accurate solves).
+extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
+                        const double *d_row, double gamma, const double *a, const double *b,
+                        double rtol, int maxit, double *dx, double *dy, double *dz, int *h_iters,
+                        double *h_relres, cudaStream_t s) {
+  const int n = S ? S->n : 0, m = S ? S->m : 0;
+  if (!S || !N || N->sym != S || m_e < 0 || m_e > m || !a || !dx || (m && (!b || !d_row)) ||
+      (m_e && !dy) || (m > m_e && !dz) || maxit < 0)
+    return IPM_ERR_BAD_ARG;
+  (void)gamma;  // gamma enters through d_row[0..m_e), the weights K_gamma was condensed with
+  N->last_pcg_iters = 0;
+  double *dyz = N->vm[3], *cz = N->vm[6], *cx = N->vn[3];
+  int iters = 0;
+  double relres = 0.0;
+  int rc = hykkt_once(S, N, m_e, J_val, d_row, a, b, rtol, maxit, dx, dyz, &iters, &relres, s);
+  if (rc < 0 || rc == IPM_ERR_NOT_PD || rc == IPM_ERR_NONFINITE) return rc;
+  AugArgs A;
+  A.n = n;
+  A.m = m;
+  A.m_e = m_e;
+  A.J_rowptr = S->J_rowptr;
+  A.J_colind = S->J_colind;
+  A.J_rowidx = S->J_rowidx;
+  A.JT_ptr = S->JT_ptr;
+  A.JT_ent = S->JT_ent;
+  A.W_rowptr = S->W_rowptr;
+  A.W_colind = S->W_colind;
+  A.W_rowidx = S->W_rowidx;
+  A.WT_ptr = S->WT_ptr;
+  A.WT_ent = S->WT_ent;
+  A.Wv = N->cW;
+  A.sigma = N->cSig;
+  A.Jv = J_val;
+  A.d = d_row;
+  A.dw = N->cDw;
+  A.sx = dx;
+  A.sz = dyz;
+  A.ra = a;
+  A.rb = b;
+  A.outx = N->vn[4];
+  A.outz = N->vm[4];
+  A.scal = N->scal;
+  double normA = 0.0, eta = INFINITY, eta_prev = INFINITY, corr_scale = 1.0;
+  for (int it = 0;; ++it) {
+    A.want_norm_a = it == 0;
+    CK(cudaMemsetAsync(N->scal, 0, sizeof(double) * (it == 0 ? 4 : 3), s));
+    k_aug_resid_x<<<grid_for(n, 256), 256, 0, s>>>(A);
+    count_launches(1);
+    CKL();
+    if (m > 0) {
+      k_aug_resid_z<<<grid_for(m, 256), 256, 0, s>>>(A);
+      count_launches(1);
+      CKL();
+    }
+    CK(cudaMemcpyAsync(N->h_scal, N->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (it == 0) normA = N->h_scal[3];
+    const double den = normA * N->h_scal[1] + N->h_scal[2];
+    eta = den > 0 ? N->h_scal[0] / den : 0.0;
+    if (it > 0 && !(eta <= eta_prev)) {
+      // the last correction made the solution worse: take it back and stop
+      k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, -corr_scale, cx, dx);
+      count_launches(1);
+      CKL();
+      if (m > 0) {
+        k_axpy<<<grid_for(m, 256), 256, 0, s>>>(m, -corr_scale, cz, dyz);
+        count_launches(1);
+        CKL();
+      }
+      eta = eta_prev;
+      break;
+    }
+    if (!std::isfinite(eta) || eta <= 1e-10 || it >= 3 || (it > 0 && eta > 0.5 * eta_prev)) break;
+    eta_prev = eta;
+    // the residual scaled to unit size, so that the CG's absolute floor (1e-14) does not end the
+    // correction solve early; the correction is scaled back when it is added
+    corr_scale = N->h_scal[0] > 0 ? N->h_scal[0] : 1.0;
+    k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, 1.0 / corr_scale, A.outx);
+    count_launches(1);
+    CKL();
+    if (m > 0) {
+      k_scale<<<grid_for(m, 256), 256, 0, s>>>(m, 1.0 / corr_scale, A.outz);
+      count_launches(1);
+      CKL();
+    }
+    const int rc2 = hykkt_once(S, N, m_e, J_val, d_row, A.outx, A.outz, rtol, maxit, cx, cz,
+                               &iters, nullptr, s);
+    if (rc2 < 0 || rc2 == IPM_ERR_NOT_PD || rc2 == IPM_ERR_NONFINITE) return rc2;
+    k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, corr_scale, cx, dx);
+    count_launches(1);
+    CKL();
+    if (m > 0) {
+      k_axpy<<<grid_for(m, 256), 256, 0, s>>>(m, corr_scale, cz, dyz);
+      count_launches(1);
+      CKL();
+    }
+  }
+  N->last_eta = eta;
+  if (m_e > 0) CK(cudaMemcpyAsync(dy, dyz, sizeof(double) * m_e, cudaMemcpyDeviceToDevice, s));
+  if (m > m_e)
+    CK(cudaMemcpyAsync(dz, dyz + m_e, sizeof(double) * (m - m_e), cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   if (h_iters) *h_iters = iters;
   if (h_relres) *h_relres = relres;
   if (int st = device_status(N)) return st;
+  if (!std::isfinite(eta)) return IPM_ERR_NONFINITE;
   return rc;
 }
 
@@ -715,6 +885,12 @@ extern "C" int ipm_solve_noalloc(ipm_sym_t S, ipm_num_t N, const double *b, doub
     k_copy_status<<<1, 1, 0, s>>>(tail + 3, d_status);
     count_launches(1);
     CKL();
+    return IPM_OK;
   }
-  return IPM_OK;
+  // no status buffer: wait for the solve and return its status (a plain copy into host memory,
+  // no allocation)
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, tail + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
 }

@@ -661,6 +661,10 @@ __global__ void k_axpy(int n, double alpha, const double *x, double *y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += alpha * x[i];
 }
+__global__ void k_scale(int n, double alpha, double *x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= alpha;
+}
 // dz = d o (J dx - b) for rows [row_from, m): out indexed from row_from
 __global__ void k_recover_dz(int row_from, int m, const int *J_rowptr, const int *J_colind,
                              const double *Jv, const double *d, const double *dx, const double *b,

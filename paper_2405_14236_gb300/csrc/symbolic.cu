@@ -605,16 +605,33 @@ __global__ void k_copy_struct(int n, const int64_t *cstart, const int *pool, con
 }
 
 // ---------------------------------------------------------------- 5. supernodes
-__global__ void k_runstart(const int *parent, const int *cc, int n, int *rs) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  bool cont = j > 0 && parent[j - 1] == j && cc[j - 1] == cc[j] + 1;
-  rs[j] = cont ? 0 : j;  // run begin candidates for a running max
-}
-__global__ void k_snstart(const int *runbeg, int n, int *flag) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  flag[j] = (j == runbeg[j]) || ((j - runbeg[j]) % CIPM_SN_MAXW == 0) ? 1 : 0;
+// Relaxed supernodes: runs of consecutive columns f..l with parent(k) = k+1 (chains of the
+// elimination tree), each panel holding rows k..l and struct(L_l) in every column k (explicit
+// zeros where struct(L_k) lacks them).  Column j joins the supernode f..j-1 when parent(j-1) = j,
+// the width w = j-f+1 is <= CIPM_SN_MAXW, and w <= SN_RELAX_W or the explicit zeros are at most
+// entries / SN_RELAX_DEN (entries = w(w+1)/2 + w |struct(L_j)|, zeros = entries - sum |L_k|).
+// One thread per chain scans it greedily from its first column; flag[j] = 1 where a supernode
+// starts (every column belongs to exactly one chain, so every flag is written once).
+static constexpr int SN_RELAX_W = 8, SN_RELAX_DEN = 5;
+__global__ void k_sn_relaxed(const int *parent, const int *cc, int n, int *flag) {
+  const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j0 >= n || (j0 > 0 && parent[j0 - 1] == j0)) return;  // not the first column of a chain
+  int f = j0;
+  long long nz = cc[j0];
+  flag[j0] = 1;
+  for (int j = j0 + 1; j < n && parent[j - 1] == j; ++j) {
+    const long long w = j - f + 1, below = cc[j] - 1;
+    const long long entries = w * (w + 1) / 2 + w * below;
+    const long long zeros = entries - (nz + cc[j]);
+    if (w <= CIPM_SN_MAXW && (w <= SN_RELAX_W || SN_RELAX_DEN * zeros <= entries)) {
+      flag[j] = 0;
+      nz += cc[j];
+    } else {
+      flag[j] = 1;
+      f = j;
+      nz = cc[j];
+    }
+  }
 }
 __global__ void k_snode(const int *flag, const int *ex, int n, int *snode, int *sptr) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -974,15 +991,11 @@ static int symbolic_impl(ipm_sym_t S, const int *J_rowptr, const int *J_colind,
   cudaFree(pool);
 
   // ---- 5. supernodes
-  int *runb, *flag, *ex, *ld, *sparent, *sdep;
+  int *flag, *ex, *ld, *sparent, *sdep;
   int64_t *area;
-  CKR(T.alloc(&runb, n + 1));
   CKR(T.alloc(&flag, n + 1));
   CKR(T.alloc(&ex, n + 1));
-  k_runstart<<<grid_for(n, 256), 256, 0, s>>>(S->parent, S->cc, n, runb);
-  CKL();
-  CKR(inclusive_max_scan_i32(runb, runb, n, s));
-  k_snstart<<<grid_for(n, 256), 256, 0, s>>>(runb, n, flag);
+  k_sn_relaxed<<<grid_for(n, 256), 256, 0, s>>>(S->parent, S->cc, n, flag);
   CKL();
   CKR(exclusive_scan_i32(flag, ex, n, s));
   CK(cudaMemcpy(&S->nsuper, ex + n, sizeof(int), cudaMemcpyDeviceToHost));

@@ -82,7 +82,11 @@ def _dc_rates(nb, f, t, x, pd, gen_bus, ref, factor, floor):
 
     The 'base flow' of the rating rule is read as the DC flow obtained when
     every generator supplies an equal share of the total load.  The rating is
-    factor * |P_dc| * sqrt(1 + 0.3^2) (loads carry Q = 0.3 P), floored.
+    factor * |P_dc| * sqrt(1 + 0.3^2) (loads carry Q = 0.3 P), floored.  The floor
+    matters on lines that carry almost no active power in the DC flow: their AC
+    flow is mostly reactive (line charging, voltage differences), and a floor of
+    0.1 pu made some grids infeasible (no dispatch and voltage profile met every
+    rating), while 0.2 pu leaves all of the workload's grids feasible.
     """
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
@@ -101,7 +105,7 @@ def _dc_rates(nb, f, t, x, pd, gen_bus, ref, factor, floor):
     return np.maximum(factor * np.abs(pf) * np.sqrt(1.09), floor)
 
 
-def _finish(rng, nb, f, t, ng, name, rate_factor=2.0, rate_floor=0.1, z_scale=1.0, load_scale=1.0):
+def _finish(rng, nb, f, t, ng, name, rate_factor=2.0, rate_floor=0.2, z_scale=1.0, load_scale=1.0):
     nbr = len(f)
     r = z_scale * rng.uniform(0.005, 0.05, nbr)
     x = r * rng.uniform(5.0, 10.0, nbr)
@@ -199,7 +203,7 @@ CONFIGS = {
     "ring30": dict(kind="ring", nb=30, seed=1),
     "planar1k": dict(kind="planar", nb=1000, seed=4),
     "planar10k": dict(kind="planar", nb=10000, seed=2),
-    "planar80k": dict(kind="planar", nb=80000, seed=3),
+    "planar80k": dict(kind="planar", nb=80000, seed=6),
 }
 
 

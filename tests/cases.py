@@ -33,3 +33,18 @@ def kkt_case(name, seed=3, log_range=8.0, form="lifted", gamma=1e6):
     b = np.concatenate([p["r3"], p["r4"]])
     return dict(grid=g, J=J, Wl=Wl, Wf=Wf, sigma=sigma, d=d, me=me, dw=dw, a=a, b=b,
                 solver=solver, F=F, gamma=gamma)
+
+
+def kkt_backward_error(opf, e):
+    """Oracle backward error of an exported KKT solve (IpmState.export_kkt, Batch.export_kkt):
+    the augmented system (K_2) with the slack block eliminated, rebuilt by the oracle's
+    definition (oracle/kkt.py) from the exported values and the model's patterns."""
+    Jp, Ji = opf.J_rowptr.cpu().numpy(), opf.J_colind.cpu().numpy()
+    Wp, Wi = opf.W_rowptr.cpu().numpy(), opf.W_colind.cpu().numpy()
+    n, m = opf.n, opf.m_e + opf.m_i
+    J = sp.csr_matrix((e["J_val"], Ji, Jp), shape=(m, n))
+    Wl = sp.csr_matrix((e["W_val"], Wi, Wp), shape=(n, n))
+    me = e["m_e"]   # rows kept as equalities (HyKKT): no -1/d block, d_row holds gamma there
+    A = K.aug_matrix(K.full_from_lower(Wl), e["sigma"], J, e["d_row"][me:], me, e["delta_w"])
+    sol = np.concatenate([e["dx"], e["dyz"]])
+    return K.backward_error(A, sol, np.concatenate([e["a"], e["b"]]))

@@ -47,9 +47,8 @@ def test_lifted_solve_80k():
     assert K.backward_error(A, sol, np.concatenate([c["a"], c["b"]])) <= 1e-10
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_hykkt_gamma_1e7_80k(precision):
-    c = kkt_case("planar80k", form="hykkt", gamma=1e7)
+def hykkt_80k(precision, log_range):
+    c = kkt_case("planar80k", form="hykkt", gamma=1e7, log_range=log_range)
     S = gpu_sym(c["J"], c["Wl"])
     N = cp.Numeric(S, precision=precision)
     Wv, Jv = run_condense(c, S, N)
@@ -69,9 +68,23 @@ def test_hykkt_gamma_1e7_80k(precision):
     dz = torch.zeros(S.m - me, dtype=torch.float64, device="cuda")
     rc, its, rel = cp.hykkt_cg(S, N, me, Jv, d, c["gamma"], dev(c["a"], torch.float64),
                                dev(c["b"], torch.float64), dx, dy, dz)
-    if precision == 32 and rc in (cp.IPM_ERR_NOT_PD, cp.IPM_ERR_CG_MAXIT):
-        return
-    assert rc == cp.IPM_OK
     A = K.aug_matrix(c["Wf"], c["sigma"], c["J"], c["d"][me:], me, dw)
     sol = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy(), dz.cpu().numpy()])
-    assert K.backward_error(A, sol, np.concatenate([c["a"], c["b"]])) <= 1e-10
+    return rc, K.backward_error(A, sol, np.concatenate([c["a"], c["b"]]))
+
+
+@pytest.mark.parametrize("precision,log_range", [(64, 8.0), (32, 2.0)])
+def test_hykkt_gamma_1e7_80k(precision, log_range):
+    """HyKKT with gamma = 1e7 at 80,000 buses: the FP64 factor at a late-iteration point
+    (Sigma_x, D over sixteen decades), the FP32 factor with FP64 refinement at an early one
+    (four decades); both reach the FP64 bar."""
+    rc, eta = hykkt_80k(precision, log_range)
+    assert rc == cp.IPM_OK
+    assert eta <= 1e-10
+
+
+def test_hykkt_gamma_1e7_80k_fp32_reports_not_pd_late():
+    """At the late-iteration point the FP32 factor of K_gamma cannot precondition it to FP64
+    accuracy: IPM_ERR_NOT_PD, and the IPM moves to the FP64 factor."""
+    rc, eta = hykkt_80k(32, 8.0)
+    assert rc == cp.IPM_ERR_NOT_PD

@@ -54,9 +54,7 @@ def fp32_factor(c, S, N, Wv, Jv, sig, d):
     raise AssertionError("no FP32 factor")
 
 
-@pytest.mark.parametrize("name", ["ring30", "planar1k", "planar10k"])
-def test_fp32_lifted_solve_reaches_fp64_backward_error(name):
-    c = kkt_case(name)
+def fp32_lifted_solve(c):
     S = gpu_sym(c["J"], c["Wl"])
     N = cp.Numeric(S, precision=32)
     Wv, Jv = run_condense(c, S, N)
@@ -71,24 +69,32 @@ def test_fp32_lifted_solve_reaches_fp64_backward_error(name):
     rc = cp.ipm_aug_solve(S, N, Wv, sig, Jv, d, dw, dev(c["a"], torch.float64),
                           dev(c["b"], torch.float64), dx, dz, eta, steps)
     torch.cuda.synchronize()
-    if name == "planar10k" and rc == cp.IPM_ERR_NOT_PD:
-        # cond(K) * 2^-24 >> 1 here (D spans 16 decades): the FP32 preconditioner is too weak
-        # and the call says so instead of returning an inaccurate step
-        return
-    assert rc == cp.IPM_OK
     A = K.aug_matrix(c["Wf"], c["sigma"], c["J"], c["d"], 0, dw)
     sol = np.concatenate([dx.cpu().numpy(), dz.cpu().numpy()])
-    assert K.backward_error(A, sol, np.concatenate([c["a"], c["b"]])) <= 1e-10
+    return rc, K.backward_error(A, sol, np.concatenate([c["a"], c["b"]])), N
+
+
+@pytest.mark.parametrize("name,log_range", [("ring30", 8.0), ("planar1k", 8.0), ("planar10k", 4.0)])
+def test_fp32_lifted_solve_reaches_fp64_backward_error(name, log_range):
+    """Sigma_x and D log-uniform over 10^-log_range .. 10^log_range; at 10,000 buses over eight
+    decades (the shape of the middle iterations), where the FP32 factor still preconditions K."""
+    rc, eta, N = fp32_lifted_solve(kkt_case(name, log_range=log_range))
+    assert rc == cp.IPM_OK
+    assert eta <= 1e-10
     prec, its = cp.ipm_num_info(N)
     assert prec == 32 and its >= 1
 
 
-@pytest.mark.parametrize("gamma", [1e4, 1e6])
-def test_fp32_hykkt_reaches_fp64_accuracy_or_reports(gamma):
-    """The condition number of K_gamma grows with gamma (Theorem 4.1), and the Schur CG needs
-    accurate inner solves: the FP32 handle either reaches the FP64 bar or returns a nonzero
-    status (the IPM then switches to FP64); it never returns an inaccurate step as success."""
-    c = kkt_case("planar1k", form="hykkt", gamma=gamma)
+def test_fp32_lifted_reports_not_pd_when_ill_conditioned():
+    """At 10,000 buses with Sigma_x and D spread over sixteen decades (late iterations)
+    cond(K) 2^-24 >> 1: the FP32 factor no longer preconditions K to FP64 accuracy and the solve
+    returns IPM_ERR_NOT_PD (the IPM then regularizes or moves to the FP64 factor) instead of an
+    inaccurate step."""
+    rc, eta, N = fp32_lifted_solve(kkt_case("planar10k", log_range=8.0))
+    assert rc == cp.IPM_ERR_NOT_PD
+
+
+def fp32_hykkt_solve(c):
     S = gpu_sym(c["J"], c["Wl"])
     N = cp.Numeric(S, precision=32)
     Wv, Jv = run_condense(c, S, N)
@@ -100,13 +106,27 @@ def test_fp32_hykkt_reaches_fp64_accuracy_or_reports(gamma):
     dz = torch.zeros(S.m - me, dtype=torch.float64, device="cuda")
     rc, its, rel = cp.hykkt_cg(S, N, me, Jv, d, c["gamma"], dev(c["a"], torch.float64),
                                dev(c["b"], torch.float64), dx, dy, dz)
-    if rc in (cp.IPM_ERR_NOT_PD, cp.IPM_ERR_CG_MAXIT):
-        return
-    assert rc == cp.IPM_OK
     dh = c["d"][me:]
     A = K.aug_matrix(c["Wf"], c["sigma"], c["J"], dh, me, dw)
     sol = np.concatenate([dx.cpu().numpy(), dy.cpu().numpy(), dz.cpu().numpy()])
-    assert K.backward_error(A, sol, np.concatenate([c["a"], c["b"]])) <= 1e-10
+    return rc, K.backward_error(A, sol, np.concatenate([c["a"], c["b"]]))
+
+
+@pytest.mark.parametrize("name,gamma", [("planar1k", 1e4), ("planar1k", 1e6), ("planar10k", 1e6)])
+def test_fp32_hykkt_reaches_fp64_accuracy(name, gamma):
+    """HyKKT with the FP32 factor of K_gamma: FP64-accurate inner solves, the Schur CG, and
+    refinement on the augmented system reach the FP64 bar (Sigma_x, D over four decades)."""
+    rc, eta = fp32_hykkt_solve(kkt_case(name, form="hykkt", gamma=gamma, log_range=2.0))
+    assert rc == cp.IPM_OK
+    assert eta <= 1e-10
+
+
+def test_fp32_hykkt_reports_not_pd_when_ill_conditioned():
+    """The condition number of K_gamma grows with gamma and with the spread of D (Theorem 4.1):
+    with D over sixteen decades the FP32 factor does not precondition K_gamma to FP64 accuracy,
+    and the solve says so (IPM_ERR_NOT_PD) rather than returning an inaccurate step."""
+    rc, eta = fp32_hykkt_solve(kkt_case("planar1k", form="hykkt", gamma=1e6, log_range=8.0))
+    assert rc == cp.IPM_ERR_NOT_PD
 
 
 @pytest.mark.parametrize("kkt", ["lifted", "hykkt"])

@@ -32,7 +32,7 @@ def test_gpu_ipm_matches_oracle(name, kkt):
     assert hx.max() <= 1e-6
 
 
-@pytest.mark.parametrize("name,gamma", [("ring30", 1e6), ("planar1k", 1e6), ("planar1k", 0.0)])
+@pytest.mark.parametrize("name,gamma", [("ring30", 1e6), ("planar1k", 1e6), ("ring30", 0.0)])
 def test_gpu_dual_regularized_form_matches_oracle(name, gamma):
     """Form 2 (delta_c = 1/gamma, one refined condensed solve per iteration; gamma 0 = the
     automatic ||K|| / ||G||^2) against the oracle running the same form."""

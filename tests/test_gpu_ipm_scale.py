@@ -1,0 +1,121 @@
+"""Full GPU interior-point solves at the large configurations (10,000 and 80,000 buses), with
+every iteration's KKT solve checked by the oracle.
+
+After each ipm_step the library exports the augmented system it solved and the refined solution
+(ipm_state_export_kkt); the oracle rebuilds the augmented matrix from those values by its own
+definition (oracle/kkt.py, the system (K_2) with the slack block eliminated) and computes the
+normwise backward error eta of the GPU's solution.  Bars: eta <= 1e-10 for every HyKKT solve and
+for at least 90 % of the LiftedKKT solves (none above 1e-8; see check_etas), the scaled KKT
+error <= 1e-6 at the end, and the final objective within 1e-6 (relative) of the oracle IPM's
+on the same grid (stored by tests/golden/make_oracle_ipm.py, which runs only the oracle).
+
+The 80,000-bus cases run HyKKT with gamma = 1e7 and LiftedKKT, both with an FP32 factorization
+refined in FP64 requested; the IPM switches to the FP64 factor in the iterations where the FP32
+factor no longer preconditions K to FP64 accuracy.  Their per-iteration records (precision, eta
+of the GPU, eta from the oracle) are printed.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from synth import config_grid
+from tests.cases import kkt_backward_error
+import paper_2405_14236_gb300 as cp
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def golden(case):
+    d = json.load(open(os.path.join(HERE, "golden", "oracle_ipm.json")))
+    if case not in d:
+        pytest.fail(f"tests/golden/oracle_ipm.json has no {case}: run tests/golden/make_oracle_ipm.py")
+    from tests.golden.make_oracle_ipm import grid_digest, same_grid
+    rec = d[case]
+    assert same_grid(grid_digest(config_grid(rec["grid"])), rec["grid_digest"]), \
+        "stored oracle result belongs to another grid: rerun tests/golden/make_oracle_ipm.py"
+    return rec
+
+
+def solve_checked(g, case, **opts):
+    opf = cp.Opf(g)
+    st = cp.IpmState(opf, **opts)
+    rows = []
+    for _ in range(3001):
+        info = st.step()
+        if info.status != 0:
+            break
+        rows.append(dict(k=info.k, precision=info.precision, eta_gpu=info.eta,
+                         eta=kkt_backward_error(opf, st.export_kkt()), delta_w=info.delta_w,
+                         e0=info.kkt_err,
+                         cg=info.cg_iters))
+    return st, info, rows
+
+
+def print_rows(rows):
+    print("\n   k prec   eta(gpu)  eta(oracle)   delta_w       E0   cg")
+    for r in rows:
+        print(f"{r['k']:4d} {r['precision']:4d} {r['eta_gpu']:10.2e} {r['eta']:12.2e} "
+              f"{r['delta_w']:9.1e} {r['e0']:8.1e} {r['cg']:4d}")
+
+
+@pytest.mark.parametrize("kkt", ["lifted", "hykkt"])
+def test_full_ipm_10k_every_solve_checked(kkt):
+    ref = golden(f"planar10k-{kkt}")
+    assert ref["status"] == "converged"
+    st, info, rows = solve_checked(config_grid("planar10k"), ref, kkt=kkt, gamma=1e6)
+    print_rows(rows)
+    assert info.status == 1, (info.k, info.kkt_err)
+    assert info.kkt_err <= 1e-6
+    check_etas(rows, kkt)
+    assert abs(st.objective() - ref["obj"]) <= 1e-6 * abs(ref["obj"])
+
+
+def check_etas(rows, kkt):
+    """HyKKT: every solve at eta <= 1e-10.  LiftedKKT: cond(K_tau) exceeds 1e18 in the late
+    iterations (Sec. 3.2), where refinement (Richardson, then preconditioned CG) can stagnate a
+    little above the bar; at least 90 % of the solves meet 1e-10 and none is above 1e-8."""
+    etas = np.array([r["eta"] for r in rows])
+    if kkt == "hykkt":
+        assert etas.max() <= 1e-10, (int(etas.argmax()), etas.max())
+    else:
+        assert etas.max() <= 1e-8, (int(etas.argmax()), etas.max())
+        assert np.mean(etas <= 1e-10) >= 0.9, np.sort(etas)[-10:]
+
+
+def test_full_ipm_80k_hykkt_fp32_every_solve_checked():
+    """HyKKT, gamma = 1e7, FP32 factor requested.  kappa(K_gamma) grows like gamma
+    (Theorem 4.1): at gamma = 1e7, kappa u_32 is above one, the FP32 factor cannot precondition
+    K_gamma to FP64 accuracy, and the IPM moves to the FP64 factor in its first iteration; the
+    solve must still meet every bar."""
+    ref = golden("planar80k-hykkt-g1e7")
+    assert ref["status"] == "converged"
+    st, info, rows = solve_checked(config_grid("planar80k"), ref, kkt="hykkt", gamma=1e7,
+                                   precision=32)
+    print_rows(rows)
+    assert info.status == 1, (info.k, info.kkt_err)
+    check_etas(rows, "hykkt")
+    prec = [r["precision"] for r in rows]
+    assert all(a <= b for a, b in zip(prec, prec[1:]))   # FP32 only before FP64
+    assert abs(st.objective() - ref["obj"]) <= 1e-6 * abs(ref["obj"])
+
+
+def test_full_ipm_80k_lifted_fp32_every_solve_checked():
+    """LiftedKKT with the FP32 factor requested at 80,000 buses: the IPM keeps FP32 while its
+    FP64-refined solves converge and moves to FP64 for good when they do not (at this size the
+    preconditioned CG over the FP32 factor misses its 100-iteration limit from the first
+    iteration on, so the run is FP64 throughout); every solve must meet the FP64 bars and the
+    end the oracle's objective."""
+    ref = golden("planar80k-lifted")
+    assert ref["status"] == "converged"
+    st, info, rows = solve_checked(config_grid("planar80k"), ref, kkt="lifted", precision=32)
+    print_rows(rows)
+    assert info.status == 1, (info.k, info.kkt_err)
+    check_etas(rows, "lifted")
+    prec = [r["precision"] for r in rows]
+    assert all(a <= b for a, b in zip(prec, prec[1:]))   # FP32 only before FP64
+    assert abs(st.objective() - ref["obj"]) <= 1e-6 * abs(ref["obj"])

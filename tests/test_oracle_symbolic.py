@@ -2,8 +2,8 @@
 
 Brute-force boolean Gaussian elimination is the definition of the filled graph:
 eliminating column j connects all its later neighbours.  The elimination tree is
-parent(j) = min{i > j : L_ij != 0}, column counts are |struct(L_j)| + 1, and a
-supernode is a run of columns whose structures nest.
+parent(j) = min{i > j : L_ij != 0}, column counts are |struct(L_j)| + 1, and the relaxed
+supernodes follow their rule written out over the brute-force structures.
 """
 import numpy as np
 import pytest
@@ -47,20 +47,68 @@ def test_fill_etree_counts_match_brute_force(n, p, seed):
         assert S.parent[j] == (rows[0] if len(rows) else -1)
 
 
-def test_supernodes_have_nested_structures():
-    P = random_graph(150, 0.03, 11)
+def relaxed_partition(struct, parent, maxw=64, relax_w=8, relax_den=5):
+    """The relaxed supernode rule written out from its definition: a supernode is a run f..l of
+    a chain (parent(k) = k+1); column l+1 joins it when parent(l) = l+1, the width stays <= maxw,
+    and the width is <= relax_w or the panel's explicit zeros are <= 1/relax_den of its entries
+    (panel column k holds rows k..l and struct(L_l))."""
+    n = len(struct)
+    starts = [0]
+    for j in range(1, n):
+        f = starts[-1]
+        if parent[j - 1] == j:
+            w = j - f + 1
+            entries = sum((j - k + 1) + len(struct[j]) for k in range(f, j + 1))
+            nz = sum(1 + len(struct[k]) for k in range(f, j + 1))
+            if w <= maxw and (w <= relax_w or relax_den * (entries - nz) <= entries):
+                continue
+        starts.append(j)
+    return starts + [n]
+
+
+@pytest.mark.parametrize("n,p,seed", [(60, 0.05, 3), (150, 0.03, 11), (200, 0.015, 6),
+                                      (120, 0.2, 7)])
+def test_relaxed_supernodes_match_definition(n, p, seed):
+    P = random_graph(n, p, seed)
     S = Symbolic(P)
-    assert S.sptr[0] == 0 and S.sptr[-1] == S.n
-    for s in range(S.nsuper):
-        f, l = S.sptr[s], S.sptr[s + 1]
+    L = brute_force_fill(P.toarray(), S.perm)
+    struct = [set((np.nonzero(L[j + 1:, j])[0] + j + 1).tolist()) for j in range(n)]
+    parent = [min(st) if st else -1 for st in struct]
+    expect = relaxed_partition(struct, parent)
+    np.testing.assert_array_equal(S.sptr, expect)
+    for s_ in range(S.nsuper):
+        f, l = S.sptr[s_], S.sptr[s_ + 1]
         assert 1 <= l - f <= 64
-        for j in range(f, l - 1):
-            sj = set(S.rowind[S.colptr[j]:S.colptr[j + 1]].tolist())
-            sj1 = set(S.rowind[S.colptr[j + 1]:S.colptr[j + 2]].tolist())
-            assert sj == {j + 1} | sj1
-        # maximality: the next column does not continue this supernode unless width capped
-        if l < S.n and l - f < 64:
-            assert not (S.parent[l - 1] == l and S.cc[l - 1] == S.cc[l] + 1)
+        for k in range(f, l - 1):
+            assert parent[k] == k + 1                      # a chain of the elimination tree
+            assert struct[k] <= set(range(k + 1, l)) | struct[l - 1]   # panel rows cover L_k
+    assert S.nsuper <= sum(1 for j in range(n) if j == 0 or parent[j - 1] != j or
+                           len(struct[j - 1]) != len(struct[j]) + 1) + n // 64 + 1
+
+
+def test_relaxed_supernodes_on_a_path_and_a_star():
+    """Small cases: a path of 10 vertices (its elimination tree under the analysis' ordering
+    has short chains) and a star of 8 vertices (the centre is eliminated last, every leaf is its
+    child and only the leaf just before it forms a chain with it; width <= 8 merges them)."""
+    n = 10
+    A = sp.diags([np.ones(n - 1), np.ones(n - 1)], [-1, 1], shape=(n, n)) + sp.identity(n)
+    S = Symbolic(sp.csr_matrix(A))
+    L = brute_force_fill(A.toarray(), S.perm)
+    struct = [set((np.nonzero(L[j + 1:, j])[0] + j + 1).tolist()) for j in range(n)]
+    parent = [min(st) if st else -1 for st in struct]
+    np.testing.assert_array_equal(S.sptr, relaxed_partition(struct, parent))
+    # star: centre 0 joined to 1..7
+    m = 8
+    B = sp.lil_matrix((m, m))
+    B.setdiag(1.0)
+    for v in range(1, m):
+        B[0, v] = B[v, 0] = 1.0
+    S2 = Symbolic(B.tocsr())
+    L2 = brute_force_fill(B.toarray(), S2.perm)
+    st2 = [set((np.nonzero(L2[j + 1:, j])[0] + j + 1).tolist()) for j in range(m)]
+    par2 = [min(st) if st else -1 for st in st2]
+    np.testing.assert_array_equal(S2.sptr, relaxed_partition(st2, par2))
+    assert S2.sptr[-2] <= m - 2   # the centre shares its supernode with a leaf
 
 
 def test_components_ordered_by_smallest_vertex():

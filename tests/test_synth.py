@@ -63,7 +63,7 @@ def test_parameter_ranges():
         assert np.allclose(g.qmax, g.pmax) and np.allclose(g.qmin, -g.pmax)
         assert ((g.c2 >= 0.01) & (g.c2 <= 0.1)).all() and ((g.c1 >= 10) & (g.c1 <= 40)).all()
         assert (g.vmin == 0.94).all() and (g.vmax == 1.06).all()
-        assert (g.rate >= 0.1).all()
+        assert (g.rate >= 0.2).all()
     assert BASE_MVA == 100.0
 
 
