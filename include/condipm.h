@@ -303,6 +303,8 @@ typedef struct {
   int n_factor, cg_iters, refine_steps, ls_steps;
   int precision;    /* factorization precision used by this iteration (32 or 64) */
   double gamma;     /* gamma used by this iteration (forms 1 and 2) */
+  int pcg_iters;    /* FP64 CG iterations over the FP32 factor in this step's solves (0 in FP64;
+                       also the CG after a stagnating refinement) */
 } ipm_iter_info;
 
 typedef struct ipm_state_s *ipm_state_t;

@@ -105,7 +105,8 @@ class IpmIterInfo(ctypes.Structure):
                 ("delta_w", ctypes.c_double), ("obj", ctypes.c_double), ("eta", ctypes.c_double),
                 ("theta", ctypes.c_double), ("n_factor", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("ls_steps", ctypes.c_int),
-                ("precision", ctypes.c_int), ("gamma", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("pcg_iters", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -569,6 +569,7 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     ok = true;
     info->precision = num == S->num32 ? 32 : 64;
     if (S->opt.kkt == 1) info->eta = num->last_eta;
+    info->pcg_iters = num->last_pcg_iters;
     break;
   }
   if (!ok) return IPM_ERR_INERTIA;
