@@ -55,8 +55,8 @@ typedef struct ipm_num_s *ipm_num_t; /* numeric factor storage + workspaces for 
  * Pattern of the condensed matrix K = W + Sigma_x + delta_w I + J^T D J (Eq. (K_1), (9),
  * (13)): pat(W) united with the diagonal and pat(J^T J).  Computed entirely on the GPU:
  * graph of K, nested-dissection ordering (project-defined deterministic rule), elimination
- * tree, column structures of L, supernodes (width <= 64), condensation index maps and the
- * level schedule.
+ * tree, column structures of L, relaxed supernodes (ipm_symbolic_relaxed with (8, 5)),
+ * condensation index maps and the level schedule.
  *   n            number of primal variables
  *   m            rows of J (m_e + m_i)
  *   J_rowptr     [m+1] CSR row pointers of J (device)
@@ -71,6 +71,19 @@ typedef struct ipm_num_s *ipm_num_t; /* numeric factor storage + workspaces for 
 int ipm_symbolic(int n, int m, const int *J_rowptr, const int *J_colind, int nnzJ,
                  const int *W_rowptr, const int *W_colind, int nnzW, cudaStream_t stream,
                  ipm_sym_t *out);
+/* ipm_symbolic with the supernode partition's parameters (the shape of the supernodal panels).
+ * A supernode is a run f..l of consecutive columns with parent(k) = k+1 (a chain of the
+ * elimination tree), width <= 64, whose panel holds in every column k the rows k..l and
+ * struct(L_l) (explicit zeros where struct(L_k) has none).  Scanning the columns in order,
+ * column l+1 joins f..l when parent(l) = l+1, the width stays <= 64, and the width is <= relax_w,
+ * or the panel has no explicit zero, or (relax_den > 0) its explicit zeros are at most 1/relax_den
+ * of its entries.  (1, 0) gives the fundamental supernodes.  The paper leaves the symbolic
+ * analysis to the sparse solver (Section 5); relaxed amalgamation and its parameters are this
+ * library's choice, and the same rule runs in the oracle.  IPM_ERR_BAD_ARG unless
+ * 1 <= relax_w <= 64 and relax_den >= 0. */
+int ipm_symbolic_relaxed(int n, int m, const int *J_rowptr, const int *J_colind, int nnzJ,
+                         const int *W_rowptr, const int *W_colind, int nnzW, int relax_w,
+                         int relax_den, cudaStream_t stream, ipm_sym_t *out);
 
 /* Sizes of a symbolic analysis (host outputs; NULL outputs are skipped).
  *   nnz_k       structural entries of the lower triangle of K (diagonal included)
@@ -293,6 +306,8 @@ typedef struct {
                        switches to an FP64 factor for good at the first iteration whose
                        FP32-preconditioned FP64 refinement does not converge (late IPM
                        iterations are too ill-conditioned for an FP32 factor) */
+  int sn_relax_w;   /* supernode partition (ipm_symbolic_relaxed); <= 0 means (8, 5) */
+  int sn_relax_den;
 } ipm_options;
 
 typedef struct {

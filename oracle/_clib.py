@@ -38,6 +38,8 @@ def lib():
             P = ctypes.c_void_p
             L.osym_analyze.restype = P
             L.osym_analyze.argtypes = [ctypes.c_int, P, P]
+            L.osym_analyze_relaxed.restype = P
+            L.osym_analyze_relaxed.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int]
             L.osym_sizes.argtypes = [P, P, P]
             L.osym_export.argtypes = [P] * 7
             L.osym_free.argtypes = [P]

@@ -38,6 +38,7 @@ KAPPA_SIGMA = 1e10
 # rounding margin of barrier-function comparisons: phi is known only to about
 # 10 eps_mach |phi|, so a trial whose phi differs by less than that counts as equal
 PHI_MARGIN = 10.0 * np.finfo(np.float64).eps
+SOFT_RESTO_REDUCTION = 1e-4   # required relative decrease of E_mu in a soft-restoration step
 
 
 def filter_accept(theta, phi, gphi, alpha, tht, pht, filt, theta_min, theta_max):
@@ -80,6 +81,7 @@ class Options:
     mu0: float = 0.1
     cg_rtol: float = 1e-10
     max_refine: int = 10
+    soft_restoration: bool = True   # pd-error fallback when the line search fails
     verbose: bool = False
 
 
@@ -239,6 +241,9 @@ def solve(model, opt: Options | None = None, x0=None):
         return float(val)
 
     def errors(gradf, J, g, h, mu_):
+        return errors_at(x, s, y, z, v, zl, zu, gradf, J, g, h, mu_)
+
+    def errors_at(x, s, y, z, v, zl, zu, gradf, J, g, h, mu_):
         G, H = J[:me], J[me:]
         gl = gradf * sig_f + G.T @ y + H.T @ z - zl + zu
         sd = max(S_MAX, (np.abs(y).sum() + np.abs(z).sum() + np.abs(v).sum() + np.abs(zl).sum()
@@ -369,6 +374,22 @@ def solve(model, opt: Options | None = None, x0=None):
             alpha *= 0.5
             if alpha < amin:
                 break
+        soft = False
+        if not accepted and opt.soft_restoration:
+            # soft restoration (Ipopt's fallback before its restoration phase): the step damped
+            # only by the fraction to the boundary (alpha_max, and az for the bound duals) is
+            # taken if it reduces the primal-dual error of the barrier problem, E_mu, by the
+            # factor 1 - 1e-4; the filter is left as it is
+            xt = x + amax * dx
+            st = s + amax * ds
+            gt, ht = model.cons(xt)
+            e_now = errors(gradf, J, g, h, mu)
+            e_try = errors_at(xt, st, y + amax * dy, z + amax * dz, v + az * dv, zl + az * dzl,
+                              zu + az * dzu, model.grad(xt), model.jacobian(xt), gt, ht, mu)
+            if e_try <= (1.0 - SOFT_RESTO_REDUCTION) * e_now:
+                accepted = soft = True
+                alpha = amax
+                ftype = True
         if not accepted:
             status = "restoration_needed"
             break
@@ -388,7 +409,7 @@ def solve(model, opt: Options | None = None, x0=None):
         zu = np.where(hu, np.clip(zu, mu / (KAPPA_SIGMA * dxu), KAPPA_SIGMA * mu / dxu), 0.0)
         v = np.clip(v, mu / (KAPPA_SIGMA * s), KAPPA_SIGMA * mu / s)
         hist.append(dict(k=it, mu=mu, e0=e0, alpha=alpha, delta_w=dw, nfac=nfac, cg=cg_its,
-                         eta=eta, ls=ls, obj=model.objective(x), gamma=gamma))
+                         eta=eta, ls=ls, obj=model.objective(x), gamma=gamma, soft=soft))
         if opt.verbose:
             print(f"{it:4d} mu={mu:.1e} E0={e0:.2e} a={alpha:.2e} dw={dw:.1e} cg={cg_its} eta={eta:.1e}")
     g, h = model.cons(x)

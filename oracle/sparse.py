@@ -37,11 +37,11 @@ def adjacency(P: sp.csr_matrix):
 class Symbolic:
     """Ordering, elimination tree, column structures and supernodes of a pattern."""
 
-    def __init__(self, P: sp.csr_matrix):
+    def __init__(self, P: sp.csr_matrix, relax=(8, 5)):
         self.n = P.shape[0]
         ap, ai = adjacency(P)
         L = lib()
-        h = L.osym_analyze(self.n, ptr(ap), ptr(ai))
+        h = L.osym_analyze_relaxed(self.n, ptr(ap), ptr(ai), int(relax[0]), int(relax[1]))
         ns = np.zeros(1, np.int32)
         nnz = np.zeros(1, np.int64)
         L.osym_sizes(h, ptr(ns), ptr(nnz))

@@ -28,11 +28,11 @@
  * parent(k) = k+1 for f <= k < l (a chain of the elimination tree).  Its panel holds, in
  * every column k, the rows k..l and the rows of struct(L_l); the entries of the panel that are
  * not in struct(L_k) are explicit zeros.  Scanning the columns in order, column l+1 joins the
- * supernode f..l when parent(l) = l+1, the width l+2-f stays <= SN_MAXW, and either that width
- * is <= SN_RELAX_W or the explicit zeros are at most 1/SN_RELAX_DEN of the panel's entries
- * (E = w(w+1)/2 + w |struct(L_{l+1})|, zeros = E - sum_k |L_k|); otherwise l+1 starts a new
- * supernode.  Fundamental supernodes (no explicit zero) are the special case where every
- * extension adds none.
+ * supernode f..l when parent(l) = l+1, the width w = l+2-f stays <= SN_MAXW, and w <= relax_w,
+ * or the panel has no explicit zero, or (relax_den > 0) the explicit zeros are at most
+ * 1/relax_den of the panel's entries (E = w(w+1)/2 + w |struct(L_{l+1})|, zeros = E -
+ * sum_k |L_k|); otherwise l+1 starts a new supernode.  (relax_w, relax_den) = (1, 0) gives the
+ * fundamental supernodes; osym_analyze uses (8, 5).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -41,8 +41,6 @@
 #define LEAF 64
 #define REROOT 4
 #define SN_MAXW 64
-#define SN_RELAX_W 8   /* always merge up to this width */
-#define SN_RELAX_DEN 5 /* otherwise explicit zeros <= entries / SN_RELAX_DEN */
 
 typedef struct {
   int n;
@@ -228,7 +226,7 @@ typedef struct {
 } osym;
 
 /* ap/ai: symmetric adjacency (no self loops). */
-osym *osym_analyze(int n, const int *ap, const int *ai) {
+osym *osym_analyze_relaxed(int n, const int *ap, const int *ai, int relax_w, int relax_den) {
   osym *s = (osym *)calloc(1, sizeof(osym));
   s->n = n;
   s->perm = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
@@ -323,7 +321,8 @@ osym *osym_analyze(int n, const int *ap, const int *ai) {
       int64_t below = s->cc[j] - 1;        /* |struct(L_j)|: the rows below the panel */
       int64_t entries = w * (w + 1) / 2 + w * below;
       int64_t zeros = entries - (nzsum + s->cc[j]);
-      join = w <= SN_MAXW && (w <= SN_RELAX_W || SN_RELAX_DEN * zeros <= entries);
+      join = w <= SN_MAXW &&
+             (w <= relax_w || zeros == 0 || (relax_den > 0 && relax_den * zeros <= entries));
     }
     if (!join) {
       s->sptr[ns++] = j;
@@ -334,6 +333,10 @@ osym *osym_analyze(int n, const int *ap, const int *ai) {
   s->sptr[ns] = n;
   s->nsuper = ns;
   return s;
+}
+
+osym *osym_analyze(int n, const int *ap, const int *ai) {
+  return osym_analyze_relaxed(n, ap, ai, 8, 5);
 }
 
 void osym_sizes(const osym *s, int *nsuper, int64_t *nnz_offdiag) {

@@ -27,6 +27,7 @@ I64 = ctypes.c_int64
 _SIGS = {
     "ipm_last_error_message": (ctypes.c_char_p, []),
     "ipm_symbolic": (I, [I, I, P, P, I, P, P, I, P, P]),
+    "ipm_symbolic_relaxed": (I, [I, I, P, P, I, P, P, I, I, I, P, P]),
     "ipm_symbolic_info": (I, [P, P, P, P, P, P, P]),
     "ipm_launch_count": (ctypes.c_longlong, []),
     "ipm_symbolic_export": (I, [P, P, P, P, P, P]),
@@ -96,7 +97,8 @@ class IpmOptions(ctypes.Structure):
     _fields_ = [("kkt", ctypes.c_int), ("tol", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("tau", ctypes.c_double), ("mu0", ctypes.c_double), ("cg_rtol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("cg_maxit", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("sn_relax_w", ctypes.c_int),
+                ("sn_relax_den", ctypes.c_int)]
 
 
 class IpmIterInfo(ctypes.Structure):
@@ -166,13 +168,14 @@ def _stream(stream=None):
 class Symbolic:
     """ipm_symbolic handle for one (J, W-lower) sparsity pattern (int32 CUDA tensors)."""
 
-    def __init__(self, n, m, J_rowptr, J_colind, W_rowptr, W_colind, stream=None):
+    def __init__(self, n, m, J_rowptr, J_colind, W_rowptr, W_colind, stream=None, relax=(8, 5)):
         import torch
         h = ctypes.c_void_p()
-        _check(lib().ipm_symbolic(n, m, _ptr(J_rowptr, torch.int32), _ptr(J_colind, torch.int32),
-                                  int(J_colind.numel()), _ptr(W_rowptr, torch.int32),
-                                  _ptr(W_colind, torch.int32), int(W_colind.numel()),
-                                  _stream(stream), ctypes.byref(h)), "ipm_symbolic")
+        _check(lib().ipm_symbolic_relaxed(n, m, _ptr(J_rowptr, torch.int32),
+                                          _ptr(J_colind, torch.int32), int(J_colind.numel()),
+                                          _ptr(W_rowptr, torch.int32), _ptr(W_colind, torch.int32),
+                                          int(W_colind.numel()), int(relax[0]), int(relax[1]),
+                                          _stream(stream), ctypes.byref(h)), "ipm_symbolic")
         self.h = h
         self.n, self.m = n, m
         nk, ns, nnz, plen, nl, fl = I64(), I(), I64(), I64(), I(), D()
@@ -346,10 +349,10 @@ class IpmState:
     """GPU interior-point iterate for an ``Opf`` problem (ipm_state_create / ipm_step)."""
 
     def __init__(self, opf, kkt="lifted", tol=1e-6, gamma=1e6, tau=0.0, mu0=0.1, cg_rtol=1e-10,
-                 max_refine=10, cg_maxit=0, precision=64, stream=None):
+                 max_refine=10, cg_maxit=0, precision=64, stream=None, relax=(0, 0)):
         self.opf = opf
         o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
-                       cg_rtol, max_refine, cg_maxit, precision)
+                       cg_rtol, max_refine, cg_maxit, precision, int(relax[0]), int(relax[1]))
         h = ctypes.c_void_p()
         _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream), ctypes.byref(h)),
                "ipm_state_create")
@@ -413,11 +416,11 @@ class Batch:
     "hykkt" (CG on the Schur complement of K_gamma) or "regularized"."""
 
     def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, kkt="lifted", gamma=1e6,
-                 cg_rtol=1e-10, cg_maxit=0, stream=None):
+                 cg_rtol=1e-10, cg_maxit=0, stream=None, relax=(0, 0)):
         self.opfs = list(opfs)
         arr = (ctypes.c_void_p * len(self.opfs))(*[o.h.value for o in self.opfs])
         o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
-                       cg_rtol, max_refine, cg_maxit, 64)
+                       cg_rtol, max_refine, cg_maxit, 64, int(relax[0]), int(relax[1]))
         h = ctypes.c_void_p()
         _check(lib().ipm_batch_create(len(self.opfs), arr, ctypes.byref(o), _stream(stream),
                                       ctypes.byref(h)), "ipm_batch_create")

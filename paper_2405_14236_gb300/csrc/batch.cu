@@ -1789,8 +1789,10 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
       }
       const OpfData &M = opfs[i]->M;
       ipm_sym_t S = nullptr;
-      rc = ipm_symbolic(M.n, M.me + M.mi, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr, M.W_colind,
-                        M.nnzW, stream, &S);
+      const bool dflt = B->opt.sn_relax_w <= 0;
+      rc = ipm_symbolic_relaxed(M.n, M.me + M.mi, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr,
+                                M.W_colind, M.nnzW, dflt ? 8 : B->opt.sn_relax_w,
+                                dflt ? 5 : B->opt.sn_relax_den, stream, &S);
       if (rc != IPM_OK) return fail(rc);
       B->pat[i] = (int)B->syms.size();
       B->syms.push_back(S);

@@ -9,6 +9,7 @@
 
 struct ipm_sym_s {
   int n = 0, m = 0, nnzJ = 0, nnzW = 0;
+  int relax_w = 8, relax_den = 5;  // relaxed-supernode rule (ipm_symbolic_relaxed)
   // copies of the caller's patterns
   int *J_rowptr = nullptr, *J_colind = nullptr, *J_rowidx = nullptr;
   int *W_rowptr = nullptr, *W_colind = nullptr, *W_rowidx = nullptr;

@@ -382,8 +382,12 @@ extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStrea
       S->nu += std::isfinite(hxu[j]);
     }
   }
-  if (rc == IPM_OK) rc = ipm_symbolic(n, m, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr,
-                                      M.W_colind, M.nnzW, stream, &S->sym);
+  if (rc == IPM_OK) {
+    const bool dflt = S->opt.sn_relax_w <= 0;
+    rc = ipm_symbolic_relaxed(n, m, M.J_rowptr, M.J_colind, M.nnzJ, M.W_rowptr, M.W_colind,
+                              M.nnzW, dflt ? 8 : S->opt.sn_relax_w, dflt ? 5 : S->opt.sn_relax_den,
+                              stream, &S->sym);
+  }
   if (rc == IPM_OK) rc = ipm_num_create(S->sym, 64, &S->num);
   if (rc == IPM_OK && S->opt.precision == 32) rc = ipm_num_create(S->sym, 32, &S->num32);
   if (rc == IPM_OK) {

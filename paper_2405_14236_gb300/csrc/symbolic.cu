@@ -608,12 +608,14 @@ __global__ void k_copy_struct(int n, const int64_t *cstart, const int *pool, con
 // Relaxed supernodes: runs of consecutive columns f..l with parent(k) = k+1 (chains of the
 // elimination tree), each panel holding rows k..l and struct(L_l) in every column k (explicit
 // zeros where struct(L_k) lacks them).  Column j joins the supernode f..j-1 when parent(j-1) = j,
-// the width w = j-f+1 is <= CIPM_SN_MAXW, and w <= SN_RELAX_W or the explicit zeros are at most
-// entries / SN_RELAX_DEN (entries = w(w+1)/2 + w |struct(L_j)|, zeros = entries - sum |L_k|).
-// One thread per chain scans it greedily from its first column; flag[j] = 1 where a supernode
-// starts (every column belongs to exactly one chain, so every flag is written once).
-static constexpr int SN_RELAX_W = 8, SN_RELAX_DEN = 5;
-__global__ void k_sn_relaxed(const int *parent, const int *cc, int n, int *flag) {
+// the width w = j-f+1 is <= CIPM_SN_MAXW, and w <= relax_w, or the panel has no explicit zero, or
+// (relax_den > 0) the explicit zeros are at most entries / relax_den (entries = w(w+1)/2 +
+// w |struct(L_j)|, zeros = entries - sum |L_k|).  (relax_w, relax_den) = (1, 0) gives the
+// fundamental supernodes.  One thread per chain scans it greedily from its first column;
+// flag[j] = 1 where a supernode starts (every column belongs to exactly one chain, so every flag
+// is written once).
+__global__ void k_sn_relaxed(const int *parent, const int *cc, int n, int relax_w, int relax_den,
+                             int *flag) {
   const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (j0 >= n || (j0 > 0 && parent[j0 - 1] == j0)) return;  // not the first column of a chain
   int f = j0;
@@ -623,7 +625,8 @@ __global__ void k_sn_relaxed(const int *parent, const int *cc, int n, int *flag)
     const long long w = j - f + 1, below = cc[j] - 1;
     const long long entries = w * (w + 1) / 2 + w * below;
     const long long zeros = entries - (nz + cc[j]);
-    if (w <= CIPM_SN_MAXW && (w <= SN_RELAX_W || SN_RELAX_DEN * zeros <= entries)) {
+    if (w <= CIPM_SN_MAXW &&
+        (w <= relax_w || zeros == 0 || (relax_den > 0 && relax_den * zeros <= entries))) {
       flag[j] = 0;
       nz += cc[j];
     } else {
@@ -995,7 +998,8 @@ static int symbolic_impl(ipm_sym_t S, const int *J_rowptr, const int *J_colind,
   int64_t *area;
   CKR(T.alloc(&flag, n + 1));
   CKR(T.alloc(&ex, n + 1));
-  k_sn_relaxed<<<grid_for(n, 256), 256, 0, s>>>(S->parent, S->cc, n, flag);
+  k_sn_relaxed<<<grid_for(n, 256), 256, 0, s>>>(S->parent, S->cc, n, S->relax_w, S->relax_den,
+                                                 flag);
   CKL();
   CKR(exclusive_scan_i32(flag, ex, n, s));
   CK(cudaMemcpy(&S->nsuper, ex + n, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1200,13 +1204,24 @@ static int symbolic_impl(ipm_sym_t S, const int *J_rowptr, const int *J_colind,
 extern "C" int ipm_symbolic(int n, int m, const int *J_rowptr, const int *J_colind, int nnzJ,
                             const int *W_rowptr, const int *W_colind, int nnzW,
                             cudaStream_t stream, ipm_sym_t *out) {
+  return ipm_symbolic_relaxed(n, m, J_rowptr, J_colind, nnzJ, W_rowptr, W_colind, nnzW, 8, 5,
+                              stream, out);
+}
+
+extern "C" int ipm_symbolic_relaxed(int n, int m, const int *J_rowptr, const int *J_colind,
+                                    int nnzJ, const int *W_rowptr, const int *W_colind, int nnzW,
+                                    int relax_w, int relax_den, cudaStream_t stream,
+                                    ipm_sym_t *out) {
   if (!out || n <= 0 || m < 0 || nnzJ < 0 || nnzW < 0 || !J_rowptr || !W_rowptr ||
-      (nnzJ > 0 && !J_colind) || (nnzW > 0 && !W_colind)) {
+      (nnzJ > 0 && !J_colind) || (nnzW > 0 && !W_colind) || relax_w < 1 ||
+      relax_w > CIPM_SN_MAXW || relax_den < 0) {
     set_error_msg("ipm_symbolic: bad argument");
     return IPM_ERR_BAD_ARG;
   }
   *out = nullptr;
   ipm_sym_t S = new ipm_sym_s();
+  S->relax_w = relax_w;
+  S->relax_den = relax_den;
   S->n = n;
   S->m = m;
   S->nnzJ = nnzJ;

@@ -213,3 +213,24 @@ def test_batch_autotune_keeps_results():
         if ref["status"][i] == 1:
             assert r["status"][i] == 1, i
             assert abs(r["obj"][i] - ref["obj"][i]) <= 1e-6 * abs(ref["obj"][i]), i
+
+
+def test_supernode_shape_tuning_keeps_results():
+    """The supernode-partition tuner times each candidate rule on the batch itself; every rule
+    gives the same optima (the partition changes only the panels' explicit zeros and the
+    schedule, not the matrix)."""
+    from paper_2405_14236_gb300 import tune
+    base = config_grid("planar1k")
+    grids = [scale_loads(base, 1000 + k) for k in range(4)] + [mixed_grid(2003)]
+    opfs = [cp.Opf(g) for g in grids]
+    best, recs = tune.supernode_shapes(opfs, sweeps=3)
+    assert best in tune.CANDIDATES and len(recs) == len(tune.CANDIDATES)
+    assert all(r["ms_per_sweep"] > 0 for r in recs)
+    objs = []
+    for relax in ((1, 0), best):
+        B = cp.Batch(opfs, relax=relax)
+        B.run(max_iter=300)
+        r = B.results()
+        assert (r["status"] == 1).all(), (relax, r["status"])
+        objs.append(r["obj"])
+    np.testing.assert_allclose(objs[1], objs[0], rtol=1e-6)

@@ -22,10 +22,10 @@ def dev(a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def gpu_sym(J, Wl):
+def gpu_sym(J, Wl, relax=(8, 5)):
     n = J.shape[1]
     return cp.Symbolic(n, J.shape[0], dev(J.indptr, torch.int32), dev(J.indices, torch.int32),
-                       dev(Wl.indptr, torch.int32), dev(Wl.indices, torch.int32))
+                       dev(Wl.indptr, torch.int32), dev(Wl.indices, torch.int32), relax=relax)
 
 
 def panels_to_lower(sym, Lx):
@@ -94,6 +94,18 @@ def test_symbolic_bit_exact(name):
     np.testing.assert_array_equal(g["sptr"], o.sptr)
     np.testing.assert_array_equal(g["colptr"], o.colptr)
     np.testing.assert_array_equal(g["rowind"], o.rowind)
+
+
+@pytest.mark.parametrize("relax", [(1, 0), (4, 10), (16, 3), (64, 1)])
+@pytest.mark.parametrize("name", ["planar1k", "planar10k"])
+def test_supernode_partition_bit_exact_for_each_relaxation(name, relax):
+    """The supernode partition for other relaxation parameters (the candidates of the
+    supernode-shape tuning), bit for bit against the oracle's."""
+    J, Wl = sym_case(name)
+    S = gpu_sym(J, Wl, relax=relax)
+    o = OSym(condensed_pattern(K.full_from_lower(Wl), J), relax=relax)
+    np.testing.assert_array_equal(S.export()["sptr"], o.sptr)
+    assert S.nsuper == o.nsuper
 
 
 def run_condense(c, S, N):

@@ -60,7 +60,9 @@ def relaxed_partition(struct, parent, maxw=64, relax_w=8, relax_den=5):
             w = j - f + 1
             entries = sum((j - k + 1) + len(struct[j]) for k in range(f, j + 1))
             nz = sum(1 + len(struct[k]) for k in range(f, j + 1))
-            if w <= maxw and (w <= relax_w or relax_den * (entries - nz) <= entries):
+            zeros = entries - nz
+            if w <= maxw and (w <= relax_w or zeros == 0 or
+                              (relax_den > 0 and relax_den * zeros <= entries)):
                 continue
         starts.append(j)
     return starts + [n]
@@ -68,13 +70,14 @@ def relaxed_partition(struct, parent, maxw=64, relax_w=8, relax_den=5):
 
 @pytest.mark.parametrize("n,p,seed", [(60, 0.05, 3), (150, 0.03, 11), (200, 0.015, 6),
                                       (120, 0.2, 7)])
-def test_relaxed_supernodes_match_definition(n, p, seed):
+@pytest.mark.parametrize("relax", [(8, 5), (1, 0), (4, 10), (64, 1)])
+def test_relaxed_supernodes_match_definition(n, p, seed, relax):
     P = random_graph(n, p, seed)
-    S = Symbolic(P)
+    S = Symbolic(P, relax=relax)
     L = brute_force_fill(P.toarray(), S.perm)
     struct = [set((np.nonzero(L[j + 1:, j])[0] + j + 1).tolist()) for j in range(n)]
     parent = [min(st) if st else -1 for st in struct]
-    expect = relaxed_partition(struct, parent)
+    expect = relaxed_partition(struct, parent, relax_w=relax[0], relax_den=relax[1])
     np.testing.assert_array_equal(S.sptr, expect)
     for s_ in range(S.nsuper):
         f, l = S.sptr[s_], S.sptr[s_ + 1]
@@ -82,8 +85,14 @@ def test_relaxed_supernodes_match_definition(n, p, seed):
         for k in range(f, l - 1):
             assert parent[k] == k + 1                      # a chain of the elimination tree
             assert struct[k] <= set(range(k + 1, l)) | struct[l - 1]   # panel rows cover L_k
-    assert S.nsuper <= sum(1 for j in range(n) if j == 0 or parent[j - 1] != j or
-                           len(struct[j - 1]) != len(struct[j]) + 1) + n // 64 + 1
+    fundamental = sum(1 for j in range(n) if j == 0 or parent[j - 1] != j or
+                      len(struct[j - 1]) != len(struct[j]) + 1)
+    assert S.nsuper <= fundamental + n // 64 + 1
+    if relax == (1, 0):   # no explicit zeros at all: the fundamental supernodes
+        for s_ in range(S.nsuper):
+            f, l = S.sptr[s_], S.sptr[s_ + 1]
+            for k in range(f, l - 1):
+                assert struct[k] == {k + 1} | struct[k + 1]
 
 
 def test_relaxed_supernodes_on_a_path_and_a_star():
