@@ -82,6 +82,7 @@ class Options:
     cg_rtol: float = 1e-10
     max_refine: int = 10
     soft_restoration: bool = True   # pd-error fallback when the line search fails
+    restoration: bool = True        # feasibility restoration phase when that fails too
     verbose: bool = False
 
 
@@ -157,6 +158,77 @@ class ScaledModel:
         return self.base.hessian(x, y * self.de, z * self.di, sigma_f)
 
 
+RHO_RESTO = 1000.0        # penalty of the restoration objective (Waechter & Biegler 2006, Sec. 3.3)
+KAPPA_RESTO = 0.9         # required reduction of theta before leaving the restoration phase
+
+
+class RestorationModel:
+    """The feasibility restoration problem of Waechter & Biegler 2006, Sec. 3.3 (the restoration
+    phase of the filter method cited in Sec. 2.2) for a model at the reference point xr:
+
+        min  rho sum(p + q) + zeta/2 ||D_R (x - xr)||_2^2
+        s.t. g(x) - p_g + q_g = 0,  h(x) - p_h + q_h <= 0,  xl <= x <= xu,  p, q >= 0,
+
+    with D_R = diag(min(1, 1/|xr_j|)); one pair (p, q) per constraint row.  Variables are
+    [x, p, q] (n + 2 m); the inequality rows keep their slacks in the IPM."""
+
+    def __init__(self, base, xr, zeta, rho=RHO_RESTO):
+        self.base, self.xr, self.zeta, self.rho = base, xr.copy(), zeta, rho
+        self.nx = base.n
+        self.mr = base.m_e + base.m_i
+        self.n, self.m_e, self.m_i = base.n + 2 * self.mr, base.m_e, base.m_i
+        self.xl = np.concatenate([base.xl, np.zeros(2 * self.mr)])
+        self.xu = np.concatenate([base.xu, np.full(2 * self.mr, np.inf)])
+        self.dr2 = np.minimum(1.0, 1.0 / np.maximum(np.abs(xr), 1e-300)) ** 2
+
+    def split(self, w):
+        n, m = self.nx, self.mr
+        return w[:n], w[n:n + m], w[n + m:]
+
+    def x0(self):
+        return np.concatenate([self.xr, np.ones(2 * self.mr)])
+
+    def objective(self, w):
+        x, p, q = self.split(w)
+        return float(self.rho * (p.sum() + q.sum()) + 0.5 * self.zeta * (self.dr2 * (x - self.xr) ** 2).sum())
+
+    def grad(self, w):
+        x, p, q = self.split(w)
+        return np.concatenate([self.zeta * self.dr2 * (x - self.xr), np.full(2 * self.mr, self.rho)])
+
+    def cons(self, w):
+        x, p, q = self.split(w)
+        g, h = self.base.cons(x)
+        c = np.concatenate([g, h]) - p + q
+        return c[:self.m_e], c[self.m_e:]
+
+    def jacobian(self, w):
+        x, p, q = self.split(w)
+        I = sp.identity(self.mr, format="csr")
+        return sp.hstack([self.base.jacobian(x), -I, I]).tocsr()
+
+    def hessian(self, w, y, z, sigma_f=1.0):
+        x, p, q = self.split(w)
+        Wx = self.base.hessian(x, y, z, 0.0) + sp.diags(sigma_f * self.zeta * self.dr2)
+        return sp.block_diag([Wx, sp.csr_matrix((2 * self.mr, 2 * self.mr))]).tocsr()
+
+
+def resto_pq(c, mu, rho=RHO_RESTO):
+    """Starting p, q of the restoration problem for the row residuals c: for each row the
+    minimizer of rho (p + q) - mu (log p + log q) subject to p - q = c, i.e. the positive root q
+    of 2 rho q^2 + 2 (rho c - mu) q - mu c = 0 (Waechter & Biegler 2006, Eq. (33)) and p = c + q,
+    the positive root of 2 rho p^2 - 2 (rho c + mu) p + mu c = 0.  Each root is evaluated in the
+    form that does not cancel (through the product of the roots when the linear coefficient
+    has the other sign); both discriminants equal mu^2 + rho^2 c^2."""
+    c = np.asarray(c, dtype=np.float64)
+    sd = np.sqrt(mu * mu + (rho * c) ** 2)
+    bq, bp = mu - rho * c, mu + rho * c
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(bq >= 0, (bq + sd) / (2.0 * rho), -mu * c / (bq - sd))
+        p = np.where(bp >= 0, (bp + sd) / (2.0 * rho), mu * c / (bp - sd))
+    return p, q
+
+
 @dataclasses.dataclass
 class Result:
     status: str
@@ -202,25 +274,38 @@ def auto_gamma(W, sigma_x, G, H, Ds):
 
 
 def solve(model, opt: Options | None = None, x0=None):
+    """The IPM on a model: Ipopt's gradient scaling at the start, LiftedKKT's relaxation
+    (Sec. 3.2) for kkt = "lifted", the starting point of the reading in the design notes, then
+    the filter line-search iterations (_ipm)."""
     opt = opt or Options()
     base = model
     model = ScaledModel(base, _push(base.x0() if x0 is None else x0, base.xl, base.xu))
     if opt.kkt == "lifted":
         model = RelaxedModel(model, opt.tau if opt.tau is not None else opt.tol)
+    hl, hu = np.isfinite(model.xl), np.isfinite(model.xu)
+    x = _push(model.x0() if x0 is None else x0, model.xl, model.xu)
+    sig_f = min(1.0, 100.0 / max(np.abs(model.grad(x)).max(), 1e-300))
+    g, h = model.cons(x)
+    start = dict(x=x, s=np.maximum(-h, KAPPA1), y=np.zeros(model.m_e), z=np.ones(model.m_i),
+                 v=np.ones(model.m_i), zl=np.where(hl, 1.0, 0.0), zu=np.where(hu, 1.0, 0.0))
+    res = _ipm(model, opt, start, opt.mu0, sig_f)
+    res.obj = base.objective(res.x)
+    return res
+
+
+def _ipm(model, opt, start, mu, sig_f, exit_check=None, restore=True, max_iter=None):
+    """Filter line-search interior-point iterations on `model` (scaling and relaxation already
+    applied) from the primal-dual point `start` with barrier parameter mu.  exit_check(x, s),
+    when given, is asked after every accepted step and ends the iterations with status
+    "exited" (the restoration phase's return test).  restore: call the restoration phase when
+    the line search and the soft restoration fail."""
+    max_iter = opt.max_iter if max_iter is None else max_iter
     n, me, mi = model.n, model.m_e, model.m_i
     xl, xu = model.xl, model.xu
     hl, hu = np.isfinite(xl), np.isfinite(xu)
     xlf, xuf = np.where(hl, xl, 0.0), np.where(hu, xu, 0.0)
-    x = _push(model.x0() if x0 is None else x0, xl, xu)
-    sig_f = min(1.0, 100.0 / max(np.abs(model.grad(x)).max(), 1e-300))
-    g, h = model.cons(x)
-    s = np.maximum(-h, KAPPA1)
-    y = np.zeros(me)
-    z = np.ones(mi)
-    v = np.ones(mi)
-    zl = np.where(hl, 1.0, 0.0)
-    zu = np.where(hu, 1.0, 0.0)
-    mu = opt.mu0
+    x, s, y, z, v, zl, zu = (np.array(start[k], dtype=np.float64)
+                             for k in ("x", "s", "y", "z", "v", "zl", "zu"))
     tau = max(TAU_MIN, 1.0 - mu)
     nl, nu = int(hl.sum()), int(hu.sum())
 
@@ -231,9 +316,14 @@ def solve(model, opt: Options | None = None, x0=None):
     delta_last = 0.0
     hist = []
     theta0 = None
+    n_resto = 0
 
     def theta_of(gx, hx, sx):
         return float(np.abs(gx).sum() + np.abs(hx + sx).sum())
+
+    def theta_at(xx, sx):
+        gx, hx = model.cons(xx)
+        return theta_of(gx, hx, sx)
 
     def phi_of(xx, sx, mu_):
         val = sig_f * model.objective(xx) - mu_ * np.log(sx).sum()
@@ -259,7 +349,7 @@ def solve(model, opt: Options | None = None, x0=None):
 
     status = "max_iter"
     it = 0
-    for it in range(opt.max_iter + 1):
+    for it in range(max_iter + 1):
         g, h = model.cons(x)
         gradf = model.grad(x)
         J = model.jacobian(x)
@@ -271,7 +361,7 @@ def solve(model, opt: Options | None = None, x0=None):
         if e0 <= opt.tol:
             status = "converged"
             break
-        if it == opt.max_iter:
+        if it == max_iter:
             break
         first = True
         while errors(gradf, J, g, h, mu) <= KAPPA_EPS * mu and (first or it == 0):
@@ -297,7 +387,11 @@ def solve(model, opt: Options | None = None, x0=None):
             d = np.concatenate([np.full(me, gamma), dh]) if opt.kkt != "lifted" else dh
             return K.condensed_matrix(W, sigma_x, J, d, dw)
 
-        dw, F, nfac = K.inertia_schedule(kmat, solver, delta_last)
+        try:
+            dw, F, nfac = K.inertia_schedule(kmat, solver, delta_last)
+        except RuntimeError:      # no delta_w up to 1e40 gives a positive definite matrix
+            status = "inertia_failed"
+            break
         if dw > 0:
             delta_last = dw
         dh = Ds + dw
@@ -390,6 +484,27 @@ def solve(model, opt: Options | None = None, x0=None):
                 accepted = soft = True
                 alpha = amax
                 ftype = True
+        if not accepted and restore and opt.restoration:
+            # feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the current point
+            # enters the filter, a point acceptable to it with a smaller constraint violation is
+            # sought by an IPM on the restoration problem, and the iterations go on from there
+            entry = ((1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta)
+            rec = _restoration(model, opt, x, s, v, zl, zu, mu, theta, theta_max,
+                               filt + [entry], theta_at, lambda xx, sx: phi_of(xx, sx, mu))
+            n_resto += 1
+            hist.append(dict(k=it, mu=mu, e0=e0, alpha=0.0, delta_w=dw, nfac=nfac, cg=cg_its,
+                             eta=eta, ls=ls, obj=model.objective(x), gamma=gamma, soft=False,
+                             resto=rec["iters"], resto_status=rec["status"]))
+            if rec["status"] != "ok":
+                status = rec["status"]
+                break
+            filt.append(entry)
+            # constraint multipliers start again from zero, bound multipliers are kept (as in
+            # Ipopt after its restoration phase)
+            x, s, v, zl, zu = rec["x"], rec["s"], rec["v"], rec["zl"], rec["zu"]
+            y = np.zeros(me)
+            z = np.zeros(mi)
+            continue
         if not accepted:
             status = "restoration_needed"
             break
@@ -410,10 +525,54 @@ def solve(model, opt: Options | None = None, x0=None):
         v = np.clip(v, mu / (KAPPA_SIGMA * s), KAPPA_SIGMA * mu / s)
         hist.append(dict(k=it, mu=mu, e0=e0, alpha=alpha, delta_w=dw, nfac=nfac, cg=cg_its,
                          eta=eta, ls=ls, obj=model.objective(x), gamma=gamma, soft=soft))
+        if exit_check is not None and exit_check(x, s):
+            status = "exited"
+            break
         if opt.verbose:
             print(f"{it:4d} mu={mu:.1e} E0={e0:.2e} a={alpha:.2e} dw={dw:.1e} cg={cg_its} eta={eta:.1e}")
     g, h = model.cons(x)
     J = model.jacobian(x)
     return Result(status=status, iters=it, x=x, s=s, y=y, z=z, v=v, zl=zl, zu=zu,
-                  obj=base.objective(x), kkt_error=errors(model.grad(x), J, g, h, 0.0), mu=mu,
+                  obj=model.objective(x), kkt_error=errors(model.grad(x), J, g, h, 0.0), mu=mu,
                   history=hist)
+
+
+def _restoration(model, opt, x, s, v, zl, zu, mu, theta, theta_max, filt, theta_at, phi_at):
+    """The restoration phase (Waechter & Biegler 2006, Sec. 3.3): an IPM on RestorationModel
+    at the reference point x, with mu_R = max(mu, ||c||_inf), zeta = sqrt(mu_R), p and q from
+    resto_pq, the constraint multipliers at zero and the bound multipliers capped at rho.  It
+    returns (status "ok") at the first restoration iterate whose x and s reduce the original
+    constraint violation to at most KAPPA_RESTO theta and are acceptable to the original filter
+    (which holds the point the phase started from); "infeasible" when it converges to a
+    stationary point of the restoration problem first (a local minimizer of the violation);
+    "restoration_failed" otherwise."""
+    n, me, mi = model.n, model.m_e, model.m_i
+    g, h = model.cons(x)
+    c = np.concatenate([g, h + s])
+    mu_r = max(mu, float(np.abs(c).max()))
+    R = RestorationModel(model, x, np.sqrt(mu_r))
+    p, q = resto_pq(c, mu_r)
+    m = len(c)
+    start = dict(x=np.concatenate([x, p, q]), s=s.copy(), y=np.zeros(me), z=np.zeros(mi),
+                 v=np.minimum(RHO_RESTO, v),
+                 zl=np.concatenate([np.minimum(RHO_RESTO, zl), mu_r / p, mu_r / q]),
+                 zu=np.concatenate([np.minimum(RHO_RESTO, zu), np.zeros(2 * m)]))
+
+    def exit_check(w, sk):
+        xk = w[:n]
+        th = theta_at(xk, sk)
+        if not th <= KAPPA_RESTO * theta:
+            return False
+        ph = phi_at(xk, sk)
+        return th < theta_max and all(th < tf or ph < pf for tf, pf in filt)
+
+    ropt = dataclasses.replace(opt, restoration=False)
+    rr = _ipm(R, ropt, start, mu_r, 1.0, exit_check=exit_check, restore=False, max_iter=500)
+    out = dict(iters=rr.iters)
+    if rr.status != "exited":
+        out["status"] = "infeasible" if rr.status == "converged" else "restoration_failed"
+        return out
+    reset = lambda a: np.where(a > 1e3, 1.0, a)   # large bound multipliers reset (Ipopt)
+    out.update(status="ok", x=rr.x[:n].copy(), s=rr.s.copy(), v=reset(rr.v),
+               zl=reset(rr.zl[:n]), zu=reset(rr.zu[:n]))
+    return out
