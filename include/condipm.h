@@ -35,9 +35,13 @@ enum {
   IPM_ERR_CG_MAXIT = 2,     /* HyKKT CG hit its iteration limit */
   IPM_ERR_NONFINITE = 3,    /* NaN/Inf in inputs or results */
   IPM_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
-  IPM_ERR_RESTORATION = 5,  /* line search failed: feasibility restoration needed */
+  IPM_ERR_RESTORATION = 5,  /* line search failed (batched solves; the single-problem IPM
+                               then runs its restoration phase, and returns this code when that
+                               phase fails) */
   IPM_ERR_INERTIA = 6,      /* inertia correction failed: delta_w reached 1e40 */
   IPM_ERR_MAXITER = 7,      /* iteration limit reached before convergence (batched solves) */
+  IPM_ERR_INFEASIBLE = 8,   /* the restoration phase converged to a stationary point of the
+                               constraint violation without reducing it: locally infeasible */
   IPM_ERR_BAD_ARG = -1,
   IPM_ERR_OOM = -2,
   IPM_ERR_CUDA = -3
@@ -313,13 +317,17 @@ typedef struct {
 typedef struct {
   int k;            /* iteration index */
   int status;       /* 0 running, 1 converged, else an IPM_ERR_* code among IPM_ERR_INERTIA,
-                       IPM_ERR_RESTORATION, IPM_ERR_TIMEOUT and IPM_ERR_NONFINITE */
+                       IPM_ERR_RESTORATION, IPM_ERR_INFEASIBLE, IPM_ERR_TIMEOUT and
+                       IPM_ERR_NONFINITE */
   double mu, kkt_err, alpha, delta_w, obj, eta, theta;
   int n_factor, cg_iters, refine_steps, ls_steps;
   int precision;    /* factorization precision used by this iteration (32 or 64) */
   double gamma;     /* gamma used by this iteration (forms 1 and 2) */
   int pcg_iters;    /* FP64 CG iterations over the FP32 factor in this step's solves (0 in FP64;
                        also the CG after a stagnating refinement) */
+  int resto;        /* 1: this call made an iteration of the restoration phase (mu, kkt_err,
+                       theta, alpha and delta_w then belong to the restoration problem); 2: the
+                       line search failed and the call started the phase; 0 otherwise */
 } ipm_iter_info;
 
 typedef struct ipm_state_s *ipm_state_t;
@@ -330,9 +338,25 @@ typedef struct ipm_state_s *ipm_state_t;
  * workspace.  The opf handle must outlive the state.  Synchronizes. */
 int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStream_t stream,
                      ipm_state_t *out);
+/* As ipm_state_create from the caller's point x0 (HOST, n values) instead of the flat start:
+ * x0 is pushed inside the bounds, and the scaling, slacks and multipliers are set there as in
+ * ipm_state_create.  IPM_ERR_BAD_ARG when x0 is NULL.  Synchronizes. */
+int ipm_state_create_at(ipm_opf_t opf, const ipm_options *opt, const double *x0,
+                        cudaStream_t stream, ipm_state_t *out);
 /* One IPM iteration (or the convergence test that ends the solve): evaluate, test E_0 <= tol,
  * update mu, inertia-corrected condensed KKT solve, fraction to the boundary, filter line search,
- * update.  host_info (HOST) receives the iteration record; after convergence or a failure
+ * update.  When the line search finds no acceptable step the call enters the feasibility
+ * restoration phase of the filter method (Waechter & Biegler 2006, Sec. 3.3, cited in
+ * Section 2.2), and the following calls make its iterations (host_info->resto = 1): an IPM on
+ *   min rho sum(p + q) + zeta/2 ||D_R (x - x_R)||^2   s.t.  c(x) - p + q = 0, p, q >= 0,
+ * c the IPM rows at the failing point x_R, rho = 1000, zeta = sqrt(mu_R), D_R = min(1, 1/|x_R|),
+ * mu_R = max(mu, ||c||_inf), p and q eliminated row by row from its Newton system, which is then
+ * solved by the refined condensed solve on the pattern of the main condensed matrix.  The phase
+ * ends at the first point whose violation is at most 0.9 times that of x_R and that the filter
+ * (with x_R's entry) accepts; the IPM goes on there with y = z = 0.  Status
+ * IPM_ERR_INFEASIBLE: the phase converged to a stationary point of its problem first (a local
+ * minimizer of the violation); IPM_ERR_RESTORATION: its own line search failed or it ran 500
+ * iterations.  host_info (HOST) receives the iteration record; after convergence or a failure
  * further calls return the final status without work.  Synchronizes.  Returns a negative code
  * only on usage/CUDA errors (numerical failures are reported in host_info->status). */
 int ipm_step(ipm_state_t state, ipm_iter_info *host_info);

@@ -81,7 +81,7 @@ class Options:
     mu0: float = 0.1
     cg_rtol: float = 1e-10
     max_refine: int = 10
-    soft_restoration: bool = True   # pd-error fallback when the line search fails
+    soft_restoration: bool = False  # Ipopt's E_mu-decrease fallback before the restoration phase
     restoration: bool = True        # feasibility restoration phase when that fails too
     verbose: bool = False
 

@@ -18,6 +18,7 @@ _lib = None
 IPM_OK, IPM_ERR_NOT_PD, IPM_ERR_CG_MAXIT, IPM_ERR_NONFINITE = 0, 1, 2, 3
 IPM_ERR_BAD_ARG, IPM_ERR_OOM, IPM_ERR_CUDA = -1, -2, -3
 IPM_ERR_TIMEOUT, IPM_ERR_RESTORATION, IPM_ERR_INERTIA, IPM_ERR_MAXITER = 4, 5, 6, 7
+IPM_ERR_INFEASIBLE = 8
 
 P = ctypes.c_void_p
 I = ctypes.c_int
@@ -53,6 +54,7 @@ _SIGS = {
     "ipm_opf_eval": (I, [P, P, P, P, D, P, P, P, P, P, P, P]),
     "ipm_opf_destroy": (None, [P]),
     "ipm_state_create": (I, [P, P, P, P]),
+    "ipm_state_create_at": (I, [P, P, P, P, P]),
     "ipm_step": (I, [P, P]),
     "ipm_state_export": (I, [P, P, P]),
     "ipm_state_export_kkt": (I, [P] * 11),
@@ -108,7 +110,7 @@ class IpmIterInfo(ctypes.Structure):
                 ("theta", ctypes.c_double), ("n_factor", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("ls_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("pcg_iters", ctypes.c_int)]
+                ("pcg_iters", ctypes.c_int), ("resto", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -349,13 +351,23 @@ class IpmState:
     """GPU interior-point iterate for an ``Opf`` problem (ipm_state_create / ipm_step)."""
 
     def __init__(self, opf, kkt="lifted", tol=1e-6, gamma=1e6, tau=0.0, mu0=0.1, cg_rtol=1e-10,
-                 max_refine=10, cg_maxit=0, precision=64, stream=None, relax=(0, 0)):
+                 max_refine=10, cg_maxit=0, precision=64, stream=None, relax=(0, 0), x0=None):
+        """x0: optional starting point (n host values, pushed inside the bounds;
+        ipm_state_create_at), else the flat start."""
         self.opf = opf
         o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
                        cg_rtol, max_refine, cg_maxit, precision, int(relax[0]), int(relax[1]))
         h = ctypes.c_void_p()
-        _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream), ctypes.byref(h)),
-               "ipm_state_create")
+        if x0 is None:
+            _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream),
+                                          ctypes.byref(h)), "ipm_state_create")
+        else:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            if x0.shape != (opf.n,):
+                raise ValueError(f"x0 must hold n = {opf.n} values")
+            _check(lib().ipm_state_create_at(opf.h, ctypes.byref(o),
+                                             x0.ctypes.data_as(ctypes.c_void_p), _stream(stream),
+                                             ctypes.byref(h)), "ipm_state_create_at")
         self.h = h
 
     def step(self):
@@ -396,16 +408,20 @@ class IpmState:
 
 
 def ipm_solve_opf(opf, max_iter=3000, **opts):
-    """Runs ipm_step until convergence, failure or max_iter; returns (status, iters, obj, history)."""
+    """Runs ipm_step until convergence, failure or max_iter iterations of the main problem
+    (iterations of the restoration phase, bounded by the library, do not count); returns
+    (status, iters, obj, history)."""
     st = IpmState(opf, **opts)
     hist = []
     status = 0
-    for _ in range(max_iter + 1):
+    main = 0
+    while main <= max_iter:
         info = st.step()
         hist.append(info.as_dict())
         status = info.status
         if status != 0:
             break
+        main += info.resto != 1
     iters = hist[-1]["k"]
     return dict(status=status, iters=iters, obj=st.objective(), x=st.x(), history=hist, state=st)
 

@@ -18,6 +18,7 @@
 #include "internal.cuh"
 #include "ipm_core.cuh"
 #include "opf.cuh"
+#include "resto_dev.cuh"
 
 namespace cipm {
 
@@ -33,6 +34,10 @@ __global__ void k_x0(int nb, int ng, const double *R, const double *xl, const do
                      double *x) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < 2 * nb + 2 * ng) x[j] = x0_at(nb, ng, R[R_PD], R[R_QD], xl, xu, j);
+}
+__global__ void k_push(int n, const double *xl, const double *xu, double *x) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[j] = push_at(x[j], xl, xu, j);
 }
 
 // row scale d_r = min(1, 100 / max_j |J_rj|) (Ipopt gradient-based scaling)
@@ -207,6 +212,77 @@ __global__ void k_init_duals(Dims D, It P, double *s) {
   init_duals_at(D, P, s, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// ------------------------------------------------------------------ restoration phase kernels
+__global__ void k_rows_absmax(Dims D, const double *geq, const double *hin, const double *s,
+                              double *R) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  red_max(R, R_RS_PRIM, i < D.me + D.mi ? fabs(r_c(D, geq, hin, s, i)) : 0.0);
+}
+__global__ void k_resto_start(RArgs A, double mu_r, double *xr, double *dr2) {
+  resto_start_at(A, mu_r, xr, dr2, blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void k_resto_rhs(RArgs A) { resto_rhs_at(A, blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void k_resto_aug(RArgs A, double *d, double *b) {
+  resto_aug_at(A, d, b, blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void k_resto_recover(RArgs A) {
+  resto_recover_at(A, blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void k_resto_ftb(RArgs A, double tau, double *R) {
+  double ap, az, g;
+  resto_ftb_at(A, tau, &ap, &az, &g, blockIdx.x * blockDim.x + threadIdx.x);
+  red_min(R, R_AMAX, ap);
+  red_min(R, R_AZ, az);
+  red_sum(R, R_GPHI_X, g);
+}
+__global__ void k_resto_trial(RArgs A, double a, double *xt, double *st, double *pt,
+                              double *qt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A.D.n) xt[i] = A.P.x[i] + a * A.dx[i];
+  if (i < A.D.mi) st[i] = A.P.s[i] + a * A.ds[i];
+  if (i < A.D.me + A.D.mi) {
+    pt[i] = A.p[i] + a * A.dp[i];
+    qt[i] = A.q[i] + a * A.dq[i];
+  }
+}
+__global__ void k_resto_merit(RArgs A, const double *xt, const double *st, const double *pt,
+                              const double *qt, const double *geqt, const double *hint,
+                              double *R) {
+  const RMerit M = resto_merit_at(A, xt, st, pt, qt, geqt, hint,
+                                  blockIdx.x * blockDim.x + threadIdx.x);
+  red_sum(R, R_TH_G, M.th);
+  red_sum(R, R_RS_OBJ, M.obj);
+  red_sum(R, R_LOG_S, M.ls);
+  red_sum(R, R_LOG_XL, M.lxl);
+  red_sum(R, R_LOG_XU, M.lxu);
+}
+__global__ void k_resto_errors(RArgs A, double mu, double *R) {
+  const RErr E = resto_errors_at(A, mu, blockIdx.x * blockDim.x + threadIdx.x);
+  red_max(R, R_RS_DUAL, E.dual);
+  red_max(R, R_RS_PRIM, E.prim);
+  red_max(R, R_RS_COMP, E.comp);
+  red_sum(R, R_RS_SUMD, E.sumd);
+  red_sum(R, R_RS_SUMC, E.sumc);
+}
+__global__ void k_resto_accept(RArgs A, double alpha, double az, const double *xt,
+                               const double *st, const double *pt, const double *qt) {
+  resto_accept_at(A, alpha, az, xt, st, pt, qt, blockIdx.x * blockDim.x + threadIdx.x);
+}
+// back to the main problem: constraint multipliers from zero, large bound multipliers reset
+// to one (as Ipopt does after its restoration phase)
+__global__ void k_resto_finish(Dims D, It P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < D.n) {
+    if (P.zl[i] > 1e3) P.zl[i] = 1.0;
+    if (P.zu[i] > 1e3) P.zu[i] = 1.0;
+  }
+  if (i < D.mi) {
+    P.z[i] = 0.0;
+    if (P.v[i] > 1e3) P.v[i] = 1.0;
+  }
+  if (i < D.me) P.y[i] = 0.0;
+}
+
 }  // namespace cipm
 
 using namespace cipm;
@@ -237,6 +313,15 @@ struct ipm_state_s {
   int nl = 0, nu = 0;
   bool have_kkt = false;  // a KKT solve has completed (ipm_state_export_kkt)
   double last_dw = 0.0;
+  // restoration phase: per IPM row p, q, their duals, steps and trial values; reference point
+  double *rp = nullptr, *rq = nullptr, *rzp = nullptr, *rzq = nullptr, *rdp = nullptr,
+         *rdq = nullptr, *rdzp = nullptr, *rdzq = nullptr, *rpt = nullptr, *rqt = nullptr;
+  double *rxr = nullptr, *rdr2 = nullptr, *rrc = nullptr, *rrp = nullptr, *rrq = nullptr;
+  bool in_resto = false, have_theta0_r = false;
+  double mu_r = 0, zeta_r = 0, tau_r = 0, theta_start = 0, theta_max_r = 0, theta_min_r = 0;
+  double delta_last_r = 0, entry_theta = 0, entry_phi = 0;
+  std::vector<double> filter_r;
+  int k_r = 0;
 };
 
 static int grid1(int64_t n) { return grid_for(n > 0 ? n : 1, 256); }
@@ -322,8 +407,22 @@ static int merit(ipm_state_t S, const double *x, const double *sv, const double 
   return IPM_OK;
 }
 
+static int state_create(ipm_opf_t opf, const ipm_options *opt, const double *x0_host,
+                        cudaStream_t stream, ipm_state_t *out);
+
 extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStream_t stream,
                                 ipm_state_t *out) {
+  return state_create(opf, opt, nullptr, stream, out);
+}
+
+extern "C" int ipm_state_create_at(ipm_opf_t opf, const ipm_options *opt, const double *x0,
+                                   cudaStream_t stream, ipm_state_t *out) {
+  if (!x0) return IPM_ERR_BAD_ARG;
+  return state_create(opf, opt, x0, stream, out);
+}
+
+static int state_create(ipm_opf_t opf, const ipm_options *opt, const double *x0_host,
+                        cudaStream_t stream, ipm_state_t *out) {
   if (!opf || !opt || !out || opt->kkt < 0 || opt->kkt > 2 || !(opt->tol > 0)) {
     set_error_msg("ipm_state_create: bad argument");
     return IPM_ERR_BAD_ARG;
@@ -365,6 +464,10 @@ extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStrea
   A(&S->dz, D.mi); A(&S->ds, D.mi); A(&S->dv, D.mi); A(&S->dzl, n); A(&S->dzu, n);
   A(&S->xt, n); A(&S->st, D.mi); A(&S->geqt, D.me); A(&S->hint, D.mi); A(&S->gst, M.me);
   A(&S->hst, M.mi); A(&S->ft, 2); A(&S->R, R_COUNT); A(&S->eta, 1);
+  const int64_t nr = (int64_t)D.me + D.mi;
+  A(&S->rp, nr); A(&S->rq, nr); A(&S->rzp, nr); A(&S->rzq, nr); A(&S->rdp, nr); A(&S->rdq, nr);
+  A(&S->rdzp, nr); A(&S->rdzq, nr); A(&S->rpt, nr); A(&S->rqt, nr); A(&S->rrc, nr);
+  A(&S->rrp, nr); A(&S->rrq, nr); A(&S->rxr, n); A(&S->rdr2, n);
   S->P.xl = M.xl;
   S->P.xu = M.xu;
   if (rc == IPM_OK) rc = dev_alloc(&S->info, 2);
@@ -395,9 +498,17 @@ extern "C" int ipm_state_create(ipm_opf_t opf, const ipm_options *opt, cudaStrea
     cudaStream_t s = stream;
     double zero = 0.0;
     for (int k = 0; k < R_COUNT; ++k) cudaMemcpy(S->R + k, &zero, sizeof(double), cudaMemcpyHostToDevice);
-    k_setup_sums<<<grid1(M.nb), 256, 0, s>>>(M.nb, M.pd, M.qd, S->R);
-    k_x0<<<grid1(n), 256, 0, s>>>(M.nb, M.ng, S->R, M.xl, M.xu, S->P.x);
-    rc = opf_flow_start(M, S->P.x, s);
+    if (x0_host) {
+      // the caller's point, pushed inside the bounds
+      if (cudaMemcpyAsync(S->P.x, x0_host, sizeof(double) * n, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+        rc = IPM_ERR_CUDA;
+      k_push<<<grid1(n), 256, 0, s>>>(n, M.xl, M.xu, S->P.x);
+    } else {
+      k_setup_sums<<<grid1(M.nb), 256, 0, s>>>(M.nb, M.pd, M.qd, S->R);
+      k_x0<<<grid1(n), 256, 0, s>>>(M.nb, M.ng, S->R, M.xl, M.xu, S->P.x);
+      rc = opf_flow_start(M, S->P.x, s);
+    }
     if (rc == IPM_OK)
       rc = opf_eval(M, S->P.x, nullptr, nullptr, 1.0, S->f, S->P.grad, S->gs, S->hs, S->Jv,
                     nullptr, s);
@@ -436,6 +547,221 @@ extern "C" void ipm_state_destroy(ipm_state_t S) {
   if (S->num32) ipm_num_destroy(S->num32);
   if (S->sym) ipm_symbolic_destroy(S->sym);
   delete S;
+}
+
+// ------------------------------------------------------------------ restoration phase (host)
+static RArgs rargs(ipm_state_t S, double dw) {
+  RArgs A;
+  A.D = S->D;
+  A.P = S->P;
+  A.p = S->rp; A.q = S->rq; A.zp = S->rzp; A.zq = S->rzq;
+  A.xr = S->rxr; A.dr2 = S->rdr2;
+  A.sigma = S->sigma; A.r1 = S->r1; A.r2 = S->r2; A.Ds = S->Ds;
+  A.rc = S->rrc; A.rp = S->rrp; A.rq = S->rrq;
+  A.mu = S->mu_r; A.zeta = S->zeta_r; A.dw = dw;
+  A.dx = S->dx; A.jdx = S->jdx;
+  A.dy = S->dy; A.dz = S->dz; A.ds = S->ds; A.dv = S->dv; A.dzl = S->dzl; A.dzu = S->dzu;
+  A.dp = S->rdp; A.dq = S->rdq; A.dzp = S->rdzp; A.dzq = S->rdzq;
+  return A;
+}
+
+static int nmax_r(ipm_state_t S) {
+  return std::max({S->D.n, S->D.me + S->D.mi, S->D.me0 + S->D.mi0});
+}
+
+// theta_R, phi_R at (xt, st, pt, qt) with the model rows geqt / hint of xt
+static int resto_merit(ipm_state_t S, const double *xt, const double *st, const double *pt,
+                       const double *qt, const double *geqt, const double *hint, double mu,
+                       double *theta, double *phi) {
+  CKR(reduce_reset(S, {R_TH_G, R_RS_OBJ, R_LOG_S, R_LOG_XL, R_LOG_XU}, 0.0));
+  k_resto_merit<<<grid1(nmax_r(S)), 256, 0, S->stream>>>(rargs(S, 0.0), xt, st, pt, qt, geqt,
+                                                          hint, S->R);
+  CKL();
+  CKR(read_R(S));
+  const double *h = S->hR;
+  *theta = h[R_TH_G];
+  *phi = h[R_RS_OBJ] - mu * (h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU]);
+  return IPM_OK;
+}
+
+// scaled optimality error of the restoration problem (Ipopt's E_mu with its s_d, s_c; the bounds
+// p, q >= 0 count among the bounds)
+static int resto_errors(ipm_state_t S, double mu, double *out) {
+  CKR(reduce_reset(S, {R_RS_DUAL, R_RS_PRIM, R_RS_COMP, R_RS_SUMD, R_RS_SUMC}, 0.0));
+  k_resto_errors<<<grid1(nmax_r(S)), 256, 0, S->stream>>>(rargs(S, 0.0), mu, S->R);
+  CKL();
+  CKR(read_R(S));
+  const double *h = S->hR;
+  const int R = S->D.me + S->D.mi, nb = S->nl + S->nu + 2 * R;
+  const double sd = std::max(S_MAX, h[R_RS_SUMD] / std::max(S->D.me + 2 * S->D.mi + nb, 1)) / S_MAX;
+  const double sc = std::max(S_MAX, h[R_RS_SUMC] / std::max(S->D.mi + nb, 1)) / S_MAX;
+  *out = std::max({h[R_RS_DUAL] / sd, h[R_RS_PRIM], h[R_RS_COMP] / sc});
+  return IPM_OK;
+}
+
+// enter the restoration phase at the current iterate (the line search failed); theta, phi of
+// the main problem there, whose filter entry the phase must beat
+static int resto_begin(ipm_state_t S, double theta, double phi) {
+  cudaStream_t s = S->stream;
+  CKR(reduce_reset(S, {R_RS_PRIM}, 0.0));
+  k_rows_absmax<<<grid1(S->D.me + S->D.mi), 256, 0, s>>>(S->D, S->P.geq, S->P.hin, S->P.s, S->R);
+  CKL();
+  CKR(read_R(S));
+  S->mu_r = std::max(S->mu, S->hR[R_RS_PRIM]);
+  S->zeta_r = std::sqrt(S->mu_r);
+  S->tau_r = std::max(TAU_MIN, 1.0 - S->mu_r);
+  k_resto_start<<<grid1(nmax_r(S)), 256, 0, s>>>(rargs(S, 0.0), S->mu_r, S->rxr, S->rdr2);
+  CKL();
+  S->entry_theta = (1 - GAMMA_THETA) * theta;
+  S->entry_phi = phi - GAMMA_PHI * theta;
+  S->theta_start = theta;
+  S->filter_r.clear();
+  S->have_theta0_r = false;
+  S->delta_last_r = 0.0;
+  S->k_r = 0;
+  S->in_resto = true;
+  CK(cudaStreamSynchronize(s));
+  return IPM_OK;
+}
+
+// one iteration of the filter IPM on the restoration problem, then the return test
+static int resto_step(ipm_state_t S, ipm_iter_info *info) {
+  cudaStream_t s = S->stream;
+  const Dims &D = S->D;
+  const OpfData &M = S->opf->M;
+  const int n = D.n, m = D.me0 + D.mi0, nr = nmax_r(S);
+  info->resto = 1;
+  if (S->k_r >= 500) return IPM_ERR_RESTORATION;
+  CKR(eval_point(S, S->P.x, S->gs, S->hs, S->P.geq, S->P.hin, S->f, true));
+  CKR(jt_lambda(S));
+  double e0, theta, phi;
+  CKR(resto_errors(S, 0.0, &e0));
+  if (!S->have_theta0_r) {
+    CKR(resto_merit(S, S->P.x, S->P.s, S->rp, S->rq, S->P.geq, S->P.hin, S->mu_r, &theta, &phi));
+    S->theta_max_r = 1e4 * std::max(1.0, theta);
+    S->theta_min_r = 1e-4 * std::max(1.0, theta);
+    S->have_theta0_r = true;
+  }
+  info->kkt_err = e0;
+  // a stationary point of the restoration problem reached before the return test passed: a
+  // local minimizer of the constraint violation
+  if (e0 <= S->opt.tol) return IPM_ERR_INFEASIBLE;
+  bool first = true;
+  while (true) {
+    double emu;
+    CKR(resto_errors(S, S->mu_r, &emu));
+    if (!(emu <= KAPPA_EPS * S->mu_r && (first || S->k_r == 0))) break;
+    S->mu_r = std::max(S->opt.tol / 10.0, std::min(KAPPA_MU * S->mu_r, std::pow(S->mu_r, THETA_MU)));
+    S->tau_r = std::max(TAU_MIN, 1.0 - S->mu_r);
+    S->filter_r.clear();
+    first = false;
+  }
+  info->mu = S->mu_r;
+  // Hessian of the constraints' Lagrangian only (the restoration objective is quadratic in x
+  // with its Hessian zeta D_R^2 on the diagonal, added to sigma)
+  k_mul<<<grid1(m), 256, 0, s>>>(m, S->lam, S->dscale, S->lamw);
+  CKL();
+  CKR(opf_eval(M, S->P.x, S->lamw, S->lamw + D.me0, 0.0, S->ft, nullptr, S->gst, S->hst, nullptr,
+               S->Wv, s));
+  k_resto_rhs<<<grid1(nr), 256, 0, s>>>(rargs(S, 0.0));
+  k_neg<<<grid1(n), 256, 0, s>>>(n, S->r1, S->a);
+  CKL();
+  // inertia correction as in the main iterations
+  double dw = 0.0;
+  bool ok = false;
+  int nfac = 0;
+  const double grow = S->delta_last_r > 0 ? 8.0 : 100.0;
+  double next = S->delta_last_r > 0 ? std::max(1e-20, S->delta_last_r / 3.0) : 1e-4;
+  for (int attempt = 0; attempt < 200; ++attempt) {
+    dw = attempt == 0 ? 0.0 : next;
+    if (attempt > 0) next *= grow;
+    if (dw >= 1e40) break;
+    k_resto_aug<<<grid1(m), 256, 0, s>>>(rargs(S, dw), S->dcond, S->baug);
+    CKL();
+    CKR(ipm_condense(S->sym, S->num, S->Wv, S->sigma, S->Jv, S->dcond, dw, s));
+    CKR(ipm_factor(S->sym, S->num, S->info, s));
+    int hinfo = 0;
+    CK(cudaMemcpyAsync(&hinfo, S->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ++nfac;
+    if (hinfo == -2) return IPM_ERR_TIMEOUT;
+    if (hinfo != -1) continue;
+    const int st = ipm_aug_solve(S->sym, S->num, S->Wv, S->sigma, S->Jv, S->dcond, dw, S->a,
+                                 S->baug, S->dx, S->dzc, S->opt.max_refine, 1e-10, S->eta,
+                                 S->steps, s);
+    if (st < 0 || st == IPM_ERR_TIMEOUT || st == IPM_ERR_NONFINITE) return st;
+    if (st == IPM_ERR_NOT_PD) continue;
+    ok = true;
+    break;
+  }
+  if (!ok) return IPM_ERR_INERTIA;
+  if (dw > 0) S->delta_last_r = dw;
+  info->delta_w = dw;
+  info->n_factor = nfac;
+  CK(cudaMemcpy(&info->eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost));
+  k_jv<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, M.J_colind, S->Jv, S->dx, S->jdx);
+  k_resto_recover<<<grid1(nr), 256, 0, s>>>(rargs(S, dw));
+  CKL();
+  // fraction to the boundary, d phi_R, theta_R and phi_R at the iterate
+  CKR(reduce_reset(S, {R_AMAX, R_AZ}, 1.0));
+  CKR(reduce_reset(S, {R_GPHI_X}, 0.0));
+  k_resto_ftb<<<grid1(nr), 256, 0, s>>>(rargs(S, dw), S->tau_r, S->R);
+  CKL();
+  CKR(read_R(S));
+  const double amax = S->hR[R_AMAX], az = S->hR[R_AZ], gphi = S->hR[R_GPHI_X];
+  CKR(resto_merit(S, S->P.x, S->P.s, S->rp, S->rq, S->P.geq, S->P.hin, S->mu_r, &theta, &phi));
+  double amin;
+  if (gphi < 0)
+    amin = GAMMA_ALPHA * std::min({GAMMA_THETA, GAMMA_PHI * theta / -gphi,
+                                   DELTA_SW * std::pow(theta, S_THETA) / std::pow(-gphi, S_PHI)});
+  else
+    amin = GAMMA_ALPHA * GAMMA_THETA;
+  double alpha = amax;
+  bool accepted = false;
+  int ft = 0, ls = 0;
+  while (true) {
+    k_resto_trial<<<grid1(nr), 256, 0, s>>>(rargs(S, dw), alpha, S->xt, S->st, S->rpt, S->rqt);
+    CKL();
+    CKR(eval_point(S, S->xt, S->gst, S->hst, S->geqt, S->hint, S->ft, false));
+    double tht, pht;
+    CKR(resto_merit(S, S->xt, S->st, S->rpt, S->rqt, S->geqt, S->hint, S->mu_r, &tht, &pht));
+    accepted = filter_accept(theta, phi, gphi, alpha, tht, pht, S->filter_r.data(),
+                             (int)(S->filter_r.size() / 2), S->theta_min_r, S->theta_max_r, &ft);
+    if (accepted) break;
+    ++ls;
+    alpha *= 0.5;
+    if (alpha < amin) break;
+  }
+  info->ls_steps = ls;
+  info->alpha = alpha;
+  info->theta = theta;
+  if (!accepted) return IPM_ERR_RESTORATION;
+  if (!ft) {
+    S->filter_r.push_back((1 - GAMMA_THETA) * theta);
+    S->filter_r.push_back(phi - GAMMA_PHI * theta);
+  }
+  RArgs A = rargs(S, dw);
+  k_resto_accept<<<grid1(nr), 256, 0, s>>>(A, alpha, az, S->xt, S->st, S->rpt, S->rqt);
+  CKL();
+  S->k_r++;
+  // return test: the original violation reduced to KAPPA_RESTO times the phase's start and the
+  // point acceptable to the original filter (with the start's entry)
+  CKR(eval_point(S, S->P.x, S->gs, S->hs, S->P.geq, S->P.hin, S->f, false));
+  double th0, ph0;
+  CKR(merit(S, S->P.x, S->P.s, S->P.geq, S->P.hin, S->f, S->mu, &th0, &ph0));
+  bool back = th0 <= KAPPA_RESTO * S->theta_start && th0 < S->theta_max &&
+              (th0 < S->entry_theta || ph0 < S->entry_phi);
+  for (size_t q = 0; back && q + 1 < S->filter.size(); q += 2)
+    if (!(th0 < S->filter[q] || ph0 < S->filter[q + 1])) back = false;
+  if (back) {
+    k_resto_finish<<<grid1(nr), 256, 0, s>>>(D, S->P);
+    CKL();
+    S->filter.push_back(S->entry_theta);
+    S->filter.push_back(S->entry_phi);
+    S->in_resto = false;
+  }
+  CK(cudaStreamSynchronize(s));
+  return IPM_OK;
 }
 
 static int step_impl(ipm_state_t S, ipm_iter_info *info) {
@@ -641,8 +967,11 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   info->alpha = alpha;
   info->theta = theta;
   if (!accepted) {
-    S->status = IPM_ERR_RESTORATION;
-    info->status = IPM_ERR_RESTORATION;
+    // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the following calls iterate
+    // on the restoration problem until its return test passes
+    CKR(resto_begin(S, theta, phi));
+    info->resto = 2;
+    S->k++;
     return IPM_OK;
   }
   if (!ftype) {
@@ -664,7 +993,14 @@ extern "C" int ipm_step(ipm_state_t S, ipm_iter_info *info) {
     info->status = S->status;
     return IPM_OK;
   }
-  int rc = step_impl(S, info);
+  int rc;
+  if (S->in_resto) {
+    *info = ipm_iter_info{};
+    info->k = S->k;
+    rc = resto_step(S, info);
+  } else {
+    rc = step_impl(S, info);
+  }
   if (rc != IPM_OK) {
     S->status = rc;
     info->status = rc;

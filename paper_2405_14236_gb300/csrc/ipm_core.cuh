@@ -55,6 +55,9 @@ enum {
   // barrier test can try several mu without another pass over the vectors.
   R_SV_MIN, R_SV_MAX, R_CL_MIN, R_CL_MAX, R_CU_MIN, R_CU_MAX,
   R_CG_A, R_CG_B,  // batched HyKKT CG: r.r and p.S p
+  // restoration phase (single-problem IPM): objective part of phi_R, maxima of the dual,
+  // primal and complementarity residuals, sums of all multipliers and of the bound-type ones
+  R_RS_OBJ, R_RS_DUAL, R_RS_PRIM, R_RS_COMP, R_RS_SUMD, R_RS_SUMC,
   R_COUNT
 };
 
@@ -114,14 +117,9 @@ struct StepArgs {
   double *dz, *ds, *dv, *dzl, *dzu;
 };
 
-// flat start (|V| = 1, theta = 0, generators share the load equally), pushed inside the bounds
-__device__ __forceinline__ double x0_at(int nb, int ng, double psum, double qsum,
-                                        const double *xl, const double *xu, int j) {
-  double v;
-  if (j < nb) v = 1.0;
-  else if (j < 2 * nb) v = 0.0;
-  else if (j < 2 * nb + ng) v = fmin(fmax(psum / ng, xl[j]), xu[j]);
-  else v = fmin(fmax(qsum / ng, xl[j]), xu[j]);
+// a starting value moved strictly inside the bounds of variable j (Ipopt's bound push with
+// kappa_1 = kappa_2 = 1e-2)
+__device__ __forceinline__ double push_at(double v, const double *xl, const double *xu, int j) {
   const bool hl = isfinite(xl[j]), hu = isfinite(xu[j]);
   double pl = hl ? KAPPA1 * fmax(1.0, fabs(xl[j])) : 0.0;
   double pu = hu ? KAPPA1 * fmax(1.0, fabs(xu[j])) : 0.0;
@@ -132,6 +130,17 @@ __device__ __forceinline__ double x0_at(int nb, int ng, double psum, double qsum
   if (hl) v = fmax(v, xl[j] + pl);
   if (hu) v = fmin(v, xu[j] - pu);
   return v;
+}
+
+// flat start (|V| = 1, theta = 0, generators share the load equally), pushed inside the bounds
+__device__ __forceinline__ double x0_at(int nb, int ng, double psum, double qsum,
+                                        const double *xl, const double *xu, int j) {
+  double v;
+  if (j < nb) v = 1.0;
+  else if (j < 2 * nb) v = 0.0;
+  else if (j < 2 * nb + ng) v = fmin(fmax(psum / ng, xl[j]), xu[j]);
+  else v = fmin(fmax(qsum / ng, xl[j]), xu[j]);
+  return push_at(v, xl, xu, j);
 }
 
 // IPM constraint values from the scaled model: HyKKT  g' = g~, h' = h~;
