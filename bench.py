@@ -559,6 +559,7 @@ def run_gpu(args, rank, world, local_rank):
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, conv, iters_mean, iters_max, sweeps = [], [], [], [], []
+    stopped, resto_phases, resto_iters = {}, [], []
     fact_ms = solve_ms = 0.0
     n_sw = 0
     nfac = 0
@@ -583,6 +584,10 @@ def run_gpu(args, rank, world, local_rank):
         fl_tot += float(np.sum(fl_inst * r["n_factor"]))
         by_tot += float(np.sum(w["bytes"] * r["n_factor"]))
         conv.append(int((r["status"] == 1).sum()))
+        for code in r["status"][r["status"] != 1]:
+            stopped[int(code)] = stopped.get(int(code), 0) + 1
+        resto_phases.append(int(r["resto_phases"].sum()))
+        resto_iters.append(int(r["resto_iters"].sum()))
         iters_mean.append(float(r["iters"].mean()))
         iters_max.append(int(r["iters"].max()))
         sweeps.append(int(r["sweeps"]))
@@ -663,6 +668,10 @@ def run_gpu(args, rank, world, local_rank):
         "gathered_converged": None if gathered is None else int((gathered["status"] == 1).sum()),
         "iters_mean": float(np.mean(iters_mean)),
         "iters_max": iters_max, "sweeps_per_step": sweeps,
+        # statuses of the instances that did not converge, over all timed steps; feasibility
+        # restoration phases entered and their iterations, per step
+        "stopped_status_counts": {str(k): v for k, v in sorted(stopped.items())},
+        "restoration": {"phases_per_step": resto_phases, "iters_per_step": resto_iters},
         "launches_per_sweep": B.info()["launches_per_sweep"], "init_s": init_s,
         "launch_shape": shape, "autotune_s": autotune_s, "supernode_shape": sn_tune,
         "roofline": {"kernel": "k_b_fact_inst (condensation + factorization, every instance)",

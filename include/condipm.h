@@ -312,6 +312,8 @@ typedef struct {
                        iterations are too ill-conditioned for an FP32 factor) */
   int sn_relax_w;   /* supernode partition (ipm_symbolic_relaxed); <= 0 means (8, 5) */
   int sn_relax_den;
+  int no_resto;     /* nonzero: no feasibility restoration phase (a failed line search ends the
+                       solve with IPM_ERR_RESTORATION) */
 } ipm_options;
 
 typedef struct {
@@ -371,7 +373,8 @@ int ipm_state_export(ipm_state_t state, double *x, double *obj);
  * W_val [nnzW]: lower-triangular Hessian values in the model's W pattern (scaled multipliers and
  * objective); sigma [n]; J_val [nnzJ]: the scaled Jacobian in the model's J pattern (rows
  * [G; H], m = m_e0 + m_i0); d_row [m]: the row weights the condensed matrix was built with
- * (LiftedKKT: the two relaxed rows of an equality merged, D1 + D2; HyKKT: gamma on G rows);
+ * (LiftedKKT: the two relaxed rows of an equality merged, D1 + D2; HyKKT: gamma on G rows; a
+ * step of the restoration phase: 1/E_r on every row, *m_e = 0 for every form);
  * *delta_w; a [n], b [m]: right-hand sides; dx [n], dyz [m]: the refined solution (HyKKT: dy
  * over the G rows, then dz).  Returns IPM_ERR_BAD_ARG before the first step.  Synchronizes. */
 int ipm_state_export_kkt(ipm_state_t state, double *W_val, double *sigma, double *J_val,
@@ -390,7 +393,8 @@ void ipm_state_destroy(ipm_state_t state);
  * the per-instance control of the algorithm of ipm_step (convergence test, barrier update,
  * inertia correction, refinement or CG, fraction to the boundary, filter line search) runs on the
  * device, so a sweep of the method is one CUDA graph and every instance follows the
- * single-problem iteration up to the order of floating-point additions. */
+ * single-problem iteration up to the order of floating-point additions (the restoration phase
+ * included; its steps are the refined condensed solves of ipm_step's phase for every form). */
 typedef struct ipm_batch_s *ipm_batch_t;
 
 /* Creates the batch over count model handles (HOST array of handles that must outlive the batch;
@@ -410,8 +414,11 @@ int ipm_batch_info(ipm_batch_t batch, int *npatterns, int64_t *device_bytes,
 /* Puts every instance back at its starting point (as after ipm_batch_create).  Stream-ordered. */
 int ipm_batch_reset(ipm_batch_t batch);
 /* Runs sweeps until every instance has converged (status 1) or stopped: IPM_ERR_INERTIA,
- * IPM_ERR_RESTORATION, IPM_ERR_NONFINITE, IPM_ERR_TIMEOUT, or IPM_ERR_MAXITER after max_iter
- * iterations (or when max_sweeps sweeps end first).  use_graph != 0 replays one captured CUDA
+ * IPM_ERR_RESTORATION, IPM_ERR_INFEASIBLE, IPM_ERR_NONFINITE, IPM_ERR_TIMEOUT, or
+ * IPM_ERR_MAXITER after max_iter iterations (or when max_sweeps sweeps end first).  An instance
+ * whose line search fails enters the feasibility restoration phase of ipm_step (unless
+ * opt->no_resto), on the device like every other step; its iterations are sweeps of the same
+ * graph, do not count against max_iter, and end as in ipm_step.  use_graph != 0 replays one captured CUDA
  * graph per sweep, else the sweep's kernels are launched one by one.  Reads one int back per
  * sweep.  Synchronizes. */
 int ipm_batch_run(ipm_batch_t batch, int max_iter, int max_sweeps, int use_graph);
@@ -433,6 +440,9 @@ int ipm_batch_autotune(ipm_batch_t batch, int sweeps, int max_results, int *n_re
 /* HyKKT batches: CG iterations per instance since creation or the last reset into a HOST array
  * [count] (0 for the other forms).  Synchronizes. */
 int ipm_batch_cg_iters(ipm_batch_t batch, int *cg_iters);
+/* Feasibility restoration per instance since creation or the last reset, into HOST arrays
+ * [count] (either may be NULL): phases entered and restoration iterations made.  Synchronizes. */
+int ipm_batch_resto_counts(ipm_batch_t batch, int *phases, int *iters);
 /* Copies instance i's x [n] into a HOST buffer.  Synchronizes. */
 int ipm_batch_export(ipm_batch_t batch, int i, double *x);
 /* Sweeps run since creation or the last reset. */

@@ -484,6 +484,13 @@ def _ipm(model, opt, start, mu, sig_f, exit_check=None, restore=True, max_iter=N
                 accepted = soft = True
                 alpha = amax
                 ftype = True
+        if (not accepted and restore and opt.restoration
+                and max(np.abs(g).max(initial=0.0), np.abs(h + s).max(initial=0.0)) <= opt.tol):
+            # a failed line search at a point that is feasible within the tolerance: the
+            # restoration phase cannot reduce a violation that is already at rounding level, and
+            # its problem is solved by the point itself (reading: the method stops there)
+            status = "restoration_failed"
+            break
         if not accepted and restore and opt.restoration:
             # feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the current point
             # enters the filter, a point acceptable to it with a smaller constraint violation is
@@ -544,8 +551,10 @@ def _restoration(model, opt, x, s, v, zl, zu, mu, theta, theta_max, filt, theta_
     returns (status "ok") at the first restoration iterate whose x and s reduce the original
     constraint violation to at most KAPPA_RESTO theta and are acceptable to the original filter
     (which holds the point the phase started from); "infeasible" when it converges to a
-    stationary point of the restoration problem first (a local minimizer of the violation);
-    "restoration_failed" otherwise."""
+    stationary point of the restoration problem first (a local minimizer of the violation) whose
+    violation ||c||_inf exceeds the tolerance; "restoration_failed" otherwise (the phase's own
+    line search or iteration limit, or convergence at a point feasible within the tolerance
+    that the filter still rejects)."""
     n, me, mi = model.n, model.m_e, model.m_i
     g, h = model.cons(x)
     c = np.concatenate([g, h + s])
@@ -570,7 +579,12 @@ def _restoration(model, opt, x, s, v, zl, zu, mu, theta, theta_max, filt, theta_
     rr = _ipm(R, ropt, start, mu_r, 1.0, exit_check=exit_check, restore=False, max_iter=500)
     out = dict(iters=rr.iters)
     if rr.status != "exited":
-        out["status"] = "infeasible" if rr.status == "converged" else "restoration_failed"
+        infeasible = False
+        if rr.status == "converged":
+            gk, hk = model.cons(rr.x[:n])
+            cinf = max(np.abs(gk).max(initial=0.0), np.abs(hk + rr.s).max(initial=0.0))
+            infeasible = cinf > opt.tol
+        out["status"] = "infeasible" if infeasible else "restoration_failed"
         return out
     reset = lambda a: np.where(a > 1e3, 1.0, a)   # large bound multipliers reset (Ipopt)
     out.update(status="ok", x=rr.x[:n].copy(), s=rr.s.copy(), v=reset(rr.v),

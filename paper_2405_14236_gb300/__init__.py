@@ -65,6 +65,7 @@ _SIGS = {
     "ipm_batch_run": (I, [P, I, I, I]),
     "ipm_batch_results": (I, [P, P, P, P, P, P, P]),
     "ipm_batch_cg_iters": (I, [P, P]),
+    "ipm_batch_resto_counts": (I, [P, P, P]),
     "ipm_batch_autotune": (I, [P, I, I, P, P, P, P]),
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
@@ -100,7 +101,7 @@ class IpmOptions(ctypes.Structure):
                 ("tau", ctypes.c_double), ("mu0", ctypes.c_double), ("cg_rtol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("cg_maxit", ctypes.c_int),
                 ("precision", ctypes.c_int), ("sn_relax_w", ctypes.c_int),
-                ("sn_relax_den", ctypes.c_int)]
+                ("sn_relax_den", ctypes.c_int), ("no_resto", ctypes.c_int)]
 
 
 class IpmIterInfo(ctypes.Structure):
@@ -351,12 +352,15 @@ class IpmState:
     """GPU interior-point iterate for an ``Opf`` problem (ipm_state_create / ipm_step)."""
 
     def __init__(self, opf, kkt="lifted", tol=1e-6, gamma=1e6, tau=0.0, mu0=0.1, cg_rtol=1e-10,
-                 max_refine=10, cg_maxit=0, precision=64, stream=None, relax=(0, 0), x0=None):
+                 max_refine=10, cg_maxit=0, precision=64, stream=None, relax=(0, 0), x0=None,
+                 restoration=True):
         """x0: optional starting point (n host values, pushed inside the bounds;
-        ipm_state_create_at), else the flat start."""
+        ipm_state_create_at), else the flat start.  restoration=False: a failed line search
+        ends the solve (IPM_ERR_RESTORATION) instead of entering the restoration phase."""
         self.opf = opf
         o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
-                       cg_rtol, max_refine, cg_maxit, precision, int(relax[0]), int(relax[1]))
+                       cg_rtol, max_refine, cg_maxit, precision, int(relax[0]), int(relax[1]),
+                       int(not restoration))
         h = ctypes.c_void_p()
         if x0 is None:
             _check(lib().ipm_state_create(opf.h, ctypes.byref(o), _stream(stream),
@@ -432,11 +436,12 @@ class Batch:
     "hykkt" (CG on the Schur complement of K_gamma) or "regularized"."""
 
     def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, kkt="lifted", gamma=1e6,
-                 cg_rtol=1e-10, cg_maxit=0, stream=None, relax=(0, 0)):
+                 cg_rtol=1e-10, cg_maxit=0, stream=None, relax=(0, 0), restoration=True):
         self.opfs = list(opfs)
         arr = (ctypes.c_void_p * len(self.opfs))(*[o.h.value for o in self.opfs])
         o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
-                       cg_rtol, max_refine, cg_maxit, 64, int(relax[0]), int(relax[1]))
+                       cg_rtol, max_refine, cg_maxit, 64, int(relax[0]), int(relax[1]),
+                       int(not restoration))
         h = ctypes.c_void_p()
         _check(lib().ipm_batch_create(len(self.opfs), arr, ctypes.byref(o), _stream(stream),
                                       ctypes.byref(h)), "ipm_batch_create")
@@ -466,8 +471,11 @@ class Batch:
                "ipm_batch_results")
         cg = np.zeros(n, np.int32)
         _check(lib().ipm_batch_cg_iters(self.h, p(cg)), "ipm_batch_cg_iters")
+        rph, rit = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        _check(lib().ipm_batch_resto_counts(self.h, p(rph), p(rit)), "ipm_batch_resto_counts")
         return dict(status=st, iters=it, obj=obj, kkt_err=err, n_factor=nf, ls_steps=ls,
-                    cg_iters=cg, sweeps=lib().ipm_batch_sweeps(self.h))
+                    cg_iters=cg, resto_phases=rph, resto_iters=rit,
+                    sweeps=lib().ipm_batch_sweeps(self.h))
 
     def autotune(self, sweeps=8):
         """Times the candidate launch shapes (ipm_batch_autotune) and keeps the fastest; every

@@ -29,6 +29,7 @@
 #include "ipm_core.cuh"
 #include "numeric_dev.cuh"
 #include "opf_dev.cuh"
+#include "resto_dev.cuh"
 
 namespace cipm {
 
@@ -53,6 +54,14 @@ struct BCtl {
   // HyKKT CG: r.r, stopping threshold, step scalars, iterations (this IPM step, in total)
   double cg_rr, cg_stop, cg_alpha, cg_beta;
   int cg_it, cg_total, cg_maxit, pad_;
+  // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): resto 0 = main problem,
+  // 2 = phase entered (its start is set at the next evaluation), 1 = in the phase; ret: the
+  // accepted trial passed the return test.  While in the phase mu, tau, delta_last, theta_max,
+  // theta_min and nfilter belong to the restoration problem and the main problem's are kept in
+  // the *_m fields; k_r counts the phase's iterations.
+  int resto, ret, k_r, nfilter_m, n_resto, total_resto;
+  double mu_m, tau_m, delta_last_m, theta_max_m, theta_min_m;
+  double zeta, theta_start, entry_theta, entry_phi;
 };
 
 // per-instance descriptor (device): pattern and model pointers, iterate and work vectors
@@ -90,7 +99,32 @@ struct BI {
   double *cg_r, *cg_p, *cg_sp, *cg_dy, *cg_rhs1, *cg_v;  // HyKKT CG vectors
   const double *dystep;  // dy of the step: cg_dy (HyKKT), dz over the G rows (form 2)
   AugArgs aug;
+  // restoration phase: p, q and their duals, steps and trial values, row residuals (one per IPM
+  // row), the reference point x_R and D_R^2 (n), the phase's filter (null without restoration)
+  double *rp, *rq, *rzp, *rzq, *rdp, *rdq, *rdzp, *rdzq, *rpt, *rqt, *rrc, *rrp, *rrq;
+  double *rxr, *rdr2, *rfilter;
 };
+
+// restoration-phase arguments of an instance (the element functions of resto_dev.cuh)
+__device__ __forceinline__ RArgs rargs_b(const BI &I, const BCtl &c) {
+  RArgs A;
+  A.D = I.D;
+  A.P = I.P;
+  A.p = I.rp; A.q = I.rq; A.zp = I.rzp; A.zq = I.rzq;
+  A.xr = I.rxr; A.dr2 = I.rdr2;
+  A.sigma = (double *)I.SA.sigma; A.r1 = I.r1; A.r2 = (double *)I.SA.r2;
+  A.Ds = (double *)I.SA.Ds;
+  A.rc = I.rrc; A.rp = I.rrp; A.rq = I.rrq;
+  A.mu = c.mu; A.zeta = c.zeta; A.dw = c.dw;
+  A.dx = I.dx; A.jdx = I.SA.jdx;
+  A.dy = (double *)I.dystep; A.dz = I.SA.dz; A.ds = I.SA.ds; A.dv = I.SA.dv;
+  A.dzl = I.SA.dzl; A.dzu = I.SA.dzu;
+  A.dp = I.rdp; A.dq = I.rdq; A.dzp = I.rdzp; A.dzq = I.rdzq;
+  return A;
+}
+__device__ __forceinline__ int resto_nmax(const BI &I) {
+  return max(I.D.n, max(I.D.me + I.D.mi, I.m));
+}
 
 
 #define B_PROLOGUE(want)                 \
@@ -136,7 +170,9 @@ __device__ __forceinline__ EvalPtrs eval_ptrs(const BI &I, const BCtl &c, int mo
   if (mode == 0) {
     E = EvalPtrs{I.P.x, nullptr, nullptr, 1.0, I.f, I.P.grad, I.gs, I.hs, I.Jv, nullptr};
   } else if (mode == 1) {
-    E = EvalPtrs{I.P.x, I.lamw, I.lamw + I.D.me0, c.sig, I.f, I.P.grad, I.gs, I.hs, I.Jv, I.Wv};
+    // (the restoration problem's W is the constraints' part only)
+    E = EvalPtrs{I.P.x, I.lamw, I.lamw + I.D.me0, c.resto ? 0.0 : c.sig, I.f, I.P.grad, I.gs,
+                 I.hs, I.Jv, I.Wv};
   } else {
     E = EvalPtrs{I.xt, nullptr, nullptr, 1.0, I.ft, nullptr, I.gst, I.hst, nullptr, nullptr};
   }
@@ -266,6 +302,16 @@ __global__ void k_b_init_duals(const BI *bi, const BCtl *ctl) {
 }
 
 // ------------------------------------------------------------------ evaluation phase
+// start of the restoration phase (instances that entered it in the line search): reference
+// point, D_R^2, p and q in closed form, multipliers (resto_start_at); before k_b_lambda, since
+// the constraint multipliers restart from zero
+__global__ void k_b_resto_start(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_EVAL);
+  if (ctl[b].resto != 2) return;
+  const RArgs A = rargs_b(I, ctl[b]);
+  for (int i = gtid; i < resto_nmax(I); i += gstride)
+    resto_start_at(A, ctl[b].mu, I.rxr, I.rdr2, i);
+}
 // multipliers of the model rows and their scaled copy (the weights of the constraint Hessians
 // in W); they depend only on the iterate, so W is evaluated together with J at x
 __global__ void k_b_lambda(const BI *bi, const BCtl *ctl) {
@@ -301,8 +347,85 @@ __global__ void k_b_jtu(const BI *bi, const BCtl *ctl) {
 // which order like the numbers and keep a NaN as the largest), the barrier logs in a LogSum
 // (their total goes to R_LOG_S): both keep FP64 instructions for the sums.
 __device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+// the same parts for the restoration problem (its variables x, p, q; p, q >= 0 count among the
+// lower bounds): x-gradient zeta D_R^2 (x - x_R) + J^T lambda - zl + zu, the p and q
+// stationarity rows with z - v, the rows c - p + q (primal error and theta_R), products of p, q
+// with their duals among the lower-bound products, the logs of s, p, q and the bound distances,
+// and the restoration objective into R_RS_OBJ
+__device__ void b_errors_resto(const BI &I, const BCtl &c, int gtid, int gstride) {
+  const RArgs A = rargs_b(I, c);
+  const Dims &D = I.D;
+  const int R = D.me + D.mi;
+  long long gl = 0, zv = 0, ge = 0, c0 = 0;
+  const long long inf = dbits(INFINITY);
+  long long svmin = inf, svmax = 0, clmin = inf, clmax = 0, cumin = inf, cumax = 0;
+  double sy = 0, sz = 0, svv = 0, szl = 0, szu = 0, th = 0, ls = 0, obj = 0;
+  auto cl = [&](double prod) {
+    const long long q = dbits(prod);
+    clmin = min(clmin, q);
+    clmax = max(clmax, q);
+  };
+  for (int i = gtid; i < resto_nmax(I); i += gstride) {
+    if (i < D.n) {
+      const double x = I.P.x[i], e = x - I.rxr[i];
+      gl = max(gl, dbits(fabs(c.zeta * I.rdr2[i] * e + I.P.jtl[i] - I.P.zl[i] + I.P.zu[i])));
+      szl += fabs(I.P.zl[i]);
+      szu += fabs(I.P.zu[i]);
+      obj += 0.5 * c.zeta * I.rdr2[i] * e * e;
+      if (isfinite(I.P.xl[i])) {
+        cl((x - I.P.xl[i]) * I.P.zl[i]);
+        ls += log(x - I.P.xl[i]);
+      }
+      if (isfinite(I.P.xu[i])) {
+        const long long q = dbits((I.P.xu[i] - x) * I.P.zu[i]);
+        cumin = min(cumin, q);
+        cumax = max(cumax, q);
+        ls += log(I.P.xu[i] - x);
+      }
+    }
+    if (i < D.mi) {
+      zv = max(zv, dbits(fabs(I.P.z[i] - I.P.v[i])));
+      const long long q = dbits(I.P.s[i] * I.P.v[i]);
+      svmin = min(svmin, q);
+      svmax = max(svmax, q);
+      sz += fabs(I.P.z[i]);
+      svv += fabs(I.P.v[i]);
+      ls += log(I.P.s[i]);
+    }
+    if (i < D.me) sy += fabs(I.P.y[i]);
+    if (i < R) {
+      const double lam = r_lam(A, i), p = I.rp[i], q = I.rq[i];
+      zv = max(zv, dbits(fabs(RHO_RESTO - lam - I.rzp[i])));
+      zv = max(zv, dbits(fabs(RHO_RESTO + lam - I.rzq[i])));
+      const double ci = r_c(D, I.P.geq, I.P.hin, I.P.s, i), r = fabs(ci - p + q);
+      c0 = max(c0, dbits(fabs(ci)));
+      ge = max(ge, dbits(r));
+      th += r;
+      szl += fabs(I.rzp[i]) + fabs(I.rzq[i]);
+      cl(p * I.rzp[i]);
+      cl(q * I.rzq[i]);
+      obj += RHO_RESTO * (p + q);
+      ls += log(p) + log(q);
+    }
+  }
+  // (R_RS_PRIM: the original problem's violation ||c||_inf)
+  const int slot[20] = {R_MAX_GL, R_MAX_ZV, R_MAX_G, R_MAX_HS, R_SUM_Y, R_SUM_Z, R_SUM_V,
+                        R_SUM_ZL, R_SUM_ZU, R_SV_MIN, R_SV_MAX, R_CL_MIN, R_CL_MAX, R_CU_MIN,
+                        R_CU_MAX, R_TH_G, R_TH_H, R_LOG_S, R_RS_OBJ, R_RS_PRIM};
+  const int op[20] = {OP_MAX, OP_MAX, OP_MAX, OP_MAX, OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM,
+                      OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_MIN, OP_MAX, OP_SUM, OP_SUM, OP_SUM,
+                      OP_SUM, OP_MAX};
+  auto d = [](long long x) { return __longlong_as_double(x); };
+  double v[20] = {d(gl), d(zv), d(ge), 0.0, sy, sz, svv, szl, szu, d(svmin), d(svmax),
+                  d(clmin), d(clmax), d(cumin), d(cumax), th, 0.0, ls, obj, d(c0)};
+  block_reduce_atomic<20>(I.R, slot, op, v);
+}
 __global__ void k_b_errors(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_EVAL);
+  if (ctl[b].resto) {
+    b_errors_resto(I, ctl[b], gtid, gstride);
+    return;
+  }
   const Dims &D = I.D;
   const double sig = ctl[b].sig;
   long long gl = 0, zv = 0, ge = 0, hs = 0;
@@ -363,30 +486,38 @@ __global__ void k_b_ctl_eval(const BI *bi, BCtl *ctl, int count, double tol, int
   const BI &I = bi[b];
   BCtl c = ctl[b];
   const double *h = I.R;
-  c.obj = *I.f;
+  const bool rs = c.resto != 0;
+  // the restoration problem has 2 (m_e + m_i) more lower bounds (p, q >= 0)
+  const int nl = rs ? I.nl + 2 * (I.D.me + I.D.mi) : I.nl;
+  c.obj = rs ? h[R_RS_OBJ] : *I.f;
   c.theta = h[R_TH_G] + h[R_TH_H];
   c.logsum = h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU];
-  const double e0 = kkt_error(h, I.D, I.nl, I.nu, fmax(h[R_SV_MAX], fmax(h[R_CL_MAX], h[R_CU_MAX])));
+  const double e0 = kkt_error(h, I.D, nl, I.nu, fmax(h[R_SV_MAX], fmax(h[R_CL_MAX], h[R_CU_MAX])));
   c.e0 = e0;
+  if (c.resto == 2) c.resto = 1;
   if (!c.have_theta0) {
     c.theta_max = 1e4 * fmax(1.0, c.theta);
     c.theta_min = 1e-4 * fmax(1.0, c.theta);
     c.have_theta0 = 1;
   }
   if (e0 <= tol) {
-    c.status = 1;
+    // a stationary point of the restoration problem before its return test passed: a local
+    // minimizer of the constraint violation, unless that violation is within the tolerance (a
+    // feasible point that the filter still rejects)
+    c.status = !rs ? 1 : h[R_RS_PRIM] > tol ? IPM_ERR_INFEASIBLE : IPM_ERR_RESTORATION;
     c.ph = PH_DONE;
   } else if (!isfinite(e0)) {
     c.status = IPM_ERR_NONFINITE;
     c.ph = PH_DONE;
-  } else if (c.k >= max_iter) {
-    c.status = IPM_ERR_MAXITER;
+  } else if (rs ? c.k_r >= 500 : c.k >= max_iter) {
+    c.status = rs ? IPM_ERR_RESTORATION : IPM_ERR_MAXITER;
     c.ph = PH_DONE;
   } else {
     bool first = true;
+    const int kk = rs ? c.k_r : c.k;
     for (int rep = 0; rep < 200; ++rep) {
-      const double emu = kkt_error(h, I.D, I.nl, I.nu, comp_mu(h, c.mu));
-      if (!(emu <= KAPPA_EPS * c.mu && (first || c.k == 0))) break;
+      const double emu = kkt_error(h, I.D, nl, I.nu, comp_mu(h, c.mu));
+      if (!(emu <= KAPPA_EPS * c.mu && (first || kk == 0))) break;
       c.mu = fmax(tol / 10.0, fmin(KAPPA_MU * c.mu, pow(c.mu, THETA_MU)));
       c.tau = fmax(TAU_MIN, 1.0 - c.mu);
       c.nfilter = 0;
@@ -401,6 +532,14 @@ __global__ void k_b_ctl_eval(const BI *bi, BCtl *ctl, int count, double tol, int
 __global__ void k_b_newton_rhs(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_BUILD);
   const Dims &D = I.D;
+  if (ctl[b].resto) {
+    const RArgs A = rargs_b(I, ctl[b]);
+    for (int i = gtid; i < resto_nmax(I); i += gstride) {
+      resto_rhs_at(A, i);
+      if (i < D.n) I.a[i] = -I.r1[i];
+    }
+    return;
+  }
   const int nmax = max(D.n, D.mi);
   for (int i = gtid; i < nmax; i += gstride) {
     newton_rhs_at(D, I.P, ctl[b].sig, ctl[b].mu, (double *)I.SA.sigma, I.r1, (double *)I.SA.r2,
@@ -424,6 +563,11 @@ __global__ void k_b_ctl_build(BCtl *ctl, int count) {
 __global__ void k_b_aug_rhs(const BI *bi, const BCtl *ctl, double gamma) {
   B_PROLOGUE(PH_FACT);
   const int nrow = max(I.D.me0, I.D.mi0);
+  if (ctl[b].resto) {  // every row condensed, d = 1/E_r (resto_row)
+    const RArgs A = rargs_b(I, ctl[b]);
+    for (int k = gtid; k < nrow; k += gstride) resto_aug_at(A, I.dcond, I.baug, k);
+    return;
+  }
   for (int k = gtid; k < nrow; k += gstride)
     aug_rhs_at(I.D, ctl[b].dw, gamma, I.SA.r2, I.SA.r4, I.SA.Ds, I.P.geq, I.dcond, I.baug, k);
 }
@@ -1038,7 +1182,7 @@ __global__ void k_b_ctl_fact(const BI *bi, BCtl *ctl, int count) {
   ++c.total_fac;
   if (*I.info == INT_MAX) {
     if (c.dw > 0) c.delta_last = c.dw;
-    if (c.cg_maxit > 0) {  // HyKKT
+    if (c.cg_maxit > 0 && !c.resto) {  // HyKKT (the restoration problem: condensed solve)
       I.R[R_CG_A] = 0.0;
       c.ph = PH_CGI;
     } else {
@@ -1146,7 +1290,7 @@ __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine,
   stop = eta <= 1e-10 || c.ref_it >= max_refine || (c.ref_it > 0 && eta > 0.5 * c.eta_prev);
   ++c.ref_it;
   if (stop) {
-    c.ph = c.k == *pause_k ? PH_PAUSE : PH_STEP;
+    c.ph = !c.resto && c.k == *pause_k ? PH_PAUSE : PH_STEP;
     return;
   }
   c.eta_prev = eta;
@@ -1175,6 +1319,11 @@ __global__ void k_b_jv(const BI *bi, const BCtl *ctl) {
 }
 __global__ void k_b_recover(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_STEP);
+  if (ctl[b].resto) {
+    const RArgs A = rargs_b(I, ctl[b]);
+    for (int i = gtid; i < resto_nmax(I); i += gstride) resto_recover_at(A, i);
+    return;
+  }
   StepArgs A = I.SA;
   A.mu = ctl[b].mu;
   A.dw = ctl[b].dw;
@@ -1187,13 +1336,24 @@ __global__ void k_b_ftb(const BI *bi, const BCtl *ctl) {
   A.mu = ctl[b].mu;
   A.dw = ctl[b].dw;
   double ap = 1.0, az = 1.0, gx = 0.0, gs = 0.0;
-  const int nmax = max(I.D.n, I.D.mi);
-  for (int i = gtid; i < nmax; i += gstride) {
-    const FtbParts F = ftb_at(A, ctl[b].tau, ctl[b].sig, i);
-    ap = fmin(ap, F.ap);
-    az = fmin(az, F.az);
-    gx += F.gx;
-    gs += F.gs;
+  if (ctl[b].resto) {
+    const RArgs R = rargs_b(I, ctl[b]);
+    for (int i = gtid; i < resto_nmax(I); i += gstride) {
+      double pa, za, g;
+      resto_ftb_at(R, ctl[b].tau, &pa, &za, &g, i);
+      ap = fmin(ap, pa);
+      az = fmin(az, za);
+      gx += g;
+    }
+  } else {
+    const int nmax = max(I.D.n, I.D.mi);
+    for (int i = gtid; i < nmax; i += gstride) {
+      const FtbParts F = ftb_at(A, ctl[b].tau, ctl[b].sig, i);
+      ap = fmin(ap, F.ap);
+      az = fmin(az, F.az);
+      gx += F.gx;
+      gs += F.gs;
+    }
   }
   const int slot[4] = {R_AMAX, R_AZ, R_GPHI_X, R_GPHI_S};
   const int op[4] = {OP_MIN, OP_MIN, OP_SUM, OP_SUM};
@@ -1208,7 +1368,7 @@ __global__ void k_b_ctl_ls0(const BI *bi, BCtl *ctl, int count) {
   c.amax = h[R_AMAX];
   c.az = h[R_AZ];
   c.gphi = h[R_GPHI_X] + h[R_GPHI_S];
-  c.phi = c.sig * c.obj - c.mu * c.logsum;
+  c.phi = (c.resto ? 1.0 : c.sig) * c.obj - c.mu * c.logsum;
   const double theta = c.theta, gphi = c.gphi;
   if (gphi < 0)
     c.amin = GAMMA_ALPHA * fmin(GAMMA_THETA, fmin(GAMMA_PHI * theta / -gphi,
@@ -1223,12 +1383,51 @@ __global__ void k_b_ctl_ls0(const BI *bi, BCtl *ctl, int count) {
 // ------------------------------------------------------------------ line search
 __global__ void k_b_trial(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_LS);
+  const double a = ctl[b].alpha;
+  if (ctl[b].resto) {
+    const int R = I.D.me + I.D.mi;
+    for (int i = gtid; i < resto_nmax(I); i += gstride) {
+      trial_at(I.D.n, I.D.mi, a, I.P.x, I.dx, I.P.s, I.SA.ds, I.xt, I.st, i);
+      if (i < R) {
+        I.rpt[i] = I.rp[i] + a * I.rdp[i];
+        I.rqt[i] = I.rq[i] + a * I.rdq[i];
+      }
+    }
+    return;
+  }
   const int nmax = max(I.D.n, I.D.mi);
   for (int i = gtid; i < nmax; i += gstride)
-    trial_at(I.D.n, I.D.mi, ctl[b].alpha, I.P.x, I.dx, I.P.s, I.SA.ds, I.xt, I.st, i);
+    trial_at(I.D.n, I.D.mi, a, I.P.x, I.dx, I.P.s, I.SA.ds, I.xt, I.st, i);
+}
+// restoration trial: theta_R, its objective and logs (resto_merit_at), and the original
+// problem's theta and barrier logs at the trial point for the return test
+__device__ void b_merit_trial_resto(const BI &I, const BCtl &c, int gtid, int gstride) {
+  const RArgs A = rargs_b(I, c);
+  const Dims &D = I.D;
+  double th = 0, obj = 0, ls = 0, th0 = 0, ls0 = 0;
+  for (int i = gtid; i < resto_nmax(I); i += gstride) {
+    const RMerit M = resto_merit_at(A, I.xt, I.st, I.rpt, I.rqt, I.geqt, I.hint, i);
+    th += M.th;
+    obj += M.obj;
+    ls += M.ls + M.lxl + M.lxu;
+    if (i < D.me) th0 += fabs(I.geqt[i]);
+    if (i < D.mi) {
+      th0 += fabs(I.hint[i] + I.st[i]);
+      ls0 += log(I.st[i]);
+    }
+    ls0 += M.lxl + M.lxu;
+  }
+  const int slot[5] = {R_TH_G, R_RS_OBJ, R_LOG_S, R_RS_TH0, R_RS_LOG0};
+  const int op[5] = {OP_SUM, OP_SUM, OP_SUM, OP_SUM, OP_SUM};
+  double v[5] = {th, obj, ls, th0, ls0};
+  block_reduce_atomic<5>(I.R, slot, op, v);
 }
 __global__ void k_b_merit_trial(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_LS);
+  if (ctl[b].resto) {
+    b_merit_trial_resto(I, ctl[b], gtid, gstride);
+    return;
+  }
   const Dims &D = I.D;
   double tg = 0, th = 0;
   LogSum lg;  // the barrier logs (total into R_LOG_S)
@@ -1251,35 +1450,85 @@ __global__ void k_b_merit_trial(const BI *bi, const BCtl *ctl) {
 }
 // filter acceptance (Ipopt: switching condition with the Armijo test on phi, else sufficient
 // decrease in theta or phi against the filter); backtrack by halves down to alpha_min
-__global__ void k_b_ctl_ls(const BI *bi, BCtl *ctl, int count) {
+// resto_on: a failed line search of the main problem enters the restoration phase
+// (Waechter & Biegler 2006, Sec. 3.3) at the current point, whose filter entry the phase must
+// beat; mu_R = max(mu, ||c||_inf) with ||c||_inf the primal error of this iteration's evaluation
+__global__ void k_b_ctl_ls(const BI *bi, BCtl *ctl, int count, int resto_on, double tol) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count || ctl[b].ph != PH_LS) return;
   const BI &I = bi[b];
   BCtl &c = ctl[b];
   const double *h = I.R;
+  const bool rs = c.resto != 0;
   const double tht = h[R_TH_G] + h[R_TH_H];
-  const double pht = c.sig * (*I.ft) - c.mu * (h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU]);
+  const double logs = h[R_LOG_S] + h[R_LOG_XL] + h[R_LOG_XU];
+  const double pht = rs ? h[R_RS_OBJ] - c.mu * logs : c.sig * (*I.ft) - c.mu * logs;
   const double theta = c.theta, phi = c.phi, gphi = c.gphi, alpha = c.alpha;
   int ftype = 0;
-  const bool accepted = filter_accept(theta, phi, gphi, alpha, tht, pht, I.filter, c.nfilter,
-                                      c.theta_min, c.theta_max, &ftype);
+  const bool accepted = filter_accept(theta, phi, gphi, alpha, tht, pht, rs ? I.rfilter : I.filter,
+                                      c.nfilter, c.theta_min, c.theta_max, &ftype);
   if (accepted) {
     c.ftype = ftype;
     c.ph = PH_ACC;
+    if (rs) {
+      // return test: the original violation at most KAPPA_RESTO times the phase's start, and
+      // the point acceptable to the original filter with the start's entry
+      const double th0 = h[R_RS_TH0], ph0 = c.sig * (*I.ft) - c.mu_m * h[R_RS_LOG0];
+      bool back = th0 <= KAPPA_RESTO * c.theta_start && th0 < c.theta_max_m &&
+                  (th0 < c.entry_theta || ph0 < c.entry_phi);
+      for (int q = 0; back && q < c.nfilter_m; ++q)
+        if (!(th0 < I.filter[2 * q] || ph0 < I.filter[2 * q + 1])) back = false;
+      c.ret = back;
+    }
     return;
   }
   ++c.ls;
   ++c.total_ls;
   c.alpha = alpha * 0.5;
   if (c.alpha < c.amin) {
-    c.status = IPM_ERR_RESTORATION;
-    c.ph = PH_DONE;
+    // (no phase at a point already feasible within the tolerance: it cannot reduce a violation
+    // at rounding level)
+    if (rs || !resto_on || fmax(h[R_MAX_G], h[R_MAX_HS]) <= tol) {
+      c.status = IPM_ERR_RESTORATION;
+      c.ph = PH_DONE;
+      return;
+    }
+    c.mu_m = c.mu;
+    c.tau_m = c.tau;
+    c.delta_last_m = c.delta_last;
+    c.theta_max_m = c.theta_max;
+    c.theta_min_m = c.theta_min;
+    c.nfilter_m = c.nfilter;
+    c.entry_theta = (1 - GAMMA_THETA) * theta;
+    c.entry_phi = phi - GAMMA_PHI * theta;
+    c.theta_start = theta;
+    c.mu = fmax(c.mu, fmax(h[R_MAX_G], h[R_MAX_HS]));
+    c.zeta = sqrt(c.mu);
+    c.tau = fmax(TAU_MIN, 1.0 - c.mu);
+    c.delta_last = 0.0;
+    c.nfilter = 0;
+    c.have_theta0 = 0;
+    c.k_r = 0;
+    c.ret = 0;
+    c.resto = 2;
+    ++c.n_resto;
+    ++c.k;
+    c.ph = PH_EVAL;
   }
 }
 
 // ------------------------------------------------------------------ accept
 __global__ void k_b_accept(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_ACC);
+  if (ctl[b].resto) {
+    const RArgs R = rargs_b(I, ctl[b]);
+    const bool back = ctl[b].ret != 0;
+    for (int i = gtid; i < resto_nmax(I); i += gstride) {
+      resto_accept_at(R, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.rpt, I.rqt, i);
+      if (back) resto_finish_at(I.D, I.P, i);
+    }
+    return;
+  }
   StepArgs A = I.SA;
   A.mu = ctl[b].mu;
   A.dw = ctl[b].dw;
@@ -1287,27 +1536,48 @@ __global__ void k_b_accept(const BI *bi, const BCtl *ctl) {
   for (int i = gtid; i < nmax; i += gstride)
     accept_at(A, ctl[b].alpha, ctl[b].az, I.xt, I.st, I.dystep, i);
 }
+// adds (theta_f, phi_f) to a filter of n entries; when full, merges it into the entry that is
+// dominated the most (largest theta), which keeps a valid (conservative) filter
+__device__ void filter_add(double *F, int &n, int cap, double theta_f, double phi_f) {
+  if (n < cap) {
+    F[2 * n] = theta_f;
+    F[2 * n + 1] = phi_f;
+    ++n;
+  } else {
+    int q = 0;
+    for (int k = 1; k < n; ++k)
+      if (F[2 * k] > F[2 * q]) q = k;
+    F[2 * q] = fmin(F[2 * q], theta_f);
+    F[2 * q + 1] = fmin(F[2 * q + 1], phi_f);
+  }
+}
 __global__ void k_b_ctl_acc(const BI *bi, BCtl *ctl, int count, int fmax_entries) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count || ctl[b].ph != PH_ACC) return;
   BCtl &c = ctl[b];
-  if (!c.ftype) {
-    double *F = bi[b].filter;
-    if (c.nfilter < fmax_entries) {
-      F[2 * c.nfilter] = (1 - GAMMA_THETA) * c.theta;
-      F[2 * c.nfilter + 1] = c.phi - GAMMA_PHI * c.theta;
-      ++c.nfilter;
-    } else {
-      // full: replace the entry that is dominated the most (largest theta), keeping a valid
-      // (conservative) filter
-      int q = 0;
-      for (int k = 1; k < c.nfilter; ++k)
-        if (F[2 * k] > F[2 * q]) q = k;
-      F[2 * q] = fmin(F[2 * q], (1 - GAMMA_THETA) * c.theta);
-      F[2 * q + 1] = fmin(F[2 * q + 1], c.phi - GAMMA_PHI * c.theta);
+  const bool rs = c.resto != 0;
+  if (!c.ftype)
+    filter_add(rs ? bi[b].rfilter : bi[b].filter, c.nfilter, fmax_entries,
+               (1 - GAMMA_THETA) * c.theta, c.phi - GAMMA_PHI * c.theta);
+  if (rs) {
+    ++c.k_r;
+    ++c.total_resto;
+    if (c.ret) {
+      // back to the main problem, whose filter takes the phase's starting entry
+      c.mu = c.mu_m;
+      c.tau = c.tau_m;
+      c.delta_last = c.delta_last_m;
+      c.theta_max = c.theta_max_m;
+      c.theta_min = c.theta_min_m;
+      c.nfilter = c.nfilter_m;
+      c.have_theta0 = 1;
+      filter_add(bi[b].filter, c.nfilter, fmax_entries, c.entry_theta, c.entry_phi);
+      c.resto = 0;
+      c.ret = 0;
     }
+  } else {
+    ++c.k;
   }
-  ++c.k;
   c.ph = PH_EVAL;
 }
 
@@ -1573,7 +1843,12 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     L(2);
     return IPM_OK;
   };
+  const bool resto_on = !B->opt.no_resto;
   // evaluate f, grad f, g, h, J and W at x, optimality error, convergence, barrier update
+  if (resto_on) {
+    k_b_resto_start<<<g2, blk, 0, s>>>(bi, ctl);
+    L(1);
+  }
   k_b_lambda<<<g2, blk, 0, s>>>(bi, ctl);
   L(1);
   eval(PH_EVAL, 1);
@@ -1628,8 +1903,10 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_cgx_dz<<<g2, blk, 0, s>>>(bi, ctl);
     k_b_ctl_cgx<<<gc, 128, 0, s>>>(ctl, C, B->d_tickets + 12);
     L(2);
-  } else {
-    // condensed solve, then Richardson refinement on the augmented system
+  }
+  if (B->opt.kkt != 1 || resto_on) {
+    // condensed solve, then Richardson refinement on the augmented system (HyKKT: the
+    // restoration problem's steps, whose rows are all condensed)
     CKR(solve(PH_SOLVE));
     k_b_ctl_solved<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(1);
@@ -1660,8 +1937,9 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_scale_model<<<g2, blk, 0, s>>>(bi, ctl, PH_LS, 2, relax);
     L(1);
     rreset(PH_LS, R_TH_G, R_LOG_XU + 1, 0.0);
+    if (resto_on) rreset(PH_LS, R_RS_OBJ, R_COUNT, 0.0);
     k_b_merit_trial<<<g2, blk, 0, s>>>(bi, ctl);
-    k_b_ctl_ls<<<gc, 128, 0, s>>>(bi, ctl, C);
+    k_b_ctl_ls<<<gc, 128, 0, s>>>(bi, ctl, C, (int)resto_on, tol);
     L(2);
   }
   k_b_accept<<<g2, blk, 0, s>>>(bi, ctl);
@@ -1806,6 +2084,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     size_t xt, st, geqt, hint, gst, hst, ft, R, filter, tJ, Lx, Dx, y_s, t, cx, cz, outx, outz,
         scal;
     size_t cg_r, cg_p, cg_sp, cg_dy, cg_rhs1, cg_v;
+    size_t rp, rq, rzp, rzq, rdp, rdq, rdzp, rdzq, rpt, rqt, rrc, rrp, rrq, rxr, rdr2, rfilter;
     size_t info;
   };
   std::vector<Off> off(count);
@@ -1839,6 +2118,13 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     const size_t ncg = B->opt.kkt == 1 ? n : 0, mcg = B->opt.kkt == 1 ? me0 : 0;
     o.cg_r = dp.take(mcg); o.cg_p = dp.take(mcg); o.cg_sp = dp.take(mcg); o.cg_dy = dp.take(mcg);
     o.cg_rhs1 = dp.take(ncg); o.cg_v = dp.take(ncg);
+    // restoration phase: per IPM row, x_R and D_R^2, the phase's filter
+    const size_t nr = B->opt.no_resto ? 0 : me + mi, nx = B->opt.no_resto ? 0 : n;
+    o.rp = dp.take(nr); o.rq = dp.take(nr); o.rzp = dp.take(nr); o.rzq = dp.take(nr);
+    o.rdp = dp.take(nr); o.rdq = dp.take(nr); o.rdzp = dp.take(nr); o.rdzq = dp.take(nr);
+    o.rpt = dp.take(nr); o.rqt = dp.take(nr); o.rrc = dp.take(nr); o.rrp = dp.take(nr);
+    o.rrq = dp.take(nr); o.rxr = dp.take(nx); o.rdr2 = dp.take(nx);
+    o.rfilter = dp.take(B->opt.no_resto ? 0 : 2 * (size_t)B->fmax_entries);
     o.info = ip.take(1);
     max_elems = std::max({max_elems, M.n, (int)mi, (int)m, M.nnzJ, M.nnzW, 2 * M.nbr});
     B->max_ns = std::max(B->max_ns, S->nsuper);
@@ -2059,6 +2345,12 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.cg_r = d + o.cg_r; I.cg_p = d + o.cg_p; I.cg_sp = d + o.cg_sp; I.cg_dy = d + o.cg_dy;
     I.cg_rhs1 = d + o.cg_rhs1; I.cg_v = d + o.cg_v;
     I.dystep = B->opt.kkt == 1 ? I.cg_dy : I.dzc;
+    if (!B->opt.no_resto) {
+      I.rp = d + o.rp; I.rq = d + o.rq; I.rzp = d + o.rzp; I.rzq = d + o.rzq; I.rdp = d + o.rdp;
+      I.rdq = d + o.rdq; I.rdzp = d + o.rdzp; I.rdzq = d + o.rdzq; I.rpt = d + o.rpt;
+      I.rqt = d + o.rqt; I.rrc = d + o.rrc; I.rrp = d + o.rrp; I.rrq = d + o.rrq;
+      I.rxr = d + o.rxr; I.rdr2 = d + o.rdr2; I.rfilter = d + o.rfilter;
+    }
     AugArgs &A = I.aug;
     A.n = M.n; A.m = I.m; A.m_e = 0;
     A.J_rowptr = S->J_rowptr; A.J_colind = S->J_colind; A.J_rowidx = S->J_rowidx;
@@ -2286,6 +2578,17 @@ extern "C" int ipm_batch_cg_iters(ipm_batch_t B, int *cg_iters) {
   std::vector<BCtl> h(B->count);
   CK(cudaMemcpy(h.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost));
   for (int i = 0; i < B->count; ++i) cg_iters[i] = h[i].cg_total;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_resto_counts(ipm_batch_t B, int *phases, int *iters) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  std::vector<BCtl> h(B->count);
+  CK(cudaMemcpy(h.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < B->count; ++i) {
+    if (phases) phases[i] = h[i].n_resto;
+    if (iters) iters[i] = h[i].total_resto;
+  }
   return IPM_OK;
 }
 

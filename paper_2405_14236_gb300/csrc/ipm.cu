@@ -257,7 +257,10 @@ __global__ void k_resto_merit(RArgs A, const double *xt, const double *st, const
   red_sum(R, R_LOG_XU, M.lxu);
 }
 __global__ void k_resto_errors(RArgs A, double mu, double *R) {
-  const RErr E = resto_errors_at(A, mu, blockIdx.x * blockDim.x + threadIdx.x);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const RErr E = resto_errors_at(A, mu, i);
+  // the original problem's violation ||c||_inf
+  red_max(R, R_MAX_G, i < A.D.me + A.D.mi ? fabs(r_c(A.D, A.P.geq, A.P.hin, A.P.s, i)) : 0.0);
   red_max(R, R_RS_DUAL, E.dual);
   red_max(R, R_RS_PRIM, E.prim);
   red_max(R, R_RS_COMP, E.comp);
@@ -268,19 +271,8 @@ __global__ void k_resto_accept(RArgs A, double alpha, double az, const double *x
                                const double *st, const double *pt, const double *qt) {
   resto_accept_at(A, alpha, az, xt, st, pt, qt, blockIdx.x * blockDim.x + threadIdx.x);
 }
-// back to the main problem: constraint multipliers from zero, large bound multipliers reset
-// to one (as Ipopt does after its restoration phase)
 __global__ void k_resto_finish(Dims D, It P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D.n) {
-    if (P.zl[i] > 1e3) P.zl[i] = 1.0;
-    if (P.zu[i] > 1e3) P.zu[i] = 1.0;
-  }
-  if (i < D.mi) {
-    P.z[i] = 0.0;
-    if (P.v[i] > 1e3) P.v[i] = 1.0;
-  }
-  if (i < D.me) P.y[i] = 0.0;
+  resto_finish_at(D, P, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 }  // namespace cipm
@@ -312,12 +304,15 @@ struct ipm_state_s {
   int status = 0;  // 0 running, 1 converged, <0/IPM_ERR_* failure
   int nl = 0, nu = 0;
   bool have_kkt = false;  // a KKT solve has completed (ipm_state_export_kkt)
+  bool kkt_resto = false;  // ... and it was a step of the restoration problem (all rows condensed)
   double last_dw = 0.0;
   // restoration phase: per IPM row p, q, their duals, steps and trial values; reference point
   double *rp = nullptr, *rq = nullptr, *rzp = nullptr, *rzq = nullptr, *rdp = nullptr,
          *rdq = nullptr, *rdzp = nullptr, *rdzq = nullptr, *rpt = nullptr, *rqt = nullptr;
   double *rxr = nullptr, *rdr2 = nullptr, *rrc = nullptr, *rrp = nullptr, *rrq = nullptr;
   bool in_resto = false, have_theta0_r = false;
+  double prim_inf = INFINITY;  // ||c||_inf of the last main evaluation
+  double rs_cinf = INFINITY;   // the same at the last restoration evaluation
   double mu_r = 0, zeta_r = 0, tau_r = 0, theta_start = 0, theta_max_r = 0, theta_min_r = 0;
   double delta_last_r = 0, entry_theta = 0, entry_phi = 0;
   std::vector<double> filter_r;
@@ -388,6 +383,7 @@ static int errors(ipm_state_t S, double mu, double *out) {
   CKR(read_R(S));
   const double *h = S->hR;
   *out = kkt_error(h, S->D, S->nl, S->nu, std::max({h[R_MAX_SV], h[R_MAX_XL], h[R_MAX_XU]}));
+  S->prim_inf = std::max(h[R_MAX_G], h[R_MAX_HS]);
   return IPM_OK;
 }
 
@@ -587,11 +583,12 @@ static int resto_merit(ipm_state_t S, const double *xt, const double *st, const 
 // scaled optimality error of the restoration problem (Ipopt's E_mu with its s_d, s_c; the bounds
 // p, q >= 0 count among the bounds)
 static int resto_errors(ipm_state_t S, double mu, double *out) {
-  CKR(reduce_reset(S, {R_RS_DUAL, R_RS_PRIM, R_RS_COMP, R_RS_SUMD, R_RS_SUMC}, 0.0));
+  CKR(reduce_reset(S, {R_RS_DUAL, R_RS_PRIM, R_RS_COMP, R_RS_SUMD, R_RS_SUMC, R_MAX_G}, 0.0));
   k_resto_errors<<<grid1(nmax_r(S)), 256, 0, S->stream>>>(rargs(S, 0.0), mu, S->R);
   CKL();
   CKR(read_R(S));
   const double *h = S->hR;
+  S->rs_cinf = h[R_MAX_G];
   const int R = S->D.me + S->D.mi, nb = S->nl + S->nu + 2 * R;
   const double sd = std::max(S_MAX, h[R_RS_SUMD] / std::max(S->D.me + 2 * S->D.mi + nb, 1)) / S_MAX;
   const double sc = std::max(S_MAX, h[R_RS_SUMC] / std::max(S->D.mi + nb, 1)) / S_MAX;
@@ -644,8 +641,9 @@ static int resto_step(ipm_state_t S, ipm_iter_info *info) {
   }
   info->kkt_err = e0;
   // a stationary point of the restoration problem reached before the return test passed: a
-  // local minimizer of the constraint violation
-  if (e0 <= S->opt.tol) return IPM_ERR_INFEASIBLE;
+  // local minimizer of the constraint violation, unless that violation is within the tolerance
+  // (a feasible point that the filter still rejects)
+  if (e0 <= S->opt.tol) return S->rs_cinf > S->opt.tol ? IPM_ERR_INFEASIBLE : IPM_ERR_RESTORATION;
   bool first = true;
   while (true) {
     double emu;
@@ -695,6 +693,9 @@ static int resto_step(ipm_state_t S, ipm_iter_info *info) {
     break;
   }
   if (!ok) return IPM_ERR_INERTIA;
+  S->have_kkt = true;
+  S->kkt_resto = true;
+  S->last_dw = dw;
   if (dw > 0) S->delta_last_r = dw;
   info->delta_w = dw;
   info->n_factor = nfac;
@@ -904,6 +905,7 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   }
   if (!ok) return IPM_ERR_INERTIA;
   S->have_kkt = true;
+  S->kkt_resto = false;
   S->last_dw = dw;
   if (dw > 0) S->delta_last = dw;
   info->delta_w = dw;
@@ -967,6 +969,9 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   info->alpha = alpha;
   info->theta = theta;
   if (!accepted) {
+    // no restoration phase at a point already feasible within the tolerance: it cannot reduce
+    // a violation at rounding level (the method stops there)
+    if (S->opt.no_resto || S->prim_inf <= S->opt.tol) return IPM_ERR_RESTORATION;
     // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the following calls iterate
     // on the restoration problem until its return test passes
     CKR(resto_begin(S, theta, phi));
@@ -1041,13 +1046,14 @@ extern "C" int ipm_state_export_kkt(ipm_state_t S, double *W_val, double *sigma,
   CKR(get(a, S->a, n));
   CKR(get(b, S->baug, m));
   CKR(get(dx, S->dx, n));
-  if (S->opt.kkt == 1) {
+  const bool kept_eq = S->opt.kkt == 1 && !S->kkt_resto;
+  if (kept_eq) {
     CKR(get(dyz, S->dy, me0));
     CKR(get(dyz ? dyz + me0 : nullptr, S->dzH, mi0));
   } else {
     CKR(get(dyz, S->dzc, m));
   }
   if (delta_w) *delta_w = S->last_dw;
-  if (m_e) *m_e = S->opt.kkt == 1 ? me0 : 0;
+  if (m_e) *m_e = kept_eq ? me0 : 0;
   return IPM_OK;
 }

@@ -58,6 +58,8 @@ enum {
   // restoration phase (single-problem IPM): objective part of phi_R, maxima of the dual,
   // primal and complementarity residuals, sums of all multipliers and of the bound-type ones
   R_RS_OBJ, R_RS_DUAL, R_RS_PRIM, R_RS_COMP, R_RS_SUMD, R_RS_SUMC,
+  // restoration trial points (batched IPM): theta and barrier logs of the original problem
+  R_RS_TH0, R_RS_LOG0,
   R_COUNT
 };
 

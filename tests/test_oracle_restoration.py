@@ -120,3 +120,50 @@ def test_restoration_recovers_from_a_bad_start(kkt):
     assert res.status == "converged"
     assert sum(1 for h in res.history if h.get("resto_status") == "ok") >= 1
     assert abs(res.obj - ref.obj) <= 1e-6 * abs(ref.obj)
+
+
+def _late_iterate(g, kkt, k):
+    """The oracle IPM's iterate after k iterations from the regular start (the model as solve
+    builds it)."""
+    base = OPFModel(g)
+    opt = ipm.Options(kkt=kkt)
+    model = ipm.ScaledModel(base, ipm._push(base.x0(), base.xl, base.xu))
+    if kkt == "lifted":
+        model = ipm.RelaxedModel(model, opt.tol)
+    hl, hu = np.isfinite(model.xl), np.isfinite(model.xu)
+    x = ipm._push(model.x0(), model.xl, model.xu)
+    sig_f = min(1.0, 100.0 / max(np.abs(model.grad(x)).max(), 1e-300))
+    gx, hx = model.cons(x)
+    start = dict(x=x, s=np.maximum(-hx, ipm.KAPPA1), y=np.zeros(model.m_e), z=np.ones(model.m_i),
+                 v=np.ones(model.m_i), zl=np.where(hl, 1.0, 0.0), zu=np.where(hu, 1.0, 0.0))
+    r = ipm._ipm(model, opt, start, opt.mu0, sig_f, max_iter=k)
+    return model, opt, r
+
+
+def test_restoration_at_a_feasible_point_is_not_infeasibility():
+    """Called at a late iterate of a feasible problem (violation at rounding level), the
+    restoration problem is solved by the point itself; that is no evidence of infeasibility (a
+    local minimizer of the violation with a positive violation), so the phase reports failure."""
+    g = config_grid("ring30")
+    model, opt, r = _late_iterate(g, "lifted", 30)
+    gx, hx = model.cons(r.x)
+    assert max(np.abs(gx).max(initial=0), np.abs(hx + r.s).max()) <= opt.tol
+    theta_at = lambda xx, sx: float(np.abs(model.cons(xx)[0]).sum()
+                                    + np.abs(model.cons(xx)[1] + sx).sum())
+    phi_at = lambda xx, sx: float(model.objective(xx))
+    rec = ipm._restoration(model, opt, r.x, r.s, r.v, r.zl, r.zu, r.mu, theta_at(r.x, r.s), 1e4,
+                           [], theta_at, phi_at)
+    assert rec["status"] == "restoration_failed"
+
+
+@pytest.mark.parametrize("kkt", ["lifted", "hykkt"])
+def test_overloaded_grid_is_locally_infeasible(kkt):
+    """Total load three times the nominal one exceeds the generators' capacity (twice the nominal
+    load): no point satisfies the power balances, and the restoration phase ends at a minimizer
+    of the violation whose violation stays well above the tolerance."""
+    import dataclasses
+    g = config_grid("ring30")
+    assert 3 * g.pd.sum() > g.pmax.sum()
+    g3 = dataclasses.replace(g, pd=3 * g.pd, qd=3 * g.qd)
+    res = ipm.solve(OPFModel(g3), ipm.Options(kkt=kkt))
+    assert res.status == "infeasible"
