@@ -78,6 +78,8 @@ struct BI {
   // numeric
   const int *sptr, *srow_ptr, *slot_ptr, *perm, *J_rowidx, *JT_ptr, *JT_ent;
   const int *srow, *snode, *level_sn, *lvl_ptr;  // lvl_ptr: level offsets into level_sn
+  // supernodes of width B_WT < w <= B_WG of each level (level L owns g8_ptr[L] .. g8_ptr[L + 1])
+  const int *g8_ptr, *g8_sn;
   // update pairs (precomputed per pattern), stored level by level: level L owns entries
   // lpair_ptr[L] .. lpair_ptr[L + 1]; each pair: the panel slots of rows i and j (i >= j >= w)
   // in column 0 of its supernode, ld << 8 | w of that panel, and the target value slot
@@ -721,6 +723,61 @@ __device__ void thread_diag_sn(const BI &I, int s) {
     if (k < w) Dd[w * w + k] = inv[k];
 }
 
+static constexpr int B_WG = 8;  // diagonal blocks up to this width: one 8-lane group each
+
+// diagonal block of a supernode of width B_WT < w <= B_WG by one group of 8 lanes (four
+// supernodes per warp, s < 0: an idle group): lane i of the group holds row i of the block, and
+// at step k every lane computes pivot k of its group (an FP64 warp instruction costs the same
+// for 8 or 32 active lanes, so the four chains of pivots run in one instruction stream).  Writes
+// L11 and the reciprocal pivots to Dd as thread_diag_sn does.
+__device__ void group_diag_sn(const BI &I, int s, int lane) {
+  const int i = lane & 7, base = lane & ~7;
+  int f = 0, w = 0, ld = 1;
+  const double *P = nullptr;
+  if (s >= 0) {
+    f = I.sptr[s];
+    w = I.sptr[s + 1] - f;
+    ld = I.srow_ptr[s + 1] - I.srow_ptr[s];
+    P = I.Lx + I.lptr[s];
+  }
+  double x[B_WG];
+#pragma unroll
+  for (int j = 0; j < B_WG; ++j) x[j] = (i < w && j <= i) ? P[i + (int64_t)j * ld] : 0.0;
+  double inv = 1.0;  // lane k keeps the reciprocal of pivot k
+#pragma unroll
+  for (int k = 0; k < B_WG; ++k) {
+    double d = __shfl_sync(0xffffffffu, x[k], base + k);
+    if (k < w) {
+      if (!pivot_ok(d)) {
+        if (i == k) atomicMin(I.info, f + k);
+        d = 1.0;
+      }
+    } else {
+      d = 1.0;
+    }
+    const double iv = rsqrt_newton(d);
+    if (i == k) {
+      x[k] = d * iv;
+      inv = iv;
+    } else if (i > k) {
+      x[k] *= iv;
+    }
+    // trailing rows: x[j] -= L_ik L_jk for k < j <= i
+#pragma unroll
+    for (int j = k + 1; j < B_WG; ++j) {
+      const double ljk = __shfl_sync(0xffffffffu, x[k], base + j);
+      if (j <= i) x[j] -= x[k] * ljk;
+    }
+  }
+  if (i < w) {
+    double *Dd = I.Dx + I.dptr[s];
+#pragma unroll
+    for (int j = 0; j < B_WG; ++j)
+      if (j < w) Dd[i + j * w] = j <= i ? x[j] : 0.0;
+    Dd[w * w + i] = inv;
+  }
+}
+
 // warp path: diagonal block, reciprocal pivots, L21 = A21 L11^{-T}, then the outer product of the
 // rows below scattered into the target panels.  D: w*w doubles, inv: w doubles (this warp's).
 __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
@@ -729,7 +786,7 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   double *P = I.Lx + I.lptr[s];
   double *Dd = I.Dx + I.dptr[s];
-  if (w <= B_WT) {  // factored by thread_diag_sn before this pass
+  if (w <= B_WG) {  // factored by thread_diag_sn or group_diag_sn before this pass
     for (int t = lane; t < w * w; t += 32) D[t] = Dd[t];
     for (int k = lane; k < w; k += 32) inv[k] = Dd[w * w + k];
     __syncwarp();
@@ -786,18 +843,29 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
   __syncwarp();
 }
 
-// block path for a wide supernode (every thread of the block calls); sm: w*w + 32*(w+1) doubles
-__device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
+// barrier of the bd threads of warp group `id` (named barrier 1 + id; bd a multiple of 32)
+__device__ __forceinline__ void group_bar(int id, int bd) {
+  switch (id) {  // constant barrier ids, so that the kernel reserves five barriers only
+    case 0: asm volatile("bar.sync 1, %0;" ::"r"(bd) : "memory"); break;
+    case 1: asm volatile("bar.sync 2, %0;" ::"r"(bd) : "memory"); break;
+    case 2: asm volatile("bar.sync 3, %0;" ::"r"(bd) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"r"(bd) : "memory"); break;
+  }
+}
+
+// group path for a wide supernode: the bd threads (tid = 0 .. bd - 1) of warp group gid call;
+// sm: w*w + 32*(w+1) doubles of this group, s_inv: w doubles of this group
+__device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv, int tid, int bd,
+                                int gid) {
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   double *P = I.Lx + I.lptr[s];
   double *sL = sm, *sR = sm + w * w;
-  const int tid = threadIdx.x, bd = blockDim.x;
   for (int t = tid; t < w * w; t += bd) {
     const int k = t / w, i = t - k * w;
     sL[t] = i >= k ? P[i + (int64_t)k * ld] : 0.0;
   }
-  __syncthreads();
+  group_bar(gid, bd);
   for (int k = 0; k < w; ++k) {
     if (tid == 0) {
       double d = sL[k + k * w];
@@ -809,17 +877,17 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
       sL[k + k * w] = d * iv;
       s_inv[k] = iv;
     }
-    __syncthreads();
+    group_bar(gid, bd);
     const double iv = s_inv[k];
     const int nr = w - k - 1;
     for (int i = k + 1 + tid; i < w; i += bd) sL[i + k * w] *= iv;
-    __syncthreads();
+    group_bar(gid, bd);
     for (int jj = tid / 32; jj < nr; jj += bd / 32) {
       const int j = k + 1 + jj;
       const double ljk = sL[j + k * w];
       for (int i = j + (tid & 31); i < w; i += 32) sL[i + j * w] -= sL[i + k * w] * ljk;
     }
-    __syncthreads();
+    group_bar(gid, bd);
   }
   double *Dd = I.Dx + I.dptr[s];
   for (int t = tid; t < w * w; t += bd) Dd[t] = sL[t];
@@ -829,12 +897,12 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
   const int warp = tid >> 5, lane = tid & 31, nw = bd >> 5;
   for (int r0 = w; r0 < ld; r0 += 32) {
     const int nrow = min(32, ld - r0);
-    __syncthreads();
+    group_bar(gid, bd);
     for (int t = tid; t < nrow * w; t += bd) {
       const int k = t / nrow, r = t - k * nrow;
       sR[r * sw + k] = P[(r0 + r) + (int64_t)k * ld];
     }
-    __syncthreads();
+    group_bar(gid, bd);
     for (int k = 0; k < w; ++k) {
       const double iv = s_inv[k];
       for (int r = warp; r < nrow; r += nw) {
@@ -845,13 +913,13 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
         __syncwarp();
       }
     }
-    __syncthreads();
+    group_bar(gid, bd);
     for (int t = tid; t < nrow * w; t += bd) {
       const int k = t / nrow, r = t - k * nrow;
       P[(r0 + r) + (int64_t)k * ld] = sR[r * sw + k];
     }
   }
-  __syncthreads();
+  group_bar(gid, bd);
 }
 
 // factorization of each instance in the FACT phase (panels condensed by k_b_condense): one
@@ -862,10 +930,9 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv) {
 static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
 
 __global__ void __launch_bounds__(B_NT_F, 3)
-    k_b_fact_inst(const BI *bi, const BCtl *ctl, const int *order) {
+    k_b_fact_inst(const BI *bi, const BCtl *ctl, int smem_doubles, const int *order) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double *sm = reinterpret_cast<double *>(sm_raw);
-  __shared__ double s_inv[CIPM_SN_MAXW];
   __shared__ int s_wide[B_WIDE_CAP], s_nwide;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -883,6 +950,13 @@ __global__ void __launch_bounds__(B_NT_F, 3)
       const int s = I.level_sn[q];
       if (I.sptr[s + 1] - I.sptr[s] <= B_WT) thread_diag_sn(I, s);
     }
+    {  // widths B_WT+1 .. B_WG: four supernodes per warp
+      const int g0 = I.g8_ptr[L], g1 = I.g8_ptr[L + 1];
+      for (int q = g0 + 4 * gw; q < g1; q += 4 * gnw) {
+        const int qq = q + (lane >> 3);
+        group_diag_sn(I, qq < g1 ? I.g8_sn[qq] : -1, lane);
+      }
+    }
     cluster.sync();  // warps of any block of the cluster read these pivots
     for (int q = q0 + gw; q < q1; q += gnw) {
       const int s = I.level_sn[q];
@@ -893,7 +967,21 @@ __global__ void __launch_bounds__(B_NT_F, 3)
       }
     }
     __syncthreads();
-    for (int k = 0; k < s_nwide; ++k) block_factor_sn(I, s_wide[k], sm, s_inv);
+    if (s_nwide > 0) {
+      // the wide supernodes of the level by G warp groups side by side (each with its own
+      // shared-memory area), G as large as the level's count, the block's warps and the
+      // dynamic shared memory allow
+      int mw = 0;
+      for (int k = 0; k < s_nwide; ++k) mw = max(mw, I.sptr[s_wide[k] + 1] - I.sptr[s_wide[k]]);
+      const int need = mw * mw + 32 * (mw + 1) + mw;
+      int G = s_nwide >= 3 ? 4 : s_nwide;
+      while (G > 1 && G * need > smem_doubles) G >>= 1;
+      const int bd = blockDim.x / G, gid = threadIdx.x / bd, gtid = threadIdx.x - gid * bd;
+      double *gsm = sm + gid * need;
+      for (int k = gid; k < s_nwide; k += G)
+        block_factor_sn(I, s_wide[k], gsm, gsm + need - mw, gtid, bd, gid);
+      __syncthreads();
+    }
     cluster.sync();
     level_updates(I, L, crank * blockDim.x + threadIdx.x, ncl * blockDim.x);
     cluster.sync();
@@ -1870,7 +1958,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     CKR(rec(r == 0 ? 0 : 4));
     k_b_condense<<<dim3(B->gx_cond, C), blk, 0, s>>>(bi, ctl);
     L(1);
-    CKR(split(k_b_fact_inst, B_NT_F, B->fact_smem));
+    CKR(split(k_b_fact_inst, B_NT_F, B->fact_smem, (int)(B->fact_smem / sizeof(double))));
     CKR(rec(r == 0 ? 1 : 5));
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(3);
@@ -2172,7 +2260,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   // update pairs of every pattern: for each supernode, the pairs (i, j) of its rows below the
   // diagonal block and the slot of the target panel that entry (i, j) of L21 L21^T updates
   std::vector<int *> pptr(B->syms.size()), pa(B->syms.size()), pb(B->syms.size()),
-      pm(B->syms.size()), ptgt(B->syms.size());
+      pm(B->syms.size()), ptgt(B->syms.size()), g8p(B->syms.size()), g8s(B->syms.size());
   std::vector<int *> cslot(B->syms.size()), ccol(B->syms.size()), cgp(B->syms.size());
   std::vector<int2 *> citm(B->syms.size());
   std::vector<int> ncslot(B->syms.size());
@@ -2193,12 +2281,13 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     std::vector<int> lsn(ns);
     if (ns && cudaMemcpy(lsn.data(), S->level_sn, sizeof(int) * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(IPM_ERR_CUDA);
-    std::vector<int> hp(S->nlevels + 1, 0), ha, hb, hm, htg;
+    std::vector<int> hp(S->nlevels + 1, 0), ha, hb, hm, htg, hg8p(S->nlevels + 1, 0), hg8s;
     for (int L = 0; L < S->nlevels; ++L) {
       for (int qq = S->h_level_ptr[L]; qq < S->h_level_ptr[L + 1]; ++qq) {
         const int sn_ = lsn[qq];
         const int w = sp[sn_ + 1] - sp[sn_], rb = rp[sn_], ld = rp[sn_ + 1] - rb;
         if (ld >= (1 << 23) || w > 255) return fail(IPM_ERR_BAD_ARG);
+        if (w > B_WT && w <= B_WG) hg8s.push_back(sn_);
         for (int j = w; j < ld; ++j) {
           const int col = rows[rb + j], ts = sn[col];
           const int tb = rp[ts], tld = rp[ts + 1] - tb;
@@ -2213,6 +2302,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
         }
       }
       hp[L + 1] = (int)ha.size();
+      hg8p[L + 1] = (int)hg8s.size();
     }
     auto upi = [&](int **dst, const std::vector<int> &v) -> int {
       if (cudaMalloc((void **)dst, sizeof(int) * std::max<size_t>(v.size(), 1)) != cudaSuccess)
@@ -2274,6 +2364,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     if (r1 == IPM_OK) r1 = upi(&pb[q], hb);
     if (r1 == IPM_OK) r1 = upi(&pm[q], hm);
     if (r1 == IPM_OK) r1 = upi(&ptgt[q], htg);
+    if (r1 == IPM_OK) r1 = upi(&g8p[q], hg8p);
+    if (r1 == IPM_OK) r1 = upi(&g8s[q], hg8s);
     if (r1 == IPM_OK) r1 = upi(&cslot[q], hcs);
     if (r1 == IPM_OK) r1 = upi(&ccol[q], hcc);
     if (r1 == IPM_OK) r1 = upi(&cgp[q], hgp);
@@ -2335,6 +2427,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.pair_b = pb[B->pat[i]];
     I.pair_m = pm[B->pat[i]];
     I.pair_tgt = ptgt[B->pat[i]];
+    I.g8_ptr = g8p[B->pat[i]];
+    I.g8_sn = g8s[B->pat[i]];
     I.cslot = cslot[B->pat[i]];
     I.ccol = ccol[B->pat[i]];
     I.cgptr = cgp[B->pat[i]];
@@ -2391,9 +2485,12 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   if (rc != IPM_OK) return fail(rc);
   int max_w = 1;
   for (ipm_sym_t S : B->syms) max_w = std::max(max_w, S->max_w);
+  // the warps' staging of the narrow supernodes, one wide supernode of the widest pattern, or up
+  // to four wide supernodes of 24 columns side by side (k_b_fact_inst)
+  const size_t need24 = 24 * 24 + 32 * 25 + 24;
   B->fact_smem = sizeof(double) *
-                 std::max((size_t)max_w * max_w + (size_t)32 * (max_w + 1),
-                          (size_t)(B_NT_F / 32) * (B_WS * B_WS + B_WS));
+                 std::max({(size_t)max_w * max_w + (size_t)32 * (max_w + 1) + max_w,
+                           (size_t)(B_NT_F / 32) * (B_WS * B_WS + B_WS), 4 * need24});
   // the solves keep the right-hand side in shared memory for instances with n <= 3,800 (with
   // the 43 KB of per-warp staging, three blocks of the solve kernel per SM still fit); larger
   // instances use global memory
