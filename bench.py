@@ -447,18 +447,29 @@ def aggregate_ranks(t_ms, converged, world, device):
     return float(t.item()), float(c.item())
 
 
-def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3):
+def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3, precision=64, relax=(0, 0)):
     """The headline's instances solved by another batched form: "regularized" (the
     dual-regularized condensed form: equality rows kept, delta_c = 1/gamma) or "hykkt" (CG on
-    the Schur complement of K_gamma, Section 3.1)."""
+    the Schur complement of K_gamma, Section 3.1); or, with precision 32, LiftedKKT with the FP32
+    factor and FP64 refinement (launch shapes autotuned for it, per-sweep kernel times, the share
+    of iterations the FP32 factor served)."""
     import torch
     import paper_2405_14236_gb300 as cp
     opfs = [cp.Opf(g) for g in grids]
-    B = cp.Batch(opfs, kkt=kkt, gamma=gamma)
+    B = cp.Batch(opfs, kkt=kkt, gamma=gamma, precision=precision, relax=relax)
+    shape = None
+    if precision == 32:
+        tune = B.autotune(sweeps=8)
+        best = tune["candidates"][tune["best"]]
+        shape = {k: best[k] for k in ("cluster", "threshold", "blocks_per_instance")}
+        B.set_timing(True)
     B.run(max_iter=MAX_ITER)
+    B.kernel_time()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms, conv, its = [], [], []
+    fact_ms = solve_ms = 0.0
+    n_sw = it32 = it_all = n64 = 0
     for _ in range(steps):
         torch.cuda.synchronize()
         e0.record(stream)
@@ -470,9 +481,26 @@ def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3):
         r = B.results()
         conv.append(int((r["status"] == 1).sum()))
         its.append(float(r["iters"].mean()))
+        if precision == 32:
+            kt = B.kernel_time()
+            fact_ms += kt["fact_ms"]
+            solve_ms += kt["solve_ms"]
+            n_sw += kt["sweeps"]
+            pr = B.solve_info()
+            it32 += int(pr["iters32"].sum())
+            it_all += int(r["iters"].sum())
+            n64 += int((pr["k64"] >= 0).sum())
     out = {"kkt": kkt, "gamma": gamma, "value": float(np.sum(conv) / (np.sum(ms) / 1e3)),
            "unit": UNIT, "converged_per_step": conv, "iters_mean": float(np.mean(its)),
            "ms_per_step": float(np.mean(ms)), "sweeps": int(r["sweeps"])}
+    if precision == 32:
+        out.update({"precision": "FP32 condensed matrix, factor and triangular solves; FP64 "
+                                 "Richardson refinement on the augmented system to 1e-10",
+                    "launch_shape": shape,
+                    "kernels_ms_per_sweep": {"factor_both_rounds": fact_ms / max(n_sw, 1),
+                                             "solve_first": solve_ms / max(n_sw, 1)},
+                    "fp32_share_of_iterations": it32 / max(it_all, 1),
+                    "instances_gone_fp64_per_step": n64 / steps})
     if kkt == "hykkt":
         out["cg_iters_per_ipm_iter"] = float(r["cg_iters"].sum() / max(1, r["iters"].sum()))
     return out
@@ -560,6 +588,7 @@ def run_gpu(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, conv, iters_mean, iters_max, sweeps = [], [], [], [], []
     stopped, resto_phases, resto_iters = {}, [], []
+    ks = {"solves": 0, "above": 0, "eta_max": 0.0}
     fact_ms = solve_ms = 0.0
     n_sw = 0
     nfac = 0
@@ -586,6 +615,10 @@ def run_gpu(args, rank, world, local_rank):
         conv.append(int((r["status"] == 1).sum()))
         for code in r["status"][r["status"] != 1]:
             stopped[int(code)] = stopped.get(int(code), 0) + 1
+        si = B.solve_info()
+        for k in ("solves", "above"):
+            ks[k] += int(si[k].sum())
+        ks["eta_max"] = max(ks["eta_max"], float(si["eta_max"].max()))
         resto_phases.append(int(r["resto_phases"].sum()))
         resto_iters.append(int(r["resto_iters"].sum()))
         iters_mean.append(float(r["iters"].mean()))
@@ -672,6 +705,12 @@ def run_gpu(args, rank, world, local_rank):
         # restoration phases entered and their iterations, per step
         "stopped_status_counts": {str(k): v for k, v in sorted(stopped.items())},
         "restoration": {"phases_per_step": resto_phases, "iters_per_step": resto_iters},
+        # every KKT solve of the timed steps by the library's own backward error of the augmented
+        # system: how many ended above 1e-10 after the refinement (the ill-conditioning of K_tau,
+        # Sec. 3.2, in the middle iterations of LiftedKKT)
+        "kkt_solves": {"per_step": ks["solves"] / args.steps,
+                       "above_1e-10_share": ks["above"] / max(ks["solves"], 1),
+                       "eta_max": ks["eta_max"]},
         "launches_per_sweep": B.info()["launches_per_sweep"], "init_s": init_s,
         "launch_shape": shape, "autotune_s": autotune_s, "supernode_shape": sn_tune,
         "roofline": {"kernel": "k_b_fact_inst (condensation + factorization, every instance)",
@@ -696,6 +735,8 @@ def run_gpu(args, rank, world, local_rank):
         line["plain"] = plain_measure([grids[i // 2] if i % 2 == 0 or ns == len(grids)
                                        else grids[ns + i // 2] for i in range(4)])
         line["plain"]["batched_speedup"] = value / line["plain"]["value"]
+    if not args.no_fp32:
+        line["batch_fp32"] = batch_form_measure(grids, kkt="lifted", precision=32, relax=relax)
     if not args.no_forms:
         line["batch_regularized"] = batch_form_measure(grids)
         line["batch_hykkt"] = batch_form_measure(grids, kkt="hykkt")

@@ -400,7 +400,14 @@ typedef struct ipm_batch_s *ipm_batch_t;
 /* Creates the batch over count model handles (HOST array of handles that must outlive the batch;
  * the same handle may not appear twice).  opt: kkt 0 (LiftedKKT), 1 (HyKKT: CG on the Schur
  * complement of K_gamma, cg_rtol and cg_maxit as in ipm_options, gamma > 0) or 2 (dual-regularized
- * form, gamma > 0), precision 0 or 64; the remaining fields as in ipm_options.  Runs one
+ * form, gamma > 0); precision 0 or 64 (FP64 factor), or 32 with kkt 0 or 2: every instance
+ * starts with an FP32 condensed matrix (summed in FP64, rounded once), an FP32 factorization and
+ * FP32 triangular solves inside FP64 Richardson refinement on the augmented system (the
+ * precision form; the rounding errors of the condensed system are those Section 4 analyses), and
+ * goes to an FP64 factor at the same delta_w for the rest of its solve when an FP32
+ * factorization breaks down or the refinement stalls above a backward error of 1e-10 (so each
+ * accepted solve still meets 1e-10; the inertia of an FP32-factored step is decided in FP32);
+ * the remaining fields as in ipm_options.  Runs one
  * ipm_symbolic per distinct pattern, allocates one
  * device pool for every instance's iterate, factor and workspace, and sets every instance to the
  * starting point of ipm_state_create.  Synchronizes.  IPM_ERR_BAD_ARG on a bad argument,
@@ -443,6 +450,14 @@ int ipm_batch_cg_iters(ipm_batch_t batch, int *cg_iters);
 /* Feasibility restoration per instance since creation or the last reset, into HOST arrays
  * [count] (either may be NULL): phases entered and restoration iterations made.  Synchronizes. */
 int ipm_batch_resto_counts(ipm_batch_t batch, int *phases, int *iters);
+/* KKT solves per instance since creation or the last reset, into HOST arrays [count] (any may
+ * be NULL): the factor precision the instance uses now (32 or 64), the IPM iterations whose KKT
+ * solve used the FP32 factor, the iteration at which it went to FP64 (-1: it did not); the KKT
+ * solves finished, how many of them ended with a normwise backward error of the augmented system
+ * (computed on the device, as ipm_aug_solve does) above 1e-10 after the refinement, and the
+ * largest such error.  Synchronizes. */
+int ipm_batch_solve_info(ipm_batch_t batch, int *current, int *iters32, int *k64, int *solves,
+                         int *above, double *eta_max);
 /* Copies instance i's x [n] into a HOST buffer.  Synchronizes. */
 int ipm_batch_export(ipm_batch_t batch, int i, double *x);
 /* Sweeps run since creation or the last reset. */

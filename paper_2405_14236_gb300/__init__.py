@@ -66,6 +66,7 @@ _SIGS = {
     "ipm_batch_results": (I, [P, P, P, P, P, P, P]),
     "ipm_batch_cg_iters": (I, [P, P]),
     "ipm_batch_resto_counts": (I, [P, P, P]),
+    "ipm_batch_solve_info": (I, [P, P, P, P, P, P, P]),
     "ipm_batch_autotune": (I, [P, I, I, P, P, P, P]),
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
@@ -433,15 +434,18 @@ def ipm_solve_opf(opf, max_iter=3000, **opts):
 class Batch:
     """Batched interior-point solves over ``Opf`` handles (ipm_batch_*): one symbolic analysis
     per distinct pattern, every instance advanced by the same launches.  kkt: "lifted",
-    "hykkt" (CG on the Schur complement of K_gamma) or "regularized"."""
+    "hykkt" (CG on the Schur complement of K_gamma) or "regularized".  precision 32 (lifted or
+    regularized): FP32 factor and triangular solves inside FP64 refinement, each instance going
+    to FP64 when its FP32 solve cannot reach a backward error of 1e-10."""
 
     def __init__(self, opfs, tol=1e-6, tau=0.0, mu0=0.1, max_refine=10, kkt="lifted", gamma=1e6,
-                 cg_rtol=1e-10, cg_maxit=0, stream=None, relax=(0, 0), restoration=True):
+                 cg_rtol=1e-10, cg_maxit=0, stream=None, relax=(0, 0), restoration=True,
+                 precision=64):
         self.opfs = list(opfs)
         arr = (ctypes.c_void_p * len(self.opfs))(*[o.h.value for o in self.opfs])
         o = IpmOptions({"lifted": 0, "hykkt": 1, "regularized": 2}[kkt], tol, gamma, tau, mu0,
-                       cg_rtol, max_refine, cg_maxit, 64, int(relax[0]), int(relax[1]),
-                       int(not restoration))
+                       cg_rtol, max_refine, cg_maxit, int(precision), int(relax[0]),
+                       int(relax[1]), int(not restoration))
         h = ctypes.c_void_p()
         _check(lib().ipm_batch_create(len(self.opfs), arr, ctypes.byref(o), _stream(stream),
                                       ctypes.byref(h)), "ipm_batch_create")
@@ -476,6 +480,19 @@ class Batch:
         return dict(status=st, iters=it, obj=obj, kkt_err=err, n_factor=nf, ls_steps=ls,
                     cg_iters=cg, resto_phases=rph, resto_iters=rit,
                     sweeps=lib().ipm_batch_sweeps(self.h))
+
+    def solve_info(self):
+        """Per instance (ipm_batch_solve_info): the factor precision used now (32 or 64), the
+        iterations whose KKT solve used the FP32 factor, the iteration at which it went to FP64
+        (-1: never), KKT solves finished, those above a backward error of 1e-10 and the
+        largest final backward error."""
+        n = self.count
+        cur, it32, k64, ns, na = (np.zeros(n, np.int32) for _ in range(5))
+        em = np.zeros(n)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().ipm_batch_solve_info(self.h, p(cur), p(it32), p(k64), p(ns), p(na), p(em)),
+               "ipm_batch_solve_info")
+        return dict(current=cur, iters32=it32, k64=k64, solves=ns, above=na, eta_max=em)
 
     def autotune(self, sweeps=8):
         """Times the candidate launch shapes (ipm_batch_autotune) and keeps the fastest; every

@@ -42,6 +42,9 @@ enum Phase {
 };
 
 static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2, B_CG_ROUNDS = 6;
+// refinement steps allowed with the FP32 factor (at a contraction rate of 1/2 per step the
+// error falls by 2^-30 ~ 1e-9; a slower rate stops at the stall test first)
+static constexpr int B_REFINE32 = 30;
 static constexpr int B_BLOCK = 256;
 
 // per-instance control record (device)
@@ -53,7 +56,14 @@ struct BCtl {
   double alpha, az, amax, amin, gphi, theta, phi, logsum, obj, e0, eta, eta_prev, normA;
   // HyKKT CG: r.r, stopping threshold, step scalars, iterations (this IPM step, in total)
   double cg_rr, cg_stop, cg_alpha, cg_beta;
-  int cg_it, cg_total, cg_maxit, pad_;
+  int cg_it, cg_total, cg_maxit;
+  // precision: p32 = 1 while the FP32 factor serves (cleared for good when an FP32
+  // factorization breaks down or its refinement does not reach 1e-10); it32: iterations whose
+  // KKT solve used it; k32: the iteration at which the instance went to FP64 (-1: never)
+  int p32, it32, k32;
+  // KKT solves finished, those left above a backward error of 1e-10, the largest final error
+  int n_solve, n_above;
+  double eta_worst;
   // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): resto 0 = main problem,
   // 2 = phase entered (its start is set at the next evaluation), 1 = in the phase; ret: the
   // accepted trial passed the return test.  While in the phase mu, tau, delta_last, theta_max,
@@ -144,8 +154,9 @@ __global__ void k_b_rreset(const BI *bi, const BCtl *ctl, int phase, int k0, int
 }
 
 // cg_maxit: HyKKT CG iteration limit (<= 0: m_e of the instance); 0 in the record = no CG
+// p32: start with the FP32 factor (precision 32)
 __global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0, int hykkt,
-                             int cg_maxit) {
+                             int cg_maxit, int p32) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count) return;
   BCtl c;
@@ -156,6 +167,8 @@ __global__ void k_b_ctl_init(const BI *bi, BCtl *ctl, int count, double mu0, int
   c.sig = 1.0;
   c.eta = c.eta_prev = INFINITY;
   if (hykkt) c.cg_maxit = cg_maxit > 0 ? cg_maxit : max(bi[b].D.me0, 1);
+  c.p32 = p32;
+  c.k32 = -1;
   ctl[b] = c;
   for (int k = 0; k < R_COUNT; ++k) bi[b].R[k] = 0.0;
 }
@@ -587,6 +600,7 @@ __global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_FACT);
   if (gtid == 0) *I.info = INT_MAX;
   const double dw = ctl[b].dw;
+  const int p32 = ctl[b].p32;
   for (int t = gtid; t < I.ncslot; t += gstride) {
     const int slot = I.cslot[t], j = I.ccol[t], g = t >> 5;
     double v = j >= 0 ? I.SA.sigma[j] + dw : 0.0;
@@ -613,7 +627,10 @@ __global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
       if (q.y == -2) a = m = 0.0;
       v = fma(a, m, v);
     }
-    I.Lx[slot] = v;
+    if (p32)
+      reinterpret_cast<float *>(I.Lx)[slot] = (float)v;  // summed in FP64, rounded once
+    else
+      I.Lx[slot] = v;
   }
 }
 
@@ -633,16 +650,17 @@ static constexpr int B_NT_F = 512;  // threads of the per-instance factorization
 // Updates of the supernodes of level L into their ancestors, every pair of the level spread over
 // all threads of the cluster: entry (i, j), i >= j >= w, of L21 L21^T of supernode s is
 // subtracted from the panel of the supernode owning column rows[j], at row rows[i].
-__device__ __forceinline__ void level_updates(const BI &I, int L, int tid, int nthreads) {
+template <typename T>
+__device__ __forceinline__ void level_updates(const BI &I, T *Lx, int L, int tid, int nthreads) {
   const int p1 = I.lpair_ptr[L + 1];
   for (int t = I.lpair_ptr[L] + tid; t < p1; t += nthreads) {
     const int m = I.pair_m[t];
     const int w = m & 0xff, ld = m >> 8;
-    const double *Pi = I.Lx + I.pair_a[t], *Pj = I.Lx + I.pair_b[t];
-    double v = 0.0;
+    const T *Pi = Lx + I.pair_a[t], *Pj = Lx + I.pair_b[t];
+    T v = 0;
     int k = 0;
     for (; k + 4 <= w; k += 4) {  // four independent load pairs in flight
-      double a[4], c[4];
+      T a[4], c[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = Pi[(int64_t)(k + u) * ld];
@@ -652,18 +670,17 @@ __device__ __forceinline__ void level_updates(const BI &I, int L, int tid, int n
       for (int u = 0; u < 4; ++u) v += a[u] * c[u];
     }
     for (; k < w; ++k) v += Pi[(int64_t)k * ld] * Pj[(int64_t)k * ld];
-    atomicAdd(&I.Lx[I.pair_tgt[t]], -v);
+    atomicAdd(&Lx[I.pair_tgt[t]], -v);
   }
 }
 
 // rows below the diagonal block of a narrow supernode of width W: L21 = A21 L11^{-T}, one row per
 // lane held in registers (one load and one store per entry; the right-looking column loop then
 // runs on registers instead of re-reading the panel)
-template <int W>
-__device__ __forceinline__ void rows_below(double *P, int ld, const double *D, const double *inv,
-                                           int lane) {
+template <int W, typename T>
+__device__ __forceinline__ void rows_below(T *P, int ld, const T *D, const T *inv, int lane) {
   for (int r = W + lane; r < ld; r += 32) {
-    double x[W];
+    T x[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) x[k] = P[r + (int64_t)k * ld];
 #pragma unroll
@@ -682,24 +699,25 @@ static constexpr int B_WT = 4;  // diagonal blocks up to this width are factored
 // diagonal block of a narrow supernode (w <= B_WT) by one thread: L11 and its reciprocal pivots
 // into Dd (the same arithmetic as the warp path); on GB300 an FP64 warp instruction costs the
 // same with one lane active as with 32, so the pivots of a level go 32 per instruction
-__device__ void thread_diag_sn(const BI &I, int s) {
+template <typename T>
+__device__ void thread_diag_sn(const BI &I, T *Lx, T *Dx, int s) {
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int ld = I.srow_ptr[s + 1] - I.srow_ptr[s];
-  const double *P = I.Lx + I.lptr[s];
-  double D[B_WT * B_WT], inv[B_WT];
+  const T *P = Lx + I.lptr[s];
+  T D[B_WT * B_WT], inv[B_WT];
 #pragma unroll
   for (int k = 0; k < B_WT; ++k)
 #pragma unroll
-    for (int i = 0; i < B_WT; ++i) D[i + k * B_WT] = (k < w && i < w && i >= k) ? P[i + (int64_t)k * ld] : 0.0;
+    for (int i = 0; i < B_WT; ++i) D[i + k * B_WT] = (k < w && i < w && i >= k) ? P[i + (int64_t)k * ld] : T(0);
 #pragma unroll
   for (int k = 0; k < B_WT; ++k) {
     if (k < w) {
-      double d = D[k + k * B_WT];
+      T d = D[k + k * B_WT];
       if (!pivot_ok(d)) {
         atomicMin(I.info, f + k);
-        d = 1.0;
+        d = 1;
       }
-      const double iv = rsqrt_newton(d);
+      const T iv = rsqrt_newton(d);
       D[k + k * B_WT] = d * iv;
       inv[k] = iv;
 #pragma unroll
@@ -712,7 +730,7 @@ __device__ void thread_diag_sn(const BI &I, int s) {
           if (i < w && j < w) D[i + j * B_WT] -= D[i + k * B_WT] * D[j + k * B_WT];
     }
   }
-  double *Dd = I.Dx + I.dptr[s];
+  T *Dd = Dx + I.dptr[s];
 #pragma unroll
   for (int k = 0; k < B_WT; ++k)
 #pragma unroll
@@ -730,32 +748,33 @@ static constexpr int B_WG = 8;  // diagonal blocks up to this width: one 8-lane 
 // at step k every lane computes pivot k of its group (an FP64 warp instruction costs the same
 // for 8 or 32 active lanes, so the four chains of pivots run in one instruction stream).  Writes
 // L11 and the reciprocal pivots to Dd as thread_diag_sn does.
-__device__ void group_diag_sn(const BI &I, int s, int lane) {
+template <typename T>
+__device__ void group_diag_sn(const BI &I, T *Lx, T *Dx, int s, int lane) {
   const int i = lane & 7, base = lane & ~7;
   int f = 0, w = 0, ld = 1;
-  const double *P = nullptr;
+  const T *P = nullptr;
   if (s >= 0) {
     f = I.sptr[s];
     w = I.sptr[s + 1] - f;
     ld = I.srow_ptr[s + 1] - I.srow_ptr[s];
-    P = I.Lx + I.lptr[s];
+    P = Lx + I.lptr[s];
   }
-  double x[B_WG];
+  T x[B_WG];
 #pragma unroll
-  for (int j = 0; j < B_WG; ++j) x[j] = (i < w && j <= i) ? P[i + (int64_t)j * ld] : 0.0;
-  double inv = 1.0;  // lane k keeps the reciprocal of pivot k
+  for (int j = 0; j < B_WG; ++j) x[j] = (i < w && j <= i) ? P[i + (int64_t)j * ld] : T(0);
+  T inv = 1;  // lane k keeps the reciprocal of pivot k
 #pragma unroll
   for (int k = 0; k < B_WG; ++k) {
-    double d = __shfl_sync(0xffffffffu, x[k], base + k);
+    T d = __shfl_sync(0xffffffffu, x[k], base + k);
     if (k < w) {
       if (!pivot_ok(d)) {
         if (i == k) atomicMin(I.info, f + k);
-        d = 1.0;
+        d = 1;
       }
     } else {
-      d = 1.0;
+      d = 1;
     }
-    const double iv = rsqrt_newton(d);
+    const T iv = rsqrt_newton(d);
     if (i == k) {
       x[k] = d * iv;
       inv = iv;
@@ -765,12 +784,12 @@ __device__ void group_diag_sn(const BI &I, int s, int lane) {
     // trailing rows: x[j] -= L_ik L_jk for k < j <= i
 #pragma unroll
     for (int j = k + 1; j < B_WG; ++j) {
-      const double ljk = __shfl_sync(0xffffffffu, x[k], base + j);
+      const T ljk = __shfl_sync(0xffffffffu, x[k], base + j);
       if (j <= i) x[j] -= x[k] * ljk;
     }
   }
   if (i < w) {
-    double *Dd = I.Dx + I.dptr[s];
+    T *Dd = Dx + I.dptr[s];
 #pragma unroll
     for (int j = 0; j < B_WG; ++j)
       if (j < w) Dd[i + j * w] = j <= i ? x[j] : 0.0;
@@ -780,12 +799,13 @@ __device__ void group_diag_sn(const BI &I, int s, int lane) {
 
 // warp path: diagonal block, reciprocal pivots, L21 = A21 L11^{-T}, then the outer product of the
 // rows below scattered into the target panels.  D: w*w doubles, inv: w doubles (this warp's).
-__device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
+template <typename T>
+__device__ void warp_factor_sn(const BI &I, T *Lx, T *Dx, int s, T *D, T *inv) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
-  double *P = I.Lx + I.lptr[s];
-  double *Dd = I.Dx + I.dptr[s];
+  T *P = Lx + I.lptr[s];
+  T *Dd = Dx + I.dptr[s];
   if (w <= B_WG) {  // factored by thread_diag_sn or group_diag_sn before this pass
     for (int t = lane; t < w * w; t += 32) D[t] = Dd[t];
     for (int k = lane; k < w; k += 32) inv[k] = Dd[w * w + k];
@@ -793,22 +813,22 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
   } else {
   for (int t = lane; t < w * w; t += 32) {
     const int k = t / w, i = t - k * w;
-    D[t] = i >= k ? P[i + (int64_t)k * ld] : 0.0;
+    D[t] = i >= k ? P[i + (int64_t)k * ld] : T(0);
   }
   __syncwarp();
   for (int k = 0; k < w; ++k) {
     if (lane == 0) {
-      double d = D[k + k * w];
+      T d = D[k + k * w];
       if (!pivot_ok(d)) {
         atomicMin(I.info, f + k);
-        d = 1.0;
+        d = 1;
       }
-      const double iv = rsqrt_newton(d);
+      const T iv = rsqrt_newton(d);
       D[k + k * w] = d * iv;
       inv[k] = iv;
     }
     __syncwarp();
-    const double iv = inv[k];
+    const T iv = inv[k];
     for (int i = k + 1 + lane; i < w; i += 32) D[i + k * w] *= iv;
     __syncwarp();
     const int nr = w - k - 1;
@@ -831,7 +851,7 @@ __device__ void warp_factor_sn(const BI &I, int s, double *D, double *inv) {
 #undef CIPM_RB_CASE
     default:  // 8 < w <= B_WS: the row in a thread-private array
       for (int r = w + lane; r < ld; r += 32) {
-        double x[B_WS];
+        T x[B_WS];
         for (int k = 0; k < w; ++k) x[k] = P[r + (int64_t)k * ld];
         for (int k = 0; k < w; ++k) {
           x[k] *= inv[k];
@@ -855,41 +875,42 @@ __device__ __forceinline__ void group_bar(int id, int bd) {
 
 // group path for a wide supernode: the bd threads (tid = 0 .. bd - 1) of warp group gid call;
 // sm: w*w + 32*(w+1) doubles of this group, s_inv: w doubles of this group
-__device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv, int tid, int bd,
-                                int gid) {
+template <typename T>
+__device__ void block_factor_sn(const BI &I, T *Lx, T *Dx, int s, T *sm, T *s_inv, int tid,
+                                int bd, int gid) {
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
-  double *P = I.Lx + I.lptr[s];
-  double *sL = sm, *sR = sm + w * w;
+  T *P = Lx + I.lptr[s];
+  T *sL = sm, *sR = sm + w * w;
   for (int t = tid; t < w * w; t += bd) {
     const int k = t / w, i = t - k * w;
-    sL[t] = i >= k ? P[i + (int64_t)k * ld] : 0.0;
+    sL[t] = i >= k ? P[i + (int64_t)k * ld] : T(0);
   }
   group_bar(gid, bd);
   for (int k = 0; k < w; ++k) {
     if (tid == 0) {
-      double d = sL[k + k * w];
+      T d = sL[k + k * w];
       if (!pivot_ok(d)) {
         atomicMin(I.info, f + k);
-        d = 1.0;
+        d = 1;
       }
-      const double iv = rsqrt_newton(d);
+      const T iv = rsqrt_newton(d);
       sL[k + k * w] = d * iv;
       s_inv[k] = iv;
     }
     group_bar(gid, bd);
-    const double iv = s_inv[k];
+    const T iv = s_inv[k];
     const int nr = w - k - 1;
     for (int i = k + 1 + tid; i < w; i += bd) sL[i + k * w] *= iv;
     group_bar(gid, bd);
     for (int jj = tid / 32; jj < nr; jj += bd / 32) {
       const int j = k + 1 + jj;
-      const double ljk = sL[j + k * w];
+      const T ljk = sL[j + k * w];
       for (int i = j + (tid & 31); i < w; i += 32) sL[i + j * w] -= sL[i + k * w] * ljk;
     }
     group_bar(gid, bd);
   }
-  double *Dd = I.Dx + I.dptr[s];
+  T *Dd = Dx + I.dptr[s];
   for (int t = tid; t < w * w; t += bd) Dd[t] = sL[t];
   for (int k = tid; k < w; k += bd) Dd[w * w + k] = s_inv[k];
   // rows below in blocks of 32: each warp owns rows, lanes split the columns
@@ -904,9 +925,9 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv, i
     }
     group_bar(gid, bd);
     for (int k = 0; k < w; ++k) {
-      const double iv = s_inv[k];
+      const T iv = s_inv[k];
       for (int r = warp; r < nrow; r += nw) {
-        const double xk = sR[r * sw + k] * iv;
+        const T xk = sR[r * sw + k] * iv;
         __syncwarp();
         for (int j = k + 1 + lane; j < w; j += 32) sR[r * sw + j] -= xk * sL[j + k * w];
         if (lane == 0) sR[r * sw + k] = xk;
@@ -922,46 +943,35 @@ __device__ void block_factor_sn(const BI &I, int s, double *sm, double *s_inv, i
   group_bar(gid, bd);
 }
 
-// factorization of each instance in the FACT phase (panels condensed by k_b_condense): one
-// block, or one thread-block cluster (big instances, launched with a cluster size), per
-// instance.  Warps of the whole cluster share the narrow supernodes of a level; each block
-// collects the wide ones its warps met and factors them with all its threads; a cluster barrier
-// (release / acquire) separates the levels.
-static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
-
-__global__ void __launch_bounds__(B_NT_F, 3)
-    k_b_fact_inst(const BI *bi, const BCtl *ctl, int smem_doubles, const int *order) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  double *sm = reinterpret_cast<double *>(sm_raw);
-  __shared__ int s_wide[B_WIDE_CAP], s_nwide;
+// Levels of one instance in precision T (the panels Lx and diagonal blocks Dx of a FP32 instance
+// hold floats at the same slot indices); sm: the dynamic shared memory, cap_t elements of T.
+template <typename T>
+__device__ __forceinline__ void fact_levels(const BI &I, T *Lx, T *Dx, T *sm, int cap_t,
+                                            int *s_wide, int &s_nwide, int crank, int ncl) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  const int crank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
-  const int b = order[blockIdx.x / ncl];
-  if (ctl[b].ph != PH_FACT) return;  // the same for every block of the cluster
-  const BI &I = bi[b];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int gw = crank * nw + warp, gnw = ncl * nw;
-  double *D = sm + warp * (B_WS * B_WS + B_WS), *inv = D + B_WS * B_WS;
+  T *D = sm + warp * (B_WS * B_WS + B_WS), *inv = D + B_WS * B_WS;
   for (int L = 0; L < I.nlevels; ++L) {
     if (threadIdx.x == 0) s_nwide = 0;
     const int q0 = I.lvl_ptr[L], q1 = I.lvl_ptr[L + 1];
     for (int q = q0 + crank * blockDim.x + threadIdx.x; q < q1; q += ncl * blockDim.x) {
       const int s = I.level_sn[q];
-      if (I.sptr[s + 1] - I.sptr[s] <= B_WT) thread_diag_sn(I, s);
+      if (I.sptr[s + 1] - I.sptr[s] <= B_WT) thread_diag_sn(I, Lx, Dx, s);
     }
     {  // widths B_WT+1 .. B_WG: four supernodes per warp
       const int g0 = I.g8_ptr[L], g1 = I.g8_ptr[L + 1];
       for (int q = g0 + 4 * gw; q < g1; q += 4 * gnw) {
         const int qq = q + (lane >> 3);
-        group_diag_sn(I, qq < g1 ? I.g8_sn[qq] : -1, lane);
+        group_diag_sn(I, Lx, Dx, qq < g1 ? I.g8_sn[qq] : -1, lane);
       }
     }
     cluster.sync();  // warps of any block of the cluster read these pivots
     for (int q = q0 + gw; q < q1; q += gnw) {
       const int s = I.level_sn[q];
       if (I.sptr[s + 1] - I.sptr[s] <= B_WS) {
-        warp_factor_sn(I, s, D, inv);
+        warp_factor_sn(I, Lx, Dx, s, D, inv);
       } else if (lane == 0) {
         s_wide[atomicAdd(&s_nwide, 1)] = s;
       }
@@ -975,24 +985,50 @@ __global__ void __launch_bounds__(B_NT_F, 3)
       for (int k = 0; k < s_nwide; ++k) mw = max(mw, I.sptr[s_wide[k] + 1] - I.sptr[s_wide[k]]);
       const int need = mw * mw + 32 * (mw + 1) + mw;
       int G = s_nwide >= 3 ? 4 : s_nwide;
-      while (G > 1 && G * need > smem_doubles) G >>= 1;
+      while (G > 1 && G * need > cap_t) G >>= 1;
       const int bd = blockDim.x / G, gid = threadIdx.x / bd, gtid = threadIdx.x - gid * bd;
-      double *gsm = sm + gid * need;
+      T *gsm = sm + gid * need;
       for (int k = gid; k < s_nwide; k += G)
-        block_factor_sn(I, s_wide[k], gsm, gsm + need - mw, gtid, bd, gid);
+        block_factor_sn(I, Lx, Dx, s_wide[k], gsm, gsm + need - mw, gtid, bd, gid);
       __syncthreads();
     }
     cluster.sync();
-    level_updates(I, L, crank * blockDim.x + threadIdx.x, ncl * blockDim.x);
+    level_updates(I, Lx, L, crank * blockDim.x + threadIdx.x, ncl * blockDim.x);
     cluster.sync();
   }
+}
+
+// factorization of each instance in the FACT phase (panels condensed by k_b_condense): one
+// block, or one thread-block cluster (big instances, launched with a cluster size), per
+// instance.  Warps of the whole cluster share the narrow supernodes of a level; each block
+// collects the wide ones its warps met and factors them with all its threads; a cluster barrier
+// (release / acquire) separates the levels.  T = float factors the instances whose FP32 factor
+// serves (p32 in the control record: panels and diagonal blocks hold floats at the same slot
+// indices), T = double the others; a batch of precision 64 launches only the latter.
+static constexpr int B_WIDE_CAP = 1024;  // wide supernodes per level and block
+
+template <typename T>
+__global__ void __launch_bounds__(B_NT_F, 3)
+    k_b_fact_inst(const BI *bi, const BCtl *ctl, int smem_doubles, const int *order) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int s_wide[B_WIDE_CAP], s_nwide;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
+  const int b = order[blockIdx.x / ncl];
+  // the same for every block of the cluster
+  if (ctl[b].ph != PH_FACT || ctl[b].p32 != (int)(sizeof(T) == sizeof(float))) return;
+  const BI &I = bi[b];
+  fact_levels<T>(I, reinterpret_cast<T *>(I.Lx), reinterpret_cast<T *>(I.Dx),
+                 reinterpret_cast<T *>(sm_raw), (int)(smem_doubles * sizeof(double) / sizeof(T)),
+                 s_wide, s_nwide, crank, ncl);
 }
 
 // L11 and the reciprocal pivots of a supernode of width w <= B_WS copied to this warp's shared
 // staging area with one load per lane (the triangular loops then read shared memory instead of
 // issuing one global round trip per column); wider supernodes read them in place
-__device__ __forceinline__ const double *stage_diag(const double *Dd, int w, double *stage,
-                                                    int lane) {
+template <typename T>
+__device__ __forceinline__ const T *stage_diag(const T *Dd, int w, T *stage, int lane) {
   if (w > B_WS) return Dd;
   for (int t = lane; t < w * w + w; t += 32) stage[t] = Dd[t];
   __syncwarp();
@@ -1001,28 +1037,29 @@ __device__ __forceinline__ const double *stage_diag(const double *Dd, int w, dou
 
 // forward step of one supernode, one warp: y_own <- L11^{-1} y_own, y_below -= L21 y_own (ys:
 // this warp's shared staging, w doubles, then L11 for w <= B_WS)
-__device__ void warp_fwd_sn(const BI &I, double *Y, int s, double *ys) {
+template <typename T>
+__device__ void warp_fwd_sn(const BI &I, const T *Lx, const T *Dx, T *Y, int s, T *ys) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   const int *rows = I.srow + rb;
-  const double *P = I.Lx + I.lptr[s];
-  const double *Dd = stage_diag(I.Dx + I.dptr[s], w, ys + CIPM_SN_MAXW, lane), *rinv = Dd + w * w;
+  const T *P = Lx + I.lptr[s];
+  const T *Dd = stage_diag(Dx + I.dptr[s], w, ys + CIPM_SN_MAXW, lane), *rinv = Dd + w * w;
   for (int k = lane; k < w; k += 32) ys[k] = Y[f + k];
   __syncwarp();
   for (int k = 0; k < w; ++k) {
     if (lane == (k & 31)) ys[k] *= rinv[k];
     __syncwarp();
-    const double yk = ys[k];
+    const T yk = ys[k];
     for (int i = k + 1 + lane; i < w; i += 32) ys[i] -= Dd[i + k * w] * yk;
     __syncwarp();
   }
   for (int k = lane; k < w; k += 32) Y[f + k] = ys[k];
   for (int i = w + lane; i < ld; i += 32) {
-    double acc = 0.0;
+    T acc = 0;
     int k = 0;
     for (; k + 4 <= w; k += 4) {  // four loads in flight
-      double p[4];
+      T p[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) p[u] = P[i + (int64_t)(k + u) * ld];
 #pragma unroll
@@ -1035,29 +1072,30 @@ __device__ void warp_fwd_sn(const BI &I, double *Y, int s, double *ys) {
 }
 
 // backward step of one supernode, one warp: y_own <- L11^{-T} (y_own - L21^T y_below)
-__device__ void warp_bwd_sn(const BI &I, double *Y, int s, double *zs) {
+template <typename T>
+__device__ void warp_bwd_sn(const BI &I, const T *Lx, const T *Dx, T *Y, int s, T *zs) {
   const int lane = threadIdx.x & 31;
   const int f = I.sptr[s], w = I.sptr[s + 1] - f;
   const int rb = I.srow_ptr[s], ld = I.srow_ptr[s + 1] - rb;
   const int *rows = I.srow + rb;
-  const double *P = I.Lx + I.lptr[s];
-  const double *Dd = stage_diag(I.Dx + I.dptr[s], w, zs + CIPM_SN_MAXW, lane), *rinv = Dd + w * w;
+  const T *P = Lx + I.lptr[s];
+  const T *Dd = stage_diag(Dx + I.dptr[s], w, zs + CIPM_SN_MAXW, lane), *rinv = Dd + w * w;
   if (w <= 32) {
     // zs = y_own - L21^T y_below: lane = g * W2 + k takes column k over the rows i = w + g
     // (mod G), then a shuffle tree over the G row groups (W2 = w rounded up to a power of two)
     int W2 = 1;
     while (W2 < w) W2 <<= 1;
     const int k = lane & (W2 - 1), g = lane / W2, G = 32 / W2;
-    double acc = 0.0;
+    T acc = 0;
     if (k < w)
       for (int i = w + g; i < ld; i += G) acc += P[i + (int64_t)k * ld] * Y[rows[i]];
     for (int o = W2; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (g == 0 && k < w) zs[k] = Y[f + k] - acc;
   } else {
     for (int k = 0; k < w; ++k) {
-      double acc = 0.0;
+      T acc = 0;
       for (int i = w + lane; i < ld; i += 32) acc += P[i + (int64_t)k * ld] * Y[rows[i]];
-      acc = warp_sum(acc);
+      acc = warp_sum_t(acc);
       if (lane == 0) zs[k] = Y[f + k] - acc;
     }
   }
@@ -1065,7 +1103,7 @@ __device__ void warp_bwd_sn(const BI &I, double *Y, int s, double *zs) {
   for (int k = w - 1; k >= 0; --k) {
     if (lane == (k & 31)) zs[k] *= rinv[k];
     __syncwarp();
-    const double xk = zs[k];
+    const T xk = zs[k];
     for (int j = lane; j < k; j += 32) zs[j] -= Dd[k + j * w] * xk;
     __syncwarp();
   }
@@ -1073,8 +1111,37 @@ __device__ void warp_bwd_sn(const BI &I, double *Y, int s, double *zs) {
   __syncwarp();
 }
 
+// forward and backward levels of one instance in precision T, then the scatter to x (FP64):
+// Y is the permuted right-hand side (shared memory or the instance's y), ys this warp's staging
+template <typename T>
+__device__ __forceinline__ void solve_levels(const BI &I, const T *Lx, const T *Dx, T *Y, T *ys,
+                                             double *x, int crank, int ncl) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gw = crank * nw + warp, gnw = ncl * nw;
+  const int gt = crank * blockDim.x + threadIdx.x, gnt = ncl * blockDim.x;
+  for (int k = gt; k < I.D.n; k += gnt) Y[k] = (T)I.t[I.perm[k]];
+  cluster.sync();
+  for (int L = 0; L < I.nlevels; ++L) {
+    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw)
+      warp_fwd_sn(I, Lx, Dx, Y, I.level_sn[q], ys);
+    cluster.sync();
+  }
+  for (int L = I.nlevels - 1; L >= 0; --L) {
+    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw)
+      warp_bwd_sn(I, Lx, Dx, Y, I.level_sn[q], ys);
+    cluster.sync();
+  }
+  for (int k = gt; k < I.D.n; k += gnt) x[I.perm[k]] = (double)Y[k];
+}
+
 // phase SOLVE: dx = K^{-1} t; phase REFINE: cx = K^{-1} t (t from k_b_jt_rhs), one cluster per
-// instance: gather by the ordering, forward levels, backward levels, scatter
+// instance: gather by the ordering, forward levels, backward levels, scatter.  With the FP32
+// factor (p32) the triangular solves run in single precision (classical mixed-precision
+// refinement: only the residual and the update of the refinement are FP64); T = float serves
+// those instances, T = double the others.
+template <typename T>
 __global__ void __launch_bounds__(B_NT, 3)
     k_b_solve_inst(const BI *bi, const BCtl *ctl, int phase, int ycap, const int *order) {
   constexpr int kArea = CIPM_SN_MAXW + B_WS * B_WS + B_WS;  // per warp: ys, then L11 stage
@@ -1084,28 +1151,18 @@ __global__ void __launch_bounds__(B_NT, 3)
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank(), ncl = (int)cluster.num_blocks();
   const int b = order[blockIdx.x / ncl];
-  if (ctl[b].ph != phase) return;  // the same for every block of the cluster
+  // the same for every block of the cluster
+  if (ctl[b].ph != phase || ctl[b].p32 != (int)(sizeof(T) == sizeof(float))) return;
   const BI &I = bi[b];
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int gw = crank * nw + warp, gnw = ncl * nw;
-  const int gt = crank * blockDim.x + threadIdx.x, gnt = ncl * blockDim.x;
-  double *ys = s_y + warp * kArea;
-  // the permuted right-hand side lives in this block's shared memory when the instance has
-  // one block and n fits (ycap doubles): its loads and atomic updates then stay on the SM
-  double *Y = ncl == 1 && I.D.n <= ycap ? s_vec : I.y;
-  for (int k = gt; k < I.D.n; k += gnt) Y[k] = I.t[I.perm[k]];
-  cluster.sync();
-  for (int L = 0; L < I.nlevels; ++L) {
-    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_fwd_sn(I, Y, I.level_sn[q], ys);
-    cluster.sync();
-  }
-  for (int L = I.nlevels - 1; L >= 0; --L) {
-    for (int q = I.lvl_ptr[L] + gw; q < I.lvl_ptr[L + 1]; q += gnw) warp_bwd_sn(I, Y, I.level_sn[q], ys);
-    cluster.sync();
-  }
+  const int warp = threadIdx.x >> 5;
   double *x = phase == PH_SOLVE || phase == PH_CGI || phase == PH_CGX ? I.dx
               : phase == PH_CG ? I.cg_v : I.cx;
-  for (int k = gt; k < I.D.n; k += gnt) x[I.perm[k]] = Y[k];
+  // the permuted right-hand side lives in this block's shared memory when the instance has
+  // one block and n fits (ycap doubles): its loads and atomic updates then stay on the SM
+  const bool in_smem = ncl == 1 && I.D.n <= ycap;
+  T *Y = in_smem ? reinterpret_cast<T *>(s_vec) : reinterpret_cast<T *>(I.y);
+  solve_levels<T>(I, reinterpret_cast<const T *>(I.Lx), reinterpret_cast<const T *>(I.Dx), Y,
+                  reinterpret_cast<T *>(s_y) + warp * kArea, x, crank, ncl);
 }
 
 // ------------------------------------------------------------------ HyKKT CG (Eq. (10))
@@ -1278,6 +1335,14 @@ __global__ void k_b_ctl_fact(const BI *bi, BCtl *ctl, int count) {
     }
     return;
   }
+  if (c.p32) {
+    // the FP32 factorization broke down: that says nothing about the inertia of K (the matrix
+    // rounded to FP32 and the FP32 pivots decide it), so the same delta_w is factored in FP64,
+    // and the instance stays in FP64 for the rest of its solve
+    c.p32 = 0;
+    c.k32 = c.k;
+    return;
+  }
   c.dw = c.next;
   c.next *= c.grow;
   if (c.dw >= 1e40) {
@@ -1328,9 +1393,9 @@ __global__ void k_b_ctl_solved(const BI *bi, BCtl *ctl, int count) {
 }
 
 // ------------------------------------------------------------------ refinement rounds
-__global__ void k_b_resid(const BI *bi, const BCtl *ctl) {
+__global__ void k_b_resid(const BI *bi, const BCtl *ctl, int phase) {
   __shared__ double sh[32];
-  B_PROLOGUE(PH_REFINE);
+  B_PROLOGUE(phase);
   AugArgs A = I.aug;
   A.dw = ctl[b].dw;
   double res = 0.0, solv = 0.0, rhsv = 0.0, asum = 0.0;
@@ -1356,6 +1421,15 @@ __global__ void k_b_resid(const BI *bi, const BCtl *ctl) {
   block_max_to(&A.scal[2], rhsv, sh);
   block_max_to(&A.scal[3], asum, sh);
 }
+// a KKT solve ends with backward error eta: counted, then the step (or the hold)
+__device__ __forceinline__ void solve_done(BCtl &c, double eta, const int *pause_k) {
+  c.eta = eta;
+  ++c.n_solve;
+  if (!(eta <= 1e-10)) ++c.n_above;
+  c.eta_worst = fmax(c.eta_worst, eta);
+  c.ph = !c.resto && c.k == *pause_k ? PH_PAUSE : PH_STEP;
+}
+
 // Richardson test: stop at eta <= 1e-10, after max_refine corrections, or when eta stops
 // halving; otherwise one more correction
 __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine,
@@ -1375,19 +1449,31 @@ __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine,
     c.ph = PH_DONE;
     return;
   }
-  stop = eta <= 1e-10 || c.ref_it >= max_refine || (c.ref_it > 0 && eta > 0.5 * c.eta_prev);
+  const int cap = c.p32 ? B_REFINE32 : max_refine;
+  stop = eta <= 1e-10 || c.ref_it >= cap || (c.ref_it > 0 && eta > 0.5 * c.eta_prev);
   ++c.ref_it;
   if (stop) {
-    c.ph = !c.resto && c.k == *pause_k ? PH_PAUSE : PH_STEP;
+    if (c.p32) {
+      if (!(eta <= 1e-10)) {
+        // the FP32 factor does not refine this solve to 1e-10 (cond(K) u_32 not small): the
+        // instance refactors at the same delta_w in FP64 and keeps FP64 from now on
+        c.p32 = 0;
+        c.k32 = c.k;
+        c.ph = PH_FACT;
+        return;
+      }
+      ++c.it32;
+    }
+    solve_done(c, eta, pause_k);
     return;
   }
   c.eta_prev = eta;
   ++c.ref_steps;
   ++c.total_ref;
 }
-__global__ void k_b_scal_zero(const BI *bi, const BCtl *ctl) {
+__global__ void k_b_scal_zero(const BI *bi, const BCtl *ctl, int phase) {
   const int b = blockIdx.x;
-  if (ctl[b].ph != PH_REFINE) return;
+  if (ctl[b].ph != phase) return;
   if (threadIdx.x < 4) bi[b].scal[threadIdx.x] = 0.0;
 }
 __global__ void k_b_axpy(const BI *bi, const BCtl *ctl) {
@@ -1858,8 +1944,14 @@ int pattern_of(const OpfData &M, std::vector<int> &out) {
 int b_smem_limits() {
   static bool done = false;
   if (done) return IPM_OK;
-  CK(cudaFuncSetAttribute(k_b_fact_inst, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-  CK(cudaFuncSetAttribute(k_b_solve_inst, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  CK(cudaFuncSetAttribute(k_b_fact_inst<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          64 * 1024));
+  CK(cudaFuncSetAttribute(k_b_fact_inst<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          64 * 1024));
+  CK(cudaFuncSetAttribute(k_b_solve_inst<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          64 * 1024));
+  CK(cudaFuncSetAttribute(k_b_solve_inst<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          64 * 1024));
   done = true;
   return IPM_OK;
 }
@@ -1925,7 +2017,9 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   auto solve = [&](int phase) -> int {
     k_b_jt_rhs<<<g2, blk, 0, s>>>(bi, ctl, phase);
     if (phase == PH_SOLVE) CKR(rec(2));
-    CKR(split(k_b_solve_inst, B_NT, B->solve_smem, phase, B->solve_ycap));
+    if (B->opt.precision == 32)  // the instances whose FP32 factor serves
+      CKR(split(k_b_solve_inst<float>, B_NT, B->solve_smem, phase, B->solve_ycap));
+    CKR(split(k_b_solve_inst<double>, B_NT, B->solve_smem, phase, B->solve_ycap));
     if (phase == PH_SOLVE) CKR(rec(3));
     k_b_recover_dz<<<g2, blk, 0, s>>>(bi, ctl, phase);
     L(2);
@@ -1958,7 +2052,9 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     CKR(rec(r == 0 ? 0 : 4));
     k_b_condense<<<dim3(B->gx_cond, C), blk, 0, s>>>(bi, ctl);
     L(1);
-    CKR(split(k_b_fact_inst, B_NT_F, B->fact_smem, (int)(B->fact_smem / sizeof(double))));
+    if (B->opt.precision == 32)
+      CKR(split(k_b_fact_inst<float>, B_NT_F, B->fact_smem, (int)(B->fact_smem / sizeof(double))));
+    CKR(split(k_b_fact_inst<double>, B_NT_F, B->fact_smem, (int)(B->fact_smem / sizeof(double))));
     CKR(rec(r == 0 ? 1 : 5));
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(3);
@@ -1969,7 +2065,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_cgi_rhs<<<g2, blk, 0, s>>>(bi, ctl);
     L(1);
     CKR(rec(2));
-    CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CGI, B->solve_ycap));
+    CKR(split(k_b_solve_inst<double>, B_NT, B->solve_smem, (int)PH_CGI, B->solve_ycap));
     CKR(rec(3));
     k_b_cgi_start<<<g2, blk, 0, s>>>(bi, ctl);
     k_b_ctl_cgi<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.cg_rtol);
@@ -1977,7 +2073,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     for (int r = 0; r < B_CG_ROUNDS; ++r) {
       k_b_cg_u<<<g2, blk, 0, s>>>(bi, ctl);
       L(1);
-      CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CG, B->solve_ycap));
+      CKR(split(k_b_solve_inst<double>, B_NT, B->solve_smem, (int)PH_CG, B->solve_ycap));
       k_b_cg_sp<<<g2, blk, 0, s>>>(bi, ctl);
       k_b_ctl_cg_alpha<<<gc, 128, 0, s>>>(bi, ctl, C);
       k_b_cg_xr<<<g2, blk, 0, s>>>(bi, ctl);
@@ -1987,7 +2083,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     }
     k_b_cgx_rhs<<<g2, blk, 0, s>>>(bi, ctl);
     L(1);
-    CKR(split(k_b_solve_inst, B_NT, B->solve_smem, (int)PH_CGX, B->solve_ycap));
+    CKR(split(k_b_solve_inst<double>, B_NT, B->solve_smem, (int)PH_CGX, B->solve_ycap));
     k_b_cgx_dz<<<g2, blk, 0, s>>>(bi, ctl);
     k_b_ctl_cgx<<<gc, 128, 0, s>>>(ctl, C, B->d_tickets + 12);
     L(2);
@@ -1999,8 +2095,8 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     k_b_ctl_solved<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(1);
     for (int r = 0; r < B_REFINE_ROUNDS; ++r) {
-      k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl);
-      k_b_resid<<<g2, blk, 0, s>>>(bi, ctl);
+      k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl, (int)PH_REFINE);
+      k_b_resid<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_REFINE);
       k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine, B->d_tickets + 12);
       L(3);
       CKR(solve(PH_REFINE));
@@ -2085,7 +2181,7 @@ int init_instances(ipm_batch_t B) {
   BCtl *ctl = B->d_ctl;
   const double mu0 = B->opt.mu0;
   k_b_ctl_init<<<grid_for(C, 128), 128, 0, s>>>(bi, ctl, C, mu0, B->opt.kkt == 1,
-                                                B->opt.cg_maxit);
+                                                B->opt.cg_maxit, B->opt.precision == 32);
   k_b_setup_sums<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_x0<<<g2, blk, 0, s>>>(bi, ctl);
   k_b_flow_start<<<g2, blk, 0, s>>>(bi, ctl);
@@ -2116,8 +2212,14 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
                   "gamma > 0) or 2 (dual-regularized, gamma > 0), tol > 0)");
     return IPM_ERR_BAD_ARG;
   }
-  if (opt->precision != 0 && opt->precision != 64) {
-    set_error_msg("ipm_batch_create: batched solves factor in FP64 (precision 0 or 64)");
+  if (opt->precision != 0 && opt->precision != 64 && opt->precision != 32) {
+    set_error_msg("ipm_batch_create: precision 0 or 64 (FP64 factor) or 32 (FP32 factor with "
+                  "FP64 refinement)");
+    return IPM_ERR_BAD_ARG;
+  }
+  if (opt->precision == 32 && opt->kkt == 1) {
+    set_error_msg("ipm_batch_create: the FP32 factor serves the refined condensed solve (kkt 0 "
+                  "or 2); HyKKT's Schur-complement CG needs exact K_gamma solves");
     return IPM_ERR_BAD_ARG;
   }
   for (int i = 0; i < count; ++i)
@@ -2675,6 +2777,22 @@ extern "C" int ipm_batch_cg_iters(ipm_batch_t B, int *cg_iters) {
   std::vector<BCtl> h(B->count);
   CK(cudaMemcpy(h.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost));
   for (int i = 0; i < B->count; ++i) cg_iters[i] = h[i].cg_total;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_solve_info(ipm_batch_t B, int *current, int *iters32, int *k64,
+                                    int *solves, int *above, double *eta_max) {
+  if (!B) return IPM_ERR_BAD_ARG;
+  std::vector<BCtl> h(B->count);
+  CK(cudaMemcpy(h.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < B->count; ++i) {
+    if (current) current[i] = h[i].p32 ? 32 : 64;
+    if (iters32) iters32[i] = h[i].it32;
+    if (k64) k64[i] = h[i].k32;
+    if (solves) solves[i] = h[i].n_solve;
+    if (above) above[i] = h[i].n_above;
+    if (eta_max) eta_max[i] = h[i].eta_worst;
+  }
   return IPM_OK;
 }
 

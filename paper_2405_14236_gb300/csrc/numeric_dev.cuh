@@ -85,6 +85,11 @@ __device__ __forceinline__ bool pivot_ok(double d) {
   return b > 0 && (b >> 52) < 0x7ff;
 }
 
+__device__ __forceinline__ bool pivot_ok(float d) {
+  const int b = __float_as_int(d);
+  return b > 0 && (b >> 23) < 0xff;
+}
+
 // 1/sqrt(d) from a single-precision seed y (relative error e0 below 2^-21) and one third-order
 // correction of the Newton-Raphson family for 1/sqrt: with e = 1 - d y^2, y <- y (1 + e/2 +
 // 3 e^2 / 8), which leaves an error of order e0^3, below double rounding.  Six dependent FP64

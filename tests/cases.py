@@ -48,3 +48,22 @@ def kkt_backward_error(opf, e):
     A = K.aug_matrix(K.full_from_lower(Wl), e["sigma"], J, e["d_row"][me:], me, e["delta_w"])
     sol = np.concatenate([e["dx"], e["dyz"]])
     return K.backward_error(A, sol, np.concatenate([e["a"], e["b"]]))
+
+
+def kkt_oracle_eta(opf, e):
+    """Backward error that the oracle's own solve reaches on an exported condensed-form KKT
+    system (m_e = 0): condensed factor, Richardson refinement and the preconditioned CG after
+    stagnation (oracle/kkt.py lifted_solve), measured like kkt_backward_error."""
+    assert e["m_e"] == 0
+    Jp, Ji = opf.J_rowptr.cpu().numpy(), opf.J_colind.cpu().numpy()
+    Wp, Wi = opf.W_rowptr.cpu().numpy(), opf.W_colind.cpu().numpy()
+    n, m = opf.n, opf.m_e + opf.m_i
+    J = sp.csr_matrix((e["J_val"], Ji, Jp), shape=(m, n))
+    Wf = K.full_from_lower(sp.csr_matrix((e["W_val"], Wi, Wp), shape=(n, n)))
+    d = e["d_row"]
+    F = K.CondensedSolver(Wf, J).factor(K.condensed_matrix(Wf, e["sigma"], J, d, e["delta_w"]))
+    if not F.ok:
+        return float("inf")
+    A = K.aug_matrix(Wf, e["sigma"], J, d, 0, e["delta_w"])
+    x, z, _ = K.lifted_solve(F, A, J, d, e["a"], e["b"])
+    return K.backward_error(A, np.concatenate([x, z]), np.concatenate([e["a"], e["b"]]))

@@ -112,8 +112,10 @@ def test_batch_argument_errors():
     o = cp.Opf(g)
     arr = (ctypes.c_void_p * 1)(o.h.value)
     h = ctypes.c_void_p()
-    # FP32 is not batched; HyKKT and form 2 need gamma > 0; kkt outside 0..2
-    for kkt, gam, prec in ((0, 1e6, 32), (1, 0.0, 64), (2, -1.0, 64), (3, 1e6, 64)):
+    # FP32 only for the refined condensed forms (not HyKKT); precision 16 does not exist;
+    # HyKKT and form 2 need gamma > 0; kkt outside 0..2
+    for kkt, gam, prec in ((1, 1e6, 32), (0, 1e6, 16), (1, 0.0, 64), (2, -1.0, 64),
+                           (3, 1e6, 64)):
         opt = cp.IpmOptions(kkt, 1e-6, gam, 0.0, 0.1, 1e-10, 10, 0, prec)
         rc = cp.lib().ipm_batch_create(1, arr, ctypes.byref(opt), None, ctypes.byref(h))
         assert rc == cp.IPM_ERR_BAD_ARG
