@@ -506,6 +506,43 @@ def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3, precision=6
     return out
 
 
+def recipe_measure(steps=2):
+    """The batched LiftedKKT IPM (with the restoration phase) on the workload's shape drawn at the
+    stated parameters (synth.recipe_batch: impedances and loads unscaled, ratings 1.2 x base
+    flow): how the instances end (converged, locally infeasible, failed line search at a
+    feasible point, iteration limit) and the time of a batch."""
+    import torch
+    import paper_2405_14236_gb300 as cp
+    from synth import recipe_batch
+    grids = recipe_batch()
+    B = cp.Batch([cp.Opf(g) for g in grids])
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        B.reset()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        B.run(max_iter=MAX_ITER)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    r = B.results()
+    names = {1: "converged", 5: "failed line search at a feasible point", 7: "iteration limit",
+             8: "locally infeasible (restoration converged with the violation)"}
+    counts = {}
+    for s in r["status"]:
+        k = names.get(int(s), f"status {int(s)}")
+        counts[k] = counts.get(k, 0) + 1
+    return {"workload": "32 load scenarios of a 1,000-bus grid + 8 grids of 118-2,000 buses at "
+                        "the stated parameters (impedances and loads unscaled, ratings 1.2 x base "
+                        "flow), batched LiftedKKT FP64 IPM with the restoration phase",
+            "instances": len(grids), "status_counts": counts,
+            "restoration_phases": int(r["resto_phases"].sum()),
+            "iters_mean": float(r["iters"].mean()), "ms_per_batch": float(np.mean(ms)),
+            "converged_per_s": float((r["status"] == 1).sum() / (np.mean(ms) / 1e3))}
+
+
 def plain_measure(grids):
     """Single-problem GPU IPM (ipm_step loop, LiftedKKT FP64) on the given instances, one after
     another; time of the iterations (the per-problem symbolic analysis excluded, as for the
@@ -740,6 +777,8 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_forms:
         line["batch_regularized"] = batch_form_measure(grids)
         line["batch_hykkt"] = batch_form_measure(grids, kkt="hykkt")
+    if not args.no_forms:
+        line["batch_recipe"] = recipe_measure()
     if not args.no_warm:
         line["warm"] = warm_measure()
         if "plain" in line:

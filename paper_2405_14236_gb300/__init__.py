@@ -67,6 +67,7 @@ _SIGS = {
     "ipm_batch_cg_iters": (I, [P, P]),
     "ipm_batch_resto_counts": (I, [P, P, P]),
     "ipm_batch_solve_info": (I, [P, P, P, P, P, P, P]),
+    "ipm_batch_set_tail": (I, [P, I, I]),
     "ipm_batch_autotune": (I, [P, I, I, P, P, P, P]),
     "ipm_batch_export": (I, [P, I, P]),
     "ipm_batch_sweeps": (I, [P]),
@@ -559,6 +560,13 @@ class Batch:
         _check(lib().ipm_batch_export(self.h, int(i), out.ctypes.data_as(ctypes.c_void_p)),
                "ipm_batch_export")
         return out
+
+    def set_tail(self, active_max, cluster=0):
+        """Once at most active_max instances remain, sweeps hold more inertia and line-search
+        rounds, and (cluster > 0) run every instance on clusters (ipm_batch_set_tail; 0
+        disables)."""
+        _check(lib().ipm_batch_set_tail(self.h, int(active_max), int(cluster)),
+               "ipm_batch_set_tail")
 
     def set_shape(self, cluster, big_num, big_den, gx):
         """Launch shape (ipm_batch_set_shape); returns the number of instances on clusters."""

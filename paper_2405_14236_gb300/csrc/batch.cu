@@ -42,6 +42,9 @@ enum Phase {
 };
 
 static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2, B_CG_ROUNDS = 6;
+// rounds of the tail sweep (few instances left: a round then costs little, and an instance that
+// backtracks or corrects its inertia many times needs fewer sweeps)
+static constexpr int B_TAIL_FACT_ROUNDS = 4, B_TAIL_LS_ROUNDS = 8;
 // refinement steps allowed with the FP32 factor (at a contraction rate of 1/2 per step the
 // error falls by 2^-30 ~ 1e-9; a slower rate stops at the stall test first)
 static constexpr int B_REFINE32 = 30;
@@ -1882,6 +1885,15 @@ struct ipm_batch_s {
   std::vector<void *> bufs;  // per-pattern level offsets
   int *d_tickets = nullptr;  // scratch counters: active count at [8], pause iteration at [12]
   int *d_order = nullptr;  // small instances by decreasing supernode count, then the big ones
+  // tail of a run: once at most tail_active instances are still running, the sweeps hold more
+  // inertia rounds and line-search trials (a round then costs little) and, with tail_cl > 0,
+  // run every instance on clusters of tail_cl blocks; d_order_all lists every instance by
+  // decreasing supernode count
+  int tail_active = 16, tail_cl = 0;
+  int fact_rounds = B_FACT_ROUNDS, ls_rounds = B_LS_ROUNDS;  // of the sweep being captured
+  int *d_order_all = nullptr;
+  cudaGraph_t graph_tail = nullptr;
+  cudaGraphExec_t exec_tail = nullptr;
   int n_small = 0, n_big = 0;
   // launch shapes (ipm_batch_autotune): cluster size of the big instances, "big" = supernode
   // count above big_num / big_den times the median (big_den = 0: none), blocks per instance of
@@ -2046,16 +2058,17 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   k_b_ctl_build<<<gc, 128, 0, s>>>(ctl, C);
   L(2);
   // inertia rounds: condense + factor with the current delta_w
-  for (int r = 0; r < B_FACT_ROUNDS; ++r) {
+  // (timing: the first round between events 0 and 1, the others between 4 and 5)
+  for (int r = 0; r < B->fact_rounds; ++r) {
     k_b_aug_rhs<<<g2, blk, 0, s>>>(bi, ctl, B->opt.gamma);
     k_b_scale_jv<<<g2, blk, 0, s>>>(bi, ctl);
-    CKR(rec(r == 0 ? 0 : 4));
+    if (r <= 1) CKR(rec(r == 0 ? 0 : 4));
     k_b_condense<<<dim3(B->gx_cond, C), blk, 0, s>>>(bi, ctl);
     L(1);
     if (B->opt.precision == 32)
       CKR(split(k_b_fact_inst<float>, B_NT_F, B->fact_smem, (int)(B->fact_smem / sizeof(double))));
     CKR(split(k_b_fact_inst<double>, B_NT_F, B->fact_smem, (int)(B->fact_smem / sizeof(double))));
-    CKR(rec(r == 0 ? 1 : 5));
+    if (r == 0 || r == B->fact_rounds - 1) CKR(rec(r == 0 ? 1 : 5));
     k_b_ctl_fact<<<gc, 128, 0, s>>>(bi, ctl, C);
     L(3);
   }
@@ -2114,7 +2127,7 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
   k_b_ctl_ls0<<<gc, 128, 0, s>>>(bi, ctl, C);
   L(2);
   // line-search trials
-  for (int r = 0; r < B_LS_ROUNDS; ++r) {
+  for (int r = 0; r < B->ls_rounds; ++r) {
     k_b_trial<<<g2, blk, 0, s>>>(bi, ctl);
     L(1);
     eval(PH_LS, 2);
@@ -2160,6 +2173,7 @@ int set_order(ipm_batch_t B) {
   B->n_big = nbig;
   B->n_small = count - nbig;
   CK(cudaMemcpy(B->d_order, ord2.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B->d_order_all, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
   return IPM_OK;
 }
 
@@ -2170,6 +2184,58 @@ void drop_graph(ipm_batch_t B) {
     B->exec = nullptr;
     B->graph = nullptr;
   }
+  if (B->exec_tail) {
+    cudaGraphExecDestroy(B->exec_tail);
+    cudaGraphDestroy(B->graph_tail);
+    B->exec_tail = nullptr;
+    B->graph_tail = nullptr;
+  }
+}
+
+int enqueue_sweep(ipm_batch_t B, cudaStream_t s);
+
+// captures one sweep into *graph / *exec; tail = true: the tail's rounds (and, with tail_cl > 0,
+// every instance on clusters of tail_cl blocks)
+int capture_sweep(ipm_batch_t B, bool tail, cudaGraph_t *graph, cudaGraphExec_t *exec) {
+  const int n_small = B->n_small, n_big = B->n_big, cl_big = B->cl_big;
+  int *order = B->d_order;
+  if (tail && B->tail_cl > 0) {
+    B->n_small = 0;
+    B->n_big = B->count;
+    B->cl_big = B->tail_cl;
+    B->d_order = B->d_order_all;
+  }
+  if (tail) {
+    B->fact_rounds = B_TAIL_FACT_ROUNDS;
+    B->ls_rounds = B_TAIL_LS_ROUNDS;
+  }
+  // sweeps are captured on a private stream: legacy default streams cannot be captured
+  cudaStream_t cs;
+  int rc = IPM_OK;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = IPM_ERR_CUDA;
+  if (rc == IPM_OK) {
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = IPM_ERR_CUDA;
+    const int launches = B->launches_per_sweep;
+    if (rc == IPM_OK) rc = enqueue_sweep(B, cs);
+    if (tail) B->launches_per_sweep = launches;  // the count of the main graph is reported
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess && rc == IPM_OK) rc = IPM_ERR_CUDA;
+    cudaStreamDestroy(cs);
+    if (rc == IPM_OK && cudaGraphInstantiate(exec, g, 0) != cudaSuccess) rc = IPM_ERR_CUDA;
+    if (rc != IPM_OK) {
+      if (g) cudaGraphDestroy(g);
+      set_error_msg("ipm_batch_run: capturing the sweep failed");
+    } else {
+      *graph = g;
+    }
+  }
+  B->n_small = n_small;
+  B->n_big = n_big;
+  B->cl_big = cl_big;
+  B->d_order = order;
+  B->fact_rounds = B_FACT_ROUNDS;
+  B->ls_rounds = B_LS_ROUNDS;
+  return rc;
 }
 
 // starting point, scaling and multipliers of every instance (Ipopt: see ipm_state_create)
@@ -2570,6 +2636,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   };
   up(&B->d_bi, hbi);
   if (rc == IPM_OK && cudaMalloc(&B->d_order, sizeof(int) * count) != cudaSuccess) rc = IPM_ERR_OOM;
+  if (rc == IPM_OK && cudaMalloc(&B->d_order_all, sizeof(int) * count) != cudaSuccess)
+    rc = IPM_ERR_OOM;
   if (rc == IPM_OK) rc = set_order(B);
   if (rc == IPM_OK && cudaMalloc(&B->d_ctl, sizeof(BCtl) * count) != cudaSuccess) rc = IPM_ERR_OOM;
   if (rc == IPM_OK && cudaMalloc(&B->d_tickets, sizeof(int) * 16) != cudaSuccess) rc = IPM_ERR_OOM;
@@ -2632,35 +2700,17 @@ extern "C" int ipm_batch_reset(ipm_batch_t B) {
 extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int use_graph) {
   if (!B || max_iter < 0 || max_sweeps < 1) return IPM_ERR_BAD_ARG;
   cudaStream_t s = B->stream;
-  if (B->max_iter != max_iter && B->exec) {
-    cudaGraphExecDestroy(B->exec);
-    cudaGraphDestroy(B->graph);
-    B->exec = nullptr;
-    B->graph = nullptr;
-  }
+  if (B->max_iter != max_iter) drop_graph(B);
   B->max_iter = max_iter;
-  if (use_graph && !B->exec) {
-    // sweeps are captured on a private stream: legacy default streams cannot be captured
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    int rc = IPM_OK;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = IPM_ERR_CUDA;
-    if (rc == IPM_OK) rc = enqueue_sweep(B, cs);
-    cudaGraph_t g = nullptr;
-    if (cudaStreamEndCapture(cs, &g) != cudaSuccess && rc == IPM_OK) rc = IPM_ERR_CUDA;
-    cudaStreamDestroy(cs);
-    if (rc != IPM_OK) {
-      if (g) cudaGraphDestroy(g);
-      set_error_msg("ipm_batch_run: capturing the sweep failed");
-      return rc;
-    }
-    B->graph = g;
-    CK(cudaGraphInstantiate(&B->exec, g, 0));
-  }
+  if (use_graph && !B->exec) CKR(capture_sweep(B, false, &B->graph, &B->exec));
+  if (use_graph && B->tail_active > 0 && !B->exec_tail)
+    CKR(capture_sweep(B, true, &B->graph_tail, &B->exec_tail));
   int rc = IPM_OK;
+  *B->h_active = B->count;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     if (use_graph) {
-      CK(cudaGraphLaunch(B->exec, s));
+      const bool tail = B->exec_tail && *B->h_active <= B->tail_active;
+      CK(cudaGraphLaunch(tail ? B->exec_tail : B->exec, s));
     } else {
       CKR(enqueue_sweep(B, s));
     }
@@ -2819,10 +2869,10 @@ extern "C" int ipm_batch_sweeps(ipm_batch_t B) { return B ? B->sweeps : 0; }
 
 extern "C" void ipm_batch_destroy(ipm_batch_t B) {
   if (!B) return;
-  if (B->exec) cudaGraphExecDestroy(B->exec);
-  if (B->graph) cudaGraphDestroy(B->graph);
+  drop_graph(B);
   for (ipm_sym_t S : B->syms) ipm_symbolic_destroy(S);
-  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_tickets, B->d_order};
+  void *ps[] = {B->dpool, B->ipool, B->d_bi, B->d_ctl, B->d_tickets, B->d_order,
+                B->d_order_all};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (B->h_active) cudaFreeHost(B->h_active);
@@ -3010,6 +3060,16 @@ extern "C" int ipm_batch_export_kkt(ipm_batch_t B, int i, double *W_val, double 
   }
   if (delta_w) *delta_w = c.dw;
   if (m_e) *m_e = hykkt ? me0 : 0;
+  return IPM_OK;
+}
+
+extern "C" int ipm_batch_set_tail(ipm_batch_t B, int active_max, int cluster) {
+  if (!B || active_max < 0 ||
+      (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8))
+    return IPM_ERR_BAD_ARG;
+  B->tail_active = active_max;
+  B->tail_cl = cluster;
+  drop_graph(B);
   return IPM_OK;
 }
 

@@ -145,7 +145,8 @@ def ring_grid(nb: int = 30, n_chords: int = 11, ng: int = 6, seed: int = 1) -> G
 
 
 def planar_grid(nb: int, ng: int, seed: int, branch_ratio: float = 1.3,
-                z_scale: float = 0.2, load_scale: float = 0.2) -> Grid:
+                z_scale: float = 0.2, load_scale: float = 0.2, rate_factor: float = 2.0,
+                rate_floor: float = 0.2) -> Grid:
     """Random geometric planar graph: Delaunay triangulation of uniform points,
     its Euclidean minimum spanning tree, then the shortest remaining Delaunay
     edges until nbr = branch_ratio * nb.  Series impedances are the ring-grid
@@ -183,7 +184,7 @@ def planar_grid(nb: int, ng: int, seed: int, branch_ratio: float = 1.3,
     perm = rng.permutation(len(chosen))
     chosen = chosen[perm]
     return _finish(rng, nb, chosen[:, 0], chosen[:, 1], ng, f"planar{nb}", z_scale=z_scale,
-                   load_scale=load_scale)
+                   load_scale=load_scale, rate_factor=rate_factor, rate_floor=rate_floor)
 
 
 def scale_loads(grid: Grid, seed: int, lo: float = 0.8, hi: float = 1.2) -> Grid:
@@ -220,6 +221,27 @@ def mixed_grid(seed: int, lo: int = 118, hi: int = 2000) -> Grid:
     rng = np.random.default_rng(seed)
     nb = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
     return make_grid(nb, seed)
+
+
+def recipe_grid(nb: int, seed: int) -> Grid:
+    """Planar grid at the workload description's stated parameters, without this project's
+    lightening: impedances and loads unscaled, ratings 1.2 x the base flow (the DC-flow reading)
+    floored at 0.05 pu."""
+    return planar_grid(nb, max(2, nb // 5), seed, z_scale=1.0, load_scale=1.0, rate_factor=1.2,
+                       rate_floor=0.05)
+
+
+def recipe_batch(n_scen: int = 32, n_mixed: int = 8):
+    """The batched workload's shape at the stated parameters (recipe_grid): n_scen load scenarios
+    of the 1,000-bus grid (seed 4; per-bus scaling U[0.8, 1.2], seeds 1000, ...) and n_mixed
+    grids of 118-2000 buses (seeds 2000, ...)."""
+    g = recipe_grid(1000, 4)
+    mixed = []
+    for k in range(n_mixed):
+        rng = np.random.default_rng(2000 + k)
+        nb = int(round(np.exp(rng.uniform(np.log(118), np.log(2000)))))
+        mixed.append(recipe_grid(nb, 2000 + k))
+    return [scale_loads(g, 1000 + k) for k in range(n_scen)] + mixed
 
 
 def batch_grids(n_scen: int = 256, n_mixed: int = 64, base: str = "planar1k", part: int = 0):

@@ -243,3 +243,28 @@ def test_supernode_shape_tuning_keeps_results():
         assert (r["status"] == 1).all(), (relax, r["status"])
         objs.append(r["obj"])
     np.testing.assert_allclose(objs[1], objs[0], rtol=1e-6)
+
+
+def test_tail_sweeps_reach_the_same_optima():
+    """The tail sweep (ipm_batch_set_tail: more inertia rounds and line-search trials per sweep
+    once few instances remain, optionally every instance on clusters) changes how many sweeps a
+    run takes, not the method: statuses and objectives equal those of runs without it."""
+    base = config_grid("planar1k")
+    grids = [scale_loads(base, 1000 + k) for k in range(3)] + [mixed_grid(2003), config_grid("ring30")]
+    B = cp.Batch([cp.Opf(g) for g in grids])
+    out = {}
+    for tail in ((0, 0), (16, 0), (16, 8)):
+        B.set_tail(*tail)
+        B.reset()
+        B.run(max_iter=300)
+        out[tail] = B.results()
+    ref = out[(0, 0)]
+    assert (ref["status"] == 1).all(), ref["status"]
+    for tail in ((16, 0), (16, 8)):
+        r = out[tail]
+        assert (r["status"] == 1).all(), (tail, r["status"])
+        assert np.allclose(r["obj"], ref["obj"], rtol=1e-8, atol=0), (tail, r["obj"], ref["obj"])
+    # the whole run is a tail here (5 instances): sweeps hold more rounds, so fewer are needed
+    assert out[(16, 0)]["sweeps"] <= ref["sweeps"] + 5, (out[(16, 0)]["sweeps"], ref["sweeps"])
+    with pytest.raises(cp.CondipmError):
+        B.set_tail(16, 3)

@@ -94,3 +94,18 @@ def test_batch_and_mixed_workload_shapes():
     assert all(g.nb == 1000 for g in grids[:4]) and [g.nb for g in grids[4:]] == sizes[:2]
     other = batch_grids(4, 2, part=1)  # another GPU's set: other seeds
     assert not np.array_equal(other[0].pd, grids[0].pd)
+
+
+def test_recipe_grid_has_the_stated_parameters():
+    """recipe_grid draws the planar topology with unscaled impedances and loads and ratings of
+    1.2 x the DC base flow floored at 0.05 pu; the default grid of the same seed is the lightened
+    one (x 0.2 impedances and loads, 2.0 x ratings floored at 0.2 pu)."""
+    from synth import recipe_grid, recipe_batch, make_grid
+    a, b = recipe_grid(300, 11), make_grid(300, 11)
+    assert np.array_equal(a.f_bus, b.f_bus) and np.array_equal(a.t_bus, b.t_bus)
+    assert np.allclose(a.r, 5 * b.r) and np.allclose(a.x, 5 * b.x)
+    assert np.allclose(a.pd, 5 * b.pd) and np.allclose(a.qd, 0.3 * a.pd)
+    assert a.r.min() >= 0.005 and a.r.max() <= 0.05
+    assert a.rate.min() >= 0.05 - 1e-15 and b.rate.min() >= 0.2 - 1e-15
+    gs = recipe_batch(3, 2)
+    assert len(gs) == 5 and all(g.nb == 1000 for g in gs[:3]) and 118 <= gs[3].nb <= 2000
