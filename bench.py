@@ -586,7 +586,9 @@ def run_gpu(args, rank, world, local_rank):
     opfs = [cp.Opf(g) for g in grids]
     # supernode partition chosen by measurement (outside the timed steps, like the launch shapes)
     relax, sn_tune = (0, 0), None
-    if not args.no_autotune and not args.launch_shape:
+    if args.relax:
+        relax = tuple(int(v) for v in args.relax.split(","))
+    elif not args.no_autotune and not args.launch_shape:
         from paper_2405_14236_gb300 import tune
         t0 = time.perf_counter()
         relax, recs = tune.supernode_shapes(opfs)
@@ -985,6 +987,8 @@ def main():
     ap.add_argument("--launch-shape", default="",
                     help="CL,NUM,DEN: fixed launch shape (clusters of CL blocks for instances above "
                          "NUM/DEN times the median supernode count) instead of the autotuner")
+    ap.add_argument("--relax", default="",
+                    help="W,DEN: fixed supernode relaxation (profiling) instead of the tuned one")
     ap.add_argument("--split", action="store_true",
                     help="N > 1: split one instance set across the GPUs by size (strong scaling) "
                          "instead of one set per GPU")

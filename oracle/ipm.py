@@ -39,6 +39,8 @@ KAPPA_SIGMA = 1e10
 # 10 eps_mach |phi|, so a trial whose phi differs by less than that counts as equal
 PHI_MARGIN = 10.0 * np.finfo(np.float64).eps
 SOFT_RESTO_REDUCTION = 1e-4   # required relative decrease of E_mu in a soft-restoration step
+MAX_LS_REGULARIZE = 8         # recomputed directions (larger delta_w) after a line search that
+                              # fails at a point feasible within the tolerance
 
 
 def filter_accept(theta, phi, gphi, alpha, tht, pht, filt, theta_min, theta_max):
@@ -273,6 +275,20 @@ def auto_gamma(W, sigma_x, G, H, Ds):
     return kn / (gn * gn) if gn > 0 else 1.0
 
 
+def schedule_from(kmat, solver, delta, grow):
+    """The inertia-correction schedule continued from the candidate delta: delta, delta grow,
+    ... until the factorization of kmat(delta_w) succeeds (RuntimeError at 1e40).  Returns
+    (delta_w, factor, factorizations)."""
+    nf = 0
+    while delta < 1e40:
+        nf += 1
+        F = solver.factor(kmat(delta))
+        if F.ok:
+            return delta, F, nf
+        delta *= grow
+    raise RuntimeError("inertia correction failed")
+
+
 def solve(model, opt: Options | None = None, x0=None):
     """The IPM on a model: Ipopt's gradient scaling at the start, LiftedKKT's relaxation
     (Sec. 3.2) for kkt = "lifted", the starting point of the reading in the design notes, then
@@ -387,131 +403,161 @@ def _ipm(model, opt, start, mu, sig_f, exit_check=None, restore=True, max_iter=N
             d = np.concatenate([np.full(me, gamma), dh]) if opt.kkt != "lifted" else dh
             return K.condensed_matrix(W, sigma_x, J, d, dw)
 
-        try:
-            dw, F, nfac = K.inertia_schedule(kmat, solver, delta_last)
-        except RuntimeError:      # no delta_w up to 1e40 gives a positive definite matrix
-            status = "inertia_failed"
-            break
-        if dw > 0:
-            delta_last = dw
-        dh = Ds + dw
-        a = -r1
-
-        def direction(r3_, r4_):
-            """Newton direction for the constraint residuals (r3_, r4_) with the factor of this
-            iteration."""
-            bH = -r4_ + r2 / dh
-            cg_its_ = 0
-            if opt.kkt == "hykkt":
-                b = np.concatenate([-r3_, bH])
-                dx_, dy_, dz_, cg_its_, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, gamma, a, b,
-                                                          rtol=opt.cg_rtol)
-                eta_ = K.backward_error(K.aug_matrix(W, sigma_x, J, dh, me, dw),
-                                        np.concatenate([dx_, dy_, dz_]), np.concatenate([a, b]))
-            elif opt.kkt == "regularized":
-                # dual regularization delta_c = 1/gamma (Remark in Sec. 3): one condensed solve
-                # of (K + G^T G / delta_c) dx = r1bar + G^T r2bar / delta_c, dy = (G dx - r2bar)
-                # / delta_c, refined on the augmented system with -delta_c I in the equality block
-                b = np.concatenate([-r3_, bH])
-                d = np.concatenate([np.full(me, gamma), dh])
-                A = K.aug_matrix(W, sigma_x, J, d, 0, dw)
-                dx_, dzall, eh = K.lifted_solve(F, A, J, d, a, b, max_refine=opt.max_refine)
-                dy_, dz_ = dzall[:me], dzall[me:]
-                eta_ = eh[-1]
-            else:
-                A = K.aug_matrix(W, sigma_x, J, dh, 0, dw)
-                dx_, dz_, eh = K.lifted_solve(F, A, J, dh, a, bH, max_refine=opt.max_refine)
-                dy_ = np.zeros(0)
-                eta_ = eh[-1]
-            ds_ = -(r2 + dz_) / dh
-            dv_ = (mu - v * ds_) / s - v
-            dzl_ = np.where(hl, mu / dxl - zl - zl / dxl * dx_, 0.0)
-            dzu_ = np.where(hu, mu / dxu - zu + zu / dxu * dx_, 0.0)
-            return dx_, dy_, dz_, ds_, dv_, dzl_, dzu_, cg_its_, eta_
-
-        dx, dy, dz, ds, dv, dzl, dzu, cg_its, eta = direction(r3, r4)
-
-        # fraction to the boundary
-        def ftb(val, dval):
-            neg = dval < 0
-            if not neg.any():
-                return 1.0
-            return float(min(1.0, np.min(-tau * val[neg] / dval[neg])))
-
-        amax = min(ftb(x[hl] - xl[hl], dx[hl]), ftb(xu[hu] - x[hu], -dx[hu]), ftb(s, ds))
-        az = min(ftb(v, dv), ftb(zl[hl], dzl[hl]), ftb(zu[hu], dzu[hu]))
-
-        theta = theta_of(g, h, s)
-        phi = phi_of(x, s, mu)
-        gphi = (sig_f * gradf @ dx - mu * np.sum(ds / s) - mu * np.sum((dx / dxl)[hl])
-                + mu * np.sum((dx / dxu)[hu]))
-        if gphi < 0:
-            amin = GAMMA_ALPHA * min(GAMMA_THETA, GAMMA_PHI * theta / -gphi,
-                                     DELTA * theta ** S_THETA / (-gphi) ** S_PHI)
-        else:
-            amin = GAMMA_ALPHA * GAMMA_THETA
-        alpha = amax
-        accepted = False
-        ls = 0
-
+        # delta_w of this iteration from the inertia-correction schedule (Sec. 2.2); after a line
+        # search that fails at a point feasible within the tolerance the schedule goes on from its
+        # next candidate (sched = (delta, growth)) and the direction is recomputed
+        delta_last0 = delta_last
+        grow0 = 8.0 if delta_last0 > 0 else 100.0
+        sched = None
+        n_reg = 0
+        outcome = None
         while True:
-            xt = x + alpha * dx
-            st = s + alpha * ds
-            gt, ht = model.cons(xt)
-            tht = theta_of(gt, ht, st)
-            pht = phi_of(xt, st, mu)
-            accepted, ftype = filter_accept(theta, phi, gphi, alpha, tht, pht, filt, theta_min,
-                                            theta_max)
-            if accepted:
+            try:
+                if sched is None:
+                    dw, F, nfac = K.inertia_schedule(kmat, solver, delta_last)
+                else:
+                    dw, F, nf2 = schedule_from(kmat, solver, *sched)
+                    nfac += nf2
+            except RuntimeError:      # no delta_w up to 1e40 gives a positive definite matrix
+                outcome = "inertia_failed"
                 break
-            ls += 1
-            alpha *= 0.5
-            if alpha < amin:
+            if dw > 0:
+                delta_last = dw
+            dh = Ds + dw
+            a = -r1
+
+            def direction(r3_, r4_):
+                """Newton direction for the constraint residuals (r3_, r4_) with the factor of this
+                iteration."""
+                bH = -r4_ + r2 / dh
+                cg_its_ = 0
+                if opt.kkt == "hykkt":
+                    b = np.concatenate([-r3_, bH])
+                    dx_, dy_, dz_, cg_its_, _ = K.hykkt_solve(F, W, sigma_x, J, dh, me, dw, gamma, a, b,
+                                                              rtol=opt.cg_rtol)
+                    eta_ = K.backward_error(K.aug_matrix(W, sigma_x, J, dh, me, dw),
+                                            np.concatenate([dx_, dy_, dz_]), np.concatenate([a, b]))
+                elif opt.kkt == "regularized":
+                    # dual regularization delta_c = 1/gamma (Remark in Sec. 3): one condensed solve
+                    # of (K + G^T G / delta_c) dx = r1bar + G^T r2bar / delta_c, dy = (G dx - r2bar)
+                    # / delta_c, refined on the augmented system with -delta_c I in the equality block
+                    b = np.concatenate([-r3_, bH])
+                    d = np.concatenate([np.full(me, gamma), dh])
+                    A = K.aug_matrix(W, sigma_x, J, d, 0, dw)
+                    dx_, dzall, eh = K.lifted_solve(F, A, J, d, a, b, max_refine=opt.max_refine)
+                    dy_, dz_ = dzall[:me], dzall[me:]
+                    eta_ = eh[-1]
+                else:
+                    A = K.aug_matrix(W, sigma_x, J, dh, 0, dw)
+                    dx_, dz_, eh = K.lifted_solve(F, A, J, dh, a, bH, max_refine=opt.max_refine)
+                    dy_ = np.zeros(0)
+                    eta_ = eh[-1]
+                ds_ = -(r2 + dz_) / dh
+                dv_ = (mu - v * ds_) / s - v
+                dzl_ = np.where(hl, mu / dxl - zl - zl / dxl * dx_, 0.0)
+                dzu_ = np.where(hu, mu / dxu - zu + zu / dxu * dx_, 0.0)
+                return dx_, dy_, dz_, ds_, dv_, dzl_, dzu_, cg_its_, eta_
+
+            dx, dy, dz, ds, dv, dzl, dzu, cg_its, eta = direction(r3, r4)
+
+            # fraction to the boundary
+            def ftb(val, dval):
+                neg = dval < 0
+                if not neg.any():
+                    return 1.0
+                return float(min(1.0, np.min(-tau * val[neg] / dval[neg])))
+
+            amax = min(ftb(x[hl] - xl[hl], dx[hl]), ftb(xu[hu] - x[hu], -dx[hu]), ftb(s, ds))
+            az = min(ftb(v, dv), ftb(zl[hl], dzl[hl]), ftb(zu[hu], dzu[hu]))
+
+            theta = theta_of(g, h, s)
+            phi = phi_of(x, s, mu)
+            gphi = (sig_f * gradf @ dx - mu * np.sum(ds / s) - mu * np.sum((dx / dxl)[hl])
+                    + mu * np.sum((dx / dxu)[hu]))
+            if gphi < 0:
+                amin = GAMMA_ALPHA * min(GAMMA_THETA, GAMMA_PHI * theta / -gphi,
+                                         DELTA * theta ** S_THETA / (-gphi) ** S_PHI)
+            else:
+                amin = GAMMA_ALPHA * GAMMA_THETA
+            alpha = amax
+            accepted = False
+            ls = 0
+
+            while True:
+                xt = x + alpha * dx
+                st = s + alpha * ds
+                gt, ht = model.cons(xt)
+                tht = theta_of(gt, ht, st)
+                pht = phi_of(xt, st, mu)
+                accepted, ftype = filter_accept(theta, phi, gphi, alpha, tht, pht, filt, theta_min,
+                                                theta_max)
+                if accepted:
+                    break
+                ls += 1
+                alpha *= 0.5
+                if alpha < amin:
+                    break
+            soft = False
+            if not accepted and opt.soft_restoration:
+                # soft restoration (Ipopt's fallback before its restoration phase): the step damped
+                # only by the fraction to the boundary (alpha_max, and az for the bound duals) is
+                # taken if it reduces the primal-dual error of the barrier problem, E_mu, by the
+                # factor 1 - 1e-4; the filter is left as it is
+                xt = x + amax * dx
+                st = s + amax * ds
+                gt, ht = model.cons(xt)
+                e_now = errors(gradf, J, g, h, mu)
+                e_try = errors_at(xt, st, y + amax * dy, z + amax * dz, v + az * dv, zl + az * dzl,
+                                  zu + az * dzu, model.grad(xt), model.jacobian(xt), gt, ht, mu)
+                if e_try <= (1.0 - SOFT_RESTO_REDUCTION) * e_now:
+                    accepted = soft = True
+                    alpha = amax
+                    ftype = True
+            if (not accepted and restore and opt.restoration
+                    and max(np.abs(g).max(initial=0.0), np.abs(h + s).max(initial=0.0)) <= opt.tol):
+                # a failed line search at a point that is feasible within the tolerance: the
+                # restoration phase cannot reduce a violation that is already at rounding level, and
+                # its problem is solved by the point itself.  The direction is computed again
+                # with the next delta_w of the iteration's inertia-correction schedule (a
+                # better conditioned, more gradient-like step), at most MAX_LS_REGULARIZE times,
+                # before the method stops there (reading)
+                if n_reg < MAX_LS_REGULARIZE:
+                    n_reg += 1
+                    # the schedule's candidate after the accepted delta_w
+                    nxt = (dw * grow0 if dw > 0 else
+                           (max(1e-20, delta_last0 / 3.0) if delta_last0 > 0 else 1e-4))
+                    sched = (nxt, grow0)
+                    continue
+                outcome = "restoration_failed"
                 break
-        soft = False
-        if not accepted and opt.soft_restoration:
-            # soft restoration (Ipopt's fallback before its restoration phase): the step damped
-            # only by the fraction to the boundary (alpha_max, and az for the bound duals) is
-            # taken if it reduces the primal-dual error of the barrier problem, E_mu, by the
-            # factor 1 - 1e-4; the filter is left as it is
-            xt = x + amax * dx
-            st = s + amax * ds
-            gt, ht = model.cons(xt)
-            e_now = errors(gradf, J, g, h, mu)
-            e_try = errors_at(xt, st, y + amax * dy, z + amax * dz, v + az * dv, zl + az * dzl,
-                              zu + az * dzu, model.grad(xt), model.jacobian(xt), gt, ht, mu)
-            if e_try <= (1.0 - SOFT_RESTO_REDUCTION) * e_now:
-                accepted = soft = True
-                alpha = amax
-                ftype = True
-        if (not accepted and restore and opt.restoration
-                and max(np.abs(g).max(initial=0.0), np.abs(h + s).max(initial=0.0)) <= opt.tol):
-            # a failed line search at a point that is feasible within the tolerance: the
-            # restoration phase cannot reduce a violation that is already at rounding level, and
-            # its problem is solved by the point itself (reading: the method stops there)
-            status = "restoration_failed"
+            if not accepted and restore and opt.restoration:
+                # feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the current point
+                # enters the filter, a point acceptable to it with a smaller constraint violation is
+                # sought by an IPM on the restoration problem, and the iterations go on from there
+                entry = ((1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta)
+                rec = _restoration(model, opt, x, s, v, zl, zu, mu, theta, theta_max,
+                                   filt + [entry], theta_at, lambda xx, sx: phi_of(xx, sx, mu))
+                n_resto += 1
+                hist.append(dict(k=it, mu=mu, e0=e0, alpha=0.0, delta_w=dw, nfac=nfac, cg=cg_its,
+                                 eta=eta, ls=ls, obj=model.objective(x), gamma=gamma, soft=False,
+                                 resto=rec["iters"], resto_status=rec["status"]))
+                if rec["status"] != "ok":
+                    outcome = rec["status"]
+                    break
+                filt.append(entry)
+                # constraint multipliers start again from zero, bound multipliers are kept (as in
+                # Ipopt after its restoration phase)
+                x, s, v, zl, zu = rec["x"], rec["s"], rec["v"], rec["zl"], rec["zu"]
+                y = np.zeros(me)
+                z = np.zeros(mi)
+                outcome = "restored"
+                break
             break
-        if not accepted and restore and opt.restoration:
-            # feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the current point
-            # enters the filter, a point acceptable to it with a smaller constraint violation is
-            # sought by an IPM on the restoration problem, and the iterations go on from there
-            entry = ((1 - GAMMA_THETA) * theta, phi - GAMMA_PHI * theta)
-            rec = _restoration(model, opt, x, s, v, zl, zu, mu, theta, theta_max,
-                               filt + [entry], theta_at, lambda xx, sx: phi_of(xx, sx, mu))
-            n_resto += 1
-            hist.append(dict(k=it, mu=mu, e0=e0, alpha=0.0, delta_w=dw, nfac=nfac, cg=cg_its,
-                             eta=eta, ls=ls, obj=model.objective(x), gamma=gamma, soft=False,
-                             resto=rec["iters"], resto_status=rec["status"]))
-            if rec["status"] != "ok":
-                status = rec["status"]
-                break
-            filt.append(entry)
-            # constraint multipliers start again from zero, bound multipliers are kept (as in
-            # Ipopt after its restoration phase)
-            x, s, v, zl, zu = rec["x"], rec["s"], rec["v"], rec["zl"], rec["zu"]
-            y = np.zeros(me)
-            z = np.zeros(mi)
+        if outcome == "restored":
             continue
+        if outcome is not None:
+            status = outcome
+            break
         if not accepted:
             status = "restoration_needed"
             break

@@ -67,6 +67,8 @@ struct BCtl {
   // KKT solves finished, those left above a backward error of 1e-10, the largest final error
   int n_solve, n_above;
   double eta_worst;
+  // directions of this iteration recomputed at a larger delta_w after a failed line search
+  int n_reg, pad_reg_;
   // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): resto 0 = main problem,
   // 2 = phase entered (its start is set at the next evaluation), 1 = in the phase; ret: the
   // accepted trial passed the return test.  While in the phase mu, tau, delta_last, theta_max,
@@ -104,6 +106,9 @@ struct BI {
   // that a warp's item loads are coalesced and its lanes loop over equal counts
   const int *cslot, *ccol, *cgptr;
   const int2 *citems;
+  // the same items as two 16-bit indices (W item: y = 0xFFFF, padding: y = 0xFFFE) when every
+  // index of the pattern fits, else null: half the bytes of the condensation's index stream
+  const ushort2 *citems16;
   int ncslot;
   const int64_t *lptr, *dptr;
   const int2 *items;
@@ -574,6 +579,7 @@ __global__ void k_b_ctl_build(BCtl *ctl, int count) {
   c.nfac = 0;
   c.grow = c.delta_last > 0 ? 8.0 : 100.0;
   c.next = c.delta_last > 0 ? fmax(1e-20, c.delta_last / 3.0) : 1e-4;
+  c.n_reg = 0;
   c.ph = PH_FACT;
 }
 
@@ -595,6 +601,40 @@ __global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
 }
 
 // ------------------------------------------------------------------ condensation
+// one condensation item as (x, y): (J entry p, J entry q), (W entry, -1) or padding (-, -2)
+__device__ __forceinline__ int2 citem(int2 q) { return q; }
+__device__ __forceinline__ int2 citem(ushort2 q) {
+  return make_int2(q.x, q.y == 0xFFFF ? -1 : q.y == 0xFFFE ? -2 : (int)q.y);
+}
+
+// the sum of one slot's items (list order), added to v; it: the slot's first item, the next one
+// 32 entries further (items interleaved per group of 32 slots)
+template <typename IT>
+__device__ __forceinline__ double slot_items(const BI &I, const IT *it, int cnt, double v) {
+  int k = 0;
+  for (; k + 4 <= cnt; k += 4) {  // four items' loads in flight, summed in list order
+    double a[4], m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int2 q = citem(it[(k + u) * 32]);
+      const bool wv = q.y < 0;
+      a[u] = wv ? I.Wv[q.x] : I.tJ[q.x];
+      m[u] = wv ? 1.0 : I.Jv[q.y];
+      if (q.y == -2) a[u] = m[u] = 0.0;  // padding
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v = fma(a[u], m[u], v);
+  }
+  for (; k < cnt; ++k) {
+    const int2 q = citem(it[k * 32]);
+    const bool wv = q.y < 0;
+    double a = wv ? I.Wv[q.x] : I.tJ[q.x], m = wv ? 1.0 : I.Jv[q.y];
+    if (q.y == -2) a = m = 0.0;
+    v = fma(a, m, v);
+  }
+  return v;
+}
+
 // K = W + Sigma_x + delta_w I + J^T D J into the lower slots of every panel of the instances in
 // the FACT phase (the diagonal block's upper triangle is never read), all slots of all instances
 // in one launch (slots are independent); the W item of a slot is taken as W * 1 so that every
@@ -607,29 +647,9 @@ __global__ void k_b_condense(const BI *bi, const BCtl *ctl) {
   for (int t = gtid; t < I.ncslot; t += gstride) {
     const int slot = I.cslot[t], j = I.ccol[t], g = t >> 5;
     double v = j >= 0 ? I.SA.sigma[j] + dw : 0.0;
-    const int2 *it = I.citems + I.cgptr[g] + (t & 31);
+    const int off = I.cgptr[g] + (t & 31);
     const int cnt = (I.cgptr[g + 1] - I.cgptr[g]) >> 5;
-    int k = 0;
-    for (; k + 4 <= cnt; k += 4) {  // four items' loads in flight, summed in list order
-      double a[4], m[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int2 q = it[(k + u) * 32];
-        const bool wv = q.y < 0;
-        a[u] = wv ? I.Wv[q.x] : I.tJ[q.x];
-        m[u] = wv ? 1.0 : I.Jv[q.y];
-        if (q.y == -2) a[u] = m[u] = 0.0;  // padding
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v = fma(a[u], m[u], v);
-    }
-    for (; k < cnt; ++k) {
-      const int2 q = it[k * 32];
-      const bool wv = q.y < 0;
-      double a = wv ? I.Wv[q.x] : I.tJ[q.x], m = wv ? 1.0 : I.Jv[q.y];
-      if (q.y == -2) a = m = 0.0;
-      v = fma(a, m, v);
-    }
+    v = I.citems16 ? slot_items(I, I.citems16 + off, cnt, v) : slot_items(I, I.citems + off, cnt, v);
     if (p32)
       reinterpret_cast<float *>(I.Lx)[slot] = (float)v;  // summed in FP64, rounded once
     else
@@ -1664,8 +1684,23 @@ __global__ void k_b_ctl_ls(const BI *bi, BCtl *ctl, int count, int resto_on, dou
   c.alpha = alpha * 0.5;
   if (c.alpha < c.amin) {
     // (no phase at a point already feasible within the tolerance: it cannot reduce a violation
-    // at rounding level)
-    if (rs || !resto_on || fmax(h[R_MAX_G], h[R_MAX_HS]) <= tol) {
+    // at rounding level; the direction is first recomputed with the next delta_w of this
+    // iteration's inertia-correction schedule, a better conditioned and more gradient-like
+    // step, at most MAX_LS_REGULARIZE times: the same iterate goes back to the factorization)
+    const bool feasible = fmax(h[R_MAX_G], h[R_MAX_HS]) <= tol;
+    if (!rs && resto_on && feasible && c.n_reg < MAX_LS_REGULARIZE) {
+      ++c.n_reg;
+      c.dw = c.next;
+      c.next *= c.grow;
+      if (c.dw >= 1e40) {
+        c.status = IPM_ERR_INERTIA;
+        c.ph = PH_DONE;
+        return;
+      }
+      c.ph = PH_FACT;
+      return;
+    }
+    if (rs || !resto_on || feasible) {
       c.status = IPM_ERR_RESTORATION;
       c.ph = PH_DONE;
       return;
@@ -2431,6 +2466,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
       pm(B->syms.size()), ptgt(B->syms.size()), g8p(B->syms.size()), g8s(B->syms.size());
   std::vector<int *> cslot(B->syms.size()), ccol(B->syms.size()), cgp(B->syms.size());
   std::vector<int2 *> citm(B->syms.size());
+  std::vector<ushort2 *> citm16(B->syms.size(), nullptr);
   std::vector<int> ncslot(B->syms.size());
   for (size_t q = 0; q < B->syms.size(); ++q) {
     ipm_sym_t S = B->syms[q];
@@ -2538,12 +2574,32 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     if (r1 == IPM_OK) r1 = upi(&ccol[q], hcc);
     if (r1 == IPM_OK) r1 = upi(&cgp[q], hgp);
     if (r1 != IPM_OK) return fail(r1);
-    if (cudaMalloc((void **)&citm[q], sizeof(int2) * std::max<size_t>(hci.size(), 1)) != cudaSuccess)
-      return fail(IPM_ERR_OOM);
-    B->bufs.push_back(citm[q]);
-    if (!hci.empty() && cudaMemcpy(citm[q], hci.data(), sizeof(int2) * hci.size(),
-                                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return fail(IPM_ERR_CUDA);
+    // 16-bit items when every J and W entry index of the pattern fits below 0xFFFE
+    int max_ix = 0;
+    for (const int2 &v : hci) max_ix = std::max(max_ix, std::max(v.x, v.y));
+    if (max_ix < 0xFFFE) {
+      std::vector<ushort2> h16(hci.size());
+      for (size_t t = 0; t < hci.size(); ++t)
+        h16[t] = make_ushort2((unsigned short)hci[t].x,
+                              hci[t].y == -1   ? (unsigned short)0xFFFF
+                              : hci[t].y == -2 ? (unsigned short)0xFFFE
+                                               : (unsigned short)hci[t].y);
+      if (cudaMalloc((void **)&citm16[q], sizeof(ushort2) * std::max<size_t>(h16.size(), 1)) !=
+          cudaSuccess)
+        return fail(IPM_ERR_OOM);
+      B->bufs.push_back(citm16[q]);
+      if (!h16.empty() && cudaMemcpy(citm16[q], h16.data(), sizeof(ushort2) * h16.size(),
+                                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(IPM_ERR_CUDA);
+    } else {
+      if (cudaMalloc((void **)&citm[q], sizeof(int2) * std::max<size_t>(hci.size(), 1)) !=
+          cudaSuccess)
+        return fail(IPM_ERR_OOM);
+      B->bufs.push_back(citm[q]);
+      if (!hci.empty() && cudaMemcpy(citm[q], hci.data(), sizeof(int2) * hci.size(),
+                                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(IPM_ERR_CUDA);
+    }
   }
   // level offsets of each pattern's supernode schedule, on the device
   std::vector<int *> lvl(B->syms.size(), nullptr);
@@ -2601,6 +2657,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.ccol = ccol[B->pat[i]];
     I.cgptr = cgp[B->pat[i]];
     I.citems = citm[B->pat[i]];
+    I.citems16 = citm16[B->pat[i]];
     I.ncslot = ncslot[B->pat[i]];
     I.y = d + o.y_s; I.t = d + o.t; I.cx = d + o.cx; I.cz = d + o.cz; I.outx = d + o.outx;
     I.outz = d + o.outz; I.scal = d + o.scal;

@@ -855,7 +855,14 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   SA.dv = S->dv;
   SA.dzl = S->dzl;
   SA.dzu = S->dzu;
-  for (int attempt = 0; attempt < 200; ++attempt) {
+  // a line search that fails at a point feasible within the tolerance sends the iteration back
+  // here with the schedule continued from its next candidate (resume), at most
+  // MAX_LS_REGULARIZE times
+  int n_reg = 0;
+  bool resume = false;
+retry_solve:
+  ok = false;
+  for (int attempt = resume ? 1 : 0; attempt < 200; ++attempt) {
     dw = attempt == 0 ? 0.0 : next;
     if (attempt > 0) next *= grow;
     if (dw >= 1e40) break;
@@ -970,7 +977,14 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
   info->theta = theta;
   if (!accepted) {
     // no restoration phase at a point already feasible within the tolerance: it cannot reduce
-    // a violation at rounding level (the method stops there)
+    // a violation at rounding level; the direction is recomputed with the next delta_w of this
+    // iteration's inertia-correction schedule (a better conditioned, more gradient-like step)
+    // at most MAX_LS_REGULARIZE times before the method stops there
+    if (!S->opt.no_resto && S->prim_inf <= S->opt.tol && n_reg < MAX_LS_REGULARIZE) {
+      ++n_reg;
+      resume = true;
+      goto retry_solve;
+    }
     if (S->opt.no_resto || S->prim_inf <= S->opt.tol) return IPM_ERR_RESTORATION;
     // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): the following calls iterate
     // on the restoration problem until its return test passes

@@ -19,6 +19,10 @@ static constexpr double GAMMA_ALPHA = 0.05, KAPPA_SIGMA = 1e10, KAPPA_SIGMA_INV 
 // values closer than that compare as equal (the Armijo test, the sufficient decrease and the
 // filter entries alike)
 static constexpr double PHI_MARGIN = 10.0 * 2.220446049250313e-16;
+// directions recomputed with the next delta_w of the iteration's inertia-correction schedule
+// after a line search that fails at a point feasible within the tolerance (where the
+// restoration phase cannot help), before the method stops there
+static constexpr int MAX_LS_REGULARIZE = 8;
 
 // Filter acceptance of a trial point (tht, pht) at step alpha from (theta, phi) with directional
 // derivative gphi (Waechter & Biegler 2006, Sec. 2.3-2.4): the filter (nfilter interleaved

@@ -167,3 +167,39 @@ def test_overloaded_grid_is_locally_infeasible(kkt):
     g3 = dataclasses.replace(g, pd=3 * g.pd, qd=3 * g.qd)
     res = ipm.solve(OPFModel(g3), ipm.Options(kkt=kkt))
     assert res.status == "infeasible"
+
+
+def test_failed_line_search_at_a_feasible_point_recomputes_a_regularized_direction(monkeypatch):
+    """A line search that fails at a point feasible within the tolerance cannot be helped by
+    the restoration phase; the iteration's direction is computed again with the next delta_w of
+    its inertia-correction schedule.  Pinned by planting an ascent direction (the negated
+    Newton step of the unregularized system) at a late, feasible iterate of the 30-bus solve:
+    the line search rejects every trial, the retry at delta_w = 1e-4 (the schedule's first
+    candidate when no earlier iteration needed one) is accepted, and the solve reaches the same
+    optimum.  Without the retry the same run stops there."""
+    g = config_grid("ring30")
+    ref = ipm.solve(OPFModel(g), ipm.Options(kkt="lifted"))
+    assert ref.status == "converged"
+    assert all(h["delta_w"] == 0 for h in ref.history[:31])
+    k_star = 30
+    orig = ipm.K.lifted_solve
+    calls = {"n": 0}
+
+    def planted(F, A, J, d, a, b, **kw):
+        dx, dz, hist = orig(F, A, J, d, a, b, **kw)
+        calls["n"] += 1
+        if calls["n"] == k_star + 1:      # the first direction of iteration k_star
+            return -dx, -dz, hist
+        return dx, dz, hist
+
+    monkeypatch.setattr(ipm.K, "lifted_solve", planted)
+    res = ipm.solve(OPFModel(g), ipm.Options(kkt="lifted"))
+    assert res.status == "converged"
+    assert abs(res.obj - ref.obj) <= 1e-8 * abs(ref.obj)
+    h = [e for e in res.history if e["k"] == k_star][0]
+    assert h["delta_w"] == 1e-4 and h["nfac"] >= 2, h
+    assert all(e["k"] != k_star or "resto" not in e for e in res.history)
+    calls["n"] = 0
+    monkeypatch.setattr(ipm, "MAX_LS_REGULARIZE", 0)
+    res0 = ipm.solve(OPFModel(g), ipm.Options(kkt="lifted"))
+    assert res0.status == "restoration_failed" and res0.iters == k_star
