@@ -177,7 +177,8 @@ int ipm_set_spin_limit(long long polls);
 int ipm_debug_add_dependency(ipm_sym_t sym, int supernode, int extra);
 
 /* ipm_solve — x = K^{-1} b with the factor: y = P b, L z = y, L^T w = z, x = P^T w.
- *   b [n], x [n] (may alias).  nrhs must be 1. */
+ *   b [n x nrhs], x [n x nrhs] device, column-major with leading dimension n (x may alias b);
+ *   nrhs >= 1 right-hand sides, solved one after another in stream order. */
 int ipm_solve(ipm_sym_t sym, ipm_num_t num, const double *b, double *x, int nrhs,
               cudaStream_t stream);
 
@@ -364,6 +365,18 @@ int ipm_state_create_at(ipm_opf_t opf, const ipm_options *opt, const double *x0,
 int ipm_step(ipm_state_t state, ipm_iter_info *host_info);
 /* Copies x [n] to a HOST buffer (NULL skipped) and the unscaled objective f(x) to *obj (HOST). */
 int ipm_state_export(ipm_state_t state, double *x, double *obj);
+/* Checkpoint of the iteration between two ipm_step calls (the paper has no counterpart; it reuses
+ * one symbolic analysis across solves of a pattern): the primal-dual iterate (x, s, y, z, v, zl,
+ * zu), the row scaling, mu, tau, the filter, delta_last, the iteration count and status, in one
+ * HOST buffer of doubles.  *len (HOST) receives the length needed; buf = NULL only asks for it.
+ * IPM_ERR_BAD_ARG when cap is smaller, or while the state is in the restoration phase.
+ * Synchronizes. */
+int ipm_state_save(ipm_state_t state, double *buf, int64_t cap, int64_t *len);
+/* Puts a saved checkpoint into a state created for the same model and options (sizes, format
+ * and length checked: IPM_ERR_BAD_ARG otherwise); the next ipm_step continues the saved
+ * iteration.  A checkpoint taken after the FP32 factor stopped serving continues in FP64.
+ * Synchronizes. */
+int ipm_state_load(ipm_state_t state, const double *buf, int64_t len);
 /* Copies the KKT system that the last completed ipm_step solved, and its solution, to HOST
  * buffers (any pointer may be NULL).  The system is the augmented system (K_2) with the slack
  * block eliminated (Sec. 2.2, the system that iterative refinement runs on; Sec. 3.1-3.2):

@@ -57,6 +57,8 @@ _SIGS = {
     "ipm_state_create_at": (I, [P, P, P, P, P]),
     "ipm_step": (I, [P, P]),
     "ipm_state_export": (I, [P, P, P]),
+    "ipm_state_save": (I, [P, P, I64, P]),
+    "ipm_state_load": (I, [P, P, I64]),
     "ipm_state_export_kkt": (I, [P] * 11),
     "ipm_state_destroy": (None, [P]),
     "ipm_batch_create": (I, [I, P, P, P, P]),
@@ -273,7 +275,13 @@ def ipm_factor(sym, num, d_info, stream=None):
 
 
 def ipm_solve(sym, num, b, x, stream=None):
-    return _check(lib().ipm_solve(sym.h, num.h, _ptr(b), _ptr(x), 1, _stream(stream)), "ipm_solve")
+    """x = K^{-1} b; b, x: [n] or [nrhs, n] contiguous float64 CUDA tensors (each row one
+    right-hand side: the C-ABI's column-major n x nrhs)."""
+    nrhs = 1 if b.dim() == 1 else int(b.shape[0])
+    if tuple(x.shape) != tuple(b.shape) or b.shape[-1] != sym.n:
+        raise ValueError("ipm_solve: b and x must both be [n] or [nrhs, n]")
+    return _check(lib().ipm_solve(sym.h, num.h, _ptr(b), _ptr(x), nrhs, _stream(stream)),
+                  "ipm_solve")
 
 
 def ipm_solve_noalloc(sym, num, b, x, d_status=None, stream=None):
@@ -385,6 +393,21 @@ class IpmState:
         out = np.zeros(self.opf.n)
         _check(lib().ipm_state_export(self.h, out.ctypes.data_as(ctypes.c_void_p), None), "export")
         return out
+
+    def save(self):
+        """Checkpoint of the iteration (ipm_state_save) as a float64 array."""
+        n = I64()
+        _check(lib().ipm_state_save(self.h, None, 0, ctypes.byref(n)), "ipm_state_save")
+        buf = np.zeros(n.value)
+        _check(lib().ipm_state_save(self.h, buf.ctypes.data_as(ctypes.c_void_p), n.value,
+                                    ctypes.byref(n)), "ipm_state_save")
+        return buf
+
+    def load(self, buf):
+        """Continue from a checkpoint of save() (ipm_state_load)."""
+        buf = np.ascontiguousarray(buf, dtype=np.float64)
+        _check(lib().ipm_state_load(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.size),
+               "ipm_state_load")
 
     def objective(self):
         v = D()

@@ -106,8 +106,8 @@ struct BI {
   // that a warp's item loads are coalesced and its lanes loop over equal counts
   const int *cslot, *ccol, *cgptr;
   const int2 *citems;
-  // the same items as two 16-bit indices (W item: y = 0xFFFF, padding: y = 0xFFFE) when every
-  // index of the pattern fits, else null: half the bytes of the condensation's index stream
+  // the same items as two 16-bit indices (x, y + 2) when every index of the pattern fits, else
+  // null: half the bytes of the condensation's index stream
   const ushort2 *citems16;
   int ncslot;
   const int64_t *lptr, *dptr;
@@ -603,9 +603,7 @@ __global__ void k_b_scale_jv(const BI *bi, const BCtl *ctl) {
 // ------------------------------------------------------------------ condensation
 // one condensation item as (x, y): (J entry p, J entry q), (W entry, -1) or padding (-, -2)
 __device__ __forceinline__ int2 citem(int2 q) { return q; }
-__device__ __forceinline__ int2 citem(ushort2 q) {
-  return make_int2(q.x, q.y == 0xFFFF ? -1 : q.y == 0xFFFE ? -2 : (int)q.y);
-}
+__device__ __forceinline__ int2 citem(ushort2 q) { return make_int2(q.x, (int)q.y - 2); }
 
 // the sum of one slot's items (list order), added to v; it: the slot's first item, the next one
 // 32 entries further (items interleaved per group of 32 slots)
@@ -2574,16 +2572,16 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     if (r1 == IPM_OK) r1 = upi(&ccol[q], hcc);
     if (r1 == IPM_OK) r1 = upi(&cgp[q], hgp);
     if (r1 != IPM_OK) return fail(r1);
-    // 16-bit items when every J and W entry index of the pattern fits below 0xFFFE
-    int max_ix = 0;
-    for (const int2 &v : hci) max_ix = std::max(max_ix, std::max(v.x, v.y));
-    if (max_ix < 0xFFFE) {
+    // 16-bit items (x, y + 2) when every J and W entry index of the pattern fits
+    int max_x = 0, max_y = 0;
+    for (const int2 &v : hci) {
+      max_x = std::max(max_x, v.x);
+      max_y = std::max(max_y, v.y);
+    }
+    if (max_x <= 0xFFFF && max_y + 2 <= 0xFFFF) {
       std::vector<ushort2> h16(hci.size());
       for (size_t t = 0; t < hci.size(); ++t)
-        h16[t] = make_ushort2((unsigned short)hci[t].x,
-                              hci[t].y == -1   ? (unsigned short)0xFFFF
-                              : hci[t].y == -2 ? (unsigned short)0xFFFE
-                                               : (unsigned short)hci[t].y);
+        h16[t] = make_ushort2((unsigned short)hci[t].x, (unsigned short)(hci[t].y + 2));
       if (cudaMalloc((void **)&citm16[q], sizeof(ushort2) * std::max<size_t>(h16.size(), 1)) !=
           cudaSuccess)
         return fail(IPM_ERR_OOM);

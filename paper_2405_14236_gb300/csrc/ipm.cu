@@ -1039,6 +1039,96 @@ extern "C" int ipm_state_export(ipm_state_t S, double *x, double *obj) {
   return IPM_OK;
 }
 
+// ---- checkpoint / resume: the iterate and the host-side algorithm state in one flat host
+// buffer of doubles: a header (format tag, version, sizes, scalars, filter length), the filter
+// entries, then x, s, y, z, v, zl, zu and the row scaling
+static constexpr double STATE_TAG = 2405.14236;
+static constexpr int STATE_HEAD = 18;
+
+static int64_t state_len(const ipm_state_t S) {
+  const Dims &D = S->D;
+  return STATE_HEAD + (int64_t)S->filter.size() + 3 * (int64_t)D.n + 3 * (int64_t)D.mi + D.me +
+         D.me0 + D.mi0;
+}
+
+extern "C" int ipm_state_save(ipm_state_t S, double *buf, int64_t cap, int64_t *len) {
+  if (!S || !len) return IPM_ERR_BAD_ARG;
+  if (S->in_resto) {
+    set_error_msg("ipm_state_save: the state is in the restoration phase (save between main "
+                  "iterations)");
+    return IPM_ERR_BAD_ARG;
+  }
+  const int64_t need = state_len(S);
+  *len = need;
+  if (!buf) return IPM_OK;
+  if (cap < need) {
+    set_error_msg("ipm_state_save: buffer too small");
+    return IPM_ERR_BAD_ARG;
+  }
+  const Dims &D = S->D;
+  const double head[STATE_HEAD] = {STATE_TAG, 1.0, (double)D.n, (double)D.me, (double)D.mi,
+                                   (double)(D.me0 + D.mi0), S->sig, S->mu, S->tau, S->delta_last,
+                                   S->theta_max, S->theta_min, S->have_theta0 ? 1.0 : 0.0,
+                                   (double)S->k, (double)S->status, S->num32 ? 1.0 : 0.0,
+                                   S->prim_inf, (double)S->filter.size()};
+  std::copy(head, head + STATE_HEAD, buf);
+  double *o = buf + STATE_HEAD;
+  std::copy(S->filter.begin(), S->filter.end(), o);
+  o += S->filter.size();
+  CK(cudaStreamSynchronize(S->stream));
+  const std::pair<const double *, int64_t> parts[] = {
+      {S->P.x, D.n}, {S->P.s, D.mi}, {S->P.y, D.me}, {S->P.z, D.mi}, {S->P.v, D.mi},
+      {S->P.zl, D.n}, {S->P.zu, D.n}, {S->dscale, D.me0 + D.mi0}};
+  for (const auto &pt : parts) {
+    if (pt.second > 0)
+      CK(cudaMemcpy(o, pt.first, sizeof(double) * pt.second, cudaMemcpyDeviceToHost));
+    o += pt.second;
+  }
+  return IPM_OK;
+}
+
+extern "C" int ipm_state_load(ipm_state_t S, const double *buf, int64_t len) {
+  if (!S || !buf || len < STATE_HEAD) return IPM_ERR_BAD_ARG;
+  const Dims &D = S->D;
+  if (buf[0] != STATE_TAG || buf[1] != 1.0 || buf[2] != D.n || buf[3] != D.me ||
+      buf[4] != D.mi || buf[5] != D.me0 + D.mi0 || !(buf[17] >= 0) ||
+      len != STATE_HEAD + (int64_t)buf[17] + 3 * (int64_t)D.n + 3 * (int64_t)D.mi + D.me +
+                 D.me0 + D.mi0) {
+    set_error_msg("ipm_state_load: not a saved state of this model and formulation");
+    return IPM_ERR_BAD_ARG;
+  }
+  S->sig = buf[6];
+  S->mu = buf[7];
+  S->tau = buf[8];
+  S->delta_last = buf[9];
+  S->theta_max = buf[10];
+  S->theta_min = buf[11];
+  S->have_theta0 = buf[12] != 0.0;
+  S->k = (int)buf[13];
+  S->status = (int)buf[14];
+  S->prim_inf = buf[16];
+  const int64_t nf = (int64_t)buf[17];
+  S->filter.assign(buf + STATE_HEAD, buf + STATE_HEAD + nf);
+  const double *o = buf + STATE_HEAD + nf;
+  const std::pair<double *, int64_t> parts[] = {
+      {S->P.x, D.n}, {S->P.s, D.mi}, {S->P.y, D.me}, {S->P.z, D.mi}, {S->P.v, D.mi},
+      {S->P.zl, D.n}, {S->P.zu, D.n}, {S->dscale, D.me0 + D.mi0}};
+  CK(cudaStreamSynchronize(S->stream));
+  for (const auto &pt : parts) {
+    if (pt.second > 0)
+      CK(cudaMemcpy(pt.first, o, sizeof(double) * pt.second, cudaMemcpyHostToDevice));
+    o += pt.second;
+  }
+  // a state saved after its FP32 factor had stopped serving goes on in FP64
+  if (buf[15] == 0.0 && S->num32) {
+    ipm_num_destroy(S->num32);
+    S->num32 = nullptr;
+  }
+  S->in_resto = false;
+  S->have_kkt = false;
+  return IPM_OK;
+}
+
 extern "C" int ipm_state_export_kkt(ipm_state_t S, double *W_val, double *sigma, double *J_val,
                                     double *d_row, double *delta_w, double *a, double *b,
                                     double *dx, double *dyz, int *m_e) {

@@ -304,8 +304,12 @@ static int solve_full(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cuda
 
 extern "C" int ipm_solve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, int nrhs,
                          cudaStream_t s) {
-  if (!S || !N || N->sym != S || !b || !x || nrhs != 1) return IPM_ERR_BAD_ARG;
-  return solve_full(S, N, b, x, s);
+  if (!S || !N || N->sym != S || !b || !x || nrhs < 1) return IPM_ERR_BAD_ARG;
+  // the columns one after another (each solve is one forward and one backward launch that
+  // read the factor once)
+  for (int k = 0; k < nrhs; ++k)
+    CKR(solve_full(S, N, b + (int64_t)k * S->n, x + (int64_t)k * S->n, s));
+  return IPM_OK;
 }
 
 // --- K x = b solved to FP64 accuracy with an FP32 factor: conjugate gradients in FP64 on K

@@ -65,3 +65,34 @@ def test_gpu_hykkt_automatic_gamma_matches_oracle():
     if want == 1:
         assert abs(res["iters"] - ref.iters) <= max(3, ref.iters // 5)
     assert abs(res["obj"] - ref.obj) <= 1e-6 * abs(ref.obj)
+
+
+@pytest.mark.parametrize("kkt", ["lifted", "hykkt"])
+def test_checkpoint_resume_continues_the_iteration(kkt):
+    """ipm_state_save after 12 iterations, loaded into a fresh state of the same model: the
+    resumed solve ends where the uninterrupted one does (same optimum, iteration counts within
+    rounding), a checkpoint round-trips unchanged, and a checkpoint of another model is
+    refused."""
+    g = config_grid("planar1k")
+    opf = cp.Opf(g)
+    a = cp.IpmState(opf, kkt=kkt, gamma=1e6)
+    for _ in range(12):
+        assert a.step().status == 0
+    ck = a.save()
+    while True:
+        info = a.step()
+        if info.status != 0:
+            break
+    assert info.status == 1
+    b = cp.IpmState(opf, kkt=kkt, gamma=1e6)
+    b.load(ck)
+    assert np.array_equal(b.save(), ck)
+    while True:
+        ib = b.step()
+        if ib.status != 0:
+            break
+    assert ib.status == 1 and abs(ib.k - info.k) <= 2, (ib.k, info.k)
+    assert abs(b.objective() - a.objective()) <= 1e-9 * abs(a.objective())
+    other = cp.IpmState(cp.Opf(config_grid("ring30")), kkt=kkt, gamma=1e6)
+    with pytest.raises(cp.CondipmError):
+        other.load(ck)

@@ -171,6 +171,15 @@ def test_factor_backward_stable_and_solve(name):
     Kf = K.condensed_matrix(c["Wf"], c["sigma"], c["J"], c["d"], c["dw"])
     eta = np.abs(Kf @ xs - b).max() / (abs(Kf).sum(axis=1).max() * np.abs(xs).max() + np.abs(b).max())
     assert eta < 1e-13
+    # several right-hand sides in one call (columns of an n x 3 column-major block, solved in
+    # place): each equals its own single solve
+    B3 = rng.standard_normal((3, S.n))
+    X3 = dev(B3, torch.float64)
+    cp.ipm_solve(S, N, X3, X3)
+    for k in range(3):
+        xk = torch.zeros(S.n, dtype=torch.float64, device="cuda")
+        cp.ipm_solve(S, N, dev(B3[k], torch.float64), xk)
+        assert torch.equal(X3[k], xk)
 
 
 @pytest.mark.parametrize("name", ["ring30", "planar1k", "planar10k"])
