@@ -2305,6 +2305,7 @@ int init_instances(ipm_batch_t B) {
 
 extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_options *opt,
                                 cudaStream_t stream, ipm_batch_t *out) {
+  NvtxRange nvtx_range("ipm_batch_create");
   if (count <= 0 || !opfs || !opt || !out || opt->kkt < 0 || opt->kkt > 2 ||
       !(opt->tol > 0) || (opt->kkt != 0 && !(opt->gamma > 0))) {
     set_error_msg("ipm_batch_create: bad argument (count > 0, kkt = 0 (LiftedKKT), 1 (HyKKT, "
@@ -2753,6 +2754,7 @@ extern "C" int ipm_batch_reset(ipm_batch_t B) {
 }
 
 extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int use_graph) {
+  NvtxRange nvtx_range("ipm_batch_run");
   if (!B || max_iter < 0 || max_sweeps < 1) return IPM_ERR_BAD_ARG;
   cudaStream_t s = B->stream;
   if (B->max_iter != max_iter) drop_graph(B);
@@ -2792,6 +2794,7 @@ extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int us
 
 extern "C" int ipm_batch_autotune(ipm_batch_t B, int sweeps, int max_results, int *n_results,
                                   int *cfg, double *ms_per_sweep, int *best) {
+  NvtxRange nvtx_range("ipm_batch_autotune");
   if (!B || sweeps < 1 || max_results < 0 || (max_results > 0 && (!cfg || !ms_per_sweep)))
     return IPM_ERR_BAD_ARG;
   struct Shape { int cl, num, den, gx; };

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/condipm.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace cipm {
 
@@ -174,5 +175,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// NVTX range over a host-side phase of an entry point (the paper's phase timers: analysis,
+// condensation, factorization, solves, CG, IPM iteration, batched sweep); a profiler shows them,
+// and without one they cost a call into an empty injection point
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace cipm

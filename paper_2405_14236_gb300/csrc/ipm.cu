@@ -1005,6 +1005,7 @@ retry_solve:
 }
 
 extern "C" int ipm_step(ipm_state_t S, ipm_iter_info *info) {
+  NvtxRange nvtx_range("ipm_step");
   if (!S || !info) return IPM_ERR_BAD_ARG;
   if (S->status != 0) {
     *info = ipm_iter_info{};

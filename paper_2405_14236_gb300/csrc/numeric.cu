@@ -180,6 +180,7 @@ static int condense_t(ipm_sym_t S, ipm_num_t N, const double *W_val, const doubl
 extern "C" int ipm_condense(ipm_sym_t S, ipm_num_t N, const double *W_val, const double *sigma_x,
                             const double *J_val, const double *d_row, double delta_w,
                             cudaStream_t s) {
+  NvtxRange nvtx_range("ipm_condense");
   if (!S || !N || N->sym != S || !sigma_x || (S->nnzW && !W_val) || (S->nnzJ && (!J_val || !d_row)))
     return IPM_ERR_BAD_ARG;
   N->cW = W_val;
@@ -235,6 +236,7 @@ static int factor_t(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s) {
 }
 
 extern "C" int ipm_factor(ipm_sym_t S, ipm_num_t N, int *d_info, cudaStream_t s) {
+  NvtxRange nvtx_range("ipm_factor");
   if (!S || !N || N->sym != S || !d_info) return IPM_ERR_BAD_ARG;
   const int ns = S->nsuper;
   // counters of the factorization (update arrivals, panel tasks done), its ticket, abort, status
@@ -304,6 +306,7 @@ static int solve_full(ipm_sym_t S, ipm_num_t N, const double *b, double *x, cuda
 
 extern "C" int ipm_solve(ipm_sym_t S, ipm_num_t N, const double *b, double *x, int nrhs,
                          cudaStream_t s) {
+  NvtxRange nvtx_range("ipm_solve");
   if (!S || !N || N->sym != S || !b || !x || nrhs < 1) return IPM_ERR_BAD_ARG;
   // the columns one after another (each solve is one forward and one backward launch that
   // read the factor once)
@@ -518,6 +521,7 @@ extern "C" int ipm_aug_solve(ipm_sym_t S, ipm_num_t N, const double *W_val, cons
                              const double *a, const double *b, double *dx, double *dz,
                              int max_refine, double tol, double *d_eta, int *d_steps,
                              cudaStream_t s) {
+  NvtxRange nvtx_range("ipm_aug_solve");
   if (!S || !N || N->sym != S || !a || !dx || !sigma_x || (S->m && (!b || !dz || !d_row)) ||
       max_refine < 0)
     return IPM_ERR_BAD_ARG;
@@ -732,6 +736,7 @@ extern "C" int hykkt_cg(ipm_sym_t S, ipm_num_t N, int m_e, const double *J_val,
                         const double *d_row, double gamma, const double *a, const double *b,
                         double rtol, int maxit, double *dx, double *dy, double *dz, int *h_iters,
                         double *h_relres, cudaStream_t s) {
+  NvtxRange nvtx_range("hykkt_cg");
   const int n = S ? S->n : 0, m = S ? S->m : 0;
   if (!S || !N || N->sym != S || m_e < 0 || m_e > m || !a || !dx || (m && (!b || !d_row)) ||
       (m_e && !dy) || (m > m_e && !dz) || maxit < 0)

@@ -1212,6 +1212,7 @@ extern "C" int ipm_symbolic_relaxed(int n, int m, const int *J_rowptr, const int
                                     int nnzJ, const int *W_rowptr, const int *W_colind, int nnzW,
                                     int relax_w, int relax_den, cudaStream_t stream,
                                     ipm_sym_t *out) {
+  NvtxRange nvtx_range("ipm_symbolic");
   if (!out || n <= 0 || m < 0 || nnzJ < 0 || nnzW < 0 || !J_rowptr || !W_rowptr ||
       (nnzJ > 0 && !J_colind) || (nnzW > 0 && !W_colind) || relax_w < 1 ||
       relax_w > CIPM_SN_MAXW || relax_den < 0) {

@@ -172,14 +172,17 @@ def test_factor_backward_stable_and_solve(name):
     eta = np.abs(Kf @ xs - b).max() / (abs(Kf).sum(axis=1).max() * np.abs(xs).max() + np.abs(b).max())
     assert eta < 1e-13
     # several right-hand sides in one call (columns of an n x 3 column-major block, solved in
-    # place): each equals its own single solve
+    # place): each equals its own single solve up to the order of the solves' atomic sums
     B3 = rng.standard_normal((3, S.n))
     X3 = dev(B3, torch.float64)
     cp.ipm_solve(S, N, X3, X3)
     for k in range(3):
         xk = torch.zeros(S.n, dtype=torch.float64, device="cuda")
         cp.ipm_solve(S, N, dev(B3[k], torch.float64), xk)
-        assert torch.equal(X3[k], xk)
+        assert float((X3[k] - xk).abs().max()) <= 1e-12 * float(xk.abs().max())
+        e = np.abs(Kf @ X3[k].cpu().numpy() - B3[k]).max() / (
+            abs(Kf).sum(axis=1).max() * np.abs(X3[k].cpu().numpy()).max() + np.abs(B3[k]).max())
+        assert e < 1e-13
 
 
 @pytest.mark.parametrize("name", ["ring30", "planar1k", "planar10k"])
