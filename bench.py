@@ -32,8 +32,13 @@ sys.path.insert(0, ROOT)
 METRIC = "IPM solves/s at 1e-6 KKT tol, plain vs batched/warm-start; factor GB/s"
 UNIT = "IPM solves/s"
 KKT_UNIT = "KKT solves/s"
-WORKLOAD = ("batch320-lifted: 256 load scenarios of a seeded 1,000-bus grid + 64 seeded grids of "
-            "118-2,000 buses, batched LiftedKKT FP64 IPM to 1e-6 scaled KKT tolerance")
+FORM_NAMES = {"lifted": "LiftedKKT", "regularized": "dual-regularized condensed (delta_c = 1/gamma, "
+               "gamma = 1e6)", "hykkt": "HyKKT (gamma = 1e6)"}
+
+
+def workload_name(kkt):
+    return (f"batch320-{kkt}: 256 load scenarios of a seeded 1,000-bus grid + 64 seeded grids of "
+            f"118-2,000 buses, batched {FORM_NAMES[kkt]} FP64 IPM to 1e-6 scaled KKT tolerance")
 KKT_WORKLOAD = ("kkt10k-lifted: LiftedKKT condensed KKT solve (condense + supernodal Cholesky + "
                 "FP64-refined solve) on a seeded synthetic 10,000-bus grid, Sigma log-uniform "
                 "[1e-8,1e8]")
@@ -154,10 +159,10 @@ def kkt_cpu_baseline(budget_s=8.0, min_solves=3):
                       f"single thread; host has {os.cpu_count()} cores)"}
 
 
-def _oracle_solve(grid):
+def _oracle_solve(grid, kkt="lifted"):
     from oracle.opf import OPFModel
     from oracle import ipm as oipm
-    r = oipm.solve(OPFModel(grid), oipm.Options(kkt="lifted"))
+    r = oipm.solve(OPFModel(grid), oipm.Options(kkt=kkt, gamma=1e6))
     return r.status == "converged", r.iters
 
 
@@ -165,9 +170,9 @@ def _oracle_solve_seed(spec):
     """Pool worker (spawned process): rebuild the instance from its seeds and solve it."""
     sys.path.insert(0, ROOT)
     from synth import config_grid, scale_loads, mixed_grid
-    kind, seed = spec
+    kind, seed, kkt = spec
     g = scale_loads(config_grid("planar1k"), seed) if kind == "scen" else mixed_grid(seed)
-    return _oracle_solve(g)
+    return _oracle_solve(g, kkt)
 
 
 def sample_specs(k, part=0):
@@ -179,7 +184,7 @@ def sample_specs(k, part=0):
     return out
 
 
-def batch_cpu_baseline(budget_s=10.0, pool=True):
+def batch_cpu_baseline(budget_s=10.0, pool=True, kkt="lifted"):
     """The oracle IPM (plain FP64 CPU, simple sparse LDL^T) on a bounded sample of the batched
     workload: one thread, then (pool) one problem per host core in spawned processes."""
     from synth import config_grid, scale_loads, mixed_grid
@@ -189,7 +194,7 @@ def batch_cpu_baseline(budget_s=10.0, pool=True):
     while k < 2 or (time.perf_counter() - t0 < budget_s and k < len(specs)):
         kind, seed = specs[k]
         g = scale_loads(config_grid("planar1k"), seed) if kind == "scen" else mixed_grid(seed)
-        ok, _ = _oracle_solve(g)
+        ok, _ = _oracle_solve(g, kkt)
         conv += ok
         k += 1
     el = time.perf_counter() - t0
@@ -200,7 +205,7 @@ def batch_cpu_baseline(budget_s=10.0, pool=True):
     if pool:
         import multiprocessing as mp
         cores = os.cpu_count() or 1
-        specs = sample_specs(2 * cores)
+        specs = [(kind, seed, kkt) for kind, seed in sample_specs(2 * cores)]
         ctx = mp.get_context("spawn")
         with ctx.Pool(cores) as P:
             P.map(_oracle_solve_seed, specs[:cores])  # start-up and imports, untimed
@@ -224,11 +229,11 @@ def run_reference(args, rank, world):
     grids = [scale_loads(config_grid("planar1k"), s_) if k_ == "scen" else mixed_grid(s_)
              for k_, s_ in specs]
     for i in range(args.warmup):
-        _oracle_solve(grids[i])
+        _oracle_solve(grids[i], args.kkt)
     t0 = time.perf_counter()
     conv = 0
     for i in range(args.steps):
-        ok, _ = _oracle_solve(grids[args.warmup + i])
+        ok, _ = _oracle_solve(grids[args.warmup + i], args.kkt)
         conv += ok
     el = time.perf_counter() - t0
     v = conv / el
@@ -236,7 +241,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "one instance per step, one thread"},
+            "config": {"workload": workload_name(args.kkt),
+                       "parallelism": "one instance per step, one thread"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} instances of the batched workload, "
                                        f"{conv} converged, single thread"},
@@ -457,12 +463,11 @@ def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3, precision=6
     import paper_2405_14236_gb300 as cp
     opfs = [cp.Opf(g) for g in grids]
     B = cp.Batch(opfs, kkt=kkt, gamma=gamma, precision=precision, relax=relax)
-    shape = None
-    if precision == 32:
-        tune = B.autotune(sweeps=8)
-        best = tune["candidates"][tune["best"]]
-        shape = {k: best[k] for k in ("cluster", "threshold", "blocks_per_instance")}
-        B.set_timing(True)
+    # launch shapes tuned for this form, as for the headline
+    tune = B.autotune(sweeps=8)
+    best = tune["candidates"][tune["best"]]
+    shape = {k: best[k] for k in ("cluster", "threshold", "blocks_per_instance")}
+    B.set_timing(True)
     B.run(max_iter=MAX_ITER)
     B.kernel_time()
     stream = torch.cuda.current_stream()
@@ -481,24 +486,24 @@ def batch_form_measure(grids, kkt="regularized", gamma=1e6, steps=3, precision=6
         r = B.results()
         conv.append(int((r["status"] == 1).sum()))
         its.append(float(r["iters"].mean()))
+        kt = B.kernel_time()
+        fact_ms += kt["fact_ms"]
+        solve_ms += kt["solve_ms"]
+        n_sw += kt["sweeps"]
         if precision == 32:
-            kt = B.kernel_time()
-            fact_ms += kt["fact_ms"]
-            solve_ms += kt["solve_ms"]
-            n_sw += kt["sweeps"]
             pr = B.solve_info()
             it32 += int(pr["iters32"].sum())
             it_all += int(r["iters"].sum())
             n64 += int((pr["k64"] >= 0).sum())
     out = {"kkt": kkt, "gamma": gamma, "value": float(np.sum(conv) / (np.sum(ms) / 1e3)),
            "unit": UNIT, "converged_per_step": conv, "iters_mean": float(np.mean(its)),
-           "ms_per_step": float(np.mean(ms)), "sweeps": int(r["sweeps"])}
+           "ms_per_step": float(np.mean(ms)), "sweeps": int(r["sweeps"]),
+           "launch_shape": shape, "relax": list(relax),
+           "kernels_ms_per_sweep": {"factor_both_rounds": fact_ms / max(n_sw, 1),
+                                    "solve_first": solve_ms / max(n_sw, 1)}}
     if precision == 32:
         out.update({"precision": "FP32 condensed matrix, factor and triangular solves; FP64 "
                                  "Richardson refinement on the augmented system to 1e-10",
-                    "launch_shape": shape,
-                    "kernels_ms_per_sweep": {"factor_both_rounds": fact_ms / max(n_sw, 1),
-                                             "solve_first": solve_ms / max(n_sw, 1)},
                     "fp32_share_of_iterations": it32 / max(it_all, 1),
                     "instances_gone_fp64_per_step": n64 / steps})
     if kkt == "hykkt":
@@ -591,11 +596,11 @@ def run_gpu(args, rank, world, local_rank):
     elif not args.no_autotune and not args.launch_shape:
         from paper_2405_14236_gb300 import tune
         t0 = time.perf_counter()
-        relax, recs = tune.supernode_shapes(opfs)
+        relax, recs = tune.supernode_shapes(opfs, kkt=args.kkt, gamma=1e6)
         sn_tune = {"relax": list(relax), "candidates": recs,
                    "tune_s": time.perf_counter() - t0}
     t0 = time.perf_counter()
-    B = cp.Batch(opfs, relax=relax)
+    B = cp.Batch(opfs, relax=relax, kkt=args.kkt, gamma=1e6)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
     # launch shapes chosen by measurement (outside the timed steps, like the symbolic analyses)
@@ -725,7 +730,7 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
         "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD,
+        "config": {"workload": workload_name(args.kkt),
                    "instances": len(all_grids) if split else len(grids),
                    "patterns": info["patterns"],
                    "tol": 1e-6, "max_iter": MAX_ITER, "pool_bytes": info["device_bytes"],
@@ -777,8 +782,10 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_fp32:
         line["batch_fp32"] = batch_form_measure(grids, kkt="lifted", precision=32, relax=relax)
     if not args.no_forms:
-        line["batch_regularized"] = batch_form_measure(grids)
-        line["batch_hykkt"] = batch_form_measure(grids, kkt="hykkt")
+        # the other batched KKT forms on the same instances
+        for form in ("lifted", "regularized", "hykkt"):
+            if form != args.kkt:
+                line[f"batch_{form}"] = batch_form_measure(grids, kkt=form, relax=relax)
     if not args.no_forms:
         line["batch_recipe"] = recipe_measure()
     if not args.no_warm:
@@ -791,7 +798,7 @@ def run_gpu(args, rank, world, local_rank):
         line["ipm"] = ipm_measure(include_oracle=not args.no_cpu_baseline)
         line["sweeps"] = sweep_measure()
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cb = batch_cpu_baseline()
+        line["cpu_baseline"] = cb = batch_cpu_baseline(kkt=args.kkt)
         # the oracle on all host cores next to the one-thread figure: context for the ratio
         line["vs_cpu"] = {"one_thread": value / cb["value"],
                           "all_cores": value / cb["pool"]["value"] if "pool" in cb else None,
@@ -987,6 +994,10 @@ def main():
     ap.add_argument("--launch-shape", default="",
                     help="CL,NUM,DEN: fixed launch shape (clusters of CL blocks for instances above "
                          "NUM/DEN times the median supernode count) instead of the autotuner")
+    ap.add_argument("--kkt", default="regularized", choices=["lifted", "regularized", "hykkt"],
+                    help="KKT form of the headline batch (and of the oracle in the reference arm); "
+                         "default: the dual-regularized condensed form, the fastest of the three "
+                         "on this workload")
     ap.add_argument("--relax", default="",
                     help="W,DEN: fixed supernode relaxation (profiling) instead of the tuned one")
     ap.add_argument("--split", action="store_true",

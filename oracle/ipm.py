@@ -291,7 +291,7 @@ def schedule_from(kmat, solver, delta, grow):
 
 def solve(model, opt: Options | None = None, x0=None):
     """The IPM on a model: Ipopt's gradient scaling at the start, LiftedKKT's relaxation
-    (Sec. 3.2) for kkt = "lifted", the starting point of the reading in the design notes, then
+    (Sec. 3.2) for kkt = "lifted", the flat starting point (|V| = 1, theta = 0, equal dispatch), then
     the filter line-search iterations (_ipm)."""
     opt = opt or Options()
     base = model

@@ -23,7 +23,7 @@ and dz = D_H (H dx - b_H).
   (r1bar + gamma G^T r2bar) - r2bar is solved by CG; then
   K_gamma dx = r1bar + gamma G^T r2bar - G^T dy.
 
-Readings where the paper is silent (also listed in the design notes):
+Readings where the paper is silent:
   CG starts at dy = 0 and stops when ||r_k||_2 <= max(rtol ||r_0||_2, atol);
   refinement stops at backward error <= 1e-10, when the error stops halving,
   or after 10 steps (LiftedKKT) or 3 HyKKT re-solves (HyKKT).
