@@ -525,15 +525,17 @@ void ipm_batch_destroy(ipm_batch_t batch);
 
 /* ---------------------------------------------------------------- learned warm start
  * Rows for training and prediction: per instance x (n), log s (m_i), log v (m_i), log zl (n),
- * log zu (n), 0 where a bound is absent (width 3 n + 2 m_i; the iterate of the scaled problem as
- * the batched IPM holds it).  ipm_batch_state_rows writes every instance's row into the DEVICE
+ * log zu (n), 0 where a bound is absent (width 3 n + 2 m_i, + m_e below; the iterate of the
+ * scaled problem as the batched IPM holds it).  ipm_batch_state_rows writes every instance's row into the DEVICE
  * float matrix out (row stride ld >= width; out NULL only reports *width); all instances must
- * have the same sizes; LiftedKKT batches only (IPM_ERR_BAD_ARG otherwise).  Stream-ordered. */
+ * have the same sizes.  HyKKT and dual-regularized batches append the equality multipliers y
+ * (m_e values, not logged) to the row.  Stream-ordered. */
 int ipm_batch_state_rows(ipm_batch_t batch, float *out, int64_t ld, int *width);
 /* Starts every instance from a predicted row (DEVICE float matrix pred, row stride ld, values
  * de-normalized as pred * stdv + mean per column when mean != NULL, else taken as they are):
  * x pushed inside its bounds (the push of the cold start), s = exp(log s), z = v = exp(log v),
- * zl, zu = exp(.) where the bound exists, mu0 = s^T v / m_i (at least tol / 10), a fresh filter.
+ * zl, zu = exp(.) where the bound exists, y from the row's last m_e values (HyKKT and the
+ * dual-regularized form), mu0 = s^T v / m_i (at least tol / 10), a fresh filter.
  * Call after ipm_batch_reset (which sets the scaling at the cold start point); an instance whose
  * row holds a non-finite value keeps its cold start.  h_used (HOST, count, may be NULL) receives
  * 1 where the prediction was used.  Synchronizes. */

@@ -560,7 +560,8 @@ class Batch:
         return dict(factor_flops=ff, condense_flops=cf, bytes=by)
 
     def state_rows(self, out=None):
-        """Every instance's (x, log s, log v, log zl, log zu) as a float32 CUDA matrix."""
+        """Every instance's (x, log s, log v, log zl, log zu[, y]) as a float32 CUDA matrix (y:
+        HyKKT and dual-regularized batches)."""
         import torch
         w = I()
         _check(lib().ipm_batch_state_rows(self.h, None, 0, ctypes.byref(w)), "ipm_batch_state_rows")

@@ -1811,7 +1811,8 @@ __global__ void k_b_finish_unfinished(BCtl *ctl, int count) {
 
 // ------------------------------------------------------------------ learned warm start
 // Row of an instance for training and prediction: x (n), log s (mi), log v (mi), log zl (n),
-// log zu (n) (0 where the bound is absent); the iterate as the IPM holds it (scaled problem).
+// log zu (n) (0 where the bound is absent), then y (me: the equality multipliers of HyKKT and
+// the dual-regularized form; none for LiftedKKT); the iterate as the IPM holds it (scaled).
 __global__ void k_b_state_rows(const BI *bi, float *out, int64_t ld) {
   const int b = blockIdx.y;
   const BI &I = bi[b];
@@ -1826,6 +1827,8 @@ __global__ void k_b_state_rows(const BI *bi, float *out, int64_t ld) {
     o[n + i] = (float)log(I.P.s[i]);
     o[n + mi + i] = (float)log(I.P.v[i]);
   }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.D.me; i += gridDim.x * blockDim.x)
+    o[3 * n + 2 * mi + i] = (float)I.P.y[i];
 }
 
 __device__ __forceinline__ float denorm(const float *pred, const float *mean, const float *stdv,
@@ -1838,7 +1841,7 @@ __global__ void k_b_warm_check(const BI *bi, const float *pred, int64_t ld, cons
                                const float *stdv) {
   const int b = blockIdx.y;
   const BI &I = bi[b];
-  const int n = I.D.n, mi = I.D.mi, w = 3 * n + 2 * mi;
+  const int n = I.D.n, mi = I.D.mi, w = 3 * n + 2 * mi + I.D.me;
   const float *p = pred + (int64_t)b * ld;
   double bad = 0.0, sv = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < w; j += gridDim.x * blockDim.x) {
@@ -1880,6 +1883,8 @@ __global__ void k_b_warm_apply(const BI *bi, const float *pred, int64_t ld, cons
     I.P.v[i] = v;
     I.P.z[i] = v;
   }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.D.me; i += gridDim.x * blockDim.x)
+    I.P.y[i] = (double)denorm(p, mean, stdv, 3 * n + 2 * mi + i);
 }
 
 // pass 3: barrier parameter mu0 = s^T v / m_i of the predicted point, fresh filter
@@ -3014,15 +3019,11 @@ extern "C" int ipm_batch_export_all(ipm_batch_t B, double *x_host) {
 
 extern "C" int ipm_batch_state_rows(ipm_batch_t B, float *out, int64_t ld, int *width) {
   if (!B) return IPM_ERR_BAD_ARG;
-  if (B->opt.kkt != 0) {
-    set_error_msg("ipm_batch_state_rows: learned warm starts are for LiftedKKT batches");
-    return IPM_ERR_BAD_ARG;
-  }
   std::vector<BI> h(B->count);
   CK(cudaMemcpy(h.data(), B->d_bi, sizeof(BI) * B->count, cudaMemcpyDeviceToHost));
-  const int w = 3 * h[0].D.n + 2 * h[0].D.mi;
+  const int w = 3 * h[0].D.n + 2 * h[0].D.mi + h[0].D.me;
   for (const BI &I : h)
-    if (3 * I.D.n + 2 * I.D.mi != w) {
+    if (3 * I.D.n + 2 * I.D.mi + I.D.me != w) {
       set_error_msg("ipm_batch_state_rows: instances of different sizes");
       return IPM_ERR_BAD_ARG;
     }

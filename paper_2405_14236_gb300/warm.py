@@ -22,16 +22,16 @@ def input_rows(grids):
     return np.stack([np.concatenate([g.pd, g.qd]) for g in grids]).astype(np.float32)
 
 
-def collect(grids, tol=1e-3, tau=1e-6, chunk=320, max_iter=300):
-    """Solves every scenario (same grid, different loads) with the batched IPM to ``tol`` (the
-    LiftedKKT relaxation tau kept at the value of the full solves) and returns the state rows
-    (float32 CUDA matrix) and the converged mask (numpy bool).  One batch of ``chunk``
-    instances is reused: loads are replaced, the batch is reset and run."""
+def collect(grids, tol=1e-3, tau=1e-6, chunk=320, max_iter=300, kkt="lifted", gamma=1e6):
+    """Solves every scenario (same grid, different loads) with the batched IPM in the KKT form
+    ``kkt`` to ``tol`` (the LiftedKKT relaxation tau kept at the value of the full solves) and
+    returns the state rows (float32 CUDA matrix) and the converged mask (numpy bool).  One batch
+    of ``chunk`` instances is reused: loads are replaced, the batch is reset and run."""
     import torch
     n = len(grids)
     chunk = min(chunk, n)
     opfs = [Opf(g) for g in grids[:chunk]]
-    B = Batch(opfs, tol=tol, tau=tau)
+    B = Batch(opfs, tol=tol, tau=tau, kkt=kkt, gamma=gamma)
     rows = None
     ok = np.zeros(n, bool)
     for c0 in range(0, n, chunk):
