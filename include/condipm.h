@@ -475,14 +475,15 @@ int ipm_batch_solve_info(ipm_batch_t batch, int *current, int *iters32, int *k64
 int ipm_batch_export(ipm_batch_t batch, int i, double *x);
 /* Sweeps run since creation or the last reset. */
 int ipm_batch_sweeps(ipm_batch_t batch);
-/* Tail of a run: once at most active_max instances are still running (read back after every
- * sweep), each sweep holds four inertia rounds and eight line-search trials instead of two and
- * two (a round costs little when few instances are left, and an instance that corrects its
- * inertia or backtracks many times then needs fewer sweeps; its iterates are the same).
- * cluster 1, 2, 4 or 8 also runs every remaining instance's factorization and solves on a
- * thread-block cluster of that many blocks; 0 keeps the launch shape (and so the rounding of
- * the sums).  active_max = 0: no tail sweep.  Default (16, 0).  Applies to graph runs
- * (use_graph != 0).  Host only. */
+/* Tail of a run: in a batch of more than active_max instances, once at most active_max are
+ * still running (read back after every sweep), each sweep holds four inertia rounds and eight
+ * line-search trials instead of two and two (a round costs little when few instances are left,
+ * and an instance that corrects its inertia or backtracks many times then needs fewer sweeps),
+ * and with cluster 1, 2, 4 or 8 every remaining instance's factorization and solves run on a
+ * thread-block cluster of that many blocks (the chain of the slowest instance, not the GPU's
+ * throughput, then sets a sweep); cluster 0 keeps the launch shape.  The iterates are those of
+ * the same method (the cluster changes only the order of floating-point sums).  active_max = 0:
+ * no tail sweep.  Default (16, 8).  Applies to graph runs (use_graph != 0).  Host only. */
 int ipm_batch_set_tail(ipm_batch_t batch, int active_max, int cluster);
 /* Sets a launch shape (the candidates of ipm_batch_autotune): instances whose supernode count
  * exceeds big_num / big_den times the median (big_den = 0: none) factor and solve on thread-block

@@ -585,10 +585,10 @@ class Batch:
                "ipm_batch_export")
         return out
 
-    def set_tail(self, active_max, cluster=0):
-        """Once at most active_max instances remain, sweeps hold more inertia and line-search
-        rounds, and (cluster > 0) run every instance on clusters (ipm_batch_set_tail; 0
-        disables)."""
+    def set_tail(self, active_max, cluster=8):
+        """In batches of more than active_max instances, once at most active_max remain, sweeps
+        hold more inertia and line-search rounds and (cluster > 0) run every instance on
+        clusters (ipm_batch_set_tail; active_max 0 disables)."""
         _check(lib().ipm_batch_set_tail(self.h, int(active_max), int(cluster)),
                "ipm_batch_set_tail")
 

@@ -1923,11 +1923,11 @@ struct ipm_batch_s {
   std::vector<void *> bufs;  // per-pattern level offsets
   int *d_tickets = nullptr;  // scratch counters: active count at [8], pause iteration at [12]
   int *d_order = nullptr;  // small instances by decreasing supernode count, then the big ones
-  // tail of a run: once at most tail_active instances are still running, the sweeps hold more
-  // inertia rounds and line-search trials (a round then costs little) and, with tail_cl > 0,
-  // run every instance on clusters of tail_cl blocks; d_order_all lists every instance by
-  // decreasing supernode count
-  int tail_active = 16, tail_cl = 0;
+  // tail of a run (batches of more than tail_active instances): once at most tail_active are
+  // still running, the sweeps hold more inertia rounds and line-search trials (a round then
+  // costs little) and, with tail_cl > 0, run every instance on clusters of tail_cl blocks;
+  // d_order_all lists every instance by decreasing supernode count
+  int tail_active = 16, tail_cl = 8;
   int fact_rounds = B_FACT_ROUNDS, ls_rounds = B_LS_ROUNDS;  // of the sweep being captured
   int *d_order_all = nullptr;
   cudaGraph_t graph_tail = nullptr;
@@ -2765,13 +2765,14 @@ extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int us
   if (B->max_iter != max_iter) drop_graph(B);
   B->max_iter = max_iter;
   if (use_graph && !B->exec) CKR(capture_sweep(B, false, &B->graph, &B->exec));
-  if (use_graph && B->tail_active > 0 && !B->exec_tail)
-    CKR(capture_sweep(B, true, &B->graph_tail, &B->exec_tail));
+  // (a batch no larger than the tail threshold keeps its launch shape throughout)
+  const bool has_tail = use_graph && B->tail_active > 0 && B->count > B->tail_active;
+  if (has_tail && !B->exec_tail) CKR(capture_sweep(B, true, &B->graph_tail, &B->exec_tail));
   int rc = IPM_OK;
   *B->h_active = B->count;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     if (use_graph) {
-      const bool tail = B->exec_tail && *B->h_active <= B->tail_active;
+      const bool tail = has_tail && *B->h_active <= B->tail_active;
       CK(cudaGraphLaunch(tail ? B->exec_tail : B->exec, s));
     } else {
       CKR(enqueue_sweep(B, s));
