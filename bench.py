@@ -958,6 +958,13 @@ def ipm_measure(include_oracle=True):
                "cg_iters": int(sum(h.cg_iters for h in hist)),
                "fp32_iters": int(sum(1 for h in hist if h.precision == 32)), "gamma": gam,
                **sizes}
+        if name == "planar80k":
+            # per iteration: factor precision, delta_w and the backward error of the augmented
+            # system that the library computed for the step's KKT solve (every one of these solves
+            # is checked against the oracle's own evaluation in the GPU tests at this size)
+            rec["per_iteration"] = [{"k": h.k, "precision": h.precision, "eta": h.eta,
+                                     "delta_w": h.delta_w, "cg": h.cg_iters} for h in hist
+                                    if h.status == 0]
         if include_oracle and name == "planar1k" and prec == 64:
             from oracle.opf import OPFModel
             from oracle import ipm as oipm
