@@ -35,16 +35,21 @@ namespace cipm {
 
 // PH_CGI, PH_CG, PH_CGX: HyKKT's Schur-complement CG (start, iterations, primal back-solve);
 // PH_PAUSE: held after the KKT solve of the iteration named by ipm_batch_pause_at (the solved
-// system and its solution stay in the instance's buffers until ipm_batch_resume)
+// system and its solution stay in the instance's buffers until ipm_batch_resume);
+// PH_PCGI, PH_PCG, PH_PCGX (LiftedKKT batches): conjugate gradients on the condensed system after
+// a refinement that stagnated above a backward error of 1e-10 (start, iterations, comparison
+// with the refined solution), as in the single-problem solve
 enum Phase {
   PH_EVAL = 0, PH_BUILD, PH_FACT, PH_SOLVE, PH_REFINE, PH_STEP, PH_LS, PH_ACC, PH_DONE,
-  PH_CGI, PH_CG, PH_CGX, PH_PAUSE
+  PH_CGI, PH_CG, PH_CGX, PH_PAUSE, PH_PCGI, PH_PCG, PH_PCGX
 };
 
 static constexpr int B_FACT_ROUNDS = 2, B_REFINE_ROUNDS = 3, B_LS_ROUNDS = 2, B_CG_ROUNDS = 6;
 // rounds of the tail sweep (few instances left: a round then costs little, and an instance that
 // backtracks or corrects its inertia many times needs fewer sweeps)
 static constexpr int B_TAIL_FACT_ROUNDS = 4, B_TAIL_LS_ROUNDS = 8;
+// conjugate-gradient iterations per sweep and per solve after a stagnating refinement
+static constexpr int B_PCG_ROUNDS = 5, B_PCG_MAXIT = 50;
 // refinement steps allowed with the FP32 factor (at a contraction rate of 1/2 per step the
 // error falls by 2^-30 ~ 1e-9; a slower rate stops at the stall test first)
 static constexpr int B_REFINE32 = 30;
@@ -69,6 +74,10 @@ struct BCtl {
   double eta_worst;
   // directions of this iteration recomputed at a larger delta_w after a failed line search
   int n_reg, pad_reg_;
+  // PCG after a stagnating refinement: runs, iterations, this run's count, whether the last
+  // refinement correction is taken back, whether the refined solution is restored
+  int pg_runs, pg_total, pg_it, pg_undo, pg_restore, pad_pg_;
+  double pg_rz, pg_tn, pg_eta0;
   // feasibility restoration (Waechter & Biegler 2006, Sec. 3.3): resto 0 = main problem,
   // 2 = phase entered (its start is set at the next evaluation), 1 = in the phase; ret: the
   // accepted trial passed the return test.  While in the phase mu, tau, delta_last, theta_max,
@@ -117,6 +126,9 @@ struct BI {
   int *info;
   double *y, *t, *cx, *cz, *outx, *outz, *scal;
   double *cg_r, *cg_p, *cg_sp, *cg_dy, *cg_rhs1, *cg_v;  // HyKKT CG vectors
+  // PCG after a stagnating refinement (LiftedKKT): condensed right-hand side t, r, z, p, K p
+  // (n), d o (J v) (m), the refined solution kept for the comparison (n, m)
+  double *pg_t, *pg_r, *pg_z, *pg_p, *pg_q, *pg_u, *pg_xs, *pg_zs;
   const double *dystep;  // dy of the step: cg_dy (HyKKT), dz over the G rows (form 2)
   AugArgs aug;
   // restoration phase: p, q and their duals, steps and trial values, row residuals (one per IPM
@@ -1177,7 +1189,7 @@ __global__ void __launch_bounds__(B_NT, 3)
   const BI &I = bi[b];
   const int warp = threadIdx.x >> 5;
   double *x = phase == PH_SOLVE || phase == PH_CGI || phase == PH_CGX ? I.dx
-              : phase == PH_CG ? I.cg_v : I.cx;
+              : phase == PH_CG ? I.cg_v : phase == PH_PCGI || phase == PH_PCG ? I.pg_z : I.cx;
   // the permuted right-hand side lives in this block's shared memory when the instance has
   // one block and n fits (ycap doubles): its loads and atomic updates then stay on the SM
   const bool in_smem = ncl == 1 && I.D.n <= ycap;
@@ -1452,9 +1464,10 @@ __device__ __forceinline__ void solve_done(BCtl &c, double eta, const int *pause
 }
 
 // Richardson test: stop at eta <= 1e-10, after max_refine corrections, or when eta stops
-// halving; otherwise one more correction
+// halving; otherwise one more correction.  With pcg_on (LiftedKKT), an FP64 solve left above
+// 1e-10 goes on with conjugate gradients on the condensed system (PH_PCGI)
 __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine,
-                            const int *pause_k) {
+                            const int *pause_k, int pcg_on) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= count || ctl[b].ph != PH_REFINE) return;
   const BI &I = bi[b];
@@ -1484,6 +1497,13 @@ __global__ void k_b_ctl_ref(const BI *bi, BCtl *ctl, int count, int max_refine,
         return;
       }
       ++c.it32;
+    } else if (pcg_on && !(eta <= 1e-10) && max_refine > 0) {
+      // the last correction is taken back when it made the solution worse
+      c.pg_undo = c.ref_it > 1 && !(eta <= c.eta_prev);
+      c.pg_eta0 = c.pg_undo ? c.eta_prev : eta;
+      bi[b].R[R_PG_A] = bi[b].R[R_PG_B] = bi[b].R[R_PG_C] = 0.0;
+      c.ph = PH_PCGI;
+      return;
     }
     solve_done(c, eta, pause_k);
     return;
@@ -1501,6 +1521,195 @@ __global__ void k_b_axpy(const BI *bi, const BCtl *ctl) {
   B_PROLOGUE(PH_REFINE);
   for (int j = gtid; j < I.D.n; j += gstride) I.dx[j] += I.cx[j];
   for (int r = gtid; r < I.m; r += gstride) I.dzc[r] += I.cz[r];
+}
+
+// ------------------------------------------------------------------ PCG after stagnation
+// LiftedKKT: Richardson refinement that stalls above 1e-10 (cond(K) eps_mach near one) is
+// followed, as in the single-problem solve, by conjugate gradients on the condensed system
+//   K dx = t,  K = W + Sigma_x + delta_w I + J^T D J,  t = a + J^T (d o b),
+// preconditioned by the same factor and started from the refined dx (at most B_PCG_MAXIT
+// iterations, stop at ||r||_2 <= 1e-14 ||t||_2 or at non-positive curvature); then
+// dz = d o (J dx - b), and the refined solution is restored when it had the smaller backward
+// error of the augmented system.
+// PCGI: take back a worsening last correction, keep the refined solution, t and ||t||^2
+__global__ void k_b_pg_save(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_PCGI);
+  const bool undo = ctl[b].pg_undo;
+  double tt = 0.0;
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    const double x = undo ? I.dx[j] - I.cx[j] : I.dx[j];
+    I.dx[j] = x;
+    I.pg_xs[j] = x;
+    double acc = 0.0;
+    for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+      const int p = I.JT_ent[t];
+      const int r = I.J_rowidx[p];
+      acc += I.Jv[p] * (I.dcond[r] * I.baug[r]);
+    }
+    const double v = I.a[j] + acc;
+    I.pg_t[j] = v;
+    tt += v * v;
+  }
+  for (int r = gtid; r < I.m; r += gstride) {
+    const double z = undo ? I.dzc[r] - I.cz[r] : I.dzc[r];
+    I.dzc[r] = z;
+    I.pg_zs[r] = z;
+  }
+  const int slot[1] = {R_PG_C};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {tt};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+// u = d o (J v), v = dx (PCGI) or p (PCG)
+__global__ void k_b_pg_ju(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  const double *v = phase == PH_PCGI ? I.dx : I.pg_p;
+  for (int r = gtid; r < I.m; r += gstride) I.pg_u[r] = I.dcond[r] * g_row_dot(I, r, v);
+}
+// (W + Sigma_x + delta_w I) v + J^T u at column j
+__device__ __forceinline__ double kmat_at(const BI &I, double dw, const double *v, int j) {
+  double acc = (I.SA.sigma[j] + dw) * v[j];
+  for (int p = I.aug.W_rowptr[j]; p < I.aug.W_rowptr[j + 1]; ++p)
+    acc += I.Wv[p] * v[I.aug.W_colind[p]];
+  for (int t = I.aug.WT_ptr[j]; t < I.aug.WT_ptr[j + 1]; ++t) {
+    const int e = I.aug.WT_ent[t];
+    const int r = I.aug.W_rowidx[e];
+    if (r != j) acc += I.Wv[e] * v[r];
+  }
+  for (int t = I.JT_ptr[j]; t < I.JT_ptr[j + 1]; ++t) {
+    const int p = I.JT_ent[t];
+    acc += I.Jv[p] * I.pg_u[I.J_rowidx[p]];
+  }
+  return acc;
+}
+// PCGI: r = t - K dx (also the solve's right-hand side), r.r; PCG: q = K p, p.q
+__global__ void k_b_pg_k(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  const double dw = ctl[b].dw;
+  double acc = 0.0;
+  if (phase == PH_PCGI) {
+    for (int j = gtid; j < I.D.n; j += gstride) {
+      const double r = I.pg_t[j] - kmat_at(I, dw, I.dx, j);
+      I.pg_r[j] = r;
+      I.t[j] = r;
+      acc += r * r;
+    }
+  } else {
+    for (int j = gtid; j < I.D.n; j += gstride) {
+      const double q = kmat_at(I, dw, I.pg_p, j);
+      I.pg_q[j] = q;
+      acc += I.pg_p[j] * q;
+    }
+  }
+  const int slot[1] = {phase == PH_PCGI ? R_PG_B : R_PG_C};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {acc};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+// after the preconditioner solve z = M^{-1} r: r.z; PCGI also p = z
+__global__ void k_b_pg_rz(const BI *bi, const BCtl *ctl, int phase) {
+  B_PROLOGUE(phase);
+  double rz = 0.0;
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    rz += I.pg_r[j] * I.pg_z[j];
+    if (phase == PH_PCGI) I.pg_p[j] = I.pg_z[j];
+  }
+  const int slot[1] = {R_PG_A};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {rz};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+__global__ void k_b_ctl_pgi(const BI *bi, BCtl *ctl, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_PCGI) return;
+  BCtl &c = ctl[b];
+  double *R = bi[b].R;
+  c.pg_rz = R[R_PG_A];
+  c.pg_tn = sqrt(R[R_PG_C]);
+  const double rn = sqrt(R[R_PG_B]);
+  R[R_PG_A] = R[R_PG_B] = R[R_PG_C] = 0.0;
+  c.pg_it = 0;
+  ++c.pg_runs;
+  c.ph = rn <= 1e-14 * c.pg_tn || !isfinite(rn) ? PH_PCGX : PH_PCG;
+}
+// alpha = r.z / p.K p (r.z of the previous iteration's preconditioned residual after the first)
+__global__ void k_b_ctl_pg_alpha(const BI *bi, BCtl *ctl, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_PCG) return;
+  BCtl &c = ctl[b];
+  double *R = bi[b].R;
+  if (c.pg_it > 0) {
+    c.pg_rz = R[R_PG_A];
+    R[R_PG_A] = 0.0;
+  }
+  const double pq = R[R_PG_C];
+  R[R_PG_C] = 0.0;
+  if (!(pq > 0.0) || !isfinite(c.pg_rz)) {  // non-positive curvature: stop with the iterate
+    c.ph = PH_PCGX;
+    return;
+  }
+  c.cg_alpha = c.pg_rz / pq;
+}
+// dx += alpha p, r -= alpha q (also the solve's right-hand side), r.r
+__global__ void k_b_pg_xr(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_PCG);
+  const double al = ctl[b].cg_alpha;
+  double rr = 0.0;
+  for (int j = gtid; j < I.D.n; j += gstride) {
+    I.dx[j] += al * I.pg_p[j];
+    const double r = I.pg_r[j] - al * I.pg_q[j];
+    I.pg_r[j] = r;
+    I.t[j] = r;
+    rr += r * r;
+  }
+  const int slot[1] = {R_PG_B};
+  const int op[1] = {OP_SUM};
+  double v1[1] = {rr};
+  block_reduce_atomic<1>(I.R, slot, op, v1);
+}
+__global__ void k_b_ctl_pg_check(const BI *bi, BCtl *ctl, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_PCG) return;
+  BCtl &c = ctl[b];
+  double *R = bi[b].R;
+  const double rn = sqrt(R[R_PG_B]);
+  R[R_PG_B] = 0.0;
+  ++c.pg_it;
+  ++c.pg_total;
+  if (!isfinite(rn) || rn <= 1e-14 * c.pg_tn || c.pg_it >= B_PCG_MAXIT) c.ph = PH_PCGX;
+}
+// p = z + beta p, beta = r.z (new) / r.z (old)
+__global__ void k_b_pg_p(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_PCG);
+  const double be = I.R[R_PG_A] / ctl[b].pg_rz;
+  for (int j = gtid; j < I.D.n; j += gstride) I.pg_p[j] = I.pg_z[j] + be * I.pg_p[j];
+}
+// PCGX: dz = d o (J dx - b), then the residual of the augmented system (k_b_resid)
+__global__ void k_b_pg_dz(const BI *bi, const BCtl *ctl) {
+  B_PROLOGUE(PH_PCGX);
+  for (int r = gtid; r < I.m; r += gstride)
+    I.dzc[r] = I.dcond[r] * (g_row_dot(I, r, I.dx) - I.baug[r]);
+}
+// the better of the refined and the PCG solution (smaller backward error)
+__global__ void k_b_ctl_pgx(const BI *bi, BCtl *ctl, int count, const int *pause_k) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count || ctl[b].ph != PH_PCGX) return;
+  BCtl &c = ctl[b];
+  const double *sc = bi[b].scal;
+  const double den = c.normA * sc[1] + sc[2];
+  const double eta = den > 0 ? sc[0] / den : 0.0;
+  c.pg_restore = !(eta < c.pg_eta0);
+  solve_done(c, c.pg_restore ? c.pg_eta0 : eta, pause_k);
+}
+// the refined solution back where it was the better one (after k_b_ctl_pgx; the flag is
+// cleared when the step begins)
+__global__ void k_b_pg_restore(const BI *bi, const BCtl *ctl) {
+  const int b = blockIdx.y;
+  if (!ctl[b].pg_restore) return;
+  const BI &I = bi[b];
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  for (int j = gtid; j < I.D.n; j += gstride) I.dx[j] = I.pg_xs[j];
+  for (int r = gtid; r < I.m; r += gstride) I.dzc[r] = I.pg_zs[r];
 }
 
 // ------------------------------------------------------------------ step
@@ -1560,6 +1769,7 @@ __global__ void k_b_ctl_ls0(const BI *bi, BCtl *ctl, int count) {
   if (b >= count || ctl[b].ph != PH_STEP) return;
   const double *h = bi[b].R;
   BCtl &c = ctl[b];
+  c.pg_restore = 0;  // (k_b_pg_restore has run)
   c.amax = h[R_AMAX];
   c.az = h[R_AZ];
   c.gphi = h[R_GPHI_X] + h[R_GPHI_S];
@@ -2148,11 +2358,47 @@ int enqueue_sweep(ipm_batch_t B, cudaStream_t s) {
     for (int r = 0; r < B_REFINE_ROUNDS; ++r) {
       k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl, (int)PH_REFINE);
       k_b_resid<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_REFINE);
-      k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine, B->d_tickets + 12);
+      k_b_ctl_ref<<<gc, 128, 0, s>>>(bi, ctl, C, B->opt.max_refine, B->d_tickets + 12,
+                                     (int)(B->opt.kkt == 0));
       L(3);
       CKR(solve(PH_REFINE));
       k_b_axpy<<<g2, blk, 0, s>>>(bi, ctl);
       L(1);
+    }
+    if (B->opt.kkt == 0) {
+      // LiftedKKT: conjugate gradients after a refinement that stagnated above 1e-10
+      auto psolve = [&](int phase) -> int {
+        if (B->opt.precision == 32)
+          CKR(split(k_b_solve_inst<float>, B_NT, B->solve_smem, phase, B->solve_ycap));
+        CKR(split(k_b_solve_inst<double>, B_NT, B->solve_smem, phase, B->solve_ycap));
+        return IPM_OK;
+      };
+      k_b_pg_save<<<g2, blk, 0, s>>>(bi, ctl);
+      k_b_pg_ju<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCGI);
+      k_b_pg_k<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCGI);
+      L(3);
+      CKR(psolve(PH_PCGI));
+      k_b_pg_rz<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCGI);
+      k_b_ctl_pgi<<<gc, 128, 0, s>>>(bi, ctl, C);
+      L(2);
+      for (int r = 0; r < B_PCG_ROUNDS; ++r) {
+        k_b_pg_ju<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCG);
+        k_b_pg_k<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCG);
+        k_b_ctl_pg_alpha<<<gc, 128, 0, s>>>(bi, ctl, C);
+        k_b_pg_xr<<<g2, blk, 0, s>>>(bi, ctl);
+        k_b_ctl_pg_check<<<gc, 128, 0, s>>>(bi, ctl, C);
+        L(5);
+        CKR(psolve(PH_PCG));
+        k_b_pg_rz<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCG);
+        k_b_pg_p<<<g2, blk, 0, s>>>(bi, ctl);
+        L(2);
+      }
+      k_b_pg_dz<<<g2, blk, 0, s>>>(bi, ctl);
+      k_b_scal_zero<<<C, 32, 0, s>>>(bi, ctl, (int)PH_PCGX);
+      k_b_resid<<<g2, blk, 0, s>>>(bi, ctl, (int)PH_PCGX);
+      k_b_ctl_pgx<<<gc, 128, 0, s>>>(bi, ctl, C, B->d_tickets + 12);
+      k_b_pg_restore<<<g2, blk, 0, s>>>(bi, ctl);
+      L(5);
     }
   }
   // step recovery, fraction to the boundary, line-search set-up
@@ -2379,6 +2625,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     size_t xt, st, geqt, hint, gst, hst, ft, R, filter, tJ, Lx, Dx, y_s, t, cx, cz, outx, outz,
         scal;
     size_t cg_r, cg_p, cg_sp, cg_dy, cg_rhs1, cg_v;
+    size_t pg_t, pg_r, pg_z, pg_p, pg_q, pg_u, pg_xs, pg_zs;
     size_t rp, rq, rzp, rzq, rdp, rdq, rdzp, rdzq, rpt, rqt, rrc, rrp, rrq, rxr, rdr2, rfilter;
     size_t info;
   };
@@ -2413,6 +2660,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     const size_t ncg = B->opt.kkt == 1 ? n : 0, mcg = B->opt.kkt == 1 ? me0 : 0;
     o.cg_r = dp.take(mcg); o.cg_p = dp.take(mcg); o.cg_sp = dp.take(mcg); o.cg_dy = dp.take(mcg);
     o.cg_rhs1 = dp.take(ncg); o.cg_v = dp.take(ncg);
+    const size_t npg = lifted ? n : 0, mpg = lifted ? m : 0;  // PCG after stagnation
+    o.pg_t = dp.take(npg); o.pg_r = dp.take(npg); o.pg_z = dp.take(npg); o.pg_p = dp.take(npg);
+    o.pg_q = dp.take(npg); o.pg_u = dp.take(mpg); o.pg_xs = dp.take(npg); o.pg_zs = dp.take(mpg);
     // restoration phase: per IPM row, x_R and D_R^2, the phase's filter
     const size_t nr = B->opt.no_resto ? 0 : me + mi, nx = B->opt.no_resto ? 0 : n;
     o.rp = dp.take(nr); o.rq = dp.take(nr); o.rzp = dp.take(nr); o.rzq = dp.take(nr);
@@ -2667,6 +2917,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     I.outz = d + o.outz; I.scal = d + o.scal;
     I.cg_r = d + o.cg_r; I.cg_p = d + o.cg_p; I.cg_sp = d + o.cg_sp; I.cg_dy = d + o.cg_dy;
     I.cg_rhs1 = d + o.cg_rhs1; I.cg_v = d + o.cg_v;
+    I.pg_t = d + o.pg_t; I.pg_r = d + o.pg_r; I.pg_z = d + o.pg_z; I.pg_p = d + o.pg_p;
+    I.pg_q = d + o.pg_q; I.pg_u = d + o.pg_u; I.pg_xs = d + o.pg_xs; I.pg_zs = d + o.pg_zs;
     I.dystep = B->opt.kkt == 1 ? I.cg_dy : I.dzc;
     if (!B->opt.no_resto) {
       I.rp = d + o.rp; I.rq = d + o.rq; I.rzp = d + o.rzp; I.rzq = d + o.rzq; I.rdp = d + o.rdp;

@@ -64,6 +64,8 @@ enum {
   R_RS_OBJ, R_RS_DUAL, R_RS_PRIM, R_RS_COMP, R_RS_SUMD, R_RS_SUMC,
   // restoration trial points (batched IPM): theta and barrier logs of the original problem
   R_RS_TH0, R_RS_LOG0,
+  // batched PCG after a stagnating refinement: r.z, r.r, p.K p (t.t at its start)
+  R_PG_A, R_PG_B, R_PG_C,
   R_COUNT
 };
 
