@@ -150,3 +150,33 @@ def test_hykkt_matches_dense_and_cg_trends():
     assert all(x >= y for x, y in zip(its, its[1:]))
     assert all(x > y for x, y in zip(spread, spread[1:]))
     assert spread[-1] < 1e-3
+
+
+def test_dual_regularized_solve_equals_dense_and_tends_to_k2():
+    """The dual-regularized condensed form (Remark in Sec. 3: delta_c > 0 on the equality block,
+    condensed with weight gamma = 1/delta_c on the G rows): the oracle's refined condensed solve
+    equals the dense solve of the augmented system whose equality block is -delta_c I, and as
+    delta_c -> 0 that solution tends to the solution of the unregularized system (equalities
+    kept exactly) with an error of order delta_c."""
+    n, me, mi = 30, 6, 20
+    J, W, sigma, dh = small_kkt(n, me, mi, 4)
+    rng = np.random.default_rng(11)
+    a, b = rng.standard_normal(n), rng.standard_normal(me + mi)
+    solver = K.CondensedSolver(W, J)
+    exact = np.linalg.solve(K.aug_matrix(W, sigma, J, dh, me, 0.0).toarray(),
+                            np.concatenate([a, b]))
+    errs = []
+    for gamma in (1e2, 1e4, 1e6):
+        d = np.concatenate([np.full(me, gamma), dh])
+        dw, F, _ = K.inertia_schedule(lambda dd: K.condensed_matrix(W, sigma, J, d, dd), solver)
+        assert dw == 0.0
+        A = K.aug_matrix(W, sigma, J, d, 0, 0.0)
+        dx, dz, hist = K.lifted_solve(F, A, J, d, a, b)
+        sol = np.concatenate([dx, dz])
+        ref = np.linalg.solve(A.toarray(), np.concatenate([a, b]))
+        np.testing.assert_allclose(sol, ref, rtol=1e-7, atol=1e-9)
+        assert hist[-1] <= 1e-10
+        errs.append(np.abs(sol - exact).max() / np.abs(exact).max())
+    # first order in delta_c = 1/gamma: a hundredfold smaller delta_c, a hundredfold smaller gap
+    assert errs[0] > 30 * errs[1] > 900 * errs[2], errs
+    assert errs[2] < 1e-4
