@@ -223,12 +223,16 @@ __device__ __forceinline__ double eval_gen_at(const OpfDims &D, const OpfData &M
   return M.c2[gi] * pm * pm + M.c1[gi] * pm;
 }
 
-// theta_ref row entry, the zero gradient on V and theta, f = sum of the block parts in order
+// theta_ref row entry, the zero gradient on V, theta and the flow variables, f = sum of the
+// block parts in order
 __device__ __forceinline__ void eval_finish_at(const OpfDims &D, const OpfData &M,
                                                const double *fpart, int nparts, double *f,
                                                double *grad, double *Jv, int i, int stride) {
-  if (grad)
+  if (grad) {
     for (int k = i; k < 2 * D.nb; k += stride) grad[k] = 0.0;
+    // the branch-flow variables (flow form) do not enter the objective either
+    for (int k = 2 * (D.nb + D.ng) + i; k < D.n; k += stride) grad[k] = 0.0;
+  }
   if (i == 0) {
     if (Jv) Jv[M.jentry[2 * D.ng + 2 * jterms_per_end(D) * D.nbr]] = 1.0;
     if (f) {

@@ -33,7 +33,9 @@ def test_flow_eval_matches_oracle(name):
     np.testing.assert_array_equal(opf.W_rowptr.cpu().numpy(), Wl.indptr)
     np.testing.assert_array_equal(opf.W_colind.cpu().numpy(), Wl.indices)
     t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
-    zz = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")
+    # outputs start as NaN: every entry must be written by the evaluation (the IPM's buffers
+    # are not cleared between evaluations, and reused device memory holds stale values)
+    zz = lambda k: torch.full((k,), float("nan"), dtype=torch.float64, device="cuda")
     f, grad, gg, hh, Jv, Wv = zz(1), zz(m.n), zz(m.m_e), zz(m.m_i), zz(opf.nnzJ), zz(opf.nnzW)
     opf.eval(t(x), t(y), t(z), 0.37, f, grad, gg, hh, Jv, Wv)
     torch.cuda.synchronize()
@@ -47,12 +49,9 @@ def test_flow_eval_matches_oracle(name):
     assert rel(Wv.cpu().numpy(), Wl.data) < 1e-12
 
 
-# (LiftedKKT on the 1,000-bus flow form is left out: its single-problem GPU solve follows
-# rounding-dependent paths (of 12 runs, 7 reached the oracle's objective, 2 a point 1e-4 away and
-# 3 stopped after a failed restoration phase; the oracle itself converges), the ill-conditioning
-# of K_tau with 4 N_br relaxed definition rows; the batched test below covers the form at 1k)
 @pytest.mark.parametrize("name,kkt", [("ring30", "hykkt"), ("ring30", "lifted"),
-                                      ("planar1k", "hykkt"), ("planar1k", "regularized")])
+                                      ("planar1k", "hykkt"), ("planar1k", "lifted"),
+                                      ("planar1k", "regularized")])
 def test_flow_ipm_matches_oracle(name, kkt):
     g = config_grid(name)
     ref = oipm.solve(FlowOPFModel(g), oipm.Options(kkt=kkt, gamma=1e6))
@@ -64,6 +63,25 @@ def test_flow_ipm_matches_oracle(name, kkt):
     if kkt == "hykkt":
         compact = oipm.solve(OPFModel(g), oipm.Options(kkt="hykkt", gamma=1e6))
         assert abs(res["obj"] - compact.obj) <= 1e-6 * abs(compact.obj)
+
+
+@pytest.mark.parametrize("kkt", ["hykkt", "lifted"])
+def test_flow_ipm_repeats_on_reused_memory(kkt):
+    """Solves of the same 1,000-bus flow-form problem one after another, each with new handles
+    whose device memory is what the previous solve freed: every solve reaches the same optimum
+    in nearly the same number of iterations (a buffer read before it is written would make the
+    result depend on the previous solve's leftovers)."""
+    g = config_grid("planar1k")
+    runs = []
+    for _ in range(4):
+        res = cp.ipm_solve_opf(cp.Opf(g, form="flow"), kkt=kkt, gamma=1e6)
+        assert res["status"] == 1, res["history"][-1]
+        runs.append((res["obj"], res["iters"]))
+        del res
+    objs = np.array([r[0] for r in runs])
+    its = np.array([r[1] for r in runs])
+    assert np.abs(objs - objs[0]).max() <= 1e-8 * abs(objs[0]), objs
+    assert its.max() - its.min() <= 3, its
 
 
 def test_batch_mixes_both_formulations():

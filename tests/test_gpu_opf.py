@@ -28,7 +28,8 @@ def test_opf_eval_matches_oracle(name):
     np.testing.assert_array_equal(opf.W_rowptr.cpu().numpy(), Wl.indptr)
     np.testing.assert_array_equal(opf.W_colind.cpu().numpy(), Wl.indices)
     t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
-    z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")
+    # outputs start as NaN: every entry must be written by the evaluation
+    z = lambda k: torch.full((k,), float("nan"), dtype=torch.float64, device="cuda")
     f, grad, gg, hh, Jv, Wv = z(1), z(g.n), z(g.m_e), z(g.m_i), z(opf.nnzJ), z(opf.nnzW)
     opf.eval(t(p["x"]), t(p["y"]), t(p["z"]), 0.37, f, grad, gg, hh, Jv, Wv)
     torch.cuda.synchronize()
