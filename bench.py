@@ -929,7 +929,10 @@ def ipm_measure():
     cases = [("planar1k", "lifted", 64), ("planar1k", "hykkt", 64), ("planar10k", "hykkt", 64),
              ("planar10k", "lifted", 64), ("planar1k", "lifted", 32), ("planar10k", "hykkt", 32),
              ("planar80k", "lifted", 64), ("planar80k", "hykkt", 32),
-             ("planar10k-flow", "hykkt", 64), ("planar10k-flow", "lifted", 64)]
+             ("planar10k-flow", "hykkt", 64), ("planar10k-flow", "lifted", 64),
+             # the branch-flow formulation at 80,000 buses: n = 608,000 and m = 784,001, the size
+             # of the paper's largest instance (78484epigrids: n = 674,562, m = 1,039,062)
+             ("planar80k-flow", "hykkt", 64), ("planar80k-flow", "regularized", 64)]
     warm = cp.ipm_solve_opf(cp.Opf(config_grid("ring30")), kkt="hykkt")
     del warm
     for name, kkt, prec in cases:
@@ -938,8 +941,9 @@ def ipm_measure():
         opf = cp.Opf(g, form="flow" if name.endswith("-flow") else "compact")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        # the 80,000-bus HyKKT case is the large configuration: gamma = 1e7, FP32 factor
-        gam = 1e7 if name == "planar80k" else 1e6
+        # the 80,000-bus cases are the large configuration: gamma = 1e7 (and, compact HyKKT, the
+        # FP32 factor requested)
+        gam = 1e7 if name.startswith("planar80k") else 1e6
         sizes = {"n": opf.n, "m_e": opf.m_e, "m_i": opf.m_i}
         st = cp.IpmState(opf, kkt=kkt, gamma=gam, precision=prec)
         torch.cuda.synchronize()
@@ -960,7 +964,7 @@ def ipm_measure():
                "cg_iters": int(sum(h.cg_iters for h in hist)),
                "fp32_iters": int(sum(1 for h in hist if h.precision == 32)), "gamma": gam,
                **sizes}
-        if name == "planar80k":
+        if name.startswith("planar80k"):
             # per iteration: factor precision, delta_w and the backward error of the augmented
             # system that the library computed for the step's KKT solve (every one of these solves
             # is checked against the oracle's own evaluation in the GPU tests at this size)

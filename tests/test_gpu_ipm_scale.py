@@ -133,3 +133,21 @@ def test_full_ipm_80k_lifted_fp32_every_solve_checked():
     prec = [r["precision"] for r in rows]
     assert all(a <= b for a, b in zip(prec, prec[1:]))   # FP32 only before FP64
     assert abs(st.objective() - ref["obj"]) <= 1e-6 * abs(ref["obj"])
+
+
+def test_flow_formulation_80k_converges_in_both_condensed_forms():
+    """The branch-flow formulation of the 80,000-bus grid (n = 608,000, m_e = 576,001,
+    m_i = 208,000: the size of the paper's largest instance) solved by HyKKT (gamma = 1e7) and by
+    the dual-regularized form: both converge to the 1e-6 tolerance at the same objective (the
+    oracle's run at this size takes hours; the flow form is checked against the oracle at 1,000
+    buses in test_gpu_flow.py)."""
+    g = config_grid("planar80k")
+    objs = []
+    for kkt in ("hykkt", "regularized"):
+        opf = cp.Opf(g, form="flow")
+        assert (opf.n, opf.m_e, opf.m_i) == (2 * g.nb + 2 * g.ng + 4 * len(g.f_bus),
+                                             2 * g.nb + 1 + 4 * len(g.f_bus), 2 * len(g.f_bus))
+        res = cp.ipm_solve_opf(opf, kkt=kkt, gamma=1e7)
+        assert res["status"] == 1, (kkt, res["history"][-1])
+        objs.append(res["obj"])
+    assert abs(objs[0] - objs[1]) <= 1e-6 * abs(objs[0]), objs
