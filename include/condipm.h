@@ -176,6 +176,15 @@ int ipm_set_spin_limit(long long polls);
  * without any fault).  Destroy the symbolic handle afterwards. */
 int ipm_debug_add_dependency(ipm_sym_t sym, int supernode, int extra);
 
+/* Debugging aid: while on (nonzero), every floating-point device buffer that the KKT and IPM
+ * entry points allocate afterwards (symbolic, numeric, OPF, IPM-state and batch handles, their
+ * temporaries, the batch's instance pool) starts filled with bytes 0xFF, a NaN in FP64 and FP32,
+ * instead of undefined contents (or zeros, for the batch pool), so that any entry a kernel reads
+ * before writing it shows up as NaN in the results.  Integer buffers and the MLP's (zeroed)
+ * buffers are left as they are.  Process-wide, off by default; costs one memset per
+ * allocation.  Always IPM_OK. */
+int ipm_debug_poison_allocations(int on);
+
 /* ipm_solve — x = K^{-1} b with the factor: y = P b, L z = y, L^T w = z, x = P^T w.
  *   b [n x nrhs], x [n x nrhs] device, column-major with leading dimension n (x may alias b);
  *   nrhs >= 1 right-hand sides, solved one after another in stream order. */

@@ -41,6 +41,7 @@ _SIGS = {
     "ipm_num_info": (I, [P, P, P]),
     "ipm_set_spin_limit": (I, [ctypes.c_longlong]),
     "ipm_debug_add_dependency": (I, [P, I, I]),
+    "ipm_debug_poison_allocations": (I, [I]),
     "ipm_condense": (I, [P, P, P, P, P, P, D, P]),
     "ipm_factor": (I, [P, P, P, P]),
     "ipm_solve": (I, [P, P, P, P, I, P]),
@@ -254,6 +255,11 @@ def ipm_num_status(num):
 
 def ipm_set_spin_limit(polls):
     return _check(lib().ipm_set_spin_limit(int(polls)), "ipm_set_spin_limit")
+
+
+def ipm_debug_poison_allocations(on=True):
+    """While on, floating-point buffers the library allocates start as NaN (debugging aid)."""
+    return _check(lib().ipm_debug_poison_allocations(int(bool(on))), "ipm_debug_poison_allocations")
 
 
 def ipm_debug_add_dependency(sym, supernode, extra=1):

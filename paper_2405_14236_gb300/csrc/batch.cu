@@ -2692,7 +2692,8 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     set_error_msg("ipm_batch_create: out of device memory for the instance pool");
     return fail(IPM_ERR_OOM);
   }
-  if (cudaMemset(B->dpool, 0, sizeof(double) * B->dpool_len) != cudaSuccess ||
+  if (cudaMemset(B->dpool, poison_allocations() ? 0xFF : 0, sizeof(double) * B->dpool_len) !=
+          cudaSuccess ||
       cudaMemset(B->ipool, 0, sizeof(int) * B->ipool_len) != cudaSuccess)
     return fail(IPM_ERR_CUDA);
   // ---- descriptors, task-argument blocks and ticket ranges

@@ -9,6 +9,9 @@ namespace cipm {
 static std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+static std::atomic<int> g_poison{0};
+bool poison_allocations() { return g_poison.load(std::memory_order_relaxed) != 0; }
+
 static std::mutex g_err_mu;
 static std::string g_err;
 
@@ -144,6 +147,11 @@ int inclusive_max_scan_i32(const int *in, int *out, int64_t n, cudaStream_t s) {
 }  // namespace cipm
 
 extern "C" long long ipm_launch_count(void) { return cipm::g_launches.load(); }
+
+extern "C" int ipm_debug_poison_allocations(int on) {
+  cipm::g_poison.store(on ? 1 : 0);
+  return IPM_OK;
+}
 
 extern "C" const char *ipm_last_error_message(void) {
   std::lock_guard<std::mutex> lk(cipm::g_err_mu);

@@ -5,6 +5,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/condipm.h"
@@ -15,6 +16,13 @@ namespace cipm {
 void set_error(const char *where, cudaError_t e);
 // Counts kernel launches issued by the numeric entry points (reported by ipm_launch_count).
 void count_launches(long long k);
+// ipm_debug_poison_allocations: floating-point buffers start as NaN (bytes 0xFF) while set
+bool poison_allocations();
+template <typename T>
+inline void poison_fresh(T *p, int64_t count) {
+  if (std::is_floating_point<T>::value && poison_allocations())
+    cudaMemset(p, 0xFF, sizeof(T) * (size_t)count);
+}
 void set_error_msg(const std::string &msg);
 
 #define CK(call)                              \
@@ -58,6 +66,7 @@ struct DevTemp {
       set_error("cudaMalloc(temp)", e);
       return IPM_ERR_OOM;
     }
+    poison_fresh(*p, count);
     ptrs.push_back(*p);
     return IPM_OK;
   }
@@ -72,6 +81,7 @@ int dev_alloc(T **p, int64_t count) {
     set_error("cudaMalloc", e);
     return IPM_ERR_OOM;
   }
+  poison_fresh(*p, count);
   return IPM_OK;
 }
 

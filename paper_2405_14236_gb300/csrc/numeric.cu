@@ -49,11 +49,14 @@ extern "C" int ipm_num_create(ipm_sym_t S, int precision, ipm_num_t *out) {
   auto bytes = [&](void **p, int64_t count) {
     if (rc == IPM_OK && cudaMalloc(p, es * (size_t)std::max<int64_t>(count, 1)) != cudaSuccess)
       rc = IPM_ERR_OOM;
+    if (rc == IPM_OK && poison_allocations())
+      cudaMemset(*p, 0xFF, es * (size_t)std::max<int64_t>(count, 1));
   };
   bytes(&N->Lx, S->panel_len);
   bytes(&N->Dx, S->diag_len);
   if (rc == IPM_OK && cudaMalloc(&N->tJ, sizeof(double) * (size_t)std::max(S->nnzJ, 1)) != cudaSuccess)
     rc = IPM_ERR_OOM;
+  if (rc == IPM_OK) poison_fresh((double *)N->tJ, std::max(S->nnzJ, 1));
   if (rc == IPM_OK) rc = dev_alloc(&N->sync, 4 * (int64_t)S->nsuper + 16);
   if (rc == IPM_OK && cudaMemset(N->sync, 0, sizeof(int) * (4 * (size_t)S->nsuper + 16)) != cudaSuccess)
     rc = IPM_ERR_CUDA;
