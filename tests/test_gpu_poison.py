@@ -1,8 +1,8 @@
 """No kernel reads a floating-point entry before writing it: with ipm_debug_poison_allocations on,
 every floating-point buffer the library allocates starts as NaN, and the solves must still
 converge to the objective they reach from ordinary allocations (single-problem IPM in both
-formulations and every KKT form, FP32 factor included; the batched IPM in every form, before and
-after a reset).  A read of an unwritten entry would carry NaN into the iterates."""
+formulations and every KKT form, FP32 factor included; the batched IPM, both formulations in one
+batch, in every form, before and after a reset).  A read of an unwritten entry would carry NaN into the iterates."""
 import numpy as np
 import pytest
 
@@ -52,13 +52,17 @@ def test_batch_ignores_initial_buffer_contents(kkt, prec, poisoned):
     base = config_grid("planar1k")
     grids = ([scale_loads(base, 1000 + k) for k in range(3)] +
              [mixed_grid(2000 + k) for k in (3, 9)] + [config_grid("ring30")])
+    # the last two instances in the branch-flow formulation
+    forms = ["compact"] * len(grids) + ["flow", "flow"]
+    grids += [scale_loads(base, 1003), config_grid("ring30")]
+    opfs = lambda: [cp.Opf(g, form=f) for g, f in zip(grids, forms)]
     cp.ipm_debug_poison_allocations(False)
-    R = cp.Batch([cp.Opf(g) for g in grids], kkt=kkt, gamma=1e6, precision=prec)
+    R = cp.Batch(opfs(), kkt=kkt, gamma=1e6, precision=prec)
     R.run(max_iter=200)
     ref = R.results()
     del R
     cp.ipm_debug_poison_allocations(True)
-    B = cp.Batch([cp.Opf(g) for g in grids], kkt=kkt, gamma=1e6, precision=prec)
+    B = cp.Batch(opfs(), kkt=kkt, gamma=1e6, precision=prec)
     for rnd in range(2):
         if rnd:
             B.reset()   # the second run starts from the first run's leftovers
