@@ -2522,6 +2522,15 @@ int capture_sweep(ipm_batch_t B, bool tail, cudaGraph_t *graph, cudaGraphExec_t 
   return rc;
 }
 
+// The host-side set-up of this file (shapes, orders, pause point) copies into device memory
+// with the synchronous copy calls, which run on the legacy default stream and may return before
+// the data lands: work on the batch's stream waits for them first.
+int after_host_copies(ipm_batch_t B) {
+  if (B->stream != cudaStreamLegacy && B->stream != nullptr)
+    CK(cudaStreamSynchronize(cudaStreamLegacy));
+  return IPM_OK;
+}
+
 // starting point, scaling and multipliers of every instance (Ipopt: see ipm_state_create)
 int init_instances(ipm_batch_t B) {
   const int C = B->count;
@@ -2580,6 +2589,9 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
     }
   *out = nullptr;
   CKR(b_smem_limits());
+  // creation runs on the set-up stream; the sweeps on the caller's
+  const cudaStream_t caller = stream;
+  stream = setup_stream(stream);
   ipm_batch_t B = new ipm_batch_s();
   auto fail = [&](int rc) {
     ipm_batch_destroy(B);
@@ -2988,6 +3000,7 @@ extern "C" int ipm_batch_create(int count, const ipm_opf_t *opfs, const ipm_opti
   rc = init_instances(B);
   if (rc == IPM_OK && cudaStreamSynchronize(stream) != cudaSuccess) rc = IPM_ERR_CUDA;
   if (rc != IPM_OK) return fail(rc);
+  B->stream = caller;
   *out = B;
   return IPM_OK;
 }
@@ -3004,6 +3017,7 @@ extern "C" int ipm_batch_info(ipm_batch_t B, int *npatterns, int64_t *device_byt
 
 extern "C" int ipm_batch_reset(ipm_batch_t B) {
   if (!B) return IPM_ERR_BAD_ARG;
+  CKR(after_host_copies(B));
   CKR(init_instances(B));
   B->sweeps = 0;
   B->t_fact_ms = B->t_solve_ms = 0.0;
@@ -3015,6 +3029,7 @@ extern "C" int ipm_batch_run(ipm_batch_t B, int max_iter, int max_sweeps, int us
   NvtxRange nvtx_range("ipm_batch_run");
   if (!B || max_iter < 0 || max_sweeps < 1) return IPM_ERR_BAD_ARG;
   cudaStream_t s = B->stream;
+  CKR(after_host_copies(B));
   if (B->max_iter != max_iter) drop_graph(B);
   B->max_iter = max_iter;
   if (use_graph && !B->exec) CKR(capture_sweep(B, false, &B->graph, &B->exec));
@@ -3261,6 +3276,7 @@ extern "C" int ipm_batch_export_all(ipm_batch_t B, double *x_host) {
     CK(cudaMemcpy(B->x_stage + B->x_total, B->x_off.data(), sizeof(int64_t) * (B->count + 1),
                   cudaMemcpyHostToDevice));
   }
+  CKR(after_host_copies(B));
   k_b_gather_x<<<dim3(B->gx, B->count), B_BLOCK, 0, B->stream>>>(
       B->d_bi, (const int64_t *)(B->x_stage + B->x_total), B->x_stage);
   count_launches(1);
@@ -3330,6 +3346,7 @@ extern "C" int ipm_batch_pause_at(ipm_batch_t B, int k) {
 
 extern "C" int ipm_batch_resume(ipm_batch_t B) {
   if (!B) return IPM_ERR_BAD_ARG;
+  CKR(after_host_copies(B));
   k_b_resume<<<grid_for(B->count, 128), 128, 0, B->stream>>>(B->d_ctl, B->count);
   count_launches(1);
   CKL();

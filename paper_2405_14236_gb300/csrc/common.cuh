@@ -16,12 +16,23 @@ namespace cipm {
 void set_error(const char *where, cudaError_t e);
 // Counts kernel launches issued by the numeric entry points (reported by ipm_launch_count).
 void count_launches(long long k);
+// Set-up entry points (symbolic analysis, model and IPM-state creation) copy between host and
+// device with the synchronous copy calls, which run on the legacy default stream, between their
+// kernels.  They run all of their device work there: after the caller's stream's earlier work
+// (their inputs may come from it), and complete on return.  Returns the stream to use.
+inline cudaStream_t setup_stream(cudaStream_t caller) {
+  cudaStreamSynchronize(caller);
+  return cudaStreamLegacy;
+}
+
 // ipm_debug_poison_allocations: floating-point buffers start as NaN (bytes 0xFF) while set
 bool poison_allocations();
 template <typename T>
 inline void poison_fresh(T *p, int64_t count) {
-  if (std::is_floating_point<T>::value && poison_allocations())
+  if (std::is_floating_point<T>::value && poison_allocations()) {
     cudaMemset(p, 0xFF, sizeof(T) * (size_t)count);
+    cudaDeviceSynchronize();  // before any stream's work on the buffer
+  }
 }
 void set_error_msg(const std::string &msg);
 

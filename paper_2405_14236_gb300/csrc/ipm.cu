@@ -424,6 +424,9 @@ static int state_create(ipm_opf_t opf, const ipm_options *opt, const double *x0_
     return IPM_ERR_BAD_ARG;
   }
   *out = nullptr;
+  // creation runs on the set-up stream; the iterations on the caller's
+  const cudaStream_t caller = stream;
+  stream = setup_stream(stream);
   ipm_state_t S = new ipm_state_s();
   S->opf = opf;
   S->opt = *opt;
@@ -492,8 +495,7 @@ static int state_create(ipm_opf_t opf, const ipm_options *opt, const double *x0_
   if (rc == IPM_OK) {
     // starting point, objective scaling and row scaling at x0 (Ipopt gradient-based scaling)
     cudaStream_t s = stream;
-    double zero = 0.0;
-    for (int k = 0; k < R_COUNT; ++k) cudaMemcpy(S->R + k, &zero, sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemsetAsync(S->R, 0, sizeof(double) * R_COUNT, s) != cudaSuccess) rc = IPM_ERR_CUDA;
     if (x0_host) {
       // the caller's point, pushed inside the bounds
       if (cudaMemcpyAsync(S->P.x, x0_host, sizeof(double) * n, cudaMemcpyHostToDevice, s) !=
@@ -529,6 +531,7 @@ static int state_create(ipm_opf_t opf, const ipm_options *opt, const double *x0_
     ipm_state_destroy(S);
     return rc;
   }
+  S->stream = caller;
   *out = S;
   return IPM_OK;
 }
@@ -699,7 +702,8 @@ static int resto_step(ipm_state_t S, ipm_iter_info *info) {
   if (dw > 0) S->delta_last_r = dw;
   info->delta_w = dw;
   info->n_factor = nfac;
-  CK(cudaMemcpy(&info->eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&info->eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   k_jv<<<grid1(m), 256, 0, s>>>(m, M.J_rowptr, M.J_colind, S->Jv, S->dx, S->jdx);
   k_resto_recover<<<grid1(nr), 256, 0, s>>>(rargs(S, dw));
   CKL();
@@ -786,7 +790,8 @@ static int step_impl(ipm_state_t S, ipm_iter_info *info) {
     S->have_theta0 = true;
   }
   double fval = 0.0;
-  CK(cudaMemcpy(&fval, S->f, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&fval, S->f, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   info->kkt_err = e0;
   info->obj = fval;
   info->mu = S->mu;
@@ -926,8 +931,9 @@ retry_solve:
   if (S->opt.kkt != 1) {
     double eta = 0;
     int steps = 0;
-    CK(cudaMemcpy(&eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&steps, S->steps, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(&eta, S->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&steps, S->steps, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     info->eta = eta;
     info->refine_steps = steps;
     if (D.lifted) {
@@ -1030,7 +1036,10 @@ extern "C" int ipm_step(ipm_state_t S, ipm_iter_info *info) {
 
 extern "C" int ipm_state_export(ipm_state_t S, double *x, double *obj) {
   if (!S) return IPM_ERR_BAD_ARG;
-  if (x) CK(cudaMemcpy(x, S->P.x, sizeof(double) * S->D.n, cudaMemcpyDeviceToHost));
+  if (x) {
+    CK(cudaMemcpyAsync(x, S->P.x, sizeof(double) * S->D.n, cudaMemcpyDeviceToHost, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+  }
   if (obj) {
     CKR(opf_eval(S->opf->M, S->P.x, nullptr, nullptr, 1.0, S->ft, nullptr, S->gst, S->hst,
                  nullptr, nullptr, S->stream));
@@ -1117,9 +1126,11 @@ extern "C" int ipm_state_load(ipm_state_t S, const double *buf, int64_t len) {
   CK(cudaStreamSynchronize(S->stream));
   for (const auto &pt : parts) {
     if (pt.second > 0)
-      CK(cudaMemcpy(pt.first, o, sizeof(double) * pt.second, cudaMemcpyHostToDevice));
+      CK(cudaMemcpyAsync(pt.first, o, sizeof(double) * pt.second, cudaMemcpyHostToDevice,
+                         S->stream));
     o += pt.second;
   }
+  CK(cudaStreamSynchronize(S->stream));
   // a state saved after its FP32 factor had stopped serving goes on in FP64
   if (buf[15] == 0.0 && S->num32) {
     ipm_num_destroy(S->num32);

@@ -174,7 +174,8 @@ static int build_pattern(bool isJ, const OpfDims &D, const OpfData &M, int nrows
   CKL();
   CKR(dev_alloc(rowptr, nrows + 1));
   CKR(exclusive_scan_i32(ucnt, *rowptr, nrows, s));
-  CK(cudaMemcpy(nnz, *rowptr + nrows, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(nnz, *rowptr + nrows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   CKR(dev_alloc(colind, *nnz));
   k_row_compact<<<nrows, 64, 0, s>>>(nrows, ptr, cand, *rowptr, *colind);
   CKL();
@@ -311,8 +312,11 @@ int opf_create(OpfData &M, int nb, int nbr, int ng, const int *f_bus, const int 
   CKR(up(M.xu, xu, sizeof(double) * nc));
   if (n > nc) {  // flow variables are free
     std::vector<double> lo(n - nc, -INFINITY), hi(n - nc, INFINITY);
-    CK(cudaMemcpy(M.xl + nc, lo.data(), sizeof(double) * (n - nc), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(M.xu + nc, hi.data(), sizeof(double) * (n - nc), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(M.xl + nc, lo.data(), sizeof(double) * (n - nc), cudaMemcpyHostToDevice,
+                       s));
+    CK(cudaMemcpyAsync(M.xu + nc, hi.data(), sizeof(double) * (n - nc), cudaMemcpyHostToDevice,
+                       s));
+    CK(cudaStreamSynchronize(s));  // lo and hi end with this block
   }
   M.ref = gen_bus[0];
   if (nbr > 0) {
@@ -377,6 +381,7 @@ static int opf_create_form(int form, int nb, int nbr, int ng, const int *f_bus,
       return IPM_ERR_BAD_ARG;
     }
   *out = nullptr;
+  s = setup_stream(s);
   ipm_opf_t P = new ipm_opf_s();
   int rc = opf_create(P->M, nb, nbr, ng, f_bus, t_bus, r, x, b, rate, pd, qd, gen_bus, c2, c1, xl,
                       xu, s, form);
@@ -407,6 +412,8 @@ extern "C" int ipm_opf_patterns(ipm_opf_t P, int *J_rowptr, int *J_colind, int *
   if (J_colind) CK(cudaMemcpy(J_colind, M.J_colind, sizeof(int) * M.nnzJ, cudaMemcpyDefault));
   if (W_rowptr) CK(cudaMemcpy(W_rowptr, M.W_rowptr, sizeof(int) * (M.n + 1), cudaMemcpyDefault));
   if (W_colind) CK(cudaMemcpy(W_colind, M.W_colind, sizeof(int) * M.nnzW, cudaMemcpyDefault));
+  // device-to-device copies may return before they land: done before any stream reads them
+  CK(cudaStreamSynchronize(cudaStreamLegacy));
   return IPM_OK;
 }
 

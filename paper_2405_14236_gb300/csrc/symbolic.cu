@@ -1220,6 +1220,7 @@ extern "C" int ipm_symbolic_relaxed(int n, int m, const int *J_rowptr, const int
     return IPM_ERR_BAD_ARG;
   }
   *out = nullptr;
+  stream = setup_stream(stream);
   ipm_sym_t S = new ipm_sym_s();
   S->relax_w = relax_w;
   S->relax_den = relax_den;
@@ -1228,8 +1229,8 @@ extern "C" int ipm_symbolic_relaxed(int n, int m, const int *J_rowptr, const int
   S->nnzJ = nnzJ;
   S->nnzW = nnzW;
   int rc = symbolic_impl(S, J_rowptr, J_colind, W_rowptr, W_colind, stream);
+  if (cudaStreamSynchronize(stream) != cudaSuccess && rc == IPM_OK) rc = IPM_ERR_CUDA;
   if (rc != IPM_OK) {
-    cudaStreamSynchronize(stream);
     free_sym(S);
     return rc;
   }
