@@ -7,8 +7,12 @@
  *  - Pointers are DEVICE pointers owned by the caller unless the argument says "host".
  *    The library never frees or keeps caller pointers beyond the call.
  *  - Index arrays are int32, CSR row pointers are int32 (nnz < 2^31), values FP64.
- *  - Work is ordered on the given cudaStream_t (0 = legacy default stream).  Calls do not
- *    synchronize the stream unless stated ("synchronizes").
+ *  - Work is ordered on the given cudaStream_t (0 = legacy default stream; blocking and
+ *    non-blocking streams both work).  Calls do not synchronize the stream unless stated
+ *    ("synchronizes").  The set-up calls (ipm_opf_create*, ipm_symbolic*, ipm_state_create*,
+ *    ipm_batch_create) wait for the given stream's earlier work, run their own device work on
+ *    the legacy default stream and return with it finished; the handles they create then work
+ *    on the stream given at creation (IPM state, batch) or at each call.
  *  - Library-owned state lives in opaque handles; all their device memory is allocated by
  *    the *_create / ipm_symbolic calls and released by *_destroy.  The numeric calls
  *    (ipm_condense, ipm_factor, ipm_solve, ipm_aug_solve, hykkt_cg) allocate nothing.
